@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark: s-step BDCD for kernel ridge regression on one GB300.
+
+Workload (default): dense K-RR, m = 50000 samples, n = 512 features, A ~
+N(0,1)/sqrt(n) stored FP32, y = sin(A w) + 0.1 N(0,1), RBF with bandwidth
+sigma = 1 (gamma = 1/(2 sigma^2) = 0.5), lambda = 1e-4, block size b = 16,
+s = 16 inner steps per outer step, bf16 tensor-core kernel block with FP64
+recurrence and gradient accumulation.  Synthetic data stand in for the
+paper's LIBSVM sets.
+
+One "step" is one outer s-step (sample, gather, Gram, FP64 recurrence, fused
+kernel-block gradient update, alpha update) = s*b coordinate updates.  The
+metric is coordinate updates per second.  L2 (129 MB) could hold the 51 MB
+bf16 operand, so a buffer larger than L2 is written before every timed step
+and each step is timed alone with CUDA events on the solver's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--prec bf16|tf32|fp64]
+  python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coordinate updates/s and time-to-duality-gap 1e-6 (mixed vs FP64 s=1, 1 GB300)"
+UNIT = "coordinate updates/s"
+WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained"), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_problem(m, n, seed=0):
+    from paper_2406_18001_gb300 import inputs
+    return inputs.krr_dense(m=m, n=n, seed=seed, dtype=np.float32)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------- reference ----
+def run_reference(args):
+    """The FP64 CPU oracle (s-step BDCD, Algorithm 4 as printed) timed on the
+    host.  Each step is one block update of the workload restricted to its
+    first m_sub rows, m_sub sized so the whole run stays within ~150 s; the
+    rate is scaled to the full m (the oracle's cost per update is linear in
+    m)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = make_problem(args.m, args.n)
+    A64 = p.A.astype(np.float64)
+    k = oracle.kernel("rbf", gamma=args.gamma)
+    cal = min(args.m, 2000)
+    t0 = time.perf_counter()
+    oracle.sstep_bdcd_krr(A64[:cal], p.y[:cal], k, args.lam, args.b, 1, 1, seed=0)
+    per_row = (time.perf_counter() - t0) / cal
+    budget = 150.0 / (args.steps + args.warmup)
+    m_sub = int(max(args.b, min(args.m, budget / max(per_row, 1e-9))))
+    As, ys = np.ascontiguousarray(A64[:m_sub]), p.y[:m_sub].copy()
+    alpha = np.zeros(m_sub)
+    for w in range(args.warmup):
+        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, 1, 1, seed=0, first_block=w, alpha0=alpha)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, 1, 1, seed=0, first_block=args.warmup + i,
+                                      alpha0=alpha)
+    dt = time.perf_counter() - t0
+    v = args.steps * args.b / dt * (m_sub / args.m)
+    sample = (f"{args.steps} BDCD block updates (b={args.b}) on the first {m_sub} of {args.m} rows "
+              f"(n={args.n}), rate scaled by {m_sub}/{args.m}; plain FP64 C, one thread")
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "s": 1, "b": args.b, "m": args.m, "n": args.n, "m_sample": m_sub},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(args, budget_s=12.0):
+    """Oracle throughput on a bounded sample (block updates of the same
+    workload until ~budget_s of CPU work)."""
+    import oracle
+    p = make_problem(args.m, args.n)
+    A64 = p.A.astype(np.float64)
+    k = oracle.kernel("rbf", gamma=args.gamma)
+    oracle.build()
+    alpha = np.zeros(args.m)
+    t0 = time.perf_counter()
+    blocks = 0
+    while time.perf_counter() - t0 < budget_s and blocks < 64:
+        alpha = oracle.sstep_bdcd_krr(A64, p.y, k, args.lam, args.b, 1, 1, seed=0, first_block=blocks,
+                                      alpha0=alpha)
+        blocks += 1
+    dt = time.perf_counter() - t0
+    return {"value": blocks * args.b / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{blocks} BDCD block updates (b={args.b}) of the full {args.m}x{args.n} workload "
+                      f"({dt:.1f} s, plain FP64 C, one thread)"}
+
+
+# ---------------------------------------------------------------- GPU -----
+def run_gpu(args):
+    import torch
+    from paper_2406_18001_gb300 import binding as B
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p = make_problem(args.m, args.n, seed=rank)
+    A = torch.from_numpy(p.A).to(dev)
+    y = torch.from_numpy(p.y).to(dev)
+    k = B.kernel("rbf", gamma=args.gamma)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    upd_per_step = args.s * args.b
+    H = (args.warmup + args.steps + 8) * args.s
+    plan = B.Plan(1, A, y, k, args.lam, args.b, args.s, H, seed=rank, prec=args.prec)
+    for _ in range(args.warmup):
+        plan.run(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            plan.run(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_steps = sorted(a.elapsed_time(b) for a, b in ev)
+    st, _ = plan.run(0)
+    launches = st["gpu_launches_per_step"] * args.steps
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # dominant kernel (fused kernel block) duration, measured live: per-phase
+    # CUDA events on the solver's stream, L2 flushed before every step
+    plan2 = B.Plan(1, A, y, k, args.lam, args.b, args.s, (args.roof_steps + 4) * args.s, seed=rank + 1,
+                   prec=args.prec, flags=B.FLAG_PHASE_TIMERS)
+    plan2.run(2)
+    base, _ = plan2.run(0)
+    for _ in range(args.roof_steps):
+        flush.zero_()
+        plan2.run(1)
+    st2, _ = plan2.run(0)
+    plan2.close()
+    nsteps2 = args.roof_steps
+    phase = {ph: (st2[f"ms_{ph}"] - base[f"ms_{ph}"]) / nsteps2 for ph in
+             ("sample", "gram", "recur", "block", "update")}
+    t_block = phase["block"] * 1e-3
+    hbm_peak, bf16_peak, bf16_sus, src = peaks()
+    sb = args.s * args.b
+    esz = 2 if args.prec == "bf16" else (4 if args.prec == "tf32" else 8)
+    n_alg = args.n
+    flops = 2.0 * args.m * n_alg * sb
+    bytes_ = args.m * n_alg * esz + sb * n_alg * esz + args.m * (8 + 8 + 4)
+    intensity = flops / bytes_
+    ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
+    if args.prec == "bf16" and intensity >= ridge:
+        roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = args.traffic
+    roof["peak_source"] = src
+    roof["kernel"] = "block_tc_kernel (fused kernel block + gradient update)" if args.prec != "fp64" \
+        else "block_simt_f64_kernel"
+    roof["algorithmic"] = {"flops_per_launch": flops, "bytes_per_launch": bytes_, "launch_ms": phase["block"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    if True:
+        A_h = torch.from_numpy(p.A).pin_memory()
+        y_h = torch.from_numpy(p.y).pin_memory()
+        al_h = torch.zeros(args.m, dtype=torch.float64).pin_memory()
+        gr_h = torch.zeros(args.m, dtype=torch.float64).pin_memory()
+        Hh = args.steps * args.s
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.krr_solve(A_h.numpy(), y_h.numpy(), k, args.lam, args.b, args.s, Hh, seed=rank, prec=args.prec,
+                    alpha=al_h.numpy(), grad=gr_h.numpy(), flags=B.FLAG_HOST_IO,
+                    stream=torch.cuda.current_stream().cuda_stream)
+        dt = time.perf_counter() - t0
+        h2d = p.A.nbytes + p.y.nbytes + args.m * 8
+        d2h = args.m * 8 * 2
+        e2e = {"value": Hh * args.b / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps, "steps": args.steps, "wall_s": dt}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        value = ws * args.steps * upd_per_step / (ms * 1e-3)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+               "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "s": args.s, "b": args.b,
+                          "gamma": args.gamma, "lambda": args.lam, "precision": args.prec,
+                          "l2": "256 MB buffer written before every timed step; steps timed alone",
+                          "parallelism": "replicas" if ws > 1 else "single"},
+               "step_ms": {"min": ms_steps[0], "median": ms_steps[len(ms_steps) // 2], "max": ms_steps[-1]},
+               "phase_ms": phase,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=50000)
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--s", type=int, default=16)
+    ap.add_argument("--b", type=int, default=16)
+    ap.add_argument("--gamma", type=float, default=0.5)
+    ap.add_argument("--lam", type=float, default=1e-4)
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--roof-steps", type=int, default=50)
+    ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

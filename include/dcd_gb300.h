@@ -1,0 +1,204 @@
+/*
+ * dcd_gb300.h -- C ABI of the GB300 (sm_103a) s-step dual coordinate descent
+ * library: s-step DCD for the kernel SVM duals and s-step block DCD for kernel
+ * ridge regression, after "Scalable Dual Coordinate Descent for Kernel
+ * Methods" (arXiv 2406.18001).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the
+ *    opts flag DCD_FLAG_HOST_IO says the solve's arrays live in host memory.
+ *    The library never frees caller memory.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream).  Each call returns only after its work on
+ *    that stream has finished, so outputs are ready when it returns.
+ *  - Errors come back as a dcd_status, never as an abort or a device trap.
+ *    Device-side failures (an index out of range, a bounded wait that ran
+ *    out) are recorded in a device error word and turned into a status.
+ *  - The library allocates its scratch memory with cudaMallocAsync on
+ *    `stream` and frees it before returning.
+ *  - All indices are 0-based.  Dense matrices are row-major with leading
+ *    dimension ld >= n (elements).  CSR uses int64 row_ptr[m+1] and int32
+ *    col_idx[nnz] with values in `dtype`.
+ */
+#ifndef DCD_GB300_H
+#define DCD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DCD_OK = 0,
+    DCD_EINVAL = 1,       /* an argument failed validation */
+    DCD_ENOMEM = 2,       /* device allocation failed */
+    DCD_ECUDA = 3,        /* a CUDA runtime call failed */
+    DCD_ETIMEOUT = 4,     /* a bounded device wait ran out (kernel returned early) */
+    DCD_ENOTCONV = 5,     /* iteration budget used before reaching opts.tol; alpha is valid */
+    DCD_EINTERNAL = 6,    /* a device-side consistency check failed */
+    DCD_ENOTSPD = 7,      /* a b x b block system G was not positive definite */
+    DCD_EUNSUPPORTED = 8  /* valid request this build does not implement */
+} dcd_status;
+
+typedef enum { DCD_DENSE = 0, DCD_CSR = 1 } dcd_format;
+typedef enum { DCD_F64 = 0, DCD_F32 = 1, DCD_BF16 = 2, DCD_FP8E4M3 = 3 } dcd_dtype;
+
+/* The data matrix A (m x n), paper Section 3: rows a_i are samples. */
+typedef struct {
+    int32_t fmt;              /* dcd_format */
+    int32_t dtype;            /* dcd_dtype of values */
+    int64_t m, n;             /* rows (samples) and columns (features) */
+    int64_t ld;               /* dense: leading dimension in elements, >= n */
+    const void *values;       /* dense: m*ld elements; CSR: nnz elements */
+    const int64_t *row_ptr;   /* CSR only: m+1 offsets, row_ptr[0] = 0, non-decreasing */
+    const int32_t *col_idx;   /* CSR only: nnz column indices in [0, n) */
+    const float *row_scale;   /* FP8 only: a_i = row_scale[i] * q_i; else NULL */
+} dcd_matrix;
+
+/* Kernel functions of Table 1 (Section 3.1). */
+typedef enum { DCD_LINEAR = 0, DCD_POLY = 1, DCD_RBF = 2 } dcd_kernel_kind;
+typedef struct {
+    int32_t kind;    /* dcd_kernel_kind */
+    int32_t degree;  /* POLY: (coef0 + a.b)^degree, degree >= 2 */
+    double gamma;    /* RBF: exp(-gamma * ||a - b||^2), gamma > 0 (the paper's sigma) */
+    double coef0;    /* POLY: coef0 >= 0 */
+} dcd_kernel;
+
+/* Arithmetic used for the m x (s*b) kernel block.  The s-step recurrence,
+ * the b x b solves and the alpha / gradient accumulation are FP64 in every
+ * mode. */
+typedef enum {
+    DCD_PREC_FP64 = 0,   /* FP64 CUDA-core block, direct RBF distances */
+    DCD_PREC_TF32 = 1,   /* tcgen05 kind::tf32 block, FP32 accumulation */
+    DCD_PREC_BF16 = 2,   /* tcgen05 kind::f16 (bf16) block, FP32 accumulation */
+    DCD_PREC_FP8 = 3,    /* reserved */
+    DCD_PREC_BF16X3 = 4  /* reserved */
+} dcd_precision;
+
+/* opts.flags */
+#define DCD_FLAG_GRAD_VALID 0x1   /* `grad` holds the gradient of `alpha` on entry */
+#define DCD_FLAG_HOST_IO 0x2      /* A.values/row_ptr/col_idx, y, alpha, grad are host memory */
+#define DCD_FLAG_PHASE_TIMERS 0x4 /* fill the per-phase times of dcd_stats (adds one sync per step) */
+#define DCD_FLAG_NO_GRAPH 0x8     /* launch every kernel directly instead of replaying CUDA graphs */
+
+typedef struct {
+    int32_t s;            /* inner steps per outer step, s >= 1 (Algorithms 2 and 4) */
+    int32_t b;            /* block size, 1 <= b <= min(m, 128); DCD requires b = 1 */
+    int64_t max_iters;    /* H: coordinate updates (DCD) or block updates (BDCD), >= 0 */
+    uint64_t seed;        /* index-stream seed */
+    uint64_t start_iter;  /* stream position of the first inner iteration (resume) */
+    double tol;           /* stop once the relative duality gap (K-SVM) or relative
+                             residual ||g||/||y|| (K-RR) is <= tol; 0 runs all H */
+    int32_t check_every;  /* outer steps between convergence checks (0: only at the end) */
+    int32_t prec;         /* dcd_precision */
+    int32_t flags;        /* DCD_FLAG_* */
+    int32_t reserved;
+} dcd_opts;
+
+typedef struct {
+    int64_t iters_done;       /* inner iterations performed */
+    int64_t outer_steps;      /* outer s-steps performed */
+    int32_t converged;        /* 1 if the tolerance was met */
+    int32_t gpu_launches_per_step; /* kernels one outer step launches */
+    double final_metric;      /* relative gap (K-SVM) or relative residual (K-RR); NaN after a
+                                 dcd_plan_run that neither reached a check point nor the budget end */
+    double primal, dual;      /* K-SVM: P and D at the final alpha (from the cached gradient) */
+    double ms_total;          /* wall time of the call, device-timed */
+    double ms_setup, ms_sample, ms_gram, ms_recur, ms_block, ms_update, ms_check;
+} dcd_stats;
+
+/*
+ * s-step DCD for the kernel SVM dual (Algorithm 2; s = 1 is Algorithm 1).
+ *   min_a 1/2 a^T Q a - 1^T a [+ ||a||^2/(4C) for loss 2],  Q = diag(y) K diag(y),
+ *   0 <= a_i <= C (loss 1, hinge) or a_i >= 0 (loss 2, squared hinge).
+ * y: m labels, each +1 or -1.  alpha: m values, alpha_0 in, alpha_H out.
+ * grad: NULL, or m values of g = Q a - 1 + omega a (omega = 1/(2C) for loss 2,
+ * else 0): input when DCD_FLAG_GRAD_VALID, always written on return (with
+ * device io the solver keeps its cached gradient in this array).
+ * Iteration t of the index stream uses coordinate floor(u_t * m / 2^64) with
+ * u_t the SplitMix64 draw (seed, stream 0, counter t).
+ * Returns DCD_EINVAL for b != 1, C <= 0, labels not +-1, bad kernel
+ * parameters or shapes.  st may be NULL.
+ */
+dcd_status dcd_svm_solve(const dcd_matrix *A, const double *y, const dcd_kernel *k, int32_t loss,
+                         double C, const dcd_opts *o, double *alpha, double *grad, dcd_stats *st,
+                         void *stream);
+
+/*
+ * s-step block DCD for kernel ridge regression (Algorithm 4; s = 1 is
+ * Algorithm 3), eq. (krr-problem):
+ *   min_a 1/2 a^T (K/lambda + m I) a - y^T a.
+ * Block t of the index stream is a b-subset of [0, m) drawn by Floyd's
+ * algorithm from SplitMix64 stream t+1.  grad: NULL or m values of
+ * g = (K/lambda + m I) a - y, as for dcd_svm_solve.  lambda > 0.
+ */
+dcd_status bdcd_krr_solve(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda,
+                          const dcd_opts *o, double *alpha, double *grad, dcd_stats *st, void *stream);
+
+/*
+ * Persistent solves ("plans").  A plan validates the arguments, allocates the
+ * workspace, packs A and initialises the cached gradient once; dcd_plan_run
+ * then continues the same iteration for up to max_outer_steps outer steps
+ * (all remaining when < 0) and can be called repeatedly -- running a budget
+ * of H in pieces gives bit-identical iterates to one call.  alpha is updated
+ * in place (device io) or copied back to the caller's host array after every
+ * dcd_plan_run (DCD_FLAG_HOST_IO); grad, when non-NULL, likewise receives the
+ * cached gradient.  A, y, alpha and grad must stay valid until
+ * dcd_plan_destroy, which frees the workspace (stream-ordered) and
+ * synchronises the stream.  st receives cumulative statistics.
+ * dcd_plan_run returns DCD_ENOTCONV only once the budget H is exhausted with
+ * opts.tol > 0 not reached.  The solve entry points above are create + run
+ * all + destroy.
+ */
+typedef struct dcd_plan dcd_plan;
+dcd_status dcd_svm_plan_create(const dcd_matrix *A, const double *y, const dcd_kernel *k, int32_t loss, double C,
+                               const dcd_opts *o, double *alpha, double *grad, void *stream, dcd_plan **plan);
+dcd_status bdcd_krr_plan_create(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda,
+                                const dcd_opts *o, double *alpha, double *grad, void *stream, dcd_plan **plan);
+dcd_status dcd_plan_run(dcd_plan *plan, int64_t max_outer_steps, dcd_stats *st);
+dcd_status dcd_plan_destroy(dcd_plan *plan);
+
+/* Human-readable name of a status code (static string). */
+const char *dcd_status_string(int32_t status);
+
+/*
+ * Component entry points (one hot-path step each; used for testing and
+ * measurement).
+ *
+ * dcd_sample_indices -- step "sample" of Algorithms 2 and 4.
+ *   method 0 (DCD): out[j] = coordinate of iteration first+j, j < count.
+ *   method 1 (BDCD): out[j*b + q], q < b, = block first+j, j < count.
+ *   out: device int32, count (method 0) or count*b (method 1) entries.
+ */
+dcd_status dcd_sample_indices(int32_t method, uint64_t seed, int64_t m, int32_t b, uint64_t first,
+                              int64_t count, int32_t *out, void *stream);
+
+/*
+ * dcd_kernel_block -- the sampled kernel block U_k / Q_k of Algorithms 2 and
+ * 4: out[r*ldo + c] = K(a_rows[r], a_cols[c]) for r < nrows, c < ncols.
+ *   rows: device int32 indices, or NULL for rows 0..nrows-1.
+ *   cols: device int32 indices.  out: device float (prec != FP64) or double
+ *   (prec == FP64), ldo >= ncols.  Dense A only.
+ */
+dcd_status dcd_kernel_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
+                            int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,
+                            void *stream);
+
+/*
+ * dcd_kernel_block_apply -- the fused "kernel block times coefficients"
+ * update that closes every outer step (the gradient form of the alpha update
+ * in Algorithms 2 and 4), without storing the block:
+ *   g[i] += rowscale[i] * sum_{c < ncols} K(a_i, a_cols[c]) * w[c],  0 <= i < m.
+ *   cols: device int32 (ncols entries); w: device double; rowscale: device
+ *   double or NULL (= 1); g: device double, m entries, updated in place.
+ */
+dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int32_t prec,
+                                  const int32_t *cols, int64_t ncols, const double *w,
+                                  const double *rowscale, double *g, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCD_GB300_H */

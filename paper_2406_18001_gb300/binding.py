@@ -1,0 +1,285 @@
+"""ctypes binding of libdcd_gb300.so (include/dcd_gb300.h).
+
+Argument marshalling only: every step of the solvers runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library cannot be built or
+loaded, every call raises.  Device arrays are torch CUDA tensors; host arrays
+(DCD_FLAG_HOST_IO) are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- enums ---
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONV, EINTERNAL, ENOTSPD, EUNSUPPORTED = range(9)
+DENSE, CSR = 0, 1
+F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
+LINEAR, POLY, RBF = 0, 1, 2
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3, 4
+FLAG_GRAD_VALID, FLAG_HOST_IO, FLAG_PHASE_TIMERS, FLAG_NO_GRAPH = 0x1, 0x2, 0x4, 0x8
+
+PREC_NAMES = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3}
+
+
+class Matrix(C.Structure):
+    _fields_ = [("fmt", C.c_int32), ("dtype", C.c_int32), ("m", C.c_int64), ("n", C.c_int64), ("ld", C.c_int64),
+                ("values", C.c_void_p), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("row_scale", C.c_void_p)]
+
+
+class Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("degree", C.c_int32), ("gamma", C.c_double), ("coef0", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("s", C.c_int32), ("b", C.c_int32), ("max_iters", C.c_int64), ("seed", C.c_uint64),
+                ("start_iter", C.c_uint64), ("tol", C.c_double), ("check_every", C.c_int32),
+                ("prec", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters_done", C.c_int64), ("outer_steps", C.c_int64), ("converged", C.c_int32),
+                ("gpu_launches_per_step", C.c_int32), ("final_metric", C.c_double), ("primal", C.c_double),
+                ("dual", C.c_double), ("ms_total", C.c_double), ("ms_setup", C.c_double),
+                ("ms_sample", C.c_double), ("ms_gram", C.c_double), ("ms_recur", C.c_double),
+                ("ms_block", C.c_double), ("ms_update", C.c_double), ("ms_check", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
+           "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
+           "dcd_kernel_block_apply"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DcdError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}")
+
+
+def lib():
+    """Load (building first if needed) the CUDA library.  Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        try:  # make sure the CUDA runtime PyTorch uses is the one resolved
+            import torch  # noqa: F401
+        except Exception:
+            pass
+        L = C.CDLL(path)
+        P, i32, i64, u64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        M, K, O, S = C.POINTER(Matrix), C.POINTER(Kernel), C.POINTER(Opts), C.POINTER(Stats)
+        sigs = {
+            "dcd_svm_solve": (i32, [M, P, K, i32, d, O, P, P, S, P]),
+            "bdcd_krr_solve": (i32, [M, P, K, d, O, P, P, S, P]),
+            "dcd_svm_plan_create": (i32, [M, P, K, i32, d, O, P, P, P, C.POINTER(C.c_void_p)]),
+            "bdcd_krr_plan_create": (i32, [M, P, K, d, O, P, P, P, C.POINTER(C.c_void_p)]),
+            "dcd_plan_run": (i32, [P, i64, S]),
+            "dcd_plan_destroy": (i32, [P]),
+            "dcd_status_string": (C.c_char_p, [i32]),
+            "dcd_sample_indices": (i32, [i32, u64, i64, i32, u64, i64, P, P]),
+            "dcd_kernel_block": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
+            "dcd_kernel_block_apply": (i32, [M, K, i32, P, i64, P, P, P, P]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(s: int) -> str:
+    return lib().dcd_status_string(int(s)).decode()
+
+
+def kernel(kind, gamma=1.0, coef0=0.0, degree=2) -> Kernel:
+    if isinstance(kind, str):
+        kind = {"linear": LINEAR, "poly": POLY, "rbf": RBF}[kind]
+    return Kernel(int(kind), int(degree), float(gamma), float(coef0))
+
+
+def _prec(p):
+    return PREC_NAMES[p] if isinstance(p, str) else int(p)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def dense_matrix(A) -> Matrix:
+    """Describe a row-major 2-D torch tensor (device) or numpy array (host)."""
+    if isinstance(A, np.ndarray):
+        dt = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[A.dtype]
+        assert A.flags.c_contiguous
+        return Matrix(DENSE, dt, A.shape[0], A.shape[1], A.shape[1], A.ctypes.data, None, None, None)
+    import torch
+    dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[A.dtype]
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major tensor")
+    return Matrix(DENSE, dt, A.shape[0], A.shape[1], A.stride(0), A.data_ptr(), None, None, None)
+
+
+def _opts(s, b, H, seed, start_iter, tol, check_every, prec, flags):
+    return Opts(int(s), int(b), int(H), int(seed) & (2**64 - 1), int(start_iter), float(tol), int(check_every),
+                _prec(prec), int(flags), 0)
+
+
+def _check(rc, what, allow_notconv=True):
+    if rc == OK or (allow_notconv and rc == ENOTCONV):
+        return rc
+    raise DcdError(rc, what)
+
+
+def svm_solve(A, y, k, loss, C_, s, H, seed=0, prec="fp64", alpha=None, grad=None, tol=0.0, check_every=0,
+              start_iter=0, flags=0, stream=None):
+    """s-step DCD for K-SVM (Algorithm 2).  A, y, alpha, grad on the device
+    (torch) or, with FLAG_HOST_IO, on the host (numpy).  alpha is updated in
+    place (alpha_0 -> alpha_H); returns (alpha, grad, stats, status)."""
+    host = bool(flags & FLAG_HOST_IO)
+    m = A.shape[0]
+    if alpha is None:
+        alpha = np.zeros(m) if host else _zeros(m, A)
+    if grad is None:
+        grad = np.empty(m) if host else _empty(m, A)
+    Am = dense_matrix(A)
+    o = _opts(s, 1, H, seed, start_iter, tol, check_every, prec, flags)
+    st = Stats()
+    rc = lib().dcd_svm_solve(C.byref(Am), _ptr(y), C.byref(k), int(loss), float(C_), C.byref(o), _ptr(alpha),
+                             _ptr(grad), C.byref(st), None if host and stream is None else _stream(stream))
+    _check(rc, "dcd_svm_solve")
+    return alpha, grad, st.as_dict(), rc
+
+
+def krr_solve(A, y, k, lam, b, s, H, seed=0, prec="fp64", alpha=None, grad=None, tol=0.0, check_every=0,
+              start_iter=0, flags=0, stream=None):
+    """s-step BDCD for K-RR (Algorithm 4); same conventions as svm_solve."""
+    host = bool(flags & FLAG_HOST_IO)
+    m = A.shape[0]
+    if alpha is None:
+        alpha = np.zeros(m) if host else _zeros(m, A)
+    if grad is None:
+        grad = np.empty(m) if host else _empty(m, A)
+    Am = dense_matrix(A)
+    o = _opts(s, b, H, seed, start_iter, tol, check_every, prec, flags)
+    st = Stats()
+    rc = lib().bdcd_krr_solve(C.byref(Am), _ptr(y), C.byref(k), float(lam), C.byref(o), _ptr(alpha), _ptr(grad),
+                              C.byref(st), None if host and stream is None else _stream(stream))
+    _check(rc, "bdcd_krr_solve")
+    return alpha, grad, st.as_dict(), rc
+
+
+class Plan:
+    """A persistent solve (dcd_*_plan_create / dcd_plan_run / dcd_plan_destroy).
+
+    Keeps references to the arrays it was created with, which the library
+    reads and updates until close()."""
+
+    def __init__(self, problem, A, y, k, param, b, s, H, seed=0, prec="fp64", alpha=None, grad=None, tol=0.0,
+                 check_every=0, start_iter=0, flags=0, stream=None, loss=1):
+        host = bool(flags & FLAG_HOST_IO)
+        m = A.shape[0]
+        self.A, self.y = A, y
+        self.alpha = alpha if alpha is not None else (np.zeros(m) if host else _zeros(m, A))
+        self.grad = grad if grad is not None else (np.empty(m) if host else _empty(m, A))
+        self._Am = dense_matrix(A)
+        self._k = k
+        self._o = _opts(s, b if problem == 1 else 1, H, seed, start_iter, tol, check_every, prec, flags)
+        self._h = C.c_void_p()
+        strm = None if host and stream is None else _stream(stream)
+        if problem == 0:
+            rc = lib().dcd_svm_plan_create(C.byref(self._Am), _ptr(y), C.byref(k), int(loss), float(param),
+                                           C.byref(self._o), _ptr(self.alpha), _ptr(self.grad), strm,
+                                           C.byref(self._h))
+        else:
+            rc = lib().bdcd_krr_plan_create(C.byref(self._Am), _ptr(y), C.byref(k), float(param), C.byref(self._o),
+                                            _ptr(self.alpha), _ptr(self.grad), strm, C.byref(self._h))
+        _check(rc, "plan_create", allow_notconv=False)
+
+    def run(self, max_outer_steps=-1):
+        st = Stats()
+        rc = lib().dcd_plan_run(self._h, int(max_outer_steps), C.byref(st))
+        _check(rc, "dcd_plan_run")
+        return st.as_dict(), rc
+
+    def close(self):
+        if self._h:
+            rc = lib().dcd_plan_destroy(self._h)
+            self._h = C.c_void_p()
+            _check(rc, "dcd_plan_destroy", allow_notconv=False)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _zeros(m, like):
+    import torch
+    return torch.zeros(m, dtype=torch.float64, device=like.device)
+
+
+def _empty(m, like):
+    import torch
+    return torch.empty(m, dtype=torch.float64, device=like.device)
+
+
+def sample_indices(method, seed, m, b, first, count, device="cuda"):
+    import torch
+    n = count * (b if method == 1 else 1)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    rc = lib().dcd_sample_indices(int(method), int(seed), int(m), int(b), int(first), int(count), _ptr(out),
+                                  _stream(None))
+    _check(rc, "dcd_sample_indices", allow_notconv=False)
+    return out[:n]
+
+
+def kernel_block(A, k, prec, cols, rows=None, nrows=None):
+    import torch
+    ncols = cols.numel()
+    nr = rows.numel() if rows is not None else (A.shape[0] if nrows is None else nrows)
+    p = _prec(prec)
+    out = torch.empty((nr, ncols), dtype=torch.float64 if p == PREC_FP64 else torch.float32, device=A.device)
+    Am = dense_matrix(A)
+    rc = lib().dcd_kernel_block(C.byref(Am), C.byref(k), p, _ptr(rows), nr, _ptr(cols), ncols, _ptr(out), ncols,
+                                _stream(None))
+    _check(rc, "dcd_kernel_block", allow_notconv=False)
+    return out
+
+
+def kernel_block_apply(A, k, prec, cols, w, g, rowscale=None):
+    Am = dense_matrix(A)
+    rc = lib().dcd_kernel_block_apply(C.byref(Am), C.byref(k), _prec(prec), _ptr(cols), cols.numel(), _ptr(w),
+                                      _ptr(rowscale), _ptr(g), _stream(None))
+    _check(rc, "dcd_kernel_block_apply", allow_notconv=False)
+    return g

@@ -1,0 +1,179 @@
+// block_simt.cu -- FP64 CUDA-core evaluation of the sampled kernel block
+// (U_k = K(A, A_k) of Algorithm 2, Q_k of Algorithm 4) for the FP64 form.
+//
+// Two epilogues share one tile loop:
+//   apply: g[i] += rs[i] * sum_c K(a_i, a_cols[c]) w[c]   (block never stored)
+//   store: out[r, c] = K(a_rows[r], a_cols[c])            (the Gram of a3)
+// RBF distances are summed from coordinate differences (Table 1's definition)
+// rather than expanded, so the FP64 form carries no cancellation error.
+// The k-order of every dot product is fixed (0..n-1 in steps of BK), so the
+// store and apply epilogues see bit-identical kernel values.
+#include "dcd_internal.cuh"
+
+namespace dcd {
+
+namespace {
+
+constexpr int TX = 16, TY = 16;   // 256 threads
+constexpr int RM = 4;             // rows per thread
+constexpr int BM = TY * RM;       // 64 rows per tile
+constexpr int BK = 16;
+
+template <int RN, bool STORE, bool RBF>
+__global__ void __launch_bounds__(256) block_simt_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
+                                                            int64_t n, KernelParams kp, const int32_t *rows,
+                                                            int64_t nrows, const int32_t *cols, int64_t ncols,
+                                                            const double *__restrict__ w,
+                                                            const double *__restrict__ rs, double *g, double *out,
+                                                            int64_t ldo, int *err)
+{
+    constexpr int BN = TX * RN;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    __shared__ double rowacc[BM];
+    __shared__ int64_t rowoff[BM];
+    __shared__ int64_t coloff[BN];
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int64_t ntiles = (nrows + BM - 1) / BM;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * BM;
+        if (threadIdx.x < BM) {
+            int64_t r = r0 + threadIdx.x, off = -1;
+            if (r < nrows) {
+                int64_t ri = rows ? (int64_t)rows[r] : r;
+                if (ri >= 0 && ri < m) off = ri * lda;
+                else set_error(err, DEV_BAD_INDEX);
+            }
+            rowoff[threadIdx.x] = off;
+            rowacc[threadIdx.x] = 0.0;
+        }
+        for (int64_t c0 = 0; c0 < ncols; c0 += BN) {
+            __syncthreads();
+            if (threadIdx.x < BN) {
+                int64_t c = c0 + threadIdx.x, off = -1;
+                if (c < ncols) {
+                    int64_t ci = cols[c];
+                    if (ci >= 0 && ci < m) off = ci * lda;
+                    else set_error(err, DEV_BAD_INDEX);
+                }
+                coloff[threadIdx.x] = off;
+            }
+            double acc[RM][RN];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RN; ++j) acc[i][j] = 0.0;
+            for (int64_t k0 = 0; k0 < n; k0 += BK) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < BM * BK; e += 256) {
+                    int rr = e / BK, kk = e % BK;
+                    int64_t off = rowoff[rr], k = k0 + kk;
+                    As[kk][rr] = (off >= 0 && k < n) ? A[off + k] : 0.0;
+                }
+                for (int e = threadIdx.x; e < BN * BK; e += 256) {
+                    int cc = e / BK, kk = e % BK;
+                    int64_t off = coloff[cc], k = k0 + kk;
+                    Bs[kk][cc] = (off >= 0 && k < n) ? A[off + k] : 0.0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    double a[RM], b[RN];
+#pragma unroll
+                    for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + TY * i];
+#pragma unroll
+                    for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + TX * j];
+#pragma unroll
+                    for (int i = 0; i < RM; ++i)
+#pragma unroll
+                        for (int j = 0; j < RN; ++j) {
+                            if (RBF) {
+                                double d = a[i] - b[j];
+                                acc[i][j] = fma(d, d, acc[i][j]);
+                            } else {
+                                acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                            }
+                        }
+                }
+            }
+            if (STORE) {
+#pragma unroll
+                for (int i = 0; i < RM; ++i) {
+                    int64_t r = r0 + ty + TY * i;
+#pragma unroll
+                    for (int j = 0; j < RN; ++j) {
+                        int64_t c = c0 + tx + TX * j;
+                        if (r < nrows && c < ncols) out[r * ldo + c] = kfun_f64(kp, acc[i][j]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < RM; ++i) {
+                    double part = 0.0;
+#pragma unroll
+                    for (int j = 0; j < RN; ++j) {
+                        int64_t c = c0 + tx + TX * j;
+                        if (c < ncols) part = fma(kfun_f64(kp, acc[i][j]), w[c], part);
+                    }
+                    // fixed-order reduction over the 16 lanes that share these rows
+#pragma unroll
+                    for (int o = TX / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    if (tx == 0) rowacc[ty + TY * i] += part;
+                }
+            }
+        }
+        __syncthreads();
+        if (!STORE && threadIdx.x < BM) {
+            int64_t r = r0 + threadIdx.x;
+            if (r < nrows) g[r] += (rs ? rs[r] : 1.0) * rowacc[threadIdx.x];
+        }
+    }
+}
+
+template <bool STORE, bool RBF>
+cudaError_t launch_rn(int rn, int64_t grid, const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
+                      const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols, const double *w,
+                      const double *rs, double *g, double *out, int64_t ldo, int *err, cudaStream_t st)
+{
+    switch (rn) {
+    case 1:
+        block_simt_f64_kernel<1, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                           w, rs, g, out, ldo, err);
+        break;
+    case 2:
+        block_simt_f64_kernel<2, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                           w, rs, g, out, ldo, err);
+        break;
+    default:
+        block_simt_f64_kernel<4, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                           w, rs, g, out, ldo, err);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
+                                  const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
+                                  const double *w, const double *rs, double *g, double *out, int64_t ldo, int *err,
+                                  cudaStream_t st)
+{
+    if (nrows <= 0 || ncols <= 0) return cudaSuccess;
+    const int rn = ncols <= 16 ? 1 : (ncols <= 32 ? 2 : 4);
+    int64_t tiles = (nrows + BM - 1) / BM;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8;
+    const bool store = (out != nullptr);
+    const bool rbf = (kp.kind == DCD_RBF);
+    if (store)
+        return rbf ? launch_rn<true, true>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st)
+                   : launch_rn<true, false>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st);
+    return rbf ? launch_rn<false, true>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st)
+               : launch_rn<false, false>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st);
+}
+
+}  // namespace dcd

@@ -1,0 +1,512 @@
+// block_tc.cu -- the sampled kernel block on the sm_103a tensor cores.
+//
+// C[i, j] = a_i . b_j for a packed, zero-padded operand A (rows of the data
+// matrix) and B (the s*b sampled rows), both K-major, is formed by
+// tcgen05.mma (kind::f16 with bf16 inputs, or kind::tf32 on fp32 inputs) with
+// FP32 accumulators in tensor memory.  The epilogue maps C through the kernel
+// function of Table 1 -- the RBF via the expansion ||a||^2 + ||b||^2 - 2 a.b
+// of Section 5.2 -- and either
+//   apply: contracts each row with the column coefficients w and adds
+//          rs[i] * sum_j K_ij w_j to the FP64 gradient g[i] (the m x sb block
+//          is never written to memory), or
+//   store: writes K_ij (FP32) -- used for the sampled Gram, so that the
+//          recurrence sees exactly the values the apply pass uses.
+//
+// CTA layout (192 threads, one CTA per SM, persistent over 128-row tiles):
+//   warp 0      TMA producer: 128-byte-swizzled k-blocks of A and B into a
+//               4-stage shared-memory ring (mbarrier complete_tx)
+//   warp 1      TMEM allocator and MMA issuer (one thread); accumulators are
+//               double-buffered (2 x BN columns) so the epilogue of one
+//               N-chunk overlaps the MMAs of the next
+//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns per load, one
+//               thread per row
+// Every mbarrier wait is bounded; on timeout the CTA records DEV_TIMEOUT,
+// drains its in-flight copies and MMAs (bounded), frees TMEM and returns.
+#include "dcd_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace dcd {
+
+namespace {
+
+constexpr int BM = 128;                 // rows per tile = TMEM lanes
+constexpr int BN_MAX = 256;             // columns per N-chunk (max)
+constexpr int STAGES = 4;
+constexpr int ROW_BYTES = 128;          // one swizzled k-block row
+constexpr int A_STAGE = BM * ROW_BYTES;          // 16 KB
+constexpr int B_STAGE = BN_MAX * ROW_BYTES;      // 32 KB
+constexpr int RING_BYTES = STAGES * (A_STAGE + B_STAGE);
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity.  Returns false if the
+// CTA is aborting (another role timed out) or this wait timed out.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (uint32_t spin = 1;; ++spin) {
+        if (mbar_test(bar, parity)) return true;
+        if ((spin & 15) == 0) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                set_error(err, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Wait without the abort shortcut (drain path), still bounded.
+__device__ __noinline__ void mbar_drain(uint64_t *bar, uint32_t parity)
+{
+    const unsigned long long t0 = gtime();
+    while (!mbar_test(bar, parity))
+        if (gtime() - t0 > WAIT_NS) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B format (bf16 = 1, tf32 = 2), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int fmt, int n, int m)
+{
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    if (TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ float ex2f(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct TcArgs {
+    const float *row_h;   // per-row RBF term gamma*log2(e)*||a_i||^2 (nrows_out entries)
+    const float *col_h;   // per-column term, padded with zeros to nchunks*BN
+    const float *col_w;   // apply: coefficients, padded with zeros
+    const double *rs;     // apply: per-row scale or null
+    double *g;            // apply: gradient (nrows_out)
+    float *out;           // store: output, row-major with ldo
+    int64_t ldo;
+    int64_t nrows_out;
+    int64_t ncols;
+    int num_tiles, nchunks, kblocks, bn;
+    int store;            // 1: store epilogue, 0: apply
+    int items;            // apply: num_tiles; store: num_tiles * nchunks
+    int degree;
+    float two_gl;         // 2 * gamma * log2(e)
+    float coef0;
+    int *err;
+};
+
+template <int KIND>
+__device__ __forceinline__ float kf32(float c, float hr, float hc, const TcArgs &a)
+{
+    if (KIND == DCD_RBF) {
+        float t = fmaf(c, a.two_gl, -(hr + hc));
+        return ex2f(fminf(t, 0.f));
+    } else if (KIND == DCD_LINEAR) {
+        return c;
+    } else {
+        float t = c + a.coef0, r = t;
+        for (int e = 1; e < a.degree; ++e) r *= t;
+        return r;
+    }
+}
+
+__device__ __forceinline__ void item_range(const TcArgs &a, int item, int &tile, int &c0, int &c1)
+{
+    if (a.store) {
+        tile = item / a.nchunks;
+        c0 = item % a.nchunks;
+        c1 = c0 + 1;
+    } else {
+        tile = item;
+        c0 = 0;
+        c1 = a.nchunks;
+    }
+}
+
+template <bool TF32, int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    block_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_STAGE;
+    uint64_t *bars = (uint64_t *)(smem + RING_BYTES);
+    uint64_t *full = bars;                 // STAGES
+    uint64_t *empty = bars + STAGES;       // STAGES
+    uint64_t *tfull = bars + 2 * STAGES;   // 2
+    uint64_t *tempty = tfull + 2;          // 2
+    uint64_t *drain = tempty + 2;          // 1
+    uint32_t *tmem_holder = (uint32_t *)(drain + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const int bn = a.bn;
+    const int kb_elems = TF32 ? 32 : 64;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- producer --
+            uint32_t it = 0;
+            bool ok = true;
+            const uint32_t bytes = (uint32_t)(A_STAGE + bn * ROW_BYTES);
+            for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
+                int tile, c0, c1;
+                item_range(a, item, tile, c0, c1);
+                for (int nc = c0; ok && nc < c1; ++nc)
+                    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&full[s], bytes);
+                        tma_load_2d(sA + s * A_STAGE, &tmA, &full[s], kb * kb_elems, tile * BM);
+                        tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], kb * kb_elems, nc * bn);
+                    }
+            }
+            if (!ok) {  // let every issued copy land before the CTA exits
+                uint32_t first = it > STAGES ? it - STAGES : 0;
+                for (uint32_t j = first; j < it; ++j) mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // --------------------------------------------------------- MMA --
+            const uint32_t idesc = make_idesc(TF32 ? 2 : 1, bn, BM);
+            uint32_t it = 0, acc_it = 0;
+            bool ok = true, issued = false;
+            for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
+                int tile, c0, c1;
+                item_range(a, item, tile, c0, c1);
+                for (int nc = c0; ok && nc < c1; ++nc, ++acc_it) {
+                    const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                    if (!mbar_wait(&tempty[buf], aph ^ 1, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t dtm = tmem_base + buf * (uint32_t)bn;
+                    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t ab = su32(sA + s * A_STAGE), bb = su32(sB + s * B_STAGE);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma<TF32>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
+                                      (kb > 0 || k > 0) ? 1u : 0u);
+                        issued = true;
+                        mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
+                }
+            }
+            if (!ok && issued) {  // wait (bounded) for the MMAs already issued
+                mma_commit(drain);
+                mbar_drain(drain, 0);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue --
+        const int quarter = warp & 3;  // warps 2,3,4,5 -> TMEM lanes 64,96,0,32
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        uint32_t acc_it = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
+            int tile, c0, c1;
+            item_range(a, item, tile, c0, c1);
+            const int64_t row = (int64_t)tile * BM + row_in_tile;
+            const bool row_ok = row < a.nrows_out;
+            const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
+            double racc = 0.0;
+            for (int nc = c0; nc < c1; ++nc, ++acc_it) {
+                const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                // every lane polls; the warp proceeds only if all lanes saw the
+                // phase complete, so the aligned tcgen05.ld never diverges
+                const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, seen)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                for (int cg = 0; cg < bn / 32; ++cg) {
+                    float v[32];
+                    tmem_ld32(tmem_base + lane_addr + buf * (uint32_t)bn + (uint32_t)(cg * 32), v);
+                    const int64_t colbase = (int64_t)nc * bn + cg * 32;
+                    if (a.store) {
+                        if (row_ok)
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const int64_t col = colbase + q;
+                                if (col < a.ncols)
+                                    a.out[row * a.ldo + col] =
+                                        kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[col] : 0.f, a);
+                            }
+                    } else {
+                        float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 32; q += 2) {
+                            const float hc0 = KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f;
+                            const float hc1 = KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f;
+                            p0 = fmaf(kf32<KIND>(v[q], hr, hc0, a), a.col_w[colbase + q], p0);
+                            p1 = fmaf(kf32<KIND>(v[q + 1], hr, hc1, a), a.col_w[colbase + q + 1], p1);
+                        }
+                        racc += (double)p0 + (double)p1;
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (ok && !a.store && row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ------------------------------------------------------------------ host --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int esz = op.is_tf32 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)op.n_pad, (cuuint64_t)op.nrows};
+    cuuint64_t strides[1] = {(cuuint64_t)(op.n_pad * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, op.is_tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(op.rows), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <bool TF32, int KIND>
+cudaError_t launch_kind(int grid, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st)
+{
+    auto kfn = block_tc_kernel<TF32, KIND>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    kfn<<<grid, NTHREADS, SMEM_BYTES, st>>>(mA, mB, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available()
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
+                            const float *col_h, const float *col_w, const double *rs, double *g, float *out,
+                            int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st)
+{
+    if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
+    if (Aop.is_tf32 != Bop.is_tf32 || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
+    const int kb_elems = Aop.is_tf32 ? 32 : 64;
+    if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
+    int bn = (int)((ncols + 31) / 32) * 32;
+    if (bn > BN_MAX) bn = BN_MAX;
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, Aop, BM) || !make_map(&mB, Bop, bn)) return cudaErrorInvalidValue;
+    TcArgs a;
+    a.row_h = row_h;
+    a.col_h = col_h;
+    a.col_w = col_w;
+    a.rs = rs;
+    a.g = g;
+    a.out = out;
+    a.ldo = ldo;
+    a.nrows_out = nrows_out;
+    a.ncols = ncols;
+    a.num_tiles = (int)((nrows_out + BM - 1) / BM);
+    a.nchunks = (int)((ncols + bn - 1) / bn);
+    a.kblocks = (int)(Aop.n_pad / kb_elems);
+    a.bn = bn;
+    a.store = out != nullptr;
+    a.items = a.store ? a.num_tiles * a.nchunks : a.num_tiles;
+    a.degree = kp.degree;
+    a.two_gl = (float)(2.0 * kp.gamma * 1.4426950408889634);
+    a.coef0 = (float)kp.coef0;
+    a.err = err;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = a.items < sms ? a.items : sms;
+    if (Aop.is_tf32) {
+        if (kp.kind == DCD_RBF) return launch_kind<true, DCD_RBF>(grid, mA, mB, a, st);
+        if (kp.kind == DCD_POLY) return launch_kind<true, DCD_POLY>(grid, mA, mB, a, st);
+        return launch_kind<true, DCD_LINEAR>(grid, mA, mB, a, st);
+    }
+    if (kp.kind == DCD_RBF) return launch_kind<false, DCD_RBF>(grid, mA, mB, a, st);
+    if (kp.kind == DCD_POLY) return launch_kind<false, DCD_POLY>(grid, mA, mB, a, st);
+    return launch_kind<false, DCD_LINEAR>(grid, mA, mB, a, st);
+}
+
+}  // namespace dcd

@@ -1,0 +1,128 @@
+// dcd_internal.cuh -- device helpers and host launch declarations shared by
+// the translation units of libdcd_gb300.so.  Nothing here is visible through
+// the C ABI (include/dcd_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/dcd_gb300.h"
+
+namespace dcd {
+
+// ---------------------------------------------------------------- errors --
+// Device error word codes (first writer wins).
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,     // an mbarrier / flag wait ran past its bound
+    DEV_BAD_INDEX = 2,   // a sampled or CSR index fell outside [0, m) / [0, n)
+    DEV_NOT_SPD = 3,     // a block system had a non-positive pivot
+    DEV_INTERNAL = 4,
+};
+
+__device__ __forceinline__ void set_error(int *err, int code)
+{
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ------------------------------------------------------------ SplitMix64 --
+// Steele, Lea & Flood (OOPSLA 2014): the state advances by the golden-ratio
+// increment and each output is the 64-bit finaliser of the new state.
+// draw(seed, stream, c) is output c+1 of the sequence whose starting state is
+// output 2*stream+1 of the sequence seeded with `seed`; stream 0 feeds DCD and
+// stream t+1 feeds BDCD block t.
+__host__ __device__ __forceinline__ uint64_t sm64_finalise(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t sm64_output(uint64_t state, uint64_t k)
+{
+    return sm64_finalise(state + k * 0x9E3779B97F4A7C15ULL);
+}
+
+__host__ __device__ __forceinline__ uint64_t sm64_draw(uint64_t seed, uint64_t stream, uint64_t ctr)
+{
+    return sm64_output(sm64_output(seed, 2 * stream + 1), ctr + 1);
+}
+
+// floor(u * range / 2^64)
+__device__ __forceinline__ uint64_t below(uint64_t u, uint64_t range) { return __umul64hi(u, range); }
+
+// ------------------------------------------------------ kernel functions --
+struct KernelParams {
+    int kind;       // DCD_LINEAR / DCD_POLY / DCD_RBF
+    int degree;
+    double gamma;
+    double coef0;
+};
+
+// Table 1 applied to a dot product (linear, poly) or to a squared distance
+// (RBF), in FP64.
+__device__ __forceinline__ double kfun_f64(const KernelParams &kp, double v)
+{
+    if (kp.kind == DCD_RBF) return exp(-kp.gamma * v);
+    if (kp.kind == DCD_LINEAR) return v;
+    double t = kp.coef0 + v, r = t;
+    for (int e = 1; e < kp.degree; ++e) r *= t;
+    return r;
+}
+
+// --------------------------------------------------------- host launches --
+// All launchers enqueue on `st` and return cudaGetLastError().
+cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host,
+                          int64_t m, int b, int64_t count, int32_t *out, int *err, cudaStream_t st);
+
+// FP64 CUDA-core kernel block over a dense matrix of doubles.
+//   apply (out == nullptr): g[i] += rs[i] * sum_c K(a_i, a_cols[c]) * w[c] for i < nrows
+//   store (g == nullptr):   out[r*ldo + c] = K(a_rows[r], a_cols[c])
+cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
+                                  const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
+                                  const double *w, const double *rs, double *g, double *out, int64_t ldo,
+                                  int *err, cudaStream_t st);
+
+// tcgen05 kernel block over the packed, padded operand copy (bf16 or fp32
+// rows of n_pad elements, zero padded).
+struct TcOperand {
+    const void *rows;     // packed matrix, row-major, ld = n_pad
+    int64_t nrows;
+    int64_t n_pad;        // multiple of the k-block
+    int is_tf32;          // 0: bf16, 1: fp32 read as tf32
+};
+bool tc_available();
+cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
+                            const float *row_h, const float *col_h, const float *col_w, const double *rs,
+                            double *g, float *out, int64_t ldo, int64_t nrows_out, int64_t ncols,
+                            int *err, cudaStream_t st);
+
+// setup / per-step helpers (sample_update.cu)
+cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st);
+cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
+cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
+cudaError_t launch_row_terms(const void *packed, int is_tf32, int64_t n_pad, int64_t m, const KernelParams &kp,
+                             float *h, cudaStream_t st);
+cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st);
+cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
+cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
+                             cudaStream_t st);
+cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,
+                          double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st);
+cudaError_t launch_check(int problem, const double *g, const double *alpha, const double *y, int64_t m,
+                         double C, int loss, double *partials, double *result, cudaStream_t st);
+cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStream_t st);
+cudaError_t launch_coef(const double *y, const double *alpha, const int32_t *cols, int64_t count, double scale,
+                        double *w, cudaStream_t st);
+
+// recurrence (recur.cu)
+cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
+                             const double *y, const double *alpha, const double *g, double omega, double nu,
+                             double *delta, double *w64, float *w32, int *err, cudaStream_t st);
+cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
+                              double lambda, double mdiag, const double *g, double *Linv, double *delta,
+                              double *w64, float *w32, int *err, cudaStream_t st);
+
+}  // namespace dcd

@@ -1,0 +1,376 @@
+// sample_update.cu -- the small kernels of one outer s-step: index sampling
+// (Algorithms 2 and 4, "choose i uniformly at random"), operand packing and
+// norms, the scatter update of alpha and the cached gradient, and the
+// convergence reductions (Section 5.1's duality gap and residual).
+#include "dcd_internal.cuh"
+
+#include <cuda_fp16.h>
+
+namespace dcd {
+
+// ----------------------------------------------------------- sampling -----
+// DCD: one thread per iteration.  out[j] = floor(u * m / 2^64), u the
+// SplitMix64 draw (seed, stream 0, counter first + j).
+__global__ void sample_dcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
+                                  int64_t count, int32_t *out)
+{
+    uint64_t first = ctr_dev ? *ctr_dev : first_host;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = (int32_t)below(sm64_draw(seed, 0, first + (uint64_t)j), (uint64_t)m);
+}
+
+// BDCD: one warp per block.  Floyd's algorithm (Bentley & Floyd 1987): for
+// q = 0..b-1, J = m-b+q, r uniform in [0, J] from draw (seed, t+1, q); take r
+// unless it was already taken, else take J.  The warp tests membership of r
+// against the q indices taken so far in parallel.
+__global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
+                                   int b, int64_t nblocks, int32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nblocks) return;
+    const uint64_t t = (ctr_dev ? *ctr_dev : first_host) + (uint64_t)warp;
+    int32_t *blk = out + warp * b;
+    for (int q = 0; q < b; ++q) {
+        const int64_t J = m - b + q;
+        const int64_t r = (int64_t)below(sm64_draw(seed, t + 1, (uint64_t)q), (uint64_t)(J + 1));
+        bool hit = false;
+        for (int p = lane; p < q; p += 32) hit |= (blk[p] == (int32_t)r);
+        const unsigned any = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) blk[q] = (int32_t)(any ? J : r);
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
+                          int b, int64_t count, int32_t *out, int *err, cudaStream_t st)
+{
+    (void)err;
+    if (count <= 0) return cudaSuccess;
+    if (method == 0) {
+        int threads = 128;
+        int64_t blocks = (count + threads - 1) / threads;
+        if (blocks > 4096) blocks = 4096;
+        sample_dcd_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, ctr_dev, first_host, m, count, out);
+    } else {
+        int threads = 128;  // 4 warps = 4 blocks per CTA
+        int64_t blocks = (count * 32 + threads - 1) / threads;
+        sample_bdcd_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, ctr_dev, first_host, m, b, count, out);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ packing -----
+__device__ __forceinline__ float load_as_f32(const void *src, int dtype, int64_t off)
+{
+    switch (dtype) {
+    case DCD_F64: return (float)((const double *)src)[off];
+    case DCD_F32: return ((const float *)src)[off];
+    case DCD_BF16: return __bfloat162float(((const __nv_bfloat16 *)src)[off]);
+    default: return 0.f;
+    }
+}
+
+// dst row r (n_pad elements, zero padded) = src row rows[r] (or r),
+// converted to bf16 (round to nearest even, dst_kind 0), fp32 (1, the tf32
+// path reads fp32 storage) or fp64 (2).
+// Row indices outside [0, m) produce a zero row and set DEV_BAD_INDEX.
+__global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                 void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err)
+{
+    const int64_t total = count * n_pad;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / n_pad, c = e - r * n_pad;
+        const int64_t sr = rows ? (int64_t)rows[r] : r;
+        const bool inb = sr >= 0 && sr < m;
+        if (!inb && c == 0) set_error(err, DEV_BAD_INDEX);
+        if (dst_kind == 2) {
+            double v = 0.0;
+            if (c < n && inb)
+                v = (dtype == DCD_F64) ? ((const double *)src)[sr * ld + c] : (double)load_as_f32(src, dtype, sr * ld + c);
+            ((double *)dst)[e] = v;
+            continue;
+        }
+        float v = (c < n && inb) ? load_as_f32(src, dtype, sr * ld + c) : 0.f;
+        if (dst_kind == 1) {
+            // round to the tf32 grid (10-bit mantissa, nearest, ties away) so the
+            // tensor core sees exactly the stored value and the row norms match
+            uint32_t t;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+            ((float *)dst)[e] = __uint_as_float(t);
+        } else {
+            ((__nv_bfloat16 *)dst)[e] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t total = count * n_pad;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    pack_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, dst, dst_kind, n_pad, count, err);
+    return cudaGetLastError();
+}
+
+// Number of labels that are not exactly +1 or -1.
+__global__ void label_check_kernel(const double *y, int64_t m, int *bad)
+{
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        local += !(y[i] == 1.0 || y[i] == -1.0);
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(bad, local);
+}
+
+cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (m + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    label_check_kernel<<<(unsigned)blocks, 256, 0, st>>>(y, m, bad);
+    return cudaGetLastError();
+}
+
+__global__ void f64_to_f32_kernel(const double *src, int64_t count, float *dst)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        dst[j] = (float)src[j];
+}
+
+cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    f64_to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, count, dst);
+    return cudaGetLastError();
+}
+
+// h[r] = gamma * log2(e) * ||x_r||^2 of the packed (already rounded) row, for
+// the RBF expansion ||a||^2 + ||b||^2 - 2 a.b (Section 5.2); 0 for the other
+// kernels.  One warp per row, FP64 partial sums, fixed order.
+__global__ void row_terms_kernel(const void *packed, int is_tf32, int64_t n_pad, int64_t m, double scale, float *h)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= m) return;
+    double s = 0.0;
+    for (int64_t c = lane; c < n_pad; c += 32) {
+        float v = is_tf32 ? ((const float *)packed)[r * n_pad + c]
+                          : __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
+        s += (double)v * (double)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) h[r] = (float)(scale * s);
+}
+
+cudaError_t launch_row_terms(const void *packed, int is_tf32, int64_t n_pad, int64_t m, const KernelParams &kp,
+                             float *h, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;
+    int64_t blocks = (m * 32 + 255) / 256;
+    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, is_tf32, n_pad, m, scale, h);
+    return cudaGetLastError();
+}
+
+__global__ void gather_f32_kernel(const float *src, const int32_t *idx, int64_t count, float *dst)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        dst[j] = src[idx[j]];
+}
+
+cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    gather_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, idx, count, dst);
+    return cudaGetLastError();
+}
+
+__global__ void fill_f64_kernel(double *p, double v, int64_t count)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        p[j] = v;
+}
+
+cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    fill_f64_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, v, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ gradient init -----
+// The diagonal and constant parts of the cached gradient:
+//   K-SVM (problem 0): g = -1 + omega * alpha     (+ Q alpha added by the block kernel)
+//   K-RR  (problem 1): g = m * alpha - y          (+ K alpha / lambda added likewise)
+__global__ void init_grad_kernel(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = alpha[i];
+        g[i] = (problem == 0) ? (-1.0 + diag * a) : (diag * a - y[i]);
+    }
+}
+
+cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
+                             cudaStream_t st)
+{
+    int64_t blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    init_grad_kernel<<<(unsigned)blocks, 256, 0, st>>>(problem, y, alpha, diag, m, g);
+    return cudaGetLastError();
+}
+
+// Coefficients of the initial gradient pass for a nonzero alpha_0:
+// w[j] = y[c] * alpha[c] (K-SVM, y given) or alpha[c] * scale (K-RR, 1/lambda).
+__global__ void coef_kernel(const double *y, const double *alpha, const int32_t *cols, int64_t count, double scale,
+                            double *w)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = cols[j];
+        w[j] = y ? y[c] * alpha[c] : alpha[c] * scale;
+    }
+}
+
+cudaError_t launch_coef(const double *y, const double *alpha, const int32_t *cols, int64_t count, double scale,
+                        double *w, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    coef_kernel<<<(unsigned)blocks, 256, 0, st>>>(y, alpha, cols, count, scale, w);
+    return cudaGetLastError();
+}
+
+__global__ void nnz_kernel(const double *alpha, int64_t m, int *count)
+{
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        local += (alpha[i] != 0.0);
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (m + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    nnz_kernel<<<(unsigned)blocks, 256, 0, st>>>(alpha, m, count);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- alpha update ---
+// alpha_{sk+s} = alpha_sk + sum_t V_t delta_t (Algorithms 2 and 4) and the
+// diagonal part of the gradient update, g[S_j] += diag * delta_j (omega for
+// K-SVM-L2, m for K-RR).  Repeated indices are merged: the first occurrence
+// of an index adds the sum of all its deltas, taken in j order, so the result
+// does not depend on thread scheduling.  Also advances the stream counter.
+__global__ void update_kernel(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,
+                              double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
+{
+    extern __shared__ int32_t sS[];
+    for (int64_t j = threadIdx.x; j < cnt; j += blockDim.x) sS[j] = S[j];
+    __syncthreads();
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr) *ctr += ctr_advance;
+    if (j >= cnt) return;
+    const int32_t i = sS[j];
+    if (i < 0 || i >= m) {
+        set_error(err, DEV_BAD_INDEX);
+        return;
+    }
+    for (int64_t t = 0; t < j; ++t)
+        if (sS[t] == i) return;  // not the first occurrence
+    double sum = delta[j];
+    for (int64_t t = j + 1; t < cnt; ++t)
+        if (sS[t] == i) sum += delta[t];
+    alpha[i] += sum;
+    g[i] += diag * sum;
+}
+
+cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha, double *g,
+                          uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st)
+{
+    if (cnt <= 0) return cudaSuccess;
+    int threads = 256;
+    int64_t blocks = (cnt + threads - 1) / threads;
+    size_t sm = sizeof(int32_t) * (size_t)cnt;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    update_kernel<<<(unsigned)blocks, threads, sm, st>>>(S, delta, cnt, diag, alpha, g, ctr, ctr_advance, m, err);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------- convergence ----
+// Partial sums over a fixed partition of [0, m), then one block combines the
+// partials in index order, so the result is reproducible.
+//   K-RR:  r[0] = ||g||^2
+//   K-SVM: with (Q a)_i = g_i + 1 - omega a_i:
+//          r[0] = a^T Q a, r[1] = sum a, r[2] = ||a||^2, r[3] = sum max(0, 1-(Qa)_i)^p
+constexpr int CHECK_BLOCKS = 256;
+constexpr int CHECK_THREADS = 256;
+
+__global__ void check_partial_kernel(int problem, const double *g, const double *alpha, int64_t m, double C, int loss,
+                                     double *partials)
+{
+    __shared__ double red[4][CHECK_THREADS];
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    const double omega = (loss == 2) ? 1.0 / (2.0 * C) : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        double gi = g[i];
+        if (problem == 1) {
+            s0 += gi * gi;
+        } else {
+            double a = alpha[i];
+            double qa = gi + 1.0 - omega * a;
+            double xi = fmax(0.0, 1.0 - qa);
+            s0 += a * qa;
+            s1 += a;
+            s2 += a * a;
+            s3 += (loss == 1) ? xi : xi * xi;
+        }
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    red[3][threadIdx.x] = s3;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void check_final_kernel(const double *partials, int nblocks, double *result)
+{
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
+        result[threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_check(int problem, const double *g, const double *alpha, const double *y, int64_t m, double C,
+                         int loss, double *partials, double *result, cudaStream_t st)
+{
+    (void)y;
+    check_partial_kernel<<<CHECK_BLOCKS, CHECK_THREADS, 0, st>>>(problem, g, alpha, m, C, loss, partials);
+    check_final_kernel<<<1, 32, 0, st>>>(partials, CHECK_BLOCKS, result);
+    return cudaGetLastError();
+}
+
+}  // namespace dcd

@@ -1,0 +1,828 @@
+// solver.cu -- host side of libdcd_gb300.so: argument validation, workspace,
+// the outer s-step loop and the C-ABI entry points of include/dcd_gb300.h.
+//
+// One outer step (Algorithm 2 for K-SVM, Algorithm 4 for K-RR), reordered so
+// the m x sb block is never stored (its contraction with the step's
+// coefficients is all the next steps need):
+//   a1 sample  S = s*b indices from the counter-based stream
+//   a2 gather  the sampled rows (tensor-core path) and their norms
+//   a3 Gram    Kss = K(A_S, A_S), with the same kernel as a5
+//   a4 recur   FP64 theta / Delta from Kss and the cached gradient g_S
+//   a5 block   g += rs * K(A, A_S) w, fused, for all m rows
+//   a6 update  alpha_S += delta, g_S += diag * delta; counter += s
+// U_j^T alpha_sk of the paper is read from the cached gradient g, which a5/a6
+// keep equal to the gradient of the current alpha.
+#include "dcd_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace dcd {
+
+namespace {
+
+constexpr int64_t SB_MAX = 8192;   // s*b per outer step
+constexpr int B_MAX = 128;         // block size
+
+struct Arena {
+    char *base = nullptr;
+    size_t used = 0, cap = 0;
+    void *take(size_t bytes, size_t align = 256)
+    {
+        size_t off = (used + align - 1) / align * align;
+        used = off + bytes;
+        return base ? base + off : nullptr;
+    }
+};
+
+dcd_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return DCD_OK;
+    if (e == cudaErrorMemoryAllocation) return DCD_ENOMEM;
+    return DCD_ECUDA;
+}
+
+#define DCD_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_);  \
+    } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+dcd_status validate_kernel(const dcd_kernel *k)
+{
+    if (!k) return DCD_EINVAL;
+    switch (k->kind) {
+    case DCD_LINEAR: return DCD_OK;
+    case DCD_POLY:
+        return (std::isfinite(k->coef0) && k->coef0 >= 0.0 && k->degree >= 2 && k->degree <= 32) ? DCD_OK : DCD_EINVAL;
+    case DCD_RBF: return finite_pos(k->gamma) ? DCD_OK : DCD_EINVAL;
+    default: return DCD_EINVAL;
+    }
+}
+
+dcd_status validate_dense(const dcd_matrix *A)
+{
+    if (!A || A->m < 1 || A->n < 1) return DCD_EINVAL;
+    if (A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;
+    if (A->fmt != DCD_DENSE) return DCD_EINVAL;
+    if (A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
+    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
+    if (A->ld < A->n || !A->values) return DCD_EINVAL;
+    if (A->m > INT32_MAX) return DCD_EINVAL;
+    return DCD_OK;
+}
+
+size_t dtype_size(int dt) { return dt == DCD_F64 ? 8 : dt == DCD_F32 ? 4 : dt == DCD_BF16 ? 2 : 1; }
+
+KernelParams to_kp(const dcd_kernel *k) { return KernelParams{k->kind, k->degree, k->gamma, k->coef0}; }
+
+bool is_tc(int prec) { return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32; }
+
+// Operand preparation shared by the solver and the component entry points.
+struct Operand {
+    // FP64 path
+    const double *a64 = nullptr;
+    int64_t lda = 0;
+    // tensor-core path
+    void *packed = nullptr;
+    int64_t n_pad = 0;
+    int tf32 = 0;
+    float *row_h = nullptr;
+};
+
+struct EventTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    void init(bool enable, cudaStream_t s)
+    {
+        on = enable;
+        st = s;
+        if (on) {
+            cudaEventCreate(&ev[0]);
+            cudaEventCreate(&ev[1]);
+        }
+    }
+    void start()
+    {
+        if (on) cudaEventRecord(ev[0], st);
+    }
+    void stop(double &acc)
+    {
+        if (!on) return;
+        cudaEventRecord(ev[1], st);
+        cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        acc += ms;
+    }
+    ~EventTimer()
+    {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+    }
+};
+
+struct Solver {
+    // problem
+    int problem = 0;  // 0: K-SVM (DCD), 1: K-RR (BDCD)
+    const dcd_matrix *A = nullptr;
+    KernelParams kp{};
+    int loss = 1;
+    double C = 1.0, lambda = 1.0, omega = 0.0, nu = 0.0, diag = 0.0;
+    dcd_opts o{};
+    cudaStream_t st = nullptr;
+    int64_t m = 0, n = 0;
+    bool tc = false;
+    // caller / device arrays
+    const double *y = nullptr;
+    double *alpha = nullptr, *grad_out = nullptr;
+    double *g = nullptr;
+    // workspace
+    void *ws = nullptr;
+    Operand op;
+    void *As = nullptr;           // packed sampled rows (tc)
+    float *col_h = nullptr, *col_w = nullptr;
+    int32_t *S = nullptr;
+    void *Kss = nullptr;
+    int64_t ldk = 0;
+    double *delta = nullptr, *w64 = nullptr, *Lbuf = nullptr;
+    uint64_t *ctr = nullptr;
+    int *err = nullptr, *flag = nullptr;
+    double *partials = nullptr, *result = nullptr;
+    int32_t *iota = nullptr;
+    // host-io copies
+    void *h_vals = nullptr;
+    int64_t sb = 0, col_pad = 0;
+    dcd_stats stats{};
+
+    ~Solver()
+    {
+        if (ws) cudaFreeAsync(ws, st);
+    }
+
+    dcd_status check_device_error()
+    {
+        int e = 0;
+        DCD_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DCD_TRY(cudaStreamSynchronize(st));
+        switch (e) {
+        case DEV_OK: return DCD_OK;
+        case DEV_TIMEOUT: return DCD_ETIMEOUT;
+        case DEV_NOT_SPD: return DCD_ENOTSPD;
+        default: return DCD_EINTERNAL;
+        }
+    }
+
+    dcd_status setup(const double *y_in, double *alpha_in, double *grad_in)
+    {
+        m = A->m;
+        n = A->n;
+        tc = is_tc(o.prec);
+        const bool host = (o.flags & DCD_FLAG_HOST_IO) != 0;
+        sb = (int64_t)o.s * o.b;
+        col_pad = (sb + 255) / 256 * 256;
+        const int kb_elems = o.prec == DCD_PREC_TF32 ? 32 : 64;
+        const int64_t n_pad = (n + kb_elems - 1) / kb_elems * kb_elems;
+        const size_t esz = tc ? (o.prec == DCD_PREC_TF32 ? 4 : 2) : 8;
+        const bool need_pack = tc || A->dtype != DCD_F64 || host;
+
+        // size the arena (two passes over the same layout)
+        Arena ar;
+        for (int pass = 0; pass < 2; ++pass) {
+            ar.used = 0;
+            char *hv = (char *)ar.take(host ? (size_t)m * A->ld * dtype_size(A->dtype) : 0, 1024);
+            double *yv = (double *)ar.take(host ? sizeof(double) * m : 0);
+            double *av = (double *)ar.take(host ? sizeof(double) * m : 0);
+            double *gv = (double *)ar.take(sizeof(double) * m);
+            void *pk = ar.take(need_pack ? (size_t)m * (tc ? n_pad : n) * esz : 0, 1024);
+            float *rh = (float *)ar.take(tc ? sizeof(float) * m : 0);
+            void *as = ar.take(tc ? (size_t)sb * n_pad * esz : 0, 1024);
+            float *ch = (float *)ar.take(sizeof(float) * col_pad);
+            float *cw = (float *)ar.take(sizeof(float) * col_pad);
+            int32_t *sidx = (int32_t *)ar.take(sizeof(int32_t) * col_pad);
+            void *kss = ar.take((size_t)sb * sb * (tc ? 4 : 8));
+            double *dl = (double *)ar.take(sizeof(double) * col_pad);
+            double *wv = (double *)ar.take(sizeof(double) * col_pad);
+            double *lb = (double *)ar.take(problem == 1 ? sizeof(double) * o.s * o.b * (o.b + 1) : 0);
+            uint64_t *cr = (uint64_t *)ar.take(sizeof(uint64_t));
+            int *er = (int *)ar.take(sizeof(int) * 2);
+            double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
+            double *rs = (double *)ar.take(sizeof(double) * 4);
+            int64_t ichunk = std::min<int64_t>(m, SB_MAX);
+            int32_t *io = (int32_t *)ar.take(sizeof(int32_t) * ichunk);
+            if (pass == 0) {
+                cudaError_t e = cudaMallocAsync(&ws, ar.used + 1024, st);
+                if (e != cudaSuccess) return cuda_status(e);
+                ar.base = (char *)ws;
+                continue;
+            }
+            h_vals = hv;
+            g = gv;
+            op.packed = pk;
+            op.row_h = rh;
+            As = as;
+            col_h = ch;
+            col_w = cw;
+            S = sidx;
+            Kss = kss;
+            ldk = sb;
+            delta = dl;
+            w64 = wv;
+            Lbuf = lb;
+            ctr = cr;
+            err = er;
+            flag = er + 1;
+            partials = pt;
+            result = rs;
+            iota = io;
+            if (host) {
+                DCD_TRY(cudaMemcpyAsync(hv, A->values, (size_t)m * A->ld * dtype_size(A->dtype),
+                                        cudaMemcpyHostToDevice, st));
+                DCD_TRY(cudaMemcpyAsync(yv, y_in, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+                DCD_TRY(cudaMemcpyAsync(av, alpha_in, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+                y = yv;
+                alpha = av;
+            } else {
+                y = y_in;
+                alpha = alpha_in;
+            }
+        }
+        const void *vals = host ? h_vals : A->values;
+        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, st));
+        DCD_TRY(cudaMemsetAsync(col_h, 0, sizeof(float) * col_pad, st));
+        DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
+        DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
+        if (tc) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * n_pad * esz, st));
+        DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+
+        // operand
+        if (tc) {
+            op.n_pad = n_pad;
+            op.tf32 = o.prec == DCD_PREC_TF32;
+            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.tf32 ? 1 : 0, n_pad, m, err, st));
+            DCD_TRY(launch_row_terms(op.packed, op.tf32, n_pad, m, kp, op.row_h, st));
+        } else if (need_pack) {
+            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st));
+            op.a64 = (const double *)op.packed;
+            op.lda = n;
+        } else {
+            op.a64 = (const double *)vals;
+            op.lda = A->ld;
+        }
+
+        // labels
+        if (problem == 0) {
+            DCD_TRY(launch_label_check(y, m, flag, st));
+            int bad = 0;
+            DCD_TRY(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            DCD_TRY(cudaStreamSynchronize(st));
+            if (bad) return DCD_EINVAL;
+        }
+
+        // cached gradient: with device io and a caller array, the solver works
+        // on that array directly
+        if (!host && grad_in) g = grad_in;
+        if (o.flags & DCD_FLAG_GRAD_VALID) {
+            if (!grad_in) return DCD_EINVAL;
+            if (host)
+                DCD_TRY(cudaMemcpyAsync(g, grad_in, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        } else {
+            DCD_TRY(launch_init_grad(problem, y, alpha, diag, m, g, st));
+            DCD_TRY(launch_nnz_count(alpha, m, flag, st));
+            int nnz = 0;
+            DCD_TRY(cudaMemcpyAsync(&nnz, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            DCD_TRY(cudaStreamSynchronize(st));
+            if (nnz > 0) {
+                dcd_status s2 = full_pass();
+                if (s2 != DCD_OK) return s2;
+            }
+        }
+        return DCD_OK;
+    }
+
+    // g += rs * K(A, A_cols) w over all columns, in chunks of SB_MAX: the
+    // kernel part of the gradient for a nonzero alpha_0.
+    dcd_status full_pass()
+    {
+        std::vector<int32_t> hidx;
+        const int64_t chunk = std::min<int64_t>(m, std::min<int64_t>(SB_MAX, sb));
+        for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+            const int64_t cnt = std::min(chunk, m - c0);
+            hidx.resize(cnt);
+            for (int64_t j = 0; j < cnt; ++j) hidx[j] = (int32_t)(c0 + j);
+            DCD_TRY(cudaMemcpyAsync(S, hidx.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st));
+            DCD_TRY(launch_coef(problem == 0 ? y : nullptr, alpha, S, cnt, 1.0 / lambda, w64, st));
+            dcd_status s2 = apply_block(cnt);
+            if (s2 != DCD_OK) return s2;
+            DCD_TRY(cudaStreamSynchronize(st));  // hidx is reused
+        }
+        return DCD_OK;
+    }
+
+    // gather A_S for the tensor-core path
+    cudaError_t gather(int64_t ncols)
+    {
+        if (!tc) return cudaSuccess;
+        cudaError_t e = launch_pack_rows(op.packed, op.tf32 ? DCD_F32 : DCD_BF16, op.n_pad, m, op.n_pad, S, As,
+                                         op.tf32 ? 1 : 0, op.n_pad, ncols, err, st);
+        if (e != cudaSuccess) return e;
+        return launch_gather_f32(op.row_h, S, ncols, col_h, st);
+    }
+
+    cudaError_t gram(int64_t ncols)
+    {
+        if (tc) {
+            TcOperand B{As, ncols, op.n_pad, op.tf32};
+            return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
+                                   err, st);
+        }
+        return launch_block_simt_f64(op.a64, op.lda, m, n, kp, S, ncols, S, ncols, nullptr, nullptr, nullptr,
+                                     (double *)Kss, ldk, err, st);
+    }
+
+    dcd_status apply_block(int64_t ncols)
+    {
+        const double *rs = problem == 0 ? y : nullptr;
+        if (tc) {
+            // the coefficients in w64 (FP64) go to the FP32 column buffer
+            cudaError_t e = gather(ncols);
+            if (e != cudaSuccess) return cuda_status(e);
+            e = launch_f64_to_f32(w64, ncols, col_w, st);
+            if (e != cudaSuccess) return cuda_status(e);
+            e = clear_col_w_tail(ncols);
+            if (e != cudaSuccess) return cuda_status(e);
+            return cuda_status(block_tc_apply(ncols, rs));
+        }
+        return cuda_status(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr,
+                                                 0, err, st));
+    }
+
+    // Columns past ncols of the FP32 coefficient buffer must be zero: the
+    // tensor-core epilogue reads whole 32-column groups.
+    int64_t col_w_hi = 0;  // entries [0, col_w_hi) may be nonzero
+    cudaError_t clear_col_w_tail(int64_t ncols)
+    {
+        cudaError_t e = cudaSuccess;
+        if (col_w_hi > ncols) e = cudaMemsetAsync(col_w + ncols, 0, sizeof(float) * (col_w_hi - ncols), st);
+        col_w_hi = ncols;
+        return e;
+    }
+
+    cudaError_t block_tc_apply(int64_t ncols, const double *rs)
+    {
+        TcOperand Aop{op.packed, m, op.n_pad, op.tf32};
+        TcOperand Bop{As, ncols, op.n_pad, op.tf32};
+        return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st);
+    }
+
+    // Convergence measure from the cached gradient (reads back 4 doubles).
+    dcd_status measure(double &metric, double &primal, double &dual, double ynorm2)
+    {
+        DCD_TRY(launch_check(problem, g, alpha, y, m, C, loss, partials, result, st));
+        double r[4];
+        DCD_TRY(cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, st));
+        DCD_TRY(cudaStreamSynchronize(st));
+        if (problem == 1) {
+            metric = std::sqrt(r[0]) / std::sqrt(ynorm2 > 0 ? ynorm2 : 1.0);
+            primal = dual = 0.0;
+        } else {
+            // r = {a^T Q a, sum a, ||a||^2, hinge}; gap = P - D, reported relative to |P|
+            primal = 0.5 * r[0] + C * r[3];
+            dual = r[1] - 0.5 * r[0] - (loss == 2 ? r[2] / (4.0 * C) : 0.0);
+            metric = (primal - dual) / std::max(std::fabs(primal), 1e-300);
+        }
+        return DCD_OK;
+    }
+
+    // ---- outer-step loop, resumable (the plan API runs it in pieces) ----
+    double ynorm2 = 1.0;
+    int64_t done = 0, steps = 0;
+    double metric = 0.0, primal = 0.0, dual = 0.0;
+    bool conv = false, begun = false;
+    double ms_accum = 0.0;
+
+    dcd_status begin()
+    {
+        if (begun) return DCD_OK;
+        begun = true;
+        if (problem == 1) {  // ||y||^2 by the same reduction as the residual
+            DCD_TRY(launch_check(1, y, alpha, y, m, C, loss, partials, result, st));
+            DCD_TRY(cudaMemcpyAsync(&ynorm2, result, sizeof(double), cudaMemcpyDeviceToHost, st));
+            DCD_TRY(cudaStreamSynchronize(st));
+        }
+        stats.gpu_launches_per_step = tc ? 9 : 5;
+        return DCD_OK;
+    }
+
+    bool finished() const { return conv || done >= o.max_iters; }
+
+    // One outer s-step (a1..a6) of cnt inner iterations.
+    dcd_status outer_step(int64_t cnt, EventTimer &tm)
+    {
+        const int64_t ncols = cnt * o.b;
+        const double *rs = problem == 0 ? y : nullptr;
+        tm.start();
+        DCD_TRY(launch_sample(problem, o.seed, ctr, 0, m, o.b, cnt, S, err, st));
+        DCD_TRY(gather(ncols));
+        tm.stop(stats.ms_sample);
+        tm.start();
+        DCD_TRY(gram(ncols));
+        tm.stop(stats.ms_gram);
+        tm.start();
+        if (problem == 0)
+            DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
+                                     tc ? col_w : nullptr, err, st));
+        else
+            DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, Lbuf, delta, w64,
+                                      tc ? col_w : nullptr, err, st));
+        if (tc) DCD_TRY(clear_col_w_tail(ncols));
+        tm.stop(stats.ms_recur);
+        tm.start();
+        if (tc)
+            DCD_TRY(block_tc_apply(ncols, rs));
+        else
+            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr, 0, err,
+                                          st));
+        tm.stop(stats.ms_block);
+        tm.start();
+        DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+        tm.stop(stats.ms_update);
+        done += cnt;
+        ++steps;
+        return DCD_OK;
+    }
+
+    // Runs up to max_steps outer steps (all remaining if < 0), then measures
+    // the convergence metric and publishes alpha / grad / stats.
+    dcd_status run_steps(int64_t max_steps, dcd_stats *st_out)
+    {
+        dcd_status s0 = begin();
+        if (s0 != DCD_OK) return s0;
+        EventTimer tm;
+        tm.init((o.flags & DCD_FLAG_PHASE_TIMERS) != 0, st);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        const int check_every = o.check_every > 0 ? o.check_every : 0;
+        for (int64_t k = 0; !finished() && (max_steps < 0 || k < max_steps); ++k) {
+            const int64_t cnt = std::min<int64_t>(o.s, o.max_iters - done);
+            s0 = outer_step(cnt, tm);
+            if (s0 != DCD_OK) break;
+            if (check_every && o.tol > 0 && steps % check_every == 0 && done < o.max_iters) {
+                tm.start();
+                s0 = measure(metric, primal, dual, ynorm2);
+                tm.stop(stats.ms_check);
+                if (s0 != DCD_OK) break;
+                if (metric <= o.tol) conv = true;
+            }
+        }
+        // the metric is measured at check points and when the budget ends;
+        // an intermediate dcd_plan_run without a tolerance leaves it NaN
+        if (s0 == DCD_OK && (finished() || o.tol > 0)) {
+            s0 = measure(metric, primal, dual, ynorm2);
+            if (s0 == DCD_OK && o.tol > 0 && metric <= o.tol) conv = true;
+        } else if (s0 == DCD_OK) {
+            metric = primal = dual = NAN;
+        }
+        dcd_status se = check_device_error();
+        if (s0 == DCD_OK) s0 = se;
+        if (s0 == DCD_OK) s0 = publish();
+        cudaEventRecord(e1, st);
+        cudaStreamSynchronize(st);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ms_accum += ms;
+        stats.iters_done = done;
+        stats.outer_steps = steps;
+        stats.converged = conv ? 1 : 0;
+        stats.final_metric = metric;
+        stats.primal = primal;
+        stats.dual = dual;
+        stats.ms_total = ms_accum;
+        if (st_out) *st_out = stats;
+        if (s0 != DCD_OK) return s0;
+        if (o.tol > 0 && !conv && done >= o.max_iters) return DCD_ENOTCONV;
+        return DCD_OK;
+    }
+
+    // alpha (host-io only) and the cached gradient back to the caller.
+    dcd_status publish()
+    {
+        const bool host = (o.flags & DCD_FLAG_HOST_IO) != 0;
+        if (host) {
+            DCD_TRY(cudaMemcpyAsync(alpha_host, alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            if (grad_out) DCD_TRY(cudaMemcpyAsync(grad_out, g, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        }
+        return DCD_OK;  // device io: g is the caller's grad array (or internal)
+    }
+
+    dcd_status run(dcd_stats *st_out) { return run_steps(-1, st_out); }
+
+    double *alpha_host = nullptr;
+};
+
+dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem)
+{
+    if (!o) return DCD_EINVAL;
+    if (o->s < 1 || o->b < 1 || o->max_iters < 0) return DCD_EINVAL;
+    if (problem == 0 && o->b != 1) return DCD_EINVAL;
+    if (o->b > B_MAX || o->b > m) return DCD_EINVAL;
+    if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
+    if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
+    if (o->prec == DCD_PREC_FP8 || o->prec == DCD_PREC_BF16X3) return DCD_EUNSUPPORTED;
+    if (o->prec != DCD_PREC_FP64 && o->prec != DCD_PREC_TF32 && o->prec != DCD_PREC_BF16) return DCD_EINVAL;
+    if (is_tc(o->prec) && !tc_available()) return DCD_EUNSUPPORTED;
+    return DCD_OK;
+}
+
+dcd_status prepare(Solver &sv, const double *y, double *alpha, double *grad)
+{
+    if (!y || !alpha) return DCD_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DCD_ECUDA;
+    if (sv.o.flags & DCD_FLAG_HOST_IO) sv.alpha_host = alpha;
+    sv.grad_out = grad;
+    return sv.setup(y, alpha, grad);
+}
+
+dcd_status init_svm(Solver &sv, const dcd_matrix *A, const dcd_kernel *k, int32_t loss, double C, const dcd_opts *o,
+                    void *stream)
+{
+    dcd_status s = validate_dense(A);
+    if (s != DCD_OK) return s;
+    if ((s = validate_kernel(k)) != DCD_OK) return s;
+    if (loss != 1 && loss != 2) return DCD_EINVAL;
+    if (!finite_pos(C)) return DCD_EINVAL;
+    if ((s = validate_opts(o, A->m, 0)) != DCD_OK) return s;
+    sv.problem = 0;
+    sv.A = A;
+    sv.kp = to_kp(k);
+    sv.loss = loss;
+    sv.C = C;
+    sv.omega = loss == 2 ? 1.0 / (2.0 * C) : 0.0;
+    sv.nu = loss == 2 ? INFINITY : C;
+    sv.diag = sv.omega;
+    sv.o = *o;
+    sv.st = (cudaStream_t)stream;
+    return DCD_OK;
+}
+
+dcd_status init_krr(Solver &sv, const dcd_matrix *A, const dcd_kernel *k, double lambda, const dcd_opts *o,
+                    void *stream)
+{
+    dcd_status s = validate_dense(A);
+    if (s != DCD_OK) return s;
+    if ((s = validate_kernel(k)) != DCD_OK) return s;
+    if (!finite_pos(lambda)) return DCD_EINVAL;
+    if ((s = validate_opts(o, A->m, 1)) != DCD_OK) return s;
+    sv.problem = 1;
+    sv.A = A;
+    sv.kp = to_kp(k);
+    sv.lambda = lambda;
+    sv.diag = (double)A->m;
+    sv.o = *o;
+    sv.st = (cudaStream_t)stream;
+    return DCD_OK;
+}
+
+}  // namespace
+}  // namespace dcd
+
+using namespace dcd;
+
+struct dcd_plan {
+    Solver sv;
+};
+
+extern "C" dcd_status dcd_svm_solve(const dcd_matrix *A, const double *y, const dcd_kernel *k, int32_t loss, double C,
+                                    const dcd_opts *o, double *alpha, double *grad, dcd_stats *st, void *stream)
+{
+    Solver sv;
+    dcd_status s = init_svm(sv, A, k, loss, C, o, stream);
+    if (s == DCD_OK) s = prepare(sv, y, alpha, grad);
+    if (s == DCD_OK) s = sv.run(st);
+    return s;
+}
+
+extern "C" dcd_status bdcd_krr_solve(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda,
+                                     const dcd_opts *o, double *alpha, double *grad, dcd_stats *st, void *stream)
+{
+    Solver sv;
+    dcd_status s = init_krr(sv, A, k, lambda, o, stream);
+    if (s == DCD_OK) s = prepare(sv, y, alpha, grad);
+    if (s == DCD_OK) s = sv.run(st);
+    return s;
+}
+
+extern "C" dcd_status dcd_svm_plan_create(const dcd_matrix *A, const double *y, const dcd_kernel *k, int32_t loss,
+                                          double C, const dcd_opts *o, double *alpha, double *grad, void *stream,
+                                          dcd_plan **plan)
+{
+    if (!plan) return DCD_EINVAL;
+    *plan = nullptr;
+    dcd_plan *p = new (std::nothrow) dcd_plan;
+    if (!p) return DCD_ENOMEM;
+    dcd_status s = init_svm(p->sv, A, k, loss, C, o, stream);
+    if (s == DCD_OK) s = prepare(p->sv, y, alpha, grad);
+    if (s != DCD_OK) {
+        delete p;
+        return s;
+    }
+    *plan = p;
+    return DCD_OK;
+}
+
+extern "C" dcd_status bdcd_krr_plan_create(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda,
+                                           const dcd_opts *o, double *alpha, double *grad, void *stream,
+                                           dcd_plan **plan)
+{
+    if (!plan) return DCD_EINVAL;
+    *plan = nullptr;
+    dcd_plan *p = new (std::nothrow) dcd_plan;
+    if (!p) return DCD_ENOMEM;
+    dcd_status s = init_krr(p->sv, A, k, lambda, o, stream);
+    if (s == DCD_OK) s = prepare(p->sv, y, alpha, grad);
+    if (s != DCD_OK) {
+        delete p;
+        return s;
+    }
+    *plan = p;
+    return DCD_OK;
+}
+
+extern "C" dcd_status dcd_plan_run(dcd_plan *plan, int64_t max_outer_steps, dcd_stats *st)
+{
+    if (!plan) return DCD_EINVAL;
+    return plan->sv.run_steps(max_outer_steps, st);
+}
+
+extern "C" dcd_status dcd_plan_destroy(dcd_plan *plan)
+{
+    if (!plan) return DCD_OK;
+    cudaStream_t st = plan->sv.st;
+    delete plan;
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+extern "C" const char *dcd_status_string(int32_t s)
+{
+    switch (s) {
+    case DCD_OK: return "DCD_OK";
+    case DCD_EINVAL: return "DCD_EINVAL: invalid argument";
+    case DCD_ENOMEM: return "DCD_ENOMEM: device allocation failed";
+    case DCD_ECUDA: return "DCD_ECUDA: CUDA runtime error";
+    case DCD_ETIMEOUT: return "DCD_ETIMEOUT: bounded device wait expired";
+    case DCD_ENOTCONV: return "DCD_ENOTCONV: iteration budget reached before tolerance";
+    case DCD_EINTERNAL: return "DCD_EINTERNAL: device-side check failed";
+    case DCD_ENOTSPD: return "DCD_ENOTSPD: block system not positive definite";
+    case DCD_EUNSUPPORTED: return "DCD_EUNSUPPORTED: not implemented in this build";
+    default: return "unknown dcd_status";
+    }
+}
+
+extern "C" dcd_status dcd_sample_indices(int32_t method, uint64_t seed, int64_t m, int32_t b, uint64_t first,
+                                         int64_t count, int32_t *out, void *stream)
+{
+    if ((method != 0 && method != 1) || m < 1 || m > INT32_MAX || count < 0 || !out) return DCD_EINVAL;
+    if (method == 1 && (b < 1 || b > m)) return DCD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_sample(method, seed, nullptr, first, m, method == 1 ? b : 1, count, out, nullptr, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
+namespace {
+
+// Scratch memory of one component call, freed (stream-ordered) on return.
+struct ComponentBufs {
+    void *mem = nullptr;
+    cudaStream_t st = nullptr;
+    ~ComponentBufs()
+    {
+        if (mem) cudaFreeAsync(mem, st);
+    }
+};
+
+size_t place(size_t &cur, size_t bytes, size_t align = 1024)
+{
+    size_t off = (cur + align - 1) / align * align;
+    cur = off + bytes;
+    return off;
+}
+
+dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t prec)
+{
+    dcd_status s = validate_dense(A);
+    if (s != DCD_OK) return s;
+    if ((s = validate_kernel(k)) != DCD_OK) return s;
+    if (prec == DCD_PREC_FP8 || prec == DCD_PREC_BF16X3) return DCD_EUNSUPPORTED;
+    if (prec != DCD_PREC_FP64 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16) return DCD_EINVAL;
+    if (is_tc(prec) && !tc_available()) return DCD_EUNSUPPORTED;
+    return DCD_OK;
+}
+
+dcd_status finish_component(int *err, cudaStream_t st)
+{
+    int he = 0;
+    DCD_TRY(cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DCD_TRY(cudaStreamSynchronize(st));
+    if (he == DEV_TIMEOUT) return DCD_ETIMEOUT;
+    if (he == DEV_BAD_INDEX) return DCD_EINVAL;
+    return he ? DCD_EINTERNAL : DCD_OK;
+}
+
+// Runs the kernel block on rows `rows` (or the first nrows) against columns
+// `cols`: store into `out` (w == nullptr) or apply into g.
+dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
+                           int64_t nrows, const int32_t *cols, int64_t ncols, const double *w, const double *rs,
+                           double *g, void *out, int64_t ldo, cudaStream_t st)
+{
+    const KernelParams kp = to_kp(k);
+    ComponentBufs cb;
+    cb.st = st;
+    if (!is_tc(prec)) {
+        const bool pack = A->dtype != DCD_F64;
+        size_t cur = 0;
+        size_t oe = place(cur, 256);
+        size_t op64 = place(cur, pack ? sizeof(double) * A->m * A->n : 0);
+        DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+        char *base = (char *)cb.mem;
+        int *err = (int *)(base + oe);
+        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        const double *a64 = (const double *)A->values;
+        int64_t lda = A->ld;
+        if (pack) {
+            double *p = (double *)(base + op64);
+            DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, p, 2, A->n, A->m, err, st));
+            a64 = p;
+            lda = A->n;
+        }
+        DCD_TRY(launch_block_simt_f64(a64, lda, A->m, A->n, kp, rows, nrows, cols, ncols, w, rs, g, (double *)out,
+                                      ldo, err, st));
+        return finish_component(err, st);
+    }
+    const int tf32 = prec == DCD_PREC_TF32;
+    const int kb = tf32 ? 32 : 64;
+    const int64_t n_pad = (A->n + kb - 1) / kb * kb;
+    const size_t esz = tf32 ? 4 : 2;
+    const int64_t cpad = (ncols + 255) / 256 * 256;
+    size_t cur = 0;
+    size_t oe = place(cur, 256);
+    size_t oa = place(cur, (size_t)nrows * n_pad * esz);
+    size_t ob = place(cur, (size_t)ncols * n_pad * esz);
+    size_t orh = place(cur, sizeof(float) * nrows);
+    size_t och = place(cur, sizeof(float) * cpad);
+    size_t ocw = place(cur, sizeof(float) * cpad);
+    DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+    char *base = (char *)cb.mem;
+    int *err = (int *)(base + oe);
+    void *pa = base + oa, *pb = base + ob;
+    float *rh = (float *)(base + orh), *ch = (float *)(base + och), *cw = (float *)(base + ocw);
+    DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
+    DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
+    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, tf32, n_pad, nrows, err, st));
+    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, tf32, n_pad, ncols, err, st));
+    DCD_TRY(launch_row_terms(pa, tf32, n_pad, nrows, kp, rh, st));
+    DCD_TRY(launch_row_terms(pb, tf32, n_pad, ncols, kp, ch, st));
+    if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
+    TcOperand Aop{pa, nrows, n_pad, tf32}, Bop{pb, ncols, n_pad, tf32};
+    DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st));
+    return finish_component(err, st);
+}
+
+}  // namespace
+
+extern "C" dcd_status dcd_kernel_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
+                                       int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,
+                                       void *stream)
+{
+    dcd_status s = component_check(A, k, prec);
+    if (s != DCD_OK) return s;
+    if (nrows < 0 || ncols < 0 || !cols || !out || ldo < ncols) return DCD_EINVAL;
+    if (!rows && nrows > A->m) return DCD_EINVAL;
+    if (nrows == 0 || ncols == 0) return DCD_OK;
+    return component_block(A, k, prec, rows, nrows, cols, ncols, nullptr, nullptr, nullptr, out, ldo,
+                           (cudaStream_t)stream);
+}
+
+extern "C" dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int32_t prec,
+                                             const int32_t *cols, int64_t ncols, const double *w,
+                                             const double *rowscale, double *g, void *stream)
+{
+    dcd_status s = component_check(A, k, prec);
+    if (s != DCD_OK) return s;
+    if (ncols < 0 || (ncols > 0 && (!cols || !w)) || !g) return DCD_EINVAL;
+    if (ncols == 0) return DCD_OK;
+    return component_block(A, k, prec, nullptr, A->m, cols, ncols, w, rowscale, g, nullptr, 0, (cudaStream_t)stream);
+}

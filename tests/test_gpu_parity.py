@@ -1,0 +1,277 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Sizes span several row tiles (64-row FP64 tiles, 128-row tensor-core tiles)
+with ragged tails in rows, features (k-blocks of 64 / 32) and sampled
+columns (32-column epilogue groups).
+
+Tolerances:
+  FP64 form          iterates within 1e-10 relative 2-norm (the FP64 target);
+                     kernel entries within 1e-12 relative.
+  mixed (bf16/tf32)  kernel entries against the oracle evaluated on the same
+                     rounded inputs: FP32 accumulation over n <= 128 products
+                     plus ex2.approx give |err| <= 3e-5 * max|K|; iterates:
+                     final dual objective within 1e-6 relative and alpha within
+                     1e-4 relative 2-norm of the FP64 oracle on the same index
+                     stream (the mixed-precision target).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_18001_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_2406_18001_gb300 import binding
+    return binding
+
+
+def dev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def round_bf16(A):
+    return inputs.bf16_bits_to_f32(inputs.to_bf16_bits(A.astype(np.float32))).astype(np.float64)
+
+
+def round_tf32(A):
+    u = np.ascontiguousarray(A, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    # nearest, ties away from zero, to 10 explicit mantissa bits
+    r = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+KERNELS = [("rbf", dict(gamma=0.35)), ("poly", dict(coef0=1.0, degree=3)), ("linear", {})]
+
+
+# ------------------------------------------------------------ sampling ----
+@pytest.mark.parametrize("m,first,count", [(1, 0, 5), (97, 0, 1000), (50000, 123456789, 4096)])
+def test_dcd_sampler_bit_exact(m, first, count):
+    got = B().sample_indices(0, 42, m, 1, first, count).cpu().numpy()
+    assert np.array_equal(got, oracle.sample_dcd(42, m, first, count))
+
+
+@pytest.mark.parametrize("m,b,first,nblk", [(16, 16, 0, 3), (100, 7, 5, 40), (50000, 16, 2**40, 64),
+                                            (400, 128, 9, 8)])
+def test_bdcd_sampler_bit_exact(m, b, first, nblk):
+    got = B().sample_indices(1, 7, m, b, first, nblk).cpu().numpy().reshape(nblk, b)
+    assert np.array_equal(got, oracle.sample_bdcd(7, m, b, first, nblk))
+
+
+# ------------------------------------------------------- kernel blocks ----
+@pytest.mark.parametrize("kind,kw", KERNELS)
+def test_kernel_block_fp64(kind, kw):
+    g = np.random.default_rng(1)
+    A = g.standard_normal((300, 37)) * 0.3
+    cols = g.integers(0, 300, size=70)
+    rows = g.integers(0, 300, size=133)
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    got = B().kernel_block(dev(A), kb, "fp64", dev(cols, torch.int32), rows=dev(rows, torch.int32)).cpu().numpy()
+    want = oracle.kernel_block(ko, A, cols, rows=rows)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("kind,kw", KERNELS)
+def test_kernel_block_tensor_core(prec, kind, kw):
+    g = np.random.default_rng(2)
+    A = (g.standard_normal((300, 77)) * 0.2).astype(np.float32)
+    cols = g.integers(0, 300, size=70)
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    got = B().kernel_block(dev(A), kb, prec, dev(cols, torch.int32)).cpu().numpy()
+    Ar = round_bf16(A) if prec == "bf16" else round_tf32(A)
+    want = oracle.kernel_block(ko, Ar, cols)
+    err = np.max(np.abs(got - want))
+    assert err <= 3e-5 * np.max(np.abs(want)), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32"])
+@pytest.mark.parametrize("kind,kw", KERNELS)
+def test_kernel_block_apply(prec, kind, kw):
+    """g += rs * K(A, A_cols) w for every row, block never stored."""
+    g = np.random.default_rng(3)
+    m, n = 333, 45
+    A = g.standard_normal((m, n)) * 0.25
+    cols = g.integers(0, m, size=45)
+    w = g.standard_normal(45)
+    rs = np.where(g.random(m) < 0.5, -1.0, 1.0)
+    g0 = g.standard_normal(m)
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    gd = dev(g0)
+    B().kernel_block_apply(dev(A if prec == "fp64" else A.astype(np.float32)), kb, prec, dev(cols, torch.int32),
+                           dev(w), gd, rowscale=dev(rs))
+    Ar = A if prec == "fp64" else (round_bf16(A) if prec == "bf16" else round_tf32(A))
+    want = g0 + rs * (oracle.kernel_block(ko, Ar, cols) @ w)
+    got = gd.cpu().numpy()
+    scale = np.max(np.abs(oracle.kernel_block(ko, Ar, cols))) * np.sum(np.abs(w))
+    tol = 1e-12 if prec == "fp64" else 3e-5
+    assert np.max(np.abs(got - want)) <= tol * scale
+
+
+def test_kernel_block_bad_index_is_an_error_not_a_fault():
+    A = dev(np.ones((10, 4)))
+    with pytest.raises(B().DcdError) as e:
+        B().kernel_block(A, B().kernel("linear"), "fp64", dev(np.array([1, 10]), torch.int32))
+    assert e.value.status == B().EINVAL
+    with pytest.raises(B().DcdError):
+        B().kernel_block(A.float(), B().kernel("linear"), "bf16", dev(np.array([-1, 2]), torch.int32))
+
+
+# ---------------------------------------------------- FP64 form solves ----
+SVM_CASES = [
+    (1, "rbf", dict(gamma=0.4), 1, 1.0),
+    (1, "rbf", dict(gamma=0.4), 8, 1.0),
+    (2, "poly", dict(coef0=1.0, degree=3), 5, 0.5),
+    (1, "linear", {}, 16, 0.7),
+    (2, "rbf", dict(gamma=0.1), 32, 2.0),
+]
+
+
+@pytest.mark.parametrize("loss,kind,kw,s,C", SVM_CASES)
+def test_dcd_fp64_iterates_match_oracle(loss, kind, kw, s, C):
+    p = inputs.blobs(m=400, n=19, seed=3)
+    A = p.A * 0.5
+    H = 1203  # not a multiple of s: the last outer step is shorter
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    al, gr, st, rc = B().svm_solve(dev(A), dev(p.y), kb, loss, C, s, H, seed=11, prec="fp64")
+    want = oracle.dcd_svm(A, p.y, ko, loss, C, H, seed=11)
+    assert st["iters_done"] == H and st["outer_steps"] == -(-H // s)
+    assert rel(al.cpu().numpy(), want) < 1e-10
+    # the cached gradient equals the gradient of the returned alpha
+    gw = oracle.svm_gradient(A, p.y, ko, loss, C, al.cpu().numpy())
+    assert rel(gr.cpu().numpy(), gw) < 1e-10
+
+
+def test_dcd_fp64_repeated_indices_within_a_step():
+    p = inputs.blobs(m=7, n=5, seed=4)
+    assert len(set(oracle.sample_dcd(2, 7, 0, 16))) < 16
+    kb, ko = B().kernel("rbf", gamma=0.5), oracle.kernel("rbf", gamma=0.5)
+    for loss in (1, 2):
+        al, _, _, _ = B().svm_solve(dev(p.A), dev(p.y), kb, loss, 0.8, 16, 160, seed=2, prec="fp64")
+        want = oracle.sstep_dcd_svm(p.A, p.y, ko, loss, 0.8, 16, 160, seed=2)
+        assert rel(al.cpu().numpy(), want) < 1e-10
+
+
+KRR_CASES = [
+    ("rbf", dict(gamma=0.5), 4, 1, 1e-2),
+    ("rbf", dict(gamma=0.5), 16, 8, 1e-3),
+    ("poly", dict(coef0=0.5, degree=2), 8, 3, 1e-1),
+    ("linear", {}, 1, 32, 1e-2),
+    ("rbf", dict(gamma=2.0), 64, 2, 1e-4),
+]
+
+
+@pytest.mark.parametrize("kind,kw,b,s,lam", KRR_CASES)
+def test_bdcd_fp64_iterates_match_oracle(kind, kw, b, s, lam):
+    p = inputs.krr_dense(m=350, n=23, seed=5, dtype=np.float64)
+    H = 301
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    al, gr, st, rc = B().krr_solve(dev(p.A), dev(p.y), kb, lam, b, s, H, seed=9, prec="fp64")
+    want = oracle.bdcd_krr(p.A, p.y, ko, lam, b, H, seed=9)
+    assert rel(al.cpu().numpy(), want) < 1e-10
+    gw = oracle.krr_gradient(p.A, p.y, ko, lam, al.cpu().numpy())
+    assert rel(gr.cpu().numpy(), gw) < 1e-10
+
+
+def test_bdcd_fp64_overlapping_blocks_small_m():
+    p = inputs.krr_dense(m=12, n=3, seed=6, dtype=np.float64)
+    kb, ko = B().kernel("rbf", gamma=0.7), oracle.kernel("rbf", gamma=0.7)
+    al, _, _, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.1, 4, 16, 37, seed=4, prec="fp64", start_iter=3)
+    want = oracle.sstep_bdcd_krr(p.A, p.y, ko, 0.1, 4, 16, 37, seed=4, first_block=3)
+    assert rel(al.cpu().numpy(), want) < 1e-10
+
+
+def test_bdcd_fp64_full_block_reaches_closed_form():
+    p = inputs.krr_dense(m=64, n=5, seed=7, dtype=np.float64)
+    kb, ko = B().kernel("rbf", gamma=1.0), oracle.kernel("rbf", gamma=1.0)
+    al, _, st, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.05, 64, 1, 1, seed=0, prec="fp64")
+    assert rel(al.cpu().numpy(), oracle.krr_closed_form(p.A, p.y, ko, 0.05)) < 1e-12
+
+
+def test_bdcd_fp64_converges_with_tolerance():
+    p = inputs.krr_dense(m=500, n=8, seed=8, dtype=np.float64)
+    kb, ko = B().kernel("rbf", gamma=0.5), oracle.kernel("rbf", gamma=0.5)
+    al, gr, st, rc = B().krr_solve(dev(p.A), dev(p.y), kb, 0.01, 16, 8, 200000, seed=1, prec="fp64", tol=1e-9,
+                                   check_every=4)
+    assert rc == B().OK and st["converged"] == 1 and st["final_metric"] <= 1e-9
+    star = oracle.krr_closed_form(p.A, p.y, ko, 0.01)
+    assert rel(al.cpu().numpy(), star) < 1e-7
+
+
+def test_resume_split_run_is_bit_identical():
+    p = inputs.krr_dense(m=300, n=11, seed=9, dtype=np.float64)
+    kb = B().kernel("rbf", gamma=0.5)
+    a1, g1, _, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.02, 8, 4, 100, seed=5, prec="fp64")
+    a2, g2, _, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.02, 8, 4, 40, seed=5, prec="fp64")
+    a2, g2, _, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.02, 8, 4, 60, seed=5, prec="fp64", alpha=a2, grad=g2,
+                                 start_iter=40, flags=B().FLAG_GRAD_VALID)
+    assert torch.equal(a1, a2) and torch.equal(g1, g2)
+
+
+def test_nonzero_alpha0_gradient_pass():
+    p = inputs.blobs(m=260, n=9, seed=10)
+    kb, ko = B().kernel("rbf", gamma=0.3), oracle.kernel("rbf", gamma=0.3)
+    a0 = np.random.default_rng(0).uniform(0, 0.5, 260)
+    al, gr, _, _ = B().svm_solve(dev(p.A), dev(p.y), kb, 1, 1.0, 4, 301, seed=3, prec="fp64", alpha=dev(a0))
+    want = oracle.dcd_svm(p.A, p.y, ko, 1, 1.0, 301, seed=3, alpha0=a0)
+    assert rel(al.cpu().numpy(), want) < 1e-10
+    assert rel(gr.cpu().numpy(), oracle.svm_gradient(p.A, p.y, ko, 1, 1.0, want)) < 1e-10
+
+
+def test_host_io_matches_device_path():
+    p = inputs.krr_dense(m=200, n=10, seed=11, dtype=np.float64)
+    kb = B().kernel("rbf", gamma=0.5)
+    ad, gd, _, _ = B().krr_solve(dev(p.A), dev(p.y), kb, 0.05, 4, 4, 50, seed=1, prec="fp64")
+    ah, gh, _, _ = B().krr_solve(np.ascontiguousarray(p.A), p.y.copy(), kb, 0.05, 4, 4, 50, seed=1, prec="fp64",
+                                 flags=B().FLAG_HOST_IO)
+    assert np.array_equal(ad.cpu().numpy(), ah) and np.array_equal(gd.cpu().numpy(), gh)
+
+
+def test_svm_rejects_non_binary_labels():
+    p = inputs.blobs(m=50, n=3, seed=1)
+    y = p.y.copy()
+    y[3] = 0.5
+    with pytest.raises(B().DcdError) as e:
+        B().svm_solve(dev(p.A), dev(y), B().kernel("linear"), 1, 1.0, 1, 10, prec="fp64")
+    assert e.value.status == B().EINVAL
+
+
+# --------------------------------------------------- mixed-form solves ----
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("s", [1, 16])
+def test_bdcd_mixed_matches_oracle(prec, s):
+    p = inputs.krr_dense(m=1000, n=64, seed=12, dtype=np.float32)
+    A64 = p.A.astype(np.float64)
+    lam, b, H = 1e-2, 16, 640
+    kb, ko = B().kernel("rbf", gamma=0.5), oracle.kernel("rbf", gamma=0.5)
+    al, gr, st, _ = B().krr_solve(dev(p.A), dev(p.y), kb, lam, b, s, H, seed=3, prec=prec)
+    want = oracle.bdcd_krr(A64, p.y, ko, lam, b, H, seed=3)
+    a = al.cpu().numpy()
+    assert rel(a, want) < 1e-4
+    f_got = oracle.krr_objective(A64, p.y, ko, lam, a)
+    f_want = oracle.krr_objective(A64, p.y, ko, lam, want)
+    assert abs(f_got - f_want) <= 1e-6 * abs(f_want)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_dcd_mixed_matches_oracle(prec):
+    p = inputs.blobs(m=700, n=64, seed=13)
+    kb, ko = B().kernel("rbf", gamma=1 / 128), oracle.kernel("rbf", gamma=1 / 128)
+    al, _, st, _ = B().svm_solve(dev(p.A.astype(np.float32)), dev(p.y), kb, 1, 1.0, 8, 2000, seed=0, prec=prec)
+    want = oracle.sstep_dcd_svm(p.A, p.y, ko, 1, 1.0, 8, 2000, seed=0)
+    a = al.cpu().numpy()
+    f = oracle.svm_objectives(p.A, p.y, ko, 1, 1.0, a)
+    fw = oracle.svm_objectives(p.A, p.y, ko, 1, 1.0, want)
+    assert abs(f["dual"] - fw["dual"]) <= 1e-6 * abs(fw["dual"])
+    assert rel(a, want) < 1e-4
