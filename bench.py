@@ -93,7 +93,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
@@ -241,13 +241,14 @@ def run_gpu(args):
     t_block = phase["block"] * 1e-3
     hbm_peak, bf16_peak, bf16_sus, src = peaks()
     sb = args.s * args.b
-    esz = 2 if args.prec == "bf16" else (4 if args.prec == "tf32" else 8)
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "fp64": 8}[args.prec]
+    mma_mult = 3 if args.prec == "bf16x3" else 1  # MMAs per k-step
     n_alg = args.n
-    flops = 2.0 * args.m * n_alg * sb
+    flops = 2.0 * args.m * n_alg * sb * mma_mult
     bytes_ = args.m * n_alg * esz + sb * n_alg * esz + args.m * (8 + 8 + 4)
     intensity = flops / bytes_
     ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
-    if args.prec == "bf16" and intensity >= ridge:
+    if args.prec in ("bf16", "bf16x3") and intensity >= ridge:
         roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
     else:
         roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
@@ -311,7 +312,7 @@ def main():
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32", "bf16x3", "fp64"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")

@@ -74,7 +74,8 @@ typedef enum {
     DCD_PREC_TF32 = 1,   /* tcgen05 kind::tf32 block, FP32 accumulation */
     DCD_PREC_BF16 = 2,   /* tcgen05 kind::f16 (bf16) block, FP32 accumulation */
     DCD_PREC_FP8 = 3,    /* reserved */
-    DCD_PREC_BF16X3 = 4  /* reserved */
+    DCD_PREC_BF16X3 = 4  /* split bf16: a = hi + lo, three tcgen05 kind::f16 MMAs per
+                            k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
 } dcd_precision;
 
 /* opts.flags */

@@ -33,11 +33,16 @@ namespace {
 
 constexpr int BM = 128;                 // rows per tile = TMEM lanes
 constexpr int BN_MAX = 256;             // columns per N-chunk (max)
-constexpr int STAGES = 4;
 constexpr int ROW_BYTES = 128;          // one swizzled k-block row
 constexpr int A_STAGE = BM * ROW_BYTES;          // 16 KB
 constexpr int B_STAGE = BN_MAX * ROW_BYTES;      // 32 KB
-constexpr int RING_BYTES = STAGES * (A_STAGE + B_STAGE);
+constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 split stages
+
+// Operand modes: bf16 (kind::f16), tf32 (kind::tf32 on fp32 storage), and
+// split bf16 ("bf16x3": a = hi + lo with hi = bf16(a), lo = bf16(a - hi);
+// a.b ~ hi.hi + hi.lo + lo.hi, three MMAs per k-step into one accumulator,
+// dropping only lo.lo, about 2^-16 relative).
+constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2;
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
@@ -186,6 +191,7 @@ __device__ __forceinline__ float ex2f(float x)
 }
 
 struct TcArgs {
+    int lo_off;           // split mode: column offset of the lo halves (= n_pad)
     const float *row_h;   // per-row RBF term gamma*log2(e)*||a_i||^2 (nrows_out entries)
     const float *col_h;   // per-column term, padded with zeros to nchunks*BN
     const float *col_w;   // apply: coefficients, padded with zeros
@@ -232,14 +238,19 @@ __device__ __forceinline__ void item_range(const TcArgs &a, int item, int &tile,
     }
 }
 
-template <bool TF32, int KIND>
+template <int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     block_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
+    constexpr bool TF32 = MODE == MODE_TF32;
+    constexpr bool SPLIT = MODE == MODE_BF16X3;
+    constexpr int STAGES = SPLIT ? 2 : 4;
+    constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
+    constexpr int B_ST = SPLIT ? 2 * B_STAGE : B_STAGE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * A_STAGE;
+    uint8_t *sB = smem + STAGES * A_ST;
     uint64_t *bars = (uint64_t *)(smem + RING_BYTES);
     uint64_t *full = bars;                 // STAGES
     uint64_t *empty = bars + STAGES;       // STAGES
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // ---------------------------------------------------- producer --
             uint32_t it = 0;
             bool ok = true;
-            const uint32_t bytes = (uint32_t)(A_STAGE + bn * ROW_BYTES);
+            const uint32_t bytes = (uint32_t)((SPLIT ? 2 : 1) * (A_STAGE + bn * ROW_BYTES));
             for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
                 int tile, c0, c1;
                 item_range(a, item, tile, c0, c1);
@@ -298,8 +309,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             break;
                         }
                         mbar_expect_tx(&full[s], bytes);
-                        tma_load_2d(sA + s * A_STAGE, &tmA, &full[s], kb * kb_elems, tile * BM);
-                        tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], kb * kb_elems, nc * bn);
+                        tma_load_2d(sA + s * A_ST, &tmA, &full[s], kb * kb_elems, tile * BM);
+                        tma_load_2d(sB + s * B_ST, &tmB, &full[s], kb * kb_elems, nc * bn);
+                        if (SPLIT) {
+                            tma_load_2d(sA + s * A_ST + A_STAGE, &tmA, &full[s], a.lo_off + kb * kb_elems, tile * BM);
+                            tma_load_2d(sB + s * B_ST + B_STAGE, &tmB, &full[s], a.lo_off + kb * kb_elems, nc * bn);
+                        }
                     }
             }
             if (!ok) {  // let every issued copy land before the CTA exits
@@ -331,11 +346,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             break;
                         }
                         fence_after();
-                        const uint32_t ab = su32(sA + s * A_STAGE), bb = su32(sB + s * B_STAGE);
+                        const uint32_t ab = su32(sA + s * A_ST), bb = su32(sB + s * B_ST);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
+                        for (int k = 0; k < 4; ++k) {
                             mma<TF32>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
                                       (kb > 0 || k > 0) ? 1u : 0u);
+                            if (SPLIT) {
+                                mma<TF32>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + B_STAGE + 32 * k), idesc, 1u);
+                                mma<TF32>(dtm, sw128_desc(ab + A_STAGE + 32 * k), sw128_desc(bb + 32 * k), idesc, 1u);
+                            }
+                        }
                         issued = true;
                         mma_commit(&empty[s]);
                     }
@@ -431,25 +451,40 @@ bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
 {
     auto fn = encode_fn();
     if (!fn) return false;
-    const int esz = op.is_tf32 ? 4 : 2;
-    cuuint64_t dims[2] = {(cuuint64_t)op.n_pad, (cuuint64_t)op.nrows};
-    cuuint64_t strides[1] = {(cuuint64_t)(op.n_pad * esz)};
+    const bool f32 = op.kind == PACK_TF32;
+    const int esz = f32 ? 4 : 2;
+    const int64_t cols = op.kind == PACK_BF16X3 ? 2 * op.n_pad : op.n_pad;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)op.nrows};
+    cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
     cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, op.is_tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     const_cast<void *>(op.rows), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <bool TF32, int KIND>
+template <int MODE, int KIND>
 cudaError_t launch_kind(int grid, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st)
 {
-    auto kfn = block_tc_kernel<TF32, KIND>;
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
+    auto kfn = block_tc_kernel<MODE, KIND>;
+    static bool attr_set = false;  // one attribute call per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     kfn<<<grid, NTHREADS, SMEM_BYTES, st>>>(mA, mB, a);
     return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(int grid, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, int kind,
+                        cudaStream_t st)
+{
+    if (kind == DCD_RBF) return launch_kind<MODE, DCD_RBF>(grid, mA, mB, a, st);
+    if (kind == DCD_POLY) return launch_kind<MODE, DCD_POLY>(grid, mA, mB, a, st);
+    return launch_kind<MODE, DCD_LINEAR>(grid, mA, mB, a, st);
 }
 
 }  // namespace
@@ -468,14 +503,16 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
                             int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
-    if (Aop.is_tf32 != Bop.is_tf32 || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
-    const int kb_elems = Aop.is_tf32 ? 32 : 64;
+    if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
+    if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3) return cudaErrorInvalidValue;
+    const int kb_elems = Aop.kind == PACK_TF32 ? 32 : 64;
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
     if (bn > BN_MAX) bn = BN_MAX;
     CUtensorMap mA, mB;
     if (!make_map(&mA, Aop, BM) || !make_map(&mB, Bop, bn)) return cudaErrorInvalidValue;
     TcArgs a;
+    a.lo_off = (int)Aop.n_pad;
     a.row_h = row_h;
     a.col_h = col_h;
     a.col_w = col_w;
@@ -495,18 +532,16 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.two_gl = (float)(2.0 * kp.gamma * 1.4426950408889634);
     a.coef0 = (float)kp.coef0;
     a.err = err;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = a.items < sms ? a.items : sms;
-    if (Aop.is_tf32) {
-        if (kp.kind == DCD_RBF) return launch_kind<true, DCD_RBF>(grid, mA, mB, a, st);
-        if (kp.kind == DCD_POLY) return launch_kind<true, DCD_POLY>(grid, mA, mB, a, st);
-        return launch_kind<true, DCD_LINEAR>(grid, mA, mB, a, st);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    if (kp.kind == DCD_RBF) return launch_kind<false, DCD_RBF>(grid, mA, mB, a, st);
-    if (kp.kind == DCD_POLY) return launch_kind<false, DCD_POLY>(grid, mA, mB, a, st);
-    return launch_kind<false, DCD_LINEAR>(grid, mA, mB, a, st);
+    int grid = a.items < sms ? a.items : sms;
+    if (Aop.kind == PACK_TF32) return launch_mode<MODE_TF32>(grid, mA, mB, a, kp.kind, st);
+    if (Aop.kind == PACK_BF16X3) return launch_mode<MODE_BF16X3>(grid, mA, mB, a, kp.kind, st);
+    return launch_mode<MODE_BF16>(grid, mA, mB, a, kp.kind, st);
 }
 
 }  // namespace dcd

@@ -86,12 +86,20 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
 
 // tcgen05 kernel block over the packed, padded operand copy (bf16 or fp32
 // rows of n_pad elements, zero padded).
+// Packed operand modes (also the pack kernel's dst_kind):
+//   0 bf16 rows of n_pad; 1 fp32 rows of n_pad rounded to tf32;
+//   3 split bf16 rows of 2*n_pad = [hi | lo].   (dst_kind 2 = fp64, FP64 path)
+enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3 };
 struct TcOperand {
-    const void *rows;     // packed matrix, row-major, ld = n_pad
+    const void *rows;     // packed matrix, row-major
     int64_t nrows;
-    int64_t n_pad;        // multiple of the k-block
-    int is_tf32;          // 0: bf16, 1: fp32 read as tf32
+    int64_t n_pad;        // features per half, multiple of the k-block
+    int kind;             // PACK_BF16, PACK_TF32 or PACK_BF16X3
 };
+__host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
+{
+    return kind == PACK_TF32 ? 4 * n_pad : (kind == PACK_BF16X3 ? 4 * n_pad : 2 * n_pad);
+}
 bool tc_available();
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
                             const float *row_h, const float *col_h, const float *col_w, const double *rs,
@@ -103,8 +111,10 @@ cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, 
                              void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
-cudaError_t launch_row_terms(const void *packed, int is_tf32, int64_t n_pad, int64_t m, const KernelParams &kp,
+cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st);
+cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
+                               void *dst, int *err, cudaStream_t st);
 cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,

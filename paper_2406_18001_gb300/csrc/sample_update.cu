@@ -92,7 +92,14 @@ __global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t
             continue;
         }
         float v = (c < n && inb) ? load_as_f32(src, dtype, sr * ld + c) : 0.f;
-        if (dst_kind == 1) {
+        if (dst_kind == PACK_BF16X3) {
+            // hi = bf16(v), lo = bf16(v - hi); v - hi is exact in fp32
+            __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            __nv_bfloat16 *d = (__nv_bfloat16 *)dst + r * 2 * n_pad;
+            d[c] = hi;
+            d[n_pad + c] = lo;
+        } else if (dst_kind == 1) {
             // round to the tf32 grid (10-bit mantissa, nearest, ties away) so the
             // tensor core sees exactly the stored value and the row norms match
             uint32_t t;
@@ -152,29 +159,70 @@ cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cuda
 
 // h[r] = gamma * log2(e) * ||x_r||^2 of the packed (already rounded) row, for
 // the RBF expansion ||a||^2 + ||b||^2 - 2 a.b (Section 5.2); 0 for the other
-// kernels.  One warp per row, FP64 partial sums, fixed order.
-__global__ void row_terms_kernel(const void *packed, int is_tf32, int64_t n_pad, int64_t m, double scale, float *h)
+// kernels.  For split rows the norm is the one the three MMAs reproduce,
+// sum(hi^2 + 2 hi lo), so that a row's distance to itself stays ~0.  One warp
+// per row, FP64 partial sums, fixed order.
+__global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, int64_t m, double scale, float *h)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= m) return;
     double s = 0.0;
     for (int64_t c = lane; c < n_pad; c += 32) {
-        float v = is_tf32 ? ((const float *)packed)[r * n_pad + c]
-                          : __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
-        s += (double)v * (double)v;
+        if (kind == PACK_TF32) {
+            double v = ((const float *)packed)[r * n_pad + c];
+            s += v * v;
+        } else if (kind == PACK_BF16X3) {
+            const __nv_bfloat16 *row = (const __nv_bfloat16 *)packed + r * 2 * n_pad;
+            double hi = __bfloat162float(row[c]), lo = __bfloat162float(row[n_pad + c]);
+            s += hi * hi + 2.0 * hi * lo;
+        } else {
+            double v = __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
+            s += v * v;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) h[r] = (float)(scale * s);
 }
 
-cudaError_t launch_row_terms(const void *packed, int is_tf32, int64_t n_pad, int64_t m, const KernelParams &kp,
+cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st)
 {
     if (m <= 0) return cudaSuccess;
     double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;
     int64_t blocks = (m * 32 + 255) / 256;
-    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, is_tf32, n_pad, m, scale, h);
+    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, kind, n_pad, m, scale, h);
+    return cudaGetLastError();
+}
+
+// dst row j = src row idx[j] (whole packed rows, 16-byte vectors; row_bytes
+// is a multiple of 128).  Indices outside [0, m) give a zero row and set
+// DEV_BAD_INDEX.
+__global__ void gather_rows_kernel(const uint4 *src, int64_t row_vec, const int32_t *idx, int64_t count, int64_t m,
+                                   uint4 *dst, int *err)
+{
+    const int64_t total = count * row_vec;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / row_vec, c = e - j * row_vec;
+        const int64_t r = idx[j];
+        if (r < 0 || r >= m) {
+            if (c == 0) set_error(err, DEV_BAD_INDEX);
+            dst[e] = make_uint4(0, 0, 0, 0);
+        } else {
+            dst[e] = src[r * row_vec + c];
+        }
+    }
+}
+
+cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
+                               void *dst, int *err, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const int64_t row_vec = row_bytes / 16;
+    int64_t blocks = (count * row_vec + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)src, row_vec, idx, count, m, (uint4 *)dst,
+                                                         err);
     return cudaGetLastError();
 }
 

@@ -82,7 +82,13 @@ size_t dtype_size(int dt) { return dt == DCD_F64 ? 8 : dt == DCD_F32 ? 4 : dt ==
 
 KernelParams to_kp(const dcd_kernel *k) { return KernelParams{k->kind, k->degree, k->gamma, k->coef0}; }
 
-bool is_tc(int prec) { return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32; }
+bool is_tc(int prec) { return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3; }
+
+// packed operand kind of a tensor-core precision
+int pack_kind(int prec)
+{
+    return prec == DCD_PREC_TF32 ? PACK_TF32 : (prec == DCD_PREC_BF16X3 ? PACK_BF16X3 : PACK_BF16);
+}
 
 // Operand preparation shared by the solver and the component entry points.
 struct Operand {
@@ -92,7 +98,7 @@ struct Operand {
     // tensor-core path
     void *packed = nullptr;
     int64_t n_pad = 0;
-    int tf32 = 0;
+    int kind = PACK_BF16;
     float *row_h = nullptr;
 };
 
@@ -190,7 +196,7 @@ struct Solver {
         col_pad = (sb + 255) / 256 * 256;
         const int kb_elems = o.prec == DCD_PREC_TF32 ? 32 : 64;
         const int64_t n_pad = (n + kb_elems - 1) / kb_elems * kb_elems;
-        const size_t esz = tc ? (o.prec == DCD_PREC_TF32 ? 4 : 2) : 8;
+        const size_t row_bytes = tc ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
         const bool need_pack = tc || A->dtype != DCD_F64 || host;
 
         // size the arena (two passes over the same layout)
@@ -201,9 +207,9 @@ struct Solver {
             double *yv = (double *)ar.take(host ? sizeof(double) * m : 0);
             double *av = (double *)ar.take(host ? sizeof(double) * m : 0);
             double *gv = (double *)ar.take(sizeof(double) * m);
-            void *pk = ar.take(need_pack ? (size_t)m * (tc ? n_pad : n) * esz : 0, 1024);
+            void *pk = ar.take(need_pack ? (size_t)m * row_bytes : 0, 1024);
             float *rh = (float *)ar.take(tc ? sizeof(float) * m : 0);
-            void *as = ar.take(tc ? (size_t)sb * n_pad * esz : 0, 1024);
+            void *as = ar.take(tc ? (size_t)sb * row_bytes : 0, 1024);
             float *ch = (float *)ar.take(sizeof(float) * col_pad);
             float *cw = (float *)ar.take(sizeof(float) * col_pad);
             int32_t *sidx = (int32_t *)ar.take(sizeof(int32_t) * col_pad);
@@ -259,15 +265,15 @@ struct Solver {
         DCD_TRY(cudaMemsetAsync(col_h, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
-        if (tc) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * n_pad * esz, st));
+        if (tc) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
 
         // operand
         if (tc) {
             op.n_pad = n_pad;
-            op.tf32 = o.prec == DCD_PREC_TF32;
-            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.tf32 ? 1 : 0, n_pad, m, err, st));
-            DCD_TRY(launch_row_terms(op.packed, op.tf32, n_pad, m, kp, op.row_h, st));
+            op.kind = pack_kind(o.prec);
+            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st));
+            DCD_TRY(launch_row_terms(op.packed, op.kind, n_pad, m, kp, op.row_h, st));
         } else if (need_pack) {
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st));
             op.a64 = (const double *)op.packed;
@@ -330,8 +336,7 @@ struct Solver {
     cudaError_t gather(int64_t ncols)
     {
         if (!tc) return cudaSuccess;
-        cudaError_t e = launch_pack_rows(op.packed, op.tf32 ? DCD_F32 : DCD_BF16, op.n_pad, m, op.n_pad, S, As,
-                                         op.tf32 ? 1 : 0, op.n_pad, ncols, err, st);
+        cudaError_t e = launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), S, ncols, m, As, err, st);
         if (e != cudaSuccess) return e;
         return launch_gather_f32(op.row_h, S, ncols, col_h, st);
     }
@@ -339,7 +344,7 @@ struct Solver {
     cudaError_t gram(int64_t ncols)
     {
         if (tc) {
-            TcOperand B{As, ncols, op.n_pad, op.tf32};
+            TcOperand B{As, ncols, op.n_pad, op.kind};
             return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
                                    err, st);
         }
@@ -377,8 +382,8 @@ struct Solver {
 
     cudaError_t block_tc_apply(int64_t ncols, const double *rs)
     {
-        TcOperand Aop{op.packed, m, op.n_pad, op.tf32};
-        TcOperand Bop{As, ncols, op.n_pad, op.tf32};
+        TcOperand Aop{op.packed, m, op.n_pad, op.kind};
+        TcOperand Bop{As, ncols, op.n_pad, op.kind};
         return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st);
     }
 
@@ -539,8 +544,8 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem)
     if (o->b > B_MAX || o->b > m) return DCD_EINVAL;
     if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
-    if (o->prec == DCD_PREC_FP8 || o->prec == DCD_PREC_BF16X3) return DCD_EUNSUPPORTED;
-    if (o->prec != DCD_PREC_FP64 && o->prec != DCD_PREC_TF32 && o->prec != DCD_PREC_BF16) return DCD_EINVAL;
+    if (o->prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
+    if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
     if (is_tc(o->prec) && !tc_available()) return DCD_EUNSUPPORTED;
     return DCD_OK;
 }
@@ -725,8 +730,8 @@ dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     dcd_status s = validate_dense(A);
     if (s != DCD_OK) return s;
     if ((s = validate_kernel(k)) != DCD_OK) return s;
-    if (prec == DCD_PREC_FP8 || prec == DCD_PREC_BF16X3) return DCD_EUNSUPPORTED;
-    if (prec != DCD_PREC_FP64 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16) return DCD_EINVAL;
+    if (prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
+    if (prec != DCD_PREC_FP64 && !is_tc(prec)) return DCD_EINVAL;
     if (is_tc(prec) && !tc_available()) return DCD_EUNSUPPORTED;
     return DCD_OK;
 }
@@ -771,15 +776,15 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
                                       ldo, err, st));
         return finish_component(err, st);
     }
-    const int tf32 = prec == DCD_PREC_TF32;
-    const int kb = tf32 ? 32 : 64;
+    const int pk = pack_kind(prec);
+    const int kb = pk == PACK_TF32 ? 32 : 64;
     const int64_t n_pad = (A->n + kb - 1) / kb * kb;
-    const size_t esz = tf32 ? 4 : 2;
+    const size_t rb = (size_t)packed_row_bytes(pk, n_pad);
     const int64_t cpad = (ncols + 255) / 256 * 256;
     size_t cur = 0;
     size_t oe = place(cur, 256);
-    size_t oa = place(cur, (size_t)nrows * n_pad * esz);
-    size_t ob = place(cur, (size_t)ncols * n_pad * esz);
+    size_t oa = place(cur, (size_t)nrows * rb);
+    size_t ob = place(cur, (size_t)ncols * rb);
     size_t orh = place(cur, sizeof(float) * nrows);
     size_t och = place(cur, sizeof(float) * cpad);
     size_t ocw = place(cur, sizeof(float) * cpad);
@@ -791,12 +796,12 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
     DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
-    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, tf32, n_pad, nrows, err, st));
-    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, tf32, n_pad, ncols, err, st));
-    DCD_TRY(launch_row_terms(pa, tf32, n_pad, nrows, kp, rh, st));
-    DCD_TRY(launch_row_terms(pb, tf32, n_pad, ncols, kp, ch, st));
+    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, pk, n_pad, nrows, err, st));
+    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, pk, n_pad, ncols, err, st));
+    DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st));
+    DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st));
     if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
-    TcOperand Aop{pa, nrows, n_pad, tf32}, Bop{pb, ncols, n_pad, tf32};
+    TcOperand Aop{pa, nrows, n_pad, pk}, Bop{pb, ncols, n_pad, pk};
     DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st));
     return finish_component(err, st);
 }
