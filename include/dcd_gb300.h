@@ -199,6 +199,37 @@ dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int3
                                   const int32_t *cols, int64_t ncols, const double *w,
                                   const double *rowscale, double *g, void *stream);
 
+/*
+ * dcd_kernel_block_static -- dcd_kernel_block (same arguments, layout, output
+ * and error codes) without any device memory allocation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory at the moment they need a kernel block: a framework that has
+ * reserved the device memory for its own caching pool (an extra cudaMalloc
+ * can fail there, or force the pool to give back cached blocks), or a
+ * deployment whose policy forbids dynamic device allocation after start-up
+ * (cudaMalloc / cudaFree may also synchronise the device).
+ *
+ * Its scratch is one library-owned device array of DCD_STATIC_SCRATCH_BYTES
+ * per GPU, held from the moment the library is loaded on that GPU until the
+ * process exits.  A call needs 256 bytes plus
+ *   tensor-core precisions: (nrows + ncols) * R + 4 * nrows + 4 * roundup(ncols, 256)
+ *     with R = 2 * n_pad (bf16), 4 * n_pad (tf32 or bf16x3), n_pad = n rounded up
+ *     to 64 (bf16, bf16x3) or 32 (tf32), plus alignment padding;
+ *   FP64 with a non-FP64 A: 8 * m * n;  FP64 with an FP64 A: nothing more.
+ * A request needing more than DCD_STATIC_SCRATCH_BYTES returns DCD_EINVAL
+ * before any device work is enqueued.
+ *
+ * The first call made on a device (with that device current) looks up the
+ * array's device address once; make that first call before any stream
+ * capture begins.  Every call reuses the same array and clears the parts that
+ * must start at zero; calls whose device work overlaps (different streams, or
+ * different host threads) race on the array and corrupt each other's output.
+ */
+#define DCD_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
+                                   int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
            "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
-           "dcd_kernel_block_apply"]
+           "dcd_kernel_block_apply", "dcd_kernel_block_static"]
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +92,7 @@ def lib():
             "dcd_sample_indices": (i32, [i32, u64, i64, i32, u64, i64, P, P]),
             "dcd_kernel_block": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
             "dcd_kernel_block_apply": (i32, [M, K, i32, P, i64, P, P, P, P]),
+            "dcd_kernel_block_static": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -274,6 +275,23 @@ def kernel_block(A, k, prec, cols, rows=None, nrows=None):
     rc = lib().dcd_kernel_block(C.byref(Am), C.byref(k), p, _ptr(rows), nr, _ptr(cols), ncols, _ptr(out), ncols,
                                 _stream(None))
     _check(rc, "dcd_kernel_block", allow_notconv=False)
+    return out
+
+
+def kernel_block_static(A, k, prec, cols, rows=None, nrows=None, out=None):
+    """dcd_kernel_block_static: the kernel block with the library's static
+    scratch array instead of any device allocation (for callers that cannot
+    allocate).  `out` may be given to avoid allocating it here as well."""
+    import torch
+    ncols = cols.numel()
+    nr = rows.numel() if rows is not None else (A.shape[0] if nrows is None else nrows)
+    p = _prec(prec)
+    if out is None:
+        out = torch.empty((nr, ncols), dtype=torch.float64 if p == PREC_FP64 else torch.float32, device=A.device)
+    Am = dense_matrix(A)
+    rc = lib().dcd_kernel_block_static(C.byref(Am), C.byref(k), p, _ptr(rows), nr, _ptr(cols), ncols, _ptr(out),
+                                       ncols, _stream(None))
+    _check(rc, "dcd_kernel_block_static", allow_notconv=False)
     return out
 
 
