@@ -50,13 +50,6 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any singl
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ unsigned long long gtime()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
@@ -87,15 +80,19 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 
 // Bounded wait for the phase with the given parity.  Returns false if the
 // CTA is aborting (another role timed out) or this wait timed out.
+// The bound counts SM clock cycles (clock64 is cheap; %globaltimer reads are
+// not): WAIT_NS at an assumed 2.1 GHz.
+constexpr long long WAIT_CYCLES = (long long)(WAIT_NS * 21 / 10);
+
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err)
 {
     if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = gtime();
+    const long long t0 = clock64();
     for (uint32_t spin = 1;; ++spin) {
         if (mbar_test(bar, parity)) return true;
         if ((spin & 15) == 0) {
             if (*abort_flag) return false;
-            if (gtime() - t0 > WAIT_NS) {
+            if (clock64() - t0 > WAIT_CYCLES) {
                 *abort_flag = 1;
                 set_error(err, DEV_TIMEOUT);
                 return false;
@@ -107,9 +104,9 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
 // Wait without the abort shortcut (drain path), still bounded.
 __device__ __noinline__ void mbar_drain(uint64_t *bar, uint32_t parity)
 {
-    const unsigned long long t0 = gtime();
+    const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (gtime() - t0 > WAIT_NS) return;
+        if (clock64() - t0 > WAIT_CYCLES) return;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
@@ -397,14 +394,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     tmem_ld32(tmem_base + lane_addr + buf * (uint32_t)bn + (uint32_t)(cg * 32), v);
                     const int64_t colbase = (int64_t)nc * bn + cg * 32;
                     if (a.store) {
-                        if (row_ok)
+                        if (row_ok) {
+                            float *dst = a.out + row * a.ldo + colbase;
+                            if (colbase + 32 <= a.ncols && (a.ldo & 3) == 0) {  // whole group: 16-byte stores
 #pragma unroll
-                            for (int q = 0; q < 32; ++q) {
-                                const int64_t col = colbase + q;
-                                if (col < a.ncols)
-                                    a.out[row * a.ldo + col] =
-                                        kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[col] : 0.f, a);
+                                for (int q = 0; q < 32; q += 4) {
+                                    float4 o;
+                                    o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, a);
+                                    o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, a);
+                                    o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, a);
+                                    o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, a);
+                                    *reinterpret_cast<float4 *>(dst + q) = o;
+                                }
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 32; ++q)
+                                    if (colbase + q < a.ncols)
+                                        dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, a);
                             }
+                        }
                     } else {
                         float p0 = 0.f, p1 = 0.f;
 #pragma unroll
@@ -509,6 +517,9 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
     if (bn > BN_MAX) bn = BN_MAX;
+    // store mode (the sampled Gram) has few rows: narrower N-chunks give
+    // more work items and spread them over more SMs
+    if (out != nullptr) bn = bn > 64 ? 64 : bn;
     CUtensorMap mA, mB;
     if (!make_map(&mA, Aop, BM) || !make_map(&mB, Bop, bn)) return cudaErrorInvalidValue;
     TcArgs a;

@@ -131,8 +131,15 @@ cudaError_t launch_coef(const double *y, const double *alpha, const int32_t *col
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
                              const double *y, const double *alpha, const double *g, double omega, double nu,
                              double *delta, double *w64, float *w32, int *err, cudaStream_t st);
+size_t recur_bdcd_scratch_bytes(int64_t nblk, int b);
+// cluster recurrence (recur_cluster.cu): cluster size, or 0 when it does not apply
+int recur_cluster_size(int nblk, int b, int rounds);
+cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
+                                 double lambda, double mdiag, const double *g, const float *W32, int rounds,
+                                 double *delta, double *w64, float *w32, int *err, cudaStream_t st);
+// refinements < 0 selects the plain FP64 forward substitution.
 cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
-                              double lambda, double mdiag, const double *g, double *Linv, double *delta,
-                              double *w64, float *w32, int *err, cudaStream_t st);
+                              double lambda, double mdiag, const double *g, int refinements, void *scratch,
+                              double *delta, double *w64, float *w32, int *err, cudaStream_t st);
 
 }  // namespace dcd

@@ -12,6 +12,7 @@
 //                       G_jt = Kss_jt / lambda + m [S_j = S_t]   (Algorithm 4)
 // All arithmetic here is FP64.
 #include "dcd_internal.cuh"
+#include "ptx.cuh"
 
 namespace dcd {
 
@@ -219,6 +220,371 @@ __global__ void __launch_bounds__(FWD_THREADS) bdcd_forward_kernel(const KT *Kss
     }
 }
 
+// ------------------------------------------- BDCD, refined FP32 chain ---
+// On GB300 an FP64 FMA has a 64-cycle dependent latency and 1/64 of the FP32
+// rate, so the sequential block forward substitution is run in FP32 and made
+// FP64-accurate by iterative refinement with FP64 residuals:
+//   round 0:  Delta = L32^-1 rhs,                    rhs = -g_S
+//   round k:  rho   = rhs - L Delta      (FP64, all rows in parallel)
+//             Delta += L32^-1 rho
+// L is the block lower triangle of G (G_jt = Kss_jt/lambda + m [S_j = S_t]),
+// L32 its FP32 rounding.  Each round multiplies the error by about
+// cond(L) * 2^-24, so one refinement reaches ~1e-13 and two reach FP64
+// rounding for the well-conditioned blocks of K-RR (G_jj >= m I).
+
+// W_j = G_jj^-1 in FP32 for every diagonal block, one warp per block,
+// Gauss-Jordan with lane p holding row p of [G_jj | I]; only the columns that
+// can still change at pivot k are touched (left half k.., right half ..k).
+template <typename KT, int BT>
+__global__ void __launch_bounds__(128) bdcd_inverse_kernel(const KT *Kss, int64_t ldk, int nblk, int b, float inv_lam,
+                                                           float mf, float *W32, int *err)
+{
+    const int j = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= nblk) return;
+    const int jb = j * b;
+    float aug[2 * BT];
+#pragma unroll
+    for (int q = 0; q < BT; ++q) {
+        float gv = 0.f;
+        if (lane < b && q < b) gv = (float)Kss[(int64_t)(jb + q) * ldk + jb + lane] * inv_lam + (q == lane ? mf : 0.f);
+        aug[q] = gv;
+        aug[BT + q] = (q == lane) ? 1.f : 0.f;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < BT; ++k) {
+        if (k < b) {
+            float piv = __shfl_sync(0xffffffffu, aug[k], k);
+            if (!(piv > 0.f)) {
+                bad = true;
+                piv = 1.f;
+            }
+            const float ip = 1.f / piv;
+            if (lane == k) {
+#pragma unroll
+                for (int q = k; q < BT + k + 1; ++q) aug[q] *= ip;
+            }
+            const float f = (lane == k) ? 0.f : aug[k];
+#pragma unroll
+            for (int q = k; q < BT + k + 1; ++q) {
+                const float rk = __shfl_sync(0xffffffffu, aug[q], k);
+                aug[q] = fmaf(-f, rk, aug[q]);
+            }
+        }
+    }
+    if (bad && lane == 0) set_error(err, DEV_NOT_SPD);
+    if (lane < b)
+#pragma unroll
+        for (int q = 0; q < BT; ++q)
+            if (q < b) W32[((int64_t)jb + lane) * b + q] = aug[BT + q];
+}
+
+// One CTA walks the blocks: the warp owning block t forms delta_t = W_t r_t
+// (W_t from shared memory), and all threads subtract G_pt delta_t from the
+// right-hand sides r_p of the later rows p, one row per thread.  The Gram
+// entries G_{p,tb+q} are read as Kss[tb+q][p] -- the kernel matrix is
+// symmetric (up to the last FP32 bit in the tensor-core modes, which the FP64
+// residual absorbs) -- so consecutive threads read consecutive addresses; with
+// fp32 storage the b rows of step t+1 are streamed into shared memory by bulk
+// copies while step t computes.  The m [S_p = S_q] terms follow a per-row
+// chain of earlier occurrences of the same index, built once with a
+// shared-memory hash table (repeated indices are rare).
+constexpr size_t CHAIN_SMEM_MAX = 224 * 1024;  // dynamic shared memory of the chain kernel
+constexpr int NBUF = 3;                        // streamed Gram panels in flight
+
+struct ChainLayout {
+    size_t pan_off, bar_off, total;
+    bool tma;
+};
+
+__host__ __device__ inline ChainLayout chain_layout(int sb, int b, int kss_bytes, int64_t ldk)
+{
+    ChainLayout L;
+    size_t cur = (size_t)sb * 20;  // r32, d32, dl32 (fp32) and sI, prev (int32)
+    cur = (cur + 15) & ~(size_t)15;
+    L.pan_off = cur;
+    size_t T = 2;
+    while (T < 2 * (size_t)sb) T <<= 1;
+    const size_t hash_bytes = 8 * T;  // keys + counts, T entries each
+    const size_t with_tma = cur + NBUF * (size_t)b * sb * 4 + 8 * NBUF;
+    L.tma = kss_bytes == 4 && b % 4 == 0 && ldk % 4 == 0 && sb > b && with_tma <= CHAIN_SMEM_MAX &&
+            (size_t)b * sb * 4 >= hash_bytes;
+    if (L.tma) {
+        L.bar_off = cur + NBUF * (size_t)b * sb * 4;
+        L.total = with_tma;
+    } else {
+        L.bar_off = 0;
+        L.total = cur + hash_bytes;  // hash table lives where the panels would be
+    }
+    return L;
+}
+
+template <typename KT, int BT, int NT>
+__global__ void __launch_bounds__(NT) bdcd_chain_kernel(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b,
+                                                        double lambda, double mdiag, const double *g,
+                                                        const double *rho, const float *W32, double *rhs64,
+                                                        double *delta, int round, int final_round, double *w64,
+                                                        float *w32, int *err)
+{
+    extern __shared__ __align__(16) unsigned char csm_raw[];
+    const int sb = nblk * b;
+    const ChainLayout L = chain_layout(sb, b, (int)sizeof(KT), ldk);
+    float *r32 = (float *)csm_raw;
+    float *d32 = r32 + sb;
+    float *dl32 = d32 + sb;   // delta / lambda
+    int32_t *sI = (int32_t *)(dl32 + sb);
+    int32_t *prev = sI + sb;  // previous position with the same index, or -1
+    float *panels = (float *)(csm_raw + L.pan_off);  // NBUF x (b rows x sb)
+    uint64_t *pbar = (uint64_t *)(csm_raw + L.bar_off);
+    __shared__ int abort_chain;
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float inv_lam = (float)(1.0 / lambda);
+    const float mf = (float)mdiag;
+
+    // hash table for the repeated-index chains (in the last panel's space)
+    int T = 2;
+    while (T < 2 * sb) T <<= 1;
+    int32_t *hkey = (int32_t *)(panels + (L.tma ? (size_t)(NBUF - 1) * b * sb : 0));
+    int32_t *hcnt = hkey + T;
+    for (int e = tid; e < T; e += NT) {
+        hkey[e] = -1;
+        hcnt[e] = 0;
+    }
+    for (int p = tid; p < sb; p += NT) {
+        const int32_t i = S[p];
+        sI[p] = i;
+        double rhs;
+        if (round == 0) {
+            rhs = -g[i];
+            rhs64[p] = rhs;
+        } else {
+            rhs = rho[p];
+        }
+        r32[p] = (float)rhs;
+    }
+    if (tid == 0) abort_chain = 0;
+    __syncthreads();
+    for (int p = tid; p < sb; p += NT) {
+        const int32_t key = sI[p];
+        int h = (int)(((uint32_t)key * 2654435761u) & (uint32_t)(T - 1));
+        for (int probe = 0; probe < T; ++probe) {
+            const int32_t old = atomicCAS(&hkey[h], -1, key);
+            if (old == -1 || old == key) break;
+            h = (h + 1) & (T - 1);
+        }
+        prev[p] = h;
+        atomicAdd(&hcnt[h], 1);
+    }
+    __syncthreads();
+    for (int p = tid; p < sb; p += NT) {
+        int pv = -1;
+        if (hcnt[prev[p]] > 1) {
+            const int32_t key = sI[p];
+            for (int q = p - 1; q >= 0; --q)
+                if (sI[q] == key) {
+                    pv = q;
+                    break;
+                }
+        }
+        prev[p] = pv;
+    }
+    if (L.tma && tid == 0) {
+        for (int k = 0; k < NBUF; ++k) ptx::mbar_init(&pbar[k], 1);
+        ptx::mbar_init_fence();
+    }
+    __syncthreads();
+
+    // Panel of step t (rows tb..tb+b-1 of Kss from column (t+1)b on) into
+    // buffer t % NBUF; warp 0 issues it, one row per lane.
+    int issued_upto = -1;  // warp 0: last step whose panel was issued
+    auto issue = [&](int t) {
+        const int ps = (t + 1) * b;
+        if (ps >= sb) return;
+        issued_upto = t;
+        const int k = t % NBUF;
+        float *pan = panels + (size_t)k * b * sb;
+        const uint32_t row_bytes = (uint32_t)(sb - ps) * 4u;
+        if (lane == 0) ptx::mbar_expect_tx(&pbar[k], row_bytes * (uint32_t)b);
+        __syncwarp();
+        for (int q = lane; q < b; q += 32)
+            ptx::bulk_g2s(pan + (size_t)q * sb + ps, (const float *)Kss + ((int64_t)t * b + q) * ldk + ps, row_bytes,
+                          &pbar[k]);
+    };
+    if (L.tma && warp == 0)
+        for (int t = 0; t < NBUF - 1 && t < nblk; ++t) issue(t);
+
+    // owner warp: inverse row of its next block (lane p: row p of W_t)
+    float wrow[BT];
+    auto load_w = [&](int t) {
+#pragma unroll
+        for (int q = 0; q < BT; ++q) wrow[q] = (lane < b && q < b) ? W32[((int64_t)t * b + lane) * b + q] : 0.f;
+    };
+    if (warp < nblk) load_w(warp);
+
+    for (int t = 0; t < nblk; ++t) {
+        const int tb = t * b;
+        if (L.tma && warp == 0 && t + NBUF - 1 < nblk) issue(t + NBUF - 1);
+        if (warp == t % NW) {
+            if (lane < b) {
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < BT; q += 2) {
+                    if (q < b) a0 = fmaf(wrow[q], r32[tb + q], a0);
+                    if (q + 1 < b) a1 = fmaf(wrow[q + 1], r32[tb + q + 1], a1);
+                }
+                const float d = a0 + a1;
+                d32[tb + lane] = d;
+                dl32[tb + lane] = d * inv_lam;
+            }
+            if (t + NW < nblk) load_w(t + NW);
+        }
+        const bool has_rows = (t + 1) * b < sb;
+        if (L.tma && has_rows &&
+            !ptx::mbar_wait_bounded(&pbar[t % NBUF], (uint32_t)((t / NBUF) & 1), 2000000000ull))
+            abort_chain = 1;
+        __syncthreads();
+        if (abort_chain) break;
+        if (has_rows) {
+            const float *pan = panels + (size_t)(t % NBUF) * b * sb;
+            for (int p = (t + 1) * b + tid; p < sb; p += NT) {
+                float s0 = 0.f, s1 = 0.f;
+                if (L.tma) {
+#pragma unroll
+                    for (int q = 0; q < BT; q += 2) {
+                        if (q < b) s0 = fmaf(pan[(size_t)q * sb + p], dl32[tb + q], s0);
+                        if (q + 1 < b) s1 = fmaf(pan[(size_t)(q + 1) * sb + p], dl32[tb + q + 1], s1);
+                    }
+                } else {
+                    for (int q = 0; q < b; ++q) s0 = fmaf((float)Kss[((int64_t)tb + q) * ldk + p], dl32[tb + q], s0);
+                }
+                for (int q = prev[p]; q >= tb; q = prev[q])
+                    if (q < tb + b) s1 = fmaf(mf, d32[q], s1);
+                r32[p] -= s0 + s1;
+            }
+        }
+        __syncthreads();
+    }
+    if (abort_chain) {
+        if (tid == 0) {
+            // Every panel issued but not consumed is still in flight: wait
+            // (bounded) for the last phase armed on each buffer.
+            set_error(err, DEV_TIMEOUT);
+            for (int k = 0; k < NBUF; ++k) {
+                int last = -1;  // the last issued step that used buffer k
+                for (int t = k; t <= issued_upto; t += NBUF) last = t;
+                if (last >= 0) ptx::mbar_wait_bounded(&pbar[k], (uint32_t)((last / NBUF) & 1), 2000000000ull);
+            }
+        }
+        __syncthreads();
+    }
+    for (int p = tid; p < sb; p += NT) {
+        double d = (double)d32[p];
+        if (round > 0) d += delta[p];
+        delta[p] = d;
+        if (final_round) {
+            if (w64) w64[p] = d / lambda;
+            if (w32) w32[p] = (float)(d / lambda);
+        }
+    }
+}
+
+// rho = rhs - L Delta in FP64, one warp per row, rows of all blocks at once.
+template <typename KT>
+__global__ void __launch_bounds__(256) bdcd_residual_kernel(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
+                                                            int b, double inv_lambda, double mdiag,
+                                                            const double *rhs64, const double *delta, double *rho)
+{
+    const int sb = nblk * b;
+    const int p = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (p >= sb) return;
+    const int end = (p / b + 1) * b;
+    const int32_t ip = S[p];
+    const KT *kr = Kss + (int64_t)p * ldk;
+    // sum_q Kss_pq delta_q and sum_{q: S_q = S_p} delta_q kept apart, so each
+    // term costs one conversion and one FP64 FMA; four accumulators hide the
+    // 64-cycle FP64 latency
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, dm = 0.0;
+    int q = lane;
+    for (; q + 96 < end; q += 128) {
+        const double d0 = delta[q], d1 = delta[q + 32], d2 = delta[q + 64], d3 = delta[q + 96];
+        a0 = fma((double)kr[q], d0, a0);
+        a1 = fma((double)kr[q + 32], d1, a1);
+        a2 = fma((double)kr[q + 64], d2, a2);
+        a3 = fma((double)kr[q + 96], d3, a3);
+        if (S[q] == ip) dm += d0;
+        if (S[q + 32] == ip) dm += d1;
+        if (S[q + 64] == ip) dm += d2;
+        if (S[q + 96] == ip) dm += d3;
+    }
+    for (; q < end; q += 32) {
+        const double d0 = delta[q];
+        a0 = fma((double)kr[q], d0, a0);
+        if (S[q] == ip) dm += d0;
+    }
+    double acc = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        dm += __shfl_xor_sync(0xffffffffu, dm, o);
+    }
+    if (lane == 0) rho[p] = rhs64[p] - (acc * inv_lambda + mdiag * dm);
+}
+
+template <typename KT, int BT, int NT>
+cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda, double mdiag,
+                         const double *g, int refinements, char *scratch, double *delta, double *w64, float *w32,
+                         int *err, cudaStream_t st)
+{
+    const int sb = nblk * b;
+    float *W32 = (float *)scratch;
+    double *rhs64 = (double *)(scratch + (((size_t)sb * b * 4 + 255) / 256) * 256);
+    double *rho = rhs64 + sb;
+    const ChainLayout L = chain_layout(sb, b, (int)sizeof(KT), ldk);
+    auto kfn = bdcd_chain_kernel<KT, BT, NT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHAIN_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (L.total > CHAIN_SMEM_MAX) return cudaErrorInvalidValue;
+    bdcd_inverse_kernel<KT, BT><<<(unsigned)((nblk + 3) / 4), 128, 0, st>>>(Kss, ldk, nblk, b, (float)(1.0 / lambda),
+                                                                            (float)mdiag, W32, err);
+    if (sizeof(KT) == 4) {  // fp32 Gram: the cluster recurrence when it applies
+        const int P = recur_cluster_size(nblk, b, refinements + 1);
+        if (P > 0)
+            return launch_recur_cluster((const float *)Kss, ldk, S, nblk, b, P, lambda, mdiag, g, W32,
+                                        refinements + 1, delta, w64, w32, err, st);
+    }
+    kfn<<<1, NT, L.total, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, nullptr, W32, rhs64, delta, 0,
+                                refinements == 0, w64, w32, err);
+    for (int r = 1; r <= refinements; ++r) {
+        bdcd_residual_kernel<KT><<<(unsigned)((sb + 7) / 8), 256, 0, st>>>(Kss, ldk, S, nblk, b, 1.0 / lambda, mdiag,
+                                                                          rhs64, delta, rho);
+        kfn<<<1, NT, L.total, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, rho, W32, rhs64, delta, r,
+                                    r == refinements, w64, w32, err);
+    }
+    return cudaGetLastError();
+}
+
+template <typename KT>
+cudaError_t refined_bdcd_b(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda,
+                           double mdiag, const double *g, int refinements, char *scratch, double *delta, double *w64,
+                           float *w32, int *err, cudaStream_t st)
+{
+    if (b <= 4)
+        return refined_bdcd<KT, 4, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
+                                         w32, err, st);
+    if (b <= 8)
+        return refined_bdcd<KT, 8, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
+                                         w32, err, st);
+    if (b <= 16)
+        return refined_bdcd<KT, 16, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
+                                          w32, err, st);
+    return refined_bdcd<KT, 32, 512>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64, w32,
+                                     err, st);
+}
+
 }  // namespace
 
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
@@ -243,11 +609,30 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
     return cudaGetLastError();
 }
 
+size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
+{
+    const size_t sb = (size_t)nblk * b;
+    size_t refined = ((sb * b * 4 + 255) / 256) * 256 + 2 * sb * 8;
+    size_t generic = sizeof(double) * (size_t)nblk * b * (b + 1);
+    return refined > generic ? refined : generic;
+}
+
+// Refined FP32 chain for b <= 32 and sb <= 8192 (the shared-memory limit of
+// one CTA: 12 bytes per sampled row); the plain FP64 kernels otherwise.
 cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
-                              double lambda, double mdiag, const double *g, double *Lbuf, double *delta, double *w64,
-                              float *w32, int *err, cudaStream_t st)
+                              double lambda, double mdiag, const double *g, int refinements, void *scratch,
+                              double *delta, double *w64, float *w32, int *err, cudaStream_t st)
 {
     if (nblk <= 0) return cudaSuccess;
+    if (b <= 32 && nblk * b <= 8192 && refinements >= 0 &&
+        chain_layout((int)(nblk * b), b, kss_f64 ? 8 : 4, ldk).total <= CHAIN_SMEM_MAX) {
+        if (kss_f64)
+            return refined_bdcd_b<double>((const double *)Kss, ldk, S, (int)nblk, b, lambda, mdiag, g, refinements,
+                                          (char *)scratch, delta, w64, w32, err, st);
+        return refined_bdcd_b<float>((const float *)Kss, ldk, S, (int)nblk, b, lambda, mdiag, g, refinements,
+                                     (char *)scratch, delta, w64, w32, err, st);
+    }
+    double *Lbuf = (double *)scratch;
     size_t smf = sizeof(double) * (size_t)b * b;
     size_t smw = sizeof(double) * ((size_t)nblk * b + b) + sizeof(int32_t) * (size_t)nblk * b;
     cudaError_t e;

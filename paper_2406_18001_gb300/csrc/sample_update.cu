@@ -26,11 +26,12 @@ __global__ void sample_dcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64
 __global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
                                    int b, int64_t nblocks, int32_t *out)
 {
+    extern __shared__ int32_t sblk[];  // b indices per warp
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (warp >= nblocks) return;
     const uint64_t t = (ctr_dev ? *ctr_dev : first_host) + (uint64_t)warp;
-    int32_t *blk = out + warp * b;
+    int32_t *blk = sblk + (threadIdx.x >> 5) * b;
     for (int q = 0; q < b; ++q) {
         const int64_t J = m - b + q;
         const int64_t r = (int64_t)below(sm64_draw(seed, t + 1, (uint64_t)q), (uint64_t)(J + 1));
@@ -40,6 +41,7 @@ __global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint6
         if (lane == 0) blk[q] = (int32_t)(any ? J : r);
         __syncwarp();
     }
+    for (int q = lane; q < b; q += 32) out[warp * b + q] = blk[q];
 }
 
 cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
@@ -55,7 +57,8 @@ cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, ui
     } else {
         int threads = 128;  // 4 warps = 4 blocks per CTA
         int64_t blocks = (count * 32 + threads - 1) / threads;
-        sample_bdcd_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, ctr_dev, first_host, m, b, count, out);
+        sample_bdcd_kernel<<<(unsigned)blocks, threads, sizeof(int32_t) * 4 * b, st>>>(seed, ctr_dev, first_host, m,
+                                                                                       b, count, out);
     }
     return cudaGetLastError();
 }
@@ -167,20 +170,22 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= m) return;
-    double s = 0.0;
+    // per-lane FP32 sums (each lane adds n_pad/32 squares), combined in FP64
+    float sf = 0.f;
     for (int64_t c = lane; c < n_pad; c += 32) {
         if (kind == PACK_TF32) {
-            double v = ((const float *)packed)[r * n_pad + c];
-            s += v * v;
+            const float v = ((const float *)packed)[r * n_pad + c];
+            sf = fmaf(v, v, sf);
         } else if (kind == PACK_BF16X3) {
             const __nv_bfloat16 *row = (const __nv_bfloat16 *)packed + r * 2 * n_pad;
-            double hi = __bfloat162float(row[c]), lo = __bfloat162float(row[n_pad + c]);
-            s += hi * hi + 2.0 * hi * lo;
+            const float hi = __bfloat162float(row[c]), lo = __bfloat162float(row[n_pad + c]);
+            sf = fmaf(hi, hi + 2.f * lo, sf);
         } else {
-            double v = __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
-            s += v * v;
+            const float v = __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
+            sf = fmaf(v, v, sf);
         }
     }
+    double s = sf;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) h[r] = (float)(scale * s);
 }
@@ -320,44 +325,69 @@ cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStr
 // --------------------------------------------------------- alpha update ---
 // alpha_{sk+s} = alpha_sk + sum_t V_t delta_t (Algorithms 2 and 4) and the
 // diagonal part of the gradient update, g[S_j] += diag * delta_j (omega for
-// K-SVM-L2, m for K-RR).  Repeated indices are merged: the first occurrence
-// of an index adds the sum of all its deltas, taken in j order, so the result
-// does not depend on thread scheduling.  Also advances the stream counter.
-__global__ void update_kernel(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,
-                              double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
+// K-SVM-L2, m for K-RR).  Repeated indices are merged deterministically: the
+// pairs (index, position) are bitonic-sorted in shared memory, and the first
+// entry of each run of equal indices adds the run's deltas in position order.
+// One CTA; cnt <= 8192.  Also advances the stream counter.
+constexpr int UPD_THREADS = 1024;
+
+__global__ void __launch_bounds__(UPD_THREADS) update_kernel(const int32_t *S, const double *delta, int cnt, int P,
+                                                             double diag, double *alpha, double *g, uint64_t *ctr,
+                                                             uint64_t ctr_advance, int64_t m, int *err)
 {
-    extern __shared__ int32_t sS[];
-    for (int64_t j = threadIdx.x; j < cnt; j += blockDim.x) sS[j] = S[j];
-    __syncthreads();
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr) *ctr += ctr_advance;
-    if (j >= cnt) return;
-    const int32_t i = sS[j];
-    if (i < 0 || i >= m) {
-        set_error(err, DEV_BAD_INDEX);
-        return;
+    extern __shared__ unsigned long long key[];  // P entries: (index << 32) | position
+    for (int j = threadIdx.x; j < P; j += UPD_THREADS) {
+        unsigned long long k = ~0ull;
+        if (j < cnt) {
+            const int32_t i = S[j];
+            if (i < 0 || i >= m) set_error(err, DEV_BAD_INDEX);
+            k = ((unsigned long long)(uint32_t)i << 32) | (unsigned)j;
+        }
+        key[j] = k;
     }
-    for (int64_t t = 0; t < j; ++t)
-        if (sS[t] == i) return;  // not the first occurrence
-    double sum = delta[j];
-    for (int64_t t = j + 1; t < cnt; ++t)
-        if (sS[t] == i) sum += delta[t];
-    alpha[i] += sum;
-    g[i] += diag * sum;
+    if (threadIdx.x == 0 && ctr) *ctr += ctr_advance;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += UPD_THREADS) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = threadIdx.x; r < cnt; r += UPD_THREADS) {
+        const unsigned long long k = key[r];
+        const uint32_t i = (uint32_t)(k >> 32);
+        if (r > 0 && (uint32_t)(key[r - 1] >> 32) == i) continue;  // not the head of its run
+        if ((int64_t)i >= m) continue;
+        double sum = delta[(uint32_t)k];
+        for (int q = r + 1; q < cnt && (uint32_t)(key[q] >> 32) == i; ++q) sum += delta[(uint32_t)key[q]];
+        alpha[i] += sum;
+        g[i] += diag * sum;
+    }
 }
 
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha, double *g,
                           uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st)
 {
     if (cnt <= 0) return cudaSuccess;
-    int threads = 256;
-    int64_t blocks = (cnt + threads - 1) / threads;
-    size_t sm = sizeof(int32_t) * (size_t)cnt;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (cnt > 8192) return cudaErrorInvalidValue;
+    int P = 2;
+    while (P < cnt) P <<= 1;
+    size_t sm = sizeof(unsigned long long) * (size_t)P;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
         if (e != cudaSuccess) return e;
+        attr = true;
     }
-    update_kernel<<<(unsigned)blocks, threads, sm, st>>>(S, delta, cnt, diag, alpha, g, ctr, ctr_advance, m, err);
+    update_kernel<<<1, UPD_THREADS, sm, st>>>(S, delta, (int)cnt, P, diag, alpha, g, ctr, ctr_advance, m, err);
     return cudaGetLastError();
 }
 
@@ -403,13 +433,23 @@ __global__ void check_partial_kernel(int problem, const double *g, const double 
     if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// one warp per quantity: each lane sums a fixed strided subset of the
+// partials, then a fixed shuffle tree (FP64 adds have a 64-cycle latency, so
+// a serial loop over the partials would dominate the check)
 __global__ void check_final_kernel(const double *partials, int nblocks, double *result)
 {
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
-        result[threadIdx.x] = s;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= 4) return;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nblocks; b += 64) {
+        s0 += partials[b * 4 + w];
+        s1 += partials[(b + 32) * 4 + w];
     }
+    if (b < nblocks) s0 += partials[b * 4 + w];
+    double s = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) result[w] = s;
 }
 
 cudaError_t launch_check(int problem, const double *g, const double *alpha, const double *y, int64_t m, double C,
@@ -417,7 +457,7 @@ cudaError_t launch_check(int problem, const double *g, const double *alpha, cons
 {
     (void)y;
     check_partial_kernel<<<CHECK_BLOCKS, CHECK_THREADS, 0, st>>>(problem, g, alpha, m, C, loss, partials);
-    check_final_kernel<<<1, 32, 0, st>>>(partials, CHECK_BLOCKS, result);
+    check_final_kernel<<<1, 128, 0, st>>>(partials, CHECK_BLOCKS, result);
     return cudaGetLastError();
 }
 

@@ -216,7 +216,7 @@ struct Solver {
             void *kss = ar.take((size_t)sb * sb * (tc ? 4 : 8));
             double *dl = (double *)ar.take(sizeof(double) * col_pad);
             double *wv = (double *)ar.take(sizeof(double) * col_pad);
-            double *lb = (double *)ar.take(problem == 1 ? sizeof(double) * o.s * o.b * (o.b + 1) : 0);
+            double *lb = (double *)ar.take(problem == 1 ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             uint64_t *cr = (uint64_t *)ar.take(sizeof(uint64_t));
             int *er = (int *)ar.take(sizeof(int) * 2);
             double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
@@ -445,8 +445,8 @@ struct Solver {
             DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
                                      tc ? col_w : nullptr, err, st));
         else
-            DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, Lbuf, delta, w64,
-                                      tc ? col_w : nullptr, err, st));
+            DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, tc ? 1 : 2, Lbuf,
+                                      delta, w64, tc ? col_w : nullptr, err, st));
         if (tc) DCD_TRY(clear_col_w_tail(ncols));
         tm.stop(stats.ms_recur);
         tm.start();

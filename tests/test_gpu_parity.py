@@ -272,11 +272,14 @@ OBJ_TOL = {"bf16x3": 1e-6, "tf32": 1e-4, "bf16": 3e-4}
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32", "bf16"])
-@pytest.mark.parametrize("s", [1, 16])
-def test_bdcd_mixed_matches_oracle(prec, s):
+@pytest.mark.parametrize("s,b", [(1, 16), (16, 16), (7, 8), (40, 4), (9, 12)])
+def test_bdcd_mixed_matches_oracle(prec, s, b):
+    """s = 1: the single-block path; (7, 8): the one-CTA refined chain with an
+    odd number of streamed panels; (16, 16), (40, 4), (9, 12): the cluster
+    recurrence with 16 and 9 CTAs and several blocks per CTA."""
     p = inputs.krr_dense(m=1000, n=64, seed=12, dtype=np.float32)
     A64 = p.A.astype(np.float64)
-    lam, b, H = 1e-2, 16, 640
+    lam, H = 1e-2, 640
     kb, ko = B().kernel("rbf", gamma=0.5), oracle.kernel("rbf", gamma=0.5)
     al, gr, st, _ = B().krr_solve(dev(p.A), dev(p.y), kb, lam, b, s, H, seed=3, prec=prec)
     want = oracle.bdcd_krr(A64, p.y, ko, lam, b, H, seed=3)
