@@ -184,7 +184,13 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    # a non-default stream: full outer steps then replay as one CUDA graph
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        return _run_gpu(args, torch, B, ws, rank, local, dev, stream)
+
+
+def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     p = make_problem(args.m, args.n, seed=rank)
     A = torch.from_numpy(p.A).to(dev)
     y = torch.from_numpy(p.y).to(dev)
@@ -209,7 +215,7 @@ def run_gpu(args):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            plan.run(1)
+            plan.enqueue(1)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     barrier()

@@ -161,6 +161,20 @@ dcd_status bdcd_krr_plan_create(const dcd_matrix *A, const double *y, const dcd_
 dcd_status dcd_plan_run(dcd_plan *plan, int64_t max_outer_steps, dcd_stats *st);
 dcd_status dcd_plan_destroy(dcd_plan *plan);
 
+/*
+ * Asynchronous continuation: enqueues up to outer_steps (>= 0) further outer
+ * steps of the plan on its stream and returns without synchronising the
+ * host.  No convergence check runs, alpha / grad are not published and no
+ * per-phase times are recorded; the next dcd_plan_run (which may be asked for
+ * 0 steps) reports any device-side error, publishes and fills the
+ * statistics.  *enqueued (may be NULL) receives the number of steps
+ * enqueued, fewer than asked once the budget H is exhausted.  Full outer
+ * steps are replayed from a CUDA graph unless DCD_FLAG_NO_GRAPH is set or
+ * the plan's stream is the legacy default stream.  Returns DCD_EINVAL for a
+ * NULL plan or outer_steps < 0, DCD_ECUDA if a launch fails.
+ */
+dcd_status dcd_plan_enqueue(dcd_plan *plan, int64_t outer_steps, int64_t *enqueued);
+
 /* Human-readable name of a status code (static string). */
 const char *dcd_status_string(int32_t status);
 

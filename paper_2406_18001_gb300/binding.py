@@ -54,7 +54,7 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
-           "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
+           "dcd_plan_enqueue", "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
            "dcd_kernel_block_apply", "dcd_kernel_block_static"]
 
 _lock = threading.Lock()
@@ -87,6 +87,7 @@ def lib():
             "dcd_svm_plan_create": (i32, [M, P, K, i32, d, O, P, P, P, C.POINTER(C.c_void_p)]),
             "bdcd_krr_plan_create": (i32, [M, P, K, d, O, P, P, P, C.POINTER(C.c_void_p)]),
             "dcd_plan_run": (i32, [P, i64, S]),
+            "dcd_plan_enqueue": (i32, [P, i64, C.POINTER(C.c_int64)]),
             "dcd_plan_destroy": (i32, [P]),
             "dcd_status_string": (C.c_char_p, [i32]),
             "dcd_sample_indices": (i32, [i32, u64, i64, i32, u64, i64, P, P]),
@@ -225,6 +226,13 @@ class Plan:
         rc = lib().dcd_plan_run(self._h, int(max_outer_steps), C.byref(st))
         _check(rc, "dcd_plan_run")
         return st.as_dict(), rc
+
+    def enqueue(self, outer_steps):
+        """Enqueue outer steps without synchronising; returns how many were enqueued."""
+        n = C.c_int64()
+        rc = lib().dcd_plan_enqueue(self._h, int(outer_steps), C.byref(n))
+        _check(rc, "dcd_plan_enqueue", allow_notconv=False)
+        return int(n.value)
 
     def close(self):
         if self._h:

@@ -31,6 +31,7 @@ __device__ __forceinline__ double kval(const KT *K, int64_t ld, int64_t r, int64
 // and folding every new theta_j into their pending corrections.
 constexpr int DCD_THREADS = 256;
 constexpr int DCD_SMEM_GRAM_MAX = 128;   // cnt <= 128: Gram staged in shared memory
+constexpr size_t DCD_SMEM_LIMIT = 224 * 1024;
 
 template <typename KT>
 __global__ void __launch_bounds__(DCD_THREADS) recur_dcd_kernel(const KT *Kss, int64_t ldk, const int32_t *S,
@@ -594,15 +595,25 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
     if (cnt <= 0) return cudaSuccess;
     size_t sm = sizeof(double) * 7 * cnt + sizeof(int32_t) * ((cnt + 1) & ~1);
     if (cnt <= DCD_SMEM_GRAM_MAX) sm += sizeof(double) * cnt * cnt;
+    if (sm > DCD_SMEM_LIMIT) return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};  // set once per instantiation (also keeps graph capture free of it)
     cudaError_t e;
     if (kss_f64) {
-        e = cudaFuncSetAttribute(recur_dcd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        if (!attr[1]) {
+            e = cudaFuncSetAttribute(recur_dcd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)DCD_SMEM_LIMIT);
+            if (e != cudaSuccess) return e;
+            attr[1] = true;
+        }
         recur_dcd_kernel<double><<<1, DCD_THREADS, sm, st>>>((const double *)Kss, ldk, S, (int)cnt, y, alpha, g,
                                                              omega, nu, delta, w64, w32, err);
     } else {
-        e = cudaFuncSetAttribute(recur_dcd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        if (!attr[0]) {
+            e = cudaFuncSetAttribute(recur_dcd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)DCD_SMEM_LIMIT);
+            if (e != cudaSuccess) return e;
+            attr[0] = true;
+        }
         recur_dcd_kernel<float><<<1, DCD_THREADS, sm, st>>>((const float *)Kss, ldk, S, (int)cnt, y, alpha, g, omega,
                                                             nu, delta, w64, w32, err);
     }
@@ -635,21 +646,23 @@ cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const i
     double *Lbuf = (double *)scratch;
     size_t smf = sizeof(double) * (size_t)b * b;
     size_t smw = sizeof(double) * ((size_t)nblk * b + b) + sizeof(int32_t) * (size_t)nblk * b;
+    if (smf > DCD_SMEM_LIMIT || smw > DCD_SMEM_LIMIT) return cudaErrorInvalidValue;
+    static bool attr_set = false;
     cudaError_t e;
+    if (!attr_set) {
+        for (auto fn : {(const void *)bdcd_factor_kernel<double>, (const void *)bdcd_forward_kernel<double>,
+                        (const void *)bdcd_factor_kernel<float>, (const void *)bdcd_forward_kernel<float>}) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DCD_SMEM_LIMIT);
+            if (e != cudaSuccess) return e;
+        }
+        attr_set = true;
+    }
     if (kss_f64) {
-        e = cudaFuncSetAttribute(bdcd_factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(bdcd_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
-        if (e != cudaSuccess) return e;
         bdcd_factor_kernel<double><<<(unsigned)nblk, FAC_THREADS, smf, st>>>((const double *)Kss, ldk, b, lambda,
                                                                              mdiag, Lbuf, err);
         bdcd_forward_kernel<double><<<1, FWD_THREADS, smw, st>>>((const double *)Kss, ldk, S, (int)nblk, b, lambda,
                                                                  mdiag, g, Lbuf, delta, w64, w32);
     } else {
-        e = cudaFuncSetAttribute(bdcd_factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(bdcd_forward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
-        if (e != cudaSuccess) return e;
         bdcd_factor_kernel<float><<<(unsigned)nblk, FAC_THREADS, smf, st>>>((const float *)Kss, ldk, b, lambda, mdiag,
                                                                             Lbuf, err);
         bdcd_forward_kernel<float><<<1, FWD_THREADS, smw, st>>>((const float *)Kss, ldk, S, (int)nblk, b, lambda,

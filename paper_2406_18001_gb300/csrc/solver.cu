@@ -102,36 +102,47 @@ struct Operand {
     float *row_h = nullptr;
 };
 
+// Per-phase device times of an outer step: an event pair per phase, recorded
+// back to back on the solver's stream, one synchronisation per step (flush).
 struct EventTimer {
+    static constexpr int MAXP = 8;
     bool on = false;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2 * MAXP] = {};
+    double *acc[MAXP] = {};
+    int n = 0;
     void init(bool enable, cudaStream_t s)
     {
         on = enable;
         st = s;
-        if (on) {
-            cudaEventCreate(&ev[0]);
-            cudaEventCreate(&ev[1]);
-        }
+        if (on)
+            for (auto &e : ev) cudaEventCreate(&e);
     }
     void start()
     {
-        if (on) cudaEventRecord(ev[0], st);
+        if (on && n < MAXP) cudaEventRecord(ev[2 * n], st);
     }
-    void stop(double &acc)
+    void stop(double &a)
     {
-        if (!on) return;
-        cudaEventRecord(ev[1], st);
-        cudaEventSynchronize(ev[1]);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        acc += ms;
+        if (!on || n >= MAXP) return;
+        cudaEventRecord(ev[2 * n + 1], st);
+        acc[n++] = &a;
+    }
+    void flush()
+    {
+        if (!on || n == 0) return;
+        cudaEventSynchronize(ev[2 * n - 1]);
+        for (int i = 0; i < n; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            *acc[i] += ms;
+        }
+        n = 0;
     }
     ~EventTimer()
     {
-        if (ev[0]) cudaEventDestroy(ev[0]);
-        if (ev[1]) cudaEventDestroy(ev[1]);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -170,6 +181,7 @@ struct Solver {
 
     ~Solver()
     {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (ws) cudaFreeAsync(ws, st);
     }
 
@@ -422,14 +434,76 @@ struct Solver {
             DCD_TRY(cudaMemcpyAsync(&ynorm2, result, sizeof(double), cudaMemcpyDeviceToHost, st));
             DCD_TRY(cudaStreamSynchronize(st));
         }
-        stats.gpu_launches_per_step = tc ? 9 : 5;
+        // kernels per outer step: sample, [gather rows, gather terms,] Gram,
+        // recurrence, block, update -- counted exactly from the graph once a
+        // full step has been captured; the recurrence is taken as the
+        // cluster (K-RR) or single-warp (K-SVM) form until then
+        stats.gpu_launches_per_step = (tc ? 3 : 1) + 1 + (problem == 0 ? 1 : 2) + 2;
         return DCD_OK;
     }
 
     bool finished() const { return conv || done >= o.max_iters; }
 
-    // One outer s-step (a1..a6) of cnt inner iterations.
+    // One outer s-step (a1..a6) of cnt inner iterations.  Full steps
+    // (cnt == s) are captured once into a CUDA graph and replayed: every
+    // kernel argument is the same from step to step (the stream position
+    // lives in device memory), so one capture serves the whole solve.
+    cudaGraphExec_t graph_exec = nullptr;
+    int direct_full_steps = 0;
+    bool graph_failed = false;
+
     dcd_status outer_step(int64_t cnt, EventTimer &tm)
+    {
+        const bool graphable = !tm.on && !(o.flags & DCD_FLAG_NO_GRAPH) && cnt == o.s && st != nullptr &&
+                               st != cudaStreamLegacy && st != cudaStreamPerThread && !graph_failed;
+        if (graphable && graph_exec) {
+            DCD_TRY(cudaGraphLaunch(graph_exec, st));
+        } else if (graphable && direct_full_steps >= 1) {
+            // capture after one direct full step has set every kernel attribute
+            DCD_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            EventTimer off;
+            off.init(false, st);
+            const dcd_status sc = enqueue_step(cnt, off);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            bool ok = sc == DCD_OK && ec == cudaSuccess && graph != nullptr &&
+                      cudaGraphInstantiate(&graph_exec, graph, 0) == cudaSuccess;
+            if (ok) stats.gpu_launches_per_step = count_kernel_nodes(graph);
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                cudaGetLastError();
+                graph_exec = nullptr;
+                graph_failed = true;
+                dcd_status s2 = enqueue_step(cnt, tm);
+                if (s2 != DCD_OK) return s2;
+            } else {
+                DCD_TRY(cudaGraphLaunch(graph_exec, st));
+            }
+        } else {
+            dcd_status s2 = enqueue_step(cnt, tm);
+            if (s2 != DCD_OK) return s2;
+            if (graphable) ++direct_full_steps;
+        }
+        done += cnt;
+        ++steps;
+        return DCD_OK;
+    }
+
+    static int count_kernel_nodes(cudaGraph_t graph)
+    {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return 0;
+        int k = 0;
+        for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+        }
+        return k;
+    }
+
+    dcd_status enqueue_step(int64_t cnt, EventTimer &tm)
     {
         const int64_t ncols = cnt * o.b;
         const double *rs = problem == 0 ? y : nullptr;
@@ -459,8 +533,7 @@ struct Solver {
         tm.start();
         DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
         tm.stop(stats.ms_update);
-        done += cnt;
-        ++steps;
+        tm.flush();
         return DCD_OK;
     }
 
@@ -485,6 +558,7 @@ struct Solver {
                 tm.start();
                 s0 = measure(metric, primal, dual, ynorm2);
                 tm.stop(stats.ms_check);
+                tm.flush();
                 if (s0 != DCD_OK) break;
                 if (metric <= o.tol) conv = true;
             }
@@ -532,6 +606,26 @@ struct Solver {
     }
 
     dcd_status run(dcd_stats *st_out) { return run_steps(-1, st_out); }
+
+    // Enqueues up to max_steps outer steps with no host synchronisation and
+    // no convergence check; device-side errors surface at the next run_steps.
+    dcd_status enqueue_steps(int64_t max_steps, int64_t *enqueued)
+    {
+        int64_t k = 0;
+        dcd_status s0 = begin();
+        if (s0 == DCD_OK) {
+            EventTimer off;
+            off.init(false, st);
+            for (; !finished() && k < max_steps; ++k) {
+                s0 = outer_step(std::min<int64_t>(o.s, o.max_iters - done), off);
+                if (s0 != DCD_OK) break;
+            }
+        }
+        stats.iters_done = done;
+        stats.outer_steps = steps;
+        if (enqueued) *enqueued = k;
+        return s0;
+    }
 
     double *alpha_host = nullptr;
 };
@@ -669,6 +763,13 @@ extern "C" dcd_status dcd_plan_run(dcd_plan *plan, int64_t max_outer_steps, dcd_
 {
     if (!plan) return DCD_EINVAL;
     return plan->sv.run_steps(max_outer_steps, st);
+}
+
+extern "C" dcd_status dcd_plan_enqueue(dcd_plan *plan, int64_t outer_steps, int64_t *enqueued)
+{
+    if (enqueued) *enqueued = 0;
+    if (!plan || outer_steps < 0) return DCD_EINVAL;
+    return plan->sv.enqueue_steps(outer_steps, enqueued);
 }
 
 extern "C" dcd_status dcd_plan_destroy(dcd_plan *plan)

@@ -232,6 +232,35 @@ def test_resume_split_run_is_bit_identical():
     assert torch.equal(a1, a2) and torch.equal(g1, g2)
 
 
+@pytest.mark.parametrize("problem,prec", [(1, "fp64"), (1, "bf16x3"), (0, "bf16")])
+def test_graph_replay_and_enqueue_match_direct_launches(problem, prec):
+    # Full outer steps replay a captured CUDA graph on a non-default stream;
+    # the replayed iterates must be bit-identical to direct launches, across
+    # enqueue/run pieces and a final short step (H not a multiple of s).
+    if problem == 1:
+        p, param, b, s = inputs.krr_dense(m=700, n=40, seed=21, dtype=np.float64), 0.01, 8, 8
+    else:
+        p, param, b, s = inputs.blobs(m=700, n=40, seed=21), 1.0, 1, 16
+    H = 10 * s + 3
+    kb = B().kernel("rbf", gamma=0.2)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        A, y = dev(p.A), dev(p.y)
+        ref = B().Plan(problem, A, y, kb, param, b, s, H, seed=4, prec=prec, flags=B().FLAG_NO_GRAPH)
+        ref.run(-1)
+        pl = B().Plan(problem, A, y, kb, param, b, s, H, seed=4, prec=prec)
+        assert pl.enqueue(3) == 3
+        st, _ = pl.run(2)
+        assert st["outer_steps"] == 5 and st["gpu_launches_per_step"] > 0
+        assert pl.enqueue(100) == 6  # 5 full steps and the short one
+        st, _ = pl.run(0)
+        assert st["iters_done"] == H
+        side.synchronize()
+        assert torch.equal(ref.alpha, pl.alpha) and torch.equal(ref.grad, pl.grad)
+        ref.close()
+        pl.close()
+
+
 def test_nonzero_alpha0_gradient_pass():
     p = inputs.blobs(m=260, n=9, seed=10)
     kb, ko = B().kernel("rbf", gamma=0.3), oracle.kernel("rbf", gamma=0.3)
