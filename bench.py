@@ -4,17 +4,18 @@
 Workload (default): dense K-RR, m = 50000 samples, n = 512 features, A ~
 N(0,1)/sqrt(n) stored FP32, y = sin(A w) + 0.1 N(0,1), RBF with bandwidth
 sigma = 1 (gamma = 1/(2 sigma^2) = 0.5), lambda = 1e-4, block size b = 16,
-s = 16 inner steps per outer step, bf16 tensor-core kernel block with FP64
-recurrence and gradient accumulation.  Synthetic data stand in for the
-paper's LIBSVM sets.
+s = 64 inner steps per outer step, split-bf16 (bf16x3) tensor-core kernel
+block with FP64-accurate recurrence and FP64 gradient accumulation (the
+mixed form that meets the alpha / objective tolerances against the FP64
+oracle).  Synthetic data stand in for the paper's LIBSVM sets.
 
 One "step" is one outer s-step (sample, gather, Gram, FP64 recurrence, fused
 kernel-block gradient update, alpha update) = s*b coordinate updates.  The
-metric is coordinate updates per second.  L2 (129 MB) could hold the 51 MB
-bf16 operand, so a buffer larger than L2 is written before every timed step
-and each step is timed alone with CUDA events on the solver's stream.
+metric is coordinate updates per second.  L2 (129 MB) could hold the 102 MB
+split-bf16 operand, so a buffer larger than L2 is written before every timed
+step and each step is timed alone with CUDA events on the solver's stream.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--prec bf16|tf32|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--prec bf16x3|bf16|tf32|fp64]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
 """
 from __future__ import annotations
@@ -35,6 +36,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coordinate updates/s and time-to-duality-gap 1e-6 (mixed vs FP64 s=1, 1 GB300)"
 UNIT = "coordinate updates/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused-block launch,
+# from an ncu capture of this build's kernel (prec, m, n, b, s) -> bytes
+NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 108.48e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 
@@ -259,7 +263,10 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     else:
         roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = args.traffic
+    traffic = args.traffic
+    if traffic is None:
+        traffic = NCU_TRAFFIC.get((args.prec, args.m, args.n, args.b, args.s))
+    roof["traffic"] = traffic
     roof["peak_source"] = src
     roof["kernel"] = "block_tc_kernel (fused kernel block + gradient update)" if args.prec != "fp64" \
         else "block_simt_f64_kernel"
@@ -314,11 +321,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=512)
-    ap.add_argument("--s", type=int, default=16)
+    ap.add_argument("--s", type=int, default=64)
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32", "bf16x3", "fp64"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16", "tf32", "bf16x3", "fp64"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")
