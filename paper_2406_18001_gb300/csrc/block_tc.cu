@@ -506,6 +506,22 @@ bool tc_available()
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
+bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t rows, int64_t ld, int box_cols,
+                     int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn || cols < 1 || rows < 1 || (ld * 4) % 16 != 0 || ((uintptr_t)base & 15) != 0) return false;
+    if (box_cols < 1 || box_cols > 256 || box_rows < 1 || box_rows > 256 || (box_cols * 4) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
                             const float *col_h, const float *col_w, const double *rs, double *g, float *out,
                             int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st)

@@ -3,6 +3,7 @@
 // the C ABI (include/dcd_gb300.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -132,14 +133,32 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
                              const double *y, const double *alpha, const double *g, double omega, double nu,
                              double *delta, double *w64, float *w32, int *err, cudaStream_t st);
 size_t recur_bdcd_scratch_bytes(int64_t nblk, int b);
-// cluster recurrence (recur_cluster.cu): cluster size, or 0 when it does not apply
+// The alpha / cached-gradient update (a6) done by the recurrence itself when
+// it can: alpha_S += Delta, g_S += mdiag * Delta (repeats summed in position
+// order) and the stream counter advanced.  `done` reports whether it ran.
+struct FusedUpdate {
+    double *alpha = nullptr;
+    uint64_t *ctr = nullptr;
+    uint64_t ctr_advance = 0;
+    bool done = false;
+};
+// cluster recurrence (recur_cluster.cu): cluster size, or 0 when it does not apply;
+// scratch of recur_cluster_scratch_bytes (super-block inverses, repeat masks and links)
 int recur_cluster_size(int nblk, int b, int rounds);
+size_t recur_cluster_scratch_bytes(int64_t nblk, int b);
 cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
-                                 double lambda, double mdiag, const double *g, const float *W32, int rounds,
-                                 double *delta, double *w64, float *w32, int *err, cudaStream_t st);
-// refinements < 0 selects the plain FP64 forward substitution.
+                                 double lambda, double mdiag, double *g, int rounds, void *scratch, double *delta,
+                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st);
+// 2-D tensor map over a row-major fp32 matrix (rows x cols, leading dimension
+// ld elements, ld * 4 a multiple of 16), box of box_rows x box_cols, no
+// swizzle, out-of-range elements read as zero (block_tc.cu)
+bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t rows, int64_t ld, int box_cols,
+                     int box_rows);
+// refinements < 0 selects the plain FP64 forward substitution.  With upd
+// non-NULL the recurrence may also apply a6 (then g must be writable and
+// upd->done is set); otherwise the caller runs launch_update.
 cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
                               double lambda, double mdiag, const double *g, int refinements, void *scratch,
-                              double *delta, double *w64, float *w32, int *err, cudaStream_t st);
+                              double *delta, double *w64, float *w32, FusedUpdate *upd, int *err, cudaStream_t st);
 
 }  // namespace dcd

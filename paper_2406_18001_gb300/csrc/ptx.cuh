@@ -33,6 +33,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
 }
 
+// Plain arrive (release at CTA scope) on a barrier initialised with count 1
+// per arriving thread.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
@@ -69,6 +76,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      su32(dst)),
                  "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
                  : "memory");
+}
+
+// 2-D tiled TMA load of the box at (x, y) (x innermost, x * element size a
+// multiple of 16 bytes) described by the tensor map `map` (a __grid_constant__
+// kernel parameter) into shared memory, completing its bytes on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
 }
 
 }  // namespace ptx

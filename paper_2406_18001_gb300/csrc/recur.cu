@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256) bdcd_residual_kernel(const KT *Kss, int64
 template <typename KT, int BT, int NT>
 cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda, double mdiag,
                          const double *g, int refinements, char *scratch, double *delta, double *w64, float *w32,
-                         int *err, cudaStream_t st)
+                         FusedUpdate *upd, int *err, cudaStream_t st)
 {
     const int sb = nblk * b;
     float *W32 = (float *)scratch;
@@ -548,15 +548,20 @@ cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (sizeof(KT) == 4) {  // fp32 Gram: the cluster recurrence when it applies
+        const int P = recur_cluster_size(nblk, b, refinements + 1);
+        if (P > 0) {
+            // the cluster kernel also applies the a6 update (alpha and g are the solver's, writable)
+            const cudaError_t e =
+                launch_recur_cluster((const float *)Kss, ldk, S, nblk, b, P, lambda, mdiag, const_cast<double *>(g),
+                                     refinements + 1, scratch, delta, w64, w32, upd, err, st);
+            if (e == cudaSuccess && upd) upd->done = true;
+            return e;
+        }
+    }
     if (L.total > CHAIN_SMEM_MAX) return cudaErrorInvalidValue;
     bdcd_inverse_kernel<KT, BT><<<(unsigned)((nblk + 3) / 4), 128, 0, st>>>(Kss, ldk, nblk, b, (float)(1.0 / lambda),
                                                                             (float)mdiag, W32, err);
-    if (sizeof(KT) == 4) {  // fp32 Gram: the cluster recurrence when it applies
-        const int P = recur_cluster_size(nblk, b, refinements + 1);
-        if (P > 0)
-            return launch_recur_cluster((const float *)Kss, ldk, S, nblk, b, P, lambda, mdiag, g, W32,
-                                        refinements + 1, delta, w64, w32, err, st);
-    }
     kfn<<<1, NT, L.total, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, nullptr, W32, rhs64, delta, 0,
                                 refinements == 0, w64, w32, err);
     for (int r = 1; r <= refinements; ++r) {
@@ -571,19 +576,19 @@ cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
 template <typename KT>
 cudaError_t refined_bdcd_b(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda,
                            double mdiag, const double *g, int refinements, char *scratch, double *delta, double *w64,
-                           float *w32, int *err, cudaStream_t st)
+                           float *w32, FusedUpdate *upd, int *err, cudaStream_t st)
 {
     if (b <= 4)
         return refined_bdcd<KT, 4, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
-                                         w32, err, st);
+                                         w32, upd, err, st);
     if (b <= 8)
         return refined_bdcd<KT, 8, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
-                                         w32, err, st);
+                                         w32, upd, err, st);
     if (b <= 16)
         return refined_bdcd<KT, 16, 1024>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64,
-                                          w32, err, st);
+                                          w32, upd, err, st);
     return refined_bdcd<KT, 32, 512>(Kss, ldk, S, nblk, b, lambda, mdiag, g, refinements, scratch, delta, w64, w32,
-                                     err, st);
+                                     upd, err, st);
 }
 
 }  // namespace
@@ -625,6 +630,8 @@ size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
     const size_t sb = (size_t)nblk * b;
     size_t refined = ((sb * b * 4 + 255) / 256) * 256 + 2 * sb * 8;
     size_t generic = sizeof(double) * (size_t)nblk * b * (b + 1);
+    const size_t cluster = recur_cluster_scratch_bytes(nblk, b);
+    if (cluster > refined) refined = cluster;
     return refined > generic ? refined : generic;
 }
 
@@ -632,16 +639,17 @@ size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
 // one CTA: 12 bytes per sampled row); the plain FP64 kernels otherwise.
 cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
                               double lambda, double mdiag, const double *g, int refinements, void *scratch,
-                              double *delta, double *w64, float *w32, int *err, cudaStream_t st)
+                              double *delta, double *w64, float *w32, FusedUpdate *upd, int *err, cudaStream_t st)
 {
+    if (upd) upd->done = false;
     if (nblk <= 0) return cudaSuccess;
     if (b <= 32 && nblk * b <= 8192 && refinements >= 0 &&
         chain_layout((int)(nblk * b), b, kss_f64 ? 8 : 4, ldk).total <= CHAIN_SMEM_MAX) {
         if (kss_f64)
             return refined_bdcd_b<double>((const double *)Kss, ldk, S, (int)nblk, b, lambda, mdiag, g, refinements,
-                                          (char *)scratch, delta, w64, w32, err, st);
+                                          (char *)scratch, delta, w64, w32, upd, err, st);
         return refined_bdcd_b<float>((const float *)Kss, ldk, S, (int)nblk, b, lambda, mdiag, g, refinements,
-                                     (char *)scratch, delta, w64, w32, err, st);
+                                     (char *)scratch, delta, w64, w32, upd, err, st);
     }
     double *Lbuf = (double *)scratch;
     size_t smf = sizeof(double) * (size_t)b * b;

@@ -373,11 +373,65 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(const int32_t *S, c
     }
 }
 
+// The same update for cnt <= UPD_SCAN_MAX without a sort: one thread per
+// position, S staged in shared memory; a position with no earlier occurrence
+// of its index is a run head and adds the deltas of its index's occurrences
+// in position order (the order of the sorted form, so the results agree bit
+// for bit).  O(cnt) work per thread spread over cnt threads.
+constexpr int UPD_SCAN_MAX = 2048;
+constexpr int UPD_SCAN_THREADS = 64;
+
+__global__ void __launch_bounds__(UPD_SCAN_THREADS)
+    update_scan_kernel(const int32_t *S, const double *delta, int cnt, double diag, double *alpha, double *g,
+                       uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
+{
+    __shared__ __align__(16) int32_t sS[UPD_SCAN_MAX];
+    const int c4 = (cnt + 3) & ~3;
+    for (int q = threadIdx.x; q < c4; q += UPD_SCAN_THREADS) sS[q] = q < cnt ? S[q] : -1;
+    __syncthreads();
+    const int p = blockIdx.x * UPD_SCAN_THREADS + threadIdx.x;
+    if (p == 0 && ctr) *ctr += ctr_advance;
+    if (p >= cnt) return;
+    const int32_t key = sS[p];
+    if (key < 0 || key >= m) {
+        set_error(err, DEV_BAD_INDEX);
+        return;
+    }
+    const int4 *s4 = (const int4 *)sS;
+    bool head = true;
+    for (int q4 = 0; q4 < (p >> 2) && head; ++q4) {
+        const int4 w = s4[q4];
+        head = !(w.x == key || w.y == key || w.z == key || w.w == key);
+    }
+    for (int q = p & ~3; q < p && head; ++q) head = sS[q] != key;
+    if (!head) return;
+    // later occurrences: a match mask per int4 group, and the (rare, FP64,
+    // 64-cycle-latency) adds only for the set bits, in position order
+    double sum = delta[p];
+    for (int q4 = p >> 2; q4 < (c4 >> 2); ++q4) {
+        const int4 w = s4[q4];
+        unsigned mk = (w.x == key ? 1u : 0u) | (w.y == key ? 2u : 0u) | (w.z == key ? 4u : 0u) | (w.w == key ? 8u : 0u);
+        mk &= q4 == (p >> 2) ? ~((2u << (p & 3)) - 1u) : 0xfu;  // positions after p only
+        while (mk) {
+            sum += delta[4 * q4 + __ffs(mk) - 1];
+            mk &= mk - 1;
+        }
+    }
+    alpha[key] += sum;
+    g[key] += diag * sum;
+}
+
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha, double *g,
                           uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st)
 {
     if (cnt <= 0) return cudaSuccess;
     if (cnt > 8192) return cudaErrorInvalidValue;
+    if (cnt <= UPD_SCAN_MAX) {
+        const unsigned grid = (unsigned)((cnt + UPD_SCAN_THREADS - 1) / UPD_SCAN_THREADS);
+        update_scan_kernel<<<grid, UPD_SCAN_THREADS, 0, st>>>(S, delta, (int)cnt, diag, alpha, g, ctr, ctr_advance,
+                                                             m, err);
+        return cudaGetLastError();
+    }
     int P = 2;
     while (P < cnt) P <<= 1;
     size_t sm = sizeof(unsigned long long) * (size_t)P;

@@ -515,12 +515,16 @@ struct Solver {
         DCD_TRY(gram(ncols));
         tm.stop(stats.ms_gram);
         tm.start();
+        FusedUpdate fu;  // a6 done by the recurrence when it can
+        fu.alpha = alpha;
+        fu.ctr = ctr;
+        fu.ctr_advance = (uint64_t)cnt;
         if (problem == 0)
             DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
                                      tc ? col_w : nullptr, err, st));
         else
             DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, tc ? 1 : 2, Lbuf,
-                                      delta, w64, tc ? col_w : nullptr, err, st));
+                                      delta, w64, tc ? col_w : nullptr, &fu, err, st));
         if (tc) DCD_TRY(clear_col_w_tail(ncols));
         tm.stop(stats.ms_recur);
         tm.start();
@@ -531,7 +535,7 @@ struct Solver {
                                           st));
         tm.stop(stats.ms_block);
         tm.start();
-        DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+        if (!fu.done) DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
         tm.stop(stats.ms_update);
         tm.flush();
         return DCD_OK;
