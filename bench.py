@@ -177,6 +177,57 @@ def cpu_baseline(args, budget_s=12.0):
                       f"({dt:.1f} s, plain FP64 C, one thread)"}
 
 
+# ------------------------------------------------------ time to tolerance --
+def time_to_tol(args, torch, B, A, y, k, seed):
+    """Time to relative residual ||(K/lambda + mI) a - y|| / ||y|| <= tol for
+    the mixed form (this bench's precision and s) and the plain FP64 s = 1
+    form, on the same index stream.  The mixed solve checks the cached
+    gradient every ~256 block updates and confirms on a recomputed gradient
+    (DCD_FLAG_REFRESH).  The FP64 s = 1 solve needs the same number of block
+    updates (same iterates up to rounding), so its time is its measured time
+    per block update times that count; a full FP64 s = 1 run takes minutes."""
+    b, m = args.b, args.m
+    ce = max(1, 256 // args.s)
+    H = args.ttt_budget
+    plan = B.Plan(1, A, y, k, args.lam, b, args.s, H, seed=seed, prec=args.prec, tol=args.tol, check_every=ce,
+                  flags=B.FLAG_REFRESH)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, _ = plan.run(-1)
+    wall = time.perf_counter() - t0
+    alpha = plan.alpha.clone()
+    plan.close()
+    mixed = {"prec": args.prec, "s": args.s, "converged": bool(st["converged"]), "block_updates": st["iters_done"],
+             "coordinate_updates": st["iters_done"] * b, "ms": st["ms_total"], "wall_s": wall,
+             "resid_recomputed": st["final_metric"], "refreshes": st["refreshes"], "ms_refresh": st["ms_refresh"],
+             "check_every_outer_steps": ce}
+    # FP64 residual of the mixed result on sampled rows (FP64 kernel block, rows x all columns)
+    g = torch.Generator().manual_seed(1234)
+    rows = torch.randperm(m, generator=g)[:args.ttt_rows].to(torch.int32).to(A.device)
+    cols = torch.arange(m, dtype=torch.int32, device=A.device)
+    Kb = B.kernel_block(A, k, "fp64", cols, rows=rows)  # rows x m, FP64
+    r = Kb @ alpha / args.lam + m * alpha[rows.long()] - y[rows.long()]
+    mixed["resid_fp64_sampled_rows"] = float(torch.linalg.norm(r) / torch.linalg.norm(y[rows.long()]))
+    mixed["sampled_rows"] = args.ttt_rows
+    del Kb
+    # FP64 s = 1: time per block update over a bounded run
+    n64 = args.ttt_fp64_steps
+    p64 = B.Plan(1, A, y, k, args.lam, b, 1, n64 + 8, seed=seed, prec="fp64")
+    p64.run(8)
+    base, _ = p64.run(0)
+    torch.cuda.synchronize()
+    p64.run(n64)
+    st64, _ = p64.run(0)
+    p64.close()
+    ms_blk = (st64["ms_total"] - base["ms_total"]) / n64
+    fp64 = {"prec": "fp64", "s": 1, "ms_per_block_update": ms_blk, "blocks_timed": n64,
+            "ms_estimated": ms_blk * st["iters_done"]}
+    out = {"tol": args.tol, "metric": "relative residual ||(K/lambda + m I) alpha - y|| / ||y||",
+           "mixed": mixed, "fp64_s1": fp64,
+           "speedup": fp64["ms_estimated"] / mixed["ms"] if mixed["converged"] and mixed["ms"] > 0 else None}
+    return out
+
+
 # ---------------------------------------------------------------- GPU -----
 def run_gpu(args):
     import torch
@@ -290,6 +341,10 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
         e2e = {"value": Hh * args.b / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps, "steps": args.steps, "wall_s": dt}
 
+    ttt = None
+    if not args.no_ttt:
+        ttt = time_to_tol(args, torch, B, A, y, k, rank)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args)
@@ -306,7 +361,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
                "step_ms": {"min": ms_steps[0], "median": ms_steps[len(ms_steps) // 2], "max": ms_steps[-1]},
                "phase_ms": phase,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary()}
+               "clocks": clk.summary(), "time_to_tol": ttt}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -329,6 +384,11 @@ def main():
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--ttt-budget", type=int, default=400000, help="block-update cap of the tolerance solve")
+    ap.add_argument("--ttt-rows", type=int, default=1000, help="rows of the FP64 residual check")
+    ap.add_argument("--ttt-fp64-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

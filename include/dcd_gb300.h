@@ -74,8 +74,12 @@ typedef enum {
     DCD_PREC_TF32 = 1,   /* tcgen05 kind::tf32 block, FP32 accumulation */
     DCD_PREC_BF16 = 2,   /* tcgen05 kind::f16 (bf16) block, FP32 accumulation */
     DCD_PREC_FP8 = 3,    /* reserved */
-    DCD_PREC_BF16X3 = 4  /* split bf16: a = hi + lo, three tcgen05 kind::f16 MMAs per
+    DCD_PREC_BF16X3 = 4, /* split bf16: a = hi + lo, three tcgen05 kind::f16 MMAs per
                             k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
+    DCD_PREC_TF32X3 = 5  /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
+                            three kind::tf32 MMAs per k-step, FP32 accumulation; also the
+                            precision of the gradient recomputed under DCD_FLAG_REFRESH in
+                            every tensor-core mode */
 } dcd_precision;
 
 /* opts.flags */
@@ -83,6 +87,9 @@ typedef enum {
 #define DCD_FLAG_HOST_IO 0x2      /* A.values/row_ptr/col_idx, y, alpha, grad are host memory */
 #define DCD_FLAG_PHASE_TIMERS 0x4 /* fill the per-phase times of dcd_stats (adds one sync per step) */
 #define DCD_FLAG_NO_GRAPH 0x8     /* launch every kernel directly instead of replaying CUDA graphs */
+#define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
+                                     recompute the gradient from alpha by full kernel passes and accept
+                                     convergence only if the recomputed metric meets tol too */
 
 typedef struct {
     int32_t s;            /* inner steps per outer step, s >= 1 (Algorithms 2 and 4) */
@@ -108,6 +115,8 @@ typedef struct {
     double primal, dual;      /* K-SVM: P and D at the final alpha (from the cached gradient) */
     double ms_total;          /* wall time of the call, device-timed */
     double ms_setup, ms_sample, ms_gram, ms_recur, ms_block, ms_update, ms_check;
+    int64_t refreshes;        /* gradient recomputations (DCD_FLAG_REFRESH) */
+    double ms_refresh;        /* their device time */
 } dcd_stats;
 
 /*

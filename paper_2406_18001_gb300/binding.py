@@ -20,10 +20,11 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONV, EINTERNAL, ENOTSPD, EUNSUPPORTED 
 DENSE, CSR = 0, 1
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 LINEAR, POLY, RBF = 0, 1, 2
-PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3, 4
-FLAG_GRAD_VALID, FLAG_HOST_IO, FLAG_PHASE_TIMERS, FLAG_NO_GRAPH = 0x1, 0x2, 0x4, 0x8
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3, PREC_TF32X3 = 0, 1, 2, 3, 4, 5
+FLAG_GRAD_VALID, FLAG_HOST_IO, FLAG_PHASE_TIMERS, FLAG_NO_GRAPH, FLAG_REFRESH = 0x1, 0x2, 0x4, 0x8, 0x10
 
-PREC_NAMES = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3}
+PREC_NAMES = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3,
+              "tf32x3": PREC_TF32X3}
 
 
 class Matrix(C.Structure):
@@ -47,7 +48,8 @@ class Stats(C.Structure):
                 ("gpu_launches_per_step", C.c_int32), ("final_metric", C.c_double), ("primal", C.c_double),
                 ("dual", C.c_double), ("ms_total", C.c_double), ("ms_setup", C.c_double),
                 ("ms_sample", C.c_double), ("ms_gram", C.c_double), ("ms_recur", C.c_double),
-                ("ms_block", C.c_double), ("ms_update", C.c_double), ("ms_check", C.c_double)]
+                ("ms_block", C.c_double), ("ms_update", C.c_double), ("ms_check", C.c_double),
+                ("refreshes", C.c_int64), ("ms_refresh", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

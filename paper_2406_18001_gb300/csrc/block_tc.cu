@@ -42,7 +42,9 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // split bf16 ("bf16x3": a = hi + lo with hi = bf16(a), lo = bf16(a - hi);
 // a.b ~ hi.hi + hi.lo + lo.hi, three MMAs per k-step into one accumulator,
 // dropping only lo.lo, about 2^-16 relative).
-constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2;
+// Split tf32 ("tf32x3") is the same with kind::tf32 and tf32 planes (~22
+// significant bits, at half the bf16 MMA rate).
+constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3;
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
@@ -239,8 +241,8 @@ template <int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     block_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
-    constexpr bool TF32 = MODE == MODE_TF32;
-    constexpr bool SPLIT = MODE == MODE_BF16X3;
+    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3;
+    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3;
     constexpr int STAGES = SPLIT ? 2 : 4;
     constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
     constexpr int B_ST = SPLIT ? 2 * B_STAGE : B_STAGE;
@@ -459,9 +461,9 @@ bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
 {
     auto fn = encode_fn();
     if (!fn) return false;
-    const bool f32 = op.kind == PACK_TF32;
+    const bool f32 = op.kind == PACK_TF32 || op.kind == PACK_TF32X3;
     const int esz = f32 ? 4 : 2;
-    const int64_t cols = op.kind == PACK_BF16X3 ? 2 * op.n_pad : op.n_pad;
+    const int64_t cols = (op.kind == PACK_BF16X3 || op.kind == PACK_TF32X3) ? 2 * op.n_pad : op.n_pad;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)op.nrows};
     cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
     cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows};
@@ -528,8 +530,9 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
-    if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3) return cudaErrorInvalidValue;
-    const int kb_elems = Aop.kind == PACK_TF32 ? 32 : 64;
+    if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3)
+        return cudaErrorInvalidValue;
+    const int kb_elems = (Aop.kind == PACK_TF32 || Aop.kind == PACK_TF32X3) ? 32 : 64;
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
     if (bn > BN_MAX) bn = BN_MAX;
@@ -568,6 +571,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     int grid = a.items < sms ? a.items : sms;
     if (Aop.kind == PACK_TF32) return launch_mode<MODE_TF32>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_BF16X3) return launch_mode<MODE_BF16X3>(grid, mA, mB, a, kp.kind, st);
+    if (Aop.kind == PACK_TF32X3) return launch_mode<MODE_TF32X3>(grid, mA, mB, a, kp.kind, st);
     return launch_mode<MODE_BF16>(grid, mA, mB, a, kp.kind, st);
 }
 

@@ -90,16 +90,23 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
 // Packed operand modes (also the pack kernel's dst_kind):
 //   0 bf16 rows of n_pad; 1 fp32 rows of n_pad rounded to tf32;
 //   3 split bf16 rows of 2*n_pad = [hi | lo].   (dst_kind 2 = fp64, FP64 path)
-enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3 };
+// Packed operand kinds.  Split kinds keep a = hi + lo as two planes per row
+// ([hi | lo], n_pad elements each): bf16x3 with hi = bf16(a), lo = bf16(a -
+// hi) (~16 significant bits), tf32x3 with both planes on the tf32 grid (~22
+// bits).
+enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4 };
 struct TcOperand {
     const void *rows;     // packed matrix, row-major
     int64_t nrows;
     int64_t n_pad;        // features per half, multiple of the k-block
-    int kind;             // PACK_BF16, PACK_TF32 or PACK_BF16X3
+    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3 or PACK_TF32X3
 };
+// elements per 128-byte k-block of a packed row (the padding unit of n_pad)
+__host__ __device__ inline int k_block_elems(int kind) { return (kind == PACK_TF32 || kind == PACK_TF32X3) ? 32 : 64; }
+
 __host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
 {
-    return kind == PACK_TF32 ? 4 * n_pad : (kind == PACK_BF16X3 ? 4 * n_pad : 2 * n_pad);
+    return kind == PACK_TF32X3 ? 8 * n_pad : (kind == PACK_TF32 || kind == PACK_BF16X3) ? 4 * n_pad : 2 * n_pad;
 }
 bool tc_available();
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,

@@ -102,6 +102,14 @@ __global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t
             __nv_bfloat16 *d = (__nv_bfloat16 *)dst + r * 2 * n_pad;
             d[c] = hi;
             d[n_pad + c] = lo;
+        } else if (dst_kind == PACK_TF32X3) {
+            // hi = tf32(v), lo = tf32(v - hi) (v - hi exact in fp32), both on the tf32 grid
+            uint32_t th, tl;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(th) : "f"(v));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tl) : "f"(v - __uint_as_float(th)));
+            float *d = (float *)dst + r * 2 * n_pad;
+            d[c] = __uint_as_float(th);
+            d[n_pad + c] = __uint_as_float(tl);
         } else if (dst_kind == 1) {
             // round to the tf32 grid (10-bit mantissa, nearest, ties away) so the
             // tensor core sees exactly the stored value and the row norms match
@@ -179,6 +187,10 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
         } else if (kind == PACK_BF16X3) {
             const __nv_bfloat16 *row = (const __nv_bfloat16 *)packed + r * 2 * n_pad;
             const float hi = __bfloat162float(row[c]), lo = __bfloat162float(row[n_pad + c]);
+            sf = fmaf(hi, hi + 2.f * lo, sf);
+        } else if (kind == PACK_TF32X3) {  // the products the three MMAs form: hi.hi + 2 hi.lo
+            const float *row = (const float *)packed + r * 2 * n_pad;
+            const float hi = row[c], lo = row[n_pad + c];
             sf = fmaf(hi, hi + 2.f * lo, sf);
         } else {
             const float v = __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);

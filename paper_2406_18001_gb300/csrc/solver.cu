@@ -82,12 +82,18 @@ size_t dtype_size(int dt) { return dt == DCD_F64 ? 8 : dt == DCD_F32 ? 4 : dt ==
 
 KernelParams to_kp(const dcd_kernel *k) { return KernelParams{k->kind, k->degree, k->gamma, k->coef0}; }
 
-bool is_tc(int prec) { return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3; }
+bool is_tc(int prec)
+{
+    return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3 || prec == DCD_PREC_TF32X3;
+}
 
 // packed operand kind of a tensor-core precision
 int pack_kind(int prec)
 {
-    return prec == DCD_PREC_TF32 ? PACK_TF32 : (prec == DCD_PREC_BF16X3 ? PACK_BF16X3 : PACK_BF16);
+    return prec == DCD_PREC_TF32 ? PACK_TF32
+           : prec == DCD_PREC_BF16X3 ? PACK_BF16X3
+           : prec == DCD_PREC_TF32X3 ? PACK_TF32X3
+                                     : PACK_BF16;
 }
 
 // Operand preparation shared by the solver and the component entry points.
@@ -164,6 +170,11 @@ struct Solver {
     // workspace
     void *ws = nullptr;
     Operand op;
+    // the operand (and column buffers) of the recomputed gradient: split tf32
+    // for the tensor-core modes (== op when the solve itself is split tf32)
+    Operand opr;
+    void *Asr = nullptr;
+    float *col_hr = nullptr;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
     int32_t *S = nullptr;
@@ -206,10 +217,13 @@ struct Solver {
         const bool host = (o.flags & DCD_FLAG_HOST_IO) != 0;
         sb = (int64_t)o.s * o.b;
         col_pad = (sb + 255) / 256 * 256;
-        const int kb_elems = o.prec == DCD_PREC_TF32 ? 32 : 64;
+        const int kb_elems = k_block_elems(pack_kind(o.prec));
         const int64_t n_pad = (n + kb_elems - 1) / kb_elems * kb_elems;
         const size_t row_bytes = tc ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
         const bool need_pack = tc || A->dtype != DCD_F64 || host;
+        const bool ref_op = tc && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
+        const int64_t n_pad_r = (n + 31) / 32 * 32;
+        const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
 
         // size the arena (two passes over the same layout)
         Arena ar;
@@ -224,6 +238,10 @@ struct Solver {
             void *as = ar.take(tc ? (size_t)sb * row_bytes : 0, 1024);
             float *ch = (float *)ar.take(sizeof(float) * col_pad);
             float *cw = (float *)ar.take(sizeof(float) * col_pad);
+            void *pkr = ar.take((size_t)m * row_bytes_r, 1024);
+            float *rhr = (float *)ar.take(ref_op ? sizeof(float) * m : 0);
+            void *asr = ar.take((size_t)sb * row_bytes_r, 1024);
+            float *chr = (float *)ar.take(ref_op ? sizeof(float) * col_pad : 0);
             int32_t *sidx = (int32_t *)ar.take(sizeof(int32_t) * col_pad);
             void *kss = ar.take((size_t)sb * sb * (tc ? 4 : 8));
             double *dl = (double *)ar.take(sizeof(double) * col_pad);
@@ -248,6 +266,10 @@ struct Solver {
             As = as;
             col_h = ch;
             col_w = cw;
+            opr.packed = pkr;
+            opr.row_h = rhr;
+            Asr = asr;
+            col_hr = chr;
             S = sidx;
             Kss = kss;
             ldk = sb;
@@ -286,6 +308,18 @@ struct Solver {
             op.kind = pack_kind(o.prec);
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st));
             DCD_TRY(launch_row_terms(op.packed, op.kind, n_pad, m, kp, op.row_h, st));
+            if (ref_op) {
+                opr.n_pad = n_pad_r;
+                opr.kind = PACK_TF32X3;
+                DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, opr.packed, opr.kind, n_pad_r, m, err,
+                                         st));
+                DCD_TRY(launch_row_terms(opr.packed, opr.kind, n_pad_r, m, kp, opr.row_h, st));
+                DCD_TRY(cudaMemsetAsync(col_hr, 0, sizeof(float) * col_pad, st));
+            } else {
+                opr = op;
+                Asr = As;
+                col_hr = col_h;
+            }
         } else if (need_pack) {
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st));
             op.a64 = (const double *)op.packed;
@@ -325,9 +359,58 @@ struct Solver {
         return DCD_OK;
     }
 
+    // Recomputes the cached gradient of the current alpha from scratch (the
+    // steps update it incrementally, so it drifts by the kernel block's
+    // rounding): the constant and diagonal part, then full kernel passes.
+    dcd_status refresh()
+    {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        dcd_status s0 = cuda_status(launch_init_grad(problem, y, alpha, diag, m, g, st));
+        if (s0 == DCD_OK) s0 = full_pass(true);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        stats.ms_refresh += ms;
+        ++stats.refreshes;
+        return s0;
+    }
+
+    // Convergence test at a check point: the metric of the cached gradient,
+    // confirmed on a recomputed gradient with DCD_FLAG_REFRESH.
+    // After a recomputed gradient misses tol, the next recomputation waits
+    // for twice as many check points as the previous wait (bounded cost when
+    // the precision's floor lies above tol).
+    int64_t refresh_wait = 0, refresh_gap = 1;
+
+    dcd_status check_converged()
+    {
+        dcd_status s0 = measure(metric, primal, dual, ynorm2);
+        if (s0 != DCD_OK || !(metric <= o.tol)) return s0;
+        if (o.flags & DCD_FLAG_REFRESH) {
+            if (refresh_wait > 0) {
+                --refresh_wait;
+                return DCD_OK;
+            }
+            if ((s0 = refresh()) != DCD_OK) return s0;
+            if ((s0 = measure(metric, primal, dual, ynorm2)) != DCD_OK) return s0;
+            if (!(metric <= o.tol)) {
+                refresh_wait = refresh_gap;
+                refresh_gap *= 2;
+            }
+        }
+        if (metric <= o.tol) conv = true;
+        return DCD_OK;
+    }
+
     // g += rs * K(A, A_cols) w over all columns, in chunks of SB_MAX: the
     // kernel part of the gradient for a nonzero alpha_0.
-    dcd_status full_pass()
+    dcd_status full_pass(bool ref = false)
     {
         std::vector<int32_t> hidx;
         const int64_t chunk = std::min<int64_t>(m, std::min<int64_t>(SB_MAX, sb));
@@ -337,20 +420,21 @@ struct Solver {
             for (int64_t j = 0; j < cnt; ++j) hidx[j] = (int32_t)(c0 + j);
             DCD_TRY(cudaMemcpyAsync(S, hidx.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st));
             DCD_TRY(launch_coef(problem == 0 ? y : nullptr, alpha, S, cnt, 1.0 / lambda, w64, st));
-            dcd_status s2 = apply_block(cnt);
+            dcd_status s2 = apply_block(cnt, ref);
             if (s2 != DCD_OK) return s2;
             DCD_TRY(cudaStreamSynchronize(st));  // hidx is reused
         }
         return DCD_OK;
     }
 
-    // gather A_S for the tensor-core path
-    cudaError_t gather(int64_t ncols)
+    // gather A_S for the tensor-core path (of the step operand, or of x)
+    cudaError_t gather(int64_t ncols) { return gather_op(ncols, op, As, col_h); }
+    cudaError_t gather_op(int64_t ncols, const Operand &x, void *Asx, float *chx)
     {
         if (!tc) return cudaSuccess;
-        cudaError_t e = launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), S, ncols, m, As, err, st);
+        cudaError_t e = launch_gather_rows(x.packed, packed_row_bytes(x.kind, x.n_pad), S, ncols, m, Asx, err, st);
         if (e != cudaSuccess) return e;
-        return launch_gather_f32(op.row_h, S, ncols, col_h, st);
+        return launch_gather_f32(x.row_h, S, ncols, chx, st);
     }
 
     cudaError_t gram(int64_t ncols)
@@ -364,18 +448,26 @@ struct Solver {
                                      (double *)Kss, ldk, err, st);
     }
 
-    dcd_status apply_block(int64_t ncols)
+    // g += rs * K(A, A_S) w64 with the step operand, or (ref) with the
+    // operand of the recomputed gradient
+    dcd_status apply_block(int64_t ncols, bool ref = false)
     {
         const double *rs = problem == 0 ? y : nullptr;
         if (tc) {
+            const Operand &x = ref ? opr : op;
+            void *Asx = ref ? Asr : As;
+            float *chx = ref ? col_hr : col_h;
             // the coefficients in w64 (FP64) go to the FP32 column buffer
-            cudaError_t e = gather(ncols);
+            cudaError_t e = gather_op(ncols, x, Asx, chx);
             if (e != cudaSuccess) return cuda_status(e);
             e = launch_f64_to_f32(w64, ncols, col_w, st);
             if (e != cudaSuccess) return cuda_status(e);
             e = clear_col_w_tail(ncols);
             if (e != cudaSuccess) return cuda_status(e);
-            return cuda_status(block_tc_apply(ncols, rs));
+            TcOperand Aop{x.packed, m, x.n_pad, x.kind};
+            TcOperand Bop{Asx, ncols, x.n_pad, x.kind};
+            return cuda_status(
+                launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st));
         }
         return cuda_status(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr,
                                                  0, err, st));
@@ -560,18 +652,21 @@ struct Solver {
             if (s0 != DCD_OK) break;
             if (check_every && o.tol > 0 && steps % check_every == 0 && done < o.max_iters) {
                 tm.start();
-                s0 = measure(metric, primal, dual, ynorm2);
+                s0 = check_converged();
                 tm.stop(stats.ms_check);
                 tm.flush();
                 if (s0 != DCD_OK) break;
-                if (metric <= o.tol) conv = true;
             }
         }
         // the metric is measured at check points and when the budget ends;
         // an intermediate dcd_plan_run without a tolerance leaves it NaN
         if (s0 == DCD_OK && (finished() || o.tol > 0)) {
-            s0 = measure(metric, primal, dual, ynorm2);
-            if (s0 == DCD_OK && o.tol > 0 && metric <= o.tol) conv = true;
+            if (conv)
+                ;  // measured (and confirmed) at the check point that converged
+            else if (o.tol > 0)
+                s0 = check_converged();
+            else
+                s0 = measure(metric, primal, dual, ynorm2);
         } else if (s0 == DCD_OK) {
             metric = primal = dual = NAN;
         }
@@ -882,7 +977,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         return finish_component(err, st);
     }
     const int pk = pack_kind(prec);
-    const int kb = pk == PACK_TF32 ? 32 : 64;
+    const int kb = k_block_elems(pk);
     const int64_t n_pad = (A->n + kb - 1) / kb * kb;
     const size_t rb = (size_t)packed_row_bytes(pk, n_pad);
     const int64_t cpad = (ncols + 255) / 256 * 256;

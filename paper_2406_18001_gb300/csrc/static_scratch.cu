@@ -87,7 +87,8 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
         return DCD_EINVAL;
     if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
     if (!kernel_ok(k)) return DCD_EINVAL;
-    if (prec != DCD_PREC_FP64 && prec != DCD_PREC_BF16 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16X3)
+    if (prec != DCD_PREC_FP64 && prec != DCD_PREC_BF16 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16X3 &&
+        prec != DCD_PREC_TF32X3)
         return DCD_EINVAL;
     if (nrows < 0 || ncols < 0 || !cols || !out || ldo < ncols) return DCD_EINVAL;
     if (!rows && nrows > A->m) return DCD_EINVAL;
@@ -98,8 +99,11 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
     const KernelParams kp{k->kind, k->degree, k->gamma, k->coef0};
 
     // scratch layout and the size check, before touching the device
-    const int pk = prec == DCD_PREC_TF32 ? PACK_TF32 : (prec == DCD_PREC_BF16X3 ? PACK_BF16X3 : PACK_BF16);
-    const int kb = pk == PACK_TF32 ? 32 : 64;
+    const int pk = prec == DCD_PREC_TF32     ? PACK_TF32
+                   : prec == DCD_PREC_BF16X3 ? PACK_BF16X3
+                   : prec == DCD_PREC_TF32X3 ? PACK_TF32X3
+                                             : PACK_BF16;
+    const int kb = k_block_elems(pk);
     const int64_t n_pad = (A->n + kb - 1) / kb * kb;
     const size_t rb = (size_t)packed_row_bytes(pk, n_pad);
     const int64_t cpad = (ncols + 255) / 256 * 256;
