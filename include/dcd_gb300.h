@@ -53,9 +53,17 @@ typedef struct {
     int64_t ld;               /* dense: leading dimension in elements, >= n */
     const void *values;       /* dense: m*ld elements; CSR: nnz elements */
     const int64_t *row_ptr;   /* CSR only: m+1 offsets, row_ptr[0] = 0, non-decreasing */
-    const int32_t *col_idx;   /* CSR only: nnz column indices in [0, n) */
+    const int32_t *col_idx;   /* CSR only: nnz column indices in [0, n), distinct within a row */
     const float *row_scale;   /* FP8 only: a_i = row_scale[i] * q_i; else NULL */
 } dcd_matrix;
+/*
+ * CSR matrices take F32 or F64 values (BF16 / FP8 give DCD_EUNSUPPORTED).
+ * Their kernel block is an SpMM on the CUDA cores, streamed once per outer
+ * step: FP64 under DCD_PREC_FP64, FP32 under every tensor-core precision
+ * (the block is bound by HBM, not arithmetic).  Offsets that decrease or
+ * exceed nnz, and columns outside [0, n), give DCD_EINVAL (checked on the
+ * device before the solve starts).
+ */
 
 /* Kernel functions of Table 1 (Section 3.1). */
 typedef enum { DCD_LINEAR = 0, DCD_POLY = 1, DCD_RBF = 2 } dcd_kernel_kind;

@@ -134,8 +134,39 @@ def _stream(stream):
     return C.c_void_p(int(stream))
 
 
+class Csr:
+    """A CSR matrix for the library: int64 row_ptr[m+1], int32 col_idx[nnz],
+    float32 / float64 values (torch tensors on one device, or numpy arrays
+    with DCD_FLAG_HOST_IO)."""
+
+    def __init__(self, row_ptr, col_idx, values, n):
+        self.row_ptr, self.col_idx, self.values, self.n = row_ptr, col_idx, values, int(n)
+        self.m = int(row_ptr.shape[0]) - 1
+
+    @property
+    def shape(self):
+        return (self.m, self.n)
+
+    @property
+    def device(self):
+        return self.values.device
+
+    def matrix(self) -> Matrix:
+        import numpy as _np
+        v = self.values
+        if isinstance(v, _np.ndarray):
+            dt = {_np.dtype(_np.float64): F64, _np.dtype(_np.float32): F32}[v.dtype]
+        else:
+            import torch
+            dt = {torch.float64: F64, torch.float32: F32}[v.dtype]
+        return Matrix(CSR, dt, self.m, self.n, 0, _ptr(v), _ptr(self.row_ptr), _ptr(self.col_idx), None)
+
+
 def dense_matrix(A) -> Matrix:
-    """Describe a row-major 2-D torch tensor (device) or numpy array (host)."""
+    """Describe a row-major 2-D torch tensor (device) or numpy array (host),
+    or a Csr."""
+    if isinstance(A, Csr):
+        return A.matrix()
     if isinstance(A, np.ndarray):
         dt = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[A.dtype]
         assert A.flags.c_contiguous

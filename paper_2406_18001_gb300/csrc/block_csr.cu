@@ -1,0 +1,413 @@
+// block_csr.cu -- the sampled kernel block for a CSR data matrix.
+//
+// With A sparse (config: 50 nonzeros in 50000 columns per row), the block
+// K(A, A_S) is an SpMM: a_i . a_j for every row i and every sampled row j,
+// then the kernel function (Table 1; RBF via ||a||^2 + ||b||^2 - 2 a.b with
+// precomputed squared row norms).  The work is bound by streaming A's CSR
+// arrays from HBM once per outer step, not by arithmetic, so it runs on the
+// CUDA cores (no tensor-core reshaping):
+//
+//   colmap   once per step, one CTA: the columns touched by the sampled rows
+//            as a bitmap over [0, n) with per-word popcount prefixes (rank of
+//            a column = its slot), and per slot the (j, value) entries of the
+//            sampled rows holding that column.
+//   block    one warp per tile of 32 rows: the tile's nonzeros are read once,
+//            coalesced; a nonzero whose column is in the bitmap (rare) is a
+//            hit, appended in element order to a per-warp list; then lane r
+//            adds value * entry for its row's hits into a per-row row of
+//            accumulators (so the partial dots are summed in a fixed order),
+//            and applies the kernel function and the epilogue (apply: g_i +=
+//            rs_i sum_j K_ij w_j, FP64 add; store: K_ij).
+//
+// Sampled columns are processed in chunks of CSR_JC per launch (a tile
+// re-reads its nonzeros per chunk); the K-SVM configuration has s*b <= 32.
+#include "dcd_internal.cuh"
+
+namespace dcd {
+
+namespace {
+
+constexpr int CSR_JC = 32;        // sampled columns per pass
+constexpr int CSR_HL = 256;       // hit-list capacity per warp (flushed when full)
+constexpr int CSR_WARPS = 8;      // warps per CTA
+constexpr int CSR_U = 4;          // nonzeros in flight per lane in the scan
+constexpr int MAP_THREADS = 1024;
+
+template <typename T>
+__device__ __forceinline__ T kfun_t(const KernelParams &kp, T dot, T na, T nb, bool same)
+{
+    if (kp.kind == DCD_LINEAR) return dot;
+    if (kp.kind == DCD_POLY) {
+        T t = (T)kp.coef0 + dot, r = t;
+        for (int e = 1; e < kp.degree; ++e) r *= t;
+        return r;
+    }
+    T d2 = same ? (T)0 : na + nb - (T)2 * dot;  // the sample's own row: distance exactly 0
+    d2 = d2 > (T)0 ? d2 : (T)0;
+    return exp(-(T)kp.gamma * d2);
+}
+
+template <typename T>
+struct WarpSmem {
+    T acc[32][CSR_JC + 1];
+    int32_t hrow[CSR_HL];
+    int32_t hslot[CSR_HL];
+    T hval[CSR_HL];
+    int64_t rp[33];
+};
+
+__device__ __forceinline__ bool col_hit(const uint32_t *bits, int32_t c)
+{
+    return (__ldg(bits + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+__device__ __forceinline__ int32_t col_slot(const uint32_t *bits, const int32_t *wprefix, int32_t c)
+{
+    const uint32_t w = __ldg(bits + (c >> 5));
+    return __ldg(wprefix + (c >> 5)) + __popc(w & ((1u << (c & 31)) - 1u));
+}
+
+// Lane r adds the hits of row r (in list order) into acc[r][.].
+template <typename T>
+__device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrColMap &M, int j0, int jc, int lane)
+{
+    __syncwarp();
+    for (int h = 0; h < nh; ++h) {
+        if (ws.hrow[h] != lane) continue;
+        const int slot = ws.hslot[h];
+        const T v = ws.hval[h];
+        for (int q = M.slot_off[slot]; q < M.slot_off[slot + 1]; ++q) {
+            const int j = M.ent_j[q] - j0;
+            if (j >= 0 && j < jc) ws.acc[lane][j] += v * (T)M.ent_v[q];
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, bool STORE>
+__global__ void __launch_bounds__(CSR_WARPS * 32)
+    csr_block_kernel(CsrOperand A, CsrColMap M, const int32_t *rows, int64_t nrows, const int32_t *S, int j0, int jc,
+                     KernelParams kp, const float *w32, const double *w64, const double *rs, double *g, float *out32,
+                     double *out64, int64_t ldo)
+{
+    extern __shared__ __align__(16) unsigned char csr_sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<T> &ws = ((WarpSmem<T> *)csr_sm)[warp];
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
+    for (int j = 0; j < CSR_JC; ++j) ws.acc[lane][j] = (T)0;
+    const int64_t ntiles = (nrows + 31) / 32;
+    for (int64_t tile = (int64_t)blockIdx.x * CSR_WARPS + warp; tile < ntiles;
+         tile += (int64_t)gridDim.x * CSR_WARPS) {
+        const int64_t t0 = tile * 32;
+        const int nr = (int)min((int64_t)32, nrows - t0);
+        int nh = 0;
+        if (!STORE) {
+            // rows t0 .. t0+nr-1 are contiguous: one coalesced pass over their nonzeros
+            for (int k = lane; k <= nr; k += 32) ws.rp[k] = A.row_ptr[t0 + k];
+            __syncwarp();
+            const int64_t e0 = ws.rp[0], e1 = ws.rp[nr];
+            for (int64_t eb = e0; eb < e1; eb += 32 * CSR_U) {
+                int32_t c[CSR_U];
+                T v[CSR_U];
+                bool hit[CSR_U];
+#pragma unroll
+                for (int u = 0; u < CSR_U; ++u) {
+                    const int64_t e = eb + 32 * u + lane;
+                    c[u] = e < e1 ? __ldg(A.col_idx + e) : -1;
+                    v[u] = e < e1 ? vals[e] : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < CSR_U; ++u) hit[u] = c[u] >= 0 && col_hit(M.bits, c[u]);
+#pragma unroll
+                for (int u = 0; u < CSR_U; ++u) {
+                    const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
+                    if (nh + __popc(mk) > CSR_HL) {
+                        flush_hits(ws, nh, M, j0, jc, lane);
+                        nh = 0;
+                    }
+                    if (hit[u]) {
+                        const int64_t e = eb + 32 * u + lane;
+                        int lo = 0, hi = nr - 1;  // the row holding element e: last k with rp[k] <= e
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (ws.rp[mid] <= e) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int pos = nh + __popc(mk & ((1u << lane) - 1u));
+                        ws.hrow[pos] = lo;
+                        ws.hslot[pos] = col_slot(M.bits, M.wprefix, c[u]);
+                        ws.hval[pos] = v[u];
+                    }
+                    nh += __popc(mk);
+                }
+            }
+        } else {
+            // listed rows: one row at a time
+            for (int k = 0; k < nr; ++k) {
+                const int64_t r = rows ? (int64_t)rows[t0 + k] : t0 + k;
+                const int64_t e0 = A.row_ptr[r], e1 = A.row_ptr[r + 1];
+                for (int64_t eb = e0; eb < e1; eb += 32) {
+                    const int64_t e = eb + lane;
+                    const int32_t c = e < e1 ? __ldg(A.col_idx + e) : -1;
+                    const bool hit = c >= 0 && col_hit(M.bits, c);
+                    const unsigned mk = __ballot_sync(0xffffffffu, hit);
+                    if (nh + __popc(mk) > CSR_HL) {
+                        flush_hits(ws, nh, M, j0, jc, lane);
+                        nh = 0;
+                    }
+                    if (hit) {
+                        const int pos = nh + __popc(mk & ((1u << lane) - 1u));
+                        ws.hrow[pos] = k;
+                        ws.hslot[pos] = col_slot(M.bits, M.wprefix, c);
+                        ws.hval[pos] = vals[e];
+                    }
+                    nh += __popc(mk);
+                }
+            }
+        }
+        flush_hits(ws, nh, M, j0, jc, lane);
+        // epilogue: lane r owns row t0 + r
+        if (lane < nr) {
+            const int64_t row = (STORE && rows) ? (int64_t)rows[t0 + lane] : t0 + lane;
+            const T na = kp.kind == DCD_RBF ? norm[row] : (T)0;
+            T sum = (T)0;
+            for (int j = 0; j < jc; ++j) {
+                const int32_t sj = S[j0 + j];
+                const T nb = kp.kind == DCD_RBF ? norm[sj] : (T)0;
+                const T kv = kfun_t<T>(kp, ws.acc[lane][j], na, nb, sj == row);
+                ws.acc[lane][j] = (T)0;
+                if (STORE) {
+                    if (sizeof(T) == 8) out64[(t0 + lane) * ldo + j0 + j] = (double)kv;
+                    else out32[(t0 + lane) * ldo + j0 + j] = (float)kv;
+                } else {
+                    sum += kv * (sizeof(T) == 8 ? (T)w64[j0 + j] : (T)w32[j0 + j]);
+                }
+            }
+            if (!STORE) g[row] += (rs ? rs[row] : 1.0) * (double)sum;
+        }
+        __syncwarp();
+    }
+}
+
+// Column map of the sampled rows S[0..cnt) (one CTA).  Slots are the ranks of
+// the touched columns; entries of a slot are (j, a_{S_j, c}).
+__global__ void __launch_bounds__(MAP_THREADS) csr_colmap_kernel(CsrOperand A, const int32_t *S, int cnt, CsrColMap M,
+                                                                 int *err)
+{
+    __shared__ int32_t part[MAP_THREADS];
+    __shared__ long long total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) total = 0;
+    for (int w = tid; w < M.nw; w += MAP_THREADS) M.bits[w] = 0u;
+    __syncthreads();
+    // 0. the sampled rows' nonzeros must fit the entry capacity
+    for (int j = tid; j < cnt; j += MAP_THREADS) {
+        const int64_t r = S[j];
+        if (r >= 0 && r < A.m) atomicAdd((unsigned long long *)&total, (unsigned long long)(A.row_ptr[r + 1] - A.row_ptr[r]));
+    }
+    __syncthreads();
+    if (total > M.cap) {  // the same value in every thread
+        if (tid == 0) set_error(err, DEV_INTERNAL);
+        return;
+    }
+    // 1. mark the columns (warp per sampled row)
+    for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
+        const int64_t r = S[j];
+        if (r < 0 || r >= A.m) {
+            if (lane == 0) set_error(err, DEV_BAD_INDEX);
+            continue;
+        }
+        for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
+            const int32_t c = A.col_idx[e];
+            atomicOr(&M.bits[c >> 5], 1u << (c & 31));
+        }
+    }
+    __syncthreads();
+    // 2. exclusive popcount prefix over the words (contiguous chunk per thread, block scan of the chunk sums)
+    const int per = (M.nw + MAP_THREADS - 1) / MAP_THREADS;
+    const int w0 = tid * per, w1 = min(M.nw, w0 + per);
+    int s = 0;
+    for (int w = w0; w < w1; ++w) s += __popc(M.bits[w]);
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < MAP_THREADS; off <<= 1) {
+        const int add = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += add;
+        __syncthreads();
+    }
+    int run = part[tid] - s;
+    for (int w = w0; w < w1; ++w) {
+        M.wprefix[w] = run;
+        run += __popc(M.bits[w]);
+    }
+    const int nslots = part[MAP_THREADS - 1];
+    __syncthreads();
+    // 3. entries per slot (counts are zero on entry and return to zero below)
+    for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
+        const int64_t r = S[j];
+        if (r < 0 || r >= A.m) continue;
+        for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
+            const int32_t c = A.col_idx[e];
+            const uint32_t w = M.bits[c >> 5];
+            atomicAdd(&M.counts[M.wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u))], 1);
+        }
+    }
+    __syncthreads();
+    // 4. slot offsets: exclusive scan of the counts
+    const int sper = (nslots + MAP_THREADS - 1) / MAP_THREADS;
+    const int s0 = tid * sper, s1 = min(nslots, s0 + sper);
+    int cs = 0;
+    for (int q = s0; q < s1; ++q) cs += M.counts[q];
+    __syncthreads();
+    part[tid] = cs;
+    __syncthreads();
+    for (int off = 1; off < MAP_THREADS; off <<= 1) {
+        const int add = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += add;
+        __syncthreads();
+    }
+    int run2 = part[tid] - cs;
+    for (int q = s0; q < s1; ++q) {
+        M.slot_off[q] = run2;
+        run2 += M.counts[q];
+    }
+    if (tid == MAP_THREADS - 1) M.slot_off[nslots] = part[MAP_THREADS - 1];
+    __syncthreads();
+    // 5. fill (taking the counts back to zero)
+    for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
+        const int64_t r = S[j];
+        if (r < 0 || r >= A.m) continue;
+        for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
+            const int32_t c = A.col_idx[e];
+            const uint32_t w = M.bits[c >> 5];
+            const int slot = M.wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u));
+            const int pos = M.slot_off[slot] + atomicSub(&M.counts[slot], 1) - 1;
+            M.ent_j[pos] = j;
+            M.ent_v[pos] = A.vals64 ? A.vals64[e] : (double)A.vals32[e];
+        }
+    }
+}
+
+// squared row norms (FP32 and FP64), the longest row, and a validity check
+// of the CSR arrays (bad counts the offending rows and entries)
+__global__ void csr_prep_kernel(CsrOperand A, int *bad, int *maxlen)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= A.m) return;
+    const int64_t e0 = A.row_ptr[r], e1 = A.row_ptr[r + 1];
+    if (lane == 0 && (e1 < e0 || e0 < 0 || e1 > A.nnz)) atomicAdd(bad, 1);
+    if (lane == 0 && e1 >= e0) atomicMax(maxlen, (int)min(e1 - e0, (int64_t)INT32_MAX));
+    double s = 0.0;
+    if (e1 >= e0 && e0 >= 0 && e1 <= A.nnz)
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t c = A.col_idx[e];
+            if (c < 0 || c >= A.n) atomicAdd(bad, 1);
+            const double v = A.vals64 ? A.vals64[e] : (double)A.vals32[e];
+            s += v * v;
+        }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        if (A.norm64) A.norm64[r] = s;
+        if (A.norm32) A.norm32[r] = (float)s;
+    }
+}
+
+template <typename T, bool STORE>
+cudaError_t launch_csr_kernel(const CsrOperand &A, const CsrColMap &M, const int32_t *rows, int64_t nrows,
+                              const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
+                              const double *w64, const double *rs, double *g, float *out32, double *out64,
+                              int64_t ldo, cudaStream_t st)
+{
+    auto kfn = csr_block_kernel<T, STORE>;
+    const size_t smem = sizeof(WarpSmem<T>) * CSR_WARPS;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t tiles = (nrows + 31) / 32, per_sm = 2;
+    int64_t grid = (tiles + CSR_WARPS - 1) / CSR_WARPS;
+    if (grid > (int64_t)sms * per_sm) grid = (int64_t)sms * per_sm;
+    for (int64_t j0 = 0; j0 < ncols; j0 += CSR_JC) {
+        const int jc = (int)min((int64_t)CSR_JC, ncols - j0);
+        kfn<<<(unsigned)grid, CSR_WARPS * 32, smem, st>>>(A, M, rows, nrows, S, (int)j0, jc, kp, w32, w64, rs, g,
+                                                          out32, out64, ldo);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t csr_colmap_bytes(int64_t n, int64_t cap)
+{
+    const int64_t nw = (n + 31) / 32;
+    return (size_t)nw * 8 + (size_t)(cap + 1) * 4 * 2 + (size_t)cap * (4 + 8) + 256 * 5;
+}
+
+CsrColMap csr_colmap_carve(void *base, int64_t n, int64_t cap)
+{
+    CsrColMap M;
+    char *p = (char *)base;
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += (bytes + 255) / 256 * 256;
+        return (void *)r;
+    };
+    M.nw = (int)((n + 31) / 32);
+    M.cap = cap;
+    M.bits = (uint32_t *)take((size_t)M.nw * 4);
+    M.wprefix = (int32_t *)take((size_t)M.nw * 4);
+    M.slot_off = (int32_t *)take((size_t)(cap + 1) * 4);
+    M.counts = (int32_t *)take((size_t)(cap + 1) * 4);
+    M.ent_j = (int32_t *)take((size_t)cap * 4);
+    M.ent_v = (double *)take((size_t)cap * 8);
+    return M;
+}
+
+cudaError_t launch_csr_prep(const CsrOperand &A, int *bad, int *maxlen, cudaStream_t st)
+{
+    if (A.m <= 0) return cudaSuccess;
+    const int64_t blocks = (A.m * 32 + 255) / 256;
+    csr_prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, bad, maxlen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_colmap(const CsrOperand &A, const int32_t *S, int64_t cnt, const CsrColMap &M, int *err,
+                              cudaStream_t st)
+{
+    if (cnt <= 0) return cudaSuccess;
+    csr_colmap_kernel<<<1, MAP_THREADS, 0, st>>>(A, S, (int)cnt, M, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_block(const CsrOperand &A, const CsrColMap &M, bool fp64, const KernelParams &kp,
+                             const int32_t *rows, int64_t nrows, const int32_t *S, int64_t ncols, const float *w32,
+                             const double *w64, const double *rs, double *g, void *out, int64_t ldo, cudaStream_t st)
+{
+    if (nrows <= 0 || ncols <= 0) return cudaSuccess;
+    const bool store = out != nullptr;
+    if (fp64)
+        return store ? launch_csr_kernel<double, true>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr,
+                                                        (double *)out, ldo, st)
+                     : launch_csr_kernel<double, false>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr,
+                                                         nullptr, ldo, st);
+    return store ? launch_csr_kernel<float, true>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, (float *)out,
+                                                   nullptr, ldo, st)
+                 : launch_csr_kernel<float, false>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr, nullptr,
+                                                    ldo, st);
+}
+
+}  // namespace dcd

@@ -135,6 +135,39 @@ cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStr
 cudaError_t launch_coef(const double *y, const double *alpha, const int32_t *cols, int64_t count, double scale,
                         double *w, cudaStream_t st);
 
+// CSR kernel block (block_csr.cu).  Values in FP32 (vals32) or FP64 (vals64,
+// which takes precedence); squared row norms filled by launch_csr_prep.
+struct CsrOperand {
+    const int64_t *row_ptr = nullptr;
+    const int32_t *col_idx = nullptr;
+    const float *vals32 = nullptr;
+    const double *vals64 = nullptr;
+    int64_t m = 0, n = 0, nnz = 0;
+    float *norm32 = nullptr;
+    double *norm64 = nullptr;
+};
+// Column map of the sampled rows: bitmap over [0, n), popcount prefix per
+// 32-column word, per-slot entry offsets and (j, value) entries; capacity
+// `cap` >= the sampled rows' nonzeros; counts zero between uses.
+struct CsrColMap {
+    uint32_t *bits = nullptr;
+    int32_t *wprefix = nullptr, *slot_off = nullptr, *counts = nullptr, *ent_j = nullptr;
+    double *ent_v = nullptr;
+    int nw = 0;
+    int64_t cap = 0;
+};
+size_t csr_colmap_bytes(int64_t n, int64_t cap);
+CsrColMap csr_colmap_carve(void *base, int64_t n, int64_t cap);
+cudaError_t launch_csr_prep(const CsrOperand &A, int *bad, int *maxlen, cudaStream_t st);
+cudaError_t launch_csr_colmap(const CsrOperand &A, const int32_t *S, int64_t cnt, const CsrColMap &M, int *err,
+                              cudaStream_t st);
+// apply (out == nullptr): g[i] += rs[i] * sum_j K(a_i, a_{S_j}) w_j for i < nrows (rows == nullptr);
+// store: out[r*ldo + j] = K(a_{rows[r]}, a_{S_j}) (rows == nullptr: row r).  FP64 (w64, out
+// double) or FP32 (w32, out float).
+cudaError_t launch_csr_block(const CsrOperand &A, const CsrColMap &M, bool fp64, const KernelParams &kp,
+                             const int32_t *rows, int64_t nrows, const int32_t *S, int64_t ncols, const float *w32,
+                             const double *w64, const double *rs, double *g, void *out, int64_t ldo, cudaStream_t st);
+
 // recurrence (recur.cu)
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
                              const double *y, const double *alpha, const double *g, double omega, double nu,

@@ -66,10 +66,18 @@ dcd_status validate_kernel(const dcd_kernel *k)
     }
 }
 
+// Dense: row-major f64/f32/bf16 with ld >= n.  CSR: f32/f64 values, int64
+// row offsets, int32 columns (checked on the device by the solver).
 dcd_status validate_dense(const dcd_matrix *A)
 {
     if (!A || A->m < 1 || A->n < 1) return DCD_EINVAL;
-    if (A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;
+    if (A->fmt == DCD_CSR) {
+        if (!A->row_ptr || !A->col_idx || !A->values) return DCD_EINVAL;
+        if (A->dtype == DCD_BF16 || A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
+        if (A->dtype != DCD_F64 && A->dtype != DCD_F32) return DCD_EINVAL;
+        if (A->m > INT32_MAX || A->n > INT32_MAX) return DCD_EINVAL;
+        return DCD_OK;
+    }
     if (A->fmt != DCD_DENSE) return DCD_EINVAL;
     if (A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
     if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
@@ -175,6 +183,11 @@ struct Solver {
     Operand opr;
     void *Asr = nullptr;
     float *col_hr = nullptr;
+    // CSR data matrix: the CUDA-core SpMM block (FP32, or FP64 in the FP64 mode)
+    bool csr = false;
+    CsrOperand ca;
+    CsrColMap cm;
+    void *ws_csr = nullptr;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
     int32_t *S = nullptr;
@@ -193,6 +206,7 @@ struct Solver {
     ~Solver()
     {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (ws_csr) cudaFreeAsync(ws_csr, st);
         if (ws) cudaFreeAsync(ws, st);
     }
 
@@ -214,14 +228,28 @@ struct Solver {
         m = A->m;
         n = A->n;
         tc = is_tc(o.prec);
+        csr = A->fmt == DCD_CSR;
         const bool host = (o.flags & DCD_FLAG_HOST_IO) != 0;
+        int64_t nnz = 0;
+        if (csr) {
+            if (host) {
+                nnz = A->row_ptr[m];
+            } else {
+                DCD_TRY(cudaMemcpyAsync(&nnz, A->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+                DCD_TRY(cudaStreamSynchronize(st));
+            }
+            if (nnz < 0) return DCD_EINVAL;
+        }
+        const bool tcd = tc && !csr;  // packed tensor-core operand (dense only)
+        // CSR values in the block's type: FP32 (tensor-core precisions) or FP64
+        const bool conv32 = csr && tc && A->dtype != DCD_F32, conv64 = csr && !tc && A->dtype != DCD_F64;
         sb = (int64_t)o.s * o.b;
         col_pad = (sb + 255) / 256 * 256;
         const int kb_elems = k_block_elems(pack_kind(o.prec));
         const int64_t n_pad = (n + kb_elems - 1) / kb_elems * kb_elems;
-        const size_t row_bytes = tc ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
-        const bool need_pack = tc || A->dtype != DCD_F64 || host;
-        const bool ref_op = tc && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
+        const size_t row_bytes = tcd ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
+        const bool need_pack = !csr && (tc || A->dtype != DCD_F64 || host);
+        const bool ref_op = tcd && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
         const int64_t n_pad_r = (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
 
@@ -229,13 +257,19 @@ struct Solver {
         Arena ar;
         for (int pass = 0; pass < 2; ++pass) {
             ar.used = 0;
-            char *hv = (char *)ar.take(host ? (size_t)m * A->ld * dtype_size(A->dtype) : 0, 1024);
+            char *hv = (char *)ar.take(host ? (csr ? (size_t)nnz : (size_t)m * A->ld) * dtype_size(A->dtype) : 0, 1024);
+            int64_t *hrp = (int64_t *)ar.take(host && csr ? sizeof(int64_t) * (m + 1) : 0);
+            int32_t *hci = (int32_t *)ar.take(host && csr ? sizeof(int32_t) * nnz : 0);
+            float *cv32 = (float *)ar.take(conv32 ? sizeof(float) * nnz : 0);
+            double *cv64 = (double *)ar.take(conv64 ? sizeof(double) * nnz : 0);
+            float *nrm32 = (float *)ar.take(csr ? sizeof(float) * m : 0);
+            double *nrm64 = (double *)ar.take(csr ? sizeof(double) * m : 0);
             double *yv = (double *)ar.take(host ? sizeof(double) * m : 0);
             double *av = (double *)ar.take(host ? sizeof(double) * m : 0);
             double *gv = (double *)ar.take(sizeof(double) * m);
             void *pk = ar.take(need_pack ? (size_t)m * row_bytes : 0, 1024);
-            float *rh = (float *)ar.take(tc ? sizeof(float) * m : 0);
-            void *as = ar.take(tc ? (size_t)sb * row_bytes : 0, 1024);
+            float *rh = (float *)ar.take(tcd ? sizeof(float) * m : 0);
+            void *as = ar.take(tcd ? (size_t)sb * row_bytes : 0, 1024);
             float *ch = (float *)ar.take(sizeof(float) * col_pad);
             float *cw = (float *)ar.take(sizeof(float) * col_pad);
             void *pkr = ar.take((size_t)m * row_bytes_r, 1024);
@@ -248,7 +282,7 @@ struct Solver {
             double *wv = (double *)ar.take(sizeof(double) * col_pad);
             double *lb = (double *)ar.take(problem == 1 ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             uint64_t *cr = (uint64_t *)ar.take(sizeof(uint64_t));
-            int *er = (int *)ar.take(sizeof(int) * 2);
+            int *er = (int *)ar.take(sizeof(int) * 4);
             double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
             double *rs = (double *)ar.take(sizeof(double) * 4);
             int64_t ichunk = std::min<int64_t>(m, SB_MAX);
@@ -260,6 +294,23 @@ struct Solver {
                 continue;
             }
             h_vals = hv;
+            if (csr) {
+                ca.row_ptr = host ? hrp : A->row_ptr;
+                ca.col_idx = host ? hci : A->col_idx;
+                const void *v = host ? (const void *)hv : A->values;
+                ca.vals32 = conv32 ? cv32 : (A->dtype == DCD_F32 ? (const float *)v : nullptr);
+                ca.vals64 = conv64 ? cv64 : (A->dtype == DCD_F64 ? (const double *)v : nullptr);
+                if (tc) ca.vals64 = nullptr;  // the FP32 block reads vals32
+                ca.m = m;
+                ca.n = n;
+                ca.nnz = nnz;
+                ca.norm32 = nrm32;
+                ca.norm64 = nrm64;
+                if (host) {
+                    DCD_TRY(cudaMemcpyAsync(hrp, A->row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, st));
+                    DCD_TRY(cudaMemcpyAsync(hci, A->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+                }
+            }
             g = gv;
             op.packed = pk;
             op.row_h = rh;
@@ -283,7 +334,8 @@ struct Solver {
             result = rs;
             iota = io;
             if (host) {
-                DCD_TRY(cudaMemcpyAsync(hv, A->values, (size_t)m * A->ld * dtype_size(A->dtype),
+                DCD_TRY(cudaMemcpyAsync(hv, A->values,
+                                        (csr ? (size_t)nnz : (size_t)m * A->ld) * dtype_size(A->dtype),
                                         cudaMemcpyHostToDevice, st));
                 DCD_TRY(cudaMemcpyAsync(yv, y_in, sizeof(double) * m, cudaMemcpyHostToDevice, st));
                 DCD_TRY(cudaMemcpyAsync(av, alpha_in, sizeof(double) * m, cudaMemcpyHostToDevice, st));
@@ -295,15 +347,35 @@ struct Solver {
             }
         }
         const void *vals = host ? h_vals : A->values;
-        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, st));
+        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
         DCD_TRY(cudaMemsetAsync(col_h, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
-        if (tc) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
+        if (tcd) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
 
         // operand
-        if (tc) {
+        if (csr) {
+            const void *v = host ? (const void *)h_vals : A->values;
+            if (conv32) DCD_TRY(launch_f64_to_f32((const double *)v, nnz, (float *)ca.vals32, st));
+            if (conv64)
+                DCD_TRY(launch_pack_rows(v, A->dtype, nnz, 1, nnz, nullptr, (double *)ca.vals64, PACK_F64, nnz, 1,
+                                         err, st));
+            // CSR checks, squared row norms and the longest row (err[2] = bad entries, err[3] = max length)
+            int *bad = err + 2, *maxlen = err + 3;
+            CsrOperand chk = ca;
+            if (!chk.vals64 && !chk.vals32) return DCD_EINTERNAL;
+            DCD_TRY(launch_csr_prep(chk, bad, maxlen, st));
+            int h[2] = {0, 0};
+            DCD_TRY(cudaMemcpyAsync(h, bad, sizeof(h), cudaMemcpyDeviceToHost, st));
+            DCD_TRY(cudaStreamSynchronize(st));
+            if (h[0]) return DCD_EINVAL;
+            const int64_t cap = std::max<int64_t>(1, sb * (int64_t)h[1]);
+            const size_t cmb = csr_colmap_bytes(n, cap);
+            DCD_TRY(cudaMallocAsync(&ws_csr, cmb, st));
+            DCD_TRY(cudaMemsetAsync(ws_csr, 0, cmb, st));
+            cm = csr_colmap_carve(ws_csr, n, cap);
+        } else if (tc) {
             op.n_pad = n_pad;
             op.kind = pack_kind(o.prec);
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st));
@@ -428,7 +500,11 @@ struct Solver {
     }
 
     // gather A_S for the tensor-core path (of the step operand, or of x)
-    cudaError_t gather(int64_t ncols) { return gather_op(ncols, op, As, col_h); }
+    cudaError_t gather(int64_t ncols)
+    {
+        if (csr) return launch_csr_colmap(ca, S, ncols, cm, err, st);
+        return gather_op(ncols, op, As, col_h);
+    }
     cudaError_t gather_op(int64_t ncols, const Operand &x, void *Asx, float *chx)
     {
         if (!tc) return cudaSuccess;
@@ -439,6 +515,9 @@ struct Solver {
 
     cudaError_t gram(int64_t ncols)
     {
+        if (csr)
+            return launch_csr_block(ca, cm, !tc, kp, S, ncols, S, ncols, nullptr, nullptr, nullptr, nullptr, Kss, ldk,
+                                    st);
         if (tc) {
             TcOperand B{As, ncols, op.n_pad, op.kind};
             return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
@@ -453,6 +532,11 @@ struct Solver {
     dcd_status apply_block(int64_t ncols, bool ref = false)
     {
         const double *rs = problem == 0 ? y : nullptr;
+        if (csr) {  // the same CSR block in every case (ref has no other operand)
+            DCD_TRY(gather(ncols));
+            if (tc) DCD_TRY(launch_f64_to_f32(w64, ncols, col_w, st));
+            return cuda_status(csr_apply(ncols, rs));
+        }
         if (tc) {
             const Operand &x = ref ? opr : op;
             void *Asx = ref ? Asr : As;
@@ -482,6 +566,11 @@ struct Solver {
         if (col_w_hi > ncols) e = cudaMemsetAsync(col_w + ncols, 0, sizeof(float) * (col_w_hi - ncols), st);
         col_w_hi = ncols;
         return e;
+    }
+
+    cudaError_t csr_apply(int64_t ncols, const double *rs)
+    {
+        return launch_csr_block(ca, cm, !tc, kp, nullptr, m, S, ncols, col_w, w64, rs, g, nullptr, 0, st);
     }
 
     cudaError_t block_tc_apply(int64_t ncols, const double *rs)
@@ -620,7 +709,9 @@ struct Solver {
         if (tc) DCD_TRY(clear_col_w_tail(ncols));
         tm.stop(stats.ms_recur);
         tm.start();
-        if (tc)
+        if (csr)
+            DCD_TRY(csr_apply(ncols, rs));
+        else if (tc)
             DCD_TRY(block_tc_apply(ncols, rs));
         else
             DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr, 0, err,
@@ -729,7 +820,7 @@ struct Solver {
     double *alpha_host = nullptr;
 };
 
-dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem)
+dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem, bool csr)
 {
     if (!o) return DCD_EINVAL;
     if (o->s < 1 || o->b < 1 || o->max_iters < 0) return DCD_EINVAL;
@@ -739,7 +830,7 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem)
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
     if (o->prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
     if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
-    if (is_tc(o->prec) && !tc_available()) return DCD_EUNSUPPORTED;
+    if (is_tc(o->prec) && !csr && !tc_available()) return DCD_EUNSUPPORTED;  // CSR: CUDA cores
     return DCD_OK;
 }
 
@@ -761,7 +852,7 @@ dcd_status init_svm(Solver &sv, const dcd_matrix *A, const dcd_kernel *k, int32_
     if ((s = validate_kernel(k)) != DCD_OK) return s;
     if (loss != 1 && loss != 2) return DCD_EINVAL;
     if (!finite_pos(C)) return DCD_EINVAL;
-    if ((s = validate_opts(o, A->m, 0)) != DCD_OK) return s;
+    if ((s = validate_opts(o, A->m, 0, A->fmt == DCD_CSR)) != DCD_OK) return s;
     sv.problem = 0;
     sv.A = A;
     sv.kp = to_kp(k);
@@ -782,7 +873,7 @@ dcd_status init_krr(Solver &sv, const dcd_matrix *A, const dcd_kernel *k, double
     if (s != DCD_OK) return s;
     if ((s = validate_kernel(k)) != DCD_OK) return s;
     if (!finite_pos(lambda)) return DCD_EINVAL;
-    if ((s = validate_opts(o, A->m, 1)) != DCD_OK) return s;
+    if ((s = validate_opts(o, A->m, 1, A->fmt == DCD_CSR)) != DCD_OK) return s;
     sv.problem = 1;
     sv.A = A;
     sv.kp = to_kp(k);
@@ -932,7 +1023,7 @@ dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     if ((s = validate_kernel(k)) != DCD_OK) return s;
     if (prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
     if (prec != DCD_PREC_FP64 && !is_tc(prec)) return DCD_EINVAL;
-    if (is_tc(prec) && !tc_available()) return DCD_EUNSUPPORTED;
+    if (is_tc(prec) && A->fmt != DCD_CSR && !tc_available()) return DCD_EUNSUPPORTED;
     return DCD_OK;
 }
 
@@ -946,6 +1037,62 @@ dcd_status finish_component(int *err, cudaStream_t st)
     return he ? DCD_EINTERNAL : DCD_OK;
 }
 
+// The CSR form of component_block: the CUDA-core SpMM block, FP64 in the
+// FP64 mode and FP32 otherwise (device arrays only).
+dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int32_t prec, const int32_t *rows,
+                               int64_t nrows, const int32_t *cols, int64_t ncols, const double *w, const double *rs,
+                               double *g, void *out, int64_t ldo, cudaStream_t st)
+{
+    const bool fp64 = !is_tc(prec);
+    const int64_t m = A->m;
+    int64_t nnz = 0;
+    DCD_TRY(cudaMemcpyAsync(&nnz, A->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    DCD_TRY(cudaStreamSynchronize(st));
+    if (nnz < 0) return DCD_EINVAL;
+    const bool conv32 = !fp64 && A->dtype != DCD_F32, conv64 = fp64 && A->dtype != DCD_F64;
+    ComponentBufs cb, cb2;
+    cb.st = cb2.st = st;
+    size_t cur = 0;
+    const size_t oe = place(cur, 256), ov = place(cur, conv32 ? 4 * (size_t)nnz : conv64 ? 8 * (size_t)nnz : 0);
+    const size_t on32 = place(cur, 4 * (size_t)m), on64 = place(cur, 8 * (size_t)m);
+    const size_t ow = place(cur, (w && !fp64) ? 4 * (size_t)ncols : 0);
+    DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+    char *base = (char *)cb.mem;
+    int *err = (int *)(base + oe);
+    DCD_TRY(cudaMemsetAsync(err, 0, 4 * sizeof(int), st));
+    CsrOperand ca;
+    ca.row_ptr = A->row_ptr;
+    ca.col_idx = A->col_idx;
+    ca.m = m;
+    ca.n = A->n;
+    ca.nnz = nnz;
+    ca.norm32 = (float *)(base + on32);
+    ca.norm64 = (double *)(base + on64);
+    if (fp64) {
+        ca.vals64 = conv64 ? (const double *)(base + ov) : (const double *)A->values;
+        if (conv64)
+            DCD_TRY(launch_pack_rows(A->values, A->dtype, nnz, 1, nnz, nullptr, base + ov, PACK_F64, nnz, 1, err, st));
+    } else {
+        ca.vals32 = conv32 ? (const float *)(base + ov) : (const float *)A->values;
+        if (conv32) DCD_TRY(launch_f64_to_f32((const double *)A->values, nnz, (float *)(base + ov), st));
+    }
+    DCD_TRY(launch_csr_prep(ca, err + 2, err + 3, st));
+    int h[2] = {0, 0};
+    DCD_TRY(cudaMemcpyAsync(h, err + 2, sizeof(h), cudaMemcpyDeviceToHost, st));
+    DCD_TRY(cudaStreamSynchronize(st));
+    if (h[0]) return DCD_EINVAL;
+    const int64_t cap = std::max<int64_t>(1, ncols * (int64_t)h[1]);
+    const size_t cmb = csr_colmap_bytes(A->n, cap);
+    DCD_TRY(cudaMallocAsync(&cb2.mem, cmb, st));
+    DCD_TRY(cudaMemsetAsync(cb2.mem, 0, cmb, st));
+    const CsrColMap cm = csr_colmap_carve(cb2.mem, A->n, cap);
+    DCD_TRY(launch_csr_colmap(ca, cols, ncols, cm, err, st));
+    float *w32 = (w && !fp64) ? (float *)(base + ow) : nullptr;
+    if (w32) DCD_TRY(launch_f64_to_f32(w, ncols, w32, st));
+    DCD_TRY(launch_csr_block(ca, cm, fp64, kp, rows, nrows, cols, ncols, w32, w, rs, g, out, ldo, st));
+    return finish_component(err, st);
+}
+
 // Runs the kernel block on rows `rows` (or the first nrows) against columns
 // `cols`: store into `out` (w == nullptr) or apply into g.
 dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
@@ -953,6 +1100,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
                            double *g, void *out, int64_t ldo, cudaStream_t st)
 {
     const KernelParams kp = to_kp(k);
+    if (A->fmt == DCD_CSR) return component_block_csr(A, kp, prec, rows, nrows, cols, ncols, w, rs, g, out, ldo, st);
     ComponentBufs cb;
     cb.st = st;
     if (!is_tc(prec)) {

@@ -83,6 +83,7 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
                                               const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
                                               void *out, int64_t ldo, void *stream)
 {
+    if (A && A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;  // the CSR block needs allocated scratch
     if (!A || A->fmt != DCD_DENSE || A->m < 1 || A->n < 1 || A->ld < A->n || !A->values || A->m > INT32_MAX)
         return DCD_EINVAL;
     if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
