@@ -368,6 +368,120 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ CSR -----
+WORKLOAD_CSR = ("K-SVM squared hinge DCD, CSR m=200000 n=50000 50 nnz/row U(0,1) rows unit-norm, "
+                "poly (a.b+1)^3, C=0.5, b=1")
+
+
+def csr_cpu_baseline(p, y, s, budget_s=12.0):
+    """The FP64 oracle (s-step DCD, Algorithm 2) on the first m_sub rows, in
+    dense form over the columns those rows touch (the oracle is dense); its
+    per-update cost is linear in rows x columns, so the rate is scaled by
+    (m_sub x n_sub) / (m x n)."""
+    import oracle
+    oracle.build()
+    m_sub = min(p.m, 500)
+    e1 = int(p.row_ptr[m_sub])
+    used, col = np.unique(p.col_idx[:e1], return_inverse=True)
+    D = np.zeros((m_sub, used.size))
+    D[np.repeat(np.arange(m_sub), np.diff(p.row_ptr[:m_sub + 1])), col] = p.values[:e1]
+    k = oracle.kernel("poly", coef0=1.0, degree=3)
+    H = s
+    t0 = time.perf_counter()
+    done = 0
+    alpha = np.zeros(m_sub)
+    while time.perf_counter() - t0 < budget_s and done < 200000:
+        alpha = oracle.sstep_dcd_svm(D, y[:m_sub], k, 2, 0.5, s, H, seed=0, first=done, alpha0=alpha)
+        done += H
+        H = min(4 * H, 4096)
+    dt = time.perf_counter() - t0
+    scale = (m_sub * used.size) / (p.m * p.n)
+    return {"value": done / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} DCD updates (s={s}) on the first {m_sub} rows x their {used.size} columns in dense "
+                      f"form ({dt:.1f} s, plain FP64 C, one thread), rate scaled by rows x columns to the full matrix"}
+
+
+def run_gpu_csr(args):
+    """Config 3: throughput of s-step DCD (squared hinge) on the CSR matrix;
+    the roofline is HBM bandwidth for the CSR block kernel."""
+    import torch
+    from paper_2406_18001_gb300 import binding as B, inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    s = args.s if args.s_set else 32
+    with torch.cuda.stream(stream):
+        p = inputs.sparse_csr(m=args.csr_m, n=args.csr_n, nnz_per_row=args.csr_nnz, seed=rank)
+        A = B.Csr(torch.from_numpy(p.row_ptr).to(dev), torch.from_numpy(p.col_idx).to(dev),
+                  torch.from_numpy(p.values).to(dev), p.n)
+        y = torch.from_numpy(p.y).to(dev)
+        k = B.kernel("poly", coef0=1.0, degree=3)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        H = (args.warmup + args.steps + 8) * s
+        plan = B.Plan(0, A, y, k, 0.5, 1, s, H, seed=rank, prec=args.prec, loss=2)
+        for _ in range(args.warmup):
+            plan.run(1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                plan.enqueue(1)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        st, _ = plan.run(0)
+        launches = st["gpu_launches_per_step"] * args.steps
+        plan.close()
+        plan2 = B.Plan(0, A, y, k, 0.5, 1, s, (args.roof_steps + 4) * s, seed=rank + 1, prec=args.prec, loss=2,
+                       flags=B.FLAG_PHASE_TIMERS)
+        plan2.run(2)
+        base, _ = plan2.run(0)
+        for _ in range(args.roof_steps):
+            flush.zero_()
+            plan2.run(1)
+        st2, _ = plan2.run(0)
+        plan2.close()
+        phase = {ph: (st2[f"ms_{ph}"] - base[f"ms_{ph}"]) / args.roof_steps for ph in
+                 ("sample", "gram", "recur", "block", "update")}
+        nnz = int(p.row_ptr[-1])
+        fp64 = args.prec == "fp64"
+        vb = 8 if fp64 else 4
+        bytes_ = nnz * (4 + vb) + (p.m + 1) * 8 + p.m * (8 + 8 + 8)  # values + columns + offsets + g rw + y
+        hbm_peak, _, _, src = peaks()
+        achieved = bytes_ / (phase["block"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "peak_source": src, "kernel": "csr_block_kernel (CSR kernel block + gradient update)",
+                "algorithmic": {"bytes_per_launch": bytes_, "launch_ms": phase["block"]}}
+        # end to end through the C ABI with host arrays
+        Ah = B.Csr(p.row_ptr, p.col_idx, p.values, p.n)
+        yh = p.y.copy()
+        al_h = np.zeros(p.m)
+        Hh = args.steps * s
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.svm_solve(Ah, yh, k, 2, 0.5, s, Hh, seed=rank, prec=args.prec, alpha=al_h, flags=B.FLAG_HOST_IO,
+                    stream=stream.cuda_stream)
+        dt = time.perf_counter() - t0
+        h2d = p.row_ptr.nbytes + p.col_idx.nbytes + p.values.nbytes + p.y.nbytes + p.m * 8
+        e2e = {"value": Hh / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": 2 * p.m * 8 / args.steps, "steps": args.steps, "wall_s": dt}
+    cpu = None if args.no_cpu else csr_cpu_baseline(p, p.y, s)
+    if rank == 0:
+        value = ws * args.steps * s / (ms * 1e-3)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD_CSR, "m": p.m, "n": p.n, "nnz_per_row": args.csr_nnz, "s": s, "b": 1,
+                          "precision": args.prec + (" (CSR block: FP64)" if fp64 else " (CSR block: FP32 CUDA cores)"),
+                          "l2": "256 MB buffer written before every timed step; steps timed alone"},
+               "phase_ms": phase, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +490,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=512)
-    ap.add_argument("--s", type=int, default=64)
+    ap.add_argument("--s", type=int, default=None)
+    ap.add_argument("--workload", default="krr", choices=["krr", "csr"],
+                    help="krr: dense K-RR BDCD (the headline); csr: sparse K-SVM DCD")
+    ap.add_argument("--csr-m", type=int, default=200000)
+    ap.add_argument("--csr-n", type=int, default=50000)
+    ap.add_argument("--csr-nnz", type=int, default=50)
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
@@ -391,8 +510,13 @@ def main():
     ap.add_argument("--ttt-fp64-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.s_set = args.s is not None
+    if args.s is None:
+        args.s = 64
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "csr":
+        run_gpu_csr(args)
     else:
         run_gpu(args)
 

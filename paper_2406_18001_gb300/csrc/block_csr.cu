@@ -27,10 +27,10 @@ namespace dcd {
 
 namespace {
 
-constexpr int CSR_JC = 32;        // sampled columns per pass
-constexpr int CSR_HL = 256;       // hit-list capacity per warp (flushed when full)
+constexpr int CSR_JC = 32;        // sampled columns per apply pass
+constexpr int CSR_HL = 128;       // hit-list capacity per warp (flushed when full)
 constexpr int CSR_WARPS = 8;      // warps per CTA
-constexpr int CSR_U = 4;          // nonzeros in flight per lane in the scan
+constexpr int CSR_GJ = 256;       // sampled columns per Gram pass
 constexpr int MAP_THREADS = 1024;
 
 template <typename T>
@@ -48,12 +48,21 @@ __device__ __forceinline__ T kfun_t(const KernelParams &kp, T dot, T na, T nb, b
 }
 
 template <typename T>
-struct WarpSmem {
+struct alignas(16) WarpSmem {
     T acc[32][CSR_JC + 1];
-    int32_t hrow[CSR_HL];
+    int32_t hoff[CSR_HL];  // element offset from the tile's first nonzero
     int32_t hslot[CSR_HL];
     T hval[CSR_HL];
-    int64_t rp[33];
+    int32_t rp[33];        // row offsets relative to the tile's first nonzero
+};
+
+constexpr int CSR_SMEM_BITS = 4096;  // bitmap words kept in shared memory (n <= 131072)
+
+template <typename T>
+struct alignas(16) CtaSmem {
+    T nb[CSR_JC], w[CSR_JC];
+    int32_t sj[CSR_JC];
+    uint32_t bits[CSR_SMEM_BITS];
 };
 
 __device__ __forceinline__ bool col_hit(const uint32_t *bits, int32_t c)
@@ -67,13 +76,17 @@ __device__ __forceinline__ int32_t col_slot(const uint32_t *bits, const int32_t 
     return __ldg(wprefix + (c >> 5)) + __popc(w & ((1u << (c & 31)) - 1u));
 }
 
-// Lane r adds the hits of row r (in list order) into acc[r][.].
+// Lane r adds the hits of its row (offsets in [rp[r], rp[r+1]), in list order)
+// into acc[r][.].
 template <typename T>
-__device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrColMap &M, int j0, int jc, int lane)
+__device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrColMap &M, int j0, int jc, int lane,
+                                           int nr)
 {
     __syncwarp();
+    const int lo = lane < nr ? ws.rp[lane] : 0, hi = lane < nr ? ws.rp[lane + 1] : 0;
     for (int h = 0; h < nh; ++h) {
-        if (ws.hrow[h] != lane) continue;
+        const int o = ws.hoff[h];
+        if (o < lo || o >= hi) continue;
         const int slot = ws.hslot[h];
         const T v = ws.hval[h];
         for (int q = M.slot_off[slot]; q < M.slot_off[slot + 1]; ++q) {
@@ -84,107 +97,213 @@ __device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrCol
     __syncwarp();
 }
 
-template <typename T, bool STORE>
+// four consecutive nonzeros from element e: one vector load of each array
+// when the quad lies inside the arrays and they are 16-byte aligned, else
+// element by element (column -1 past the arrays)
+template <typename T>
+__device__ __forceinline__ void load_quad(const CsrOperand &A, const T *vals, int64_t e, int32_t (&c)[4], T (&v)[4])
+{
+    if (A.vec && e + 4 <= A.nnz) {
+        const int4 ci = __ldg((const int4 *)(A.col_idx + e));
+        c[0] = ci.x;
+        c[1] = ci.y;
+        c[2] = ci.z;
+        c[3] = ci.w;
+        if (sizeof(T) == 4) {
+            const float4 vv = __ldg((const float4 *)((const float *)vals + e));
+            v[0] = (T)vv.x;
+            v[1] = (T)vv.y;
+            v[2] = (T)vv.z;
+            v[3] = (T)vv.w;
+        } else {
+            const double2 a = __ldg((const double2 *)((const double *)vals + e));
+            const double2 b = __ldg((const double2 *)((const double *)vals + e + 2));
+            v[0] = (T)a.x;
+            v[1] = (T)a.y;
+            v[2] = (T)b.x;
+            v[3] = (T)b.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = e + q < A.nnz;
+            c[q] = in ? __ldg(A.col_idx + e + q) : -1;
+            v[q] = in ? vals[e + q] : (T)0;
+        }
+    }
+}
+
+// Kernel function of Table 1, the kind fixed at compile time.
+template <typename T, int KIND>
+__device__ __forceinline__ T kfun_k(T dot, T na, T nb, bool same, T gamma, T coef0, int degree)
+{
+    if (KIND == DCD_LINEAR) return dot;
+    if (KIND == DCD_POLY) {
+        const T t = coef0 + dot;
+        T r = t;
+        for (int e = 1; e < degree; ++e) r *= t;
+        return r;
+    }
+    T d2 = same ? (T)0 : na + nb - (T)2 * dot;  // the sample's own row: distance exactly 0
+    d2 = d2 > (T)0 ? d2 : (T)0;
+    return exp(-gamma * d2);
+}
+
+// Apply: one warp per tile of 32 consecutive rows.  The tile's nonzeros are
+// read as quads (lane l: elements 4 l .. 4 l + 3 of a 128-element chunk, two
+// chunks in flight), tested against the column bitmap (shared memory when it
+// fits); hits are listed in element order (warp prefix sum of the per-lane
+// counts) as offsets, so lane r later takes its row's hits by range.
+template <typename T, int KIND, bool SBITS>
 __global__ void __launch_bounds__(CSR_WARPS * 32)
-    csr_block_kernel(CsrOperand A, CsrColMap M, const int32_t *rows, int64_t nrows, const int32_t *S, int j0, int jc,
-                     KernelParams kp, const float *w32, const double *w64, const double *rs, double *g, float *out32,
-                     double *out64, int64_t ldo)
+    csr_block_kernel(CsrOperand A, CsrColMap M, int64_t nrows, const int32_t *S, int j0, int jc, KernelParams kp,
+                     const float *w32, const double *w64, const double *rs, double *g)
 {
     extern __shared__ __align__(16) unsigned char csr_sm[];
+    CtaSmem<T> &cs = *(CtaSmem<T> *)csr_sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<T> &ws = ((WarpSmem<T> *)csr_sm)[warp];
+    WarpSmem<T> &ws = ((WarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>)))[warp];
     const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
     const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
+    for (int j = threadIdx.x; j < jc; j += blockDim.x) {
+        const int32_t sj = S[j0 + j];
+        cs.sj[j] = sj;
+        cs.nb[j] = KIND == DCD_RBF ? norm[sj] : (T)0;
+        cs.w[j] = sizeof(T) == 8 ? (T)w64[j0 + j] : (T)w32[j0 + j];
+    }
+    if (SBITS)
+        for (int w = threadIdx.x; w < M.nw; w += blockDim.x) cs.bits[w] = M.bits[w];
     for (int j = 0; j < CSR_JC; ++j) ws.acc[lane][j] = (T)0;
+    __syncthreads();
+    const uint32_t *bits = SBITS ? cs.bits : M.bits;
+    const T gamma = (T)kp.gamma, coef0 = (T)kp.coef0;
     const int64_t ntiles = (nrows + 31) / 32;
     for (int64_t tile = (int64_t)blockIdx.x * CSR_WARPS + warp; tile < ntiles;
          tile += (int64_t)gridDim.x * CSR_WARPS) {
         const int64_t t0 = tile * 32;
         const int nr = (int)min((int64_t)32, nrows - t0);
+        const int64_t e0 = A.row_ptr[t0];
+        for (int k = lane; k <= nr; k += 32) ws.rp[k] = (int32_t)(A.row_ptr[t0 + k] - e0);
+        __syncwarp();
+        const int n_e = ws.rp[nr];
         int nh = 0;
-        if (!STORE) {
-            // rows t0 .. t0+nr-1 are contiguous: one coalesced pass over their nonzeros
-            for (int k = lane; k <= nr; k += 32) ws.rp[k] = A.row_ptr[t0 + k];
-            __syncwarp();
-            const int64_t e0 = ws.rp[0], e1 = ws.rp[nr];
-            for (int64_t eb = e0; eb < e1; eb += 32 * CSR_U) {
-                int32_t c[CSR_U];
-                T v[CSR_U];
-                bool hit[CSR_U];
+        const int64_t ea = e0 & ~(int64_t)3;  // quad-aligned start; offsets from e0 may be -3 .. -1 there
+        const int lead = (int)(e0 - ea);
+        for (int ob = -lead; ob < n_e; ob += 256) {
+            int32_t c[2][4];
+            T v[2][4];
+            load_quad<T>(A, vals, e0 + ob + 4 * lane, c[0], v[0]);
+            load_quad<T>(A, vals, e0 + ob + 128 + 4 * lane, c[1], v[1]);
 #pragma unroll
-                for (int u = 0; u < CSR_U; ++u) {
-                    const int64_t e = eb + 32 * u + lane;
-                    c[u] = e < e1 ? __ldg(A.col_idx + e) : -1;
-                    v[u] = e < e1 ? vals[e] : (T)0;
-                }
+            for (int h = 0; h < 2; ++h) {
+                const int oq = ob + 128 * h + 4 * lane;  // offset of this lane's quad
+                unsigned mk = 0;
 #pragma unroll
-                for (int u = 0; u < CSR_U; ++u) hit[u] = c[u] >= 0 && col_hit(M.bits, c[u]);
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t cc = c[h][q];
+                    const bool in = oq + q >= 0 && oq + q < n_e && cc >= 0;
+                    if (in && ((SBITS ? bits[cc >> 5] : __ldg(bits + (cc >> 5))) >> (cc & 31)) & 1u) mk |= 1u << q;
+                }
+                if (!__any_sync(0xffffffffu, mk != 0)) continue;
+                // exclusive prefix of the per-lane hit counts = element order
+                const int cnt = __popc(mk);
+                int incl = cnt;
 #pragma unroll
-                for (int u = 0; u < CSR_U; ++u) {
-                    const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
-                    if (nh + __popc(mk) > CSR_HL) {
-                        flush_hits(ws, nh, M, j0, jc, lane);
-                        nh = 0;
-                    }
-                    if (hit[u]) {
-                        const int64_t e = eb + 32 * u + lane;
-                        int lo = 0, hi = nr - 1;  // the row holding element e: last k with rp[k] <= e
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (ws.rp[mid] <= e) lo = mid;
-                            else hi = mid - 1;
-                        }
-                        const int pos = nh + __popc(mk & ((1u << lane) - 1u));
-                        ws.hrow[pos] = lo;
-                        ws.hslot[pos] = col_slot(M.bits, M.wprefix, c[u]);
-                        ws.hval[pos] = v[u];
-                    }
-                    nh += __popc(mk);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
                 }
-            }
-        } else {
-            // listed rows: one row at a time
-            for (int k = 0; k < nr; ++k) {
-                const int64_t r = rows ? (int64_t)rows[t0 + k] : t0 + k;
-                const int64_t e0 = A.row_ptr[r], e1 = A.row_ptr[r + 1];
-                for (int64_t eb = e0; eb < e1; eb += 32) {
-                    const int64_t e = eb + lane;
-                    const int32_t c = e < e1 ? __ldg(A.col_idx + e) : -1;
-                    const bool hit = c >= 0 && col_hit(M.bits, c);
-                    const unsigned mk = __ballot_sync(0xffffffffu, hit);
-                    if (nh + __popc(mk) > CSR_HL) {
-                        flush_hits(ws, nh, M, j0, jc, lane);
-                        nh = 0;
-                    }
-                    if (hit) {
-                        const int pos = nh + __popc(mk & ((1u << lane) - 1u));
-                        ws.hrow[pos] = k;
-                        ws.hslot[pos] = col_slot(M.bits, M.wprefix, c);
-                        ws.hval[pos] = vals[e];
-                    }
-                    nh += __popc(mk);
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (nh + total > CSR_HL) {
+                    flush_hits(ws, nh, M, j0, jc, lane, nr);
+                    nh = 0;
                 }
+                int pos = nh + incl - cnt;
+                while (mk) {
+                    const int q = __ffs(mk) - 1;
+                    mk &= mk - 1;
+                    // the quad's q-th entry without a dynamically indexed array
+                    const int32_t cq = q == 0 ? c[h][0] : q == 1 ? c[h][1] : q == 2 ? c[h][2] : c[h][3];
+                    const T vq = q == 0 ? v[h][0] : q == 1 ? v[h][1] : q == 2 ? v[h][2] : v[h][3];
+                    ws.hoff[pos] = oq + q;
+                    ws.hslot[pos] = col_slot(M.bits, M.wprefix, cq);
+                    ws.hval[pos] = vq;
+                    ++pos;
+                }
+                nh += total;
             }
         }
-        flush_hits(ws, nh, M, j0, jc, lane);
+        flush_hits(ws, nh, M, j0, jc, lane, nr);
         // epilogue: lane r owns row t0 + r
         if (lane < nr) {
-            const int64_t row = (STORE && rows) ? (int64_t)rows[t0 + lane] : t0 + lane;
-            const T na = kp.kind == DCD_RBF ? norm[row] : (T)0;
-            T sum = (T)0;
-            for (int j = 0; j < jc; ++j) {
-                const int32_t sj = S[j0 + j];
-                const T nb = kp.kind == DCD_RBF ? norm[sj] : (T)0;
-                const T kv = kfun_t<T>(kp, ws.acc[lane][j], na, nb, sj == row);
+            const int64_t row = t0 + lane;
+            const T na = KIND == DCD_RBF ? norm[row] : (T)0;
+            T sum0 = (T)0, sum1 = (T)0;
+            int j = 0;
+            for (; j + 1 < jc; j += 2) {
+                const T k0 = kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree);
+                const T k1 =
+                    kfun_k<T, KIND>(ws.acc[lane][j + 1], na, cs.nb[j + 1], cs.sj[j + 1] == row, gamma, coef0, kp.degree);
                 ws.acc[lane][j] = (T)0;
-                if (STORE) {
-                    if (sizeof(T) == 8) out64[(t0 + lane) * ldo + j0 + j] = (double)kv;
-                    else out32[(t0 + lane) * ldo + j0 + j] = (float)kv;
-                } else {
-                    sum += kv * (sizeof(T) == 8 ? (T)w64[j0 + j] : (T)w32[j0 + j]);
-                }
+                ws.acc[lane][j + 1] = (T)0;
+                sum0 = fma(k0, cs.w[j], sum0);
+                sum1 = fma(k1, cs.w[j + 1], sum1);
             }
-            if (!STORE) g[row] += (rs ? rs[row] : 1.0) * (double)sum;
+            if (j < jc) {
+                sum0 = fma(kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree),
+                           cs.w[j], sum0);
+                ws.acc[lane][j] = (T)0;
+            }
+            g[row] += (rs ? rs[row] : 1.0) * (double)(sum0 + sum1);
+        }
+        __syncwarp();
+    }
+}
+
+// Store (the sampled Gram and the component block): one warp per listed row
+// (rows == nullptr: row r), columns S[j0 .. j0 + jc).  The row's hits are
+// taken one at a time in element order and their slot entries (distinct j)
+// spread over the lanes, so every partial dot is summed in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(CSR_WARPS * 32)
+    csr_gram_kernel(CsrOperand A, CsrColMap M, const int32_t *rows, int64_t nrows, const int32_t *S, int j0, int jc,
+                    KernelParams kp, float *out32, double *out64, int64_t ldo)
+{
+    __shared__ T acc[CSR_WARPS][CSR_GJ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
+    for (int64_t k = (int64_t)blockIdx.x * CSR_WARPS + warp; k < nrows; k += (int64_t)gridDim.x * CSR_WARPS) {
+        for (int j = lane; j < jc; j += 32) acc[warp][j] = (T)0;
+        __syncwarp();
+        const int64_t r = rows ? (int64_t)rows[k] : k;
+        const int64_t e0 = A.row_ptr[r], e1 = A.row_ptr[r + 1];
+        for (int64_t eb = e0; eb < e1; eb += 32) {
+            const int64_t e = eb + lane;
+            const int32_t c = e < e1 ? __ldg(A.col_idx + e) : -1;
+            const bool hit = c >= 0 && col_hit(M.bits, c);
+            const int slot = hit ? col_slot(M.bits, M.wprefix, c) : 0;
+            const T v = hit ? vals[e] : (T)0;
+            unsigned mk = __ballot_sync(0xffffffffu, hit);
+            while (mk) {
+                const int src = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const int sl = __shfl_sync(0xffffffffu, slot, src);
+                const T vv = __shfl_sync(0xffffffffu, v, src);
+                for (int q = M.slot_off[sl] + lane; q < M.slot_off[sl + 1]; q += 32) {
+                    const int j = M.ent_j[q] - j0;
+                    if (j >= 0 && j < jc) acc[warp][j] += vv * (T)M.ent_v[q];
+                }
+                __syncwarp();
+            }
+        }
+        const T na = kp.kind == DCD_RBF ? norm[r] : (T)0;
+        for (int j = lane; j < jc; j += 32) {
+            const int32_t sj = S[j0 + j];
+            const T nb = kp.kind == DCD_RBF ? norm[sj] : (T)0;
+            const T kv = kfun_t<T>(kp, acc[warp][j], na, nb, sj == r);
+            if (sizeof(T) == 8) out64[k * ldo + j0 + j] = (double)kv;
+            else out32[k * ldo + j0 + j] = (float)kv;
         }
         __syncwarp();
     }
@@ -316,33 +435,69 @@ __global__ void csr_prep_kernel(CsrOperand A, int *bad, int *maxlen)
     }
 }
 
-template <typename T, bool STORE>
-cudaError_t launch_csr_kernel(const CsrOperand &A, const CsrColMap &M, const int32_t *rows, int64_t nrows,
-                              const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
-                              const double *w64, const double *rs, double *g, float *out32, double *out64,
-                              int64_t ldo, cudaStream_t st)
+int sm_count()
 {
-    auto kfn = csr_block_kernel<T, STORE>;
-    const size_t smem = sizeof(WarpSmem<T>) * CSR_WARPS;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int64_t tiles = (nrows + 31) / 32, per_sm = 2;
+    return sms;
+}
+
+template <typename T, int KIND, bool SBITS>
+cudaError_t launch_csr_apply_k(const CsrOperand &A, const CsrColMap &M, int64_t nrows, const int32_t *S,
+                               int64_t ncols, const KernelParams &kp, const float *w32, const double *w64,
+                               const double *rs, double *g, cudaStream_t st)
+{
+    auto kfn = csr_block_kernel<T, KIND, SBITS>;
+    const size_t smem = sizeof(CtaSmem<T>) + sizeof(WarpSmem<T>) * CSR_WARPS;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t per_sm = (int64_t)(200 * 1024 / smem) > 0 ? (int64_t)(200 * 1024 / smem) : 1;
+    const int64_t tiles = (nrows + 31) / 32;
     int64_t grid = (tiles + CSR_WARPS - 1) / CSR_WARPS;
-    if (grid > (int64_t)sms * per_sm) grid = (int64_t)sms * per_sm;
+    if (grid > sm_count() * per_sm) grid = sm_count() * per_sm;
     for (int64_t j0 = 0; j0 < ncols; j0 += CSR_JC) {
         const int jc = (int)min((int64_t)CSR_JC, ncols - j0);
-        kfn<<<(unsigned)grid, CSR_WARPS * 32, smem, st>>>(A, M, rows, nrows, S, (int)j0, jc, kp, w32, w64, rs, g,
-                                                          out32, out64, ldo);
+        kfn<<<(unsigned)grid, CSR_WARPS * 32, smem, st>>>(A, M, nrows, S, (int)j0, jc, kp, w32, w64, rs, g);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_csr_apply(const CsrOperand &A, const CsrColMap &M, int64_t nrows, const int32_t *S, int64_t ncols,
+                             const KernelParams &kp, const float *w32, const double *w64, const double *rs, double *g,
+                             cudaStream_t st)
+{
+    const bool sb = M.nw <= CSR_SMEM_BITS;
+#define CSR_K(KD)                                                                                    \
+    return sb ? launch_csr_apply_k<T, KD, true>(A, M, nrows, S, ncols, kp, w32, w64, rs, g, st)     \
+              : launch_csr_apply_k<T, KD, false>(A, M, nrows, S, ncols, kp, w32, w64, rs, g, st)
+    if (kp.kind == DCD_RBF) CSR_K(DCD_RBF);
+    if (kp.kind == DCD_POLY) CSR_K(DCD_POLY);
+    CSR_K(DCD_LINEAR);
+#undef CSR_K
+}
+
+template <typename T>
+cudaError_t launch_csr_gram(const CsrOperand &A, const CsrColMap &M, const int32_t *rows, int64_t nrows,
+                            const int32_t *S, int64_t ncols, const KernelParams &kp, float *out32, double *out64,
+                            int64_t ldo, cudaStream_t st)
+{
+    int64_t grid = (nrows + CSR_WARPS - 1) / CSR_WARPS;
+    if (grid > sm_count() * 8) grid = sm_count() * 8;
+    for (int64_t j0 = 0; j0 < ncols; j0 += CSR_GJ) {
+        const int jc = (int)min((int64_t)CSR_GJ, ncols - j0);
+        csr_gram_kernel<T><<<(unsigned)grid, CSR_WARPS * 32, 0, st>>>(A, M, rows, nrows, S, (int)j0, jc, kp, out32,
+                                                                       out64, ldo);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -398,16 +553,16 @@ cudaError_t launch_csr_block(const CsrOperand &A, const CsrColMap &M, bool fp64,
                              const double *w64, const double *rs, double *g, void *out, int64_t ldo, cudaStream_t st)
 {
     if (nrows <= 0 || ncols <= 0) return cudaSuccess;
-    const bool store = out != nullptr;
-    if (fp64)
-        return store ? launch_csr_kernel<double, true>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr,
-                                                        (double *)out, ldo, st)
-                     : launch_csr_kernel<double, false>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr,
-                                                         nullptr, ldo, st);
-    return store ? launch_csr_kernel<float, true>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, (float *)out,
-                                                   nullptr, ldo, st)
-                 : launch_csr_kernel<float, false>(A, M, rows, nrows, S, ncols, kp, w32, w64, rs, g, nullptr, nullptr,
-                                                    ldo, st);
+    if (out) {
+        return fp64 ? launch_csr_gram<double>(A, M, rows, nrows, S, ncols, kp, nullptr, (double *)out, ldo, st)
+                    : launch_csr_gram<float>(A, M, rows, nrows, S, ncols, kp, (float *)out, nullptr, ldo, st);
+    }
+    if (rows) return cudaErrorInvalidValue;  // apply runs over rows 0 .. nrows-1
+    CsrOperand Av = A;
+    const void *vp = fp64 ? (const void *)A.vals64 : (const void *)A.vals32;
+    Av.vec = ((uintptr_t)A.col_idx & 15) == 0 && ((uintptr_t)vp & 15) == 0;
+    return fp64 ? launch_csr_apply<double>(Av, M, nrows, S, ncols, kp, w32, w64, rs, g, st)
+                : launch_csr_apply<float>(Av, M, nrows, S, ncols, kp, w32, w64, rs, g, st);
 }
 
 }  // namespace dcd

@@ -145,6 +145,7 @@ struct CsrOperand {
     int64_t m = 0, n = 0, nnz = 0;
     float *norm32 = nullptr;
     double *norm64 = nullptr;
+    bool vec = false;  // col_idx and the values are 16-byte aligned (set by the launcher)
 };
 // Column map of the sampled rows: bitmap over [0, n), popcount prefix per
 // 32-column word, per-slot entry offsets and (j, value) entries; capacity
