@@ -125,6 +125,7 @@ typedef struct {
     double ms_setup, ms_sample, ms_gram, ms_recur, ms_block, ms_update, ms_check;
     int64_t refreshes;        /* gradient recomputations (DCD_FLAG_REFRESH) */
     double ms_refresh;        /* their device time */
+    int64_t s_used;           /* inner steps per outer step of this solve (batched: the autotuner's) */
 } dcd_stats;
 
 /*
@@ -191,6 +192,56 @@ dcd_status dcd_plan_destroy(dcd_plan *plan);
  * NULL plan or outer_steps < 0, DCD_ECUDA if a launch fails.
  */
 dcd_status dcd_plan_enqueue(dcd_plan *plan, int64_t outer_steps, int64_t *enqueued);
+
+/*
+ * Batched K-RR (many independent s-step BDCD solves, e.g. a sweep over sigma
+ * and lambda or cross-validation folds).  Every problem is a full solve of
+ * its own (its own A, y, kernel, lambda, b, s, budget, seed; the results
+ * equal those of bdcd_krr_solve with the same arguments); the batch runs
+ * them together: one plan per problem spread over `streams` worker streams,
+ * `rounds_per_graph` outer steps of every active problem captured into one
+ * CUDA graph (fork/join over the streams) and replayed, the graph rebuilt
+ * only when the set of active problems or their step lengths change.
+ * Convergence (tol > 0) is checked every check_every rounds for all active
+ * problems with one synchronisation; converged problems leave the graph.
+ * A problem with s <= 0 takes the s the autotuner measures fastest for its
+ * (m, b) (dcd_krr_autotune_s; one measurement per bucket of m within a
+ * factor of 2 and b).  st[i] (may be NULL) receives problem i's statistics.
+ * Returns the first failing problem's status.
+ */
+typedef struct {
+    dcd_matrix A;             /* dense or CSR, device arrays */
+    const double *y;          /* m targets (device) */
+    dcd_kernel k;
+    double lambda;            /* > 0 */
+    int32_t b;                /* block size */
+    int32_t s;                /* inner steps per outer step; <= 0: autotuned */
+    int64_t max_iters;        /* H block updates */
+    uint64_t seed;
+    double *alpha;            /* m (device): alpha_0 in, result out */
+    double *grad;             /* NULL or m (device): gradient out */
+} dcd_krr_problem;
+
+typedef struct {
+    int32_t prec;             /* dcd_precision of every solve */
+    int32_t streams;          /* worker streams (0: 16) */
+    int32_t rounds_per_graph; /* outer steps per problem in one graph replay (0: 8) */
+    int32_t check_every;      /* graph replays between convergence checks (0: only at the end) */
+    double tol;               /* as dcd_opts.tol */
+    int32_t flags;            /* DCD_FLAG_REFRESH, DCD_FLAG_NO_GRAPH */
+    int32_t reserved;
+} dcd_batch_opts;
+
+dcd_status bdcd_krr_solve_batched(const dcd_krr_problem *probs, int32_t count, const dcd_batch_opts *o,
+                                  dcd_stats *st, void *stream);
+
+/*
+ * The autotuner: times a few outer steps of each candidate s in {1, 2, 4,
+ * ..., 128} with s*b <= 8192 on this problem (alpha = 0, a scratch copy) and
+ * returns the fastest per block update in *s_out (ties to the smaller s).
+ */
+dcd_status dcd_krr_autotune_s(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda, int32_t b,
+                              int32_t prec, int32_t *s_out, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *dcd_status_string(int32_t status);

@@ -49,13 +49,25 @@ class Stats(C.Structure):
                 ("dual", C.c_double), ("ms_total", C.c_double), ("ms_setup", C.c_double),
                 ("ms_sample", C.c_double), ("ms_gram", C.c_double), ("ms_recur", C.c_double),
                 ("ms_block", C.c_double), ("ms_update", C.c_double), ("ms_check", C.c_double),
-                ("refreshes", C.c_int64), ("ms_refresh", C.c_double)]
+                ("refreshes", C.c_int64), ("ms_refresh", C.c_double), ("s_used", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
+class KrrProblem(C.Structure):
+    _fields_ = [("A", Matrix), ("y", C.c_void_p), ("k", Kernel), ("lam", C.c_double), ("b", C.c_int32),
+                ("s", C.c_int32), ("max_iters", C.c_int64), ("seed", C.c_uint64), ("alpha", C.c_void_p),
+                ("grad", C.c_void_p)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("streams", C.c_int32), ("rounds_per_graph", C.c_int32),
+                ("check_every", C.c_int32), ("tol", C.c_double), ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "bdcd_krr_solve_batched", "dcd_krr_autotune_s",
+           "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
            "dcd_plan_enqueue", "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
            "dcd_kernel_block_apply", "dcd_kernel_block_static"]
 
@@ -90,6 +102,8 @@ def lib():
             "bdcd_krr_plan_create": (i32, [M, P, K, d, O, P, P, P, C.POINTER(C.c_void_p)]),
             "dcd_plan_run": (i32, [P, i64, S]),
             "dcd_plan_enqueue": (i32, [P, i64, C.POINTER(C.c_int64)]),
+            "bdcd_krr_solve_batched": (i32, [C.POINTER(KrrProblem), i32, C.POINTER(BatchOpts), S, P]),
+            "dcd_krr_autotune_s": (i32, [M, P, K, d, i32, i32, C.POINTER(C.c_int32), P]),
             "dcd_plan_destroy": (i32, [P]),
             "dcd_status_string": (C.c_char_p, [i32]),
             "dcd_sample_indices": (i32, [i32, u64, i64, i32, u64, i64, P, P]),
@@ -342,3 +356,43 @@ def kernel_block_apply(A, k, prec, cols, w, g, rowscale=None):
                                       _ptr(rowscale), _ptr(g), _stream(None))
     _check(rc, "dcd_kernel_block_apply", allow_notconv=False)
     return g
+
+
+def krr_solve_batched(problems, prec="bf16x3", tol=0.0, check_every=0, streams=0, rounds_per_graph=0, flags=0,
+                      stream=None):
+    """Batched K-RR (bdcd_krr_solve_batched).  problems: list of dicts with
+    A (device tensor or Csr), y, k (Kernel), lam, b, s (<= 0: autotuned), H,
+    seed, and optional alpha / grad (device tensors; zeros / fresh if
+    absent).  Returns (alphas, grads, stats list, rc)."""
+    n = len(problems)
+    arr = (KrrProblem * n)()
+    keep = []
+    alphas, grads = [], []
+    for i, p in enumerate(problems):
+        A = p["A"]
+        m = A.shape[0]
+        al = p.get("alpha")
+        if al is None:
+            al = _zeros(m, A)
+        gr = p.get("grad")
+        if gr is None:
+            gr = _empty(m, A)
+        alphas.append(al)
+        grads.append(gr)
+        keep.append((A, p["y"]))
+        arr[i] = KrrProblem(dense_matrix(A), _ptr(p["y"]), p["k"], float(p["lam"]), int(p["b"]), int(p.get("s", 0)),
+                            int(p["H"]), int(p.get("seed", 0)), _ptr(al), _ptr(gr))
+    bo = BatchOpts(_prec(prec), int(streams), int(rounds_per_graph), int(check_every), float(tol), int(flags), 0)
+    st = (Stats * n)()
+    rc = lib().bdcd_krr_solve_batched(arr, n, C.byref(bo), st, _stream(stream))
+    _check(rc, "bdcd_krr_solve_batched")
+    return alphas, grads, [x.as_dict() for x in st], rc
+
+
+def krr_autotune_s(A, y, k, lam, b, prec="bf16x3", stream=None):
+    Am = dense_matrix(A)
+    out = C.c_int32()
+    rc = lib().dcd_krr_autotune_s(C.byref(Am), _ptr(y), C.byref(k), float(lam), int(b), _prec(prec), C.byref(out),
+                                  _stream(stream))
+    _check(rc, "dcd_krr_autotune_s", allow_notconv=False)
+    return int(out.value)

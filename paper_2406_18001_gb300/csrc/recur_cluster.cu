@@ -38,6 +38,9 @@
 #include "dcd_internal.cuh"
 #include "ptx.cuh"
 
+#include <map>
+#include <mutex>
+
 namespace dcd {
 namespace {
 
@@ -614,16 +617,18 @@ int recur_cluster_size(int nblk, int b, int rounds)
     if (b % 4 != 0 || b > 32 || rounds < 1 || rounds > 2 || nblk < 1) return 0;
     const ClGeom G = cl_geom(nblk, b);
     if (G.nsup > CL_NSUP_MAX) return 0;
-    static int cache_P = -1, cache_key[3] = {0, 0, 0};
-    if (cache_key[0] == nblk && cache_key[1] == b && cache_key[2] == rounds) return cache_P;
+    // one occupancy query per shape (a map: batched solves mix shapes)
+    static std::mutex mu;
+    static std::map<long long, int> cache;
+    const long long key = ((long long)nblk << 20) | ((long long)b << 4) | rounds;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
     const int P = cluster_ctas(G.nsup);
     const size_t smem = cluster_smem(nblk, b, P);
     const bool ok = smem <= CL_SMEM_MAX && cluster_fits(P, smem);
-    cache_key[0] = nblk;
-    cache_key[1] = b;
-    cache_key[2] = rounds;
-    cache_P = ok ? P : 0;
-    return cache_P;
+    cache[key] = ok ? P : 0;
+    return ok ? P : 0;
 }
 
 size_t recur_cluster_scratch_bytes(int64_t nblk, int b)

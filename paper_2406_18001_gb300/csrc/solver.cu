@@ -19,6 +19,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <vector>
 
 namespace dcd {
@@ -583,10 +585,23 @@ struct Solver {
     // Convergence measure from the cached gradient (reads back 4 doubles).
     dcd_status measure(double &metric, double &primal, double &dual, double ynorm2)
     {
-        DCD_TRY(launch_check(problem, g, alpha, y, m, C, loss, partials, result, st));
         double r[4];
-        DCD_TRY(cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, st));
+        DCD_TRY(measure_enqueue(r));
         DCD_TRY(cudaStreamSynchronize(st));
+        measure_finish(r, metric, primal, dual, ynorm2);
+        return DCD_OK;
+    }
+
+    // the two halves of measure, for checks of many solves with one synchronisation
+    cudaError_t measure_enqueue(double *r4)
+    {
+        cudaError_t e = launch_check(problem, g, alpha, y, m, C, loss, partials, result, st);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(r4, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+
+    void measure_finish(const double *r, double &metric, double &primal, double &dual, double ynorm2) const
+    {
         if (problem == 1) {
             metric = std::sqrt(r[0]) / std::sqrt(ynorm2 > 0 ? ynorm2 : 1.0);
             primal = dual = 0.0;
@@ -596,7 +611,6 @@ struct Solver {
             dual = r[1] - 0.5 * r[0] - (loss == 2 ? r[2] / (4.0 * C) : 0.0);
             metric = (primal - dual) / std::max(std::fabs(primal), 1e-300);
         }
-        return DCD_OK;
     }
 
     // ---- outer-step loop, resumable (the plan API runs it in pieces) ----
@@ -620,6 +634,7 @@ struct Solver {
         // full step has been captured; the recurrence is taken as the
         // cluster (K-RR) or single-warp (K-SVM) form until then
         stats.gpu_launches_per_step = (tc ? 3 : 1) + 1 + (problem == 0 ? 1 : 2) + 2;
+        stats.s_used = o.s;
         return DCD_OK;
     }
 
@@ -1178,4 +1193,279 @@ extern "C" dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kern
     if (ncols < 0 || (ncols > 0 && (!cols || !w)) || !g) return DCD_EINVAL;
     if (ncols == 0) return DCD_OK;
     return component_block(A, k, prec, nullptr, A->m, cols, ncols, w, rowscale, g, nullptr, 0, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------- batched --
+namespace dcd {
+namespace {
+
+struct StreamSet {
+    std::vector<cudaStream_t> s;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t fork = nullptr;
+    ~StreamSet()
+    {
+        for (auto x : s) cudaStreamDestroy(x);
+        for (auto e : ev) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
+    cudaError_t create(int n)
+    {
+        s.resize(n, nullptr);
+        ev.resize(n, nullptr);
+        for (int i = 0; i < n; ++i) {
+            cudaError_t e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+            e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    }
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+// Device time per block update of s-step BDCD with this s (a few outer
+// steps after a warm-up one; alpha starts at 0 in scratch arrays).
+dcd_status time_per_update(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda, int b, int s,
+                           int prec, double *alpha, double *grad, cudaStream_t st, double &ms_per)
+{
+    const int warm = 2, timed = 3;  // warm-up: one direct step and the step that is captured
+    dcd_opts o{};
+    o.s = s;
+    o.b = b;
+    o.max_iters = (int64_t)(warm + timed) * s;
+    o.prec = prec;
+    DCD_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * A->m, st));
+    Solver sv;
+    dcd_status r = init_krr(sv, A, k, lambda, &o, st);
+    if (r == DCD_OK) r = prepare(sv, y, alpha, grad);
+    if (r != DCD_OK) return r;
+    dcd_stats a{}, c{};
+    if ((r = sv.run_steps(warm, &a)) != DCD_OK) return r;
+    if ((r = sv.run_steps(timed, &c)) != DCD_OK) return r;
+    ms_per = (c.ms_total - a.ms_total) / ((double)timed * s);
+    return DCD_OK;
+}
+
+}  // namespace
+}  // namespace dcd
+
+extern "C" dcd_status dcd_krr_autotune_s(const dcd_matrix *A, const double *y, const dcd_kernel *k, double lambda,
+                                         int32_t b, int32_t prec, int32_t *s_out, void *stream)
+{
+    using namespace dcd;
+    if (!A || !y || !k || !s_out || b < 1 || b > B_MAX || b > A->m) return DCD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf buf;
+    buf.st = st;
+    DCD_TRY(cudaMallocAsync(&buf.p, 2 * sizeof(double) * A->m, st));
+    double *alpha = (double *)buf.p, *grad = alpha + A->m;
+    double best = 1e300;
+    int best_s = 1;
+    for (int s = 1; s <= 128 && (int64_t)s * b <= SB_MAX; s *= 2) {
+        double ms = 0.0;
+        const dcd_status r = time_per_update(A, y, k, lambda, b, s, prec, alpha, grad, st, ms);
+        if (r != DCD_OK) return r;
+        if (ms < best * 0.98) {  // a larger s must win by more than the timing noise
+            best = ms;
+            best_s = s;
+        }
+    }
+    *s_out = best_s;
+    return DCD_OK;
+}
+
+extern "C" dcd_status bdcd_krr_solve_batched(const dcd_krr_problem *probs, int32_t count, const dcd_batch_opts *bo,
+                                             dcd_stats *st_out, void *stream)
+{
+    using namespace dcd;
+    if (!probs || !bo || count < 0) return DCD_EINVAL;
+    if (count == 0) return DCD_OK;
+    if (!(std::isfinite(bo->tol) && bo->tol >= 0.0) || bo->check_every < 0 || bo->streams < 0 ||
+        bo->rounds_per_graph < 0)
+        return DCD_EINVAL;
+    cudaStream_t main = (cudaStream_t)stream;
+    const int nstreams = bo->streams > 0 ? std::min(bo->streams, 64) : 16;
+    const int R = bo->rounds_per_graph > 0 ? bo->rounds_per_graph : 8;
+    StreamSet ss;
+    DCD_TRY(ss.create(nstreams));
+
+    // s per problem: given, or the autotuner's per (m bucket, b)
+    std::vector<int> s_of(count);
+    std::map<std::pair<int, int>, int> tuned;
+    for (int i = 0; i < count; ++i) {
+        if (probs[i].s > 0) {
+            s_of[i] = probs[i].s;
+            continue;
+        }
+        int bucket = 0;
+        while ((2LL << bucket) <= probs[i].A.m) ++bucket;
+        const auto key = std::make_pair(bucket, (int)probs[i].b);
+        auto it = tuned.find(key);
+        if (it == tuned.end()) {
+            int32_t s = 1;
+            const dcd_status r = dcd_krr_autotune_s(&probs[i].A, probs[i].y, &probs[i].k, probs[i].lambda,
+                                                    probs[i].b, bo->prec, &s, ss.s[0]);
+            if (r != DCD_OK) return r;
+            it = tuned.emplace(key, s).first;
+        }
+        s_of[i] = it->second;
+    }
+
+    // one plan per problem, round-robin over the worker streams
+    std::vector<std::unique_ptr<dcd_plan>> plans(count);
+    for (int i = 0; i < count; ++i) {
+        dcd_opts o{};
+        o.s = s_of[i];
+        o.b = probs[i].b;
+        o.max_iters = probs[i].max_iters;
+        o.seed = probs[i].seed;
+        o.tol = bo->tol;
+        o.prec = bo->prec;
+        o.flags = bo->flags & (DCD_FLAG_REFRESH | DCD_FLAG_NO_GRAPH);
+        dcd_plan *p = nullptr;
+        const dcd_status r = bdcd_krr_plan_create(&probs[i].A, probs[i].y, &probs[i].k, probs[i].lambda, &o,
+                                                  probs[i].alpha, probs[i].grad, ss.s[i % nstreams], &p);
+        if (r != DCD_OK) return r;
+        plans[i].reset(p);
+    }
+    // a first direct step per problem sets every kernel attribute and cached
+    // launch shape before any capture
+    std::vector<char> active(count, 1);
+    EventTimer off;
+    off.init(false, nullptr);
+    for (int i = 0; i < count; ++i) {
+        Solver &sv = plans[i]->sv;
+        dcd_status r = sv.begin();
+        if (r != DCD_OK) return r;
+        if (sv.finished()) {
+            active[i] = 0;
+            continue;
+        }
+        const int64_t cnt = std::min<int64_t>(sv.o.s, sv.o.max_iters - sv.done);
+        if ((r = sv.enqueue_step(cnt, off)) != DCD_OK) return r;
+        sv.done += cnt;
+        ++sv.steps;
+    }
+    for (auto x : ss.s) DCD_TRY(cudaStreamSynchronize(x));
+
+    // pinned buffer for the batched convergence checks
+    double *hres = nullptr;
+    DCD_TRY(cudaMallocHost(&hres, sizeof(double) * 4 * count));
+    struct HostFree {
+        double *p;
+        ~HostFree() { cudaFreeHost(p); }
+    } hf{hres};
+
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphFree {
+        cudaGraphExec_t *g;
+        ~GraphFree()
+        {
+            if (*g) cudaGraphExecDestroy(*g);
+        }
+    } gf{&gexec};
+    std::vector<int> rounds_in_graph(count, 0);
+    bool dirty = true;
+    const bool use_graph = !(bo->flags & DCD_FLAG_NO_GRAPH) && main != nullptr && main != cudaStreamLegacy &&
+                           main != cudaStreamPerThread;
+    int64_t replays = 0;
+    for (;;) {
+        // full outer steps each active problem can take in this replay
+        bool any = false;
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            Solver &sv = plans[i]->sv;
+            const int64_t full = (sv.o.max_iters - sv.done) / sv.o.s;
+            const int r = (int)std::min<int64_t>(R, full);
+            if (r != rounds_in_graph[i]) dirty = true;
+            rounds_in_graph[i] = r;
+            any = any || r > 0;
+        }
+        if (!any) break;
+        if (use_graph) {
+            if (dirty) {
+                if (gexec) {
+                    cudaGraphExecDestroy(gexec);
+                    gexec = nullptr;
+                }
+                DCD_TRY(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaEventRecord(ss.fork, main);
+                for (int k = 0; k < nstreams && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(ss.s[k], ss.fork, 0);
+                dcd_status r = ce == cudaSuccess ? DCD_OK : DCD_ECUDA;
+                for (int rr = 0; rr < R && r == DCD_OK; ++rr)
+                    for (int i = 0; i < count && r == DCD_OK; ++i)
+                        if (active[i] && rr < rounds_in_graph[i]) r = plans[i]->sv.enqueue_step(plans[i]->sv.o.s, off);
+                for (int k = 0; k < nstreams && ce == cudaSuccess; ++k) {
+                    ce = cudaEventRecord(ss.ev[k], ss.s[k]);
+                    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(main, ss.ev[k], 0);
+                }
+                cudaGraph_t graph = nullptr;
+                const cudaError_t ee = cudaStreamEndCapture(main, &graph);
+                const bool ok = r == DCD_OK && ce == cudaSuccess && ee == cudaSuccess && graph &&
+                                cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+                if (graph) cudaGraphDestroy(graph);
+                if (!ok) {
+                    cudaGetLastError();
+                    return r != DCD_OK ? r : DCD_ECUDA;
+                }
+                dirty = false;
+            }
+            DCD_TRY(cudaGraphLaunch(gexec, main));
+        } else {
+            for (int rr = 0; rr < R; ++rr)
+                for (int i = 0; i < count; ++i)
+                    if (active[i] && rr < rounds_in_graph[i]) {
+                        const dcd_status r = plans[i]->sv.enqueue_step(plans[i]->sv.o.s, off);
+                        if (r != DCD_OK) return r;
+                    }
+        }
+        for (int i = 0; i < count; ++i)
+            if (active[i]) {
+                plans[i]->sv.done += (int64_t)rounds_in_graph[i] * plans[i]->sv.o.s;
+                plans[i]->sv.steps += rounds_in_graph[i];
+            }
+        ++replays;
+        // convergence of every active problem, one synchronisation
+        if (bo->tol > 0 && bo->check_every > 0 && replays % bo->check_every == 0) {
+            if (use_graph) DCD_TRY(cudaStreamSynchronize(main));
+            for (int i = 0; i < count; ++i)
+                if (active[i]) DCD_TRY(plans[i]->sv.measure_enqueue(hres + 4 * i));
+            for (auto x : ss.s) DCD_TRY(cudaStreamSynchronize(x));
+            for (int i = 0; i < count; ++i) {
+                if (!active[i]) continue;
+                Solver &sv = plans[i]->sv;
+                sv.measure_finish(hres + 4 * i, sv.metric, sv.primal, sv.dual, sv.ynorm2);
+                if (sv.metric <= bo->tol) {
+                    // confirmed (on a recomputed gradient with DCD_FLAG_REFRESH) by the solver's own test
+                    const dcd_status r = sv.check_converged();
+                    if (r != DCD_OK) return r;
+                    if (sv.conv) {
+                        active[i] = 0;
+                        dirty = true;
+                    }
+                }
+            }
+        }
+    }
+    if (use_graph) DCD_TRY(cudaStreamSynchronize(main));
+    // the last, shorter outer steps, then each problem's final measure, publish and statistics
+    dcd_status first_err = DCD_OK;
+    for (int i = 0; i < count; ++i) {
+        dcd_stats st{};
+        const dcd_status r = dcd_plan_run(plans[i].get(), -1, &st);
+        if (st_out) st_out[i] = st;
+        if (r != DCD_OK && r != DCD_ENOTCONV && first_err == DCD_OK) first_err = r;
+        if (r == DCD_ENOTCONV && first_err == DCD_OK) first_err = r;
+    }
+    for (auto x : ss.s) DCD_TRY(cudaStreamSynchronize(x));
+    return first_err;
 }

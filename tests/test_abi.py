@@ -56,6 +56,12 @@ int main(void) {
   printf("dcd_stats %zu\n", sizeof(dcd_stats));
   F(dcd_matrix, values); F(dcd_matrix, row_scale); F(dcd_kernel, gamma); F(dcd_kernel, coef0);
   F(dcd_opts, seed); F(dcd_opts, tol); F(dcd_opts, flags); F(dcd_stats, final_metric); F(dcd_stats, ms_check);
+  F(dcd_stats, refreshes); F(dcd_stats, s_used);
+  printf("dcd_krr_problem %zu\n", sizeof(dcd_krr_problem));
+  printf("dcd_batch_opts %zu\n", sizeof(dcd_batch_opts));
+  F(dcd_krr_problem, y); F(dcd_krr_problem, k); F(dcd_krr_problem, lambda); F(dcd_krr_problem, b);
+  F(dcd_krr_problem, max_iters); F(dcd_krr_problem, alpha); F(dcd_krr_problem, grad);
+  F(dcd_batch_opts, tol); F(dcd_batch_opts, flags);
   return 0;
 }
 """
@@ -82,6 +88,15 @@ def test_ctypes_layout_matches_header(tmp_path):
     assert int(got["dcd_opts.flags"]) == b.Opts.flags.offset
     assert int(got["dcd_stats.final_metric"]) == b.Stats.final_metric.offset
     assert int(got["dcd_stats.ms_check"]) == b.Stats.ms_check.offset
+    assert int(got["dcd_stats.refreshes"]) == b.Stats.refreshes.offset
+    assert int(got["dcd_stats.s_used"]) == b.Stats.s_used.offset
+    assert int(got["dcd_krr_problem"]) == C.sizeof(b.KrrProblem)
+    assert int(got["dcd_batch_opts"]) == C.sizeof(b.BatchOpts)
+    for f, cf in (("y", "y"), ("k", "k"), ("lambda", "lam"), ("b", "b"), ("max_iters", "max_iters"),
+                  ("alpha", "alpha"), ("grad", "grad")):
+        assert int(got[f"dcd_krr_problem.{f}"]) == getattr(b.KrrProblem, cf).offset
+    assert int(got["dcd_batch_opts.tol"]) == b.BatchOpts.tol.offset
+    assert int(got["dcd_batch_opts.flags"]) == b.BatchOpts.flags.offset
 
 
 def test_host_validation_rejects_bad_arguments_without_gpu():
