@@ -18,6 +18,9 @@ Parity status per routine (pins live in tests/test_oracle_pins.py):
   sstep_bdcd_krr (Alg. 4)      pinned: equals Alg. 3 iterates (paper Sec. 3.4)
   svm_objectives / gradients   pinned: linear-kernel primal from w = A^T(y*alpha)
   krr_closed_form              pinned: numpy.linalg.solve
+  e4m3_* / quantize_e4m3_rows  pinned: all 256 codes of the format, rounding
+                               special cases, torch.float8_e4m3fn conversion,
+                               half-ulp error bound, row maxima at +-448
 """
 from __future__ import annotations
 
@@ -229,3 +232,58 @@ def krr_closed_form(A, y, k, lam) -> np.ndarray:
     al = np.empty(m)
     _check(_load().orc_krr_closed_form(_ptr(A), m, n, n, _ptr(y), _K(k), lam, _ptr(al)), "krr_closed_form")
     return al
+
+
+# ------------------------------------------------------- FP8 storage ---
+# The stress configuration stores A as FP8 e4m3 with one FP32 scale per row,
+# a_i ~ s_i q_i (the precision pattern of the method's mixed form; the paper
+# itself computes in FP64).  e4m3 is the OCP 8-bit format: sign, 4 exponent
+# bits (bias 7), 3 mantissa bits, subnormals, no infinities, largest finite
+# value 448, code 0x7f / 0xff NaN.
+E4M3_MAX = 448.0
+
+
+def e4m3_value(code) -> np.ndarray:
+    """The value of e4m3 codes (uint8), from the format definition."""
+    c = np.asarray(code, dtype=np.uint8).astype(np.int64)
+    e, f = (c >> 3) & 15, c & 7
+    v = np.where(e == 0, f * 2.0 ** -9, (8 + f) * 2.0 ** (e - 10))
+    v = np.where((c & 0x7F) == 0x7F, np.nan, v)
+    return np.where(c & 0x80, -v, v)
+
+
+def e4m3_encode(x) -> np.ndarray:
+    """Nearest e4m3 code of each value (ties to the even code), saturating at
+    +-448; x is exact in FP64 (an FP32 value).  Values that round to zero keep
+    their sign (code 0x80 for negatives)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(a)                      # a = f * 2^ex, f in [0.5, 1)
+    ulp = np.exp2(np.maximum(ex - 1, -6) - 3)  # spacing in the binade; 2^-9 below 2^-6
+    r = np.minimum(np.round(a / ulp) * ulp, E4M3_MAX)  # np.round: half to even
+    # r is now an e4m3 magnitude: recover its code
+    _, er = np.frexp(r)
+    e = np.where(r >= 2.0 ** -6, er - 1 + 7, 0)
+    f = np.where(e == 0, r / 2.0 ** -9, r / np.exp2(e - 7) - 1.0) * np.where(e == 0, 1.0, 8.0)
+    code = (e.astype(np.int64) << 3) | f.astype(np.int64)
+    return (code | np.where(np.signbit(x), 0x80, 0)).astype(np.uint8)  # -0 keeps its sign
+
+
+def quantize_e4m3_rows(A):
+    """Per-row FP8 storage of A: each row is rounded to FP32, s_i =
+    fl32(max_k |a_ik| / 448) and q_ik = e4m3(fl32(a_ik / s_i)) with FP32
+    division; a row of zeros gets s_i = 0 and q = 0.  Returns (codes uint8
+    m x n, scales float32 m)."""
+    A32 = np.asarray(A).astype(np.float32)
+    amax = np.max(np.abs(A32), axis=1) if A32.shape[1] else np.zeros(A32.shape[0], np.float32)
+    s = (amax / np.float32(E4M3_MAX)).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1.0)).astype(np.float32)
+    x = (A32 / safe[:, None]).astype(np.float32)
+    q = e4m3_encode(x)
+    q[s == 0] = 0
+    return q, s
+
+
+def dequantize_e4m3_rows(codes, scales) -> np.ndarray:
+    """a_ik = s_i * value(q_ik) in FP64 (exact: 4 x 24 significant bits)."""
+    return np.asarray(scales, np.float64)[:, None] * e4m3_value(codes)

@@ -321,3 +321,60 @@ def test_krr_gradient_and_objective():
     assert rel(oracle.krr_gradient(p.A, p.y, k, lam, a), M @ a - p.y) < 1e-13
     f = 0.5 * a @ M @ a - p.y @ a
     assert abs(oracle.krr_objective(p.A, p.y, k, lam, a) - f) < 1e-12 * abs(f)
+
+
+# ------------------------------------------------- FP8 e4m3 row storage ---
+def test_e4m3_values_of_the_format():
+    v = oracle.e4m3_value(np.arange(256, dtype=np.uint8))
+    assert v[0x7E] == 448.0 and v[0x01] == 2.0 ** -9 and v[0x08] == 2.0 ** -6 and v[0x38] == 1.0
+    assert v[0x07] == 7 * 2.0 ** -9 and v[0x0F] == 1.875 * 2.0 ** -6  # largest subnormal / normal of binade -6
+    assert np.isnan(v[0x7F]) and np.isnan(v[0xFF]) and np.all(v[0x80:0xFF] == -v[0:0x7F])
+    finite = v[:0x7F]
+    assert np.all(np.diff(finite) > 0)  # codes 0..0x7e are increasing magnitudes
+    c = np.arange(256, dtype=np.uint8)[~np.isnan(v)]
+    assert np.array_equal(oracle.e4m3_encode(oracle.e4m3_value(c)), c)
+
+
+def test_e4m3_rounding_special_cases():
+    x = np.array([17.0, 19.0, 2.0 ** -10, 3 * 2.0 ** -10, 464.0, 1e30, -1e30, -2.0 ** -11, 0.0, 240.0 + 8.0])
+    want = [16.0, 20.0, 0.0, 2 * 2.0 ** -9, 448.0, 448.0, -448.0, -0.0, 0.0, 256.0]
+    got = oracle.e4m3_value(oracle.e4m3_encode(x))
+    assert np.array_equal(got, want) and np.signbit(got[7])
+
+
+def test_e4m3_encode_matches_torch_float8():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    g = np.random.default_rng(0)
+    v = oracle.e4m3_value(np.arange(127, dtype=np.uint8))
+    x = np.concatenate([g.uniform(-448, 448, 20000), g.uniform(-0.03, 0.03, 20000), g.standard_normal(20000),
+                        (v[1:126] + v[2:127]) / 2, -(v[1:126] + v[:125]) / 2]).astype(np.float32)
+    t = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(t, oracle.e4m3_encode(x.astype(np.float64)))
+
+
+def test_quantize_rows_scale_range_and_error_bound():
+    g = np.random.default_rng(1)
+    A = g.standard_normal((64, 45)) * np.exp(g.uniform(-8, 8, (64, 1)))
+    A[5] = 0.0
+    A[9, :] = 0.0
+    A[9, 3] = -2.5
+    q, s = oracle.quantize_e4m3_rows(A)
+    assert q.dtype == np.uint8 and s.dtype == np.float32
+    A32 = A.astype(np.float32).astype(np.float64)
+    amax = np.max(np.abs(A32), axis=1)
+    from fractions import Fraction
+    for si, ai in zip(s, amax):  # s_i is amax_i / 448 correctly rounded to FP32
+        half_ulp = Fraction(float(np.spacing(si))) / 2
+        assert abs(Fraction(float(si)) - Fraction(float(ai)) / 448) <= half_ulp
+    assert s[5] == 0 and np.all(q[5] == 0)
+    qv = oracle.e4m3_value(q)
+    nz = amax > 0
+    assert np.all(np.max(np.abs(qv[nz]), axis=1) == 448.0)  # each row's largest entry maps to +-448
+    assert q[9, 3] == 0xFE and np.all(q[9, np.arange(45) != 3] == 0)
+    D = oracle.dequantize_e4m3_rows(q, s)
+    x = np.abs(A32 / np.where(s > 0, s, 1)[:, None])
+    # half a unit in the last place: 2^-4 relative for normals, 2^-10 absolute (in units of s) below 2^-6
+    bound = np.where(x >= 2.0 ** -6, 2.0 ** -4 * np.abs(A32), 2.0 ** -10 * s[:, None].astype(np.float64))
+    assert np.all(np.abs(D - A32) <= bound * (1 + 1e-6))
