@@ -302,15 +302,17 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     t_block = phase["block"] * 1e-3
     hbm_peak, bf16_peak, bf16_sus, src = peaks()
     sb = args.s * args.b
-    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "fp64": 8}[args.prec]
-    mma_mult = 3 if args.prec == "bf16x3" else 1  # MMAs per k-step
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
+    mma_mult = 3 if args.prec in ("bf16x3", "tf32x3") else 1  # MMAs per k-step
     n_alg = args.n
     flops = 2.0 * args.m * n_alg * sb * mma_mult
     bytes_ = args.m * n_alg * esz + sb * n_alg * esz + args.m * (8 + 8 + 4)
     intensity = flops / bytes_
     ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
-    if args.prec in ("bf16", "bf16x3") and intensity >= ridge:
-        roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
+    # a contraction's peak is its own dtype's: the measured bf16 figure times the nominal ratio
+    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}.get(args.prec, 0.0) * bf16_peak
+    if tc_peak and intensity >= ridge:
+        roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
     else:
         roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -482,6 +484,172 @@ def run_gpu_csr(args):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ FP8 stress -----
+WORKLOAD_FP8 = ("K-RR precision stress: m=400000, n=2048 dense, A = Z diag(sig) W^T (sig log-spaced, cond 1e4, "
+                "E||a||^2 = 64) stored BF16 and as FP8 e4m3 with per-row scales, y = sin(A w) + 0.1 N(0,1), "
+                "RBF sigma=8, lambda=1e-6, b=32, s=128")
+
+
+def _fp8_arm(B, torch, A, y, k, lam, b, s, prec, args, stream, flush, seed):
+    """Throughput of one storage / precision arm: K timed outer steps, then
+    the per-phase device times from a second plan with phase timers."""
+    H = (args.warmup + args.steps + 4) * s
+    plan = B.Plan(1, A, y, k, lam, b, s, H, seed=seed, prec=prec)
+    for _ in range(args.warmup):
+        plan.run(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.enqueue(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    st, _ = plan.run(0)
+    plan.close()
+    nroof = max(3, min(args.roof_steps, 10))
+    plan2 = B.Plan(1, A, y, k, lam, b, s, (nroof + 3) * s, seed=seed + 1, prec=prec, flags=B.FLAG_PHASE_TIMERS)
+    plan2.run(1)
+    base, _ = plan2.run(0)
+    for _ in range(nroof):
+        flush.zero_()
+        plan2.run(1)
+    st2, _ = plan2.run(0)
+    plan2.close()
+    phase = {ph: (st2[f"ms_{ph}"] - base[f"ms_{ph}"]) / nroof for ph in ("sample", "gram", "recur", "block", "update")}
+    return ms, st["gpu_launches_per_step"] * args.steps, phase
+
+
+def run_gpu_fp8(args):
+    """Config 5: the K-RR stress configuration.  Throughput of FP8 storage
+    (kind::f8f6f4 block) and BF16 storage (kind::f16 block) at m = 400000,
+    n = 2048, b = 32, s = 128; alpha error on rows 0..19999 against the FP64
+    oracle (same index stream, fixed H) and against the FP64 GPU path."""
+    import torch
+    from paper_2406_18001_gb300 import binding as B, inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    m, n, b = args.fp8_m, args.fp8_n, 32
+    s = args.s if args.s_set else 128
+    gam, lam = 1.0 / 128, 1e-6
+    k = B.kernel("rbf", gamma=gam)
+    with torch.cuda.stream(stream):
+        # the stored matrices, generated on the device from the seeded recipe
+        mix = torch.from_numpy(inputs.ill_conditioned_mixer(n, seed=rank)).to(dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5000 + rank)
+        w = torch.randn(n, generator=gen, device=dev, dtype=torch.float32) / 8.0  # A w ~ N(0, 1)
+        A16 = torch.empty((m, n), dtype=torch.bfloat16, device=dev)
+        y = torch.empty(m, dtype=torch.float64, device=dev)
+        for r0 in range(0, m, 65536):
+            r1 = min(m, r0 + 65536)
+            Z = torch.randn((r1 - r0, n), generator=gen, device=dev, dtype=torch.float32)
+            A16[r0:r1] = (Z @ mix).to(torch.bfloat16)
+            y[r0:r1] = torch.sin(A16[r0:r1].float() @ w).double() + 0.1 * torch.randn(
+                r1 - r0, generator=gen, device=dev, dtype=torch.float64)
+        del Z
+        F = B.quantize_e4m3(A16, stream=stream.cuda_stream)  # FP8 storage of the BF16 matrix
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ms8, launches, ph8 = _fp8_arm(B, torch, F, y, k, lam, b, s, "fp8", args, stream, flush, rank)
+        ms16, _, ph16 = _fp8_arm(B, torch, A16, y, k, lam, b, s, "bf16", args, stream, flush, rank)
+
+        # end to end through the C ABI with host buffers (FP8 codes, scales, y)
+        q_h = F.codes.cpu().pin_memory()
+        sc_h = F.scale.cpu().pin_memory()
+        y_h = y.cpu().pin_memory()
+        al_h = torch.zeros(m, dtype=torch.float64).pin_memory()
+        gr_h = torch.zeros(m, dtype=torch.float64).pin_memory()
+        Hh = args.steps * s
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.krr_solve(B.Fp8(q_h.numpy(), sc_h.numpy()), y_h.numpy(), k, lam, b, s, Hh, seed=rank, prec="fp8",
+                    alpha=al_h.numpy(), grad=gr_h.numpy(), flags=B.FLAG_HOST_IO, stream=stream.cuda_stream)
+        dt = time.perf_counter() - t0
+        e2e = {"value": Hh * b / dt, "unit": UNIT, "h2d_bytes_per_step": (m * n + 4 * m + 16 * m) / args.steps,
+               "d2h_bytes_per_step": 16 * m / args.steps, "steps": args.steps, "wall_s": dt}
+        del q_h, sc_h
+
+        # alpha error on the 20000-row subproblem (rows 0..19999 of the stored matrix)
+        msub = min(m, args.fp8_sub)
+        Asub16 = A16[:msub].contiguous()
+        ysub = y[:msub].contiguous()
+        Fsub = B.quantize_e4m3(Asub16, stream=stream.cuda_stream)
+        Hs = args.fp8_oracle_blocks
+        Hl = args.fp8_long_steps * s
+        err = {}
+        ref_long = {}
+        for tag, Am, prec in (("fp64_on_bf16", Asub16, "fp64"), ("fp64_on_fp8", Fsub, "fp64")):
+            ref_long[tag] = B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec="fp64")[0].cpu().numpy()
+        arms = {}
+        for tag, Am, prec in (("fp8", Fsub, "fp8"), ("bf16", Asub16, "bf16"), ("fp64_on_bf16", Asub16, "fp64"),
+                              ("fp64_on_fp8", Fsub, "fp64")):
+            arms[tag] = (B.krr_solve(Am, ysub, k, lam, b, s, Hs, seed=7, prec=prec)[0].cpu().numpy(),
+                         B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec=prec)[0].cpu().numpy())
+        torch.cuda.synchronize()
+        A_sub_h = Asub16.float().cpu().numpy().astype(np.float64)
+        y_sub_h = ysub.cpu().numpy()
+
+    def rel(a, b_):
+        return float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
+
+    out_err = None
+    cpu = None
+    if rank == 0:
+        out_err = {"rows": msub, "seed": 7,
+                   "long_H_blocks": Hl,
+                   "vs_fp64_gpu_long": {"fp8_vs_fp64_on_fp8_data": rel(arms["fp8"][1], ref_long["fp64_on_fp8"]),
+                                        "bf16_vs_fp64_on_bf16_data": rel(arms["bf16"][1], ref_long["fp64_on_bf16"]),
+                                        "fp8_storage_vs_bf16_storage_fp64": rel(ref_long["fp64_on_fp8"],
+                                                                                ref_long["fp64_on_bf16"]),
+                                        "fp8_vs_fp64_on_bf16_data": rel(arms["fp8"][1], ref_long["fp64_on_bf16"])}}
+        if not args.no_cpu:
+            import oracle
+            oracle.build()
+            ko = oracle.kernel("rbf", gamma=gam)
+            t0 = time.perf_counter()
+            want = oracle.bdcd_krr(A_sub_h, y_sub_h, ko, lam, b, Hs, seed=7)
+            t_or = time.perf_counter() - t0
+            out_err["oracle_H_blocks"] = Hs
+            out_err["vs_oracle"] = {t: rel(arms[t][0], want) for t in arms}
+            out_err["vs_oracle_note"] = ("oracle = FP64 BDCD (Algorithm 3) on the BF16-stored rows; fp64_on_fp8 and "
+                                         "fp8 differ from it by the FP8 storage")
+            upd = Hs * b
+            cpu = {"value": upd / t_or * msub / m, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{Hs} BDCD block updates (b={b}) on rows 0..{msub - 1} ({t_or:.1f} s, plain FP64 C, "
+                             f"one thread), rate scaled by rows to m={m}"}
+        hbm_peak, bf16_peak, bf16_sus, src = peaks()
+        sb = s * b
+        flops = 2.0 * m * n * sb
+        fp8_peak = 2.0 * bf16_peak
+        roof = {"bound": "tensor", "achieved": flops / (ph8["block"] * 1e-3) / 1e12, "peak": fp8_peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"{src} bf16 burst x 2 (nominal fp8 / bf16 dense ratio 4.5 / 2.25)",
+                "kernel": "block_tc_kernel<MODE_FP8> (kind::f8f6f4 kernel block + gradient update)",
+                "algorithmic": {"flops_per_launch": flops, "launch_ms": ph8["block"]}}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof16 = {"achieved": flops / (ph16["block"] * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
+        roof16["frac"] = roof16["achieved"] / bf16_peak
+        value = ws * args.steps * s * b / (ms8 * 1e-3)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms8 / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "fp8-e4m3", "data": "synthetic",
+               "config": {"workload": WORKLOAD_FP8, "m": m, "n": n, "b": b, "s": s, "gamma": gam, "lambda": lam,
+                          "precision": "fp8 (per-row-scaled e4m3, kind::f8f6f4, FP32 accumulation)",
+                          "l2": "A (0.82 GB FP8 / 1.64 GB BF16) above L2; 256 MB buffer written before every step"},
+               "phase_ms": ph8,
+               "bf16_storage": {"value": ws * args.steps * s * b / (ms16 * 1e-3), "ms_per_step": ms16 / args.steps,
+                                "phase_ms": ph16, "roofline": roof16},
+               "alpha_error": out_err,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- sweep -----
 WORKLOAD_SWEEP = ("batched K-RR sweep: 256 BDCD solves, m ~ U[1000, 20000], n=128, A, y ~ N(0,1), RBF sigma on a "
                   "log grid [0.1, 10] x lambda on a log grid [1e-6, 1e-1], b alternating 8 / 32, s autotuned")
@@ -557,17 +725,23 @@ def main():
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--s", type=int, default=None)
-    ap.add_argument("--workload", default="krr", choices=["krr", "csr", "sweep"],
-                    help="krr: dense K-RR BDCD (the headline); csr: sparse K-SVM DCD; sweep: batched K-RR")
+    ap.add_argument("--workload", default="krr", choices=["krr", "csr", "sweep", "fp8"],
+                    help="krr: dense K-RR BDCD (the headline); csr: sparse K-SVM DCD; sweep: batched K-RR; "
+                         "fp8: the FP8 / BF16 storage stress configuration")
     ap.add_argument("--sweep-count", type=int, default=256)
     ap.add_argument("--sweep-H", type=int, default=2048, help="block updates per problem")
+    ap.add_argument("--fp8-m", type=int, default=400000)
+    ap.add_argument("--fp8-n", type=int, default=2048)
+    ap.add_argument("--fp8-sub", type=int, default=20000, help="rows of the alpha-error subproblem")
+    ap.add_argument("--fp8-oracle-blocks", type=int, default=128, help="block updates the oracle runs")
+    ap.add_argument("--fp8-long-steps", type=int, default=20, help="outer steps of the GPU-only comparison")
     ap.add_argument("--csr-m", type=int, default=200000)
     ap.add_argument("--csr-n", type=int, default=50000)
     ap.add_argument("--csr-nnz", type=int, default=50)
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16", "tf32", "bf16x3", "fp64"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")
@@ -587,6 +761,8 @@ def main():
         run_gpu_csr(args)
     elif args.workload == "sweep":
         run_gpu_sweep(args)
+    elif args.workload == "fp8":
+        run_gpu_fp8(args)
     else:
         run_gpu(args)
 

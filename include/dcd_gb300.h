@@ -54,8 +54,17 @@ typedef struct {
     const void *values;       /* dense: m*ld elements; CSR: nnz elements */
     const int64_t *row_ptr;   /* CSR only: m+1 offsets, row_ptr[0] = 0, non-decreasing */
     const int32_t *col_idx;   /* CSR only: nnz column indices in [0, n), distinct within a row */
-    const float *row_scale;   /* FP8 only: a_i = row_scale[i] * q_i; else NULL */
+    const float *row_scale;   /* FP8 only: a_i = row_scale[i] * q_i (m finite scales >= 0,
+                                 host memory under DCD_FLAG_HOST_IO); else ignored */
 } dcd_matrix;
+/*
+ * FP8 storage (dtype DCD_FP8E4M3, dense only): values holds one OCP e4m3 code
+ * per element (sign, 4 exponent bits with bias 7, 3 mantissa bits, largest
+ * finite 448, codes 0x7f/0xff NaN) and row i stands for row_scale[i] * q_i.
+ * A NaN code or a negative or non-finite scale gives DCD_EINVAL.  Under
+ * DCD_PREC_FP8 the codes feed the tensor cores as they are; every other
+ * precision dequantises first (exactly for DCD_PREC_FP64).
+ */
 /*
  * CSR matrices take F32 or F64 values (BF16 / FP8 give DCD_EUNSUPPORTED).
  * Their kernel block is an SpMM on the CUDA cores, streamed once per outer
@@ -81,7 +90,10 @@ typedef enum {
     DCD_PREC_FP64 = 0,   /* FP64 CUDA-core block, direct RBF distances */
     DCD_PREC_TF32 = 1,   /* tcgen05 kind::tf32 block, FP32 accumulation */
     DCD_PREC_BF16 = 2,   /* tcgen05 kind::f16 (bf16) block, FP32 accumulation */
-    DCD_PREC_FP8 = 3,    /* reserved */
+    DCD_PREC_FP8 = 3,    /* tcgen05 kind::f8f6f4 block on e4m3 codes with per-row scales (the
+                            FP8 storage below), FP32 accumulation; the epilogue scales each
+                            dot by s_i s_j.  A non-FP8 dense A is quantised first as
+                            dcd_quantize_e4m3 does.  Dense A only (CSR: DCD_EUNSUPPORTED) */
     DCD_PREC_BF16X3 = 4, /* split bf16: a = hi + lo, three tcgen05 kind::f16 MMAs per
                             k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
     DCD_PREC_TF32X3 = 5  /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
@@ -308,9 +320,24 @@ dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int3
  * different host threads) race on the array and corrupt each other's output.
  */
 #define DCD_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+/* (DCD_PREC_FP8 and FP8 data matrices: DCD_EUNSUPPORTED here.) */
 dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
                                    int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,
                                    void *stream);
+
+/*
+ * dcd_quantize_e4m3 -- per-row FP8 storage of a dense matrix (the FP8 form
+ * of the data matrix; the paper computes in FP64 and has no counterpart):
+ *   row i is first rounded to FP32; row_scale[i] = fl32(max_k |a_ik| / 448);
+ *   q[i*ldq + k] = e4m3 code of fl32(a_ik / row_scale[i]) (IEEE FP32
+ *   division, round to nearest even, saturating at +-448; a value that rounds
+ *   to zero keeps its sign); a row of zeros gets row_scale 0 and zero codes.
+ *   Columns n..ldq-1 of q are set to 0.
+ *   A: dense F64/F32/BF16 on the device.  q: device, m*ldq bytes, ldq >= n.
+ *   row_scale: device, m floats.  Both are caller-owned.
+ * A non-finite value gives DCD_EINVAL (q and row_scale are then unspecified).
+ */
+dcd_status dcd_quantize_e4m3(const dcd_matrix *A, uint8_t *q, int64_t ldq, float *row_scale, void *stream);
 
 #ifdef __cplusplus
 }

@@ -69,7 +69,7 @@ class BatchOpts(C.Structure):
 EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "bdcd_krr_solve_batched", "dcd_krr_autotune_s",
            "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
            "dcd_plan_enqueue", "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
-           "dcd_kernel_block_apply", "dcd_kernel_block_static"]
+           "dcd_kernel_block_apply", "dcd_kernel_block_static", "dcd_quantize_e4m3"]
 
 _lock = threading.Lock()
 _lib = None
@@ -110,6 +110,7 @@ def lib():
             "dcd_kernel_block": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
             "dcd_kernel_block_apply": (i32, [M, K, i32, P, i64, P, P, P, P]),
             "dcd_kernel_block_static": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
+            "dcd_quantize_e4m3": (i32, [M, P, i64, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -176,10 +177,53 @@ class Csr:
         return Matrix(CSR, dt, self.m, self.n, 0, _ptr(v), _ptr(self.row_ptr), _ptr(self.col_idx), None)
 
 
+class Fp8:
+    """FP8 storage of a dense matrix: e4m3 codes (uint8, m x n row-major, a
+    torch tensor on the device or a numpy array with DCD_FLAG_HOST_IO) and
+    one float32 scale per row; row i stands for scale[i] * value(codes[i])."""
+
+    def __init__(self, codes, scale):
+        self.codes, self.scale = codes, scale
+        if codes.shape[0] != scale.shape[0]:
+            raise ValueError("one scale per row")
+
+    @property
+    def shape(self):
+        return tuple(self.codes.shape)
+
+    @property
+    def device(self):
+        return self.codes.device
+
+    def matrix(self) -> Matrix:
+        q = self.codes
+        if isinstance(q, np.ndarray):
+            assert q.dtype == np.uint8 and q.flags.c_contiguous and self.scale.dtype == np.float32
+            ld = q.shape[1]
+        else:
+            import torch
+            assert q.dtype == torch.uint8 and q.dim() == 2 and q.stride(1) == 1
+            assert self.scale.dtype == torch.float32 and self.scale.is_contiguous()
+            ld = q.stride(0)
+        return Matrix(DENSE, FP8E4M3, q.shape[0], q.shape[1], ld, _ptr(q), None, None, _ptr(self.scale))
+
+
+def quantize_e4m3(A, stream=None) -> Fp8:
+    """Per-row FP8 storage of a dense device matrix (dcd_quantize_e4m3)."""
+    import torch
+    m, n = A.shape
+    q = torch.empty((m, n), dtype=torch.uint8, device=A.device)
+    sc = torch.empty(m, dtype=torch.float32, device=A.device)
+    Am = dense_matrix(A)
+    _check(lib().dcd_quantize_e4m3(C.byref(Am), _ptr(q), n, _ptr(sc), _stream(stream)), "dcd_quantize_e4m3",
+           allow_notconv=False)
+    return Fp8(q, sc)
+
+
 def dense_matrix(A) -> Matrix:
     """Describe a row-major 2-D torch tensor (device) or numpy array (host),
-    or a Csr."""
-    if isinstance(A, Csr):
+    a Csr or an Fp8."""
+    if isinstance(A, (Csr, Fp8)):
         return A.matrix()
     if isinstance(A, np.ndarray):
         dt = {np.dtype(np.float64): F64, np.dtype(np.float32): F32}[A.dtype]

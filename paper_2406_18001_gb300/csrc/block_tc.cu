@@ -2,8 +2,9 @@
 //
 // C[i, j] = a_i . b_j for a packed, zero-padded operand A (rows of the data
 // matrix) and B (the s*b sampled rows), both K-major, is formed by
-// tcgen05.mma (kind::f16 with bf16 inputs, or kind::tf32 on fp32 inputs) with
-// FP32 accumulators in tensor memory.  The epilogue maps C through the kernel
+// tcgen05.mma (kind::f16 with bf16 inputs, kind::tf32 on fp32 inputs, or
+// kind::f8f6f4 on per-row-scaled e4m3 codes) with FP32 accumulators in tensor
+// memory.  The epilogue maps C through the kernel
 // function of Table 1 -- the RBF via the expansion ||a||^2 + ||b||^2 - 2 a.b
 // of Section 5.2 -- and either
 //   apply: contracts each row with the column coefficients w and adds
@@ -44,7 +45,10 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // dropping only lo.lo, about 2^-16 relative).
 // Split tf32 ("tf32x3") is the same with kind::tf32 and tf32 planes (~22
 // significant bits, at half the bf16 MMA rate).
-constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3;
+// fp8: e4m3 codes q with per-row scales (a_i ~ s_i q_i), kind::f8f6f4 with 32
+// codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
+// q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
+constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4;
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
@@ -136,21 +140,28 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: D = F32, A/B format (bf16 = 1, tf32 = 2), both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+// Instruction descriptor: D = F32, A/B format (kind::f16: bf16 = 1;
+// kind::tf32: tf32 = 2; kind::f8f6f4: e4m3 = 0), both K-major, N >> 3 at bit
+// 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t make_idesc(int fmt, int n, int m)
 {
     return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(m >> 4) << 24);
 }
 
-template <bool TF32>
+// MK: 0 kind::f16, 1 kind::tf32, 2 kind::f8f6f4
+template <int MK>
 __device__ __forceinline__ void mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
-    if (TF32)
+    if (MK == 1)
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    else if (MK == 2)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
     else
         asm volatile(
@@ -195,6 +206,8 @@ struct TcArgs {
     const float *col_h;   // per-column term, padded with zeros to nchunks*BN
     const float *col_w;   // apply: coefficients, padded with zeros
     const double *rs;     // apply: per-row scale or null
+    const float *row_s;   // fp8: per-row scales of the A operand (nrows_out entries)
+    const float *col_s;   // fp8: per-column scales, padded with zeros like col_h
     double *g;            // apply: gradient (nrows_out)
     float *out;           // store: output, row-major with ldo
     int64_t ldo;
@@ -209,16 +222,19 @@ struct TcArgs {
     int *err;
 };
 
+// K(a_i, b_j) from the accumulator c; rf is the per-row factor: 2 gamma
+// log2(e) (RBF) or 1 (poly, linear), times the row scale in fp8 mode (where
+// c already carries the column scale).
 template <int KIND>
-__device__ __forceinline__ float kf32(float c, float hr, float hc, const TcArgs &a)
+__device__ __forceinline__ float kf32(float c, float hr, float hc, float rf, const TcArgs &a)
 {
     if (KIND == DCD_RBF) {
-        float t = fmaf(c, a.two_gl, -(hr + hc));
+        float t = fmaf(c, rf, -(hr + hc));
         return ex2f(fminf(t, 0.f));
     } else if (KIND == DCD_LINEAR) {
-        return c;
+        return c * rf;
     } else {
-        float t = c + a.coef0, r = t;
+        float t = fmaf(c, rf, a.coef0), r = t;
         for (int e = 1; e < a.degree; ++e) r *= t;
         return r;
     }
@@ -242,6 +258,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     block_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
     constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3;
+    constexpr bool FP8 = MODE == MODE_FP8;
+    constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
     constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3;
     constexpr int STAGES = SPLIT ? 2 : 4;
     constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
@@ -289,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_after();
     const uint32_t tmem_base = *tmem_holder;
     const int bn = a.bn;
-    const int kb_elems = TF32 ? 32 : 64;
+    const int kb_elems = TF32 ? 32 : FP8 ? 128 : 64;  // elements per 128-byte k-block
 
     if (warp == 0) {
         if (lane == 0) {
@@ -324,7 +342,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // --------------------------------------------------------- MMA --
-            const uint32_t idesc = make_idesc(TF32 ? 2 : 1, bn, BM);
+            const uint32_t idesc = make_idesc(TF32 ? 2 : FP8 ? 0 : 1, bn, BM);
             uint32_t it = 0, acc_it = 0;
             bool ok = true, issued = false;
             for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
@@ -348,11 +366,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint32_t ab = su32(sA + s * A_ST), bb = su32(sB + s * B_ST);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            mma<TF32>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
-                                      (kb > 0 || k > 0) ? 1u : 0u);
+                            mma<MK>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
+                                    (kb > 0 || k > 0) ? 1u : 0u);
                             if (SPLIT) {
-                                mma<TF32>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + B_STAGE + 32 * k), idesc, 1u);
-                                mma<TF32>(dtm, sw128_desc(ab + A_STAGE + 32 * k), sw128_desc(bb + 32 * k), idesc, 1u);
+                                mma<MK>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + B_STAGE + 32 * k), idesc, 1u);
+                                mma<MK>(dtm, sw128_desc(ab + A_STAGE + 32 * k), sw128_desc(bb + 32 * k), idesc, 1u);
                             }
                         }
                         issued = true;
@@ -380,6 +398,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t row = (int64_t)tile * BM + row_in_tile;
             const bool row_ok = row < a.nrows_out;
             const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
+            const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
+            const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
             double racc = 0.0;
             for (int nc = c0; nc < c1; ++nc, ++acc_it) {
                 const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
@@ -395,6 +415,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float v[32];
                     tmem_ld32(tmem_base + lane_addr + buf * (uint32_t)bn + (uint32_t)(cg * 32), v);
                     const int64_t colbase = (int64_t)nc * bn + cg * 32;
+                    if (FP8) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] *= a.col_s[colbase + q];
+                    }
                     if (a.store) {
                         if (row_ok) {
                             float *dst = a.out + row * a.ldo + colbase;
@@ -402,17 +426,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                                 for (int q = 0; q < 32; q += 4) {
                                     float4 o;
-                                    o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, a);
-                                    o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, a);
-                                    o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, a);
-                                    o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, a);
+                                    o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
+                                    o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf, a);
+                                    o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf, a);
+                                    o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf, a);
                                     *reinterpret_cast<float4 *>(dst + q) = o;
                                 }
                             } else {
 #pragma unroll
                                 for (int q = 0; q < 32; ++q)
                                     if (colbase + q < a.ncols)
-                                        dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, a);
+                                        dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
                             }
                         }
                     } else {
@@ -421,8 +445,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         for (int q = 0; q < 32; q += 2) {
                             const float hc0 = KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f;
                             const float hc1 = KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f;
-                            p0 = fmaf(kf32<KIND>(v[q], hr, hc0, a), a.col_w[colbase + q], p0);
-                            p1 = fmaf(kf32<KIND>(v[q + 1], hr, hc1, a), a.col_w[colbase + q + 1], p1);
+                            p0 = fmaf(kf32<KIND>(v[q], hr, hc0, rf, a), a.col_w[colbase + q], p0);
+                            p1 = fmaf(kf32<KIND>(v[q + 1], hr, hc1, rf, a), a.col_w[colbase + q + 1], p1);
                         }
                         racc += (double)p0 + (double)p1;
                     }
@@ -461,14 +485,17 @@ bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
 {
     auto fn = encode_fn();
     if (!fn) return false;
-    const bool f32 = op.kind == PACK_TF32 || op.kind == PACK_TF32X3;
-    const int esz = f32 ? 4 : 2;
+    const bool f32 = op.kind == PACK_TF32 || op.kind == PACK_TF32X3, fp8 = op.kind == PACK_FP8;
+    const int esz = f32 ? 4 : fp8 ? 1 : 2;
     const int64_t cols = (op.kind == PACK_BF16X3 || op.kind == PACK_TF32X3) ? 2 * op.n_pad : op.n_pad;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)op.nrows};
     cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
     cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(map, dt, 2,
                     const_cast<void *>(op.rows), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -530,9 +557,11 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
-    if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3)
+    if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3 &&
+        Aop.kind != PACK_FP8)
         return cudaErrorInvalidValue;
-    const int kb_elems = (Aop.kind == PACK_TF32 || Aop.kind == PACK_TF32X3) ? 32 : 64;
+    if (Aop.kind == PACK_FP8 && (!Aop.scale || !Bop.scale)) return cudaErrorInvalidValue;
+    const int kb_elems = k_block_elems(Aop.kind);
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
     if (bn > BN_MAX) bn = BN_MAX;
@@ -547,6 +576,8 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.col_h = col_h;
     a.col_w = col_w;
     a.rs = rs;
+    a.row_s = Aop.scale;
+    a.col_s = Bop.scale;
     a.g = g;
     a.out = out;
     a.ldo = ldo;
@@ -572,6 +603,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     if (Aop.kind == PACK_TF32) return launch_mode<MODE_TF32>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_BF16X3) return launch_mode<MODE_BF16X3>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_TF32X3) return launch_mode<MODE_TF32X3>(grid, mA, mB, a, kp.kind, st);
+    if (Aop.kind == PACK_FP8) return launch_mode<MODE_FP8>(grid, mA, mB, a, kp.kind, st);
     return launch_mode<MODE_BF16>(grid, mA, mB, a, kp.kind, st);
 }
 

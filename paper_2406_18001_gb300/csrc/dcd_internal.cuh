@@ -20,6 +20,7 @@ enum DevErr : int {
     DEV_BAD_INDEX = 2,   // a sampled or CSR index fell outside [0, m) / [0, n)
     DEV_NOT_SPD = 3,     // a block system had a non-positive pivot
     DEV_INTERNAL = 4,
+    DEV_BAD_VALUE = 5,   // a non-finite data value, FP8 code or row scale
 };
 
 __device__ __forceinline__ void set_error(int *err, int code)
@@ -94,19 +95,28 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
 // ([hi | lo], n_pad elements each): bf16x3 with hi = bf16(a), lo = bf16(a -
 // hi) (~16 significant bits), tf32x3 with both planes on the tf32 grid (~22
 // bits).
-enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4 };
+// fp8: e4m3 codes (one byte per feature) of the per-row-scaled storage
+// a_i ~ scale_i * q_i; the scales travel beside the packed rows.
+enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4, PACK_FP8 = 5 };
 struct TcOperand {
     const void *rows;     // packed matrix, row-major
     int64_t nrows;
     int64_t n_pad;        // features per half, multiple of the k-block
-    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3 or PACK_TF32X3
+    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3 or PACK_FP8
+    const float *scale = nullptr;  // PACK_FP8: per-row scales (padded with zeros like the rows)
 };
 // elements per 128-byte k-block of a packed row (the padding unit of n_pad)
-__host__ __device__ inline int k_block_elems(int kind) { return (kind == PACK_TF32 || kind == PACK_TF32X3) ? 32 : 64; }
+__host__ __device__ inline int k_block_elems(int kind)
+{
+    return (kind == PACK_TF32 || kind == PACK_TF32X3) ? 32 : kind == PACK_FP8 ? 128 : 64;
+}
 
 __host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
 {
-    return kind == PACK_TF32X3 ? 8 * n_pad : (kind == PACK_TF32 || kind == PACK_BF16X3) ? 4 * n_pad : 2 * n_pad;
+    return kind == PACK_TF32X3                          ? 8 * n_pad
+           : (kind == PACK_TF32 || kind == PACK_BF16X3) ? 4 * n_pad
+           : kind == PACK_FP8                           ? n_pad
+                                                        : 2 * n_pad;
 }
 bool tc_available();
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
@@ -115,12 +125,20 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
                             int *err, cudaStream_t st);
 
 // setup / per-step helpers (sample_update.cu)
+// src_scale: the per-row scales of an FP8 source (dtype DCD_FP8E4M3), else unused
 cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
-                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st);
+                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st,
+                             const float *src_scale = nullptr);
+// Per-row e4m3 codes and scales of rows `rows` (or the first count) of a
+// dense source: quantised from F64/F32/BF16, copied from an FP8 source.
+// dst rows have ldq bytes (zero past n); a non-finite row sets DEV_BAD_VALUE.
+cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                 const float *src_scale, uint8_t *dst, int64_t ldq, float *dst_scale, int64_t count,
+                                 int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
-                             float *h, cudaStream_t st);
+                             float *h, cudaStream_t st, const float *scale = nullptr);
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
                                void *dst, int *err, cudaStream_t st);
 cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st);

@@ -64,22 +64,48 @@ cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, ui
 }
 
 // ------------------------------------------------------------ packing -----
-__device__ __forceinline__ float load_as_f32(const void *src, int dtype, int64_t off)
+// Value of an e4m3 code (OCP FP8: sign, 4 exponent bits with bias 7, 3
+// mantissa bits; exponent field 0 holds the subnormals f * 2^-9; 0x7f / 0xff
+// are NaN).  Exact in FP32: the float's bits are assembled directly.
+__device__ __forceinline__ float e4m3_value(uint32_t c)
+{
+    const uint32_t e = (c >> 3) & 15u, f = c & 7u;
+    float v;
+    if ((c & 0x7Fu) == 0x7Fu) v = __int_as_float(0x7fc00000);
+    else if (e) v = __uint_as_float(((e + 120u) << 23) | (f << 20));  // (1 + f/8) * 2^(e-7)
+    else v = (float)f * 0.001953125f;                                 // f * 2^-9
+    return (c & 0x80u) ? -v : v;
+}
+
+// Nearest e4m3 code of x (ties to even), saturating at +-448.
+__device__ __forceinline__ uint32_t e4m3_code(float x)
+{
+    uint16_t pair;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(pair) : "f"(0.f), "f"(x));  // x -> low byte
+    return pair & 0xFFu;
+}
+
+// Element `off` of a dense source as FP32; an FP8 source is scale * value(q)
+// rounded once.
+__device__ __forceinline__ float load_as_f32(const void *src, int dtype, int64_t off, float scale = 0.f)
 {
     switch (dtype) {
     case DCD_F64: return (float)((const double *)src)[off];
     case DCD_F32: return ((const float *)src)[off];
     case DCD_BF16: return __bfloat162float(((const __nv_bfloat16 *)src)[off]);
+    case DCD_FP8E4M3: return (float)((double)scale * (double)e4m3_value(((const uint8_t *)src)[off]));
     default: return 0.f;
     }
 }
 
 // dst row r (n_pad elements, zero padded) = src row rows[r] (or r),
 // converted to bf16 (round to nearest even, dst_kind 0), fp32 (1, the tf32
-// path reads fp32 storage) or fp64 (2).
+// path reads fp32 storage) or fp64 (2).  An FP8 source is dequantised with
+// its row scales (exactly, for fp64).
 // Row indices outside [0, m) produce a zero row and set DEV_BAD_INDEX.
 __global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
-                                 void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err)
+                                 void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err,
+                                 const float *src_scale)
 {
     const int64_t total = count * n_pad;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -87,14 +113,17 @@ __global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t
         const int64_t sr = rows ? (int64_t)rows[r] : r;
         const bool inb = sr >= 0 && sr < m;
         if (!inb && c == 0) set_error(err, DEV_BAD_INDEX);
+        const float rsc = (dtype == DCD_FP8E4M3 && inb) ? src_scale[sr] : 0.f;
         if (dst_kind == 2) {
             double v = 0.0;
             if (c < n && inb)
-                v = (dtype == DCD_F64) ? ((const double *)src)[sr * ld + c] : (double)load_as_f32(src, dtype, sr * ld + c);
+                v = (dtype == DCD_F64)       ? ((const double *)src)[sr * ld + c]
+                    : (dtype == DCD_FP8E4M3) ? (double)rsc * (double)e4m3_value(((const uint8_t *)src)[sr * ld + c])
+                                             : (double)load_as_f32(src, dtype, sr * ld + c);
             ((double *)dst)[e] = v;
             continue;
         }
-        float v = (c < n && inb) ? load_as_f32(src, dtype, sr * ld + c) : 0.f;
+        float v = (c < n && inb) ? load_as_f32(src, dtype, sr * ld + c, rsc) : 0.f;
         if (dst_kind == PACK_BF16X3) {
             // hi = bf16(v), lo = bf16(v - hi); v - hi is exact in fp32
             __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -123,13 +152,79 @@ __global__ void pack_rows_kernel(const void *src, int dtype, int64_t ld, int64_t
 }
 
 cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
-                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st)
+                             void *dst, int dst_kind, int64_t n_pad, int64_t count, int *err, cudaStream_t st,
+                             const float *src_scale)
 {
+    if (dst_kind == PACK_FP8 || (dtype == DCD_FP8E4M3 && !src_scale)) return cudaErrorInvalidValue;
     if (count <= 0) return cudaSuccess;
     int64_t total = count * n_pad;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    pack_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, dst, dst_kind, n_pad, count, err);
+    pack_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, dst, dst_kind, n_pad, count, err,
+                                                        src_scale);
+    return cudaGetLastError();
+}
+
+// Per-row FP8 storage (one warp per row): the row is rounded to FP32,
+// scale = fl32(max|a| / 448), code = e4m3(fl32(a / scale)) with IEEE FP32
+// division; a row of zeros gets scale 0 and zero codes.  An FP8 source is
+// copied with its scale.  Columns n..ldq-1 of the destination are zero.
+__global__ void quantize_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n,
+                                     const int32_t *rows, const float *src_scale, uint8_t *dst, int64_t ldq,
+                                     float *dst_scale, int64_t count, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= count) return;
+    const int64_t sr = rows ? (int64_t)rows[r] : r;
+    uint8_t *d = dst + r * ldq;
+    if (sr < 0 || sr >= m) {
+        if (lane == 0) {
+            set_error(err, DEV_BAD_INDEX);
+            dst_scale[r] = 0.f;
+        }
+        for (int64_t c = lane; c < ldq; c += 32) d[c] = 0;
+        return;
+    }
+    bool bad = false;
+    float scale;
+    if (dtype == DCD_FP8E4M3) {
+        const uint8_t *s = (const uint8_t *)src + sr * ld;
+        for (int64_t c = lane; c < ldq; c += 32) {
+            const uint8_t v = c < n ? s[c] : 0;
+            bad |= (v & 0x7F) == 0x7F;
+            d[c] = v;
+        }
+        scale = src_scale[sr];
+        bad |= !(scale >= 0.f && scale <= 3.4028234e38f);
+    } else {
+        float amax = 0.f;
+        for (int64_t c = lane; c < n; c += 32) {
+            const float v = load_as_f32(src, dtype, sr * ld + c);
+            bad |= !(fabsf(v) <= 3.4028234e38f);
+            amax = fmaxf(amax, fabsf(v));
+        }
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        scale = __fdiv_rn(amax, 448.f);
+        for (int64_t c = lane; c < ldq; c += 32) {
+            uint32_t code = 0;
+            if (c < n && scale > 0.f) code = e4m3_code(__fdiv_rn(load_as_f32(src, dtype, sr * ld + c), scale));
+            d[c] = (uint8_t)code;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(err, DEV_BAD_VALUE);
+    if (lane == 0) dst_scale[r] = scale;
+}
+
+cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                 const float *src_scale, uint8_t *dst, int64_t ldq, float *dst_scale, int64_t count,
+                                 int *err, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    if (ldq < n || (dtype == DCD_FP8E4M3 && !src_scale)) return cudaErrorInvalidValue;
+    const int64_t blocks = (count * 32 + 255) / 256;
+    quantize_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, src_scale, dst, ldq, dst_scale,
+                                                           count, err);
     return cudaGetLastError();
 }
 
@@ -171,9 +266,11 @@ cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cuda
 // h[r] = gamma * log2(e) * ||x_r||^2 of the packed (already rounded) row, for
 // the RBF expansion ||a||^2 + ||b||^2 - 2 a.b (Section 5.2); 0 for the other
 // kernels.  For split rows the norm is the one the three MMAs reproduce,
-// sum(hi^2 + 2 hi lo), so that a row's distance to itself stays ~0.  One warp
-// per row, FP64 partial sums, fixed order.
-__global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, int64_t m, double scale, float *h)
+// sum(hi^2 + 2 hi lo), so that a row's distance to itself stays ~0; FP8 rows
+// take the dequantised norm rscale[r]^2 * sum value(q)^2.  One warp per row,
+// FP64 partial sums, fixed order.
+__global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, int64_t m, double scale, float *h,
+                                 const float *rscale)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -192,6 +289,9 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
             const float *row = (const float *)packed + r * 2 * n_pad;
             const float hi = row[c], lo = row[n_pad + c];
             sf = fmaf(hi, hi + 2.f * lo, sf);
+        } else if (kind == PACK_FP8) {  // sum of value(q)^2; the row scale comes in below
+            const float v = e4m3_value(((const uint8_t *)packed)[r * n_pad + c]);
+            sf = fmaf(v, v, sf);
         } else {
             const float v = __bfloat162float(((const __nv_bfloat16 *)packed)[r * n_pad + c]);
             sf = fmaf(v, v, sf);
@@ -199,16 +299,18 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
     }
     double s = sf;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (kind == PACK_FP8) s *= (double)rscale[r] * (double)rscale[r];
     if (lane == 0) h[r] = (float)(scale * s);
 }
 
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
-                             float *h, cudaStream_t st)
+                             float *h, cudaStream_t st, const float *rscale)
 {
+    if (kind == PACK_FP8 && !rscale) return cudaErrorInvalidValue;
     if (m <= 0) return cudaSuccess;
     double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;
     int64_t blocks = (m * 32 + 255) / 256;
-    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, kind, n_pad, m, scale, h);
+    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, kind, n_pad, m, scale, h, rscale);
     return cudaGetLastError();
 }
 

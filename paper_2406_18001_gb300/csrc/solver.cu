@@ -68,8 +68,9 @@ dcd_status validate_kernel(const dcd_kernel *k)
     }
 }
 
-// Dense: row-major f64/f32/bf16 with ld >= n.  CSR: f32/f64 values, int64
-// row offsets, int32 columns (checked on the device by the solver).
+// Dense: row-major f64/f32/bf16, or e4m3 codes with per-row scales, with
+// ld >= n.  CSR: f32/f64 values, int64 row offsets, int32 columns (checked on
+// the device by the solver).
 dcd_status validate_dense(const dcd_matrix *A)
 {
     if (!A || A->m < 1 || A->n < 1) return DCD_EINVAL;
@@ -81,8 +82,9 @@ dcd_status validate_dense(const dcd_matrix *A)
         return DCD_OK;
     }
     if (A->fmt != DCD_DENSE) return DCD_EINVAL;
-    if (A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
-    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
+    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16 && A->dtype != DCD_FP8E4M3)
+        return DCD_EINVAL;
+    if (A->dtype == DCD_FP8E4M3 && !A->row_scale) return DCD_EINVAL;
     if (A->ld < A->n || !A->values) return DCD_EINVAL;
     if (A->m > INT32_MAX) return DCD_EINVAL;
     return DCD_OK;
@@ -94,7 +96,8 @@ KernelParams to_kp(const dcd_kernel *k) { return KernelParams{k->kind, k->degree
 
 bool is_tc(int prec)
 {
-    return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3 || prec == DCD_PREC_TF32X3;
+    return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3 || prec == DCD_PREC_TF32X3 ||
+           prec == DCD_PREC_FP8;
 }
 
 // packed operand kind of a tensor-core precision
@@ -103,6 +106,7 @@ int pack_kind(int prec)
     return prec == DCD_PREC_TF32 ? PACK_TF32
            : prec == DCD_PREC_BF16X3 ? PACK_BF16X3
            : prec == DCD_PREC_TF32X3 ? PACK_TF32X3
+           : prec == DCD_PREC_FP8    ? PACK_FP8
                                      : PACK_BF16;
 }
 
@@ -116,6 +120,7 @@ struct Operand {
     int64_t n_pad = 0;
     int kind = PACK_BF16;
     float *row_h = nullptr;
+    float *row_s = nullptr;  // PACK_FP8: per-row scales
 };
 
 // Per-phase device times of an outer step: an event pair per phase, recorded
@@ -192,6 +197,8 @@ struct Solver {
     void *ws_csr = nullptr;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
+    float *col_s = nullptr;       // fp8: scales of the sampled rows
+    const float *src_scale = nullptr;  // the row scales of an FP8 data matrix (device)
     int32_t *S = nullptr;
     void *Kss = nullptr;
     int64_t ldk = 0;
@@ -221,6 +228,7 @@ struct Solver {
         case DEV_OK: return DCD_OK;
         case DEV_TIMEOUT: return DCD_ETIMEOUT;
         case DEV_NOT_SPD: return DCD_ENOTSPD;
+        case DEV_BAD_VALUE: return DCD_EINVAL;
         default: return DCD_EINTERNAL;
         }
     }
@@ -252,6 +260,8 @@ struct Solver {
         const size_t row_bytes = tcd ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
         const bool need_pack = !csr && (tc || A->dtype != DCD_F64 || host);
         const bool ref_op = tcd && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
+        const bool fp8 = tcd && pack_kind(o.prec) == PACK_FP8;
+        const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
         const int64_t n_pad_r = (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
 
@@ -264,6 +274,9 @@ struct Solver {
             int32_t *hci = (int32_t *)ar.take(host && csr ? sizeof(int32_t) * nnz : 0);
             float *cv32 = (float *)ar.take(conv32 ? sizeof(float) * nnz : 0);
             double *cv64 = (double *)ar.take(conv64 ? sizeof(double) * nnz : 0);
+            float *hsc = (float *)ar.take(host && fp8in ? sizeof(float) * m : 0);
+            float *rsc = (float *)ar.take(fp8 ? sizeof(float) * m : 0);
+            float *csc = (float *)ar.take(fp8 ? sizeof(float) * col_pad : 0);
             float *nrm32 = (float *)ar.take(csr ? sizeof(float) * m : 0);
             double *nrm64 = (double *)ar.take(csr ? sizeof(double) * m : 0);
             double *yv = (double *)ar.take(host ? sizeof(double) * m : 0);
@@ -316,6 +329,11 @@ struct Solver {
             g = gv;
             op.packed = pk;
             op.row_h = rh;
+            op.row_s = rsc;
+            col_s = csc;
+            src_scale = fp8in ? (host ? hsc : A->row_scale) : nullptr;
+            if (host && fp8in)
+                DCD_TRY(cudaMemcpyAsync(hsc, A->row_scale, sizeof(float) * m, cudaMemcpyHostToDevice, st));
             As = as;
             col_h = ch;
             col_w = cw;
@@ -354,6 +372,7 @@ struct Solver {
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
         if (tcd) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
+        if (fp8) DCD_TRY(cudaMemsetAsync(col_s, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
 
         // operand
@@ -380,13 +399,21 @@ struct Solver {
         } else if (tc) {
             op.n_pad = n_pad;
             op.kind = pack_kind(o.prec);
-            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st));
-            DCD_TRY(launch_row_terms(op.packed, op.kind, n_pad, m, kp, op.row_h, st));
+            if (fp8) {
+                DCD_TRY(launch_quantize_rows(vals, A->dtype, A->ld, m, n, nullptr, src_scale, (uint8_t *)op.packed,
+                                             n_pad, op.row_s, m, err, st));
+                dcd_status qs = check_device_error();  // non-finite values or scales: EINVAL
+                if (qs != DCD_OK) return qs;
+            } else {
+                DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st,
+                                         src_scale));
+            }
+            DCD_TRY(launch_row_terms(op.packed, op.kind, n_pad, m, kp, op.row_h, st, op.row_s));
             if (ref_op) {
                 opr.n_pad = n_pad_r;
                 opr.kind = PACK_TF32X3;
                 DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, opr.packed, opr.kind, n_pad_r, m, err,
-                                         st));
+                                         st, src_scale));
                 DCD_TRY(launch_row_terms(opr.packed, opr.kind, n_pad_r, m, kp, opr.row_h, st));
                 DCD_TRY(cudaMemsetAsync(col_hr, 0, sizeof(float) * col_pad, st));
             } else {
@@ -395,7 +422,7 @@ struct Solver {
                 col_hr = col_h;
             }
         } else if (need_pack) {
-            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st));
+            DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st, src_scale));
             op.a64 = (const double *)op.packed;
             op.lda = n;
         } else {
@@ -512,6 +539,7 @@ struct Solver {
         if (!tc) return cudaSuccess;
         cudaError_t e = launch_gather_rows(x.packed, packed_row_bytes(x.kind, x.n_pad), S, ncols, m, Asx, err, st);
         if (e != cudaSuccess) return e;
+        if (x.kind == PACK_FP8 && (e = launch_gather_f32(x.row_s, S, ncols, col_s, st)) != cudaSuccess) return e;
         return launch_gather_f32(x.row_h, S, ncols, chx, st);
     }
 
@@ -521,7 +549,7 @@ struct Solver {
             return launch_csr_block(ca, cm, !tc, kp, S, ncols, S, ncols, nullptr, nullptr, nullptr, nullptr, Kss, ldk,
                                     st);
         if (tc) {
-            TcOperand B{As, ncols, op.n_pad, op.kind};
+            TcOperand B{As, ncols, op.n_pad, op.kind, col_s};
             return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
                                    err, st);
         }
@@ -550,8 +578,8 @@ struct Solver {
             if (e != cudaSuccess) return cuda_status(e);
             e = clear_col_w_tail(ncols);
             if (e != cudaSuccess) return cuda_status(e);
-            TcOperand Aop{x.packed, m, x.n_pad, x.kind};
-            TcOperand Bop{Asx, ncols, x.n_pad, x.kind};
+            TcOperand Aop{x.packed, m, x.n_pad, x.kind, x.row_s};
+            TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 ? col_s : nullptr};
             return cuda_status(
                 launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st));
         }
@@ -577,8 +605,8 @@ struct Solver {
 
     cudaError_t block_tc_apply(int64_t ncols, const double *rs)
     {
-        TcOperand Aop{op.packed, m, op.n_pad, op.kind};
-        TcOperand Bop{As, ncols, op.n_pad, op.kind};
+        TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
+        TcOperand Bop{As, ncols, op.n_pad, op.kind, col_s};
         return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st);
     }
 
@@ -843,8 +871,8 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem, bool csr)
     if (o->b > B_MAX || o->b > m) return DCD_EINVAL;
     if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
-    if (o->prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
     if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
+    if (o->prec == DCD_PREC_FP8 && csr) return DCD_EUNSUPPORTED;  // the CSR block has no fp8 form
     if (is_tc(o->prec) && !csr && !tc_available()) return DCD_EUNSUPPORTED;  // CSR: CUDA cores
     return DCD_OK;
 }
@@ -1036,8 +1064,8 @@ dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     dcd_status s = validate_dense(A);
     if (s != DCD_OK) return s;
     if ((s = validate_kernel(k)) != DCD_OK) return s;
-    if (prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
     if (prec != DCD_PREC_FP64 && !is_tc(prec)) return DCD_EINVAL;
+    if (prec == DCD_PREC_FP8 && A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;
     if (is_tc(prec) && A->fmt != DCD_CSR && !tc_available()) return DCD_EUNSUPPORTED;
     return DCD_OK;
 }
@@ -1048,7 +1076,7 @@ dcd_status finish_component(int *err, cudaStream_t st)
     DCD_TRY(cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     DCD_TRY(cudaStreamSynchronize(st));
     if (he == DEV_TIMEOUT) return DCD_ETIMEOUT;
-    if (he == DEV_BAD_INDEX) return DCD_EINVAL;
+    if (he == DEV_BAD_INDEX || he == DEV_BAD_VALUE) return DCD_EINVAL;
     return he ? DCD_EINTERNAL : DCD_OK;
 }
 
@@ -1131,7 +1159,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         int64_t lda = A->ld;
         if (pack) {
             double *p = (double *)(base + op64);
-            DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, p, 2, A->n, A->m, err, st));
+            DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, p, 2, A->n, A->m, err, st,
+                                     A->row_scale));
             a64 = p;
             lda = A->n;
         }
@@ -1151,25 +1180,57 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     size_t orh = place(cur, sizeof(float) * nrows);
     size_t och = place(cur, sizeof(float) * cpad);
     size_t ocw = place(cur, sizeof(float) * cpad);
+    const bool fp8 = pk == PACK_FP8;
+    size_t ors = place(cur, fp8 ? sizeof(float) * nrows : 0);
+    size_t ocs = place(cur, fp8 ? sizeof(float) * cpad : 0);
     DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
     char *base = (char *)cb.mem;
     int *err = (int *)(base + oe);
     void *pa = base + oa, *pb = base + ob;
     float *rh = (float *)(base + orh), *ch = (float *)(base + och), *cw = (float *)(base + ocw);
+    float *rsa = fp8 ? (float *)(base + ors) : nullptr, *rsb = fp8 ? (float *)(base + ocs) : nullptr;
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
     DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
-    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, pk, n_pad, nrows, err, st));
-    DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, pk, n_pad, ncols, err, st));
-    DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st));
-    DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st));
+    if (fp8) {
+        DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
+        DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, A->row_scale, (uint8_t *)pa, n_pad,
+                                     rsa, nrows, err, st));
+        DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, A->row_scale, (uint8_t *)pb, n_pad,
+                                     rsb, ncols, err, st));
+    } else {
+        DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, pk, n_pad, nrows, err, st,
+                                 A->row_scale));
+        DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, pk, n_pad, ncols, err, st,
+                                 A->row_scale));
+    }
+    DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st, rsa));
+    DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st, rsb));
     if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
-    TcOperand Aop{pa, nrows, n_pad, pk}, Bop{pb, ncols, n_pad, pk};
+    TcOperand Aop{pa, nrows, n_pad, pk, rsa}, Bop{pb, ncols, n_pad, pk, rsb};
     DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st));
     return finish_component(err, st);
 }
 
 }  // namespace
+
+extern "C" dcd_status dcd_quantize_e4m3(const dcd_matrix *A, uint8_t *q, int64_t ldq, float *row_scale,
+                                        void *stream)
+{
+    if (!A || A->fmt != DCD_DENSE || A->m < 1 || A->n < 1 || A->ld < A->n || !A->values || A->m > INT32_MAX)
+        return DCD_EINVAL;
+    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
+    if (!q || !row_scale || ldq < A->n) return DCD_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    ComponentBufs cb;
+    cb.st = st;
+    DCD_TRY(cudaMallocAsync(&cb.mem, 256, st));
+    int *err = (int *)cb.mem;
+    DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, nullptr, q, ldq, row_scale, A->m, err,
+                                 st));
+    return finish_component(err, st);
+}
 
 extern "C" dcd_status dcd_kernel_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
                                        int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,

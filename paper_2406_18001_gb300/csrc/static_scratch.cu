@@ -86,6 +86,7 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
     if (A && A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;  // the CSR block needs allocated scratch
     if (!A || A->fmt != DCD_DENSE || A->m < 1 || A->n < 1 || A->ld < A->n || !A->values || A->m > INT32_MAX)
         return DCD_EINVAL;
+    if (A->dtype == DCD_FP8E4M3 || prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
     if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
     if (!kernel_ok(k)) return DCD_EINVAL;
     if (prec != DCD_PREC_FP64 && prec != DCD_PREC_BF16 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16X3 &&

@@ -129,17 +129,23 @@ def sweep_grid(count: int = 256, sig_lo: float = 0.1, sig_hi: float = 10.0,
     return pairs[:count]
 
 
+def ill_conditioned_mixer(n: int, seed: int = 0, cond: float = 1e4, row_norm2: float = 64.0) -> np.ndarray:
+    """The n x n factor diag(sig) W^T of ill_conditioned (float32): rows of
+    A are z^T diag(sig) W^T with z ~ N(0, I)."""
+    gw = _rng(seed, 5)
+    W, _ = np.linalg.qr(gw.standard_normal((n, n)))
+    sig = np.logspace(-np.log10(cond), 0.0, n)
+    sig *= np.sqrt(row_norm2 / np.sum(sig ** 2))
+    return (sig[:, None] * W.T).astype(np.float32)
+
+
 def ill_conditioned(m: int, n: int, seed: int = 0, cond: float = 1e4, row_norm2: float = 64.0,
                     dtype=np.float32, row_start: int = 0, chunk: int = 65536) -> np.ndarray:
     """A = Z diag(sig) W^T with Z ~ N(0,1), W a seeded random orthogonal n x n
     matrix and sig log-spaced over [1/cond, 1] * c, where c makes the expected
     squared row norm equal to row_norm2.  Rows are drawn in fixed chunks from
     per-chunk streams, so any row range is reproducible on its own."""
-    gw = _rng(seed, 5)
-    W, _ = np.linalg.qr(gw.standard_normal((n, n)))
-    sig = np.logspace(-np.log10(cond), 0.0, n)
-    sig *= np.sqrt(row_norm2 / np.sum(sig ** 2))
-    B = (sig[:, None] * W.T).astype(np.float32)
+    B = ill_conditioned_mixer(n, seed, cond, row_norm2)
     out = np.empty((m, n), dtype=dtype)
     r = 0
     while r < m:
