@@ -205,9 +205,12 @@ struct FusedUpdate {
 // scratch of recur_cluster_scratch_bytes (super-block inverses, repeat masks and links)
 int recur_cluster_size(int nblk, int b, int rounds);
 size_t recur_cluster_scratch_bytes(int64_t nblk, int b);
+// rhs: the right-hand sides by position (default -g[S]), for a diagonal panel of a longer chain
 cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                  double lambda, double mdiag, double *g, int rounds, void *scratch, double *delta,
-                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st);
+                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st,
+                                 const double *rhs = nullptr);
+int recur_cluster_panel_blocks(int b, int rounds);
 // 2-D tensor map over a row-major fp32 matrix (rows x cols, leading dimension
 // ld elements, ld * 4 a multiple of 16), box of box_rows x box_cols, no
 // swizzle, out-of-range elements read as zero (block_tc.cu)

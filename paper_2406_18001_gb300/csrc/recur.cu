@@ -14,6 +14,8 @@
 #include "dcd_internal.cuh"
 #include "ptx.cuh"
 
+#include <algorithm>
+
 namespace dcd {
 
 namespace {
@@ -531,6 +533,81 @@ __global__ void __launch_bounds__(256) bdcd_residual_kernel(const KT *Kss, int64
     if (lane == 0) rho[p] = rhs64[p] - (acc * inv_lambda + mdiag * dm);
 }
 
+// Chains longer than one cluster launch takes: blocked forward substitution.
+// The chain is cut into diagonal panels of pb blocks; each panel is solved by
+// the cluster recurrence (with its own refinement rounds) from right-hand
+// sides that already hold every earlier panel's contribution, and after each
+// panel one launch moves its contribution into the right-hand sides of all
+// later rows:
+//   rhs_p (= -g[S_p] for the first panel) -= sum_{q in panel} Kss[p][q] delta_q / lambda
+//                                            + mdiag * sum_{q in panel, S_q = S_p} delta_q
+// One warp per later row, FP64 sums of the FP32 Gram entries times FP64 delta.
+__global__ void bdcd_panel_update_kernel(const float *Kss, int64_t ldk, const int32_t *S, int r0, int rows, int sb,
+                                         double inv_lambda, double mdiag, const double *g, const double *delta,
+                                         double *rhs, int first)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t p = r0 + rows + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (p >= sb) return;
+    const float *kr = Kss + p * ldk + r0;
+    const int32_t ip = S[p];
+    double a0 = 0.0, a1 = 0.0, dm = 0.0;
+    int q = lane;
+    for (; q + 32 < rows; q += 64) {
+        const double d0 = delta[r0 + q], d1 = delta[r0 + q + 32];
+        a0 = fma((double)kr[q], d0, a0);
+        a1 = fma((double)kr[q + 32], d1, a1);
+        if (S[r0 + q] == ip) dm += d0;
+        if (S[r0 + q + 32] == ip) dm += d1;
+    }
+    if (q < rows) {
+        const double d0 = delta[r0 + q];
+        a0 = fma((double)kr[q], d0, a0);
+        if (S[r0 + q] == ip) dm += d0;
+    }
+    double acc = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        dm += __shfl_xor_sync(0xffffffffu, dm, o);
+    }
+    if (lane == 0) rhs[p] = (first ? -g[ip] : rhs[p]) - (acc * inv_lambda + mdiag * dm);
+}
+
+// scratch: the cluster scratch of one panel, then sb FP64 right-hand sides
+size_t blocked_cluster_scratch_bytes(int64_t nblk, int b)
+{
+    if (b % 4 != 0 || b > 32) return 0;
+    const int64_t q = b >= 32 ? 1 : 32 / b;
+    const size_t cl = (recur_cluster_scratch_bytes(std::min<int64_t>(nblk, 32 * q), b) + 255) / 256 * 256;
+    return cl + sizeof(double) * (size_t)nblk * b;
+}
+
+cudaError_t blocked_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int pb, double lambda,
+                            double mdiag, const double *g, int rounds, char *scratch, double *delta, double *w64,
+                            float *w32, int *err, cudaStream_t st)
+{
+    const int sb = nblk * b;
+    const int64_t q = b >= 32 ? 1 : 32 / b;
+    double *rhs = (double *)(scratch + (recur_cluster_scratch_bytes(std::min<int64_t>(nblk, 32 * q), b) + 255) / 256 * 256);
+    for (int p0 = 0; p0 < nblk; p0 += pb) {
+        const int nb = std::min(pb, nblk - p0), r0 = p0 * b, rows = nb * b;
+        const int P = recur_cluster_size(nb, b, rounds);
+        if (P <= 0) return cudaErrorInvalidValue;
+        cudaError_t e = launch_recur_cluster(Kss + (int64_t)r0 * ldk + r0, ldk, S + r0, nb, b, P, lambda, mdiag,
+                                             const_cast<double *>(g), rounds, scratch, delta + r0,
+                                             w64 ? w64 + r0 : nullptr, w32 ? w32 + r0 : nullptr, nullptr, err, st,
+                                             p0 ? rhs + r0 : nullptr);
+        if (e != cudaSuccess) return e;
+        if (r0 + rows < sb) {
+            const int later = sb - r0 - rows;
+            bdcd_panel_update_kernel<<<(unsigned)((later + 7) / 8), 256, 0, st>>>(
+                Kss, ldk, S, r0, rows, sb, 1.0 / lambda, mdiag, g, delta, rhs, p0 == 0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 template <typename KT, int BT, int NT>
 cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda, double mdiag,
                          const double *g, int refinements, char *scratch, double *delta, double *w64, float *w32,
@@ -558,6 +635,10 @@ cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
             if (e == cudaSuccess && upd) upd->done = true;
             return e;
         }
+        const int pb = recur_cluster_panel_blocks(b, refinements + 1);
+        if (pb > 0 && pb < nblk && blocked_cluster_scratch_bytes(nblk, b) <= recur_bdcd_scratch_bytes(nblk, b))
+            return blocked_cluster((const float *)Kss, ldk, S, nblk, b, pb, lambda, mdiag, g, refinements + 1,
+                                   scratch, delta, w64, w32, err, st);
     }
     if (L.total > CHAIN_SMEM_MAX) return cudaErrorInvalidValue;
     bdcd_inverse_kernel<KT, BT><<<(unsigned)((nblk + 3) / 4), 128, 0, st>>>(Kss, ldk, nblk, b, (float)(1.0 / lambda),
@@ -632,6 +713,8 @@ size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
     size_t generic = sizeof(double) * (size_t)nblk * b * (b + 1);
     const size_t cluster = recur_cluster_scratch_bytes(nblk, b);
     if (cluster > refined) refined = cluster;
+    const size_t blocked = blocked_cluster_scratch_bytes(nblk, b);
+    if (blocked > refined) refined = blocked;
     return refined > generic ? refined : generic;
 }
 

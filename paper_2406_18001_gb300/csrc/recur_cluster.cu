@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     bdcd_cluster_kernel(const __grid_constant__ CUtensorMap kmap, const int32_t *S, const float *X,
                         const float *Ng, const uint32_t *Mg, const int32_t *nextg, int nblk, int b, double lambda,
                         double mdiag, double *g, int rounds, double *delta, double *w64, float *w32, double *alpha,
-                        uint64_t *ctr, uint64_t ctr_advance, int *err)
+                        uint64_t *ctr, uint64_t ctr_advance, const double *rhs_in, int *err)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int P = (int)gridDim.x;  // the grid is one cluster
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         // ---- the chain of round r ----
         // r'_J: all updates but the one from J-1, which N_J = X_J L_{J,J-1} applies after the product:
         // Delta_J = X_J r'_J - N_J Delta_{J-1}.  X_J r'_J is formed while Delta_{J-1} is on its way.
-        const double rhs = lane < rows ? -g[S[row]] : 0.0;
+        const double rhs = lane < rows ? (rhs_in ? rhs_in[row] : -g[S[row]]) : 0.0;
         float rr = r == 0 ? (float)rhs : 0.f;  // round 0: -g_S minus updates; round 1: sum of updates
         float hi = 0.f, lo = 0.f;              // round 0: double-single sum of L_{row, T<J} Delta0_T
         bool alive = J == 0 || wait_local(pbar, abort_flag, err);
@@ -641,7 +641,8 @@ size_t recur_cluster_scratch_bytes(int64_t nblk, int b)
 
 cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                  double lambda, double mdiag, double *g, int rounds, void *scratch, double *delta,
-                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st)
+                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st,
+                                 const double *rhs)
 {
     const ClGeom G = cl_geom(nblk, b);
     const int sb = nblk * b;
@@ -681,7 +682,18 @@ cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S
     return cudaLaunchKernelEx(&cfg, kfn, kmap, S, (const float *)X, (const float *)N, (const uint32_t *)M,
                               (const int32_t *)next, nblk, b, lambda, mdiag, g, rounds, delta, w64, w32,
                               upd ? upd->alpha : (double *)nullptr, upd ? upd->ctr : (uint64_t *)nullptr,
-                              upd ? upd->ctr_advance : (uint64_t)0, err);
+                              upd ? upd->ctr_advance : (uint64_t)0, rhs, err);
+}
+
+// The largest diagonal panel (in blocks) one cluster launch solves: the
+// blocked recurrence for longer chains runs panels of this size.
+int recur_cluster_panel_blocks(int b, int rounds)
+{
+    if (b % 4 != 0 || b > 32) return 0;
+    const int q = cl_geom(1, b).q;
+    for (int nsup = CL_NSUP_MAX; nsup >= 2; nsup -= 2)
+        if (recur_cluster_size(nsup * q, b, rounds) > 0) return nsup * q;
+    return 0;
 }
 
 }  // namespace dcd

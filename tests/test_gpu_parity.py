@@ -368,6 +368,32 @@ def test_bdcd_mixed_matches_oracle(prec, s, b):
     assert abs(f_got - f_want) <= OBJ_TOL[prec] * abs(f_want)
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp8"])
+@pytest.mark.parametrize("m,s,b", [(3000, 48, 32), (700, 128, 32), (5000, 100, 16), (2500, 300, 8)])
+def test_bdcd_long_chain_blocked_panels(prec, m, s, b):
+    """s*b above one cluster launch (1024 rows): diagonal panels of the
+    cluster recurrence joined by FP64 updates of the later right-hand sides;
+    m = 700 with s*b = 4096 repeats every index several times per step, also
+    across panels.  fp8: the oracle runs on the dequantised rows."""
+    p = inputs.krr_dense(m=m, n=64, seed=21, dtype=np.float32)
+    lam, H = 1e-2, 2 * s
+    kb, ko = B().kernel("rbf", gamma=0.5), oracle.kernel("rbf", gamma=0.5)
+    if prec == "fp8":
+        q, sc = oracle.quantize_e4m3_rows(p.A)
+        A64 = oracle.dequantize_e4m3_rows(q, sc)
+        Ad = B().Fp8(dev(q), dev(sc))
+    else:
+        A64 = p.A.astype(np.float64)
+        Ad = dev(p.A)
+    al, gr, st, _ = B().krr_solve(Ad, dev(p.y), kb, lam, b, s, H, seed=5, prec=prec)
+    want = oracle.bdcd_krr(A64, p.y, ko, lam, b, H, seed=5)
+    a = al.cpu().numpy()
+    assert rel(a, want) < ALPHA_TOL.get(prec, 1e-4)
+    f_got = oracle.krr_objective(A64, p.y, ko, lam, a)
+    f_want = oracle.krr_objective(A64, p.y, ko, lam, want)
+    assert abs(f_got - f_want) <= OBJ_TOL.get(prec, 1e-6) * abs(f_want)
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
 def test_dcd_mixed_matches_oracle(prec):
     p = inputs.blobs(m=700, n=64, seed=13)
