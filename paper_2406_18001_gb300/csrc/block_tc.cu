@@ -13,17 +13,22 @@
 //   store: writes K_ij (FP32) -- used for the sampled Gram, so that the
 //          recurrence sees exactly the values the apply pass uses.
 //
-// CTA layout (192 threads, one CTA per SM, persistent over 128-row tiles):
+// CTA layout (320 threads, one CTA per SM, persistent over 128-row tiles):
 //   warp 0      TMA producer: 128-byte-swizzled k-blocks of A and B into a
 //               4-stage shared-memory ring (mbarrier complete_tx)
 //   warp 1      TMEM allocator and MMA issuer (one thread); accumulators are
 //               double-buffered (2 x BN columns) so the epilogue of one
 //               N-chunk overlaps the MMAs of the next
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns per load, one
-//               thread per row
+//   warps 2..9  epilogue: tcgen05.ld 32 lanes x 32 columns per load, one
+//               thread per row; warp w reads TMEM lanes 32 (w % 4)..+31, warps
+//               2..5 take the first half of each N-chunk's columns and warps
+//               6..9 the second half (two warps per scheduler hide the load and
+//               MUFU latency); the second half's row sums reach the first half
+//               through shared memory once per tile, in a fixed order
 // Every mbarrier wait is bounded; on timeout the CTA records DEV_TIMEOUT,
 // drains its in-flight copies and MMAs (bounded), frees TMEM and returns.
 #include "dcd_internal.cuh"
+#include "ptx.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -49,8 +54,9 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
 // q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
 constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4;
-constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
-constexpr int NTHREADS = 192;
+constexpr int XCH_BYTES = 2 * BM * 8;  // row sums of the second epilogue half, double-buffered
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/ + XCH_BYTES;
+constexpr int NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
 
@@ -176,6 +182,34 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+// tcgen05.ld of 32 lanes x 32 columns, issued and waited for separately (the
+// next group's load overlaps this group's arithmetic); the wait names the
+// destination registers, so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -188,7 +222,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tmem_ld_wait(r);
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
@@ -274,7 +308,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *tfull = bars + 2 * STAGES;   // 2
     uint64_t *tempty = tfull + 2;          // 2
     uint64_t *drain = tempty + 2;          // 1
-    uint32_t *tmem_holder = (uint32_t *)(drain + 1);
+    uint64_t *xfull = drain + 1;           // 2: second-half row sums written
+    uint64_t *xfree = xfull + 2;           // 2: ... and consumed
+    double *xch = (double *)(smem + RING_BYTES + 256);  // [2][BM]
+    uint32_t *tmem_holder = (uint32_t *)(xfree + 2);
     volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -285,7 +322,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], 8);
+            mbar_init(&xfull[b], 4);
+            mbar_init(&xfree[b], 4);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -387,12 +426,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ------------------------------------------------------ epilogue --
-        const int quarter = warp & 3;  // warps 2,3,4,5 -> TMEM lanes 64,96,0,32
+        const int quarter = warp & 3;  // warps 2..9 -> TMEM lanes 64,96,0,32,64,96,0,32
+        const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        uint32_t acc_it = 0;
+        const int ngrp = bn / 32, cg0 = half ? ngrp / 2 : 0, cg1 = half ? ngrp : ngrp / 2;
+        uint32_t acc_it = 0, item_it = 0;
         bool ok = true;
-        for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
+        for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x, ++item_it) {
             int tile, c0, c1;
             item_range(a, item, tile, c0, c1);
             const int64_t row = (int64_t)tile * BM + row_in_tile;
@@ -411,7 +452,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 fence_after();
-                for (int cg = 0; cg < bn / 32; ++cg) {
+                for (int cg = cg0; cg < cg1; ++cg) {
                     float v[32];
                     tmem_ld32(tmem_base + lane_addr + buf * (uint32_t)bn + (uint32_t)(cg * 32), v);
                     const int64_t colbase = (int64_t)nc * bn + cg * 32;
@@ -455,7 +496,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
-            if (ok && !a.store && row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
+            if (!ok || a.store) continue;
+            // row sum = first half + second half (this order): the second half hands its part over
+            // in shared memory (double-buffered by tile; xfree keeps a buffer until it is read)
+            const uint32_t xb = item_it & 1, xph = (item_it >> 1) & 1;
+            double *xc = xch + xb * BM;
+            if (half) {
+                const bool fr = mbar_wait(&xfree[xb], xph ^ 1, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, fr)) {
+                    ok = false;
+                    break;
+                }
+                xc[row_in_tile] = racc;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xfull[xb]);
+            } else {
+                const bool fu = mbar_wait(&xfull[xb], xph, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, fu)) {
+                    ok = false;
+                    break;
+                }
+                racc += xc[row_in_tile];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xfree[xb]);
+                if (row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
+            }
         }
     }
     fence_before();
@@ -463,6 +528,333 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ------------------------------------------------ two-SM apply kernel --
+// The apply form on CTA pairs (clusters of 2, tcgen05 cta_group::2).  The
+// pair owns a 256-row tile; the even CTA issues M = 256 MMAs whose A rows come
+// 128 from each CTA's shared memory and whose N-chunk of B is split in two
+// halves, one per CTA.  A CTA therefore receives 128 + bn/2 rows per k-block
+// instead of 128 + bn -- a third less operand traffic per MMA -- and one MMA
+// instruction does twice the work.  Each CTA's tensor memory holds its own
+// 128 rows x bn accumulator columns, read back by its own 8 epilogue warps
+// exactly as in block_tc_kernel.
+//   full[s]   (even CTA) its producer arrives expecting the bytes of both
+//             CTAs' loads, which complete_tx on it (the odd CTA's may land
+//             first: the transaction count may dip below zero meanwhile)
+//   empty[s]  (both) the MMA commit, multicast to the pair
+//   tfull[b]  (both) the MMA commit of a finished accumulator, multicast
+//   tempty[b] (even CTA) all 16 epilogue warps of the pair arrive
+// Every wait is bounded as in block_tc_kernel; the pair meets at a cluster
+// barrier after set-up and before tensor memory is released.
+constexpr int BM2 = 2 * BM;                          // rows per pair tile
+constexpr int B2_STAGE = (BN_MAX / 2) * ROW_BYTES;   // 16 KB: half of an N-chunk
+constexpr int RING2_BYTES = 6 * (A_STAGE + B2_STAGE);  // 6 single or 3 split stages
+constexpr int CST_FLOATS = 3 * 128;                   // staged column terms per epilogue warp
+constexpr int SMEM2_BYTES = RING2_BYTES + 1024 + 256 + XCH_BYTES + 8 * CST_FLOATS * 4;
+
+// arrive on an mbarrier of the pair given by its shared::cluster address
+__device__ __forceinline__ void arrive_cl(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// TMA tile load into this CTA's shared memory, completing on an mbarrier of
+// either CTA of the pair (cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+        "%4}], [%2];" ::"r"(su32(dst)),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+template <int MK>
+__device__ __forceinline__ void mma2(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    if (MK == 1)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    else if (MK == 2)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// arrive on `bar` in both CTAs of the pair once the issued MMAs complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_own2(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+template <int MODE, int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    block_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+{
+    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3;
+    constexpr bool FP8 = MODE == MODE_FP8;
+    constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
+    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3;
+    constexpr int STAGES = SPLIT ? 3 : 6;
+    constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
+    constexpr int B_ST = SPLIT ? 2 * B2_STAGE : B2_STAGE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_ST;
+    uint64_t *bars = (uint64_t *)(smem + RING2_BYTES);
+    uint64_t *full = bars;                 // STAGES (even CTA)
+    uint64_t *empty = bars + STAGES;       // STAGES
+    uint64_t *tfull = bars + 2 * STAGES;   // 2
+    uint64_t *tempty = tfull + 2;          // 2 (even CTA)
+    uint64_t *drain = tempty + 2;          // 1
+    uint64_t *xfull = drain + 1;           // 2
+    uint64_t *xfree = xfull + 2;           // 2
+    double *xch = (double *)(smem + RING2_BYTES + 256);  // [2][BM]
+    uint32_t *tmem_holder = (uint32_t *)(xfree + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+
+    const uint32_t rank = ptx::cluster_ctarank();
+    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 16);
+            mbar_init(&xfull[b], 4);
+            mbar_init(&xfree[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    ptx::cluster_sync();  // both CTAs' barriers exist before any cross-CTA arrive
+    fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const int bn = a.bn, bh = bn / 2;
+    const int kb_elems = TF32 ? 32 : FP8 ? 128 : 64;
+    const uint32_t full0 = ptx::mapa(su32(full), 0), tempty0 = ptx::mapa(su32(tempty), 0);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- producer --
+            uint32_t it = 0;
+            bool ok = true;
+            const uint32_t bytes = (uint32_t)(2 * (SPLIT ? 2 : 1) * (A_STAGE + bh * ROW_BYTES));  // both CTAs'
+            for (int item = pair; ok && item < a.items; item += npairs)
+                for (int nc = 0; ok && nc < a.nchunks; ++nc)
+                    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = full0 + 8u * s;
+                        const int ya = item * BM2 + (int)rank * BM, yb = nc * bn + (int)rank * bh;
+                        if (rank == 0) mbar_expect_tx(&full[s], bytes);
+                        tma_load_2d_pair(sA + s * A_ST, &tmA, fb, kb * kb_elems, ya);
+                        tma_load_2d_pair(sB + s * B_ST, &tmB, fb, kb * kb_elems, yb);
+                        if (SPLIT) {
+                            tma_load_2d_pair(sA + s * A_ST + A_STAGE, &tmA, fb, a.lo_off + kb * kb_elems, ya);
+                            tma_load_2d_pair(sB + s * B_ST + B2_STAGE, &tmB, fb, a.lo_off + kb * kb_elems, yb);
+                        }
+                    }
+            // the last stages' empties arrive after the final MMAs: wait for them, so that no
+            // commit is still addressed to this CTA when the pair leaves (bounded)
+            const uint32_t first = it > STAGES ? it - STAGES : 0;
+            for (uint32_t j = first; j < it; ++j) mbar_drain(&empty[j % STAGES], ((j / STAGES) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // --------------------------------------------------------- MMA --
+            const uint32_t idesc = make_idesc(TF32 ? 2 : FP8 ? 0 : 1, bn, BM2);
+            uint32_t it = 0, acc_it = 0;
+            bool ok = true, issued = false;
+            for (int item = pair; ok && item < a.items; item += npairs)
+                for (int nc = 0; ok && nc < a.nchunks; ++nc, ++acc_it) {
+                    const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                    if (!mbar_wait(&tempty[buf], aph ^ 1, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t dtm = tmem_base + buf * (uint32_t)bn;
+                    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&full[s], ph, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t ab = su32(sA + s * A_ST), bb = su32(sB + s * B_ST);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            mma2<MK>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
+                                     (kb > 0 || k > 0) ? 1u : 0u);
+                            if (SPLIT) {
+                                mma2<MK>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + B2_STAGE + 32 * k), idesc, 1u);
+                                mma2<MK>(dtm, sw128_desc(ab + A_STAGE + 32 * k), sw128_desc(bb + 32 * k), idesc, 1u);
+                            }
+                        }
+                        issued = true;
+                        mma_commit_pair(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(&tfull[buf]);
+                }
+            if (issued) {  // every MMA (and its commits) done before the pair tears down
+                mma_commit_own2(drain);
+                mbar_drain(drain, 0);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue --
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        const int ngrp = bn / 32, cg0 = half ? ngrp / 2 : 0, cg1 = half ? ngrp : ngrp / 2;
+        // this warp's column terms of the current chunk (its half: <= 4 groups): K-term, coefficient, scale
+        float *cst = (float *)(smem + RING2_BYTES + 256 + XCH_BYTES) + (warp - 2) * CST_FLOATS;
+        uint32_t acc_it = 0, item_it = 0;
+        bool ok = true;
+        for (int item = pair; ok && item < a.items; item += npairs, ++item_it) {
+            const int64_t row = (int64_t)item * BM2 + (int64_t)rank * BM + row_in_tile;
+            const bool row_ok = row < a.nrows_out;
+            const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
+            const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
+            const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
+            double racc = 0.0;
+            // one 32-column group: terms from the staged columns (4 per shared-memory load), the
+            // same sums in the same order as a column-by-column loop
+            auto group = [&](const uint32_t(&r)[32], int j0) {
+                const float4 *h4 = (const float4 *)(cst + j0), *w4 = (const float4 *)(cst + 128 + j0),
+                             *s4 = (const float4 *)(cst + 256 + j0);
+                float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    const float4 hh = KIND == DCD_RBF ? h4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 ww = w4[q4];
+                    float c0 = __uint_as_float(r[4 * q4]), c1 = __uint_as_float(r[4 * q4 + 1]);
+                    float c2 = __uint_as_float(r[4 * q4 + 2]), c3 = __uint_as_float(r[4 * q4 + 3]);
+                    if (FP8) {
+                        const float4 ss = s4[q4];
+                        c0 *= ss.x;
+                        c1 *= ss.y;
+                        c2 *= ss.z;
+                        c3 *= ss.w;
+                    }
+                    p0 = fmaf(kf32<KIND>(c0, hr, hh.x, rf, a), ww.x, p0);
+                    p1 = fmaf(kf32<KIND>(c1, hr, hh.y, rf, a), ww.y, p1);
+                    p0 = fmaf(kf32<KIND>(c2, hr, hh.z, rf, a), ww.z, p0);
+                    p1 = fmaf(kf32<KIND>(c3, hr, hh.w, rf, a), ww.w, p1);
+                }
+                racc += (double)p0 + (double)p1;
+            };
+            for (int nc = 0; nc < a.nchunks; ++nc, ++acc_it) {
+                const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                // stage this warp's columns while the accumulator is still being formed
+                const int64_t cbase = (int64_t)nc * bn + cg0 * 32;
+                for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
+                    if (KIND == DCD_RBF) cst[j] = a.col_h[cbase + j];
+                    cst[128 + j] = a.col_w[cbase + j];
+                    if (FP8) cst[256 + j] = a.col_s[cbase + j];
+                }
+                __syncwarp();
+                const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, seen)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t tb = tmem_base + lane_addr + buf * (uint32_t)bn;
+                uint32_t ra[32], rb[32];
+                if (cg0 < cg1) {
+                    tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
+                    tmem_ld_wait(ra);
+                }
+                for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
+                    if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
+                    group(ra, (cg - cg0) * 32);
+                    if (cg + 1 < cg1) {
+                        tmem_ld_wait(rb);
+                        if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
+                        group(rb, (cg + 1 - cg0) * 32);
+                        if (cg + 2 < cg1) tmem_ld_wait(ra);
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) arrive_cl(tempty0 + 8u * buf);
+            }
+            if (!ok) break;
+            const uint32_t xb = item_it & 1, xph = (item_it >> 1) & 1;
+            double *xc = xch + xb * BM;
+            if (half) {
+                const bool fr = mbar_wait(&xfree[xb], xph ^ 1, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, fr)) {
+                    ok = false;
+                    break;
+                }
+                xc[row_in_tile] = racc;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xfull[xb]);
+            } else {
+                const bool fu = mbar_wait(&xfull[xb], xph, abort_flag, a.err);
+                if (!__all_sync(0xffffffffu, fu)) {
+                    ok = false;
+                    break;
+                }
+                racc += xc[row_in_tile];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&xfree[xb]);
+                if (row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    ptx::cluster_sync();  // the pair is done with each other's barriers and tensor memory
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                      : "memory");
 }
 
@@ -524,6 +916,38 @@ cudaError_t launch_mode(int grid, const CUtensorMap &mA, const CUtensorMap &mB, 
     return launch_kind<MODE, DCD_LINEAR>(grid, mA, mB, a, st);
 }
 
+template <int MODE, int KIND>
+cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st)
+{
+    auto kfn = block_tc2_kernel<MODE, KIND>;
+    static int max_pairs = 0;  // co-resident pairs, queried once per instantiation (before any capture)
+    if (!max_pairs) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM2_BYTES);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(NTHREADS, 1, 1);
+        cfg.dynamicSmemBytes = SMEM2_BYTES;
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, kfn, &cfg);
+        if (e != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        max_pairs = n;
+    }
+    if (npairs > max_pairs) npairs = max_pairs;
+    kfn<<<2 * npairs, NTHREADS, SMEM2_BYTES, st>>>(mA, mB, a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, int kind,
+                         cudaStream_t st)
+{
+    if (kind == DCD_RBF) return launch_kind2<MODE, DCD_RBF>(npairs, mA, mB, a, st);
+    if (kind == DCD_POLY) return launch_kind2<MODE, DCD_POLY>(npairs, mA, mB, a, st);
+    return launch_kind2<MODE, DCD_LINEAR>(npairs, mA, mB, a, st);
+}
+
 }  // namespace
 
 bool tc_available()
@@ -568,8 +992,10 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     // store mode (the sampled Gram) has few rows: narrower N-chunks give
     // more work items and spread them over more SMs
     if (out != nullptr) bn = bn > 64 ? 64 : bn;
+    // the apply form runs on CTA pairs (each CTA stages half of an N-chunk of B)
+    const bool pair = out == nullptr;
     CUtensorMap mA, mB;
-    if (!make_map(&mA, Aop, BM) || !make_map(&mB, Bop, bn)) return cudaErrorInvalidValue;
+    if (!make_map(&mA, Aop, BM) || !make_map(&mB, Bop, pair ? bn / 2 : bn)) return cudaErrorInvalidValue;
     TcArgs a;
     a.lo_off = (int)Aop.n_pad;
     a.row_h = row_h;
@@ -583,7 +1009,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.ldo = ldo;
     a.nrows_out = nrows_out;
     a.ncols = ncols;
-    a.num_tiles = (int)((nrows_out + BM - 1) / BM);
+    a.num_tiles = (int)((nrows_out + (pair ? 2 * BM : BM) - 1) / (pair ? 2 * BM : BM));
     a.nchunks = (int)((ncols + bn - 1) / bn);
     a.kblocks = (int)(Aop.n_pad / kb_elems);
     a.bn = bn;
@@ -598,6 +1024,14 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (pair) {
+        const int npairs = a.items < sms / 2 ? a.items : sms / 2;
+        if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st);
+        if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st);
+        if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st);
+        if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st);
+        return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st);
     }
     int grid = a.items < sms ? a.items : sms;
     if (Aop.kind == PACK_TF32) return launch_mode<MODE_TF32>(grid, mA, mB, a, kp.kind, st);

@@ -551,21 +551,20 @@ __global__ void bdcd_panel_update_kernel(const float *Kss, int64_t ldk, const in
     if (p >= sb) return;
     const float *kr = Kss + p * ldk + r0;
     const int32_t ip = S[p];
-    double a0 = 0.0, a1 = 0.0, dm = 0.0;
-    int q = lane;
-    for (; q + 32 < rows; q += 64) {
-        const double d0 = delta[r0 + q], d1 = delta[r0 + q + 32];
-        a0 = fma((double)kr[q], d0, a0);
-        a1 = fma((double)kr[q + 32], d1, a1);
-        if (S[r0 + q] == ip) dm += d0;
-        if (S[r0 + q + 32] == ip) dm += d1;
+    // four independent FP64 chains per lane; the (rare) repeat term only when some lane matches
+    double a[4] = {0.0, 0.0, 0.0, 0.0}, dm = 0.0;
+    for (int q0 = 0; q0 < rows; q0 += 128) {  // warp-uniform bounds
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + 32 * u + lane;
+            const bool in = q < rows;
+            const double d = in ? delta[r0 + q] : 0.0;
+            a[u] = fma(in ? (double)kr[q] : 0.0, d, a[u]);
+            const bool hit = in && S[r0 + q] == ip;
+            if (__any_sync(0xffffffffu, hit)) dm += hit ? d : 0.0;
+        }
     }
-    if (q < rows) {
-        const double d0 = delta[r0 + q];
-        a0 = fma((double)kr[q], d0, a0);
-        if (S[r0 + q] == ip) dm += d0;
-    }
-    double acc = a0 + a1;
+    double acc = (a[0] + a[1]) + (a[2] + a[3]);
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
         dm += __shfl_xor_sync(0xffffffffu, dm, o);

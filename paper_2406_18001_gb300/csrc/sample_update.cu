@@ -439,123 +439,62 @@ cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStr
 // --------------------------------------------------------- alpha update ---
 // alpha_{sk+s} = alpha_sk + sum_t V_t delta_t (Algorithms 2 and 4) and the
 // diagonal part of the gradient update, g[S_j] += diag * delta_j (omega for
-// K-SVM-L2, m for K-RR).  Repeated indices are merged deterministically: the
-// pairs (index, position) are bitonic-sorted in shared memory, and the first
-// entry of each run of equal indices adds the run's deltas in position order.
-// One CTA; cnt <= 8192.  Also advances the stream counter.
-constexpr int UPD_THREADS = 1024;
+// K-SVM-L2, m for K-RR).  Repeated indices are merged deterministically: a
+// position with no earlier occurrence of its index is a run head and adds the
+// deltas of its index's occurrences in position order.  One warp per
+// position, S staged in shared memory: the warp compares 32 positions per
+// step (ballot), so a position costs cnt / 32 steps.  cnt <= 8192.  Also
+// advances the stream counter.
+constexpr int UPD_MAX = 8192;
+constexpr int UPD_WARPS = 8;
 
-__global__ void __launch_bounds__(UPD_THREADS) update_kernel(const int32_t *S, const double *delta, int cnt, int P,
-                                                             double diag, double *alpha, double *g, uint64_t *ctr,
-                                                             uint64_t ctr_advance, int64_t m, int *err)
+__global__ void __launch_bounds__(UPD_WARPS * 32)
+    update_kernel(const int32_t *S, const double *delta, int cnt, double diag, double *alpha, double *g,
+                  uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
 {
-    extern __shared__ unsigned long long key[];  // P entries: (index << 32) | position
-    for (int j = threadIdx.x; j < P; j += UPD_THREADS) {
-        unsigned long long k = ~0ull;
-        if (j < cnt) {
-            const int32_t i = S[j];
-            if (i < 0 || i >= m) set_error(err, DEV_BAD_INDEX);
-            k = ((unsigned long long)(uint32_t)i << 32) | (unsigned)j;
-        }
-        key[j] = k;
-    }
-    if (threadIdx.x == 0 && ctr) *ctr += ctr_advance;
+    __shared__ int32_t sS[UPD_MAX];
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) sS[q] = S[q];
     __syncthreads();
-    for (int size = 2; size <= P; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < P / 2; t += UPD_THREADS) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long a = key[lo], b = key[hi];
-                if ((a > b) == up) {
-                    key[lo] = b;
-                    key[hi] = a;
-                }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr) *ctr += ctr_advance;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * UPD_WARPS;
+    for (int p = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); p < cnt; p += nw) {  // warp-uniform
+        const int32_t key = sS[p];
+        if (key < 0 || key >= m) {
+            if (lane == 0) set_error(err, DEV_BAD_INDEX);
+            continue;
+        }
+        bool head = true;
+        for (int q0 = 0; q0 < p && head; q0 += 32) {
+            const int q = q0 + lane;
+            head = !__any_sync(0xffffffffu, q < p && sS[q] == key);
+        }
+        if (!head) continue;
+        double sum = 0.0;  // occurrences at positions >= p, in position order (every lane the same)
+        for (int q0 = p; q0 < cnt; q0 += 32) {
+            const int q = q0 + lane;
+            unsigned mk = __ballot_sync(0xffffffffu, q < cnt && sS[q] == key);
+            while (mk) {
+                sum += delta[q0 + __ffs(mk) - 1];
+                mk &= mk - 1;
             }
-            __syncthreads();
         }
-    for (int r = threadIdx.x; r < cnt; r += UPD_THREADS) {
-        const unsigned long long k = key[r];
-        const uint32_t i = (uint32_t)(k >> 32);
-        if (r > 0 && (uint32_t)(key[r - 1] >> 32) == i) continue;  // not the head of its run
-        if ((int64_t)i >= m) continue;
-        double sum = delta[(uint32_t)k];
-        for (int q = r + 1; q < cnt && (uint32_t)(key[q] >> 32) == i; ++q) sum += delta[(uint32_t)key[q]];
-        alpha[i] += sum;
-        g[i] += diag * sum;
-    }
-}
-
-// The same update for cnt <= UPD_SCAN_MAX without a sort: one thread per
-// position, S staged in shared memory; a position with no earlier occurrence
-// of its index is a run head and adds the deltas of its index's occurrences
-// in position order (the order of the sorted form, so the results agree bit
-// for bit).  O(cnt) work per thread spread over cnt threads.
-constexpr int UPD_SCAN_MAX = 2048;
-constexpr int UPD_SCAN_THREADS = 64;
-
-__global__ void __launch_bounds__(UPD_SCAN_THREADS)
-    update_scan_kernel(const int32_t *S, const double *delta, int cnt, double diag, double *alpha, double *g,
-                       uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
-{
-    __shared__ __align__(16) int32_t sS[UPD_SCAN_MAX];
-    const int c4 = (cnt + 3) & ~3;
-    for (int q = threadIdx.x; q < c4; q += UPD_SCAN_THREADS) sS[q] = q < cnt ? S[q] : -1;
-    __syncthreads();
-    const int p = blockIdx.x * UPD_SCAN_THREADS + threadIdx.x;
-    if (p == 0 && ctr) *ctr += ctr_advance;
-    if (p >= cnt) return;
-    const int32_t key = sS[p];
-    if (key < 0 || key >= m) {
-        set_error(err, DEV_BAD_INDEX);
-        return;
-    }
-    const int4 *s4 = (const int4 *)sS;
-    bool head = true;
-    for (int q4 = 0; q4 < (p >> 2) && head; ++q4) {
-        const int4 w = s4[q4];
-        head = !(w.x == key || w.y == key || w.z == key || w.w == key);
-    }
-    for (int q = p & ~3; q < p && head; ++q) head = sS[q] != key;
-    if (!head) return;
-    // later occurrences: a match mask per int4 group, and the (rare, FP64,
-    // 64-cycle-latency) adds only for the set bits, in position order
-    double sum = delta[p];
-    for (int q4 = p >> 2; q4 < (c4 >> 2); ++q4) {
-        const int4 w = s4[q4];
-        unsigned mk = (w.x == key ? 1u : 0u) | (w.y == key ? 2u : 0u) | (w.z == key ? 4u : 0u) | (w.w == key ? 8u : 0u);
-        mk &= q4 == (p >> 2) ? ~((2u << (p & 3)) - 1u) : 0xfu;  // positions after p only
-        while (mk) {
-            sum += delta[4 * q4 + __ffs(mk) - 1];
-            mk &= mk - 1;
+        if (lane == 0) {
+            alpha[key] += sum;
+            g[key] += diag * sum;
         }
     }
-    alpha[key] += sum;
-    g[key] += diag * sum;
 }
 
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha, double *g,
                           uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st)
 {
     if (cnt <= 0) return cudaSuccess;
-    if (cnt > 8192) return cudaErrorInvalidValue;
-    if (cnt <= UPD_SCAN_MAX) {
-        const unsigned grid = (unsigned)((cnt + UPD_SCAN_THREADS - 1) / UPD_SCAN_THREADS);
-        update_scan_kernel<<<grid, UPD_SCAN_THREADS, 0, st>>>(S, delta, (int)cnt, diag, alpha, g, ctr, ctr_advance,
-                                                             m, err);
-        return cudaGetLastError();
-    }
-    int P = 2;
-    while (P < cnt) P <<= 1;
-    size_t sm = sizeof(unsigned long long) * (size_t)P;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    update_kernel<<<1, UPD_THREADS, sm, st>>>(S, delta, (int)cnt, P, diag, alpha, g, ctr, ctr_advance, m, err);
+    if (cnt > UPD_MAX) return cudaErrorInvalidValue;
+    int64_t blocks = (cnt + UPD_WARPS - 1) / UPD_WARPS;
+    if (blocks > 152) blocks = 152;
+    update_kernel<<<(unsigned)blocks, UPD_WARPS * 32, 0, st>>>(S, delta, (int)cnt, diag, alpha, g, ctr, ctr_advance,
+                                                               m, err);
     return cudaGetLastError();
 }
 

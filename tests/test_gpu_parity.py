@@ -147,6 +147,32 @@ def test_kernel_block_apply(prec, kind, kw):
     assert np.max(np.abs(got - want)) <= tol * scale
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3", "fp8"])
+@pytest.mark.parametrize("m,ncols,n", [(1100, 600, 300), (257, 33, 16), (3000, 1024, 64), (129, 300, 200)])
+def test_kernel_block_apply_pair_tiles(prec, m, ncols, n):
+    """The apply form runs on CTA pairs over 256-row tiles: ragged pair tiles
+    (a pair whose second CTA has no rows), several N-chunks with a ragged last
+    one, odd halves of an N-chunk, k-blocks with a ragged tail."""
+    g = np.random.default_rng(m + ncols)
+    A = g.standard_normal((m, n)) / np.sqrt(n)
+    cols = g.integers(0, m, size=ncols)
+    w = g.standard_normal(ncols)
+    g0 = g.standard_normal(m)
+    kb, ko = B().kernel("rbf", gamma=0.7), oracle.kernel("rbf", gamma=0.7)
+    gd = dev(g0)
+    if prec == "fp8":
+        q, sc = oracle.quantize_e4m3_rows(A)
+        Ar = oracle.dequantize_e4m3_rows(q, sc)
+        Ad, tol = B().Fp8(dev(q), dev(sc)), 2e-5
+    else:
+        Ar = ROUND.get(prec, round_tf32)(A)
+        Ad, tol = dev(A.astype(np.float32)), TC_TOL[prec]
+    B().kernel_block_apply(Ad, kb, prec, dev(cols, torch.int32), dev(w), gd)
+    Kb = oracle.kernel_block(ko, Ar, cols)
+    want = g0 + Kb @ w
+    assert np.max(np.abs(gd.cpu().numpy() - want)) <= tol * np.max(np.abs(Kb)) * np.sum(np.abs(w))
+
+
 def test_kernel_block_bad_index_is_an_error_not_a_fault():
     A = dev(np.ones((10, 4)))
     with pytest.raises(B().DcdError) as e:
