@@ -13,9 +13,13 @@
 //   store: writes K_ij (FP32) -- used for the sampled Gram, so that the
 //          recurrence sees exactly the values the apply pass uses.
 //
-// CTA layout (320 threads, one CTA per SM, persistent over 128-row tiles):
+// Two kernels, both persistent with one CTA per SM and 320 threads:
+//   block_tc_kernel  (store) over 128-row tiles x 64-column N-chunks;
+//   block_tc2_kernel (apply) on CTA pairs over 256-row tiles (tcgen05
+//                    cta_group::2), each CTA staging half of an N-chunk of B.
+// Warp roles in both:
 //   warp 0      TMA producer: 128-byte-swizzled k-blocks of A and B into a
-//               4-stage shared-memory ring (mbarrier complete_tx)
+//               shared-memory ring (mbarrier complete_tx)
 //   warp 1      TMEM allocator and MMA issuer (one thread); accumulators are
 //               double-buffered (2 x BN columns) so the epilogue of one
 //               N-chunk overlaps the MMAs of the next
@@ -23,8 +27,9 @@
 //               thread per row; warp w reads TMEM lanes 32 (w % 4)..+31, warps
 //               2..5 take the first half of each N-chunk's columns and warps
 //               6..9 the second half (two warps per scheduler hide the load and
-//               MUFU latency); the second half's row sums reach the first half
-//               through shared memory once per tile, in a fixed order
+//               MUFU latency); in the apply form the second half's row sums
+//               reach the first half through shared memory once per tile, in a
+//               fixed order
 // Every mbarrier wait is bounded; on timeout the CTA records DEV_TIMEOUT,
 // drains its in-flight copies and MMAs (bounded), frees TMEM and returns.
 #include "dcd_internal.cuh"
@@ -54,8 +59,8 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
 // q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
 constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4;
-constexpr int XCH_BYTES = 2 * BM * 8;  // row sums of the second epilogue half, double-buffered
-constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/ + XCH_BYTES;
+constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
@@ -249,6 +254,7 @@ struct TcArgs {
     int64_t ncols;
     int num_tiles, nchunks, kblocks, bn;
     int store;            // 1: store epilogue, 0: apply
+    int lower;            // store: skip the N-chunks above the diagonal
     int items;            // apply: num_tiles; store: num_tiles * nchunks
     int degree;
     float two_gl;         // 2 * gamma * log2(e)
@@ -274,17 +280,15 @@ __device__ __forceinline__ float kf32(float c, float hr, float hc, float rf, con
     }
 }
 
+// store form: one item = one (row tile, N-chunk) pair; with `lower`, the
+// chunks that start past the tile's last row are empty items (every role
+// skips them alike)
 __device__ __forceinline__ void item_range(const TcArgs &a, int item, int &tile, int &c0, int &c1)
 {
-    if (a.store) {
-        tile = item / a.nchunks;
-        c0 = item % a.nchunks;
-        c1 = c0 + 1;
-    } else {
-        tile = item;
-        c0 = 0;
-        c1 = a.nchunks;
-    }
+    tile = item / a.nchunks;
+    c0 = item % a.nchunks;
+    c1 = c0 + 1;
+    if (a.lower && (int64_t)c0 * a.bn > (int64_t)tile * BM + BM - 1) c1 = c0;
 }
 
 template <int MODE, int KIND>
@@ -308,10 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *tfull = bars + 2 * STAGES;   // 2
     uint64_t *tempty = tfull + 2;          // 2
     uint64_t *drain = tempty + 2;          // 1
-    uint64_t *xfull = drain + 1;           // 2: second-half row sums written
-    uint64_t *xfree = xfull + 2;           // 2: ... and consumed
-    double *xch = (double *)(smem + RING_BYTES + 256);  // [2][BM]
-    uint32_t *tmem_holder = (uint32_t *)(xfree + 2);
+    uint32_t *tmem_holder = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -323,8 +324,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 8);
-            mbar_init(&xfull[b], 4);
-            mbar_init(&xfree[b], 4);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -431,9 +430,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int row_in_tile = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         const int ngrp = bn / 32, cg0 = half ? ngrp / 2 : 0, cg1 = half ? ngrp : ngrp / 2;
-        uint32_t acc_it = 0, item_it = 0;
+        uint32_t acc_it = 0;
         bool ok = true;
-        for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x, ++item_it) {
+        for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
             int tile, c0, c1;
             item_range(a, item, tile, c0, c1);
             const int64_t row = (int64_t)tile * BM + row_in_tile;
@@ -441,7 +440,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
             const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
             const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
-            double racc = 0.0;
             for (int nc = c0; nc < c1; ++nc, ++acc_it) {
                 const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
                 // every lane polls; the warp proceeds only if all lanes saw the
@@ -460,66 +458,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int q = 0; q < 32; ++q) v[q] *= a.col_s[colbase + q];
                     }
-                    if (a.store) {
-                        if (row_ok) {
-                            float *dst = a.out + row * a.ldo + colbase;
-                            if (colbase + 32 <= a.ncols && (a.ldo & 3) == 0) {  // whole group: 16-byte stores
+                    if (row_ok) {
+                        float *dst = a.out + row * a.ldo + colbase;
+                        if (colbase + 32 <= a.ncols && (a.ldo & 3) == 0) {  // whole group: 16-byte stores
 #pragma unroll
-                                for (int q = 0; q < 32; q += 4) {
-                                    float4 o;
-                                    o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
-                                    o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf, a);
-                                    o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf, a);
-                                    o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf, a);
-                                    *reinterpret_cast<float4 *>(dst + q) = o;
-                                }
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < 32; ++q)
-                                    if (colbase + q < a.ncols)
-                                        dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
+                            for (int q = 0; q < 32; q += 4) {
+                                float4 o;
+                                o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
+                                o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf, a);
+                                o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf, a);
+                                o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf, a);
+                                *reinterpret_cast<float4 *>(dst + q) = o;
                             }
-                        }
-                    } else {
-                        float p0 = 0.f, p1 = 0.f;
+                        } else {
 #pragma unroll
-                        for (int q = 0; q < 32; q += 2) {
-                            const float hc0 = KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f;
-                            const float hc1 = KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f;
-                            p0 = fmaf(kf32<KIND>(v[q], hr, hc0, rf, a), a.col_w[colbase + q], p0);
-                            p1 = fmaf(kf32<KIND>(v[q + 1], hr, hc1, rf, a), a.col_w[colbase + q + 1], p1);
+                            for (int q = 0; q < 32; ++q)
+                                if (colbase + q < a.ncols)
+                                    dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
                         }
-                        racc += (double)p0 + (double)p1;
                     }
                 }
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
-            }
-            if (!ok || a.store) continue;
-            // row sum = first half + second half (this order): the second half hands its part over
-            // in shared memory (double-buffered by tile; xfree keeps a buffer until it is read)
-            const uint32_t xb = item_it & 1, xph = (item_it >> 1) & 1;
-            double *xc = xch + xb * BM;
-            if (half) {
-                const bool fr = mbar_wait(&xfree[xb], xph ^ 1, abort_flag, a.err);
-                if (!__all_sync(0xffffffffu, fr)) {
-                    ok = false;
-                    break;
-                }
-                xc[row_in_tile] = racc;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&xfull[xb]);
-            } else {
-                const bool fu = mbar_wait(&xfull[xb], xph, abort_flag, a.err);
-                if (!__all_sync(0xffffffffu, fu)) {
-                    ok = false;
-                    break;
-                }
-                racc += xc[row_in_tile];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&xfree[xb]);
-                if (row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
             }
         }
     }
@@ -977,7 +938,7 @@ bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t 
 
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
                             const float *col_h, const float *col_w, const double *rs, double *g, float *out,
-                            int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st)
+                            int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st, bool lower)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
@@ -1014,6 +975,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.kblocks = (int)(Aop.n_pad / kb_elems);
     a.bn = bn;
     a.store = out != nullptr;
+    a.lower = a.store && lower;
     a.items = a.store ? a.num_tiles * a.nchunks : a.num_tiles;
     a.degree = kp.degree;
     a.two_gl = (float)(2.0 * kp.gamma * 1.4426950408889634);

@@ -119,10 +119,12 @@ __host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
                                                         : 2 * n_pad;
 }
 bool tc_available();
+// lower (store form only): write only the N-chunks that reach the diagonal
+// (column chunk start <= last row of the tile); the rest of out is left as is
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
                             const float *row_h, const float *col_h, const float *col_w, const double *rs,
                             double *g, float *out, int64_t ldo, int64_t nrows_out, int64_t ncols,
-                            int *err, cudaStream_t st);
+                            int *err, cudaStream_t st, bool lower = false);
 
 // setup / per-step helpers (sample_update.cu)
 // src_scale: the per-row scales of an FP8 source (dtype DCD_FP8E4M3), else unused
@@ -192,6 +194,9 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
                              const double *y, const double *alpha, const double *g, double omega, double nu,
                              double *delta, double *w64, float *w32, int *err, cudaStream_t st);
 size_t recur_bdcd_scratch_bytes(int64_t nblk, int b);
+// true when launch_recur_bdcd with these arguments reads only the lower
+// triangle (with the diagonal blocks) of an FP32 Gram
+bool recur_bdcd_lower_gram(int64_t nblk, int b, int refinements, int64_t ldk);
 // The alpha / cached-gradient update (a6) done by the recurrence itself when
 // it can: alpha_S += Delta, g_S += mdiag * Delta (repeats summed in position
 // order) and the stream counter advanced.  `done` reports whether it ran.

@@ -719,6 +719,16 @@ size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
 
 // Refined FP32 chain for b <= 32 and sb <= 8192 (the shared-memory limit of
 // one CTA: 12 bytes per sampled row); the plain FP64 kernels otherwise.
+bool recur_bdcd_lower_gram(int64_t nblk, int b, int refinements, int64_t ldk)
+{
+    if (!(b <= 32 && nblk >= 1 && nblk * b <= 8192 && refinements >= 0 &&
+          chain_layout((int)(nblk * b), b, 4, ldk).total <= CHAIN_SMEM_MAX))
+        return false;
+    if (recur_cluster_size((int)nblk, b, refinements + 1) > 0) return true;
+    const int pb = recur_cluster_panel_blocks(b, refinements + 1);
+    return pb > 0 && pb < nblk && blocked_cluster_scratch_bytes(nblk, b) <= recur_bdcd_scratch_bytes(nblk, b);
+}
+
 cudaError_t launch_recur_bdcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t nblk, int b,
                               double lambda, double mdiag, const double *g, int refinements, void *scratch,
                               double *delta, double *w64, float *w32, FusedUpdate *upd, int *err, cudaStream_t st)

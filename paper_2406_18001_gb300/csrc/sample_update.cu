@@ -442,9 +442,9 @@ cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStr
 // K-SVM-L2, m for K-RR).  Repeated indices are merged deterministically: a
 // position with no earlier occurrence of its index is a run head and adds the
 // deltas of its index's occurrences in position order.  One warp per
-// position, S staged in shared memory: the warp compares 32 positions per
-// step (ballot), so a position costs cnt / 32 steps.  cnt <= 8192.  Also
-// advances the stream counter.
+// position, S staged in shared memory: the warp compares 128 positions per
+// step (4 per lane, ballot), so a position costs cnt / 128 steps.
+// cnt <= 8192.  Also advances the stream counter.
 constexpr int UPD_MAX = 8192;
 constexpr int UPD_WARPS = 8;
 
@@ -452,31 +452,53 @@ __global__ void __launch_bounds__(UPD_WARPS * 32)
     update_kernel(const int32_t *S, const double *delta, int cnt, double diag, double *alpha, double *g,
                   uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
 {
-    __shared__ int32_t sS[UPD_MAX];
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) sS[q] = S[q];
+    __shared__ __align__(16) int32_t sS[UPD_MAX];
+    const int c4 = (cnt + 3) & ~3;
+    for (int q = threadIdx.x; q < c4; q += blockDim.x) sS[q] = q < cnt ? S[q] : -1;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0 && ctr) *ctr += ctr_advance;
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * UPD_WARPS;
+    const int4 *s4 = (const int4 *)sS;
     for (int p = blockIdx.x * UPD_WARPS + (threadIdx.x >> 5); p < cnt; p += nw) {  // warp-uniform
         const int32_t key = sS[p];
         if (key < 0 || key >= m) {
             if (lane == 0) set_error(err, DEV_BAD_INDEX);
             continue;
         }
+        // head: no earlier position holds key (128 positions per step, 4 per lane)
         bool head = true;
-        for (int q0 = 0; q0 < p && head; q0 += 32) {
-            const int q = q0 + lane;
-            head = !__any_sync(0xffffffffu, q < p && sS[q] == key);
+        for (int q0 = 0; q0 < p && head; q0 += 128) {
+            const int q = q0 + 4 * lane;
+            bool hit = false;
+            if (q < p) {
+                const int4 w = s4[q >> 2];
+                hit = (w.x == key) || (q + 1 < p && w.y == key) || (q + 2 < p && w.z == key) ||
+                      (q + 3 < p && w.w == key);
+            }
+            head = !__any_sync(0xffffffffu, hit);
         }
         if (!head) continue;
-        double sum = 0.0;  // occurrences at positions >= p, in position order (every lane the same)
-        for (int q0 = p; q0 < cnt; q0 += 32) {
-            const int q = q0 + lane;
-            unsigned mk = __ballot_sync(0xffffffffu, q < cnt && sS[q] == key);
-            while (mk) {
-                sum += delta[q0 + __ffs(mk) - 1];
-                mk &= mk - 1;
+        // occurrences at positions >= p, in position order (every lane the same sum)
+        double sum = 0.0;
+        for (int q0 = p & ~3; q0 < c4; q0 += 128) {
+            const int q = q0 + 4 * lane;
+            unsigned mk = 0;
+            if (q < c4) {
+                const int4 w = s4[q >> 2];
+                mk = (w.x == key ? 1u : 0u) | (w.y == key ? 2u : 0u) | (w.z == key ? 4u : 0u) | (w.w == key ? 8u : 0u);
+                if (q < p) mk &= ~((1u << (p - q)) - 1u);  // only the group holding p starts below p
+            }
+            unsigned lanes = __ballot_sync(0xffffffffu, mk != 0);
+            while (lanes) {  // rare: lanes in order, each lane's hits in order
+                const int l = __ffs(lanes) - 1;
+                unsigned ml = __shfl_sync(0xffffffffu, mk, l);
+                const int ql = q0 + 4 * l;
+                while (ml) {
+                    sum += delta[ql + __ffs(ml) - 1];
+                    ml &= ml - 1;
+                }
+                lanes &= lanes - 1;
             }
         }
         if (lane == 0) {

@@ -549,9 +549,11 @@ struct Solver {
             return launch_csr_block(ca, cm, !tc, kp, S, ncols, S, ncols, nullptr, nullptr, nullptr, nullptr, Kss, ldk,
                                     st);
         if (tc) {
+            // the cluster and blocked recurrences read the lower triangle only
+            const bool lower = problem == 1 && recur_bdcd_lower_gram(ncols / o.b, o.b, 1, ldk);
             TcOperand B{As, ncols, op.n_pad, op.kind, col_s};
             return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
-                                   err, st);
+                                   err, st, lower);
         }
         return launch_block_simt_f64(op.a64, op.lda, m, n, kp, S, ncols, S, ncols, nullptr, nullptr, nullptr,
                                      (double *)Kss, ldk, err, st);
