@@ -38,7 +38,7 @@ METRIC = "coordinate updates/s and time-to-duality-gap 1e-6 (mixed vs FP64 s=1, 
 UNIT = "coordinate updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused-block launch,
 # from an ncu capture of this build's kernel (prec, m, n, b, s) -> bytes
-NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 108.48e6}
+NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 109.45e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 
@@ -321,7 +321,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
         traffic = NCU_TRAFFIC.get((args.prec, args.m, args.n, args.b, args.s))
     roof["traffic"] = traffic
     roof["peak_source"] = src
-    roof["kernel"] = "block_tc_kernel (fused kernel block + gradient update)" if args.prec != "fp64" \
+    roof["kernel"] = "block_tc2_kernel (fused kernel block + gradient update, CTA pairs)" if args.prec != "fp64" \
         else "block_simt_f64_kernel"
     roof["algorithmic"] = {"flops_per_launch": flops, "bytes_per_launch": bytes_, "launch_ms": phase["block"]}
 
@@ -626,10 +626,12 @@ def run_gpu_fp8(args):
         sb = s * b
         flops = 2.0 * m * n * sb
         fp8_peak = 2.0 * bf16_peak
+        # DRAM bytes of one launch from the m = 65536 capture, scaled by rows (the 8.4 MB of sampled rows fixed)
+        traffic = (150.97e6 - 8.4e6) * m / 65536 + 8.4e6 if (n, s, b) == (2048, 128, 32) else None
         roof = {"bound": "tensor", "achieved": flops / (ph8["block"] * 1e-3) / 1e12, "peak": fp8_peak,
-                "unit": "TFLOP/s", "traffic": None,
+                "unit": "TFLOP/s", "traffic": traffic,
                 "peak_source": f"{src} bf16 burst x 2 (nominal fp8 / bf16 dense ratio 4.5 / 2.25)",
-                "kernel": "block_tc_kernel<MODE_FP8> (kind::f8f6f4 kernel block + gradient update)",
+                "kernel": "block_tc2_kernel<MODE_FP8> (kind::f8f6f4 kernel block + gradient update, CTA pairs)",
                 "algorithmic": {"flops_per_launch": flops, "launch_ms": ph8["block"]}}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof16 = {"achieved": flops / (ph16["block"] * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
