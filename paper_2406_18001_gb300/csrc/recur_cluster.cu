@@ -13,7 +13,8 @@
 // (Bs = q b <= 32 rows, one row per lane).  bdcd_prep_kernel inverts the
 // diagonal part L_JJ of every super-block at once (Gauss-Jordan with one
 // thread per entry; L_JJ is block lower triangular with SPD diagonal blocks,
-// so no pivoting) and marks repeated indices, so a chain step is
+// so no pivoting; one CTA per super-block) while a second set of CTAs marks
+// repeated indices and links their occurrences, so a chain step is
 // Delta_J = L_JJ^-1 r_J after r_J -= L_JT Delta_T for every earlier T: the
 // block forward substitution with the steps inside a super-block regrouped
 // into one matrix-vector product.
@@ -247,22 +248,41 @@ __global__ void __launch_bounds__(PREP_THREADS)
     __shared__ int sIJ[32], sIT[CL_NSUP_MAX * 32];
     __shared__ int bad, nxt[32];
     const ClGeom G = cl_geom(nblk, b);
-    const int Bs = G.Bs, sb = nblk * b, J = blockIdx.x;
+    const int Bs = G.Bs, sb = nblk * b;
+    const bool links = (int)blockIdx.x >= G.nsup;  // the second half of the grid: masks and links
+    const int J = links ? (int)blockIdx.x - G.nsup : (int)blockIdx.x;
     const int base = J * Bs, rows = cl_rows(J, Bs, sb);
     const int i0 = threadIdx.x >> 5, j = threadIdx.x & 31;  // rows i0 + 8 r
     if (threadIdx.x == 0) bad = 0;
     if (threadIdx.x < 32) nxt[threadIdx.x] = INT32_MAX;
     for (int e = threadIdx.x; e < sb; e += PREP_THREADS) sIT[e] = S[e];
     __syncthreads();
-    // next[row]: the next position holding the same index (-1: none); warp i0 scans the positions
-    // row + 1 + i0, row + 9 + i0, ... up to its first match, the minimum over the warps wins
-    if (j < rows) {
-        const int row = base + j, key = sIT[row];
-        for (int q = row + 1 + i0; q < sb; q += PREP_THREADS / 32)
-            if (sIT[q] == key) {
-                atomicMin(&nxt[j], q);
-                break;
+    if (links) {
+        // next[row]: the next position holding the same index (-1: none); warp i0 scans the
+        // positions row + 1 + i0, row + 9 + i0, ... up to its first match, the minimum wins
+        if (j < rows) {
+            const int row = base + j, key = sIT[row];
+            for (int q = row + 1 + i0; q < sb; q += PREP_THREADS / 32)
+                if (sIT[q] == key) {
+                    atomicMin(&nxt[j], q);
+                    break;
+                }
+        }
+        // repeat masks: (T, p = j) for T = i0 + 8 r <= J
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int T = i0 + 8 * r;
+            if (T <= J) {
+                const int key = j < rows ? sIT[base + j] : -1, row = base + j, tb = T * Bs, tr = cl_rows(T, Bs, sb);
+                uint32_t mask = 0;
+                for (int q = 0; q < tr; ++q)
+                    if (sIT[tb + q] == key && tb + q < row) mask |= 1u << q;
+                M[((size_t)J * CL_NSUP_MAX + T) * 32 + j] = mask;
             }
+        }
+        __syncthreads();
+        if (threadIdx.x < rows) next[base + threadIdx.x] = nxt[threadIdx.x] == INT32_MAX ? -1 : nxt[threadIdx.x];
+        return;
     }
     if (threadIdx.x < 32) sIJ[threadIdx.x] = threadIdx.x < rows ? sIT[base + threadIdx.x] : -1;
     // [L_JJ | I]
@@ -278,18 +298,6 @@ __global__ void __launch_bounds__(PREP_THREADS)
         a[0][i][j] = v;
         a[0][i][j + 32] = (i == j) ? 1.f : 0.f;
     }
-    // repeat masks: (T, p = j) for T = i0 + 8 r <= J
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int T = i0 + 8 * r;
-        if (T <= J) {
-            const int key = j < rows ? sIT[base + j] : -1, row = base + j, tb = T * Bs, tr = cl_rows(T, Bs, sb);
-            uint32_t mask = 0;
-            for (int q = 0; q < tr; ++q)
-                if (sIT[tb + q] == key && tb + q < row) mask |= 1u << q;
-            M[((size_t)J * CL_NSUP_MAX + T) * 32 + j] = mask;
-        }
-    }
     __syncthreads();
     int cur = 0;
     for (int k = 0; k < 32; ++k) {
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(PREP_THREADS)
             if (threadIdx.x == 0) bad = 1;
             break;
         }
-        const float ip = 1.f / piv;
+        const float ip = __frcp_rn(piv);  // = 1.f / piv (both correctly rounded)
         const float p0 = a[cur][k][j] * ip, p1 = a[cur][k][j + 32] * ip;
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
@@ -317,7 +325,6 @@ __global__ void __launch_bounds__(PREP_THREADS)
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) X[(size_t)J * 1024 + (i0 + 8 * r) * 32 + j] = a[cur][i0 + 8 * r][j + 32];
-    if (threadIdx.x < rows) next[base + threadIdx.x] = nxt[threadIdx.x] == INT32_MAX ? -1 : nxt[threadIdx.x];
     if (J == 0) return;
     // N_J = X_J (K_{J,J-1} / lambda + m D): B[t][c] in the other buffer, then row i of X times column j of B
     const int pb = (J - 1) * Bs;
@@ -654,7 +661,7 @@ cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S
     int32_t *next = (int32_t *)(M + (size_t)G.nsup * CL_NSUP_MAX * 32);
     CUtensorMap kmap;
     if (!make_map_f32_2d(&kmap, Kss, sb, sb, ldk, G.Bs, G.Bs)) return cudaErrorInvalidValue;
-    bdcd_prep_kernel<<<(unsigned)G.nsup, PREP_THREADS, 0, st>>>(Kss, ldk, S, nblk, b, (float)(1.0 / lambda),
+    bdcd_prep_kernel<<<(unsigned)(2 * G.nsup), PREP_THREADS, 0, st>>>(Kss, ldk, S, nblk, b, (float)(1.0 / lambda),
                                                                (float)mdiag, X, N, M, next, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
