@@ -451,12 +451,16 @@ def run_gpu_csr(args):
         nnz = int(p.row_ptr[-1])
         fp64 = args.prec == "fp64"
         vb = 8 if fp64 else 4
-        bytes_ = nnz * (4 + vb) + (p.m + 1) * 8 + p.m * (8 + 8 + 8)  # values + columns + offsets + g rw + y
+        # column indices of every nonzero, values of the hits only (nonzeros in a column some sampled row
+        # touches: expected nnz * touched / n for uniform columns), offsets, g read + write, y
+        touched = p.n * (1.0 - (1.0 - args.csr_nnz / p.n) ** s)
+        hits = nnz * touched / p.n
+        bytes_ = nnz * 4 + hits * vb + (p.m + 1) * 8 + p.m * (8 + 8 + 8)
         hbm_peak, _, _, src = peaks()
         achieved = bytes_ / (phase["block"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": None, "peak_source": src, "kernel": "csr_block_kernel (CSR kernel block + gradient update)",
-                "algorithmic": {"bytes_per_launch": bytes_, "launch_ms": phase["block"]}}
+                "algorithmic": {"bytes_per_launch": bytes_, "expected_hits": hits, "launch_ms": phase["block"]}}
         # end to end through the C ABI with host arrays
         Ah = B.Csr(p.row_ptr, p.col_idx, p.values, p.n)
         yh = p.y.copy()

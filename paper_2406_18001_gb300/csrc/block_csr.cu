@@ -11,13 +11,14 @@
 //            as a bitmap over [0, n) with per-word popcount prefixes (rank of
 //            a column = its slot), and per slot the (j, value) entries of the
 //            sampled rows holding that column.
-//   block    one warp per tile of 32 rows: the tile's nonzeros are read once,
-//            coalesced; a nonzero whose column is in the bitmap (rare) is a
-//            hit, appended in element order to a per-warp list; then lane r
-//            adds value * entry for its row's hits into a per-row row of
-//            accumulators (so the partial dots are summed in a fixed order),
-//            and applies the kernel function and the epilogue (apply: g_i +=
-//            rs_i sum_j K_ij w_j, FP64 add; store: K_ij).
+//   block    one warp per tile of 32 rows: the tile's column indices are
+//            read once, coalesced (values only for hits); an index whose
+//            column is in the bitmap (rare) is a hit, appended in element order
+//            to a per-warp list; then lane r adds value * entry for its row's
+//            hits into a per-row row of accumulators (so the partial dots are
+//            summed in a fixed order) and marks the touched sampled columns;
+//            apply: g_i += rs_i (base_i + sum over touched j of w_j (K_ij -
+//            K0_ij)), FP64 add (see csr_block_kernel); store: K_ij.
 //
 // Sampled columns are processed in chunks of CSR_JC per launch (a tile
 // re-reads its nonzeros per chunk); the K-SVM configuration has s*b <= 32.
@@ -28,7 +29,6 @@ namespace dcd {
 namespace {
 
 constexpr int CSR_JC = 32;        // sampled columns per apply pass
-constexpr int CSR_HL = 128;       // hit-list capacity per warp (flushed when full)
 constexpr int CSR_WARPS = 8;      // warps per CTA
 constexpr int CSR_GJ = 256;       // sampled columns per Gram pass
 constexpr int MAP_THREADS = 1024;
@@ -47,12 +47,27 @@ __device__ __forceinline__ T kfun_t(const KernelParams &kp, T dot, T na, T nb, b
     return exp(-(T)kp.gamma * d2);
 }
 
+// Apply: the block is never formed.  For row i, K(a_i, a_{S_j}) differs from
+// its value at a_i . a_{S_j} = 0 only for the sampled rows j sharing a column
+// with a_i ("hits", a few per row), so
+//   sum_j w_j K_ij = base_i + sum_{j touched by i} w_j (K_ij - K0_ij),
+// with K0_ij the kernel at a zero dot: c^d for the polynomial (base_i =
+// c^d sum_j w_j), 0 for the linear kernel, exp(-gamma ||a_i||^2) exp(-gamma
+// ||a_j||^2) for the RBF (base_i = exp(-gamma ||a_i||^2) sum_j w_j
+// exp(-gamma ||a_j||^2)).  The stream over A is therefore its column indices
+// only; a nonzero's value is read when its column is in the map.
+constexpr int CSR_AW = 8;      // warps per CTA (apply)
+constexpr int CSR_HL = 128;    // hit-list capacity per warp (applied when it could overflow)
+constexpr int CSR_PF = 4;      // 128-index chunks per prefetch group (two groups in flight)
+
 template <typename T>
 struct alignas(16) WarpSmem {
     T acc[32][CSR_JC + 1];
-    int32_t hoff[CSR_HL];  // element offset from the tile's first nonzero
-    int32_t hslot[CSR_HL];
-    T hval[CSR_HL];
+    int32_t hoff[CSR_HL];  // element offset from the tile's first nonzero, ascending
+    int32_t hcol[CSR_HL];  // its column
+    int32_t hj[CSR_HL];    // resolved: the slot's entry column j - j0 (single entry), -1 (outside
+                           // this column chunk), or -2 - slot (several entries)
+    T hprod[CSR_HL];       // resolved: value * entry value (single entry) or the value
     int32_t rp[33];        // row offsets relative to the tile's first nonzero
 };
 
@@ -60,8 +75,9 @@ constexpr int CSR_SMEM_BITS = 4096;  // bitmap words kept in shared memory (n <=
 
 template <typename T>
 struct alignas(16) CtaSmem {
-    T nb[CSR_JC], w[CSR_JC];
+    T nb[CSR_JC], w[CSR_JC], k0[CSR_JC];  // k0: RBF exp(-gamma ||a_j||^2)
     int32_t sj[CSR_JC];
+    T base;                               // poly: c^d sum w; RBF: sum w_j k0_j
     uint32_t bits[CSR_SMEM_BITS];
 };
 
@@ -76,61 +92,72 @@ __device__ __forceinline__ int32_t col_slot(const uint32_t *bits, const int32_t 
     return __ldg(wprefix + (c >> 5)) + __popc(w & ((1u << (c & 31)) - 1u));
 }
 
-// Lane r adds the hits of its row (offsets in [rp[r], rp[r+1]), in list order)
-// into acc[r][.].
+// Applies the warp's listed hits.  First the lanes resolve the hits in
+// parallel (value, slot, and for a slot with one entry -- nearly all -- the
+// product with that entry); then lane r adds its row's hits (offsets in
+// [rp[r], rp[r+1]), a contiguous run of the ascending list found by binary
+// search) into acc[r][.] in list order and marks the touched columns.
 template <typename T>
-__device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrColMap &M, int j0, int jc, int lane,
-                                           int nr)
+__device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrColMap &M, const uint32_t *bits,
+                                           const T *vals, int64_t e0, int j0, int jc, int lane, int nr,
+                                           uint32_t &touched)
 {
     __syncwarp();
-    const int lo = lane < nr ? ws.rp[lane] : 0, hi = lane < nr ? ws.rp[lane + 1] : 0;
-    for (int h = 0; h < nh; ++h) {
-        const int o = ws.hoff[h];
-        if (o < lo || o >= hi) continue;
-        const int slot = ws.hslot[h];
-        const T v = ws.hval[h];
-        for (int q = M.slot_off[slot]; q < M.slot_off[slot + 1]; ++q) {
-            const int j = M.ent_j[q] - j0;
-            if (j >= 0 && j < jc) ws.acc[lane][j] += v * (T)M.ent_v[q];
+    for (int h = lane; h < nh; h += 32) {
+        const int32_t c = ws.hcol[h];
+        const T v = vals[e0 + ws.hoff[h]];
+        const int slot = __ldg(M.wprefix + (c >> 5)) + __popc(bits[c >> 5] & ((1u << (c & 31)) - 1u));
+        const int q0 = M.slot_off[slot], q1 = M.slot_off[slot + 1];
+        if (q1 - q0 == 1) {
+            const int j = M.ent_j[q0] - j0;
+            ws.hj[h] = j >= 0 && j < jc ? j : -1;
+            ws.hprod[h] = v * (T)M.ent_v[q0];
+        } else {
+            ws.hj[h] = -2 - slot;
+            ws.hprod[h] = v;
+        }
+    }
+    __syncwarp();
+    if (lane < nr) {
+        const int lo = ws.rp[lane], hi = ws.rp[lane + 1];
+        int a = 0, b = nh;
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (ws.hoff[mid] < lo) a = mid + 1;
+            else b = mid;
+        }
+        for (int h = a; h < nh && ws.hoff[h] < hi; ++h) {
+            const int jj = ws.hj[h];
+            if (jj >= 0) {
+                ws.acc[lane][jj] += ws.hprod[h];
+                touched |= 1u << jj;
+            } else if (jj <= -2) {
+                const int slot = -2 - jj;
+                const T v = ws.hprod[h];
+                for (int q = M.slot_off[slot]; q < M.slot_off[slot + 1]; ++q) {
+                    const int j = M.ent_j[q] - j0;
+                    if (j >= 0 && j < jc) {
+                        ws.acc[lane][j] += v * (T)M.ent_v[q];
+                        touched |= 1u << j;
+                    }
+                }
+            }
         }
     }
     __syncwarp();
 }
 
-// four consecutive nonzeros from element e: one vector load of each array
-// when the quad lies inside the arrays and they are 16-byte aligned, else
-// element by element (column -1 past the arrays)
-template <typename T>
-__device__ __forceinline__ void load_quad(const CsrOperand &A, const T *vals, int64_t e, int32_t (&c)[4], T (&v)[4])
+// four consecutive column indices from element e (-1 past the array): one
+// vector load when the quad lies inside the array and it is 16-byte aligned
+__device__ __forceinline__ int4 load_cols(const CsrOperand &A, int64_t e)
 {
-    if (A.vec && e + 4 <= A.nnz) {
-        const int4 ci = __ldg((const int4 *)(A.col_idx + e));
-        c[0] = ci.x;
-        c[1] = ci.y;
-        c[2] = ci.z;
-        c[3] = ci.w;
-        if (sizeof(T) == 4) {
-            const float4 vv = __ldg((const float4 *)((const float *)vals + e));
-            v[0] = (T)vv.x;
-            v[1] = (T)vv.y;
-            v[2] = (T)vv.z;
-            v[3] = (T)vv.w;
-        } else {
-            const double2 a = __ldg((const double2 *)((const double *)vals + e));
-            const double2 b = __ldg((const double2 *)((const double *)vals + e + 2));
-            v[0] = (T)a.x;
-            v[1] = (T)a.y;
-            v[2] = (T)b.x;
-            v[3] = (T)b.y;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool in = e + q < A.nnz;
-            c[q] = in ? __ldg(A.col_idx + e + q) : -1;
-            v[q] = in ? vals[e + q] : (T)0;
-        }
-    }
+    if (A.vec && e >= 0 && e + 4 <= A.nnz) return __ldg((const int4 *)(A.col_idx + e));
+    int4 c;
+    c.x = e >= 0 && e < A.nnz ? __ldg(A.col_idx + e) : -1;
+    c.y = e + 1 >= 0 && e + 1 < A.nnz ? __ldg(A.col_idx + e + 1) : -1;
+    c.z = e + 2 >= 0 && e + 2 < A.nnz ? __ldg(A.col_idx + e + 2) : -1;
+    c.w = e + 3 >= 0 && e + 3 < A.nnz ? __ldg(A.col_idx + e + 3) : -1;
+    return c;
 }
 
 // Kernel function of Table 1, the kind fixed at compile time.
@@ -149,13 +176,15 @@ __device__ __forceinline__ T kfun_k(T dot, T na, T nb, bool same, T gamma, T coe
     return exp(-gamma * d2);
 }
 
-// Apply: one warp per tile of 32 consecutive rows.  The tile's nonzeros are
-// read as quads (lane l: elements 4 l .. 4 l + 3 of a 128-element chunk, two
-// chunks in flight), tested against the column bitmap (shared memory when it
-// fits); hits are listed in element order (warp prefix sum of the per-lane
-// counts) as offsets, so lane r later takes its row's hits by range.
+// Apply: one warp per tile of 32 consecutive rows.  The tile's column indices
+// are streamed as int4 quads (lane l: indices 4 l .. 4 l + 3 of a 128-index
+// chunk), the next group of CSR_PF chunks loaded while the current one is
+// tested against the column bitmap (shared memory when it fits); hits are
+// listed in element order (warp prefix sum of the per-lane counts) as offsets
+// and columns only.  flush_hits resolves and applies them; lane r then forms
+// row t0 + r's sum from the base term and the touched columns (ascending j).
 template <typename T, int KIND, bool SBITS>
-__global__ void __launch_bounds__(CSR_WARPS * 32)
+__global__ void __launch_bounds__(CSR_AW * 32, 3)
     csr_block_kernel(CsrOperand A, CsrColMap M, int64_t nrows, const int32_t *S, int j0, int jc, KernelParams kp,
                      const float *w32, const double *w64, const double *rs, double *g)
 {
@@ -165,44 +194,76 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
     WarpSmem<T> &ws = ((WarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>)))[warp];
     const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
     const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
+    const T gamma = (T)kp.gamma, coef0 = (T)kp.coef0;
     for (int j = threadIdx.x; j < jc; j += blockDim.x) {
         const int32_t sj = S[j0 + j];
         cs.sj[j] = sj;
         cs.nb[j] = KIND == DCD_RBF ? norm[sj] : (T)0;
+        cs.k0[j] = KIND == DCD_RBF ? exp(-gamma * cs.nb[j]) : (T)0;
         cs.w[j] = sizeof(T) == 8 ? (T)w64[j0 + j] : (T)w32[j0 + j];
     }
     if (SBITS)
         for (int w = threadIdx.x; w < M.nw; w += blockDim.x) cs.bits[w] = M.bits[w];
     for (int j = 0; j < CSR_JC; ++j) ws.acc[lane][j] = (T)0;
     __syncthreads();
+    if (threadIdx.x == 0) {  // the base term's column sum, in column order
+        T sw = (T)0;
+        for (int j = 0; j < jc; ++j) sw += KIND == DCD_RBF ? cs.w[j] * cs.k0[j] : cs.w[j];
+        if (KIND == DCD_POLY) {
+            T cd = coef0;
+            for (int e = 1; e < kp.degree; ++e) cd *= coef0;
+            sw *= cd;
+        }
+        cs.base = KIND == DCD_LINEAR ? (T)0 : sw;
+    }
+    __syncthreads();
     const uint32_t *bits = SBITS ? cs.bits : M.bits;
-    const T gamma = (T)kp.gamma, coef0 = (T)kp.coef0;
+    const T cd = KIND == DCD_POLY ? kfun_k<T, KIND>((T)0, (T)0, (T)0, false, gamma, coef0, kp.degree) : (T)0;
     const int64_t ntiles = (nrows + 31) / 32;
-    for (int64_t tile = (int64_t)blockIdx.x * CSR_WARPS + warp; tile < ntiles;
-         tile += (int64_t)gridDim.x * CSR_WARPS) {
+    const int64_t tstride = (int64_t)gridDim.x * CSR_AW;
+    // row offsets of a tile: lane r holds row_ptr[t0 + r], every lane row_ptr[t0 + nr]; the next
+    // tile's are loaded while this one is streamed
+    auto load_rp = [&](int64_t tl, int64_t &rv, int64_t &re) {
+        if (tl < ntiles) {
+            const int64_t t0 = tl * 32;
+            const int nr = (int)min((int64_t)32, nrows - t0);
+            rv = lane < nr ? A.row_ptr[t0 + lane] : 0;
+            re = A.row_ptr[t0 + nr];
+        }
+    };
+    int64_t rpv_n = 0, rend_n = 0;
+    load_rp((int64_t)blockIdx.x * CSR_AW + warp, rpv_n, rend_n);
+    for (int64_t tile = (int64_t)blockIdx.x * CSR_AW + warp; tile < ntiles; tile += tstride) {
         const int64_t t0 = tile * 32;
         const int nr = (int)min((int64_t)32, nrows - t0);
-        const int64_t e0 = A.row_ptr[t0];
-        for (int k = lane; k <= nr; k += 32) ws.rp[k] = (int32_t)(A.row_ptr[t0 + k] - e0);
-        __syncwarp();
-        const int n_e = ws.rp[nr];
+        const int64_t rpv = rpv_n, rend = rend_n;
+        load_rp(tile + tstride, rpv_n, rend_n);
+        const int64_t e0 = __shfl_sync(0xffffffffu, rpv, 0);
+        if (lane < nr) ws.rp[lane] = (int32_t)(rpv - e0);
+        if (lane == 0) ws.rp[nr] = (int32_t)(rend - e0);
+        const int n_e = (int)(rend - e0);
+        const int lead = (int)(e0 & 3);  // quad-aligned start; offsets -3 .. -1 lie before the tile
         int nh = 0;
-        const int64_t ea = e0 & ~(int64_t)3;  // quad-aligned start; offsets from e0 may be -3 .. -1 there
-        const int lead = (int)(e0 - ea);
-        for (int ob = -lead; ob < n_e; ob += 256) {
-            int32_t c[2][4];
-            T v[2][4];
-            load_quad<T>(A, vals, e0 + ob + 4 * lane, c[0], v[0]);
-            load_quad<T>(A, vals, e0 + ob + 128 + 4 * lane, c[1], v[1]);
+        uint32_t touched = 0;
+        int4 cur[CSR_PF], nxt[CSR_PF];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int oq = ob + 128 * h + 4 * lane;  // offset of this lane's quad
+        for (int b = 0; b < CSR_PF; ++b)
+            cur[b] = -lead + 128 * b < n_e ? load_cols(A, e0 - lead + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
+        for (int ob = -lead; ob < n_e; ob += 128 * CSR_PF) {
+            const int obn = ob + 128 * CSR_PF;
+#pragma unroll
+            for (int b = 0; b < CSR_PF; ++b)  // the next group, in flight while this one is tested
+                nxt[b] = obn + 128 * b < n_e ? load_cols(A, e0 + obn + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+            for (int b = 0; b < CSR_PF; ++b) {
+                const int oq = ob + 128 * b + 4 * lane;  // offset of this lane's quad
+                const int32_t cc[4] = {cur[b].x, cur[b].y, cur[b].z, cur[b].w};
                 unsigned mk = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int32_t cc = c[h][q];
-                    const bool in = oq + q >= 0 && oq + q < n_e && cc >= 0;
-                    if (in && ((SBITS ? bits[cc >> 5] : __ldg(bits + (cc >> 5))) >> (cc & 31)) & 1u) mk |= 1u << q;
+                    const bool in = oq + q >= 0 && oq + q < n_e && cc[q] >= 0;
+                    if (in && ((SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5))) >> (cc[q] & 31)) & 1u)
+                        mk |= 1u << q;
                 }
                 if (!__any_sync(0xffffffffu, mk != 0)) continue;
                 // exclusive prefix of the per-lane hit counts = element order
@@ -215,46 +276,38 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
                 }
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
                 if (nh + total > CSR_HL) {
-                    flush_hits(ws, nh, M, j0, jc, lane, nr);
+                    flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
                     nh = 0;
                 }
                 int pos = nh + incl - cnt;
-                while (mk) {
-                    const int q = __ffs(mk) - 1;
-                    mk &= mk - 1;
-                    // the quad's q-th entry without a dynamically indexed array
-                    const int32_t cq = q == 0 ? c[h][0] : q == 1 ? c[h][1] : q == 2 ? c[h][2] : c[h][3];
-                    const T vq = q == 0 ? v[h][0] : q == 1 ? v[h][1] : q == 2 ? v[h][2] : v[h][3];
-                    ws.hoff[pos] = oq + q;
-                    ws.hslot[pos] = col_slot(M.bits, M.wprefix, cq);
-                    ws.hval[pos] = vq;
-                    ++pos;
-                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if ((mk >> q) & 1u) {
+                        ws.hoff[pos] = oq + q;
+                        ws.hcol[pos] = cc[q];
+                        ++pos;
+                    }
                 nh += total;
             }
+#pragma unroll
+            for (int b = 0; b < CSR_PF; ++b) cur[b] = nxt[b];
         }
-        flush_hits(ws, nh, M, j0, jc, lane, nr);
-        // epilogue: lane r owns row t0 + r
-        if (lane < nr) {
-            const int64_t row = t0 + lane;
+        flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
+        const int64_t row = t0 + lane;
+        const bool live = lane < nr;
+        if (live) {
             const T na = KIND == DCD_RBF ? norm[row] : (T)0;
-            T sum0 = (T)0, sum1 = (T)0;
-            int j = 0;
-            for (; j + 1 < jc; j += 2) {
-                const T k0 = kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree);
-                const T k1 =
-                    kfun_k<T, KIND>(ws.acc[lane][j + 1], na, cs.nb[j + 1], cs.sj[j + 1] == row, gamma, coef0, kp.degree);
+            const T ea = KIND == DCD_RBF ? exp(-gamma * na) : (T)0;
+            T sum = KIND == DCD_RBF ? ea * cs.base : cs.base;
+            while (touched) {
+                const int j = __ffs(touched) - 1;
+                touched &= touched - 1;
+                const T kv = kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree);
+                const T k0 = KIND == DCD_RBF ? ea * cs.k0[j] : cd;
                 ws.acc[lane][j] = (T)0;
-                ws.acc[lane][j + 1] = (T)0;
-                sum0 = fma(k0, cs.w[j], sum0);
-                sum1 = fma(k1, cs.w[j + 1], sum1);
+                sum = fma(cs.w[j], kv - k0, sum);
             }
-            if (j < jc) {
-                sum0 = fma(kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree),
-                           cs.w[j], sum0);
-                ws.acc[lane][j] = (T)0;
-            }
-            g[row] += (rs ? rs[row] : 1.0) * (double)(sum0 + sum1);
+            g[row] += (rs ? rs[row] : 1.0) * (double)sum;
         }
         __syncwarp();
     }
@@ -452,20 +505,21 @@ cudaError_t launch_csr_apply_k(const CsrOperand &A, const CsrColMap &M, int64_t 
                                const double *rs, double *g, cudaStream_t st)
 {
     auto kfn = csr_block_kernel<T, KIND, SBITS>;
-    const size_t smem = sizeof(CtaSmem<T>) + sizeof(WarpSmem<T>) * CSR_WARPS;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(CtaSmem<T>) + sizeof(WarpSmem<T>) * CSR_AW;
+    static int per_sm = 0;  // resident CTAs per SM, queried once per instantiation (before any capture)
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, CSR_AW * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
     }
-    const int64_t per_sm = (int64_t)(200 * 1024 / smem) > 0 ? (int64_t)(200 * 1024 / smem) : 1;
     const int64_t tiles = (nrows + 31) / 32;
-    int64_t grid = (tiles + CSR_WARPS - 1) / CSR_WARPS;
-    if (grid > sm_count() * per_sm) grid = sm_count() * per_sm;
+    int64_t grid = (tiles + CSR_AW - 1) / CSR_AW;
+    if (grid > (int64_t)sm_count() * per_sm) grid = (int64_t)sm_count() * per_sm;
     for (int64_t j0 = 0; j0 < ncols; j0 += CSR_JC) {
         const int jc = (int)min((int64_t)CSR_JC, ncols - j0);
-        kfn<<<(unsigned)grid, CSR_WARPS * 32, smem, st>>>(A, M, nrows, S, (int)j0, jc, kp, w32, w64, rs, g);
+        kfn<<<(unsigned)grid, CSR_AW * 32, smem, st>>>(A, M, nrows, S, (int)j0, jc, kp, w32, w64, rs, g);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
