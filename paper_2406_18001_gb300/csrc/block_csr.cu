@@ -314,9 +314,11 @@ __global__ void __launch_bounds__(CSR_AW * 32, 3)
 }
 
 // Store (the sampled Gram and the component block): one warp per listed row
-// (rows == nullptr: row r), columns S[j0 .. j0 + jc).  The row's hits are
-// taken one at a time in element order and their slot entries (distinct j)
-// spread over the lanes, so every partial dot is summed in a fixed order.
+// (rows == nullptr: row r), columns S[j0 .. j0 + jc).  The lanes resolve a
+// group of 32 nonzeros' hits in parallel, then the hits are added one at a
+// time in element order (a slot with several entries spreads its distinct j
+// over the lanes), so every partial dot is summed in a fixed order -- the
+// products and order of the apply kernel.
 template <typename T>
 __global__ void __launch_bounds__(CSR_WARPS * 32)
     csr_gram_kernel(CsrOperand A, CsrColMap M, const int32_t *rows, int64_t nrows, const int32_t *S, int j0, int jc,
@@ -332,20 +334,41 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
         const int64_t r = rows ? (int64_t)rows[k] : k;
         const int64_t e0 = A.row_ptr[r], e1 = A.row_ptr[r + 1];
         for (int64_t eb = e0; eb < e1; eb += 32) {
+            // the lanes resolve their hits in parallel: value, slot, and for a slot with one entry
+            // (nearly all) its column and the product
             const int64_t e = eb + lane;
             const int32_t c = e < e1 ? __ldg(A.col_idx + e) : -1;
             const bool hit = c >= 0 && col_hit(M.bits, c);
-            const int slot = hit ? col_slot(M.bits, M.wprefix, c) : 0;
-            const T v = hit ? vals[e] : (T)0;
+            int jj = -1;
+            T prod = (T)0;
+            if (hit) {
+                const T v = vals[e];
+                const int slot = col_slot(M.bits, M.wprefix, c);
+                const int q0 = M.slot_off[slot], q1 = M.slot_off[slot + 1];
+                if (q1 - q0 == 1) {
+                    const int j = M.ent_j[q0] - j0;
+                    jj = j >= 0 && j < jc ? j : -1;
+                    prod = v * (T)M.ent_v[q0];
+                } else {
+                    jj = -2 - slot;
+                    prod = v;
+                }
+            }
+            // then add them in element order
             unsigned mk = __ballot_sync(0xffffffffu, hit);
             while (mk) {
                 const int src = __ffs(mk) - 1;
                 mk &= mk - 1;
-                const int sl = __shfl_sync(0xffffffffu, slot, src);
-                const T vv = __shfl_sync(0xffffffffu, v, src);
-                for (int q = M.slot_off[sl] + lane; q < M.slot_off[sl + 1]; q += 32) {
-                    const int j = M.ent_j[q] - j0;
-                    if (j >= 0 && j < jc) acc[warp][j] += vv * (T)M.ent_v[q];
+                const int js = __shfl_sync(0xffffffffu, jj, src);
+                const T ps = __shfl_sync(0xffffffffu, prod, src);
+                if (js >= 0) {
+                    if (lane == 0) acc[warp][js] += ps;
+                } else if (js <= -2) {  // several sampled rows hold this column: distinct j, one per lane
+                    const int sl = -2 - js;
+                    for (int q = M.slot_off[sl] + lane; q < M.slot_off[sl + 1]; q += 32) {
+                        const int j = M.ent_j[q] - j0;
+                        if (j >= 0 && j < jc) acc[warp][j] += ps * (T)M.ent_v[q];
+                    }
                 }
                 __syncwarp();
             }

@@ -673,11 +673,144 @@ cudaError_t refined_bdcd_b(const KT *Kss, int64_t ldk, const int32_t *S, int nbl
 
 }  // namespace
 
+// The same chain for cnt <= DCD_FAST_MAX with its state in registers: the
+// whole CTA first forms the coupling coefficients C[j][t] = y_t y_j K_tj
+// (+ omega when S_t = S_j, the repeat term of the unrolled update) in shared
+// memory; then one warp runs the chain with lane l holding, for t = l, l+32,
+// ..., alpha_t, g_t, 1/eta_t and the pending corrections of g_t and rho_t in
+// registers (the gradient correction starts at g_t, so the step's gradient
+// is read, not formed).  A step is the owner lane's clipped Newton step
+// (Algorithm 2, the arithmetic of recur_dcd_kernel), a broadcast, and one FMA
+// per later coordinate.  GB300's FP64 compare-and-select costs ~110 cycles
+// of latency against 25 for min/max and 65 for add/FMA (measured), so the
+// zero tests on the chain are integer tests of the bit patterns.
+constexpr int DCD_FAST_MAX = 128;
+constexpr int DCD_FAST_K = DCD_FAST_MAX / 32;
+
+template <typename KT>
+__global__ void __launch_bounds__(DCD_THREADS) recur_dcd_fast_kernel(const KT *Kss, int64_t ldk, const int32_t *S,
+                                                                     int cnt, const double *y, const double *alpha,
+                                                                     const double *g, double omega, double nu,
+                                                                     double *delta, double *w64, float *w32)
+{
+    extern __shared__ double fsm[];
+    double *C = fsm;                                   // C[j * cnt + t]
+    double *yS = C + (size_t)cnt * cnt;
+    int32_t *sI = (int32_t *)(yS + cnt);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int32_t i = S[t];
+        sI[t] = i;
+        yS[t] = y[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double a[DCD_FAST_K], gg[DCD_FAST_K], ie[DCD_FAST_K], corr[DCD_FAST_K], rc[DCD_FAST_K], th[DCD_FAST_K];
+    auto nonzero = [](double x) { return (__double_as_longlong(x) << 1) != 0; };  // x != 0 (+-0 are zero)
+    int32_t id[DCD_FAST_K];
+    if (threadIdx.x < 32) {  // the chain warp's state (loads in flight while C is formed)
+#pragma unroll
+        for (int k = 0; k < DCD_FAST_K; ++k) {
+            const int t = 32 * k + lane;
+            const bool v = t < cnt;
+            const int32_t i = v ? sI[t] : -1;
+            id[k] = i;
+            a[k] = v ? alpha[i] : 0.0;
+            gg[k] = v ? g[i] : 0.0;
+            const double eta = v ? kval(Kss, ldk, t, t) + omega : 0.0;  // G_k = V^T U_k + omega I, y_t^2 = 1
+            ie[k] = eta > 0.0 ? 1.0 / eta : 0.0;
+            corr[k] = gg[k];  // the gradient of coordinate t as the corrections arrive
+            rc[k] = 0.0;
+            th[k] = 0.0;
+        }
+    }
+    for (int e = threadIdx.x; e < cnt * cnt; e += blockDim.x) {
+        const int j = e / cnt, t = e - j * cnt;
+        C[e] = yS[t] * yS[j] * kval(Kss, ldk, t, j) + (sI[t] == sI[j] ? omega : 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    double rh[DCD_FAST_K];  // rho_t = alpha_t plus the steps of earlier repeats of its index
+#pragma unroll
+    for (int k = 0; k < DCD_FAST_K; ++k) rh[k] = a[k] + rc[k];
+    const bool clipnu = nu <= 1.7976931348623157e308;  // L1: the box's upper bound; L2: none
+#pragma unroll
+    for (int k = 0; k < DCD_FAST_K; ++k) {
+        if (32 * k >= cnt) break;
+        for (int jj = 0; jj < 32 && 32 * k + jj < cnt; ++jj) {
+            const int j = 32 * k + jj;
+            // every lane forms its coordinate's candidate step (convergent code: GB300's FP64 pipe
+            // charges a warp instruction the same with one lane or 32); lane jj's is the step
+            double t_j;
+            {
+                const double rho = rh[k], gj = corr[k];
+                double c1 = fmax(rho - gj, 0.0), c2 = fmax(rho - gj * ie[k], 0.0);
+                if (clipnu) {
+                    c1 = fmin(c1, nu);
+                    c2 = fmin(c2, nu);
+                }
+                // the projected gradient clip(rho - g) - rho is nonzero iff the clip moved rho
+                const long long b1 = __double_as_longlong(c1), b0 = __double_as_longlong(rho);
+                const bool moved = b1 != b0 && ((b1 | b0) << 1) != 0;  // +0 and -0 are the same value
+                t_j = moved && nonzero(ie[k]) ? c2 - rho : 0.0;
+                if (lane == jj) th[k] = t_j;
+            }
+            t_j = __shfl_sync(0xffffffffu, t_j, jj);
+            if (nonzero(t_j)) {
+                const int32_t ij = __shfl_sync(0xffffffffu, id[k], jj);
+                const double *Cj = C + (size_t)j * cnt;
+#pragma unroll
+                for (int kk = k; kk < DCD_FAST_K; ++kk) {
+                    if (32 * kk >= cnt) break;  // warp-uniform
+                    const int t = 32 * kk + lane;
+                    const bool later = t > j && t < cnt;
+                    corr[kk] = fma(later ? Cj[t] : 0.0, t_j, corr[kk]);
+                    const bool rep = later && id[kk] == ij;
+                    if (__any_sync(0xffffffffu, rep) && rep) rh[kk] += t_j;  // repeats are rare
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DCD_FAST_K; ++k) {
+        const int t = 32 * k + lane;
+        if (t < cnt) {
+            delta[t] = th[k];
+            const double wv = yS[t] * th[k];
+            if (w64) w64[t] = wv;
+            if (w32) w32[t] = (float)wv;
+        }
+    }
+}
+
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
                              const double *y, const double *alpha, const double *g, double omega, double nu,
                              double *delta, double *w64, float *w32, int *err, cudaStream_t st)
 {
     if (cnt <= 0) return cudaSuccess;
+    if (cnt <= DCD_FAST_MAX) {
+        const size_t fsm = sizeof(double) * (size_t)(cnt * cnt + cnt) + sizeof(int32_t) * cnt;
+        static bool fattr[2] = {false, false};
+        if (kss_f64) {
+            if (!fattr[1]) {
+                cudaError_t e = cudaFuncSetAttribute(recur_dcd_fast_kernel<double>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DCD_SMEM_LIMIT);
+                if (e != cudaSuccess) return e;
+                fattr[1] = true;
+            }
+            recur_dcd_fast_kernel<double><<<1, DCD_THREADS, fsm, st>>>((const double *)Kss, ldk, S, (int)cnt, y, alpha,
+                                                                       g, omega, nu, delta, w64, w32);
+        } else {
+            if (!fattr[0]) {
+                cudaError_t e = cudaFuncSetAttribute(recur_dcd_fast_kernel<float>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DCD_SMEM_LIMIT);
+                if (e != cudaSuccess) return e;
+                fattr[0] = true;
+            }
+            recur_dcd_fast_kernel<float><<<1, DCD_THREADS, fsm, st>>>((const float *)Kss, ldk, S, (int)cnt, y, alpha,
+                                                                      g, omega, nu, delta, w64, w32);
+        }
+        return cudaGetLastError();
+    }
     size_t sm = sizeof(double) * 7 * cnt + sizeof(int32_t) * ((cnt + 1) & ~1);
     if (cnt <= DCD_SMEM_GRAM_MAX) sm += sizeof(double) * cnt * cnt;
     if (sm > DCD_SMEM_LIMIT) return cudaErrorInvalidValue;
