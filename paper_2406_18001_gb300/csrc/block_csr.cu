@@ -385,16 +385,52 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
     }
 }
 
+// Exclusive scan of one value per thread over the CTA (warp shuffles, two
+// barriers); *total receives the sum.
+__device__ __forceinline__ int cta_excl_scan(int v, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nw ? wsum[lane] : 0, xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) wsum[lane] = xi - x;  // exclusive warp offsets
+        if (lane == 31) *total = xi;
+    }
+    __syncthreads();
+    return wsum[warp] + incl - v;
+}
+
 // Column map of the sampled rows S[0..cnt) (one CTA).  Slots are the ranks of
-// the touched columns; entries of a slot are (j, a_{S_j, c}).
+// the touched columns; entries of a slot are (j, a_{S_j, c}).  The bitmap and
+// the word prefixes are built in shared memory when they fit (SMAP) and
+// copied out at the end.
+constexpr int MAP_SMEM_WORDS = 8192;  // n <= 262144
+
+template <bool SMAP>
 __global__ void __launch_bounds__(MAP_THREADS) csr_colmap_kernel(CsrOperand A, const int32_t *S, int cnt, CsrColMap M,
                                                                  int *err)
 {
-    __shared__ int32_t part[MAP_THREADS];
+    extern __shared__ uint32_t map_sm[];
+    __shared__ int wsum[MAP_THREADS / 32];
+    __shared__ int tot_slots, tot_ent;
     __shared__ long long total;
+    uint32_t *bits = SMAP ? map_sm : M.bits;
+    int32_t *wprefix = SMAP ? (int32_t *)(map_sm + M.nw) : M.wprefix;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) total = 0;
-    for (int w = tid; w < M.nw; w += MAP_THREADS) M.bits[w] = 0u;
+    for (int w = tid; w < M.nw; w += MAP_THREADS) bits[w] = 0u;
     __syncthreads();
     // 0. the sampled rows' nonzeros must fit the entry capacity
     for (int j = tid; j < cnt; j += MAP_THREADS) {
@@ -415,38 +451,30 @@ __global__ void __launch_bounds__(MAP_THREADS) csr_colmap_kernel(CsrOperand A, c
         }
         for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
             const int32_t c = A.col_idx[e];
-            atomicOr(&M.bits[c >> 5], 1u << (c & 31));
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
         }
     }
     __syncthreads();
-    // 2. exclusive popcount prefix over the words (contiguous chunk per thread, block scan of the chunk sums)
+    // 2. exclusive popcount prefix over the words (contiguous chunk per thread)
     const int per = (M.nw + MAP_THREADS - 1) / MAP_THREADS;
     const int w0 = tid * per, w1 = min(M.nw, w0 + per);
     int s = 0;
-    for (int w = w0; w < w1; ++w) s += __popc(M.bits[w]);
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < MAP_THREADS; off <<= 1) {
-        const int add = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += add;
-        __syncthreads();
-    }
-    int run = part[tid] - s;
+    for (int w = w0; w < w1; ++w) s += __popc(bits[w]);
+    int run = cta_excl_scan(s, wsum, &tot_slots);
     for (int w = w0; w < w1; ++w) {
-        M.wprefix[w] = run;
-        run += __popc(M.bits[w]);
+        wprefix[w] = run;
+        run += __popc(bits[w]);
     }
-    const int nslots = part[MAP_THREADS - 1];
     __syncthreads();
+    const int nslots = tot_slots;
     // 3. entries per slot (counts are zero on entry and return to zero below)
     for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
         const int64_t r = S[j];
         if (r < 0 || r >= A.m) continue;
         for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
             const int32_t c = A.col_idx[e];
-            const uint32_t w = M.bits[c >> 5];
-            atomicAdd(&M.counts[M.wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u))], 1);
+            const uint32_t w = bits[c >> 5];
+            atomicAdd(&M.counts[wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u))], 1);
         }
     }
     __syncthreads();
@@ -455,30 +483,26 @@ __global__ void __launch_bounds__(MAP_THREADS) csr_colmap_kernel(CsrOperand A, c
     const int s0 = tid * sper, s1 = min(nslots, s0 + sper);
     int cs = 0;
     for (int q = s0; q < s1; ++q) cs += M.counts[q];
-    __syncthreads();
-    part[tid] = cs;
-    __syncthreads();
-    for (int off = 1; off < MAP_THREADS; off <<= 1) {
-        const int add = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += add;
-        __syncthreads();
-    }
-    int run2 = part[tid] - cs;
+    int run2 = cta_excl_scan(cs, wsum, &tot_ent);
     for (int q = s0; q < s1; ++q) {
         M.slot_off[q] = run2;
         run2 += M.counts[q];
     }
-    if (tid == MAP_THREADS - 1) M.slot_off[nslots] = part[MAP_THREADS - 1];
+    if (tid == 0) M.slot_off[nslots] = tot_ent;
     __syncthreads();
-    // 5. fill (taking the counts back to zero)
+    // 5. fill (taking the counts back to zero); the shared map goes out meanwhile
+    if (SMAP)
+        for (int w = tid; w < M.nw; w += MAP_THREADS) {
+            M.bits[w] = bits[w];
+            M.wprefix[w] = wprefix[w];
+        }
     for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
         const int64_t r = S[j];
         if (r < 0 || r >= A.m) continue;
         for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
             const int32_t c = A.col_idx[e];
-            const uint32_t w = M.bits[c >> 5];
-            const int slot = M.wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u));
+            const uint32_t w = bits[c >> 5];
+            const int slot = wprefix[c >> 5] + __popc(w & ((1u << (c & 31)) - 1u));
             const int pos = M.slot_off[slot] + atomicSub(&M.counts[slot], 1) - 1;
             M.ent_j[pos] = j;
             M.ent_v[pos] = A.vals64 ? A.vals64[e] : (double)A.vals32[e];
@@ -621,7 +645,19 @@ cudaError_t launch_csr_colmap(const CsrOperand &A, const int32_t *S, int64_t cnt
                               cudaStream_t st)
 {
     if (cnt <= 0) return cudaSuccess;
-    csr_colmap_kernel<<<1, MAP_THREADS, 0, st>>>(A, S, (int)cnt, M, err);
+    if (M.nw <= MAP_SMEM_WORDS) {
+        const size_t smem = (size_t)M.nw * 8;
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute(csr_colmap_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, MAP_SMEM_WORDS * 8);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        csr_colmap_kernel<true><<<1, MAP_THREADS, smem, st>>>(A, S, (int)cnt, M, err);
+    } else {
+        csr_colmap_kernel<false><<<1, MAP_THREADS, 0, st>>>(A, S, (int)cnt, M, err);
+    }
     return cudaGetLastError();
 }
 
