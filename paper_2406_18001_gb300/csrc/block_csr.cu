@@ -259,11 +259,19 @@ __global__ void __launch_bounds__(CSR_AW * 32, 3)
                 const int oq = ob + 128 * b + 4 * lane;  // offset of this lane's quad
                 const int32_t cc[4] = {cur[b].x, cur[b].y, cur[b].z, cur[b].w};
                 unsigned mk = 0;
+                if (ob + 128 * b >= 0 && ob + 128 * b + 128 <= n_e) {  // warp-uniform: the chunk lies in the tile
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool in = oq + q >= 0 && oq + q < n_e && cc[q] >= 0;
-                    if (in && ((SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5))) >> (cc[q] & 31)) & 1u)
-                        mk |= 1u << q;
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t wd = SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5));
+                        mk |= ((wd >> (cc[q] & 31)) & 1u) << q;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool in = oq + q >= 0 && oq + q < n_e && cc[q] >= 0;
+                        if (in && ((SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5))) >> (cc[q] & 31)) & 1u)
+                            mk |= 1u << q;
+                    }
                 }
                 if (!__any_sync(0xffffffffu, mk != 0)) continue;
                 // exclusive prefix of the per-lane hit counts = element order
