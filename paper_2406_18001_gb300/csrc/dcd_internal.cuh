@@ -138,6 +138,8 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
                                  const float *src_scale, uint8_t *dst, int64_t ldq, float *dst_scale, int64_t count,
                                  int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
+// *c += n (one thread)
+cudaError_t launch_advance(uint64_t *c, uint64_t n, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *scale = nullptr);
@@ -216,6 +218,14 @@ cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S
                                  double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st,
                                  const double *rhs = nullptr);
 int recur_cluster_panel_blocks(int b, int rounds);
+// the prep and chain halves of launch_recur_cluster (a step's prep may run
+// ahead, on another stream, of the previous step's chain)
+cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda,
+                                      double mdiag, void *scratch, int *err, cudaStream_t st);
+cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
+                                       double lambda, double mdiag, double *g, int rounds, void *scratch,
+                                       double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
+                                       cudaStream_t st, const double *rhs = nullptr);
 // 2-D tensor map over a row-major fp32 matrix (rows x cols, leading dimension
 // ld elements, ld * 4 a multiple of 16), box of box_rows x box_cols, no
 // swizzle, out-of-range elements read as zero (block_tc.cu)

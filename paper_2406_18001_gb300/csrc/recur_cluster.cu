@@ -646,10 +646,27 @@ size_t recur_cluster_scratch_bytes(int64_t nblk, int b)
     return 2 * (size_t)G.nsup * 1024 * 4 + (size_t)G.nsup * CL_NSUP_MAX * 32 * 4 + (size_t)nblk * b * 4;
 }
 
-cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
-                                 double lambda, double mdiag, double *g, int rounds, void *scratch, double *delta,
-                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st,
-                                 const double *rhs)
+// The two halves of launch_recur_cluster: the prep kernel (inverses,
+// couplings, repeat masks, links; it needs only Kss and S, so a step's prep
+// may run ahead of the previous step's chain) and the chain.
+cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, double lambda,
+                                      double mdiag, void *scratch, int *err, cudaStream_t st)
+{
+    const ClGeom G = cl_geom(nblk, b);
+    if (((uintptr_t)scratch & 15) != 0) return cudaErrorInvalidValue;
+    float *X = (float *)scratch;
+    float *N = X + (size_t)G.nsup * 1024;
+    uint32_t *M = (uint32_t *)(N + (size_t)G.nsup * 1024);
+    int32_t *next = (int32_t *)(M + (size_t)G.nsup * CL_NSUP_MAX * 32);
+    bdcd_prep_kernel<<<(unsigned)(2 * G.nsup), PREP_THREADS, 0, st>>>(Kss, ldk, S, nblk, b, (float)(1.0 / lambda),
+                                                                     (float)mdiag, X, N, M, next, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
+                                       double lambda, double mdiag, double *g, int rounds, void *scratch,
+                                       double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
+                                       cudaStream_t st, const double *rhs)
 {
     const ClGeom G = cl_geom(nblk, b);
     const int sb = nblk * b;
@@ -661,12 +678,9 @@ cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S
     int32_t *next = (int32_t *)(M + (size_t)G.nsup * CL_NSUP_MAX * 32);
     CUtensorMap kmap;
     if (!make_map_f32_2d(&kmap, Kss, sb, sb, ldk, G.Bs, G.Bs)) return cudaErrorInvalidValue;
-    bdcd_prep_kernel<<<(unsigned)(2 * G.nsup), PREP_THREADS, 0, st>>>(Kss, ldk, S, nblk, b, (float)(1.0 / lambda),
-                                                               (float)mdiag, X, N, M, next, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     auto kfn = bdcd_cluster_kernel;
     static bool attr = false;
+    cudaError_t e;
     if (!attr) {
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM_MAX);
         if (e != cudaSuccess) return e;
@@ -690,6 +704,17 @@ cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S
                               (const int32_t *)next, nblk, b, lambda, mdiag, g, rounds, delta, w64, w32,
                               upd ? upd->alpha : (double *)nullptr, upd ? upd->ctr : (uint64_t *)nullptr,
                               upd ? upd->ctr_advance : (uint64_t)0, rhs, err);
+}
+
+cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
+                                 double lambda, double mdiag, double *g, int rounds, void *scratch, double *delta,
+                                 double *w64, float *w32, const FusedUpdate *upd, int *err, cudaStream_t st,
+                                 const double *rhs)
+{
+    cudaError_t e = launch_recur_cluster_prep(Kss, ldk, S, nblk, b, lambda, mdiag, scratch, err, st);
+    if (e != cudaSuccess) return e;
+    return launch_recur_cluster_chain(Kss, ldk, S, nblk, b, P, lambda, mdiag, g, rounds, scratch, delta, w64, w32, upd,
+                                      err, st, rhs);
 }
 
 // The largest diagonal panel (in blocks) one cluster launch solves: the

@@ -14,7 +14,7 @@ namespace dcd {
 __global__ void sample_dcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
                                   int64_t count, int32_t *out)
 {
-    uint64_t first = ctr_dev ? *ctr_dev : first_host;
+    uint64_t first = (ctr_dev ? *ctr_dev : 0) + first_host;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
         out[j] = (int32_t)below(sm64_draw(seed, 0, first + (uint64_t)j), (uint64_t)m);
 }
@@ -30,7 +30,7 @@ __global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint6
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (warp >= nblocks) return;
-    const uint64_t t = (ctr_dev ? *ctr_dev : first_host) + (uint64_t)warp;
+    const uint64_t t = (ctr_dev ? *ctr_dev : 0) + first_host + (uint64_t)warp;
     int32_t *blk = sblk + (threadIdx.x >> 5) * b;
     for (int q = 0; q < b; ++q) {
         const int64_t J = m - b + q;
@@ -225,6 +225,14 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
     const int64_t blocks = (count * 32 + 255) / 256;
     quantize_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, src_scale, dst, ldq, dst_scale,
                                                            count, err);
+    return cudaGetLastError();
+}
+
+__global__ void advance_kernel(uint64_t *c, uint64_t n) { *c += n; }
+
+cudaError_t launch_advance(uint64_t *c, uint64_t n, cudaStream_t st)
+{
+    advance_kernel<<<1, 1, 0, st>>>(c, n);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,15 @@ namespace {
 constexpr int64_t SB_MAX = 8192;   // s*b per outer step
 constexpr int B_MAX = 128;         // block size
 
+// Set while the batched driver and the autotuner build their plans: those
+// capture many plans' steps into one graph and run without the look-ahead.
+thread_local bool t_no_lookahead = false;
+struct NoLookahead {
+    bool prev = t_no_lookahead;
+    NoLookahead() { t_no_lookahead = true; }
+    ~NoLookahead() { t_no_lookahead = prev; }
+};
+
 struct Arena {
     char *base = nullptr;
     size_t used = 0, cap = 0;
@@ -215,6 +224,14 @@ struct Solver {
     ~Solver()
     {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        for (auto &ge : graph_la)
+            if (ge) cudaGraphExecDestroy(ge);
+        if (st2) {
+            cudaStreamSynchronize(st2);
+            cudaStreamDestroy(st2);
+        }
+        if (la_fork) cudaEventDestroy(la_fork);
+        if (la_join) cudaEventDestroy(la_join);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
         if (ws) cudaFreeAsync(ws, st);
     }
@@ -262,6 +279,12 @@ struct Solver {
         const bool ref_op = tcd && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
         const bool fp8 = tcd && pack_kind(o.prec) == PACK_FP8;
         const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
+        // the look-ahead needs a stream of its own to fork from, graphs allowed, no per-phase
+        // timers, and a full step that fits one cluster recurrence
+        const bool la_pos = !t_no_lookahead && problem == 1 && tcd &&
+                            !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
+                            st != cudaStreamLegacy && st != cudaStreamPerThread &&
+                            recur_cluster_size((int)o.s, o.b, 2) > 0;
         const int64_t n_pad_r = (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
 
@@ -297,6 +320,14 @@ struct Solver {
             double *wv = (double *)ar.take(sizeof(double) * col_pad);
             double *lb = (double *)ar.take(problem == 1 ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             uint64_t *cr = (uint64_t *)ar.take(sizeof(uint64_t));
+            // the second set of step buffers and the look-ahead counter
+            int32_t *sidx_b = (int32_t *)ar.take(la_pos ? sizeof(int32_t) * col_pad : 0);
+            void *as_b = ar.take(la_pos ? (size_t)sb * row_bytes : 0, 1024);
+            float *ch_b = (float *)ar.take(la_pos ? sizeof(float) * col_pad : 0);
+            float *cs_b = (float *)ar.take(la_pos && fp8 ? sizeof(float) * col_pad : 0);
+            void *kss_b = ar.take(la_pos ? (size_t)sb * sb * 4 : 0);
+            double *lb_b = (double *)ar.take(la_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
+            uint64_t *crl = (uint64_t *)ar.take(la_pos ? sizeof(uint64_t) : 0);
             int *er = (int *)ar.take(sizeof(int) * 4);
             double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
             double *rs = (double *)ar.take(sizeof(double) * 4);
@@ -353,6 +384,19 @@ struct Solver {
             partials = pt;
             result = rs;
             iota = io;
+            sbuf[0].S = sidx;
+            sbuf[0].As = as;
+            sbuf[0].col_h = ch;
+            sbuf[0].col_s = csc;
+            sbuf[0].Kss = kss;
+            sbuf[0].Lbuf = lb;
+            sbuf[1].S = sidx_b;
+            sbuf[1].As = as_b;
+            sbuf[1].col_h = ch_b;
+            sbuf[1].col_s = cs_b;
+            sbuf[1].Kss = kss_b;
+            sbuf[1].Lbuf = lb_b;
+            ctr_la = crl;
             if (host) {
                 DCD_TRY(cudaMemcpyAsync(hv, A->values,
                                         (csr ? (size_t)nnz : (size_t)m * A->ld) * dtype_size(A->dtype),
@@ -373,6 +417,16 @@ struct Solver {
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
         if (tcd) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
         if (fp8) DCD_TRY(cudaMemsetAsync(col_s, 0, sizeof(float) * col_pad, st));
+        if (la_pos) {
+            DCD_TRY(cudaMemsetAsync(sbuf[1].S, 0, sizeof(int32_t) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[1].col_h, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[1].As, 0, (size_t)sb * row_bytes, st));
+            if (fp8) DCD_TRY(cudaMemsetAsync(sbuf[1].col_s, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+            DCD_TRY(cudaEventCreateWithFlags(&la_fork, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&la_join, cudaEventDisableTiming));
+            la = true;
+        }
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
 
         // operand
@@ -420,6 +474,7 @@ struct Solver {
                 opr = op;
                 Asr = As;
                 col_hr = col_h;
+                ref_shared = true;
             }
         } else if (need_pack) {
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st, src_scale));
@@ -678,8 +733,157 @@ struct Solver {
     int direct_full_steps = 0;
     bool graph_failed = false;
 
+    // ---- look-ahead (dense tensor-core K-RR on the single-cluster recurrence) ----
+    // Step k+1's sample, gathers, Gram and recurrence prep depend on its
+    // indices only, not on alpha or g, so they run on a second stream beside
+    // step k's chain (which occupies one cluster of SMs) and fused block.
+    // The step products live in two buffer sets used alternately; ctr_la is
+    // the index-stream position of the next step to sample, one step ahead of
+    // ctr (which the chain's a6 advances as before).
+    struct StepBufs {
+        int32_t *S = nullptr;
+        void *As = nullptr;
+        float *col_h = nullptr, *col_s = nullptr;
+        void *Kss = nullptr;
+        double *Lbuf = nullptr;
+    };
+    bool la = false;
+    StepBufs sbuf[2];
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t la_fork = nullptr, la_join = nullptr;
+    uint64_t *ctr_la = nullptr;
+    int la_par = 0;        // the buffer set holding the next step's products
+    int64_t la_cnt = 0;    // their step size (0: none pending)
+    bool ref_shared = false;  // the recomputed gradient uses the step operand's buffers
+    cudaGraphExec_t graph_la[2] = {nullptr, nullptr};
+    int la_direct[2] = {0, 0};
+
+    // the step members point at buffer set p
+    void use_bufs(int p)
+    {
+        S = sbuf[p].S;
+        As = sbuf[p].As;
+        col_h = sbuf[p].col_h;
+        col_s = sbuf[p].col_s;
+        Kss = sbuf[p].Kss;
+        Lbuf = sbuf[p].Lbuf;
+        if (ref_shared) {
+            Asr = As;
+            col_hr = col_h;
+        }
+    }
+
+    // step products of a step of cnt blocks into buffer set q, on stream s2
+    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2)
+    {
+        const StepBufs &Bq = sbuf[q];
+        const int64_t ncols = cnt * o.b;
+        DCD_TRY(launch_sample(problem, o.seed, ctr_la, 0, m, o.b, cnt, Bq.S, err, s2));
+        DCD_TRY(launch_advance(ctr_la, (uint64_t)cnt, s2));
+        DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2));
+        if (op.kind == PACK_FP8) DCD_TRY(launch_gather_f32(op.row_s, Bq.S, ncols, Bq.col_s, s2));
+        DCD_TRY(launch_gather_f32(op.row_h, Bq.S, ncols, Bq.col_h, s2));
+        TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s};
+        DCD_TRY(launch_block_tc(Bo, Bo, kp, Bq.col_h, Bq.col_h, nullptr, nullptr, nullptr, (float *)Bq.Kss, ldk, ncols,
+                                ncols, err, s2, true));
+        DCD_TRY(launch_recur_cluster_prep((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, lambda, (double)m, Bq.Lbuf,
+                                          err, s2));
+        return DCD_OK;
+    }
+
+    // the chain (with the a6 update) and the fused block of a step whose products are in set p
+    dcd_status la_main(int p, int64_t cnt)
+    {
+        const StepBufs &Bp = sbuf[p];
+        const int64_t ncols = cnt * o.b;
+        FusedUpdate fu;
+        fu.alpha = alpha;
+        fu.ctr = ctr;
+        fu.ctr_advance = (uint64_t)cnt;
+        const int P = recur_cluster_size((int)cnt, o.b, 2);
+        if (P <= 0) return DCD_EINTERNAL;
+        DCD_TRY(launch_recur_cluster_chain((const float *)Bp.Kss, ldk, Bp.S, (int)cnt, o.b, P, lambda, (double)m, g, 2,
+                                           Bp.Lbuf, delta, w64, col_w, &fu, err, st));
+        DCD_TRY(clear_col_w_tail(ncols));
+        TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
+        TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s};
+        DCD_TRY(launch_block_tc(Aop, Bop, kp, op.row_h, Bp.col_h, col_w, nullptr, g, nullptr, 0, m, ncols, err, st));
+        return DCD_OK;
+    }
+
+    // one look-ahead step: this step's chain and block on st; the next full
+    // step's products on st2 beside them (forked from and joined back into st)
+    dcd_status la_body(int p, int64_t cnt, int64_t next)
+    {
+        if (next) {
+            DCD_TRY(cudaEventRecord(la_fork, st));
+            DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
+            dcd_status r = la_side(1 - p, next, st2);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(la_join, st2));
+        }
+        dcd_status r = la_main(p, cnt);
+        if (r != DCD_OK) return r;
+        if (next) DCD_TRY(cudaStreamWaitEvent(st, la_join, 0));
+        return DCD_OK;
+    }
+
+    dcd_status la_step(int64_t cnt)
+    {
+        if (la_cnt != cnt) {  // nothing pending: this step's products first, on st
+            DCD_TRY(cudaMemcpyAsync(ctr_la, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+            dcd_status r = la_side(la_par, cnt, st);
+            if (r != DCD_OK) return r;
+            la_cnt = cnt;
+        }
+        const int p = la_par;
+        const int64_t next = (o.max_iters - done - cnt) >= o.s ? o.s : 0;  // only full steps are prepared ahead
+        if (next && cnt == o.s && !graph_failed) {
+            if (graph_la[p]) {
+                DCD_TRY(cudaGraphLaunch(graph_la[p], st));
+            } else if (la_direct[p] >= 1) {
+                DCD_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                const dcd_status sc = la_body(p, cnt, next);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+                const bool ok = sc == DCD_OK && ec == cudaSuccess && graph != nullptr &&
+                                cudaGraphInstantiate(&graph_la[p], graph, 0) == cudaSuccess;
+                if (ok) stats.gpu_launches_per_step = count_kernel_nodes(graph);
+                if (graph) cudaGraphDestroy(graph);
+                if (!ok) {
+                    cudaGetLastError();
+                    graph_la[p] = nullptr;
+                    graph_failed = true;
+                    dcd_status r = la_body(p, cnt, next);
+                    if (r != DCD_OK) return r;
+                } else {
+                    DCD_TRY(cudaGraphLaunch(graph_la[p], st));
+                }
+            } else {
+                dcd_status r = la_body(p, cnt, next);
+                if (r != DCD_OK) return r;
+                ++la_direct[p];
+            }
+        } else {
+            dcd_status r = la_body(p, cnt, next);
+            if (r != DCD_OK) return r;
+        }
+        la_par = 1 - p;
+        la_cnt = next;
+        use_bufs(p);  // the set just used is free (for a gradient recomputation) while the other holds products
+        return DCD_OK;
+    }
+
     dcd_status outer_step(int64_t cnt, EventTimer &tm)
     {
+        if (la && !tm.on && recur_cluster_size((int)cnt, o.b, 2) > 0) {
+            dcd_status r = la_step(cnt);
+            if (r != DCD_OK) return r;
+            done += cnt;
+            ++steps;
+            return DCD_OK;
+        }
+        if (la_cnt) return DCD_EINTERNAL;  // prepared products would be skipped
         const bool graphable = !tm.on && !(o.flags & DCD_FLAG_NO_GRAPH) && cnt == o.s && st != nullptr &&
                                st != cudaStreamLegacy && st != cudaStreamPerThread && !graph_failed;
         if (graphable && graph_exec) {
@@ -1301,6 +1505,7 @@ dcd_status time_per_update(const dcd_matrix *A, const double *y, const dcd_kerne
                            int prec, double *alpha, double *grad, cudaStream_t st, double &ms_per)
 {
     const int warm = 2, timed = 3;  // warm-up: one direct step and the step that is captured
+    NoLookahead nla;  // timed as the batched driver runs it
     dcd_opts o{};
     o.s = s;
     o.b = b;
@@ -1384,6 +1589,7 @@ extern "C" dcd_status bdcd_krr_solve_batched(const dcd_krr_problem *probs, int32
     }
 
     // one plan per problem, round-robin over the worker streams
+    NoLookahead nla;  // the batch graph captures rounds of many plans' steps
     std::vector<std::unique_ptr<dcd_plan>> plans(count);
     for (int i = 0; i < count; ++i) {
         dcd_opts o{};
