@@ -681,7 +681,7 @@ def run_gpu_sweep(args):
             sig, lam = grid[p % len(grid)]
             probs.append(dict(A=torch.from_numpy(pr.A).to(dev), y=torch.from_numpy(pr.y).to(dev),
                               k=B.kernel("rbf", gamma=1.0 / (2 * sig * sig)), lam=lam, b=8 if p % 2 == 0 else 32,
-                              s=0, H=args.sweep_H, seed=p))
+                              s=args.sweep_s if args.sweep_s else 0, H=args.sweep_H, seed=p))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, st0, _ = B.krr_solve_batched(probs, prec=args.prec, stream=stream.cuda_stream)  # autotune + warm-up
@@ -692,7 +692,8 @@ def run_gpu_sweep(args):
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
-            _, _, sts, _ = B.krr_solve_batched(probs, prec=args.prec, stream=stream.cuda_stream)
+            _, _, sts, _ = B.krr_solve_batched(probs, prec=args.prec, streams=args.sweep_streams,
+                                               stream=stream.cuda_stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
         # the same solves one after another (bdcd_krr_solve each), for the batching gain
@@ -703,7 +704,44 @@ def run_gpu_sweep(args):
                         stream=stream.cuda_stream)
         torch.cuda.synchronize()
         wall_seq = time.perf_counter() - t0
+        # end to end: pinned host inputs in, the batched call, every alpha back
+        host = []
+        for p in range(count):
+            pr = inputs.sweep_problem(p + 1000 * rank)
+            host.append((torch.from_numpy(pr.A).pin_memory(), torch.from_numpy(pr.y).pin_memory()))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p, (Ah, yh) in zip(probs, host):
+            p["A"] = Ah.to(dev, non_blocking=True)
+            p["y"] = yh.to(dev, non_blocking=True)
+        al_e2e, _, _, _ = B.krr_solve_batched(probs, prec=args.prec, stream=stream.cuda_stream)
+        al_h = [a.to("cpu", non_blocking=True) for a in al_e2e]
+        torch.cuda.synchronize()
+        wall_e2e = time.perf_counter() - t0
+        h2d = sum(Ah.nbytes + yh.nbytes for Ah, yh in host)
+        d2h = sum(a.numel() * 8 for a in al_h)
     upd = sum(int(st["iters_done"]) * p["b"] for st, p in zip(sts, probs))
+    launches = sum(int(st["gpu_launches_per_step"]) * int(st["outer_steps"]) for st in sts)
+    # roofline of the whole call: every outer step is one fused block, 2 m n sb flops per MMA pass (x3
+    # for the split forms), and reads its problem's packed operand once
+    n_sw = 128
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
+    mult = 3 if args.prec in ("bf16x3", "tf32x3") else 1
+    flops = sum(int(st["outer_steps"]) * 2.0 * p["A"].shape[0] * n_sw * p["s"] * p["b"] * mult
+                for st, p in zip(sts, probs))
+    bytes_ = sum(int(st["outer_steps"]) * (p["A"].shape[0] * (n_sw * esz + 20) + p["s"] * p["b"] * n_sw * esz)
+                 for st, p in zip(sts, probs))
+    hbm_peak, bf16_peak, _, src = peaks()
+    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}.get(args.prec, 0.0) * bf16_peak
+    roof = {"bound": "tensor", "achieved": flops / wall / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+            "frac": flops / wall / 1e12 / tc_peak if tc_peak else None, "traffic": None, "peak_source": src,
+            "kernel": "whole batched call (all problems' steps)",
+            "algorithmic": {"flops": flops, "bytes": bytes_, "hbm_gbs": bytes_ / wall / 1e9, "wall_s": wall}}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = sweep_cpu_baseline(probs, upd)
+    e2e = {"value": ws * upd / wall_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "steps": 1, "wall_s": wall_e2e}
     s_hist = {}
     for p in probs:
         s_hist[f"b{p['b']}_s{p['s']}"] = s_hist.get(f"b{p['b']}_s{p['s']}", 0) + 1
@@ -712,14 +750,42 @@ def run_gpu_sweep(args):
                "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                "config": {"workload": WORKLOAD_SWEEP, "problems": count, "H_block_updates": args.sweep_H,
-                          "precision": args.prec, "streams": 16, "rounds_per_graph": 8,
+                          "precision": args.prec, "streams": args.sweep_streams, "rounds_per_graph": 8,
                           "l2": "problems total ~0.65 GB of A (above L2); one timed batched call"},
                "sweep": {"coordinate_updates": upd, "wall_s": wall, "sequential_single_solves_wall_s": wall_seq,
                          "first_call_with_autotune_s": t_first,
                          "s_chosen": s_hist, "converged": sum(int(st["converged"]) for st in sts)},
-               "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
+
+
+def sweep_cpu_baseline(probs, upd_total, nsample=8, budget_s=15.0):
+    """The FP64 oracle (Algorithm 3, one thread) on a few of the sweep's
+    problems for a bounded time; a block update costs ~ m * n * b, so the
+    rate is measured as m * coordinate updates per second and the whole
+    sweep's time estimated from it."""
+    import oracle
+    oracle.build()
+    idx = np.linspace(0, len(probs) - 1, nsample).astype(int)
+    work = 0.0
+    t0 = time.perf_counter()
+    for i in idx:
+        p = probs[i]
+        A = p["A"].cpu().numpy().astype(np.float64)
+        y = p["y"].cpu().numpy()
+        k = oracle.kernel("rbf", gamma=p["k"].gamma)
+        blocks = max(1, int(2.4e9 / (A.shape[0] * A.shape[1] * p["b"])))  # ~ the same work per sampled problem
+        oracle.bdcd_krr(A, y, k, p["lam"], p["b"], blocks, seed=p["seed"])
+        work += A.shape[0] * blocks * p["b"]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    rate_mu = work / dt  # m * coordinate updates per second
+    total_mu = sum(p["A"].shape[0] * p["H"] * p["b"] for p in probs)
+    return {"value": upd_total / (total_mu / rate_mu), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Algorithm 3 on {len(idx)} of the {len(probs)} problems ({dt:.1f} s, plain FP64 C, one "
+                      f"thread); the whole sweep's time estimated from the measured m x updates per second"}
 
 
 def main():
@@ -736,6 +802,8 @@ def main():
                          "fp8: the FP8 / BF16 storage stress configuration")
     ap.add_argument("--sweep-count", type=int, default=256)
     ap.add_argument("--sweep-H", type=int, default=2048, help="block updates per problem")
+    ap.add_argument("--sweep-s", type=int, default=0, help="fixed s for every problem (0: the autotuner's)")
+    ap.add_argument("--sweep-streams", type=int, default=16, help="worker streams of the batched call")
     ap.add_argument("--fp8-m", type=int, default=400000)
     ap.add_argument("--fp8-n", type=int, default=2048)
     ap.add_argument("--fp8-sub", type=int, default=20000, help="rows of the alpha-error subproblem")
