@@ -336,6 +336,34 @@ def test_graph_replay_and_enqueue_match_direct_launches(problem, prec):
         pl.close()
 
 
+@pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("fp8", True), ("tf32x3", False)])
+def test_lookahead_matches_one_stream_steps(prec, fp8):
+    """The look-ahead (next step's sample, Gram and prep on a second stream,
+    ping-pong step buffers, even/odd step graphs) must give the iterates of
+    the one-stream steps bit for bit, also with convergence checks and
+    gradient recomputations between steps (which use the idle buffer set)."""
+    p = inputs.krr_dense(m=2000, n=48, seed=31, dtype=np.float32)
+    kb = B().kernel("rbf", gamma=0.5)
+    b, s, H = 16, 64, 23 * 64 + 16 * 5
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        if fp8:
+            q, sc = oracle.quantize_e4m3_rows(p.A)
+            A = B().Fp8(dev(q), dev(sc))
+        else:
+            A = dev(p.A)
+        y = dev(p.y)
+        runs = []
+        for flags in (B().FLAG_NO_GRAPH, 0):  # one stream (direct) / look-ahead (graphs)
+            al, gr, st, rc = B().krr_solve(A, y, kb, 1e-3, b, s, H, seed=7, prec=prec, tol=5e-3, check_every=2,
+                                           flags=flags | B().FLAG_REFRESH, stream=side.cuda_stream)
+            runs.append((al, gr, st))
+        side.synchronize()
+    (a0, g0, s0), (a1, g1, s1) = runs
+    assert s0["iters_done"] == s1["iters_done"] and s0["refreshes"] == s1["refreshes"] >= 1
+    assert torch.equal(a0, a1) and torch.equal(g0, g1)
+
+
 def test_nonzero_alpha0_gradient_pass():
     p = inputs.blobs(m=260, n=9, seed=10)
     kb, ko = B().kernel("rbf", gamma=0.3), oracle.kernel("rbf", gamma=0.3)
