@@ -260,6 +260,10 @@ struct TcArgs {
     float two_gl;         // 2 * gamma * log2(e)
     float coef0;
     int *err;
+    double *part;         // apply on pairs: per-chunk row sums of the row tiles two pairs share (or null)
+    unsigned *cnt;        // apply on pairs: arrivals per shared tile and CTA rank
+    int late_pairs;       // apply on pairs: the last late_pairs pairs take late_units units fewer
+    int late_units;
 };
 
 // K(a_i, b_j) from the accumulator c; rf is the per-row factor: 2 gamma
@@ -568,6 +572,50 @@ __device__ __forceinline__ void mma_commit_own2(uint64_t *bar)
                  : "memory");
 }
 
+// The (row tile, N-chunk) units of a pair.  Ranged: the units, in row-major
+// order, are cut into npairs contiguous ranges (each at least one tile long,
+// so a tile is shared by at most two pairs) of near-equal length, or, with
+// late pairs, the last L pairs' ranges D units shorter than the others'.
+// Else each pair takes whole tiles pair, pair + npairs, ...
+// (The host keeps items * nchunks below 2^31.)
+__device__ __forceinline__ int64_t range_start(int64_t U, int npairs, int L, int D, int p)
+{
+    // sum of the first p range lengths (times npairs): early ranges s = (U + L D) / npairs, late s - D
+    const int64_t late = p > npairs - L ? p - (npairs - L) : 0;
+    return ((int64_t)p * (U + (int64_t)L * D) - (int64_t)npairs * D * late) / npairs;
+}
+
+__device__ __forceinline__ void pair_units(const TcArgs &a, int pair, int npairs, bool &ranged, int &u0, int &u1,
+                                           int &n)
+{
+    const int64_t U = (int64_t)a.items * a.nchunks;
+    ranged = a.part != nullptr && U / npairs >= a.nchunks;
+    if (ranged) {
+        int L = a.late_pairs, D = a.late_units;
+        if (L <= 0 || L >= npairs || D <= 0 || (U + (int64_t)L * D) / npairs - D < a.nchunks) L = D = 0;
+        u0 = (int)range_start(U, npairs, L, D, pair);
+        u1 = (int)range_start(U, npairs, L, D, pair + 1);
+        n = u1 - u0;
+    } else {
+        u0 = 0;
+        u1 = (int)U;
+        n = pair < a.items ? (a.items - pair + npairs - 1) / npairs * a.nchunks : 0;
+    }
+}
+
+__device__ __forceinline__ void pair_unit(const TcArgs &a, int pair, int npairs, bool ranged, int u0, int i, int &tile,
+                                          int &nc)
+{
+    if (ranged) {
+        const int u = u0 + i;
+        tile = u / a.nchunks;
+        nc = u % a.nchunks;
+    } else {
+        tile = pair + i / a.nchunks * npairs;
+        nc = i % a.nchunks;
+    }
+}
+
 template <int MODE, int KIND>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     block_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
@@ -632,6 +680,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const int bn = a.bn, bh = bn / 2;
     const int kb_elems = TF32 ? 32 : FP8 ? 128 : 64;
     const uint32_t full0 = ptx::mapa(su32(full), 0), tempty0 = ptx::mapa(su32(tempty), 0);
+    bool ranged;
+    int u0, u1, nunits;
+    pair_units(a, pair, npairs, ranged, u0, u1, nunits);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -639,9 +690,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             const uint32_t bytes = (uint32_t)(2 * (SPLIT ? 2 : 1) * (A_STAGE + bh * ROW_BYTES));  // both CTAs'
-            for (int item = pair; ok && item < a.items; item += npairs)
-                for (int nc = 0; ok && nc < a.nchunks; ++nc)
-                    for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+            for (int i = 0; ok && i < nunits; ++i) {
+                int item, nc;
+                pair_unit(a, pair, npairs, ranged, u0, i, item, nc);
+                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
                         if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
                             ok = false;
@@ -657,6 +709,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                             tma_load_2d_pair(sB + s * B_ST + B2_STAGE, &tmB, fb, a.lo_off + kb * kb_elems, yb);
                         }
                     }
+            }
             // the last stages' empties arrive after the final MMAs: wait for them, so that no
             // commit is still addressed to this CTA when the pair leaves (bounded)
             const uint32_t first = it > STAGES ? it - STAGES : 0;
@@ -668,8 +721,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const uint32_t idesc = make_idesc(TF32 ? 2 : FP8 ? 0 : 1, bn, BM2);
             uint32_t it = 0, acc_it = 0;
             bool ok = true, issued = false;
-            for (int item = pair; ok && item < a.items; item += npairs)
-                for (int nc = 0; ok && nc < a.nchunks; ++nc, ++acc_it) {
+            for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
                     const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
                     if (!mbar_wait(&tempty[buf], aph ^ 1, abort_flag, a.err)) {
                         ok = false;
@@ -707,6 +759,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ------------------------------------------------------ epilogue --
+        // the coefficients and the gradient may come from the grid before this one (a programmatic
+        // dependency: the tensor-memory products above start without it); a no-op otherwise
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
@@ -716,13 +771,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         float *cst = (float *)(smem + RING2_BYTES + 256 + XCH_BYTES) + (warp - 2) * CST_FLOATS;
         uint32_t acc_it = 0, item_it = 0;
         bool ok = true;
-        for (int item = pair; ok && item < a.items; item += npairs, ++item_it) {
-            const int64_t row = (int64_t)item * BM2 + (int64_t)rank * BM + row_in_tile;
-            const bool row_ok = row < a.nrows_out;
-            const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
-            const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
-            const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
-            double racc = 0.0;
+        int64_t row = 0;
+        bool row_ok = false;
+        float hr = 0.f, rf = 0.f;
+        double tacc = 0.0;  // this half's row sum over the tile's chunks so far, in chunk order
+        const int nch = a.nchunks;
+        for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
+            int item, nc;
+            pair_unit(a, pair, npairs, ranged, u0, i, item, nc);
+            if (i == 0 || nc == 0) {  // first chunk of a tile in this pair's units
+                row = (int64_t)item * BM2 + (int64_t)rank * BM + row_in_tile;
+                row_ok = row < a.nrows_out;
+                hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
+                const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
+                rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
+                tacc = 0.0;
+            }
+            const bool whole = !ranged || (item * nch >= u0 && (item + 1) * nch <= u1);
+            const bool last = nc == nch - 1 || i == nunits - 1;  // last chunk of the tile in this pair's units
+            double cs = 0.0;  // this chunk's part of the row sum (this half's column groups)
             // one 32-column group: terms from the staged columns (4 per shared-memory load), the
             // same sums in the same order as a column-by-column loop
             auto group = [&](const uint32_t(&r)[32], int j0) {
@@ -747,46 +814,76 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     p0 = fmaf(kf32<KIND>(c2, hr, hh.z, rf, a), ww.z, p0);
                     p1 = fmaf(kf32<KIND>(c3, hr, hh.w, rf, a), ww.w, p1);
                 }
-                racc += (double)p0 + (double)p1;
+                cs += (double)p0 + (double)p1;
             };
-            for (int nc = 0; nc < a.nchunks; ++nc, ++acc_it) {
-                const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
-                // stage this warp's columns while the accumulator is still being formed
-                const int64_t cbase = (int64_t)nc * bn + cg0 * 32;
-                for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
-                    if (KIND == DCD_RBF) cst[j] = a.col_h[cbase + j];
-                    cst[128 + j] = a.col_w[cbase + j];
-                    if (FP8) cst[256 + j] = a.col_s[cbase + j];
+            const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+            // stage this warp's columns while the accumulator is still being formed
+            const int64_t cbase = (int64_t)nc * bn + cg0 * 32;
+            for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
+                if (KIND == DCD_RBF) cst[j] = a.col_h[cbase + j];
+                cst[128 + j] = a.col_w[cbase + j];
+                if (FP8) cst[256 + j] = a.col_s[cbase + j];
+            }
+            __syncwarp();
+            const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
+            if (!__all_sync(0xffffffffu, seen)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t tb = tmem_base + lane_addr + buf * (uint32_t)bn;
+            uint32_t ra[32], rb[32];
+            if (cg0 < cg1) {
+                tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
+                tmem_ld_wait(ra);
+            }
+            for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
+                if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
+                group(ra, (cg - cg0) * 32);
+                if (cg + 1 < cg1) {
+                    tmem_ld_wait(rb);
+                    if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
+                    group(rb, (cg + 1 - cg0) * 32);
+                    if (cg + 2 < cg1) tmem_ld_wait(ra);
                 }
-                __syncwarp();
-                const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
-                if (!__all_sync(0xffffffffu, seen)) {
-                    ok = false;
-                    break;
-                }
-                fence_after();
-                const uint32_t tb = tmem_base + lane_addr + buf * (uint32_t)bn;
-                uint32_t ra[32], rb[32];
-                if (cg0 < cg1) {
-                    tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
-                    tmem_ld_wait(ra);
-                }
-                for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
-                    if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
-                    group(ra, (cg - cg0) * 32);
-                    if (cg + 1 < cg1) {
-                        tmem_ld_wait(rb);
-                        if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
-                        group(rb, (cg + 1 - cg0) * 32);
-                        if (cg + 2 < cg1) tmem_ld_wait(ra);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) arrive_cl(tempty0 + 8u * buf);
+            if (!whole) {
+                // a tile shared with the neighbouring pair: park this chunk's sums in its slot (the
+                // index of the pair boundary inside the tile); the last of the 16 epilogue warps of
+                // the two pairs (this CTA rank) to arrive adds every chunk's sums in chunk order
+                const int slot = item * nch < u0 ? pair : pair + 1;
+                double *pt = a.part + (size_t)slot * nch * 2 * BM2 + (size_t)rank * BM;
+                pt[((size_t)nc * 2 + half) * BM2 + row_in_tile] = cs;
+                if (last) {
+                    __threadfence();
+                    __syncwarp();
+                    unsigned old = 0;
+                    if (lane == 0) old = atomicAdd(&a.cnt[2 * slot + (int)rank], 1u);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    if (old == 15u) {
+                        __threadfence();
+                        for (int r = lane; r < BM; r += 32) {
+                            const int64_t grow = (int64_t)item * BM2 + (int64_t)rank * BM + r;
+                            if (grow >= a.nrows_out) continue;
+                            double t0 = 0.0, t1 = 0.0;
+                            for (int k = 0; k < nch; ++k) {
+                                t0 += __ldcg(pt + (size_t)k * 2 * BM2 + r);
+                                t1 += __ldcg(pt + ((size_t)k * 2 + 1) * BM2 + r);
+                            }
+                            a.g[grow] += (a.rs ? a.rs[grow] : 1.0) * (t0 + t1);
+                        }
+                        if (lane == 0) a.cnt[2 * slot + (int)rank] = 0u;
                     }
                 }
-                fence_before();
-                __syncwarp();
-                if (lane == 0) arrive_cl(tempty0 + 8u * buf);
+                continue;
             }
-            if (!ok) break;
+            tacc += cs;
+            if (!last) continue;
             const uint32_t xb = item_it & 1, xph = (item_it >> 1) & 1;
+            ++item_it;
             double *xc = xch + xb * BM;
             if (half) {
                 const bool fr = mbar_wait(&xfree[xb], xph ^ 1, abort_flag, a.err);
@@ -794,7 +891,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     ok = false;
                     break;
                 }
-                xc[row_in_tile] = racc;
+                xc[row_in_tile] = tacc;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&xfull[xb]);
             } else {
@@ -803,10 +900,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     ok = false;
                     break;
                 }
-                racc += xc[row_in_tile];
+                const double tot = tacc + xc[row_in_tile];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&xfree[xb]);
-                if (row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * racc;
+                if (row_ok) a.g[row] += (a.rs ? a.rs[row] : 1.0) * tot;
             }
         }
     }
@@ -878,7 +975,8 @@ cudaError_t launch_mode(int grid, const CUtensorMap &mA, const CUtensorMap &mB, 
 }
 
 template <int MODE, int KIND>
-cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st)
+cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st,
+                         bool pdl)
 {
     auto kfn = block_tc2_kernel<MODE, KIND>;
     static int max_pairs = 0;  // co-resident pairs, queried once per instantiation (before any capture)
@@ -896,17 +994,30 @@ cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &m
         max_pairs = n;
     }
     if (npairs > max_pairs) npairs = max_pairs;
-    kfn<<<2 * npairs, NTHREADS, SMEM2_BYTES, st>>>(mA, mB, a);
-    return cudaGetLastError();
+    if (!pdl) {
+        kfn<<<2 * npairs, NTHREADS, SMEM2_BYTES, st>>>(mA, mB, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * npairs, 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM2_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kfn, mA, mB, a);
 }
 
 template <int MODE>
 cudaError_t launch_mode2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, int kind,
-                         cudaStream_t st)
+                         cudaStream_t st, bool pdl)
 {
-    if (kind == DCD_RBF) return launch_kind2<MODE, DCD_RBF>(npairs, mA, mB, a, st);
-    if (kind == DCD_POLY) return launch_kind2<MODE, DCD_POLY>(npairs, mA, mB, a, st);
-    return launch_kind2<MODE, DCD_LINEAR>(npairs, mA, mB, a, st);
+    if (kind == DCD_RBF) return launch_kind2<MODE, DCD_RBF>(npairs, mA, mB, a, st, pdl);
+    if (kind == DCD_POLY) return launch_kind2<MODE, DCD_POLY>(npairs, mA, mB, a, st, pdl);
+    return launch_kind2<MODE, DCD_LINEAR>(npairs, mA, mB, a, st, pdl);
 }
 
 }  // namespace
@@ -938,7 +1049,8 @@ bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t 
 
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
                             const float *col_h, const float *col_w, const double *rs, double *g, float *out,
-                            int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st, bool lower)
+                            int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st, bool lower,
+                            const TcSplit *split, bool pdl, int max_pairs)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
@@ -951,8 +1063,9 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     int bn = (int)((ncols + 31) / 32) * 32;
     if (bn > BN_MAX) bn = BN_MAX;
     // store mode (the sampled Gram) has few rows: narrower N-chunks give
-    // more work items and spread them over more SMs
-    if (out != nullptr) bn = bn > 64 ? 64 : bn;
+    // more work items and spread them over more SMs -- unless it is held to a
+    // few CTAs (max_pairs), where wide chunks mean fewer, longer items
+    if (out != nullptr && max_pairs <= 0) bn = bn > 64 ? 64 : bn;
     // the apply form runs on CTA pairs (each CTA stages half of an N-chunk of B)
     const bool pair = out == nullptr;
     CUtensorMap mA, mB;
@@ -981,6 +1094,10 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.two_gl = (float)(2.0 * kp.gamma * 1.4426950408889634);
     a.coef0 = (float)kp.coef0;
     a.err = err;
+    a.part = nullptr;
+    a.cnt = nullptr;
+    a.late_pairs = 0;
+    a.late_units = 0;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -988,14 +1105,23 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     if (pair) {
-        const int npairs = a.items < sms / 2 ? a.items : sms / 2;
-        if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st);
-        if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st);
-        if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st);
-        if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st);
-        return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st);
+        if ((int64_t)a.num_tiles * a.nchunks >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+        int npairs = a.items < sms / 2 ? a.items : sms / 2;
+        if (max_pairs > 0 && npairs > max_pairs) npairs = max_pairs;
+        if (split && split->part && split->cnt && split->pairs >= npairs && split->chunks >= a.nchunks) {
+            a.part = split->part;
+            a.cnt = split->cnt;
+            a.late_pairs = split->late_pairs;
+            a.late_units = split->late_units;
+        }
+        if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st, pdl);
+        if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl);
+        if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st, pdl);
+        if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st, pdl);
+        return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st, pdl);
     }
     int grid = a.items < sms ? a.items : sms;
+    if (max_pairs > 0 && grid > max_pairs) grid = max_pairs;
     if (Aop.kind == PACK_TF32) return launch_mode<MODE_TF32>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_BF16X3) return launch_mode<MODE_BF16X3>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_TF32X3) return launch_mode<MODE_TF32X3>(grid, mA, mB, a, kp.kind, st);

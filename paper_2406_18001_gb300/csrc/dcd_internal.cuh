@@ -75,8 +75,11 @@ __device__ __forceinline__ double kfun_f64(const KernelParams &kp, double v)
 
 // --------------------------------------------------------- host launches --
 // All launchers enqueue on `st` and return cudaGetLastError().
+// ctr_next (optional, not ctr_dev): receives the stream position after this
+// sample, *ctr_dev + first_host + count.
 cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host,
-                          int64_t m, int b, int64_t count, int32_t *out, int *err, cudaStream_t st);
+                          int64_t m, int b, int64_t count, int32_t *out, int *err, cudaStream_t st,
+                          uint64_t *ctr_next = nullptr);
 
 // FP64 CUDA-core kernel block over a dense matrix of doubles.
 //   apply (out == nullptr): g[i] += rs[i] * sum_c K(a_i, a_cols[c]) * w[c] for i < nrows
@@ -121,10 +124,37 @@ __host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
 bool tc_available();
 // lower (store form only): write only the N-chunks that reach the diagonal
 // (column chunk start <= last row of the tile); the rest of out is left as is
+//
+// pdl (apply form): launch as a programmatic dependent of the kernel before
+// it on st; the products start at once, the epilogue waits for that kernel
+// to finish before it reads col_w or g (the kernel before must not write
+// anything else this launch reads).  max_pairs > 0 caps the CTA pairs of
+// the apply form (to leave SMs to a kernel running beside it), or the CTAs
+// of the store form (which then takes N-chunks of up to 256 columns).
+//
+// Apply form: the CTA pairs split the (row tile, N-chunk) units into equal
+// contiguous ranges when a TcSplit scratch is given (a row tile may then be
+// shared by two pairs; the one finishing last adds the per-chunk sums of
+// both), else each pair takes whole row tiles round-robin.  Both orders
+// give the same bits: every row sum is formed from per-chunk partial sums
+// added in chunk order.
+struct TcSplit {
+    double *part = nullptr;    // tc_split_part_elems(pairs, chunks) doubles
+    unsigned *cnt = nullptr;   // 2 * pairs counters, zero before the first launch (left at zero)
+    int pairs = 0;             // capacity: CTA pairs
+    int chunks = 0;            // capacity: N-chunks of 256 columns
+    // the last late_pairs pairs of the grid take late_units units fewer than the
+    // others (pairs that start late, on SMs a kernel before this one still holds)
+    int late_pairs = 0;
+    int late_units = 0;
+};
+inline int64_t tc_split_part_elems(int pairs, int chunks) { return (int64_t)pairs * chunks * 2 * 256; }
+inline int tc_split_chunks(int64_t ncols) { return ncols <= 256 ? 1 : (int)((ncols + 255) / 256); }
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
                             const float *row_h, const float *col_h, const float *col_w, const double *rs,
                             double *g, float *out, int64_t ldo, int64_t nrows_out, int64_t ncols,
-                            int *err, cudaStream_t st, bool lower = false);
+                            int *err, cudaStream_t st, bool lower = false, const TcSplit *split = nullptr,
+                            bool pdl = false, int max_pairs = 0);
 
 // setup / per-step helpers (sample_update.cu)
 // src_scale: the per-row scales of an FP8 source (dtype DCD_FP8E4M3), else unused
@@ -143,8 +173,11 @@ cudaError_t launch_advance(uint64_t *c, uint64_t n, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *scale = nullptr);
+// with the rows, optionally the per-row values f0 (and f1) of the same
+// indices: d0[j] = f0[idx[j]] (0 for an index outside [0, m))
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
-                               void *dst, int *err, cudaStream_t st);
+                               void *dst, int *err, cudaStream_t st, const float *f0 = nullptr, float *d0 = nullptr,
+                               const float *f1 = nullptr, float *d1 = nullptr);
 cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
@@ -225,7 +258,9 @@ cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32
 cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                        double lambda, double mdiag, double *g, int rounds, void *scratch,
                                        double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
-                                       cudaStream_t st, const double *rhs = nullptr);
+                                       cudaStream_t st, const double *rhs = nullptr, int trig_sup = -1);
+// (trig_sup: the super-block of 32 rows after whose first-round result a
+// kernel launched as this one's programmatic dependent may start; -1: at once)
 // 2-D tensor map over a row-major fp32 matrix (rows x cols, leading dimension
 // ld elements, ld * 4 a multiple of 16), box of box_rows x box_cols, no
 // swizzle, out-of-range elements read as zero (block_tc.cu)

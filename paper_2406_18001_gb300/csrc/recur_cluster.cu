@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     bdcd_cluster_kernel(const __grid_constant__ CUtensorMap kmap, const int32_t *S, const float *X,
                         const float *Ng, const uint32_t *Mg, const int32_t *nextg, int nblk, int b, double lambda,
                         double mdiag, double *g, int rounds, double *delta, double *w64, float *w32, double *alpha,
-                        uint64_t *ctr, uint64_t ctr_advance, const double *rhs_in, int *err)
+                        uint64_t *ctr, uint64_t ctr_advance, const double *rhs_in, int trig_sup, int *err)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int P = (int)gridDim.x;  // the grid is one cluster
@@ -376,6 +376,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int slot = warp & 1, role = warp >> 1;
     const int nown = L.nown;
+    // A kernel launched after this one as a programmatic dependent (the fused block, on the SMs
+    // this cluster leaves free) may start its set-up and tensor-core products once every CTA has
+    // signalled; it waits for this grid to finish before it reads the coefficients or the
+    // gradient.  The CTA owning super-block trig_sup signals when its round-0 Delta is out (the
+    // kernels forked beside the chain have the other SMs until then); every other CTA at once.
+    const bool trig_own = trig_sup >= 0 && (trig_sup == cl_own(0, c, P) || (nown > 1 && trig_sup == cl_own(1, c, P)));
+    if (tid == 0 && !trig_own) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float inv_lam = (float)(1.0 / lambda);
     const float mf = (float)mdiag;
 
@@ -529,6 +536,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
                 if (w32) w32[row] = (float)(dd / lambda);
             }
         }
+        if (r == 0 && J == trig_sup && lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         if (r == 0 && rounds > 1) {  // always release the round-1 warp (it gives up if this one did)
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(rbar);
@@ -666,7 +674,7 @@ cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32
 cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                        double lambda, double mdiag, double *g, int rounds, void *scratch,
                                        double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
-                                       cudaStream_t st, const double *rhs)
+                                       cudaStream_t st, const double *rhs, int trig_sup)
 {
     const ClGeom G = cl_geom(nblk, b);
     const int sb = nblk * b;
@@ -703,7 +711,7 @@ cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int3
     return cudaLaunchKernelEx(&cfg, kfn, kmap, S, (const float *)X, (const float *)N, (const uint32_t *)M,
                               (const int32_t *)next, nblk, b, lambda, mdiag, g, rounds, delta, w64, w32,
                               upd ? upd->alpha : (double *)nullptr, upd ? upd->ctr : (uint64_t *)nullptr,
-                              upd ? upd->ctr_advance : (uint64_t)0, rhs, err);
+                              upd ? upd->ctr_advance : (uint64_t)0, rhs, trig_sup, err);
 }
 
 cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,

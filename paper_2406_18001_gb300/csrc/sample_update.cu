@@ -12,9 +12,10 @@ namespace dcd {
 // DCD: one thread per iteration.  out[j] = floor(u * m / 2^64), u the
 // SplitMix64 draw (seed, stream 0, counter first + j).
 __global__ void sample_dcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
-                                  int64_t count, int32_t *out)
+                                  int64_t count, int32_t *out, uint64_t *ctr_next)
 {
     uint64_t first = (ctr_dev ? *ctr_dev : 0) + first_host;
+    if (ctr_next && blockIdx.x == 0 && threadIdx.x == 0) *ctr_next = first + (uint64_t)count;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
         out[j] = (int32_t)below(sm64_draw(seed, 0, first + (uint64_t)j), (uint64_t)m);
 }
@@ -24,13 +25,15 @@ __global__ void sample_dcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64
 // unless it was already taken, else take J.  The warp tests membership of r
 // against the q indices taken so far in parallel.
 __global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
-                                   int b, int64_t nblocks, int32_t *out)
+                                   int b, int64_t nblocks, int32_t *out, uint64_t *ctr_next)
 {
     extern __shared__ int32_t sblk[];  // b indices per warp
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (warp >= nblocks) return;
-    const uint64_t t = (ctr_dev ? *ctr_dev : 0) + first_host + (uint64_t)warp;
+    const uint64_t t0 = (ctr_dev ? *ctr_dev : 0) + first_host;
+    if (ctr_next && warp == 0 && lane == 0) *ctr_next = t0 + (uint64_t)nblocks;
+    const uint64_t t = t0 + (uint64_t)warp;
     int32_t *blk = sblk + (threadIdx.x >> 5) * b;
     for (int q = 0; q < b; ++q) {
         const int64_t J = m - b + q;
@@ -45,7 +48,7 @@ __global__ void sample_bdcd_kernel(uint64_t seed, const uint64_t *ctr_dev, uint6
 }
 
 cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, uint64_t first_host, int64_t m,
-                          int b, int64_t count, int32_t *out, int *err, cudaStream_t st)
+                          int b, int64_t count, int32_t *out, int *err, cudaStream_t st, uint64_t *ctr_next)
 {
     (void)err;
     if (count <= 0) return cudaSuccess;
@@ -53,12 +56,12 @@ cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, ui
         int threads = 128;
         int64_t blocks = (count + threads - 1) / threads;
         if (blocks > 4096) blocks = 4096;
-        sample_dcd_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, ctr_dev, first_host, m, count, out);
+        sample_dcd_kernel<<<(unsigned)blocks, threads, 0, st>>>(seed, ctr_dev, first_host, m, count, out, ctr_next);
     } else {
         int threads = 128;  // 4 warps = 4 blocks per CTA
         int64_t blocks = (count * 32 + threads - 1) / threads;
         sample_bdcd_kernel<<<(unsigned)blocks, threads, sizeof(int32_t) * 4 * b, st>>>(seed, ctr_dev, first_host, m,
-                                                                                       b, count, out);
+                                                                                       b, count, out, ctr_next);
     }
     return cudaGetLastError();
 }
@@ -323,33 +326,41 @@ cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_
 }
 
 // dst row j = src row idx[j] (whole packed rows, 16-byte vectors; row_bytes
-// is a multiple of 128).  Indices outside [0, m) give a zero row and set
+// is a multiple of 128), and d0[j] = f0[idx[j]], d1[j] = f1[idx[j]] where
+// given.  Indices outside [0, m) give a zero row (and zero values) and set
 // DEV_BAD_INDEX.
 __global__ void gather_rows_kernel(const uint4 *src, int64_t row_vec, const int32_t *idx, int64_t count, int64_t m,
-                                   uint4 *dst, int *err)
+                                   uint4 *dst, int *err, const float *f0, float *d0, const float *f1, float *d1)
 {
     const int64_t total = count * row_vec;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / row_vec, c = e - j * row_vec;
         const int64_t r = idx[j];
-        if (r < 0 || r >= m) {
+        const bool bad = r < 0 || r >= m;
+        if (bad) {
             if (c == 0) set_error(err, DEV_BAD_INDEX);
             dst[e] = make_uint4(0, 0, 0, 0);
         } else {
             dst[e] = src[r * row_vec + c];
         }
+        if (c == 0) {
+            if (d0) d0[j] = bad ? 0.f : f0[r];
+            if (d1) d1[j] = bad ? 0.f : f1[r];
+        }
     }
 }
 
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
-                               void *dst, int *err, cudaStream_t st)
+                               void *dst, int *err, cudaStream_t st, const float *f0, float *d0, const float *f1,
+                               float *d1)
 {
     if (count <= 0) return cudaSuccess;
+    if ((d0 && !f0) || (d1 && !f1)) return cudaErrorInvalidValue;
     const int64_t row_vec = row_bytes / 16;
     int64_t blocks = (count * row_vec + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)src, row_vec, idx, count, m, (uint4 *)dst,
-                                                         err);
+                                                         err, f0, d0, f1, d1);
     return cudaGetLastError();
 }
 

@@ -197,6 +197,7 @@ struct Solver {
     // the operand (and column buffers) of the recomputed gradient: split tf32
     // for the tensor-core modes (== op when the solve itself is split tf32)
     Operand opr;
+    TcSplit tsplit;  // scratch of the balanced tensor-core apply
     void *Asr = nullptr;
     float *col_hr = nullptr;
     // CSR data matrix: the CUDA-core SpMM block (FP32, or FP64 in the FP64 mode)
@@ -288,6 +289,14 @@ struct Solver {
         const int64_t n_pad_r = (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
 
+        int split_pairs = 0;
+        const int split_chunks = tc_split_chunks(std::max<int64_t>(sb, 1));
+        if (tcd) {
+            int dev = 0, sms = 0;
+            DCD_TRY(cudaGetDevice(&dev));
+            DCD_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            split_pairs = std::max(sms / 2, 1);
+        }
         // size the arena (two passes over the same layout)
         Arena ar;
         for (int pass = 0; pass < 2; ++pass) {
@@ -327,7 +336,10 @@ struct Solver {
             float *cs_b = (float *)ar.take(la_pos && fp8 ? sizeof(float) * col_pad : 0);
             void *kss_b = ar.take(la_pos ? (size_t)sb * sb * 4 : 0);
             double *lb_b = (double *)ar.take(la_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
-            uint64_t *crl = (uint64_t *)ar.take(la_pos ? sizeof(uint64_t) : 0);
+            uint64_t *crl = (uint64_t *)ar.take(la_pos ? 2 * sizeof(uint64_t) : 0);
+            // the balanced split of the tensor-core apply over CTA pairs
+            double *tsp = (double *)ar.take(tcd ? sizeof(double) * tc_split_part_elems(split_pairs, split_chunks) : 0);
+            unsigned *tsc = (unsigned *)ar.take(tcd ? sizeof(unsigned) * 2 * split_pairs : 0);
             int *er = (int *)ar.take(sizeof(int) * 4);
             double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
             double *rs = (double *)ar.take(sizeof(double) * 4);
@@ -397,6 +409,12 @@ struct Solver {
             sbuf[1].Kss = kss_b;
             sbuf[1].Lbuf = lb_b;
             ctr_la = crl;
+            if (tcd) {
+                tsplit.part = tsp;
+                tsplit.cnt = tsc;
+                tsplit.pairs = split_pairs;
+                tsplit.chunks = split_chunks;
+            }
             if (host) {
                 DCD_TRY(cudaMemcpyAsync(hv, A->values,
                                         (csr ? (size_t)nnz : (size_t)m * A->ld) * dtype_size(A->dtype),
@@ -412,6 +430,7 @@ struct Solver {
         }
         const void *vals = host ? h_vals : A->values;
         DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
+        if (tcd) DCD_TRY(cudaMemsetAsync(tsplit.cnt, 0, sizeof(unsigned) * 2 * split_pairs, st));
         DCD_TRY(cudaMemsetAsync(col_h, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
@@ -592,10 +611,9 @@ struct Solver {
     cudaError_t gather_op(int64_t ncols, const Operand &x, void *Asx, float *chx)
     {
         if (!tc) return cudaSuccess;
-        cudaError_t e = launch_gather_rows(x.packed, packed_row_bytes(x.kind, x.n_pad), S, ncols, m, Asx, err, st);
-        if (e != cudaSuccess) return e;
-        if (x.kind == PACK_FP8 && (e = launch_gather_f32(x.row_s, S, ncols, col_s, st)) != cudaSuccess) return e;
-        return launch_gather_f32(x.row_h, S, ncols, chx, st);
+        const bool f8 = x.kind == PACK_FP8;
+        return launch_gather_rows(x.packed, packed_row_bytes(x.kind, x.n_pad), S, ncols, m, Asx, err, st, x.row_h,
+                                  chx, f8 ? x.row_s : nullptr, f8 ? col_s : nullptr);
     }
 
     cudaError_t gram(int64_t ncols)
@@ -638,7 +656,7 @@ struct Solver {
             TcOperand Aop{x.packed, m, x.n_pad, x.kind, x.row_s};
             TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 ? col_s : nullptr};
             return cuda_status(
-                launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st));
+                launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st, false, &tsplit));
         }
         return cuda_status(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr,
                                                  0, err, st));
@@ -664,7 +682,8 @@ struct Solver {
     {
         TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
         TcOperand Bop{As, ncols, op.n_pad, op.kind, col_s};
-        return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st);
+        return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st, false,
+                               &tsplit);
     }
 
     // Convergence measure from the cached gradient (reads back 4 doubles).
@@ -737,9 +756,10 @@ struct Solver {
     // Step k+1's sample, gathers, Gram and recurrence prep depend on its
     // indices only, not on alpha or g, so they run on a second stream beside
     // step k's chain (which occupies one cluster of SMs) and fused block.
-    // The step products live in two buffer sets used alternately; ctr_la is
-    // the index-stream position of the next step to sample, one step ahead of
-    // ctr (which the chain's a6 advances as before).
+    // The step products live in two buffer sets used alternately; ctr_la[q]
+    // holds the index-stream position of the step to be sampled into set q,
+    // one step ahead of ctr (which the chain's a6 advances as before); the
+    // sample into set q leaves the following position in ctr_la[1 - q].
     struct StepBufs {
         int32_t *S = nullptr;
         void *As = nullptr;
@@ -774,25 +794,31 @@ struct Solver {
     }
 
     // step products of a step of cnt blocks into buffer set q, on stream s2
-    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2)
+    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2, int gram_ctas = 0)
     {
         const StepBufs &Bq = sbuf[q];
         const int64_t ncols = cnt * o.b;
-        DCD_TRY(launch_sample(problem, o.seed, ctr_la, 0, m, o.b, cnt, Bq.S, err, s2));
-        DCD_TRY(launch_advance(ctr_la, (uint64_t)cnt, s2));
-        DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2));
-        if (op.kind == PACK_FP8) DCD_TRY(launch_gather_f32(op.row_s, Bq.S, ncols, Bq.col_s, s2));
-        DCD_TRY(launch_gather_f32(op.row_h, Bq.S, ncols, Bq.col_h, s2));
+        // the sample reads the position in ctr_la[q] and leaves the next one in ctr_la[1 - q]
+        DCD_TRY(launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, Bq.S, err, s2, ctr_la + (1 - q)));
+        const bool f8 = op.kind == PACK_FP8;
+        DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2,
+                                   op.row_h, Bq.col_h, f8 ? op.row_s : nullptr, f8 ? Bq.col_s : nullptr));
         TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s};
+        // beside a running block the Gram gets the SMs of the chain's cluster only
         DCD_TRY(launch_block_tc(Bo, Bo, kp, Bq.col_h, Bq.col_h, nullptr, nullptr, nullptr, (float *)Bq.Kss, ldk, ncols,
-                                ncols, err, s2, true));
+                                ncols, err, s2, true, nullptr, false, gram_ctas));
         DCD_TRY(launch_recur_cluster_prep((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, lambda, (double)m, Bq.Lbuf,
                                           err, s2));
         return DCD_OK;
     }
 
-    // the chain (with the a6 update) and the fused block of a step whose products are in set p
-    dcd_status la_main(int p, int64_t cnt)
+    // one look-ahead step, products in set p: the chain (with the a6 update) on st, then the fused
+    // block as its programmatic dependent on the SMs the chain's cluster leaves free: its
+    // tensor-core products start beside the chain, its epilogue waits for it.  The next full step's
+    // products (next > 0) go to set 1 - p on st2, forked before the chain and joined back into st
+    // after the block: the sample and the gathers fit beside the block's CTAs, the Gram and the
+    // prep take the chain's SMs once it ends.
+    dcd_status la_body(int p, int64_t cnt, int64_t next)
     {
         const StepBufs &Bp = sbuf[p];
         const int64_t ncols = cnt * o.b;
@@ -802,19 +828,6 @@ struct Solver {
         fu.ctr_advance = (uint64_t)cnt;
         const int P = recur_cluster_size((int)cnt, o.b, 2);
         if (P <= 0) return DCD_EINTERNAL;
-        DCD_TRY(launch_recur_cluster_chain((const float *)Bp.Kss, ldk, Bp.S, (int)cnt, o.b, P, lambda, (double)m, g, 2,
-                                           Bp.Lbuf, delta, w64, col_w, &fu, err, st));
-        DCD_TRY(clear_col_w_tail(ncols));
-        TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
-        TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s};
-        DCD_TRY(launch_block_tc(Aop, Bop, kp, op.row_h, Bp.col_h, col_w, nullptr, g, nullptr, 0, m, ncols, err, st));
-        return DCD_OK;
-    }
-
-    // one look-ahead step: this step's chain and block on st; the next full
-    // step's products on st2 beside them (forked from and joined back into st)
-    dcd_status la_body(int p, int64_t cnt, int64_t next)
-    {
         if (next) {
             DCD_TRY(cudaEventRecord(la_fork, st));
             DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
@@ -822,8 +835,22 @@ struct Solver {
             if (r != DCD_OK) return r;
             DCD_TRY(cudaEventRecord(la_join, st2));
         }
-        dcd_status r = la_main(p, cnt);
-        if (r != DCD_OK) return r;
+        // the block may start once the side kernels are done: about 5/8 of the chain
+        const int trig = next ? (int)((cnt * o.b / 32) * 5 / 8) : -1;
+        DCD_TRY(launch_recur_cluster_chain((const float *)Bp.Kss, ldk, Bp.S, (int)cnt, o.b, P, lambda, (double)m, g, 2,
+                                           Bp.Lbuf, delta, w64, col_w, &fu, err, st, nullptr, trig));
+        DCD_TRY(clear_col_w_tail(ncols));
+        TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
+        TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s};
+        // the chain writes only delta, the coefficients, alpha, g and the counter: the block's
+        // products read none of them.  The pairs that land on the chain's SMs (the grid's last,
+        // launched once the chain ends) take two units fewer: the others fill both tensor-memory
+        // accumulators while the chain runs.
+        TcSplit sp = tsplit;
+        sp.late_pairs = (P + 1) / 2;
+        sp.late_units = 2;
+        DCD_TRY(launch_block_tc(Aop, Bop, kp, op.row_h, Bp.col_h, col_w, nullptr, g, nullptr, 0, m, ncols, err, st,
+                                false, &sp, true));
         if (next) DCD_TRY(cudaStreamWaitEvent(st, la_join, 0));
         return DCD_OK;
     }
@@ -831,7 +858,7 @@ struct Solver {
     dcd_status la_step(int64_t cnt)
     {
         if (la_cnt != cnt) {  // nothing pending: this step's products first, on st
-            DCD_TRY(cudaMemcpyAsync(ctr_la, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+            DCD_TRY(cudaMemcpyAsync(ctr_la + la_par, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
             dcd_status r = la_side(la_par, cnt, st);
             if (r != DCD_OK) return r;
             la_cnt = cnt;
@@ -1389,6 +1416,17 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     const bool fp8 = pk == PACK_FP8;
     size_t ors = place(cur, fp8 ? sizeof(float) * nrows : 0);
     size_t ocs = place(cur, fp8 ? sizeof(float) * cpad : 0);
+    // the apply form's balanced split over CTA pairs
+    TcSplit sp;
+    if (!out) {
+        int dev = 0, sms = 0;
+        DCD_TRY(cudaGetDevice(&dev));
+        DCD_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        sp.pairs = std::max(sms / 2, 1);
+        sp.chunks = tc_split_chunks(ncols);
+    }
+    size_t osp = place(cur, sizeof(double) * tc_split_part_elems(sp.pairs, sp.chunks));
+    size_t osc = place(cur, sizeof(unsigned) * 2 * sp.pairs);
     DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
     char *base = (char *)cb.mem;
     int *err = (int *)(base + oe);
@@ -1398,6 +1436,11 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
     DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
+    if (!out) {
+        sp.part = (double *)(base + osp);
+        sp.cnt = (unsigned *)(base + osc);
+        DCD_TRY(cudaMemsetAsync(sp.cnt, 0, sizeof(unsigned) * 2 * sp.pairs, st));
+    }
     if (fp8) {
         DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
         DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, A->row_scale, (uint8_t *)pa, n_pad,
@@ -1414,7 +1457,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st, rsb));
     if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
     TcOperand Aop{pa, nrows, n_pad, pk, rsa}, Bop{pb, ncols, n_pad, pk, rsb};
-    DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st));
+    DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st,
+                            false, &sp));
     return finish_component(err, st);
 }
 

@@ -173,6 +173,54 @@ def test_kernel_block_apply_pair_tiles(prec, m, ncols, n):
     assert np.max(np.abs(gd.cpu().numpy() - want)) <= tol * np.max(np.abs(Kb)) * np.sum(np.abs(w))
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp8", "tf32"])
+@pytest.mark.parametrize("m,ncols,n", [(40000, 1000, 64), (20001, 300, 96), (50000, 1024, 512)])
+def test_kernel_block_apply_shared_tiles(prec, m, ncols, n):
+    """More 256-row tiles than CTA pairs: the pairs split the (tile, N-chunk)
+    units into equal ranges, so some tiles are shared by two pairs.  Parity
+    with the oracle on every row, and each shared tile's rows bit-identical
+    to the same rows computed as the only tile of a small apply."""
+    g = np.random.default_rng(m + 7 * ncols)
+    A = g.standard_normal((m, n)) / np.sqrt(n)
+    cols = g.integers(0, m, size=ncols)
+    w = g.standard_normal(ncols)
+    g0 = g.standard_normal(m)
+    kb, ko = B().kernel("rbf", gamma=0.7), oracle.kernel("rbf", gamma=0.7)
+
+    def run(Ah, c, gi):
+        gd = dev(gi)
+        if prec == "fp8":
+            q, sc = oracle.quantize_e4m3_rows(Ah)
+            Ad = B().Fp8(dev(q), dev(sc))
+        else:
+            Ad = dev(Ah.astype(np.float32))
+        B().kernel_block_apply(Ad, kb, prec, dev(c, torch.int32), dev(w), gd)
+        return gd.cpu().numpy()
+
+    got = run(A, cols, g0)
+    if prec == "fp8":
+        q, sc = oracle.quantize_e4m3_rows(A)
+        Ar, tol = oracle.dequantize_e4m3_rows(q, sc), 2e-5
+    else:
+        Ar, tol = ROUND.get(prec, round_tf32)(A), TC_TOL[prec]
+    Kb = oracle.kernel_block(ko, Ar, cols)
+    want = g0 + Kb @ w
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(Kb)) * np.sum(np.abs(w))
+    # the tiles holding a boundary between two pairs' unit ranges
+    tiles, nch = (m + 255) // 256, (ncols + 255) // 256 if ncols > 256 else 1
+    pairs = min(tiles, torch.cuda.get_device_properties(0).multi_processor_count // 2)
+    U = tiles * nch
+    shared = sorted({(p * U // pairs) // nch for p in range(1, pairs) if (p * U // pairs) % nch})
+    assert shared
+    for t in shared[:3]:
+        r0, r1 = 256 * t, min(256 * t + 256, m)
+        A2 = np.concatenate([A[r0:r1], A[cols]])
+        c2 = (r1 - r0) + np.arange(ncols)
+        g2 = np.concatenate([g0[r0:r1], np.zeros(ncols)])
+        got2 = run(A2, c2, g2)
+        assert np.array_equal(got2[: r1 - r0], got[r0:r1]), t
+
+
 def test_kernel_block_bad_index_is_an_error_not_a_fault():
     A = dev(np.ones((10, 4)))
     with pytest.raises(B().DcdError) as e:
