@@ -38,7 +38,7 @@ METRIC = "coordinate updates/s and time-to-duality-gap 1e-6 (mixed vs FP64 s=1, 
 UNIT = "coordinate updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused-block launch,
 # from an ncu capture of this build's kernel (prec, m, n, b, s) -> bytes
-NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 109.45e6}
+NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 108.39e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 

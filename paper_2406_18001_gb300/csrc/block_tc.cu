@@ -603,13 +603,29 @@ __device__ __forceinline__ void pair_units(const TcArgs &a, int pair, int npairs
     }
 }
 
-__device__ __forceinline__ void pair_unit(const TcArgs &a, int pair, int npairs, bool ranged, int u0, int i, int &tile,
-                                          int &nc)
+// The i-th unit of a pair.  Ranged: even pairs take their tiles first to
+// last, odd pairs last to first (the chunks of a tile in order either way),
+// so that both pairs that share a tile reach it at about the same time (at
+// the start of both ranges, or at the end of both) and its rows of A are
+// read from memory once.
+__device__ __forceinline__ void pair_unit(const TcArgs &a, int pair, int npairs, bool ranged, int u0, int u1, int i,
+                                          int &tile, int &nc)
 {
     if (ranged) {
-        const int u = u0 + i;
-        tile = u / a.nchunks;
-        nc = u % a.nchunks;
+        const int nch = a.nchunks;
+        int u = u0 + i;
+        if (pair & 1) {
+            const int thi = (u1 - 1) / nch, tlo = u0 / nch;
+            const int top = u1 - max(u0, thi * nch);  // units of the last tile
+            if (i < top) {
+                u = u1 - top + i;
+            } else {
+                const int j = i - top, mid = (thi - 1 - tlo) * nch;  // units of the full tiles between
+                u = j < mid ? (thi - 1 - j / nch) * nch + j % nch : u0 + (j - mid);
+            }
+        }
+        tile = u / nch;
+        nc = u % nch;
     } else {
         tile = pair + i / a.nchunks * npairs;
         nc = i % a.nchunks;
@@ -692,7 +708,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const uint32_t bytes = (uint32_t)(2 * (SPLIT ? 2 : 1) * (A_STAGE + bh * ROW_BYTES));  // both CTAs'
             for (int i = 0; ok && i < nunits; ++i) {
                 int item, nc;
-                pair_unit(a, pair, npairs, ranged, u0, i, item, nc);
+                pair_unit(a, pair, npairs, ranged, u0, u1, i, item, nc);
                 for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
                         if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) {
@@ -778,8 +794,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         const int nch = a.nchunks;
         for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
             int item, nc;
-            pair_unit(a, pair, npairs, ranged, u0, i, item, nc);
-            if (i == 0 || nc == 0) {  // first chunk of a tile in this pair's units
+            pair_unit(a, pair, npairs, ranged, u0, u1, i, item, nc);
+            const int u = item * nch + nc;
+            if (u == u0 || nc == 0) {  // first chunk of a tile in this pair's units
                 row = (int64_t)item * BM2 + (int64_t)rank * BM + row_in_tile;
                 row_ok = row < a.nrows_out;
                 hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
@@ -788,7 +805,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 tacc = 0.0;
             }
             const bool whole = !ranged || (item * nch >= u0 && (item + 1) * nch <= u1);
-            const bool last = nc == nch - 1 || i == nunits - 1;  // last chunk of the tile in this pair's units
+            const bool last = nc == nch - 1 || u == u1 - 1;  // last chunk of the tile in this pair's units
             double cs = 0.0;  // this chunk's part of the row sum (this half's column groups)
             // one 32-column group: terms from the staged columns (4 per shared-memory load), the
             // same sums in the same order as a column-by-column loop
