@@ -168,8 +168,6 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
                                  const float *src_scale, uint8_t *dst, int64_t ldq, float *dst_scale, int64_t count,
                                  int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
-// *c += n (one thread)
-cudaError_t launch_advance(uint64_t *c, uint64_t n, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *scale = nullptr);
@@ -178,7 +176,6 @@ cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
                                void *dst, int *err, cudaStream_t st, const float *f0 = nullptr, float *d0 = nullptr,
                                const float *f1 = nullptr, float *d1 = nullptr);
-cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st);
 cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
                              cudaStream_t st);

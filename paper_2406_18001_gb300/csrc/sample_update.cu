@@ -231,14 +231,6 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
     return cudaGetLastError();
 }
 
-__global__ void advance_kernel(uint64_t *c, uint64_t n) { *c += n; }
-
-cudaError_t launch_advance(uint64_t *c, uint64_t n, cudaStream_t st)
-{
-    advance_kernel<<<1, 1, 0, st>>>(c, n);
-    return cudaGetLastError();
-}
-
 // Number of labels that are not exactly +1 or -1.
 __global__ void label_check_kernel(const double *y, int64_t m, int *bad)
 {
@@ -361,21 +353,6 @@ cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t
     if (blocks > 152 * 16) blocks = 152 * 16;
     gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)src, row_vec, idx, count, m, (uint4 *)dst,
                                                          err, f0, d0, f1, d1);
-    return cudaGetLastError();
-}
-
-__global__ void gather_f32_kernel(const float *src, const int32_t *idx, int64_t count, float *dst)
-{
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
-        dst[j] = src[idx[j]];
-}
-
-cudaError_t launch_gather_f32(const float *src, const int32_t *idx, int64_t count, float *dst, cudaStream_t st)
-{
-    if (count <= 0) return cudaSuccess;
-    int64_t blocks = (count + 255) / 256;
-    if (blocks > 1024) blocks = 1024;
-    gather_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, idx, count, dst);
     return cudaGetLastError();
 }
 
