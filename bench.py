@@ -807,7 +807,7 @@ def main():
     ap.add_argument("--fp8-m", type=int, default=400000)
     ap.add_argument("--fp8-n", type=int, default=2048)
     ap.add_argument("--fp8-sub", type=int, default=20000, help="rows of the alpha-error subproblem")
-    ap.add_argument("--fp8-oracle-blocks", type=int, default=128, help="block updates the oracle runs")
+    ap.add_argument("--fp8-oracle-blocks", type=int, default=32, help="block updates the oracle runs (about 28 s of one core)")
     ap.add_argument("--fp8-long-steps", type=int, default=20, help="outer steps of the GPU-only comparison")
     ap.add_argument("--csr-m", type=int, default=200000)
     ap.add_argument("--csr-n", type=int, default=50000)
