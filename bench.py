@@ -114,6 +114,30 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_max(x, ws, device):
+    """The maximum of x over the ranks of the job (x itself at one rank): the
+    job's time is its slowest replica's.  Joins the default process group
+    (NCCL on a GPU device, gloo on the CPU) if none is up yet."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        if device.type == "cuda":
+            dist.init_process_group("nccl", device_id=device)
+        else:
+            dist.init_process_group("gloo")
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ms, ws):
+    """Whole-job throughput of ws replicas that each processed units_per_rank
+    units, the job taking ms milliseconds (the max over ranks)."""
+    return ws * units_per_rank / (ms * 1e-3)
+
+
 # ----------------------------------------------------------- reference ----
 def run_reference(args):
     """The FP64 CPU oracle (s-step BDCD, Algorithm 4 as printed) timed on the
@@ -279,11 +303,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     st, _ = plan.run(0)
     launches = st["gpu_launches_per_step"] * args.steps
     plan.close()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(ms, ws, dev)
 
     # dominant kernel (fused kernel block) duration, measured live: per-phase
     # CUDA events on the solver's stream, L2 flushed before every step
@@ -352,7 +372,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
         cpu = cpu_baseline(args)
 
     if rank == 0:
-        value = ws * args.steps * upd_per_step / (ms * 1e-3)
+        value = job_rate(args.steps * upd_per_step, ms, ws)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
@@ -434,6 +454,7 @@ def run_gpu_csr(args):
                 ev[i][1].record(stream)
             torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev)
+        ms = rank_max(ms, ws, dev)
         st, _ = plan.run(0)
         launches = st["gpu_launches_per_step"] * args.steps
         plan.close()
@@ -476,7 +497,7 @@ def run_gpu_csr(args):
                "d2h_bytes_per_step": 2 * p.m * 8 / args.steps, "steps": args.steps, "wall_s": dt}
     cpu = None if args.no_cpu else csr_cpu_baseline(p, p.y, s)
     if rank == 0:
-        value = ws * args.steps * s / (ms * 1e-3)
+        value = job_rate(args.steps * s, ms, ws)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
@@ -510,6 +531,7 @@ def _fp8_arm(B, torch, A, y, k, lam, b, s, prec, args, stream, flush, seed):
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    ms = rank_max(ms, dist_env()[0], torch.device("cuda", torch.cuda.current_device()))
     st, _ = plan.run(0)
     plan.close()
     nroof = max(3, min(args.roof_steps, 10))
@@ -640,7 +662,7 @@ def run_gpu_fp8(args):
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof16 = {"achieved": flops / (ph16["block"] * 1e-3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s"}
         roof16["frac"] = roof16["achieved"] / bf16_peak
-        value = ws * args.steps * s * b / (ms8 * 1e-3)
+        value = job_rate(args.steps * s * b, ms8, ws)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms8 / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "fp8-e4m3", "data": "synthetic",
@@ -648,7 +670,7 @@ def run_gpu_fp8(args):
                           "precision": "fp8 (per-row-scaled e4m3, kind::f8f6f4, FP32 accumulation)",
                           "l2": "A (0.82 GB FP8 / 1.64 GB BF16) above L2; 256 MB buffer written before every step"},
                "phase_ms": ph8,
-               "bf16_storage": {"value": ws * args.steps * s * b / (ms16 * 1e-3), "ms_per_step": ms16 / args.steps,
+               "bf16_storage": {"value": job_rate(args.steps * s * b, ms16, ws), "ms_per_step": ms16 / args.steps,
                                 "phase_ms": ph16, "roofline": roof16},
                "alpha_error": out_err,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -721,6 +743,8 @@ def run_gpu_sweep(args):
         h2d = sum(Ah.nbytes + yh.nbytes for Ah, yh in host)
         d2h = sum(a.numel() * 8 for a in al_h)
     upd = sum(int(st["iters_done"]) * p["b"] for st, p in zip(sts, probs))
+    wall = rank_max(wall, ws, dev)  # the job's times are its slowest replica's
+    wall_e2e = rank_max(wall_e2e, ws, dev)
     launches = sum(int(st["gpu_launches_per_step"]) * int(st["outer_steps"]) for st in sts)
     # roofline of the whole call: every outer step is one fused block, 2 m n sb flops per MMA pass (x3
     # for the split forms), and reads its problem's packed operand once
@@ -740,13 +764,13 @@ def run_gpu_sweep(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = sweep_cpu_baseline(probs, upd)
-    e2e = {"value": ws * upd / wall_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    e2e = {"value": job_rate(upd, wall_e2e * 1e3, ws), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "steps": 1, "wall_s": wall_e2e}
     s_hist = {}
     for p in probs:
         s_hist[f"b{p['b']}_s{p['s']}"] = s_hist.get(f"b{p['b']}_s{p['s']}", 0) + 1
     if rank == 0:
-        out = {"metric": METRIC, "value": ws * upd / wall, "unit": UNIT, "n_gpus": ws, "steps": 1,
+        out = {"metric": METRIC, "value": job_rate(upd, wall * 1e3, ws), "unit": UNIT, "n_gpus": ws, "steps": 1,
                "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                "config": {"workload": WORKLOAD_SWEEP, "problems": count, "H_block_updates": args.sweep_H,
