@@ -14,9 +14,13 @@
 //          recurrence sees exactly the values the apply pass uses.
 //
 // Two kernels, both persistent with one CTA per SM and 320 threads:
-//   block_tc_kernel  (store) over 128-row tiles x 64-column N-chunks;
-//   block_tc2_kernel (apply) on CTA pairs over 256-row tiles (tcgen05
-//                    cta_group::2), each CTA staging half of an N-chunk of B.
+//   block_tc_kernel  (store) over 128-row tiles x N-chunks of 64 columns
+//                    (up to 256 when held to a few CTAs);
+//   block_tc2_kernel (apply) on CTA pairs (tcgen05 cta_group::2) over
+//                    (256-row tile, N-chunk) units, each CTA staging half of
+//                    an N-chunk of B; the pairs take contiguous ranges of the
+//                    units, a tile split between two pairs summed by the one
+//                    that finishes it last (see pair_units).
 // Warp roles in both:
 //   warp 0      TMA producer: 128-byte-swizzled k-blocks of A and B into a
 //               shared-memory ring (mbarrier complete_tx)
@@ -29,7 +33,9 @@
 //               6..9 the second half (two warps per scheduler hide the load and
 //               MUFU latency); in the apply form the second half's row sums
 //               reach the first half through shared memory once per tile, in a
-//               fixed order
+//               fixed order; the apply's epilogue waits (griddepcontrol.wait)
+//               for the grid before it, so that it may run as a programmatic
+//               dependent whose products start early
 // Every mbarrier wait is bounded; on timeout the CTA records DEV_TIMEOUT,
 // drains its in-flight copies and MMAs (bounded), frees TMEM and returns.
 #include "dcd_internal.cuh"
