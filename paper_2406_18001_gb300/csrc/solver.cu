@@ -794,7 +794,7 @@ struct Solver {
     }
 
     // step products of a step of cnt blocks into buffer set q, on stream s2
-    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2, int gram_ctas = 0)
+    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2)
     {
         const StepBufs &Bq = sbuf[q];
         const int64_t ncols = cnt * o.b;
@@ -804,9 +804,8 @@ struct Solver {
         DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2,
                                    op.row_h, Bq.col_h, f8 ? op.row_s : nullptr, f8 ? Bq.col_s : nullptr));
         TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s};
-        // beside a running block the Gram gets the SMs of the chain's cluster only
         DCD_TRY(launch_block_tc(Bo, Bo, kp, Bq.col_h, Bq.col_h, nullptr, nullptr, nullptr, (float *)Bq.Kss, ldk, ncols,
-                                ncols, err, s2, true, nullptr, false, gram_ctas));
+                                ncols, err, s2, true));
         DCD_TRY(launch_recur_cluster_prep((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, lambda, (double)m, Bq.Lbuf,
                                           err, s2));
         return DCD_OK;
