@@ -304,8 +304,8 @@ dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int3
  * (cudaMalloc / cudaFree may also synchronise the device).
  *
  * Its scratch is one library-owned device array of DCD_STATIC_SCRATCH_BYTES
- * per GPU, held from the moment the library is loaded on that GPU until the
- * process exits.  A call needs 256 bytes plus
+ * per GPU, held from the first call on that GPU (below) until the process
+ * exits.  A call needs 256 bytes plus
  *   tensor-core precisions: (nrows + ncols) * R + 4 * nrows + 4 * roundup(ncols, 256)
  *     with R = 2 * n_pad (bf16), 4 * n_pad (tf32 or bf16x3), n_pad = n rounded up
  *     to 64 (bf16, bf16x3) or 32 (tf32), plus alignment padding;
@@ -314,13 +314,22 @@ dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int3
  * before any device work is enqueued.
  *
  * The first call made on a device (with that device current) looks up the
- * array's device address once; make that first call before any stream
- * capture begins.  Every call reuses the same array and clears the parts that
- * must start at zero; calls whose device work overlaps (different streams, or
- * different host threads) race on the array and corrupt each other's output.
+ * array's device address once; the CUDA runtime may load the array's module
+ * and commit its memory only then (lazy module loading).  A caller that must
+ * not allocate later therefore makes one call at start-up -- an empty request
+ * (nrows or ncols 0) does it -- before its own pool reserves the device
+ * memory and before any stream capture begins.  The address is kept for the
+ * device's primary context (the one the CUDA runtime and PyTorch use): it is
+ * not valid under another driver context or after cudaDeviceReset.  Every
+ * call reuses the same array and clears the parts that must start at zero;
+ * calls whose device work overlaps (different streams, or different host
+ * threads) race on the array and corrupt each other's output.
+ *
+ * Arguments are checked as dcd_kernel_block checks them.  Two valid requests
+ * that dcd_kernel_block serves give DCD_EUNSUPPORTED here: a CSR data matrix
+ * (its column map is sized per call) and FP8 (DCD_PREC_FP8, or FP8 storage).
  */
 #define DCD_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
-/* (DCD_PREC_FP8 and FP8 data matrices: DCD_EUNSUPPORTED here.) */
 dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
                                    int64_t nrows, const int32_t *cols, int64_t ncols, void *out, int64_t ldo,
                                    void *stream);

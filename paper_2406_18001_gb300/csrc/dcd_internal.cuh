@@ -73,6 +73,13 @@ __device__ __forceinline__ double kfun_f64(const KernelParams &kp, double v)
     return r;
 }
 
+// ------------------------------------------------- argument validation --
+// The checks every entry point applies to a data matrix and a kernel
+// (solver.cu): DCD_OK, DCD_EINVAL, or DCD_EUNSUPPORTED for a valid request
+// the build does not implement (CSR with BF16 / FP8 values).
+dcd_status validate_kernel(const dcd_kernel *k);
+dcd_status validate_dense(const dcd_matrix *A);
+
 // --------------------------------------------------------- host launches --
 // All launchers enqueue on `st` and return cudaGetLastError().
 // ctr_next (optional, not ctr_dev): receives the stream position after this

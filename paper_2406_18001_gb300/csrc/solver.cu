@@ -25,6 +25,42 @@
 
 namespace dcd {
 
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+dcd_status validate_kernel(const dcd_kernel *k)
+{
+    if (!k) return DCD_EINVAL;
+    switch (k->kind) {
+    case DCD_LINEAR: return DCD_OK;
+    case DCD_POLY:
+        return (std::isfinite(k->coef0) && k->coef0 >= 0.0 && k->degree >= 2 && k->degree <= 32) ? DCD_OK : DCD_EINVAL;
+    case DCD_RBF: return finite_pos(k->gamma) ? DCD_OK : DCD_EINVAL;
+    default: return DCD_EINVAL;
+    }
+}
+
+// Dense: row-major f64/f32/bf16, or e4m3 codes with per-row scales, with
+// ld >= n.  CSR: f32/f64 values, int64 row offsets, int32 columns (checked on
+// the device by the solver).
+dcd_status validate_dense(const dcd_matrix *A)
+{
+    if (!A || A->m < 1 || A->n < 1) return DCD_EINVAL;
+    if (A->fmt == DCD_CSR) {
+        if (!A->row_ptr || !A->col_idx || !A->values) return DCD_EINVAL;
+        if (A->dtype == DCD_BF16 || A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
+        if (A->dtype != DCD_F64 && A->dtype != DCD_F32) return DCD_EINVAL;
+        if (A->m > INT32_MAX || A->n > INT32_MAX) return DCD_EINVAL;
+        return DCD_OK;
+    }
+    if (A->fmt != DCD_DENSE) return DCD_EINVAL;
+    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16 && A->dtype != DCD_FP8E4M3)
+        return DCD_EINVAL;
+    if (A->dtype == DCD_FP8E4M3 && !A->row_scale) return DCD_EINVAL;
+    if (A->ld < A->n || !A->values) return DCD_EINVAL;
+    if (A->m > INT32_MAX) return DCD_EINVAL;
+    return DCD_OK;
+}
+
 namespace {
 
 constexpr int64_t SB_MAX = 8192;   // s*b per outer step
@@ -62,42 +98,6 @@ dcd_status cuda_status(cudaError_t e)
         cudaError_t e_ = (expr);                        \
         if (e_ != cudaSuccess) return cuda_status(e_);  \
     } while (0)
-
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
-dcd_status validate_kernel(const dcd_kernel *k)
-{
-    if (!k) return DCD_EINVAL;
-    switch (k->kind) {
-    case DCD_LINEAR: return DCD_OK;
-    case DCD_POLY:
-        return (std::isfinite(k->coef0) && k->coef0 >= 0.0 && k->degree >= 2 && k->degree <= 32) ? DCD_OK : DCD_EINVAL;
-    case DCD_RBF: return finite_pos(k->gamma) ? DCD_OK : DCD_EINVAL;
-    default: return DCD_EINVAL;
-    }
-}
-
-// Dense: row-major f64/f32/bf16, or e4m3 codes with per-row scales, with
-// ld >= n.  CSR: f32/f64 values, int64 row offsets, int32 columns (checked on
-// the device by the solver).
-dcd_status validate_dense(const dcd_matrix *A)
-{
-    if (!A || A->m < 1 || A->n < 1) return DCD_EINVAL;
-    if (A->fmt == DCD_CSR) {
-        if (!A->row_ptr || !A->col_idx || !A->values) return DCD_EINVAL;
-        if (A->dtype == DCD_BF16 || A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
-        if (A->dtype != DCD_F64 && A->dtype != DCD_F32) return DCD_EINVAL;
-        if (A->m > INT32_MAX || A->n > INT32_MAX) return DCD_EINVAL;
-        return DCD_OK;
-    }
-    if (A->fmt != DCD_DENSE) return DCD_EINVAL;
-    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16 && A->dtype != DCD_FP8E4M3)
-        return DCD_EINVAL;
-    if (A->dtype == DCD_FP8E4M3 && !A->row_scale) return DCD_EINVAL;
-    if (A->ld < A->n || !A->values) return DCD_EINVAL;
-    if (A->m > INT32_MAX) return DCD_EINVAL;
-    return DCD_OK;
-}
 
 size_t dtype_size(int dt) { return dt == DCD_F64 ? 8 : dt == DCD_F32 ? 4 : dt == DCD_BF16 ? 2 : 1; }
 

@@ -15,9 +15,16 @@
 // The array's device address is looked up once per device
 // (cudaGetSymbolAddress) on the first call made with that device current; the
 // host-side name of the array is only a stand-in and is never passed to a
-// kernel.  All calls share the array: each call clears what must start at
-// zero, and two calls whose work overlaps on the GPU (different streams, or
-// different host threads) race on it.
+// kernel.  That first lookup is also when the CUDA runtime may load this
+// file's module and commit the array's memory (lazy module loading), so a
+// caller that must not allocate later makes one call at start-up -- an empty
+// request (nrows or ncols 0) is enough -- before its pool reserves the
+// device's memory and before any stream capture.  The cached address belongs
+// to the device's primary context (the one the runtime and PyTorch use); it
+// is not valid after cudaDeviceReset or under another driver context.  All
+// calls share the array: each call clears what must start at zero, and two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads) race on it.
 #include "dcd_internal.cuh"
 
 #include <mutex>
@@ -65,15 +72,6 @@ dcd_status to_status(cudaError_t e)
         if (e_ != cudaSuccess) return to_status(e_);   \
     } while (0)
 
-bool kernel_ok(const dcd_kernel *k)
-{
-    if (!k) return false;
-    if (k->kind == DCD_LINEAR) return true;
-    if (k->kind == DCD_POLY) return k->coef0 >= 0.0 && k->degree >= 2 && k->degree <= 32;
-    if (k->kind == DCD_RBF) return k->gamma > 0.0 && k->gamma < 1e300;
-    return false;
-}
-
 }  // namespace
 }  // namespace dcd
 
@@ -83,17 +81,20 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
                                               const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
                                               void *out, int64_t ldo, void *stream)
 {
-    if (A && A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;  // the CSR block needs allocated scratch
-    if (!A || A->fmt != DCD_DENSE || A->m < 1 || A->n < 1 || A->ld < A->n || !A->values || A->m > INT32_MAX)
-        return DCD_EINVAL;
-    if (A->dtype == DCD_FP8E4M3 || prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
-    if (A->dtype != DCD_F64 && A->dtype != DCD_F32 && A->dtype != DCD_BF16) return DCD_EINVAL;
-    if (!kernel_ok(k)) return DCD_EINVAL;
+    // the argument checks of dcd_kernel_block, then the two requests this entry point does not serve
+    dcd_status vs = validate_dense(A);
+    if (vs != DCD_OK) return vs;
+    if ((vs = validate_kernel(k)) != DCD_OK) return vs;
     if (prec != DCD_PREC_FP64 && prec != DCD_PREC_BF16 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16X3 &&
-        prec != DCD_PREC_TF32X3)
+        prec != DCD_PREC_TF32X3 && prec != DCD_PREC_FP8)
         return DCD_EINVAL;
     if (nrows < 0 || ncols < 0 || !cols || !out || ldo < ncols) return DCD_EINVAL;
     if (!rows && nrows > A->m) return DCD_EINVAL;
+    if (A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;  // the CSR block's column map is sized per call
+    if (A->dtype == DCD_FP8E4M3 || prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
+    // the array's address first, so that an empty request makes it resident
+    void *base_v = nullptr;
+    STATIC_TRY(scratch_address(&base_v));
     if (nrows == 0 || ncols == 0) return DCD_OK;
     const bool tc = prec != DCD_PREC_FP64;
     if (tc && !tc_available()) return DCD_EUNSUPPORTED;
@@ -125,8 +126,6 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
     }
     if (need > (size_t)DCD_STATIC_SCRATCH_BYTES) return DCD_EINVAL;  // larger than the static scratch
 
-    void *base_v = nullptr;
-    STATIC_TRY(scratch_address(&base_v));
     char *base = (char *)base_v;
     int *err = (int *)base;
     STATIC_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -158,6 +157,6 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
     STATIC_TRY(cudaMemcpyAsync(&he, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     STATIC_TRY(cudaStreamSynchronize(st));
     if (he == DEV_TIMEOUT) return DCD_ETIMEOUT;
-    if (he == DEV_BAD_INDEX) return DCD_EINVAL;
+    if (he == DEV_BAD_INDEX || he == DEV_BAD_VALUE) return DCD_EINVAL;
     return he ? DCD_EINTERNAL : DCD_OK;
 }

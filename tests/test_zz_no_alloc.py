@@ -5,17 +5,16 @@ when they need a kernel block -- a framework that has reserved the device
 memory for its own caching pool, or a deployment that forbids allocation
 after start-up.  It keeps its scratch in one library-owned device array, so
 it must produce the same block as the allocating entry point, call after
-call, while that array is reused.  This file is collected last: if it fails,
-a run that stops at the first failure has already run every other test.
+call, while that array is reused.  Both entry points run the same pack,
+norm and block kernels with the same arguments, so the blocks are compared
+bit for bit.  This file is collected last: if it fails, a run that stops at
+the first failure has already run every other test.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-# the kernel-block tolerances of tests/test_gpu_parity.py
-TOL = {"fp64": 1e-12, "bf16": 3e-5, "bf16x3": 3e-5}
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp64"])
@@ -24,6 +23,13 @@ def test_static_scratch_matches_allocating_entry_point(prec):
     g = np.random.default_rng(11)
     k = B.kernel("rbf", gamma=0.3)
     dt = np.float64 if prec == "fp64" else np.float32
+    # the start-up call a caller that must not allocate later makes: an empty
+    # request, which looks up (and makes resident) the scratch array
+    A0 = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    c0 = torch.zeros(2, dtype=torch.int32, device="cuda")
+    o0 = torch.full((1, 2), -7.0, device="cuda", dtype=torch.float64 if prec == "fp64" else torch.float32)
+    B.kernel_block_static(A0, k, prec, c0, nrows=0, out=o0)
+    assert torch.all(o0 == -7.0)  # nothing written
     # two calls in a row with different shapes: the second reuses (and must
     # not be disturbed by) what the first left in the shared scratch array
     for m, n, nc, nr in ((300, 77, 70, 133), (517, 40, 103, 260)):
@@ -33,7 +39,7 @@ def test_static_scratch_matches_allocating_entry_point(prec):
         want = B.kernel_block(A, k, prec, cols, rows=rows).cpu().numpy()
         got = B.kernel_block_static(A, k, prec, cols, rows=rows).cpu().numpy()
         assert got.shape == want.shape
-        assert np.max(np.abs(got - want)) <= TOL[prec] * np.max(np.abs(want))
+        assert np.array_equal(got, want)
 
 
 def test_static_scratch_rejects_requests_beyond_its_size():
@@ -44,3 +50,14 @@ def test_static_scratch_rejects_requests_beyond_its_size():
     with pytest.raises(B.DcdError) as e:
         B.kernel_block_static(A, B.kernel("linear"), "bf16", cols)
     assert e.value.status == B.EINVAL
+
+
+def test_static_scratch_checks_arguments_as_the_allocating_entry_point():
+    from paper_2406_18001_gb300 import binding as B
+    A = torch.zeros((10, 4), dtype=torch.float32, device="cuda")
+    cols = torch.arange(3, dtype=torch.int32, device="cuda")
+    bad = B.kernel("poly", coef0=float("inf"), degree=3)
+    for fn in (B.kernel_block, B.kernel_block_static):
+        with pytest.raises(B.DcdError) as e:
+            fn(A, bad, "bf16", cols)
+        assert e.value.status == B.EINVAL
