@@ -13,6 +13,13 @@
  * blocking or reordering.  All arithmetic is IEEE double; the build uses
  * -ffp-contract=off so x86 and Arm produce the same bits.
  *
+ * Threads (OpenMP, when the compiler has it): only loops whose iterations
+ * write separate outputs run in parallel -- the rows of U_k / Q_k and of a
+ * kernel block, the rows of Q alpha and K alpha -- and each output is formed
+ * by the same operations in the same order as with one thread, so every
+ * result is bit-identical for any thread count (orc_set_threads).  Sums over
+ * rows stay sequential.
+ *
  * Readings of points the paper leaves open (each listed in the design notes):
  *  - Q = diag(y) K diag(y), as the dual in Section 3.1 defines it (the
  *    Algorithm 1/2 shorthand K(diag(y)A, .) agrees only for the linear kernel
@@ -31,6 +38,22 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by the parallel row loops (1 without OpenMP); returns the
+ * count in effect. */
+int orc_set_threads(int32_t threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
 
 #define ORC_LINEAR 0
 #define ORC_POLY 1
@@ -133,6 +156,7 @@ void orc_kernel_block(const orc_kernel *k, const double *A, int64_t m, int64_t n
                       const int64_t *rows, int64_t nr, const int64_t *cols, int64_t nc, double *out)
 {
     if (rows == NULL) nr = m;
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < nr; ++r) {
         const double *ar = A + (rows ? rows[r] : r) * lda;
         for (int64_t c = 0; c < nc; ++c) out[r * nc + c] = orc_kernel_eval(k, ar, A + cols[c] * lda, n);
@@ -199,6 +223,7 @@ int orc_dcd_svm(const double *A, int64_t m, int64_t n, int64_t lda, const double
     for (int64_t it = 0; it < H; ++it) {
         int64_t i = orc_dcd_index(seed, m, first + (uint64_t)it);
         /* u_k = Q e_{i_k}: column i of diag(y) K diag(y) */
+#pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < m; ++r)
             u[r] = y[r] * y[i] * orc_kernel_eval(k, A + r * lda, A + i * lda, n);
         double eta = u[i] + omega;
@@ -231,6 +256,7 @@ int orc_sstep_dcd_svm(const double *A, int64_t m, int64_t n, int64_t lda, const 
         int64_t cnt = (H - done < s) ? (H - done) : s;
         for (int64_t j = 0; j < cnt; ++j) idx[j] = orc_dcd_index(seed, m, first + (uint64_t)(done + j));
         /* U_k = K(A~, A~_k) with the y_i y_j reading: U[r][j] = Q(r, i_j) */
+#pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < m; ++r)
             for (int64_t j = 0; j < cnt; ++j)
                 U[r * cnt + j] = y[r] * y[idx[j]] * orc_kernel_eval(k, A + r * lda, A + idx[j] * lda, n);
@@ -274,6 +300,7 @@ int orc_bdcd_krr(const double *A, int64_t m, int64_t n, int64_t lda, const doubl
     if (!U || !G || !L || !rhs || !d || !idx) rc = -2;
     for (int64_t it = 0; rc == 0 && it < H; ++it) {
         orc_bdcd_block(seed, m, b, first_block + (uint64_t)it, idx);
+#pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < m; ++r) /* U_k = K(A, V_k^T A) */
             for (int32_t p = 0; p < b; ++p)
                 U[r * b + p] = orc_kernel_eval(k, A + r * lda, A + idx[p] * lda, n);
@@ -315,6 +342,7 @@ int orc_sstep_bdcd_krr(const double *A, int64_t m, int64_t n, int64_t lda, const
         int64_t w = cnt * b; /* columns of Q_k this outer step */
         for (int64_t j = 0; j < cnt; ++j)
             orc_bdcd_block(seed, m, b, first_block + (uint64_t)(done + j), idx + j * b);
+#pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < m; ++r)
             for (int64_t c = 0; c < w; ++c) Q[r * w + c] = orc_kernel_eval(k, A + r * lda, A + idx[c] * lda, n);
         for (int64_t j = 0; j < cnt; ++j) {
@@ -352,6 +380,7 @@ int orc_sstep_bdcd_krr(const double *A, int64_t m, int64_t n, int64_t lda, const
 static void svm_q_alpha(const double *A, int64_t m, int64_t n, int64_t lda, const double *y,
                         const orc_kernel *k, const double *alpha, double *qa)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         double s = 0.0;
         for (int64_t j = 0; j < m; ++j)
@@ -414,6 +443,7 @@ int orc_svm_objectives(const double *A, int64_t m, int64_t n, int64_t lda, const
 int orc_krr_gradient(const double *A, int64_t m, int64_t n, int64_t lda, const double *y,
                      const orc_kernel *k, double lambda, const double *alpha, double *g)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         double s = 0.0;
         for (int64_t j = 0; j < m; ++j)
@@ -427,14 +457,21 @@ int orc_krr_gradient(const double *A, int64_t m, int64_t n, int64_t lda, const d
 double orc_krr_objective(const double *A, int64_t m, int64_t n, int64_t lda, const double *y,
                          const orc_kernel *k, double lambda, const double *alpha)
 {
-    double quad = 0.0, lin = 0.0;
+    double *ka = (double *)malloc(sizeof(double) * (size_t)m); /* (K alpha)_i */
+    if (!ka) return NAN;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         double s = 0.0;
         for (int64_t j = 0; j < m; ++j)
             if (alpha[j] != 0.0) s += orc_kernel_eval(k, A + i * lda, A + j * lda, n) * alpha[j];
-        quad += alpha[i] * (s / lambda + (double)m * alpha[i]);
+        ka[i] = s;
+    }
+    double quad = 0.0, lin = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        quad += alpha[i] * (ka[i] / lambda + (double)m * alpha[i]);
         lin += y[i] * alpha[i];
     }
+    free(ka);
     return 0.5 * quad - lin;
 }
 
@@ -447,6 +484,7 @@ int orc_krr_closed_form(const double *A, int64_t m, int64_t n, int64_t lda, cons
     double *M = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
     double *L = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
     if (!M || !L) { free(M); free(L); return -2; }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i)
         for (int64_t j = 0; j < m; ++j)
             M[i * m + j] = orc_kernel_eval(k, A + i * lda, A + j * lda, n) / lambda + (i == j ? (double)m : 0.0);

@@ -323,6 +323,30 @@ def test_krr_gradient_and_objective():
     assert abs(oracle.krr_objective(p.A, p.y, k, lam, a) - f) < 1e-12 * abs(f)
 
 
+def test_thread_count_does_not_change_any_result():
+    """The parallel row loops write separate outputs, each formed as with one
+    thread: every routine gives the same bits at 1 and at 4 threads."""
+    p = inputs.krr_dense(m=90, n=7, seed=12, dtype=np.float64)
+    q = inputs.blobs(m=80, n=5, seed=13)
+    k = oracle.kernel("rbf", gamma=0.6)
+    a = np.random.default_rng(7).standard_normal(90)
+    res = []
+    for t in (1, 4):
+        oracle.set_threads(t)
+        res.append([oracle.sstep_bdcd_krr(p.A, p.y, k, 0.05, 4, 8, 60, seed=2),
+                    oracle.bdcd_krr(p.A, p.y, k, 0.05, 4, 20, seed=2),
+                    oracle.sstep_dcd_svm(q.A, q.y, k, 1, 1.0, 8, 300, seed=3),
+                    oracle.dcd_svm(q.A, q.y, k, 2, 1.0, 100, seed=3),
+                    oracle.kernel_block(k, p.A, np.arange(30)),
+                    oracle.krr_gradient(p.A, p.y, k, 0.05, a),
+                    np.array([oracle.krr_objective(p.A, p.y, k, 0.05, a)]),
+                    oracle.svm_gradient(q.A, q.y, k, 2, 1.0, np.abs(a[:80])),
+                    oracle.krr_closed_form(p.A, p.y, k, 0.05)])
+    oracle.set_threads(os.cpu_count() or 1)
+    for x1, x4 in zip(*res):
+        assert np.array_equal(x1, x4)
+
+
 # ------------------------------------------------- FP8 e4m3 row storage ---
 def test_e4m3_values_of_the_format():
     v = oracle.e4m3_value(np.arange(256, dtype=np.uint8))
