@@ -35,6 +35,35 @@ constexpr int DCD_THREADS = 256;
 constexpr int DCD_SMEM_GRAM_MAX = 128;   // cnt <= 128: Gram staged in shared memory
 constexpr size_t DCD_SMEM_LIMIT = 224 * 1024;
 
+// Refinement state of one FP64-form outer step (the last 256 bytes of the
+// recurrence scratch).  The FP64 form does not fix its number of refinement
+// rounds: after each round the chain kernel compares the size of the
+// correction it added with the size of Delta and with the previous round's
+// correction, and decides on the device whether to
+//   stop      (the correction is below 2^-44 |Delta|: the error left is that
+//              times the contraction factor),
+//   go on     (the correction shrank by more than 10x: one more round), or
+//   fall back (no contraction, or REFINE_MAX rounds without reaching the
+//              stop test while the correction is still above 1e-10 |Delta|:
+//              cond(L) * 2^-24 is too close to 1 for the FP32 chain), in which
+//              case the FP64 factor / forward kernels solve the step instead.
+// Kernels of rounds after the stop, and the fallback kernels when there is
+// no fallback, return at once (they stay in the launch sequence, so a
+// captured step graph is the same for every step).
+struct RefineState {
+    int done;        // no further refinement round runs
+    int fallback;    // the FP64 factor / forward kernels run
+    int inv_bad;     // the FP32 inverse met a non-positive pivot (reset by round 0)
+    int rounds;      // refinement rounds run (statistics)
+    double prev_corr;
+};
+constexpr int REFINE_MAX = 4;
+constexpr size_t REFINE_STATE_BYTES = 256;
+
+// max that keeps a NaN (fmax drops it), so a non-finite round takes the fallback
+__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
+
 template <typename KT>
 __global__ void __launch_bounds__(DCD_THREADS) recur_dcd_kernel(const KT *Kss, int64_t ldk, const int32_t *S,
                                                                 int cnt, const double *y, const double *alpha,
@@ -116,8 +145,10 @@ constexpr int FAC_THREADS = 128;
 
 template <typename KT>
 __global__ void __launch_bounds__(FAC_THREADS) bdcd_factor_kernel(const KT *Kss, int64_t ldk, int b, double lambda,
-                                                                  double mdiag, double *Lbuf, int *err)
+                                                                  double mdiag, double *Lbuf, int *err,
+                                                                  const RefineState *rs = nullptr)
 {
+    if (rs && !*(volatile const int *)&rs->fallback) return;  // the refined chain solved this step
     extern __shared__ double G[];  // b x b
     const int j = blockIdx.x;
     const int64_t o = (int64_t)j * b;
@@ -163,8 +194,10 @@ template <typename KT>
 __global__ void __launch_bounds__(FWD_THREADS) bdcd_forward_kernel(const KT *Kss, int64_t ldk, const int32_t *S,
                                                                    int nblk, int b, double lambda, double mdiag,
                                                                    const double *g, const double *Lbuf,
-                                                                   double *delta, double *w64, float *w32)
+                                                                   double *delta, double *w64, float *w32,
+                                                                   const RefineState *rs = nullptr)
 {
+    if (rs && !*(volatile const int *)&rs->fallback) return;  // the refined chain solved this step
     extern __shared__ double smd[];
     const int sb = nblk * b;
     double *r = smd;             // right-hand sides, then solutions
@@ -240,7 +273,7 @@ __global__ void __launch_bounds__(FWD_THREADS) bdcd_forward_kernel(const KT *Kss
 // can still change at pivot k are touched (left half k.., right half ..k).
 template <typename KT, int BT>
 __global__ void __launch_bounds__(128) bdcd_inverse_kernel(const KT *Kss, int64_t ldk, int nblk, int b, float inv_lam,
-                                                           float mf, float *W32, int *err)
+                                                           float mf, float *W32, int *err, RefineState *rs)
 {
     const int j = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (j >= nblk) return;
@@ -275,7 +308,11 @@ __global__ void __launch_bounds__(128) bdcd_inverse_kernel(const KT *Kss, int64_
             }
         }
     }
-    if (bad && lane == 0) set_error(err, DEV_NOT_SPD);
+    // with a refinement state the FP64 factorisation decides (the FP32 pivots may fail first)
+    if (bad && lane == 0) {
+        if (rs) atomicExch(&rs->inv_bad, 1);
+        else set_error(err, DEV_NOT_SPD);
+    }
     if (lane < b)
 #pragma unroll
         for (int q = 0; q < BT; ++q)
@@ -327,9 +364,10 @@ __global__ void __launch_bounds__(NT) bdcd_chain_kernel(const KT *Kss, int64_t l
                                                         double lambda, double mdiag, const double *g,
                                                         const double *rho, const float *W32, double *rhs64,
                                                         double *delta, int round, int final_round, double *w64,
-                                                        float *w32, int *err)
+                                                        float *w32, int *err, RefineState *rs)
 {
     extern __shared__ __align__(16) unsigned char csm_raw[];
+    if (rs && round > 0 && *(volatile int *)&rs->done) return;  // refinement already stopped
     const int sb = nblk * b;
     const ChainLayout L = chain_layout(sb, b, (int)sizeof(KT), ldk);
     float *r32 = (float *)csm_raw;
@@ -481,13 +519,56 @@ __global__ void __launch_bounds__(NT) bdcd_chain_kernel(const KT *Kss, int64_t l
         }
         __syncthreads();
     }
+    double cmax = 0.0, dmax = 0.0;  // this round's correction and the new Delta, max norms
     for (int p = tid; p < sb; p += NT) {
-        double d = (double)d32[p];
+        const double c = (double)d32[p];
+        double d = c;
         if (round > 0) d += delta[p];
         delta[p] = d;
-        if (final_round) {
+        cmax = nanmax(cmax, fabs(c));
+        dmax = nanmax(dmax, fabs(d));
+        if (final_round || rs) {  // adaptive rounds: every round may be the last
             if (w64) w64[p] = d / lambda;
             if (w32) w32[p] = (float)(d / lambda);
+        }
+    }
+    if (rs) {
+        __shared__ double red[2][NT / 32];
+        for (int o = 16; o > 0; o >>= 1) {
+            cmax = nanmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            dmax = nanmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        }
+        if (lane == 0) {
+            red[0][warp] = cmax;
+            red[1][warp] = dmax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < NT / 32; ++w) {
+                cmax = nanmax(cmax, red[0][w]);
+                dmax = nanmax(dmax, red[1][w]);
+            }
+            int done = 0, fb = 0;
+            if (round == 0) {
+                fb = rs->inv_bad;  // the FP32 inverse failed: the FP64 factorisation decides
+                rs->inv_bad = 0;
+                done = fb;
+                rs->rounds = 0;
+            } else {
+                rs->rounds = round;
+                const bool small = cmax <= 0x1p-44 * dmax;          // converged to FP64 working accuracy
+                const bool floor = cmax <= 1e-10 * dmax;            // at a conditioning floor, still accurate
+                const bool stalled = !(cmax <= 0.1 * rs->prev_corr);  // no contraction (or not finite)
+                if (small) done = 1;
+                else if (stalled || round >= REFINE_MAX) {
+                    done = 1;
+                    fb = floor ? 0 : 1;
+                }
+            }
+            rs->prev_corr = cmax;
+            rs->fallback = fb;
+            __threadfence();
+            *(volatile int *)&rs->done = done;
         }
     }
 }
@@ -496,8 +577,10 @@ __global__ void __launch_bounds__(NT) bdcd_chain_kernel(const KT *Kss, int64_t l
 template <typename KT>
 __global__ void __launch_bounds__(256) bdcd_residual_kernel(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
                                                             int b, double inv_lambda, double mdiag,
-                                                            const double *rhs64, const double *delta, double *rho)
+                                                            const double *rhs64, const double *delta, double *rho,
+                                                            const RefineState *rs)
 {
+    if (rs && *(volatile const int *)&rs->done) return;  // refinement already stopped
     const int sb = nblk * b;
     const int p = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (p >= sb) return;
@@ -640,15 +723,42 @@ cudaError_t refined_bdcd(const KT *Kss, int64_t ldk, const int32_t *S, int nblk,
                                    scratch, delta, w64, w32, err, st);
     }
     if (L.total > CHAIN_SMEM_MAX) return cudaErrorInvalidValue;
+    // FP64 Gram (the FP64 form): refinement rounds decided on the device, with the FP64
+    // factor / forward kernels as the fallback (see RefineState); other forms: fixed rounds
+    RefineState *rs = nullptr;
+    size_t smf = 0, smw = 0;
+    if (sizeof(KT) == 8) {
+        smf = sizeof(double) * (size_t)b * b;
+        smw = sizeof(double) * ((size_t)sb + b) + sizeof(int32_t) * (size_t)sb;
+        if (smf <= DCD_SMEM_LIMIT && smw <= DCD_SMEM_LIMIT) {
+            rs = (RefineState *)(scratch + recur_bdcd_scratch_bytes(nblk, b) - REFINE_STATE_BYTES);
+            static bool fb_attr = false;
+            if (!fb_attr) {
+                for (auto fn : {(const void *)bdcd_factor_kernel<KT>, (const void *)bdcd_forward_kernel<KT>}) {
+                    const cudaError_t e =
+                        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DCD_SMEM_LIMIT);
+                    if (e != cudaSuccess) return e;
+                }
+                fb_attr = true;
+            }
+        }
+    }
+    const int rounds = rs ? REFINE_MAX : refinements;
     bdcd_inverse_kernel<KT, BT><<<(unsigned)((nblk + 3) / 4), 128, 0, st>>>(Kss, ldk, nblk, b, (float)(1.0 / lambda),
-                                                                            (float)mdiag, W32, err);
+                                                                            (float)mdiag, W32, err, rs);
     kfn<<<1, NT, L.total, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, nullptr, W32, rhs64, delta, 0,
-                                refinements == 0, w64, w32, err);
-    for (int r = 1; r <= refinements; ++r) {
+                                rounds == 0, w64, w32, err, rs);
+    for (int r = 1; r <= rounds; ++r) {
         bdcd_residual_kernel<KT><<<(unsigned)((sb + 7) / 8), 256, 0, st>>>(Kss, ldk, S, nblk, b, 1.0 / lambda, mdiag,
-                                                                          rhs64, delta, rho);
+                                                                          rhs64, delta, rho, rs);
         kfn<<<1, NT, L.total, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, rho, W32, rhs64, delta, r,
-                                    r == refinements, w64, w32, err);
+                                    r == rounds, w64, w32, err, rs);
+    }
+    if (rs) {  // the fallback overwrites the chain's scratch (its Cholesky factors), never the state
+        double *Lbuf = (double *)scratch;
+        bdcd_factor_kernel<KT><<<(unsigned)nblk, FAC_THREADS, smf, st>>>(Kss, ldk, b, lambda, mdiag, Lbuf, err, rs);
+        bdcd_forward_kernel<KT><<<1, FWD_THREADS, smw, st>>>(Kss, ldk, S, nblk, b, lambda, mdiag, g, Lbuf, delta, w64,
+                                                             w32, rs);
     }
     return cudaGetLastError();
 }
@@ -847,7 +957,8 @@ size_t recur_bdcd_scratch_bytes(int64_t nblk, int b)
     if (cluster > refined) refined = cluster;
     const size_t blocked = blocked_cluster_scratch_bytes(nblk, b);
     if (blocked > refined) refined = blocked;
-    return refined > generic ? refined : generic;
+    // the refinement state of the FP64 form sits past everything a step uses
+    return ((refined > generic ? refined : generic) + 255) / 256 * 256 + REFINE_STATE_BYTES;
 }
 
 // Refined FP32 chain for b <= 32 and sb <= 8192 (the shared-memory limit of
