@@ -96,10 +96,14 @@ typedef enum {
                             dcd_quantize_e4m3 does.  Dense A only (CSR: DCD_EUNSUPPORTED) */
     DCD_PREC_BF16X3 = 4, /* split bf16: a = hi + lo, three tcgen05 kind::f16 MMAs per
                             k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
-    DCD_PREC_TF32X3 = 5  /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
-                            three kind::tf32 MMAs per k-step, FP32 accumulation; also the
-                            precision of the gradient recomputed under DCD_FLAG_REFRESH in
-                            every tensor-core mode */
+    DCD_PREC_TF32X3 = 5, /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
+                            three kind::tf32 MMAs per k-step, FP32 accumulation */
+    DCD_PREC_TF32X3A = 6 /* the split-tf32 products with an accurate epilogue: the RBF exponent
+                            and kernel value in double-single arithmetic (exp2 by reduction to the
+                            nearest integer and a degree-7 Taylor polynomial) and the contraction
+                            with the FP64 coefficients in double-single.  The precision of the
+                            gradient recomputed under DCD_FLAG_REFRESH in every tensor-core mode.
+                            dcd_kernel_block_apply only (elsewhere DCD_EUNSUPPORTED) */
 } dcd_precision;
 
 /* opts.flags */
@@ -108,8 +112,10 @@ typedef enum {
 #define DCD_FLAG_PHASE_TIMERS 0x4 /* fill the per-phase times of dcd_stats (adds one sync per step) */
 #define DCD_FLAG_NO_GRAPH 0x8     /* launch every kernel directly instead of replaying CUDA graphs */
 #define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
-                                     recompute the gradient from alpha by full kernel passes and accept
-                                     convergence only if the recomputed metric meets tol too */
+                                     recompute the gradient from alpha by full kernel passes (tensor-core
+                                     modes: DCD_PREC_TF32X3A; FP64 mode: FP64) and accept convergence only
+                                     if the recomputed metric meets tol too; the check at the end of the
+                                     budget always recomputes */
 
 typedef struct {
     int32_t s;            /* inner steps per outer step, s >= 1 (Algorithms 2 and 4) */

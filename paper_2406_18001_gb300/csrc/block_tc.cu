@@ -12,6 +12,12 @@
 //          is never written to memory), or
 //   store: writes K_ij (FP32) -- used for the sampled Gram, so that the
 //          recurrence sees exactly the values the apply pass uses.
+// The apply form has a third, accurate epilogue (MODE_ACC, on the split-tf32
+// operand) for recomputing the gradient from alpha: the RBF exponent in
+// double-single arithmetic, exp2 by reduction to the nearest integer and a
+// degree-7 Taylor polynomial, and the contraction with FP64 coefficients in
+// double-single; its kernel entries are within a few FP32 ulps of the exact
+// kernel of the data, where the fast epilogue's are within ~2.5e-7.
 //
 // Two kernels, both persistent with one CTA per SM and 320 threads:
 //   block_tc_kernel  (store) over 128-row tiles x N-chunks of 64 columns
@@ -64,7 +70,8 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // fp8: e4m3 codes q with per-row scales (a_i ~ s_i q_i), kind::f8f6f4 with 32
 // codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
 // q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
-constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4;
+// MODE_ACC: the split-tf32 products with the accurate apply epilogue (pairs only).
+constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5;
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 320;
@@ -270,7 +277,59 @@ struct TcArgs {
     unsigned *cnt;        // apply on pairs: arrivals per shared tile and CTA rank
     int late_pairs;       // apply on pairs: the last late_pairs pairs take late_units units fewer
     int late_units;
+    // MODE_ACC: low parts of the RBF terms (h + h_lo), FP64 coefficients, 2 gamma log2(e) as hi + lo
+    const float *row_hl;
+    const float *col_hl;
+    const double *col_w64;
+    float two_gl_lo;
+    // data-matrix row of each block row / column (null: the row / column number); RBF: K = 1
+    // where they are equal (d^2 = 0 on a row's own sample)
+    const int32_t *row_id;
+    const int32_t *col_id;
 };
+
+// ------------------------------------------------- double-single helpers --
+// Error-free transformations (Knuth's TwoSum, Dekker's Fast2Sum and the
+// FMA product): s + e equals a + b (a * b) exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)  // |a| >= |b|
+{
+    s = a + b;
+    e = b - (s - a);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// 2^x for x <= 0 given as x_hi + x_lo (|x_lo| <= ulp(x_hi)): x = k + f with
+// k = rint(x_hi) and |f| <= 1/2, 2^f = e^(f ln 2) by the Taylor polynomial of
+// degree 7 (truncation below 5.3e-9 relative for |f ln 2| <= 0.35), evaluated
+// by Horner's rule, then 2^k applied to the exponent field.  Results below
+// 2^-125 are returned as 0.
+__device__ __forceinline__ float exp2_ds(float xh, float xl)
+{
+    if (xh < -125.f) return 0.f;
+    const float k = rintf(xh);
+    const float f = (xh - k) + xl;  // xh - k is exact
+    // f ln 2 with ln 2 = 0x1.62e430p-1 + 0x1.fdf474p-26 (hi + lo)
+    const float u = fmaf(f, 0x1.62e430p-1f, f * 0x1.fdf474p-26f);
+    float p = 1.f / 5040.f;
+    p = fmaf(p, u, 1.f / 720.f);
+    p = fmaf(p, u, 1.f / 120.f);
+    p = fmaf(p, u, 1.f / 24.f);
+    p = fmaf(p, u, 1.f / 6.f);
+    p = fmaf(p, u, 0.5f);
+    p = fmaf(p, u, 1.f);
+    p = fmaf(p, u, 1.f);
+    return p * __int_as_float(((int)k + 127) << 23);
+}
 
 // K(a_i, b_j) from the accumulator c; rf is the per-row factor: 2 gamma
 // log2(e) (RBF) or 1 (poly, linear), times the row scale in fp8 mode (where
@@ -288,6 +347,16 @@ __device__ __forceinline__ float kf32(float c, float hr, float hc, float rf, con
         for (int e = 1; e < a.degree; ++e) r *= t;
         return r;
     }
+}
+
+// K with the own-sample rule of the RBF (d^2 = 0 where the row and column
+// are the same data row)
+template <int KIND>
+__device__ __forceinline__ float kf32_id(float c, float hr, float hc, float rf, const TcArgs &a, int64_t rid,
+                                         int64_t cid)
+{
+    if (KIND == DCD_RBF && rid == cid) return 1.f;
+    return kf32<KIND>(c, hr, hc, rf, a);
 }
 
 // store form: one item = one (row tile, N-chunk) pair; with `lower`, the
@@ -470,21 +539,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     if (row_ok) {
                         float *dst = a.out + row * a.ldo + colbase;
+                        const int64_t rid = a.row_id ? (int64_t)a.row_id[row] : row;
+                        // column ids inside the block (the last group may be ragged)
+                        auto cid = [&](int q) -> int64_t {
+                            const int64_t c = colbase + q;
+                            return c < a.ncols ? (a.col_id ? (int64_t)a.col_id[c] : c) : -1;
+                        };
                         if (colbase + 32 <= a.ncols && (a.ldo & 3) == 0) {  // whole group: 16-byte stores
 #pragma unroll
                             for (int q = 0; q < 32; q += 4) {
                                 float4 o;
-                                o.x = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
-                                o.y = kf32<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf, a);
-                                o.z = kf32<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf, a);
-                                o.w = kf32<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf, a);
+                                o.x = kf32_id<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a,
+                                                    rid, cid(q));
+                                o.y = kf32_id<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf,
+                                                    a, rid, cid(q + 1));
+                                o.z = kf32_id<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf,
+                                                    a, rid, cid(q + 2));
+                                o.w = kf32_id<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf,
+                                                    a, rid, cid(q + 3));
                                 *reinterpret_cast<float4 *>(dst + q) = o;
                             }
                         } else {
 #pragma unroll
                             for (int q = 0; q < 32; ++q)
                                 if (colbase + q < a.ncols)
-                                    dst[q] = kf32<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a);
+                                    dst[q] = kf32_id<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf,
+                                                           a, rid, cid(q));
                         }
                     }
                 }
@@ -522,7 +602,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 constexpr int BM2 = 2 * BM;                          // rows per pair tile
 constexpr int B2_STAGE = (BN_MAX / 2) * ROW_BYTES;   // 16 KB: half of an N-chunk
 constexpr int RING2_BYTES = 6 * (A_STAGE + B2_STAGE);  // 6 single or 3 split stages
-constexpr int CST_FLOATS = 3 * 128;                   // staged column terms per epilogue warp
+constexpr int CST_FLOATS = 5 * 128;                   // staged column terms per epilogue warp
 constexpr int SMEM2_BYTES = RING2_BYTES + 1024 + 256 + XCH_BYTES + 8 * CST_FLOATS * 4;
 
 // arrive on an mbarrier of the pair given by its shared::cluster address
@@ -642,10 +722,11 @@ template <int MODE, int KIND>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     block_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
-    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3;
+    constexpr bool ACC = MODE == MODE_ACC;
+    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3 || ACC;
     constexpr bool FP8 = MODE == MODE_FP8;
     constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
-    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3;
+    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3 || ACC;
     constexpr int STAGES = SPLIT ? 3 : 6;
     constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
     constexpr int B_ST = SPLIT ? 2 * B2_STAGE : B2_STAGE;
@@ -795,7 +876,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         int64_t row = 0;
         bool row_ok = false;
-        float hr = 0.f, rf = 0.f;
+        float hr = 0.f, hrl = 0.f, rf = 0.f;
+        int rid = -2;  // data-matrix row of this thread's row (-2: none)
+        const int *cid = (const int *)(cst + 512);  // staged column ids (-1 past the block)
         double tacc = 0.0;  // this half's row sum over the tile's chunks so far, in chunk order
         const int nch = a.nchunks;
         for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
@@ -806,6 +889,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 row = (int64_t)item * BM2 + (int64_t)rank * BM + row_in_tile;
                 row_ok = row < a.nrows_out;
                 hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
+                if (ACC) hrl = (KIND == DCD_RBF && row_ok) ? a.row_hl[row] : 0.f;
+                rid = row_ok ? (a.row_id ? a.row_id[row] : (int)row) : -2;
                 const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
                 rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
                 tacc = 0.0;
@@ -815,10 +900,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             double cs = 0.0;  // this chunk's part of the row sum (this half's column groups)
             // one 32-column group: terms from the staged columns (4 per shared-memory load), the
             // same sums in the same order as a column-by-column loop
-            auto group = [&](const uint32_t(&r)[32], int j0) {
+            // the 32 columns' kernel values (`own`: bit q set where column q is this row's own
+            // sample, d^2 = 0 there; the checked form runs only for the rare groups that hold one)
+            auto group_terms = [&](const uint32_t(&r)[32], int j0, unsigned own, float &p0, float &p1) {
                 const float4 *h4 = (const float4 *)(cst + j0), *w4 = (const float4 *)(cst + 128 + j0),
                              *s4 = (const float4 *)(cst + 256 + j0);
-                float p0 = 0.f, p1 = 0.f;
 #pragma unroll
                 for (int q4 = 0; q4 < 8; ++q4) {
                     const float4 hh = KIND == DCD_RBF ? h4[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -832,20 +918,118 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                         c2 *= ss.z;
                         c3 *= ss.w;
                     }
-                    p0 = fmaf(kf32<KIND>(c0, hr, hh.x, rf, a), ww.x, p0);
-                    p1 = fmaf(kf32<KIND>(c1, hr, hh.y, rf, a), ww.y, p1);
-                    p0 = fmaf(kf32<KIND>(c2, hr, hh.z, rf, a), ww.z, p0);
-                    p1 = fmaf(kf32<KIND>(c3, hr, hh.w, rf, a), ww.w, p1);
+                    float k0 = kf32<KIND>(c0, hr, hh.x, rf, a), k1 = kf32<KIND>(c1, hr, hh.y, rf, a);
+                    float k2 = kf32<KIND>(c2, hr, hh.z, rf, a), k3 = kf32<KIND>(c3, hr, hh.w, rf, a);
+                    if (own) {
+                        k0 = (own >> (4 * q4)) & 1u ? 1.f : k0;
+                        k1 = (own >> (4 * q4 + 1)) & 1u ? 1.f : k1;
+                        k2 = (own >> (4 * q4 + 2)) & 1u ? 1.f : k2;
+                        k3 = (own >> (4 * q4 + 3)) & 1u ? 1.f : k3;
+                    }
+                    p0 = fmaf(k0, ww.x, p0);
+                    p1 = fmaf(k1, ww.y, p1);
+                    p0 = fmaf(k2, ww.z, p0);
+                    p1 = fmaf(k3, ww.w, p1);
                 }
+            };
+            // one 32-column group: terms from the staged columns (4 per shared-memory load), the
+            // same sums in the same order as a column-by-column loop
+            auto group = [&](const uint32_t(&r)[32], int j0) {
+                float p0 = 0.f, p1 = 0.f;
+                // the own-sample columns of this warp's 32 rows: each lane tests one column id
+                unsigned own = 0;
+                if (KIND == DCD_RBF && !a.row_id) {
+                    const int wr0 = __shfl_sync(0xffffffffu, rid, 0);  // lanes hold consecutive rows
+                    const unsigned off = (unsigned)(cid[j0 + lane] - wr0);
+                    unsigned hits = __ballot_sync(0xffffffffu, rid >= 0 && off < 32u);
+                    while (hits) {
+                        const int q = __ffs(hits) - 1;
+                        hits &= hits - 1;
+                        if (cid[j0 + q] == rid) own |= 1u << q;
+                    }
+                } else if (KIND == DCD_RBF) {  // rows given by id: every column tested
+                    for (int q = 0; q < 32; ++q) own |= (cid[j0 + q] == rid ? 1u : 0u) << q;
+                }
+                if (own) group_terms(r, j0, own, p0, p1);
+                else group_terms(r, j0, 0u, p0, p1);
                 cs += (double)p0 + (double)p1;
+            };
+            // the accurate form of one group: staged columns [h | w_hi | w_lo | h_lo]; the exponent
+            // x = 2 gamma log2(e) c - (h_i + h_j) = -gamma log2(e) d^2 and the kernel value in
+            // double-single, the products with w summed in double-single (two sums, alternate columns)
+            auto group_acc = [&](const uint32_t(&r)[32], int j0) {
+                float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + q;
+                    const float c = __uint_as_float(r[q]);
+                    float kh, kl = 0.f;
+                    if (KIND == DCD_RBF && cid[j] == rid) {  // the own sample: d^2 = 0
+                        kh = 1.f;
+                    } else if (KIND == DCD_RBF) {
+                        float sh, sl, ph, pl, xh, xl;
+                        two_sum(hr, cst[j], sh, sl);
+                        sl += hrl + cst[384 + j];
+                        two_prod(a.two_gl, c, ph, pl);
+                        pl = fmaf(a.two_gl_lo, c, pl);
+                        two_sum(ph, -sh, xh, xl);
+                        xl += pl - sl;
+                        fast_two_sum(xh, xl, xh, xl);
+                        if (xh > 0.f) {  // d^2 >= 0
+                            xh = 0.f;
+                            xl = 0.f;
+                        }
+                        kh = exp2_ds(xh, xl);
+                    } else if (KIND == DCD_LINEAR) {
+                        kh = c;
+                    } else {  // (coef0 + c)^degree by repeated double-single products
+                        float th, tl;
+                        two_sum(a.coef0, c, th, tl);
+                        float rh = th, rl = tl;
+                        for (int e = 1; e < a.degree; ++e) {
+                            float pp, pe;
+                            two_prod(rh, th, pp, pe);
+                            pe = fmaf(rh, tl, fmaf(rl, th, pe));
+                            fast_two_sum(pp, pe, rh, rl);
+                        }
+                        kh = rh;
+                        kl = rl;
+                    }
+                    const float wh = cst[128 + j], wl = cst[256 + j];
+                    float pp, pe, sm, se;
+                    two_prod(kh, wh, pp, pe);
+                    pe = fmaf(kh, wl, fmaf(kl, wh, pe));
+                    if (q & 1) {
+                        two_sum(ah1, pp, sm, se);
+                        al1 += se + pe;
+                        ah1 = sm;
+                    } else {
+                        two_sum(ah0, pp, sm, se);
+                        al0 += se + pe;
+                        ah0 = sm;
+                    }
+                }
+                cs += ((double)ah0 + (double)al0) + ((double)ah1 + (double)al1);
             };
             const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
             // stage this warp's columns while the accumulator is still being formed
             const int64_t cbase = (int64_t)nc * bn + cg0 * 32;
             for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
-                if (KIND == DCD_RBF) cst[j] = a.col_h[cbase + j];
-                cst[128 + j] = a.col_w[cbase + j];
-                if (FP8) cst[256 + j] = a.col_s[cbase + j];
+                if (KIND == DCD_RBF) {
+                    cst[j] = a.col_h[cbase + j];
+                    const int64_t c = cbase + j;
+                    ((int *)cst)[512 + j] = c < a.ncols ? (a.col_id ? a.col_id[c] : (int)c) : -1;
+                }
+                if (ACC) {
+                    const double wv = cbase + j < a.ncols ? a.col_w64[cbase + j] : 0.0;
+                    const float wh = (float)wv;
+                    cst[128 + j] = wh;
+                    cst[256 + j] = (float)(wv - (double)wh);
+                    if (KIND == DCD_RBF) cst[384 + j] = a.col_hl[cbase + j];
+                } else {
+                    cst[128 + j] = a.col_w[cbase + j];
+                    if (FP8) cst[256 + j] = a.col_s[cbase + j];
+                }
             }
             __syncwarp();
             const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
@@ -860,13 +1044,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
                 tmem_ld_wait(ra);
             }
+            auto any_group = [&](const uint32_t(&r)[32], int j0) {
+                if constexpr (ACC) group_acc(r, j0);
+                else group(r, j0);
+            };
             for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
                 if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
-                group(ra, (cg - cg0) * 32);
+                any_group(ra, (cg - cg0) * 32);
                 if (cg + 1 < cg1) {
                     tmem_ld_wait(rb);
                     if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
-                    group(rb, (cg + 1 - cg0) * 32);
+                    any_group(rb, (cg + 1 - cg0) * 32);
                     if (cg + 2 < cg1) tmem_ld_wait(ra);
                 }
             }
@@ -1073,9 +1261,13 @@ bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t 
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
                             const float *col_h, const float *col_w, const double *rs, double *g, float *out,
                             int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st, bool lower,
-                            const TcSplit *split, bool pdl, int max_pairs)
+                            const TcSplit *split, bool pdl, int max_pairs, const TcAccurate *acc)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
+    // the accurate apply epilogue: split-tf32 operands, FP64 coefficients, RBF terms as hi + lo
+    if (acc && (out != nullptr || Aop.kind != PACK_TF32X3 || !acc->w64 ||
+                (kp.kind == DCD_RBF && (!acc->row_hl || !acc->col_hl))))
+        return cudaErrorInvalidValue;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
     if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3 &&
         Aop.kind != PACK_FP8)
@@ -1121,6 +1313,15 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.cnt = nullptr;
     a.late_pairs = 0;
     a.late_units = 0;
+    a.row_id = Aop.ids;
+    a.col_id = Bop.ids;
+    a.row_hl = acc ? acc->row_hl : nullptr;
+    a.col_hl = acc ? acc->col_hl : nullptr;
+    a.col_w64 = acc ? acc->w64 : nullptr;
+    {
+        const double tg = 2.0 * kp.gamma * 1.4426950408889634;
+        a.two_gl_lo = (float)(tg - (double)a.two_gl);
+    }
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -1137,6 +1338,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
             a.late_pairs = split->late_pairs;
             a.late_units = split->late_units;
         }
+        if (acc) return launch_mode2<MODE_ACC>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st, pdl);

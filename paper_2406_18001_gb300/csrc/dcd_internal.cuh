@@ -114,6 +114,11 @@ struct TcOperand {
     int64_t n_pad;        // features per half, multiple of the k-block
     int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3 or PACK_FP8
     const float *scale = nullptr;  // PACK_FP8: per-row scales (padded with zeros like the rows)
+    // the data-matrix row each packed row holds (nrows entries; nullptr: row r holds row r).
+    // The RBF kernel of a row with itself is 1: where the ids of a block's row and column
+    // are equal the epilogues take d^2 = 0 instead of the expansion, whose cancellation
+    // there leaves the FP32-accumulated dot's error (a bias of up to ~1e-5 in K_ii)
+    const int32_t *ids = nullptr;
 };
 // elements per 128-byte k-block of a packed row (the padding unit of n_pad)
 __host__ __device__ inline int k_block_elems(int kind)
@@ -157,11 +162,21 @@ struct TcSplit {
 };
 inline int64_t tc_split_part_elems(int pairs, int chunks) { return (int64_t)pairs * chunks * 2 * 256; }
 inline int tc_split_chunks(int64_t ncols) { return ncols <= 256 ? 1 : (int)((ncols + 255) / 256); }
+// The accurate apply epilogue (split-tf32 operands only): the RBF exponent and
+// kernel value in double-single arithmetic and the contraction with FP64
+// coefficients w64 (col_w is then unused); row_hl / col_hl are the low parts
+// of the RBF terms from launch_row_terms(..., h_lo) (RBF only).  Columns past
+// ncols read as zero coefficients.
+struct TcAccurate {
+    const double *w64 = nullptr;
+    const float *row_hl = nullptr;
+    const float *col_hl = nullptr;
+};
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp,
                             const float *row_h, const float *col_h, const float *col_w, const double *rs,
                             double *g, float *out, int64_t ldo, int64_t nrows_out, int64_t ncols,
                             int *err, cudaStream_t st, bool lower = false, const TcSplit *split = nullptr,
-                            bool pdl = false, int max_pairs = 0);
+                            bool pdl = false, int max_pairs = 0, const TcAccurate *acc = nullptr);
 
 // setup / per-step helpers (sample_update.cu)
 // src_scale: the per-row scales of an FP8 source (dtype DCD_FP8E4M3), else unused
@@ -176,8 +191,9 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
                                  int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
+// h_lo (PACK_TF32X3 only): the term as a pair of floats h + h_lo (FP64 sums), for the accurate epilogue
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
-                             float *h, cudaStream_t st, const float *scale = nullptr);
+                             float *h, cudaStream_t st, const float *scale = nullptr, float *h_lo = nullptr);
 // with the rows, optionally the per-row values f0 (and f1) of the same
 // indices: d0[j] = f0[idx[j]] (0 for an index outside [0, m))
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,

@@ -273,11 +273,30 @@ cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cuda
 // take the dequantised norm rscale[r]^2 * sum value(q)^2.  One warp per row,
 // FP64 partial sums, fixed order.
 __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, int64_t m, double scale, float *h,
-                                 const float *rscale)
+                                 const float *rscale, float *h_lo)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= m) return;
+    if (kind == PACK_TF32X3) {
+        // split tf32: the products the three MMAs form, hi.hi + 2 hi.lo, each exact in FP64 (24-bit
+        // factors) and summed in FP64; the term is stored as a pair of floats hi + lo (h_lo given) for
+        // the accurate epilogue, or rounded to one float
+        const float *row = (const float *)packed + r * 2 * n_pad;
+        double sd = 0.0;
+        for (int64_t c = lane; c < n_pad; c += 32) {
+            const double hi = row[c], lo = row[n_pad + c];
+            sd = fma(hi, hi + 2.0 * lo, sd);
+        }
+        for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        if (lane == 0) {
+            const double v = scale * sd;
+            const float vh = (float)v;
+            h[r] = vh;
+            if (h_lo) h_lo[r] = (float)(v - (double)vh);
+        }
+        return;
+    }
     // per-lane FP32 sums (each lane adds n_pad/32 squares), combined in FP64
     float sf = 0.f;
     for (int64_t c = lane; c < n_pad; c += 32) {
@@ -287,10 +306,6 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
         } else if (kind == PACK_BF16X3) {
             const __nv_bfloat16 *row = (const __nv_bfloat16 *)packed + r * 2 * n_pad;
             const float hi = __bfloat162float(row[c]), lo = __bfloat162float(row[n_pad + c]);
-            sf = fmaf(hi, hi + 2.f * lo, sf);
-        } else if (kind == PACK_TF32X3) {  // the products the three MMAs form: hi.hi + 2 hi.lo
-            const float *row = (const float *)packed + r * 2 * n_pad;
-            const float hi = row[c], lo = row[n_pad + c];
             sf = fmaf(hi, hi + 2.f * lo, sf);
         } else if (kind == PACK_FP8) {  // sum of value(q)^2; the row scale comes in below
             const float v = e4m3_value(((const uint8_t *)packed)[r * n_pad + c]);
@@ -307,13 +322,14 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
 }
 
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
-                             float *h, cudaStream_t st, const float *rscale)
+                             float *h, cudaStream_t st, const float *rscale, float *h_lo)
 {
     if (kind == PACK_FP8 && !rscale) return cudaErrorInvalidValue;
+    if (h_lo && kind != PACK_TF32X3) return cudaErrorInvalidValue;
     if (m <= 0) return cudaSuccess;
     double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;
     int64_t blocks = (m * 32 + 255) / 256;
-    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, kind, n_pad, m, scale, h, rscale);
+    row_terms_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, kind, n_pad, m, scale, h, rscale, h_lo);
     return cudaGetLastError();
 }
 

@@ -200,6 +200,8 @@ struct Solver {
     TcSplit tsplit;  // scratch of the balanced tensor-core apply
     void *Asr = nullptr;
     float *col_hr = nullptr;
+    // the accurate epilogue of the recomputed gradient: low parts of the RBF terms
+    float *row_hlr = nullptr, *col_hlr = nullptr;
     // CSR data matrix: the CUDA-core SpMM block (FP32, or FP64 in the FP64 mode)
     bool csr = false;
     CsrOperand ca;
@@ -278,6 +280,7 @@ struct Solver {
         const size_t row_bytes = tcd ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
         const bool need_pack = !csr && (tc || A->dtype != DCD_F64 || host);
         const bool ref_op = tcd && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
+        const bool acc_ref = tcd && (o.flags & DCD_FLAG_REFRESH);  // recomputed gradient: accurate epilogue
         const bool fp8 = tcd && pack_kind(o.prec) == PACK_FP8;
         const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
         // the look-ahead needs a stream of its own to fork from, graphs allowed, no per-phase
@@ -323,6 +326,8 @@ struct Solver {
             float *rhr = (float *)ar.take(ref_op ? sizeof(float) * m : 0);
             void *asr = ar.take((size_t)sb * row_bytes_r, 1024);
             float *chr = (float *)ar.take(ref_op ? sizeof(float) * col_pad : 0);
+            float *rhl = (float *)ar.take(acc_ref ? sizeof(float) * m : 0);
+            float *chl = (float *)ar.take(acc_ref ? sizeof(float) * col_pad : 0);
             int32_t *sidx = (int32_t *)ar.take(sizeof(int32_t) * col_pad);
             void *kss = ar.take((size_t)sb * sb * (tc ? 4 : 8));
             double *dl = (double *)ar.take(sizeof(double) * col_pad);
@@ -384,6 +389,8 @@ struct Solver {
             opr.row_h = rhr;
             Asr = asr;
             col_hr = chr;
+            row_hlr = rhl;
+            col_hlr = chl;
             S = sidx;
             Kss = kss;
             ldk = sb;
@@ -447,6 +454,8 @@ struct Solver {
             la = true;
         }
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        // the recurrence scratch starts zeroed (the FP64 form keeps its refinement state there)
+        if (problem == 1) DCD_TRY(cudaMemsetAsync(Lbuf, 0, recur_bdcd_scratch_bytes(o.s, o.b), st));
 
         // operand
         if (csr) {
@@ -494,6 +503,10 @@ struct Solver {
                 Asr = As;
                 col_hr = col_h;
                 ref_shared = true;
+            }
+            if (acc_ref) {  // the terms again, as hi + lo pairs (the hi parts are unchanged)
+                DCD_TRY(launch_row_terms(opr.packed, opr.kind, opr.n_pad, m, kp, opr.row_h, st, nullptr, row_hlr));
+                DCD_TRY(cudaMemsetAsync(col_hlr, 0, sizeof(float) * col_pad, st));
             }
         } else if (need_pack) {
             DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, 2, n, m, err, st, src_scale));
@@ -563,12 +576,14 @@ struct Solver {
     // the precision's floor lies above tol).
     int64_t refresh_wait = 0, refresh_gap = 1;
 
-    dcd_status check_converged()
+    // final: the check at the end of the budget, which always confirms (a
+    // reported metric is then never the cached gradient's alone)
+    dcd_status check_converged(bool final = false)
     {
         dcd_status s0 = measure(metric, primal, dual, ynorm2);
         if (s0 != DCD_OK || !(metric <= o.tol)) return s0;
         if (o.flags & DCD_FLAG_REFRESH) {
-            if (refresh_wait > 0) {
+            if (refresh_wait > 0 && !final) {
                 --refresh_wait;
                 return DCD_OK;
             }
@@ -624,7 +639,7 @@ struct Solver {
         if (tc) {
             // the cluster and blocked recurrences read the lower triangle only
             const bool lower = problem == 1 && recur_bdcd_lower_gram(ncols / o.b, o.b, 1, ldk);
-            TcOperand B{As, ncols, op.n_pad, op.kind, col_s};
+            TcOperand B{As, ncols, op.n_pad, op.kind, col_s, S};
             return launch_block_tc(B, B, kp, col_h, col_h, nullptr, nullptr, nullptr, (float *)Kss, ldk, ncols, ncols,
                                    err, st, lower);
         }
@@ -642,6 +657,20 @@ struct Solver {
             if (tc) DCD_TRY(launch_f64_to_f32(w64, ncols, col_w, st));
             return cuda_status(csr_apply(ncols, rs));
         }
+        if (tc && ref && row_hlr) {
+            // the recomputed gradient: split-tf32 products, accurate epilogue, FP64 coefficients
+            cudaError_t e = launch_gather_rows(opr.packed, packed_row_bytes(opr.kind, opr.n_pad), S, ncols, m, Asr,
+                                               err, st, opr.row_h, col_hr, row_hlr, col_hlr);
+            if (e != cudaSuccess) return cuda_status(e);
+            TcOperand Aop{opr.packed, m, opr.n_pad, opr.kind, nullptr};
+            TcOperand Bop{Asr, ncols, opr.n_pad, opr.kind, nullptr, S};
+            TcAccurate acc;
+            acc.w64 = w64;
+            acc.row_hl = row_hlr;
+            acc.col_hl = col_hlr;
+            return cuda_status(launch_block_tc(Aop, Bop, kp, opr.row_h, col_hr, col_w, rs, g, nullptr, 0, m, ncols,
+                                               err, st, false, &tsplit, false, 0, &acc));
+        }
         if (tc) {
             const Operand &x = ref ? opr : op;
             void *Asx = ref ? Asr : As;
@@ -654,7 +683,7 @@ struct Solver {
             e = clear_col_w_tail(ncols);
             if (e != cudaSuccess) return cuda_status(e);
             TcOperand Aop{x.packed, m, x.n_pad, x.kind, x.row_s};
-            TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 ? col_s : nullptr};
+            TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 ? col_s : nullptr, S};
             return cuda_status(
                 launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st, false, &tsplit));
         }
@@ -681,7 +710,7 @@ struct Solver {
     cudaError_t block_tc_apply(int64_t ncols, const double *rs)
     {
         TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
-        TcOperand Bop{As, ncols, op.n_pad, op.kind, col_s};
+        TcOperand Bop{As, ncols, op.n_pad, op.kind, col_s, S};
         return launch_block_tc(Aop, Bop, kp, op.row_h, col_h, col_w, rs, g, nullptr, 0, m, ncols, err, st, false,
                                &tsplit);
     }
@@ -803,7 +832,7 @@ struct Solver {
         const bool f8 = op.kind == PACK_FP8;
         DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2,
                                    op.row_h, Bq.col_h, f8 ? op.row_s : nullptr, f8 ? Bq.col_s : nullptr));
-        TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s};
+        TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s, Bq.S};
         DCD_TRY(launch_block_tc(Bo, Bo, kp, Bq.col_h, Bq.col_h, nullptr, nullptr, nullptr, (float *)Bq.Kss, ldk, ncols,
                                 ncols, err, s2, true));
         DCD_TRY(launch_recur_cluster_prep((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, lambda, (double)m, Bq.Lbuf,
@@ -840,7 +869,7 @@ struct Solver {
                                            Bp.Lbuf, delta, w64, col_w, &fu, err, st, nullptr, trig));
         DCD_TRY(clear_col_w_tail(ncols));
         TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
-        TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s};
+        TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s, Bp.S};
         // the chain writes only delta, the coefficients, alpha, g and the counter: the block's
         // products read none of them.  The pairs that land on the chain's SMs (the grid's last,
         // launched once the chain ends) take two units fewer: the others fill both tensor-memory
@@ -1030,7 +1059,7 @@ struct Solver {
             if (conv)
                 ;  // measured (and confirmed) at the check point that converged
             else if (o.tol > 0)
-                s0 = check_converged();
+                s0 = check_converged(finished());
             else
                 s0 = measure(metric, primal, dual, ynorm2);
         } else if (s0 == DCD_OK) {
@@ -1103,6 +1132,7 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem, bool csr)
     if (o->b > B_MAX || o->b > m) return DCD_EINVAL;
     if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
+    if (o->prec == DCD_PREC_TF32X3A) return DCD_EUNSUPPORTED;  // an apply-only precision
     if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
     if (o->prec == DCD_PREC_FP8 && csr) return DCD_EUNSUPPORTED;  // the CSR block has no fp8 form
     if (is_tc(o->prec) && !csr && !tc_available()) return DCD_EUNSUPPORTED;  // CSR: CUDA cores
@@ -1291,11 +1321,15 @@ size_t place(size_t &cur, size_t bytes, size_t align = 1024)
     return off;
 }
 
-dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t prec)
+dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, bool apply = false)
 {
     dcd_status s = validate_dense(A);
     if (s != DCD_OK) return s;
     if ((s = validate_kernel(k)) != DCD_OK) return s;
+    if (prec == DCD_PREC_TF32X3A) {  // the accurate epilogue: dense apply form only
+        if (!apply || A->fmt == DCD_CSR || A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
+        return tc_available() ? DCD_OK : DCD_EUNSUPPORTED;
+    }
     if (prec != DCD_PREC_FP64 && !is_tc(prec)) return DCD_EINVAL;
     if (prec == DCD_PREC_FP8 && A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;
     if (is_tc(prec) && A->fmt != DCD_CSR && !tc_available()) return DCD_EUNSUPPORTED;
@@ -1378,7 +1412,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     if (A->fmt == DCD_CSR) return component_block_csr(A, kp, prec, rows, nrows, cols, ncols, w, rs, g, out, ldo, st);
     ComponentBufs cb;
     cb.st = st;
-    if (!is_tc(prec)) {
+    if (!is_tc(prec) && prec != DCD_PREC_TF32X3A) {
         const bool pack = A->dtype != DCD_F64;
         size_t cur = 0;
         size_t oe = place(cur, 256);
@@ -1400,7 +1434,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
                                       ldo, err, st));
         return finish_component(err, st);
     }
-    const int pk = pack_kind(prec);
+    const bool accurate = prec == DCD_PREC_TF32X3A;
+    const int pk = accurate ? PACK_TF32X3 : pack_kind(prec);
     const int kb = k_block_elems(pk);
     const int64_t n_pad = (A->n + kb - 1) / kb * kb;
     const size_t rb = (size_t)packed_row_bytes(pk, n_pad);
@@ -1415,6 +1450,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     const bool fp8 = pk == PACK_FP8;
     size_t ors = place(cur, fp8 ? sizeof(float) * nrows : 0);
     size_t ocs = place(cur, fp8 ? sizeof(float) * cpad : 0);
+    size_t orl = place(cur, accurate ? sizeof(float) * nrows : 0);
+    size_t ocl = place(cur, accurate ? sizeof(float) * cpad : 0);
     // the apply form's balanced split over CTA pairs
     TcSplit sp;
     if (!out) {
@@ -1452,12 +1489,18 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, pk, n_pad, ncols, err, st,
                                  A->row_scale));
     }
-    DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st, rsa));
-    DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st, rsb));
+    float *rl = accurate ? (float *)(base + orl) : nullptr, *cl = accurate ? (float *)(base + ocl) : nullptr;
+    if (cl) DCD_TRY(cudaMemsetAsync(cl, 0, sizeof(float) * cpad, st));
+    DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st, rsa, rl));
+    DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st, rsb, cl));
     if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
-    TcOperand Aop{pa, nrows, n_pad, pk, rsa}, Bop{pb, ncols, n_pad, pk, rsb};
+    TcOperand Aop{pa, nrows, n_pad, pk, rsa, rows}, Bop{pb, ncols, n_pad, pk, rsb, cols};
+    TcAccurate acc;
+    acc.w64 = w;
+    acc.row_hl = rl;
+    acc.col_hl = cl;
     DCD_TRY(launch_block_tc(Aop, Bop, kp, rh, ch, w ? cw : nullptr, rs, g, (float *)out, ldo, nrows, ncols, err, st,
-                            false, &sp));
+                            false, &sp, false, 0, accurate ? &acc : nullptr));
     return finish_component(err, st);
 }
 
@@ -1498,7 +1541,7 @@ extern "C" dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kern
                                              const int32_t *cols, int64_t ncols, const double *w,
                                              const double *rowscale, double *g, void *stream)
 {
-    dcd_status s = component_check(A, k, prec);
+    dcd_status s = component_check(A, k, prec, true);
     if (s != DCD_OK) return s;
     if (ncols < 0 || (ncols > 0 && (!cols || !w)) || !g) return DCD_EINVAL;
     if (ncols == 0) return DCD_OK;
