@@ -36,10 +36,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coordinate updates/s and time-to-duality-gap 1e-6 (mixed vs FP64 s=1, 1 GB300)"
 UNIT = "coordinate updates/s"
-# dram__bytes_read.sum + dram__bytes_write.sum of one fused-block launch,
-# from an ncu capture of this build's kernel (prec, m, n, b, s) -> bytes
-NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64): 108.39e6}
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused-block launch from
+# an ncu capture: (prec, m, n, b, s, first 16 hex digits of the sha256 of
+# csrc/block_tc.cu when it was taken) -> bytes.  A changed kernel source
+# matches no entry, so its traffic reads null until it is captured again.
+NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64, "30c8c00e927fe3ab"): 108.39e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
+
+
+def kernel_source_sha16():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2406_18001_gb300", "csrc", "block_tc.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def oracle_threads():
+    """All host cores for the oracle's parallel row loops (results do not
+    depend on the count); returns the count in effect."""
+    import oracle
+    oracle.build()
+    return oracle.set_threads(os.cpu_count() or 1)
 
 
 def peaks():
@@ -140,100 +157,119 @@ def job_rate(units_per_rank, ms, ws):
 
 # ----------------------------------------------------------- reference ----
 def run_reference(args):
-    """The FP64 CPU oracle (s-step BDCD, Algorithm 4 as printed) timed on the
-    host.  Each step is one block update of the workload restricted to its
-    first m_sub rows, m_sub sized so the whole run stays within ~150 s; the
-    rate is scaled to the full m (the oracle's cost per update is linear in
-    m)."""
+    """The FP64 CPU oracle (s-step BDCD, Algorithm 4 as printed, the same s
+    and b as this bench's arm) timed on the host, its row loops on every core.
+    Each step is one outer s-step of the workload restricted to its first
+    m_sub rows, m_sub sized so the whole run stays within ~150 s; the rate is
+    scaled to the full m (the oracle's cost per step is linear in m)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    oracle.build()
+    nt = oracle_threads()
     p = make_problem(args.m, args.n)
     A64 = p.A.astype(np.float64)
     k = oracle.kernel("rbf", gamma=args.gamma)
+    s = args.s
     cal = min(args.m, 2000)
     t0 = time.perf_counter()
-    oracle.sstep_bdcd_krr(A64[:cal], p.y[:cal], k, args.lam, args.b, 1, 1, seed=0)
+    oracle.sstep_bdcd_krr(A64[:cal], p.y[:cal], k, args.lam, args.b, s, s, seed=0)
     per_row = (time.perf_counter() - t0) / cal
     budget = 150.0 / (args.steps + args.warmup)
     m_sub = int(max(args.b, min(args.m, budget / max(per_row, 1e-9))))
     As, ys = np.ascontiguousarray(A64[:m_sub]), p.y[:m_sub].copy()
     alpha = np.zeros(m_sub)
     for w in range(args.warmup):
-        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, 1, 1, seed=0, first_block=w, alpha0=alpha)
+        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, s, s, seed=0, first_block=w * s, alpha0=alpha)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, 1, 1, seed=0, first_block=args.warmup + i,
+        alpha = oracle.sstep_bdcd_krr(As, ys, k, args.lam, args.b, s, s, seed=0, first_block=(args.warmup + i) * s,
                                       alpha0=alpha)
     dt = time.perf_counter() - t0
-    v = args.steps * args.b / dt * (m_sub / args.m)
-    sample = (f"{args.steps} BDCD block updates (b={args.b}) on the first {m_sub} of {args.m} rows "
-              f"(n={args.n}), rate scaled by {m_sub}/{args.m}; plain FP64 C, one thread")
+    v = args.steps * s * args.b / dt * (m_sub / args.m)
+    sample = (f"{args.steps} outer s-steps (s={s}, b={args.b}) on the first {m_sub} of {args.m} rows "
+              f"(n={args.n}), rate scaled by {m_sub}/{args.m}; plain FP64 C, row loops on {nt} threads")
     out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "s": 1, "b": args.b, "m": args.m, "n": args.n, "m_sample": m_sub},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOAD, "s": s, "b": args.b, "m": args.m, "n": args.n, "m_sample": m_sub},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def cpu_baseline(args, budget_s=12.0):
-    """Oracle throughput on a bounded sample (block updates of the same
-    workload until ~budget_s of CPU work)."""
+    """Oracle throughput on a bounded sample: block updates (Algorithm 3,
+    s = 1) of the full workload until ~budget_s, its row loops on every host
+    core."""
     import oracle
     p = make_problem(args.m, args.n)
     A64 = p.A.astype(np.float64)
     k = oracle.kernel("rbf", gamma=args.gamma)
-    oracle.build()
+    nt = oracle_threads()
     alpha = np.zeros(args.m)
     t0 = time.perf_counter()
     blocks = 0
-    while time.perf_counter() - t0 < budget_s and blocks < 64:
+    while time.perf_counter() - t0 < budget_s and blocks < 512:
         alpha = oracle.sstep_bdcd_krr(A64, p.y, k, args.lam, args.b, 1, 1, seed=0, first_block=blocks,
                                       alpha0=alpha)
         blocks += 1
     dt = time.perf_counter() - t0
-    return {"value": blocks * args.b / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": blocks * args.b / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
             "sample": f"{blocks} BDCD block updates (b={args.b}) of the full {args.m}x{args.n} workload "
-                      f"({dt:.1f} s, plain FP64 C, one thread)"}
+                      f"({dt:.1f} s, plain FP64 C, row loops of U_k on {nt} threads)"}
 
 
 # ------------------------------------------------------ time to tolerance --
-def time_to_tol(args, torch, B, A, y, k, seed):
-    """Time to relative residual ||(K/lambda + mI) a - y|| / ||y|| <= tol for
-    the mixed form (this bench's precision and s) and the plain FP64 s = 1
-    form, on the same index stream.  The mixed solve checks the cached
-    gradient every ~256 block updates and confirms on a recomputed gradient
-    (DCD_FLAG_REFRESH).  The FP64 s = 1 solve needs the same number of block
-    updates (same iterates up to rounding), so its time is its measured time
-    per block update times that count; a full FP64 s = 1 run takes minutes."""
-    b, m = args.b, args.m
-    ce = max(1, 256 // args.s)
-    H = args.ttt_budget
-    plan = B.Plan(1, A, y, k, args.lam, b, args.s, H, seed=seed, prec=args.prec, tol=args.tol, check_every=ce,
-                  flags=B.FLAG_REFRESH)
+def fp64_residual(B, torch, A, y, alpha, k, lam):
+    """||(K/lambda + m I) alpha - y|| / ||y|| over all m rows: K alpha by the
+    FP64 CUDA-core kernel block (RBF distances from coordinate differences),
+    one pass over every column."""
+    m = alpha.numel()
+    g = torch.zeros(m, dtype=torch.float64, device=alpha.device)
+    cols = torch.arange(m, dtype=torch.int32, device=alpha.device)
+    B.kernel_block_apply(A, k, "fp64", cols, alpha / lam, g)
+    r = g + m * alpha - y
+    return float(torch.linalg.norm(r) / torch.linalg.norm(y))
+
+
+def solve_to_tol(B, torch, A, y, k, lam, b, s, prec, tol, budget, seed):
+    """One solve to relative residual tol: the mixed forms check the cached
+    gradient every ~256 block updates and confirm on a recomputed gradient
+    (DCD_FLAG_REFRESH); the FP64 form's cached gradient is exact to rounding."""
+    ce = max(1, 256 // s)
+    flags = B.FLAG_REFRESH if prec != "fp64" else 0
+    plan = B.Plan(1, A, y, k, lam, b, s, budget, seed=seed, prec=prec, tol=tol, check_every=ce, flags=flags)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st, _ = plan.run(-1)
     wall = time.perf_counter() - t0
     alpha = plan.alpha.clone()
     plan.close()
-    mixed = {"prec": args.prec, "s": args.s, "converged": bool(st["converged"]), "block_updates": st["iters_done"],
-             "coordinate_updates": st["iters_done"] * b, "ms": st["ms_total"], "wall_s": wall,
-             "resid_recomputed": st["final_metric"], "refreshes": st["refreshes"], "ms_refresh": st["ms_refresh"],
-             "check_every_outer_steps": ce}
-    # FP64 residual of the mixed result on sampled rows (FP64 kernel block, rows x all columns)
-    g = torch.Generator().manual_seed(1234)
-    rows = torch.randperm(m, generator=g)[:args.ttt_rows].to(torch.int32).to(A.device)
-    cols = torch.arange(m, dtype=torch.int32, device=A.device)
-    Kb = B.kernel_block(A, k, "fp64", cols, rows=rows)  # rows x m, FP64
-    r = Kb @ alpha / args.lam + m * alpha[rows.long()] - y[rows.long()]
-    mixed["resid_fp64_sampled_rows"] = float(torch.linalg.norm(r) / torch.linalg.norm(y[rows.long()]))
-    mixed["sampled_rows"] = args.ttt_rows
-    del Kb
+    out = {"prec": prec, "s": s, "converged": bool(st["converged"]), "block_updates": st["iters_done"],
+           "coordinate_updates": st["iters_done"] * b, "ms": st["ms_total"], "wall_s": wall,
+           "resid_solver": st["final_metric"], "refreshes": st["refreshes"], "ms_refresh": st["ms_refresh"],
+           "check_every_outer_steps": ce}
+    out["resid_fp64"] = fp64_residual(B, torch, A, y, alpha, k, lam)
+    out["reached_tol_fp64"] = bool(out["converged"] and out["resid_fp64"] <= tol)
+    return out, alpha
+
+
+def time_to_tol(args, torch, B, A, y, k, seed):
+    """Time to relative residual ||(K/lambda + mI) a - y|| / ||y|| <= tol:
+    the mixed form (this bench's precision and s) against the plain FP64 s = 1
+    form, on the same index stream.  Every result's residual is re-evaluated
+    over all rows with the FP64 kernel block, and a speedup is reported only
+    when the mixed result meets tol there.
+      full:  the workload itself.  A FP64 s = 1 run to tol takes minutes
+             here, so its time is ESTIMATED: its measured time per block
+             update times the mixed solve's block-update count.
+      small: the first ttt_small_m rows of the same workload, both forms run
+             to tol and timed (a measured ratio), and the mixed result
+             compared with the closed form alpha* = (K/lambda + m I)^-1 y
+             (kernel block from the FP64 oracle, dense solve)."""
+    b, m = args.b, args.m
+    mixed, _ = solve_to_tol(B, torch, A, y, k, args.lam, b, args.s, args.prec, args.tol, args.ttt_budget, seed)
     # FP64 s = 1: time per block update over a bounded run
     n64 = args.ttt_fp64_steps
     p64 = B.Plan(1, A, y, k, args.lam, b, 1, n64 + 8, seed=seed, prec="fp64")
@@ -244,12 +280,104 @@ def time_to_tol(args, torch, B, A, y, k, seed):
     st64, _ = p64.run(0)
     p64.close()
     ms_blk = (st64["ms_total"] - base["ms_total"]) / n64
-    fp64 = {"prec": "fp64", "s": 1, "ms_per_block_update": ms_blk, "blocks_timed": n64,
-            "ms_estimated": ms_blk * st["iters_done"]}
-    out = {"tol": args.tol, "metric": "relative residual ||(K/lambda + m I) alpha - y|| / ||y||",
-           "mixed": mixed, "fp64_s1": fp64,
-           "speedup": fp64["ms_estimated"] / mixed["ms"] if mixed["converged"] and mixed["ms"] > 0 else None}
+    fp64 = {"prec": "fp64", "s": 1, "estimated": True, "ms_per_block_update": ms_blk, "blocks_timed": n64,
+            "ms_estimated": ms_blk * mixed["block_updates"],
+            "how": "measured ms per block update x the mixed solve's block updates (same index stream)"}
+    full = {"mixed": mixed, "fp64_s1": fp64,
+            "speedup_estimated": fp64["ms_estimated"] / mixed["ms"] if mixed["reached_tol_fp64"] else None}
+    out = {"tol": args.tol, "metric": "relative residual ||(K/lambda + m I) alpha - y|| / ||y||", "full": full}
+    if args.ttt_small_m > 0:
+        ms_ = min(args.ttt_small_m, m)
+        As, ys = A[:ms_].contiguous(), y[:ms_].contiguous()
+        mx, a_mx = solve_to_tol(B, torch, As, ys, k, args.lam, b, args.s, args.prec, args.tol, args.ttt_budget, seed)
+        f6, a_64 = solve_to_tol(B, torch, As, ys, k, args.lam, b, 1, "fp64", args.tol, args.ttt_budget, seed)
+        small = {"m": ms_, "mixed": mx, "fp64_s1": f6,
+                 "speedup_measured": f6["ms"] / mx["ms"] if mx["reached_tol_fp64"] and f6["reached_tol_fp64"]
+                 else None}
+        if not args.no_cpu:
+            import oracle
+            oracle_threads()
+            A64 = As.double().cpu().numpy()
+            ko = oracle.kernel("rbf", gamma=args.gamma)
+            t0 = time.perf_counter()
+            Kf = oracle.kernel_block(ko, A64, np.arange(ms_))
+            star = np.linalg.solve(Kf / args.lam + ms_ * np.eye(ms_), ys.cpu().numpy())
+            small["closed_form_s"] = time.perf_counter() - t0
+            del Kf
+            a1, a2 = a_mx.cpu().numpy(), a_64.cpu().numpy()
+            small["alpha_vs_closed_form"] = {"mixed": float(np.linalg.norm(a1 - star) / np.linalg.norm(star)),
+                                             "fp64_s1": float(np.linalg.norm(a2 - star) / np.linalg.norm(star))}
+        out["small"] = small
     return out
+
+
+# ------------------------------------------- headline error vs the oracle --
+def krr_objective_on_support(oracle, A64, y, ko, lam, alpha):
+    """1/2 a^T (K/lambda + m I) a - y^T a for an alpha with few nonzeros: only
+    the support's kernel entries (from the oracle) enter."""
+    supp = np.nonzero(alpha)[0]
+    Kss = oracle.kernel_block(ko, A64, supp, rows=supp)
+    a = alpha[supp]
+    return 0.5 * (a @ (Kss @ a) / lam + len(alpha) * (a @ a)) - y[supp] @ a
+
+
+def headline_error(args, torch, B, A, y, k, p, seed):
+    """Error of the headline configuration against the FP64 oracle (Algorithm
+    4 as printed) on the same index stream: err_steps outer steps from
+    alpha = 0 of the full workload, alpha's relative 2-norm error and the dual
+    objective's relative error, for this bench's precision and for bf16x3."""
+    import oracle
+    H = args.err_steps * args.s
+    nt = oracle_threads()
+    A64 = p.A.astype(np.float64)
+    ko = oracle.kernel("rbf", gamma=args.gamma)
+    t0 = time.perf_counter()
+    want = oracle.sstep_bdcd_krr(A64, p.y, ko, args.lam, args.b, args.s, H, seed=seed)
+    t_or = time.perf_counter() - t0
+    f_want = krr_objective_on_support(oracle, A64, p.y, ko, args.lam, want)
+    out = {"H_block_updates": H, "outer_steps": args.err_steps, "seed": seed, "oracle_s": t_or,
+           "oracle_threads": nt, "oracle": "sstep_bdcd_krr (Algorithm 4, FP64, Q_k materialised)"}
+    for prec in dict.fromkeys((args.prec, "bf16x3")):
+        al = B.krr_solve(A, y, k, args.lam, args.b, args.s, H, seed=seed, prec=prec)[0].cpu().numpy()
+        f = krr_objective_on_support(oracle, A64, p.y, ko, args.lam, al)
+        out[prec] = {"alpha_rel_err": float(np.linalg.norm(al - want) / np.linalg.norm(want)),
+                     "objective_rel_err": float(abs(f - f_want) / abs(f_want))}
+    return out
+
+
+def dense_roofline(prec, m, n, b, s, t_block, bf16_peak, hbm_peak, src, traffic=None):
+    """Roofline of one fused kernel-block launch (a5) on the method's own
+    work: 2 m n sb flops (the paper's sbfmn of Thm 2 with f = 2n) and one read
+    of the packed operand plus the gradient.  The split precisions issue 3
+    MMAs per k-step; that tensor-pipe work is reported apart (mma_pipe) and is
+    not what frac measures."""
+    sb = s * b
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[prec]
+    mma_mult = 3 if prec in ("bf16x3", "tf32x3") else 1  # MMAs per k-step
+    flops = 2.0 * m * n * sb
+    bytes_ = m * n * esz + sb * n * esz + m * (8 + 8 + 4)
+    ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
+    # a contraction's peak is its own dtype's: the measured bf16 figure times the nominal ratio
+    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25,
+               "tf32x3": 1.1 / 2.25}.get(prec, 0.0) * bf16_peak
+    if tc_peak and flops * mma_mult / bytes_ >= ridge:
+        roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if traffic is None:
+        traffic = NCU_TRAFFIC.get((prec, m, n, b, s, kernel_source_sha16()))
+    roof["traffic"] = traffic
+    roof["peak_source"] = f"{src} (MEASURED_PEAKS.json bf16 burst; HBM copy)"
+    roof["kernel"] = ("block_tc2_kernel (fused kernel block + gradient update, CTA pairs)" if prec != "fp64"
+                      else "block_simt_f64_kernel")
+    roof["algorithmic"] = {"flops_per_launch": flops, "bytes_per_launch": bytes_,
+                           "flops_rule": "2*m*n*s*b (method flops; split MMA passes not counted)"}
+    if tc_peak:
+        roof["mma_pipe"] = {"mma_per_k_step": mma_mult, "flops_per_launch": flops * mma_mult,
+                            "achieved": flops * mma_mult / t_block / 1e12, "unit": "TFLOP/s",
+                            "frac": flops * mma_mult / t_block / 1e12 / tc_peak}
+    return roof
 
 
 # ---------------------------------------------------------------- GPU -----
@@ -321,29 +449,9 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
              ("sample", "gram", "recur", "block", "update")}
     t_block = phase["block"] * 1e-3
     hbm_peak, bf16_peak, bf16_sus, src = peaks()
-    sb = args.s * args.b
-    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
-    mma_mult = 3 if args.prec in ("bf16x3", "tf32x3") else 1  # MMAs per k-step
-    n_alg = args.n
-    flops = 2.0 * args.m * n_alg * sb * mma_mult
-    bytes_ = args.m * n_alg * esz + sb * n_alg * esz + args.m * (8 + 8 + 4)
-    intensity = flops / bytes_
-    ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
-    # a contraction's peak is its own dtype's: the measured bf16 figure times the nominal ratio
-    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}.get(args.prec, 0.0) * bf16_peak
-    if tc_peak and intensity >= ridge:
-        roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_ / t_block / 1e9, "peak": hbm_peak, "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    traffic = args.traffic
-    if traffic is None:
-        traffic = NCU_TRAFFIC.get((args.prec, args.m, args.n, args.b, args.s))
-    roof["traffic"] = traffic
-    roof["peak_source"] = src
-    roof["kernel"] = "block_tc2_kernel (fused kernel block + gradient update, CTA pairs)" if args.prec != "fp64" \
-        else "block_simt_f64_kernel"
-    roof["algorithmic"] = {"flops_per_launch": flops, "bytes_per_launch": bytes_, "launch_ms": phase["block"]}
+    roof = dense_roofline(args.prec, args.m, args.n, args.b, args.s, t_block, bf16_peak, hbm_peak, src,
+                          args.traffic)
+    roof["algorithmic"]["launch_ms"] = phase["block"]
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     if True:
@@ -366,6 +474,9 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     ttt = None
     if not args.no_ttt:
         ttt = time_to_tol(args, torch, B, A, y, k, rank)
+    herr = None
+    if rank == 0 and not args.no_cpu and args.err_steps > 0:
+        herr = headline_error(args, torch, B, A, y, k, p, rank)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -383,7 +494,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
                "step_ms": {"min": ms_steps[0], "median": ms_steps[len(ms_steps) // 2], "max": ms_steps[-1]},
                "phase_ms": phase,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary(), "time_to_tol": ttt}
+               "clocks": clk.summary(), "time_to_tol": ttt, "error_vs_oracle": herr}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -401,7 +512,7 @@ def csr_cpu_baseline(p, y, s, budget_s=12.0):
     per-update cost is linear in rows x columns, so the rate is scaled by
     (m_sub x n_sub) / (m x n)."""
     import oracle
-    oracle.build()
+    nt = oracle_threads()
     m_sub = min(p.m, 500)
     e1 = int(p.row_ptr[m_sub])
     used, col = np.unique(p.col_idx[:e1], return_inverse=True)
@@ -418,9 +529,10 @@ def csr_cpu_baseline(p, y, s, budget_s=12.0):
         H = min(4 * H, 4096)
     dt = time.perf_counter() - t0
     scale = (m_sub * used.size) / (p.m * p.n)
-    return {"value": done / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": done / dt * scale, "unit": UNIT, "cores": nt, "kind": "oracle",
             "sample": f"{done} DCD updates (s={s}) on the first {m_sub} rows x their {used.size} columns in dense "
-                      f"form ({dt:.1f} s, plain FP64 C, one thread), rate scaled by rows x columns to the full matrix"}
+                      f"form ({dt:.1f} s, plain FP64 C, row loops on {nt} threads), rate scaled by rows x columns "
+                      f"to the full matrix"}
 
 
 def run_gpu_csr(args):
@@ -635,7 +747,7 @@ def run_gpu_fp8(args):
                                         "fp8_vs_fp64_on_bf16_data": rel(arms["fp8"][1], ref_long["fp64_on_bf16"])}}
         if not args.no_cpu:
             import oracle
-            oracle.build()
+            nt = oracle_threads()
             ko = oracle.kernel("rbf", gamma=gam)
             t0 = time.perf_counter()
             want = oracle.bdcd_krr(A_sub_h, y_sub_h, ko, lam, b, Hs, seed=7)
@@ -645,9 +757,9 @@ def run_gpu_fp8(args):
             out_err["vs_oracle_note"] = ("oracle = FP64 BDCD (Algorithm 3) on the BF16-stored rows; fp64_on_fp8 and "
                                          "fp8 differ from it by the FP8 storage")
             upd = Hs * b
-            cpu = {"value": upd / t_or * msub / m, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": upd / t_or * msub / m, "unit": UNIT, "cores": nt, "kind": "oracle",
                    "sample": f"{Hs} BDCD block updates (b={b}) on rows 0..{msub - 1} ({t_or:.1f} s, plain FP64 C, "
-                             f"one thread), rate scaled by rows to m={m}"}
+                             f"row loops on {nt} threads), rate scaled by rows to m={m}"}
         hbm_peak, bf16_peak, bf16_sus, src = peaks()
         sb = s * b
         flops = 2.0 * m * n * sb
@@ -746,12 +858,12 @@ def run_gpu_sweep(args):
     wall = rank_max(wall, ws, dev)  # the job's times are its slowest replica's
     wall_e2e = rank_max(wall_e2e, ws, dev)
     launches = sum(int(st["gpu_launches_per_step"]) * int(st["outer_steps"]) for st in sts)
-    # roofline of the whole call: every outer step is one fused block, 2 m n sb flops per MMA pass (x3
-    # for the split forms), and reads its problem's packed operand once
+    # roofline of the whole call on the method's work: every outer step is one fused block of 2 m n sb
+    # flops that reads its problem's packed operand once (the split forms' extra MMA passes apart)
     n_sw = 128
     esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
     mult = 3 if args.prec in ("bf16x3", "tf32x3") else 1
-    flops = sum(int(st["outer_steps"]) * 2.0 * p["A"].shape[0] * n_sw * p["s"] * p["b"] * mult
+    flops = sum(int(st["outer_steps"]) * 2.0 * p["A"].shape[0] * n_sw * p["s"] * p["b"]
                 for st, p in zip(sts, probs))
     bytes_ = sum(int(st["outer_steps"]) * (p["A"].shape[0] * (n_sw * esz + 20) + p["s"] * p["b"] * n_sw * esz)
                  for st, p in zip(sts, probs))
@@ -760,7 +872,10 @@ def run_gpu_sweep(args):
     roof = {"bound": "tensor", "achieved": flops / wall / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
             "frac": flops / wall / 1e12 / tc_peak if tc_peak else None, "traffic": None, "peak_source": src,
             "kernel": "whole batched call (all problems' steps)",
-            "algorithmic": {"flops": flops, "bytes": bytes_, "hbm_gbs": bytes_ / wall / 1e9, "wall_s": wall}}
+            "algorithmic": {"flops": flops, "flops_rule": "sum over steps of 2*m*n*s*b (method flops)",
+                            "bytes": bytes_, "hbm_gbs": bytes_ / wall / 1e9, "wall_s": wall},
+            "mma_pipe": {"mma_per_k_step": mult, "flops": flops * mult,
+                         "frac": flops * mult / wall / 1e12 / tc_peak if tc_peak else None}}
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = sweep_cpu_baseline(probs, upd)
@@ -790,7 +905,7 @@ def sweep_cpu_baseline(probs, upd_total, nsample=8, budget_s=15.0):
     rate is measured as m * coordinate updates per second and the whole
     sweep's time estimated from it."""
     import oracle
-    oracle.build()
+    nt = oracle_threads()
     idx = np.linspace(0, len(probs) - 1, nsample).astype(int)
     work = 0.0
     t0 = time.perf_counter()
@@ -807,9 +922,10 @@ def sweep_cpu_baseline(probs, upd_total, nsample=8, budget_s=15.0):
     dt = time.perf_counter() - t0
     rate_mu = work / dt  # m * coordinate updates per second
     total_mu = sum(p["A"].shape[0] * p["H"] * p["b"] for p in probs)
-    return {"value": upd_total / (total_mu / rate_mu), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Algorithm 3 on {len(idx)} of the {len(probs)} problems ({dt:.1f} s, plain FP64 C, one "
-                      f"thread); the whole sweep's time estimated from the measured m x updates per second"}
+    return {"value": upd_total / (total_mu / rate_mu), "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"Algorithm 3 on {len(idx)} of the {len(probs)} problems ({dt:.1f} s, plain FP64 C, row "
+                      f"loops on {nt} threads); the whole sweep's time estimated from the measured m x updates "
+                      f"per second"}
 
 
 def main():
@@ -846,7 +962,10 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--ttt-budget", type=int, default=400000, help="block-update cap of the tolerance solve")
-    ap.add_argument("--ttt-rows", type=int, default=1000, help="rows of the FP64 residual check")
+    ap.add_argument("--ttt-small-m", type=int, default=6000,
+                    help="rows of the subproblem on which both forms run to tolerance (0: skip)")
+    ap.add_argument("--err-steps", type=int, default=2,
+                    help="outer steps of the headline compared with the oracle (0: skip)")
     ap.add_argument("--ttt-fp64-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
