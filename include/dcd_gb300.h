@@ -98,12 +98,16 @@ typedef enum {
                             k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
     DCD_PREC_TF32X3 = 5, /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
                             three kind::tf32 MMAs per k-step, FP32 accumulation */
-    DCD_PREC_TF32X3A = 6 /* the split-tf32 products with an accurate epilogue: the RBF exponent
-                            and kernel value in double-single arithmetic (exp2 by reduction to the
-                            nearest integer and a degree-7 Taylor polynomial) and the contraction
-                            with the FP64 coefficients in double-single.  The precision of the
-                            gradient recomputed under DCD_FLAG_REFRESH in every tensor-core mode.
-                            dcd_kernel_block_apply only (elsewhere DCD_EUNSUPPORTED) */
+    DCD_PREC_REFRESH = 6 /* the arithmetic of the gradient recomputed under DCD_FLAG_REFRESH (every
+                            tensor-core mode): each row scaled by a power of two and cut into four
+                            bf16 planes of integers in [-64, 64] (27 bits of the row's largest
+                            entry); the 10 plane products of order <= 3 are summed in FP32 tensor
+                            memory, where their sums are exact integers for n <= 1024 (beyond:
+                            split tf32 products); the RBF exponent and kernel value in
+                            double-single arithmetic (exp2 by reduction to the nearest integer and
+                            a degree-7 Taylor polynomial), and the contraction with the FP64
+                            coefficients in double-single.  dcd_kernel_block_apply only
+                            (elsewhere DCD_EUNSUPPORTED) */
 } dcd_precision;
 
 /* opts.flags */
@@ -113,7 +117,7 @@ typedef enum {
 #define DCD_FLAG_NO_GRAPH 0x8     /* launch every kernel directly instead of replaying CUDA graphs */
 #define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
                                      recompute the gradient from alpha by full kernel passes (tensor-core
-                                     modes: DCD_PREC_TF32X3A; FP64 mode: FP64) and accept convergence only
+                                     modes: DCD_PREC_REFRESH; FP64 mode: FP64) and accept convergence only
                                      if the recomputed metric meets tol too; the check at the end of the
                                      budget always recomputes */
 

@@ -16,8 +16,9 @@
 // operand) for recomputing the gradient from alpha: the RBF exponent in
 // double-single arithmetic, exp2 by reduction to the nearest integer and a
 // degree-7 Taylor polynomial, and the contraction with FP64 coefficients in
-// double-single; its kernel entries are within a few FP32 ulps of the exact
-// kernel of the data, where the fast epilogue's are within ~2.5e-7.
+// double-single.  On the sliced operand (exact products) its kernel values
+// are within ~1e-8 of the exact kernel of the data; the fast epilogue's carry
+// the FP32-accumulated dot's ~1e-7 and the FP32 exponent's ~2.5e-7.
 //
 // Two kernels, both persistent with one CTA per SM and 320 threads:
 //   block_tc_kernel  (store) over 128-row tiles x N-chunks of 64 columns
@@ -71,7 +72,12 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
 // q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
 // MODE_ACC: the split-tf32 products with the accurate apply epilogue (pairs only).
-constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5;
+// MODE_SLICED: sliced operands (4 planes of small integers, per-row powers of
+// two); the 10 plane products with p + q <= 3 go into 4 accumulators by
+// p + q, whose FP32 sums are exact integers; accurate epilogue (pairs only).
+constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5,
+              MODE_SLICED = 6;
+constexpr int SLICED_BN = 128;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 320;
@@ -228,6 +234,26 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32])
                  : "memory");
 }
 
+// tcgen05.ld of 32 lanes x 16 columns, waited for at once
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -308,27 +334,39 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
     e = fmaf(a, b, -p);
 }
 
-// 2^x for x <= 0 given as x_hi + x_lo (|x_lo| <= ulp(x_hi)): x = k + f with
-// k = rint(x_hi) and |f| <= 1/2, 2^f = e^(f ln 2) by the Taylor polynomial of
-// degree 7 (truncation below 5.3e-9 relative for |f ln 2| <= 0.35), evaluated
-// by Horner's rule, then 2^k applied to the exponent field.  Results below
-// 2^-125 are returned as 0.
-__device__ __forceinline__ float exp2_ds(float xh, float xl)
+// 2^x for x <= 0 given as x_hi + x_lo (|x_lo| <= ulp(x_hi)), as a
+// double-single kh + kl: x = k + f with k = rint(x_hi), |f| <= 1/2, and
+// u = f ln 2 (double-single, ln 2 as hi + lo); e^u = 1 + u + u^2 T(u) with T
+// the Taylor polynomial of degree 5 of (e^u - 1 - u) / u^2 (truncation below
+// 5.3e-9 relative for |u| <= 0.35), the small u^2 T(u) in FP32 from u's high
+// part, 1 + u + u^2 T(u) summed in double-single; then 2^k applied to the
+// exponent fields.  Results below 2^-125 are returned as 0.
+__device__ __forceinline__ void exp2_ds(float xh, float xl, float &kh, float &kl)
 {
-    if (xh < -125.f) return 0.f;
+    if (xh < -125.f) {
+        kh = 0.f;
+        kl = 0.f;
+        return;
+    }
     const float k = rintf(xh);
-    const float f = (xh - k) + xl;  // xh - k is exact
-    // f ln 2 with ln 2 = 0x1.62e430p-1 + 0x1.fdf474p-26 (hi + lo)
-    const float u = fmaf(f, 0x1.62e430p-1f, f * 0x1.fdf474p-26f);
-    float p = 1.f / 5040.f;
-    p = fmaf(p, u, 1.f / 720.f);
-    p = fmaf(p, u, 1.f / 120.f);
-    p = fmaf(p, u, 1.f / 24.f);
-    p = fmaf(p, u, 1.f / 6.f);
-    p = fmaf(p, u, 0.5f);
-    p = fmaf(p, u, 1.f);
-    p = fmaf(p, u, 1.f);
-    return p * __int_as_float(((int)k + 127) << 23);
+    const float fh = xh - k;  // exact
+    float uh, ul;
+    two_prod(fh, 0x1.62e430p-1f, uh, ul);
+    ul = fmaf(fh, 0x1.fdf474p-26f, fmaf(xl, 0x1.62e430p-1f, ul));
+    float t = 1.f / 5040.f;
+    t = fmaf(t, uh, 1.f / 720.f);
+    t = fmaf(t, uh, 1.f / 120.f);
+    t = fmaf(t, uh, 1.f / 24.f);
+    t = fmaf(t, uh, 1.f / 6.f);
+    t = fmaf(t, uh, 0.5f);
+    const float tail = t * uh * uh;
+    float sh, sl;
+    fast_two_sum(1.f, uh, sh, sl);  // |uh| < 1
+    sl += ul + tail;
+    fast_two_sum(sh, sl, sh, sl);
+    const float sc = __int_as_float(((int)k + 127) << 23);
+    kh = sh * sc;
+    kl = sl * sc;
 }
 
 // K(a_i, b_j) from the accumulator c; rf is the per-row factor: 2 gamma
@@ -357,6 +395,49 @@ __device__ __forceinline__ float kf32_id(float c, float hr, float hc, float rf, 
 {
     if (KIND == DCD_RBF && rid == cid) return 1.f;
     return kf32<KIND>(c, hr, hc, rf, a);
+}
+
+// The accurate epilogue's kernel value (kh + kl) from a dot product given as
+// dh + dl (double-single): the RBF exponent x = 2 gamma log2(e) (a.b) - (h_i
+// + h_j) = -gamma log2(e) d^2 in double-single, clamped at 0, then exp2_ds;
+// the polynomial by repeated double-single products; linear as it is.
+template <int KIND>
+__device__ __forceinline__ void k_accurate(float dh, float dl, float hr, float hrl, float hc, float hcl,
+                                           const TcArgs &a, float &kh, float &kl)
+{
+    kl = 0.f;
+    if (KIND == DCD_RBF) {
+        float sh, sl, ph, pl, xh, xl;
+        two_sum(hr, hc, sh, sl);
+        sl += hrl + hcl;
+        two_prod(a.two_gl, dh, ph, pl);
+        pl = fmaf(a.two_gl, dl, fmaf(a.two_gl_lo, dh, pl));
+        two_sum(ph, -sh, xh, xl);
+        xl += pl - sl;
+        fast_two_sum(xh, xl, xh, xl);
+        if (xh > 0.f) {  // d^2 >= 0
+            xh = 0.f;
+            xl = 0.f;
+        }
+        exp2_ds(xh, xl, kh, kl);
+    } else if (KIND == DCD_LINEAR) {
+        kh = dh;
+        kl = dl;
+    } else {
+        float th, tl;
+        two_sum(a.coef0, dh, th, tl);
+        tl += dl;
+        fast_two_sum(th, tl, th, tl);
+        float rh = th, rl = tl;
+        for (int e = 1; e < a.degree; ++e) {
+            float pp, pe;
+            two_prod(rh, th, pp, pe);
+            pe = fmaf(rh, tl, fmaf(rl, th, pe));
+            fast_two_sum(pp, pe, rh, rl);
+        }
+        kh = rh;
+        kl = rl;
+    }
 }
 
 // store form: one item = one (row tile, N-chunk) pair; with `lower`, the
@@ -602,7 +683,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 constexpr int BM2 = 2 * BM;                          // rows per pair tile
 constexpr int B2_STAGE = (BN_MAX / 2) * ROW_BYTES;   // 16 KB: half of an N-chunk
 constexpr int RING2_BYTES = 6 * (A_STAGE + B2_STAGE);  // 6 single or 3 split stages
-constexpr int CST_FLOATS = 5 * 128;                   // staged column terms per epilogue warp
+constexpr int CST_FLOATS = 6 * 128;                   // staged column terms per epilogue warp
 constexpr int SMEM2_BYTES = RING2_BYTES + 1024 + 256 + XCH_BYTES + 8 * CST_FLOATS * 4;
 
 // arrive on an mbarrier of the pair given by its shared::cluster address
@@ -722,14 +803,20 @@ template <int MODE, int KIND>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     block_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
-    constexpr bool ACC = MODE == MODE_ACC;
-    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3 || ACC;
+    constexpr bool SL = MODE == MODE_SLICED;
+    constexpr bool ACC = MODE == MODE_ACC || SL;  // the accurate epilogue
+    constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3 || MODE == MODE_ACC;
     constexpr bool FP8 = MODE == MODE_FP8;
     constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
-    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3 || ACC;
-    constexpr int STAGES = SPLIT ? 3 : 6;
-    constexpr int A_ST = SPLIT ? 2 * A_STAGE : A_STAGE;  // hi then lo
-    constexpr int B_ST = SPLIT ? 2 * B2_STAGE : B2_STAGE;
+    constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3 || MODE == MODE_ACC;
+    constexpr int PLANES = SL ? 4 : SPLIT ? 2 : 1;  // operand planes (hi, lo / the four slices)
+    constexpr int STAGES = SL ? 2 : SPLIT ? 3 : 6;
+    // a stage holds every plane of one k-block; the sliced form's B planes are SLICED_BN / 2 rows
+    constexpr int B_PLANE = SL ? (SLICED_BN / 2) * ROW_BYTES : B2_STAGE;
+    constexpr int A_ST = PLANES * A_STAGE;
+    constexpr int B_ST = PLANES * B_PLANE;
+    constexpr int NACC = SL ? 1 : 2;  // accumulator buffers in tensor memory
+    static_assert(STAGES * (A_ST + B_ST) <= RING2_BYTES, "operand ring exceeds its shared memory");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
@@ -792,7 +879,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             // ---------------------------------------------------- producer --
             uint32_t it = 0;
             bool ok = true;
-            const uint32_t bytes = (uint32_t)(2 * (SPLIT ? 2 : 1) * (A_STAGE + bh * ROW_BYTES));  // both CTAs'
+            const uint32_t bytes = (uint32_t)(2 * PLANES * (A_STAGE + bh * ROW_BYTES));  // both CTAs'
             for (int i = 0; ok && i < nunits; ++i) {
                 int item, nc;
                 pair_unit(a, pair, npairs, ranged, u0, u1, i, item, nc);
@@ -805,11 +892,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                         const uint32_t fb = full0 + 8u * s;
                         const int ya = item * BM2 + (int)rank * BM, yb = nc * bn + (int)rank * bh;
                         if (rank == 0) mbar_expect_tx(&full[s], bytes);
-                        tma_load_2d_pair(sA + s * A_ST, &tmA, fb, kb * kb_elems, ya);
-                        tma_load_2d_pair(sB + s * B_ST, &tmB, fb, kb * kb_elems, yb);
-                        if (SPLIT) {
-                            tma_load_2d_pair(sA + s * A_ST + A_STAGE, &tmA, fb, a.lo_off + kb * kb_elems, ya);
-                            tma_load_2d_pair(sB + s * B_ST + B2_STAGE, &tmB, fb, a.lo_off + kb * kb_elems, yb);
+#pragma unroll
+                        for (int pl = 0; pl < PLANES; ++pl) {  // plane pl starts at column pl * lo_off
+                            tma_load_2d_pair(sA + s * A_ST + pl * A_STAGE, &tmA, fb, pl * a.lo_off + kb * kb_elems, ya);
+                            tma_load_2d_pair(sB + s * B_ST + pl * B_PLANE, &tmB, fb, pl * a.lo_off + kb * kb_elems, yb);
                         }
                     }
             }
@@ -825,7 +911,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             uint32_t it = 0, acc_it = 0;
             bool ok = true, issued = false;
             for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
-                    const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                    const uint32_t buf = acc_it % NACC, aph = (acc_it / NACC) & 1;
                     if (!mbar_wait(&tempty[buf], aph ^ 1, abort_flag, a.err)) {
                         ok = false;
                         break;
@@ -842,6 +928,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                         const uint32_t ab = su32(sA + s * A_ST), bb = su32(sB + s * B_ST);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
+                            if (SL) {
+                                // accumulator g (columns g * bn..) takes the products of slices p and g - p
+#pragma unroll
+                                for (int g = 0; g < 4; ++g)
+#pragma unroll
+                                    for (int p = 0; p <= g; ++p)
+                                        mma2<MK>(dtm + (uint32_t)(g * bn), sw128_desc(ab + p * A_STAGE + 32 * k),
+                                                 sw128_desc(bb + (g - p) * B_PLANE + 32 * k), idesc,
+                                                 (kb > 0 || k > 0 || p > 0) ? 1u : 0u);
+                                continue;
+                            }
                             mma2<MK>(dtm, sw128_desc(ab + 32 * k), sw128_desc(bb + 32 * k), idesc,
                                      (kb > 0 || k > 0) ? 1u : 0u);
                             if (SPLIT) {
@@ -876,7 +973,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         int64_t row = 0;
         bool row_ok = false;
-        float hr = 0.f, hrl = 0.f, rf = 0.f;
+        float hr = 0.f, hrl = 0.f, rf = 0.f, rsl = 0.f;
         int rid = -2;  // data-matrix row of this thread's row (-2: none)
         const int *cid = (const int *)(cst + 512);  // staged column ids (-1 past the block)
         double tacc = 0.0;  // this half's row sum over the tile's chunks so far, in chunk order
@@ -890,6 +987,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 row_ok = row < a.nrows_out;
                 hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
                 if (ACC) hrl = (KIND == DCD_RBF && row_ok) ? a.row_hl[row] : 0.f;
+                if (SL) rsl = row_ok ? a.row_s[row] * 0x1p-12f : 0.f;  // 2^(e_i - 12)
                 rid = row_ok ? (a.row_id ? a.row_id[row] : (int)row) : -2;
                 const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
                 rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
@@ -897,7 +995,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             }
             const bool whole = !ranged || (item * nch >= u0 && (item + 1) * nch <= u1);
             const bool last = nc == nch - 1 || u == u1 - 1;  // last chunk of the tile in this pair's units
-            double cs = 0.0;  // this chunk's part of the row sum (this half's column groups)
+            // this chunk's part of the row sum (this half's column groups): the fast epilogue adds
+            // its groups in double-single FP32 (GB300's FP64 pipe issues ~1.6 operations per clock
+            // per SM, too few for per-group FP64 sums at the bf16 MMA rate), the accurate ones in FP64
+            double cs = 0.0;
+            float cs_h = 0.f, cs_l = 0.f;
             // one 32-column group: terms from the staged columns (4 per shared-memory load), the
             // same sums in the same order as a column-by-column loop
             // the 32 columns' kernel values (`own`: bit q set where column q is this row's own
@@ -952,66 +1054,81 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 }
                 if (own) group_terms(r, j0, own, p0, p1);
                 else group_terms(r, j0, 0u, p0, p1);
-                cs += (double)p0 + (double)p1;
+                float a0, b0, e0;
+                two_sum(p0, p1, a0, b0);
+                two_sum(cs_h, a0, cs_h, e0);
+                cs_l += e0 + b0;
             };
             // the accurate form of one group: staged columns [h | w_hi | w_lo | h_lo]; the exponent
             // x = 2 gamma log2(e) c - (h_i + h_j) = -gamma log2(e) d^2 and the kernel value in
             // double-single, the products with w summed in double-single (two sums, alternate columns)
+            auto contract = [&](float kh, float kl, int j, int q, float &ah0, float &al0, float &ah1, float &al1) {
+                const float wh = cst[128 + j], wl = cst[256 + j];
+                float pp, pe, sm, se;
+                two_prod(kh, wh, pp, pe);
+                pe = fmaf(kh, wl, fmaf(kl, wh, pe));
+                if (q & 1) {
+                    two_sum(ah1, pp, sm, se);
+                    al1 += se + pe;
+                    ah1 = sm;
+                } else {
+                    two_sum(ah0, pp, sm, se);
+                    al0 += se + pe;
+                    ah0 = sm;
+                }
+            };
             auto group_acc = [&](const uint32_t(&r)[32], int j0) {
                 float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int j = j0 + q;
-                    const float c = __uint_as_float(r[q]);
-                    float kh, kl = 0.f;
+                    float kh, kl;
                     if (KIND == DCD_RBF && cid[j] == rid) {  // the own sample: d^2 = 0
                         kh = 1.f;
-                    } else if (KIND == DCD_RBF) {
-                        float sh, sl, ph, pl, xh, xl;
-                        two_sum(hr, cst[j], sh, sl);
-                        sl += hrl + cst[384 + j];
-                        two_prod(a.two_gl, c, ph, pl);
-                        pl = fmaf(a.two_gl_lo, c, pl);
-                        two_sum(ph, -sh, xh, xl);
-                        xl += pl - sl;
-                        fast_two_sum(xh, xl, xh, xl);
-                        if (xh > 0.f) {  // d^2 >= 0
-                            xh = 0.f;
-                            xl = 0.f;
-                        }
-                        kh = exp2_ds(xh, xl);
-                    } else if (KIND == DCD_LINEAR) {
-                        kh = c;
-                    } else {  // (coef0 + c)^degree by repeated double-single products
-                        float th, tl;
-                        two_sum(a.coef0, c, th, tl);
-                        float rh = th, rl = tl;
-                        for (int e = 1; e < a.degree; ++e) {
-                            float pp, pe;
-                            two_prod(rh, th, pp, pe);
-                            pe = fmaf(rh, tl, fmaf(rl, th, pe));
-                            fast_two_sum(pp, pe, rh, rl);
-                        }
-                        kh = rh;
-                        kl = rl;
-                    }
-                    const float wh = cst[128 + j], wl = cst[256 + j];
-                    float pp, pe, sm, se;
-                    two_prod(kh, wh, pp, pe);
-                    pe = fmaf(kh, wl, fmaf(kl, wh, pe));
-                    if (q & 1) {
-                        two_sum(ah1, pp, sm, se);
-                        al1 += se + pe;
-                        ah1 = sm;
+                        kl = 0.f;
                     } else {
-                        two_sum(ah0, pp, sm, se);
-                        al0 += se + pe;
-                        ah0 = sm;
+                        k_accurate<KIND>(__uint_as_float(r[q]), 0.f, hr, hrl, cst[j], cst[384 + j], a, kh, kl);
+                    }
+                    contract(kh, kl, j, q, ah0, al0, ah1, al1);
+                }
+                cs += ((double)ah0 + (double)al0) + ((double)ah1 + (double)al1);
+            };
+            // the sliced form of one group: the four accumulators' exact integer sums G_g (plane
+            // products with p + q = g) for 16 columns at a time, combined in double-single as
+            // a.b = 2^(e_i + e_j - 12) (G0 + 2^-7 G1 + 2^-14 G2 + 2^-21 G3)
+            auto group_sl = [&](uint32_t tb, int cg, int j0) {
+                float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
+#pragma unroll 1
+                for (int hh = 0; hh < 2; ++hh) {
+                    float G0[16], G1[16], G2[16], G3[16];
+                    const uint32_t ta = tb + (uint32_t)(cg * 32 + hh * 16);
+                    tmem_ld16(ta, G0);
+                    tmem_ld16(ta + (uint32_t)bn, G1);
+                    tmem_ld16(ta + 2u * (uint32_t)bn, G2);
+                    tmem_ld16(ta + 3u * (uint32_t)bn, G3);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int j = j0 + hh * 16 + q;
+                        float kh, kl;
+                        if (KIND == DCD_RBF && cid[j] == rid) {  // the own sample: d^2 = 0
+                            kh = 1.f;
+                            kl = 0.f;
+                        } else {
+                            float th, tl, uh, ul, vh, vl, e1;
+                            two_sum(G2[q] * 0x1p-14f, G3[q] * 0x1p-21f, th, tl);
+                            two_sum(G1[q] * 0x1p-7f, th, uh, e1);
+                            ul = e1 + tl;
+                            two_sum(G0[q], uh, vh, e1);
+                            vl = e1 + ul;
+                            const float scl = rsl * cst[640 + j];  // 2^(e_i + e_j - 12), exact
+                            k_accurate<KIND>(vh * scl, vl * scl, hr, hrl, cst[j], cst[384 + j], a, kh, kl);
+                        }
+                        contract(kh, kl, j, q, ah0, al0, ah1, al1);
                     }
                 }
                 cs += ((double)ah0 + (double)al0) + ((double)ah1 + (double)al1);
             };
-            const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+            const uint32_t buf = acc_it % NACC, aph = (acc_it / NACC) & 1;
             // stage this warp's columns while the accumulator is still being formed
             const int64_t cbase = (int64_t)nc * bn + cg0 * 32;
             for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
@@ -1026,6 +1143,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                     cst[128 + j] = wh;
                     cst[256 + j] = (float)(wv - (double)wh);
                     if (KIND == DCD_RBF) cst[384 + j] = a.col_hl[cbase + j];
+                    if (SL) cst[640 + j] = cbase + j < a.ncols ? a.col_s[cbase + j] : 0.f;
                 } else {
                     cst[128 + j] = a.col_w[cbase + j];
                     if (FP8) cst[256 + j] = a.col_s[cbase + j];
@@ -1039,25 +1157,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             }
             fence_after();
             const uint32_t tb = tmem_base + lane_addr + buf * (uint32_t)bn;
-            uint32_t ra[32], rb[32];
-            if (cg0 < cg1) {
-                tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
-                tmem_ld_wait(ra);
-            }
-            auto any_group = [&](const uint32_t(&r)[32], int j0) {
-                if constexpr (ACC) group_acc(r, j0);
-                else group(r, j0);
-            };
-            for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
-                if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
-                any_group(ra, (cg - cg0) * 32);
-                if (cg + 1 < cg1) {
-                    tmem_ld_wait(rb);
-                    if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
-                    any_group(rb, (cg + 1 - cg0) * 32);
-                    if (cg + 2 < cg1) tmem_ld_wait(ra);
+            if constexpr (SL) {
+                for (int cg = cg0; cg < cg1; ++cg) group_sl(tb, cg, (cg - cg0) * 32);
+            } else {
+                uint32_t ra[32], rb[32];
+                if (cg0 < cg1) {
+                    tmem_ld32_issue(tb + (uint32_t)(cg0 * 32), ra);
+                    tmem_ld_wait(ra);
+                }
+                auto any_group = [&](const uint32_t(&r)[32], int j0) {
+                    if constexpr (ACC) group_acc(r, j0);
+                    else group(r, j0);
+                };
+                for (int cg = cg0; cg < cg1; cg += 2) {  // ra holds group cg
+                    if (cg + 1 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 1) * 32), rb);
+                    any_group(ra, (cg - cg0) * 32);
+                    if (cg + 1 < cg1) {
+                        tmem_ld_wait(rb);
+                        if (cg + 2 < cg1) tmem_ld32_issue(tb + (uint32_t)((cg + 2) * 32), ra);
+                        any_group(rb, (cg + 1 - cg0) * 32);
+                        if (cg + 2 < cg1) tmem_ld_wait(ra);
+                    }
                 }
             }
+            cs += (double)cs_h + (double)cs_l;
             fence_before();
             __syncwarp();
             if (lane == 0) arrive_cl(tempty0 + 8u * buf);
@@ -1148,7 +1271,9 @@ bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
     if (!fn) return false;
     const bool f32 = op.kind == PACK_TF32 || op.kind == PACK_TF32X3, fp8 = op.kind == PACK_FP8;
     const int esz = f32 ? 4 : fp8 ? 1 : 2;
-    const int64_t cols = (op.kind == PACK_BF16X3 || op.kind == PACK_TF32X3) ? 2 * op.n_pad : op.n_pad;
+    const int64_t cols = op.kind == PACK_SLICED                                  ? 4 * op.n_pad
+                         : (op.kind == PACK_BF16X3 || op.kind == PACK_TF32X3) ? 2 * op.n_pad
+                                                                              : op.n_pad;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)op.nrows};
     cuuint64_t strides[1] = {(cuuint64_t)(cols * esz)};
     cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esz), (cuuint32_t)box_rows};
@@ -1264,19 +1389,21 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
                             const TcSplit *split, bool pdl, int max_pairs, const TcAccurate *acc)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
-    // the accurate apply epilogue: split-tf32 operands, FP64 coefficients, RBF terms as hi + lo
-    if (acc && (out != nullptr || Aop.kind != PACK_TF32X3 || !acc->w64 ||
+    // the accurate apply epilogue: split-tf32 or sliced operands, FP64 coefficients, RBF terms as hi + lo
+    const bool sliced = Aop.kind == PACK_SLICED;
+    if (acc && (out != nullptr || (Aop.kind != PACK_TF32X3 && !sliced) || !acc->w64 ||
                 (kp.kind == DCD_RBF && (!acc->row_hl || !acc->col_hl))))
         return cudaErrorInvalidValue;
+    if (sliced && (!acc || !Aop.scale || !Bop.scale || Aop.n_pad > SLICED_N_MAX)) return cudaErrorInvalidValue;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
     if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3 &&
-        Aop.kind != PACK_FP8)
+        Aop.kind != PACK_FP8 && Aop.kind != PACK_SLICED)
         return cudaErrorInvalidValue;
     if (Aop.kind == PACK_FP8 && (!Aop.scale || !Bop.scale)) return cudaErrorInvalidValue;
     const int kb_elems = k_block_elems(Aop.kind);
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
-    if (bn > BN_MAX) bn = BN_MAX;
+    if (bn > (sliced ? SLICED_BN : BN_MAX)) bn = sliced ? SLICED_BN : BN_MAX;
     // store mode (the sampled Gram) has few rows: narrower N-chunks give
     // more work items and spread them over more SMs -- unless it is held to a
     // few CTAs (max_pairs), where wide chunks mean fewer, longer items
@@ -1338,6 +1465,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
             a.late_pairs = split->late_pairs;
             a.late_units = split->late_units;
         }
+        if (sliced) return launch_mode2<MODE_SLICED>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (acc) return launch_mode2<MODE_ACC>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl);

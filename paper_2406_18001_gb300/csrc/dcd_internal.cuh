@@ -107,13 +107,20 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
 // bits).
 // fp8: e4m3 codes (one byte per feature) of the per-row-scaled storage
 // a_i ~ scale_i * q_i; the scales travel beside the packed rows.
-enum PackKind : int { PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4, PACK_FP8 = 5 };
+// sliced: every row scaled by a power of two sc_i = 2^e_i with max |a_ik| < sc_i and cut into 4
+// planes of integers in [-64, 64] (exact in bf16), a_ik ~ sc_i (s0 2^-6 + s1 2^-13 + s2 2^-20 +
+// s3 2^-27); the per-row scales travel beside the rows like FP8 scales.  The products of two
+// such rows are exact integers, and their FP32-accumulated sums stay exact for n_pad <= 1024.
+enum PackKind : int {
+    PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4, PACK_FP8 = 5, PACK_SLICED = 6
+};
+constexpr int64_t SLICED_N_MAX = 1024;  // exact slice-product sums up to this many features
 struct TcOperand {
     const void *rows;     // packed matrix, row-major
     int64_t nrows;
     int64_t n_pad;        // features per half, multiple of the k-block
-    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3 or PACK_FP8
-    const float *scale = nullptr;  // PACK_FP8: per-row scales (padded with zeros like the rows)
+    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3, PACK_FP8 or PACK_SLICED
+    const float *scale = nullptr;  // PACK_FP8, PACK_SLICED: per-row scales (padded with zeros like the rows)
     // the data-matrix row each packed row holds (nrows entries; nullptr: row r holds row r).
     // The RBF kernel of a row with itself is 1: where the ids of a block's row and column
     // are equal the epilogues take d^2 = 0 instead of the expansion, whose cancellation
@@ -128,7 +135,7 @@ __host__ __device__ inline int k_block_elems(int kind)
 
 __host__ __device__ inline int64_t packed_row_bytes(int kind, int64_t n_pad)
 {
-    return kind == PACK_TF32X3                          ? 8 * n_pad
+    return (kind == PACK_TF32X3 || kind == PACK_SLICED) ? 8 * n_pad
            : (kind == PACK_TF32 || kind == PACK_BF16X3) ? 4 * n_pad
            : kind == PACK_FP8                           ? n_pad
                                                         : 2 * n_pad;
@@ -161,12 +168,14 @@ struct TcSplit {
     int late_units = 0;
 };
 inline int64_t tc_split_part_elems(int pairs, int chunks) { return (int64_t)pairs * chunks * 2 * 256; }
-inline int tc_split_chunks(int64_t ncols) { return ncols <= 256 ? 1 : (int)((ncols + 255) / 256); }
-// The accurate apply epilogue (split-tf32 operands only): the RBF exponent and
-// kernel value in double-single arithmetic and the contraction with FP64
-// coefficients w64 (col_w is then unused); row_hl / col_hl are the low parts
-// of the RBF terms from launch_row_terms(..., h_lo) (RBF only).  Columns past
-// ncols read as zero coefficients.
+// N-chunks of a block of ncols columns (capacity: chunks of 128 columns, the narrowest the apply uses)
+inline int tc_split_chunks(int64_t ncols) { return ncols <= 128 ? 1 : (int)((ncols + 127) / 128); }
+// The accurate apply epilogue (PACK_SLICED or PACK_TF32X3 operands): the RBF
+// exponent and kernel value in double-single arithmetic and the contraction
+// with FP64 coefficients w64 (col_w is then unused); row_hl / col_hl are the
+// low parts of the RBF terms from launch_row_terms(..., h_lo) (RBF only).
+// Columns past ncols read as zero coefficients.  On sliced operands the dot
+// products come from the slices' exact integer sums (4 group accumulators).
 struct TcAccurate {
     const double *w64 = nullptr;
     const float *row_hl = nullptr;
@@ -191,14 +200,22 @@ cudaError_t launch_quantize_rows(const void *src, int dtype, int64_t ld, int64_t
                                  int *err, cudaStream_t st);
 cudaError_t launch_label_check(const double *y, int64_t m, int *bad, cudaStream_t st);
 cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cudaStream_t st);
-// h_lo (PACK_TF32X3 only): the term as a pair of floats h + h_lo (FP64 sums), for the accurate epilogue
+// h_lo (PACK_TF32X3, PACK_SLICED): the term as a pair of floats h + h_lo (FP64 sums), for the accurate
+// epilogue; PACK_SLICED takes its per-row scales in `scale`
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *scale = nullptr, float *h_lo = nullptr);
 // with the rows, optionally the per-row values f0 (and f1) of the same
 // indices: d0[j] = f0[idx[j]] (0 for an index outside [0, m))
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
                                void *dst, int *err, cudaStream_t st, const float *f0 = nullptr, float *d0 = nullptr,
-                               const float *f1 = nullptr, float *d1 = nullptr);
+                               const float *f1 = nullptr, float *d1 = nullptr, const float *f2 = nullptr,
+                               float *d2 = nullptr);
+// Sliced rows (PACK_SLICED) of rows `rows` (or the first count) of a dense
+// source, with their power-of-two scales in sc (count floats); an FP8
+// source is dequantised first.  dst rows are 4 planes of n_pad bf16.
+cudaError_t launch_pack_sliced(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                               void *dst, int64_t n_pad, int64_t count, float *sc, int *err, cudaStream_t st,
+                               const float *src_scale = nullptr);
 cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
                              cudaStream_t st);

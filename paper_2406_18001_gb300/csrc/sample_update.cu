@@ -172,6 +172,66 @@ cudaError_t launch_pack_rows(const void *src, int dtype, int64_t ld, int64_t m, 
 // scale = fl32(max|a| / 448), code = e4m3(fl32(a / scale)) with IEEE FP32
 // division; a row of zeros gets scale 0 and zero codes.  An FP8 source is
 // copied with its scale.  Columns n..ldq-1 of the destination are zero.
+// One warp per row: the row's largest magnitude fixes sc = 2^e with
+// max |a| in [2^(e-1), 2^e) (1 for a zero row); u = a / sc in (-1, 1) is cut
+// by round-to-nearest into s0 = rint(64 u) and, from the remainder r in
+// [-1/2, 1/2], s_p = rint(128 r) for p = 1..3 -- integers in [-64, 64], exact
+// in bf16, with u = s0 2^-6 + s1 2^-13 + s2 2^-20 + s3 2^-27 to within 2^-28.
+// Every step is exact in FP64 (power-of-two scalings and differences of
+// numbers within a factor two).  Columns n..n_pad-1 are zero.
+__global__ void pack_sliced_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                   __nv_bfloat16 *dst, int64_t n_pad, int64_t count, float *sc, int *err,
+                                   const float *src_scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= count) return;
+    const int64_t sr = rows ? (int64_t)rows[r] : r;
+    const bool inb = sr >= 0 && sr < m;
+    if (!inb && lane == 0) set_error(err, DEV_BAD_INDEX);
+    const float rsc = (dtype == DCD_FP8E4M3 && inb) ? src_scale[sr] : 0.f;
+    auto val = [&](int64_t c) -> double {
+        if (c >= n || !inb) return 0.0;
+        if (dtype == DCD_F64) return ((const double *)src)[sr * ld + c];
+        if (dtype == DCD_FP8E4M3) return (double)rsc * (double)e4m3_value(((const uint8_t *)src)[sr * ld + c]);
+        return (double)load_as_f32(src, dtype, sr * ld + c);
+    };
+    double mx = 0.0;
+    for (int64_t c = lane; c < n; c += 32) mx = fmax(mx, fabs(val(c)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    else if (!(mx == 0.0) && lane == 0) set_error(err, DEV_BAD_VALUE);
+    if (lane == 0) sc[r] = (float)ldexp(1.0, e);
+    __nv_bfloat16 *d = dst + r * 4 * n_pad;
+    for (int64_t c = lane; c < n_pad; c += 32) {
+        double v = ldexp(val(c), 6 - e);
+        const double s0 = rint(v);
+        v = (v - s0) * 128.0;
+        const double s1 = rint(v);
+        v = (v - s1) * 128.0;
+        const double s2 = rint(v);
+        v = (v - s2) * 128.0;
+        const double s3 = rint(v);
+        d[c] = __double2bfloat16(s0);
+        d[n_pad + c] = __double2bfloat16(s1);
+        d[2 * n_pad + c] = __double2bfloat16(s2);
+        d[3 * n_pad + c] = __double2bfloat16(s3);
+    }
+}
+
+cudaError_t launch_pack_sliced(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                               void *dst, int64_t n_pad, int64_t count, float *sc, int *err, cudaStream_t st,
+                               const float *src_scale)
+{
+    if (count <= 0) return cudaSuccess;
+    if (!sc || n_pad < n || n_pad % 64 || (dtype == DCD_FP8E4M3 && !src_scale)) return cudaErrorInvalidValue;
+    const int64_t blocks = (count * 32 + 255) / 256;
+    pack_sliced_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, (__nv_bfloat16 *)dst, n_pad,
+                                                         count, sc, err, src_scale);
+    return cudaGetLastError();
+}
+
 __global__ void quantize_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n,
                                      const int32_t *rows, const float *src_scale, uint8_t *dst, int64_t ldq,
                                      float *dst_scale, int64_t count, int *err)
@@ -278,6 +338,34 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= m) return;
+    if (kind == PACK_SLICED) {
+        // the slices' own product sums, truncated as the apply truncates them (groups p + q <= 3),
+        // exact in FP64: a.a = sc^2 2^-12 (S0 + 2^-7 S1 + 2^-14 S2 + 2^-21 S3)
+        const __nv_bfloat16 *row = (const __nv_bfloat16 *)packed + r * 4 * n_pad;
+        double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0;
+        for (int64_t c = lane; c < n_pad; c += 32) {
+            const double a0 = __bfloat162float(row[c]), a1 = __bfloat162float(row[n_pad + c]);
+            const double a2 = __bfloat162float(row[2 * n_pad + c]), a3 = __bfloat162float(row[3 * n_pad + c]);
+            S0 += a0 * a0;
+            S1 += 2.0 * a0 * a1;
+            S2 += 2.0 * a0 * a2 + a1 * a1;
+            S3 += 2.0 * (a0 * a3 + a1 * a2);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            S0 += __shfl_xor_sync(0xffffffffu, S0, o);
+            S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+            S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+            S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+        }
+        if (lane == 0) {
+            const double sc = rscale[r];
+            const double v = scale * (sc * sc) * 0x1p-12 * (S0 + 0x1p-7 * S1 + 0x1p-14 * S2 + 0x1p-21 * S3);
+            const float vh = (float)v;
+            h[r] = vh;
+            if (h_lo) h_lo[r] = (float)(v - (double)vh);
+        }
+        return;
+    }
     if (kind == PACK_TF32X3) {
         // split tf32: the products the three MMAs form, hi.hi + 2 hi.lo, each exact in FP64 (24-bit
         // factors) and summed in FP64; the term is stored as a pair of floats hi + lo (h_lo given) for
@@ -324,8 +412,8 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *rscale, float *h_lo)
 {
-    if (kind == PACK_FP8 && !rscale) return cudaErrorInvalidValue;
-    if (h_lo && kind != PACK_TF32X3) return cudaErrorInvalidValue;
+    if ((kind == PACK_FP8 || kind == PACK_SLICED) && !rscale) return cudaErrorInvalidValue;
+    if (h_lo && kind != PACK_TF32X3 && kind != PACK_SLICED) return cudaErrorInvalidValue;
     if (m <= 0) return cudaSuccess;
     double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;
     int64_t blocks = (m * 32 + 255) / 256;
@@ -338,7 +426,8 @@ cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_
 // given.  Indices outside [0, m) give a zero row (and zero values) and set
 // DEV_BAD_INDEX.
 __global__ void gather_rows_kernel(const uint4 *src, int64_t row_vec, const int32_t *idx, int64_t count, int64_t m,
-                                   uint4 *dst, int *err, const float *f0, float *d0, const float *f1, float *d1)
+                                   uint4 *dst, int *err, const float *f0, float *d0, const float *f1, float *d1,
+                                   const float *f2, float *d2)
 {
     const int64_t total = count * row_vec;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -354,21 +443,22 @@ __global__ void gather_rows_kernel(const uint4 *src, int64_t row_vec, const int3
         if (c == 0) {
             if (d0) d0[j] = bad ? 0.f : f0[r];
             if (d1) d1[j] = bad ? 0.f : f1[r];
+            if (d2) d2[j] = bad ? 0.f : f2[r];
         }
     }
 }
 
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t count, int64_t m,
                                void *dst, int *err, cudaStream_t st, const float *f0, float *d0, const float *f1,
-                               float *d1)
+                               float *d1, const float *f2, float *d2)
 {
     if (count <= 0) return cudaSuccess;
-    if ((d0 && !f0) || (d1 && !f1)) return cudaErrorInvalidValue;
+    if ((d0 && !f0) || (d1 && !f1) || (d2 && !f2)) return cudaErrorInvalidValue;
     const int64_t row_vec = row_bytes / 16;
     int64_t blocks = (count * row_vec + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint4 *)src, row_vec, idx, count, m, (uint4 *)dst,
-                                                         err, f0, d0, f1, d1);
+                                                         err, f0, d0, f1, d1, f2, d2);
     return cudaGetLastError();
 }
 

@@ -200,8 +200,9 @@ struct Solver {
     TcSplit tsplit;  // scratch of the balanced tensor-core apply
     void *Asr = nullptr;
     float *col_hr = nullptr;
-    // the accurate epilogue of the recomputed gradient: low parts of the RBF terms
-    float *row_hlr = nullptr, *col_hlr = nullptr;
+    // the accurate epilogue of the recomputed gradient: low parts of the RBF terms, and the
+    // gathered columns' power-of-two scales of the sliced operand
+    float *row_hlr = nullptr, *col_hlr = nullptr, *col_sr = nullptr;
     // CSR data matrix: the CUDA-core SpMM block (FP32, or FP64 in the FP64 mode)
     bool csr = false;
     CsrOperand ca;
@@ -279,8 +280,12 @@ struct Solver {
         const int64_t n_pad = (n + kb_elems - 1) / kb_elems * kb_elems;
         const size_t row_bytes = tcd ? (size_t)packed_row_bytes(pack_kind(o.prec), n_pad) : 8 * (size_t)n;
         const bool need_pack = !csr && (tc || A->dtype != DCD_F64 || host);
-        const bool ref_op = tcd && (o.flags & DCD_FLAG_REFRESH) && o.prec != DCD_PREC_TF32X3;
-        const bool acc_ref = tcd && (o.flags & DCD_FLAG_REFRESH);  // recomputed gradient: accurate epilogue
+        // the recomputed gradient (DCD_FLAG_REFRESH): sliced operand (exact products) for n up to
+        // SLICED_N_MAX, split tf32 beyond; accurate epilogue either way
+        const bool acc_ref = tcd && (o.flags & DCD_FLAG_REFRESH);
+        const bool sliced_ref = acc_ref && (n + 63) / 64 * 64 <= SLICED_N_MAX;
+        const bool ref_op = acc_ref && (sliced_ref || o.prec != DCD_PREC_TF32X3);
+        const int kind_r = sliced_ref ? PACK_SLICED : PACK_TF32X3;
         const bool fp8 = tcd && pack_kind(o.prec) == PACK_FP8;
         const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
         // the look-ahead needs a stream of its own to fork from, graphs allowed, no per-phase
@@ -289,8 +294,8 @@ struct Solver {
                             !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                             st != cudaStreamLegacy && st != cudaStreamPerThread &&
                             recur_cluster_size((int)o.s, o.b, 2) > 0;
-        const int64_t n_pad_r = (n + 31) / 32 * 32;
-        const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(PACK_TF32X3, n_pad_r) : 0;
+        const int64_t n_pad_r = sliced_ref ? (n + 63) / 64 * 64 : (n + 31) / 32 * 32;
+        const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(kind_r, n_pad_r) : 0;
 
         int split_pairs = 0;
         const int split_chunks = tc_split_chunks(std::max<int64_t>(sb, 1));
@@ -328,6 +333,8 @@ struct Solver {
             float *chr = (float *)ar.take(ref_op ? sizeof(float) * col_pad : 0);
             float *rhl = (float *)ar.take(acc_ref ? sizeof(float) * m : 0);
             float *chl = (float *)ar.take(acc_ref ? sizeof(float) * col_pad : 0);
+            float *rscr = (float *)ar.take(sliced_ref ? sizeof(float) * m : 0);
+            float *cscr = (float *)ar.take(sliced_ref ? sizeof(float) * col_pad : 0);
             int32_t *sidx = (int32_t *)ar.take(sizeof(int32_t) * col_pad);
             void *kss = ar.take((size_t)sb * sb * (tc ? 4 : 8));
             double *dl = (double *)ar.take(sizeof(double) * col_pad);
@@ -391,6 +398,8 @@ struct Solver {
             col_hr = chr;
             row_hlr = rhl;
             col_hlr = chl;
+            opr.row_s = rscr;
+            col_sr = cscr;
             S = sidx;
             Kss = kss;
             ldk = sb;
@@ -493,10 +502,16 @@ struct Solver {
             DCD_TRY(launch_row_terms(op.packed, op.kind, n_pad, m, kp, op.row_h, st, op.row_s));
             if (ref_op) {
                 opr.n_pad = n_pad_r;
-                opr.kind = PACK_TF32X3;
-                DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, opr.packed, opr.kind, n_pad_r, m, err,
-                                         st, src_scale));
-                DCD_TRY(launch_row_terms(opr.packed, opr.kind, n_pad_r, m, kp, opr.row_h, st));
+                opr.kind = kind_r;
+                if (sliced_ref) {
+                    DCD_TRY(launch_pack_sliced(vals, A->dtype, A->ld, m, n, nullptr, opr.packed, n_pad_r, m, opr.row_s,
+                                               err, st, src_scale));
+                    DCD_TRY(cudaMemsetAsync(col_sr, 0, sizeof(float) * col_pad, st));
+                } else {
+                    opr.row_s = nullptr;
+                    DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, opr.packed, opr.kind, n_pad_r, m,
+                                             err, st, src_scale));
+                }
                 DCD_TRY(cudaMemsetAsync(col_hr, 0, sizeof(float) * col_pad, st));
             } else {
                 opr = op;
@@ -504,8 +519,9 @@ struct Solver {
                 col_hr = col_h;
                 ref_shared = true;
             }
-            if (acc_ref) {  // the terms again, as hi + lo pairs (the hi parts are unchanged)
-                DCD_TRY(launch_row_terms(opr.packed, opr.kind, opr.n_pad, m, kp, opr.row_h, st, nullptr, row_hlr));
+            if (acc_ref) {  // the RBF terms of the recomputed gradient's operand, as hi + lo pairs
+                DCD_TRY(launch_row_terms(opr.packed, opr.kind, opr.n_pad, m, kp, opr.row_h, st,
+                                         opr.kind == PACK_SLICED ? opr.row_s : nullptr, row_hlr));
                 DCD_TRY(cudaMemsetAsync(col_hlr, 0, sizeof(float) * col_pad, st));
             }
         } else if (need_pack) {
@@ -658,12 +674,14 @@ struct Solver {
             return cuda_status(csr_apply(ncols, rs));
         }
         if (tc && ref && row_hlr) {
-            // the recomputed gradient: split-tf32 products, accurate epilogue, FP64 coefficients
+            // the recomputed gradient: sliced (or split-tf32) products, accurate epilogue, FP64 coefficients
+            const bool sl = opr.kind == PACK_SLICED;
             cudaError_t e = launch_gather_rows(opr.packed, packed_row_bytes(opr.kind, opr.n_pad), S, ncols, m, Asr,
-                                               err, st, opr.row_h, col_hr, row_hlr, col_hlr);
+                                               err, st, opr.row_h, col_hr, row_hlr, col_hlr, sl ? opr.row_s : nullptr,
+                                               sl ? col_sr : nullptr);
             if (e != cudaSuccess) return cuda_status(e);
-            TcOperand Aop{opr.packed, m, opr.n_pad, opr.kind, nullptr};
-            TcOperand Bop{Asr, ncols, opr.n_pad, opr.kind, nullptr, S};
+            TcOperand Aop{opr.packed, m, opr.n_pad, opr.kind, sl ? opr.row_s : nullptr};
+            TcOperand Bop{Asr, ncols, opr.n_pad, opr.kind, sl ? col_sr : nullptr, S};
             TcAccurate acc;
             acc.w64 = w64;
             acc.row_hl = row_hlr;
@@ -1132,7 +1150,7 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem, bool csr)
     if (o->b > B_MAX || o->b > m) return DCD_EINVAL;
     if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
-    if (o->prec == DCD_PREC_TF32X3A) return DCD_EUNSUPPORTED;  // an apply-only precision
+    if (o->prec == DCD_PREC_REFRESH) return DCD_EUNSUPPORTED;  // an apply-only precision
     if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
     if (o->prec == DCD_PREC_FP8 && csr) return DCD_EUNSUPPORTED;  // the CSR block has no fp8 form
     if (is_tc(o->prec) && !csr && !tc_available()) return DCD_EUNSUPPORTED;  // CSR: CUDA cores
@@ -1326,7 +1344,7 @@ dcd_status component_check(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     dcd_status s = validate_dense(A);
     if (s != DCD_OK) return s;
     if ((s = validate_kernel(k)) != DCD_OK) return s;
-    if (prec == DCD_PREC_TF32X3A) {  // the accurate epilogue: dense apply form only
+    if (prec == DCD_PREC_REFRESH) {  // the accurate epilogue: dense apply form only
         if (!apply || A->fmt == DCD_CSR || A->dtype == DCD_FP8E4M3) return DCD_EUNSUPPORTED;
         return tc_available() ? DCD_OK : DCD_EUNSUPPORTED;
     }
@@ -1412,7 +1430,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     if (A->fmt == DCD_CSR) return component_block_csr(A, kp, prec, rows, nrows, cols, ncols, w, rs, g, out, ldo, st);
     ComponentBufs cb;
     cb.st = st;
-    if (!is_tc(prec) && prec != DCD_PREC_TF32X3A) {
+    if (!is_tc(prec) && prec != DCD_PREC_REFRESH) {
         const bool pack = A->dtype != DCD_F64;
         size_t cur = 0;
         size_t oe = place(cur, 256);
@@ -1434,8 +1452,9 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
                                       ldo, err, st));
         return finish_component(err, st);
     }
-    const bool accurate = prec == DCD_PREC_TF32X3A;
-    const int pk = accurate ? PACK_TF32X3 : pack_kind(prec);
+    const bool accurate = prec == DCD_PREC_REFRESH;
+    const bool sliced = accurate && (A->n + 63) / 64 * 64 <= SLICED_N_MAX;
+    const int pk = sliced ? PACK_SLICED : accurate ? PACK_TF32X3 : pack_kind(prec);
     const int kb = k_block_elems(pk);
     const int64_t n_pad = (A->n + kb - 1) / kb * kb;
     const size_t rb = (size_t)packed_row_bytes(pk, n_pad);
@@ -1448,8 +1467,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     size_t och = place(cur, sizeof(float) * cpad);
     size_t ocw = place(cur, sizeof(float) * cpad);
     const bool fp8 = pk == PACK_FP8;
-    size_t ors = place(cur, fp8 ? sizeof(float) * nrows : 0);
-    size_t ocs = place(cur, fp8 ? sizeof(float) * cpad : 0);
+    size_t ors = place(cur, (fp8 || sliced) ? sizeof(float) * nrows : 0);
+    size_t ocs = place(cur, (fp8 || sliced) ? sizeof(float) * cpad : 0);
     size_t orl = place(cur, accurate ? sizeof(float) * nrows : 0);
     size_t ocl = place(cur, accurate ? sizeof(float) * cpad : 0);
     // the apply form's balanced split over CTA pairs
@@ -1468,7 +1487,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     int *err = (int *)(base + oe);
     void *pa = base + oa, *pb = base + ob;
     float *rh = (float *)(base + orh), *ch = (float *)(base + och), *cw = (float *)(base + ocw);
-    float *rsa = fp8 ? (float *)(base + ors) : nullptr, *rsb = fp8 ? (float *)(base + ocs) : nullptr;
+    float *rsa = (fp8 || sliced) ? (float *)(base + ors) : nullptr;
+    float *rsb = (fp8 || sliced) ? (float *)(base + ocs) : nullptr;
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
     DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
@@ -1477,7 +1497,13 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         sp.cnt = (unsigned *)(base + osc);
         DCD_TRY(cudaMemsetAsync(sp.cnt, 0, sizeof(unsigned) * 2 * sp.pairs, st));
     }
-    if (fp8) {
+    if (sliced) {
+        DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
+        DCD_TRY(launch_pack_sliced(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, n_pad, nrows, rsa, err, st,
+                                   A->row_scale));
+        DCD_TRY(launch_pack_sliced(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, n_pad, ncols, rsb, err, st,
+                                   A->row_scale));
+    } else if (fp8) {
         DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
         DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, A->row_scale, (uint8_t *)pa, n_pad,
                                      rsa, nrows, err, st));

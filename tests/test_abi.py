@@ -145,13 +145,13 @@ def test_host_validation_rejects_bad_arguments_without_gpu():
     assert L.dcd_svm_solve(C.byref(Am), b._ptr(y), C.byref(k), 1, 1.0, C.byref(o5), b._ptr(al), None, None,
                            None) == b.EUNSUPPORTED
     # the accurate split-tf32 epilogue is an apply-only precision
-    o6 = b._opts(1, 1, 10, 0, 0, 0.0, 0, "tf32x3a", 0)
+    o6 = b._opts(1, 1, 10, 0, 0, 0.0, 0, "refresh", 0)
     assert L.bdcd_krr_solve(C.byref(Am), b._ptr(y), C.byref(k), 1.0, C.byref(o6), b._ptr(al), None, None,
                             None) == b.EUNSUPPORTED
     cols = np.zeros(2, dtype=np.int32)
     out = np.zeros(8)
     for fn in (L.dcd_kernel_block, L.dcd_kernel_block_static):
-        assert fn(C.byref(Am), C.byref(k), b.PREC_TF32X3A, None, 4, b._ptr(cols), 2, b._ptr(out), 2,
+        assert fn(C.byref(Am), C.byref(k), b.PREC_REFRESH, None, 4, b._ptr(cols), 2, b._ptr(out), 2,
                   None) == b.EUNSUPPORTED
     # sampler argument checks
     assert L.dcd_sample_indices(2, 0, 10, 1, 0, 5, None, None) == b.EINVAL
