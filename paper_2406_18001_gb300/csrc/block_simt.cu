@@ -153,6 +153,54 @@ cudaError_t launch_rn(int rn, int64_t grid, const double *A, int64_t lda, int64_
     return cudaGetLastError();
 }
 
+// Small blocks (few rows, at most 32 columns): one thread per (row, column)
+// entry, so that the FP64 work (GB300 issues ~1.6 FP64 lane operations per
+// clock per SM) spreads over every SM instead of filling a few 64 x 16 tiles.
+// Each entry's dot product (or squared distance) runs over k = 0..n-1 with the
+// operations of block_simt_f64_kernel, so both kernels produce the same bits.
+// A warp holds 32 / CW rows x CW columns (CW a power of two >= the columns);
+// the apply sums a row's CW terms by a fixed butterfly and lane 0 of the row's
+// group adds rs * sum to g.
+template <bool STORE, bool RBF>
+__global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
+                                                              int64_t n, KernelParams kp, const int32_t *rows,
+                                                              int64_t nrows, const int32_t *cols, int64_t ncols,
+                                                              int cw, const double *__restrict__ w,
+                                                              const double *__restrict__ rs, double *g, double *out,
+                                                              int64_t ldo, int *err)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = (int)(t % cw);
+    const int64_t r = t / cw;
+    const bool ok = r < nrows && c < ncols;
+    double kv = 0.0;
+    if (ok) {
+        const int64_t ri = rows ? (int64_t)rows[r] : r, ci = cols[c];
+        if (ri >= 0 && ri < m && ci >= 0 && ci < m) {
+            const double *a = A + ri * lda, *b = A + ci * lda;
+            double acc = 0.0;
+            for (int64_t k = 0; k < n; ++k) {
+                if (RBF) {
+                    const double d = a[k] - b[k];
+                    acc = fma(d, d, acc);
+                } else {
+                    acc = fma(a[k], b[k], acc);
+                }
+            }
+            kv = kfun_f64(kp, acc);
+        } else {
+            set_error(err, DEV_BAD_INDEX);
+        }
+    }
+    if (STORE) {
+        if (ok) out[r * ldo + c] = kv;
+        return;
+    }
+    double part = ok ? kv * w[c] : 0.0;
+    for (int o = 1; o < cw; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (c == 0 && r < nrows) g[r] += (rs ? rs[r] : 1.0) * part;
+}
+
 }  // namespace
 
 cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
@@ -166,6 +214,26 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ncols <= 32 && tiles < 2 * (int64_t)sms) {  // too few tiles to occupy the GPU: an entry per thread
+        int cw = 1;
+        while (cw < ncols) cw <<= 1;
+        const int64_t threads = nrows * cw;
+        const unsigned blocks = (unsigned)((threads + 127) / 128);
+        const bool store = (out != nullptr), rbf = (kp.kind == DCD_RBF);
+        if (store && rbf)
+            block_small_f64_kernel<true, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols, cw,
+                                                                      w, rs, g, out, ldo, err);
+        else if (store)
+            block_small_f64_kernel<true, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                       cw, w, rs, g, out, ldo, err);
+        else if (rbf)
+            block_small_f64_kernel<false, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                       cw, w, rs, g, out, ldo, err);
+        else
+            block_small_f64_kernel<false, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
+                                                                        cw, w, rs, g, out, ldo, err);
+        return cudaGetLastError();
+    }
     int64_t grid = tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8;
     const bool store = (out != nullptr);
     const bool rbf = (kp.kind == DCD_RBF);
