@@ -115,6 +115,13 @@ typedef enum {
 #define DCD_FLAG_HOST_IO 0x2      /* A.values/row_ptr/col_idx, y, alpha, grad are host memory */
 #define DCD_FLAG_PHASE_TIMERS 0x4 /* fill the per-phase times of dcd_stats (adds one sync per step) */
 #define DCD_FLAG_NO_GRAPH 0x8     /* launch every kernel directly instead of replaying CUDA graphs */
+#define DCD_FLAG_LITERAL 0x20     /* run every outer step in the order Algorithms 2 and 4 print: the m x sb
+                                     block U_k / Q_k is stored in device memory, U_j^T alpha_sk is formed
+                                     from it and the Gram is its rows at the sample (G_k = V_k^T U_k); no
+                                     gradient is cached between steps (grad, when given, is recomputed at
+                                     the end).  The verification and byte-comparison form of the fused
+                                     step: it moves the m x sb block through memory twice.  Dense data
+                                     matrices only; requires tol = 0 (else DCD_EINVAL) */
 #define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
                                      recompute the gradient from alpha by full kernel passes (tensor-core
                                      modes: DCD_PREC_REFRESH; FP64 mode: FP64) and accept convergence only

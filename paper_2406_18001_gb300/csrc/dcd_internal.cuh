@@ -221,6 +221,15 @@ cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, 
                              cudaStream_t st);
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,
                           double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st);
+// The literal-order step's middle (Algorithms 2 and 4 as printed): from the stored
+// block Q (m x ncols, FP64 or FP32, leading dimension ldq) and alpha, the gradient
+// values of the step's coordinates written at their positions in g (K-SVM:
+// y_i (U^T alpha)_p - 1 + diag alpha_i; K-RR: (U^T alpha)_p / lambda + diag alpha_i - y_i),
+// and the Gram Kss = rows S of Q.  partials: max_blocks * ncols doubles.
+cudaError_t launch_literal_terms(const void *Q, int q_f64, int64_t ldq, int64_t m, int64_t ncols, const int32_t *S,
+                                 int problem, const double *y, const double *alpha, double inv_lambda, double diag,
+                                 double *partials, int64_t max_blocks, double *g, void *Kss, int64_t ldk,
+                                 cudaStream_t st);
 cudaError_t launch_check(int problem, const double *g, const double *alpha, const double *y, int64_t m,
                          double C, int loss, double *partials, double *result, cudaStream_t st);
 cudaError_t launch_nnz_count(const double *alpha, int64_t m, int *count, cudaStream_t st);

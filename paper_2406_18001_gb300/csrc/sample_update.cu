@@ -232,6 +232,81 @@ cudaError_t launch_pack_sliced(const void *src, int dtype, int64_t ld, int64_t m
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ literal-order step --
+// The paper's printed order (Algorithms 2 and 4) keeps the m x sb block U_k /
+// Q_k in memory and forms U_j^T alpha_sk from it.  literal_partial_kernel:
+// block b sums rows [b R, (b+1) R) of (y_i) Q[i][c] alpha_i for every column
+// c (consecutive threads read consecutive columns of a row), in row order.
+template <typename QT>
+__global__ void literal_partial_kernel(const QT *Q, int64_t ldq, int64_t m, int64_t ncols, const double *alpha,
+                                       const double *y, int64_t rows_per_block, double *partials)
+{
+    const int64_t r0 = blockIdx.x * rows_per_block, r1 = min(m, r0 + rows_per_block);
+    for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const double a = y ? y[i] * alpha[i] : alpha[i];
+            acc = fma((double)Q[i * ldq + c], a, acc);
+        }
+        partials[blockIdx.x * ncols + c] = acc;
+    }
+}
+
+// u_p = sum of the partials in block order, then the gradient value of the
+// step's coordinate i = S[p] written at position i of a full-length array g
+// (repeats write the same value):
+//   K-SVM: g_i = y_i u_p - 1 + omega alpha_i        (u = U_k^T alpha)
+//   K-RR:  g_i = u_p / lambda + m alpha_i - y_i
+__global__ void literal_grad_kernel(const double *partials, int64_t nblk, int64_t ncols, const int32_t *S,
+                                    int problem, const double *y, const double *alpha, double inv_lambda,
+                                    double diag, double *g)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= ncols) return;
+    double u = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) u += partials[b * ncols + p];
+    const int32_t i = S[p];
+    g[i] = problem == 0 ? fma(y[i], u, -1.0) + diag * alpha[i] : u * inv_lambda + diag * alpha[i] - y[i];
+}
+
+// G_k = V_k^T U_k: row r of the Gram is row S[r] of the stored block
+template <typename QT>
+__global__ void literal_gram_kernel(const QT *Q, int64_t ldq, const int32_t *S, int64_t ncols, QT *Kss,
+                                    int64_t ldk)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ncols * ncols) return;
+    const int64_t r = e / ncols, c = e - r * ncols;
+    Kss[r * ldk + c] = Q[(int64_t)S[r] * ldq + c];
+}
+
+cudaError_t launch_literal_terms(const void *Q, int q_f64, int64_t ldq, int64_t m, int64_t ncols, const int32_t *S,
+                                 int problem, const double *y, const double *alpha, double inv_lambda, double diag,
+                                 double *partials, int64_t max_blocks, double *g, void *Kss, int64_t ldk,
+                                 cudaStream_t st)
+{
+    if (ncols <= 0) return cudaSuccess;
+    int64_t nblk = max_blocks < 1 ? 1 : max_blocks;
+    const int64_t rpb = (m + nblk - 1) / nblk;
+    nblk = (m + rpb - 1) / rpb;
+    const int thr = ncols >= 256 ? 256 : (int)((ncols + 31) / 32 * 32);
+    const double *ys = problem == 0 ? y : nullptr;
+    if (q_f64)
+        literal_partial_kernel<double><<<(unsigned)nblk, thr, 0, st>>>((const double *)Q, ldq, m, ncols, alpha, ys,
+                                                                     rpb, partials);
+    else
+        literal_partial_kernel<float><<<(unsigned)nblk, thr, 0, st>>>((const float *)Q, ldq, m, ncols, alpha, ys, rpb,
+                                                                    partials);
+    literal_grad_kernel<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(partials, nblk, ncols, S, problem, y, alpha,
+                                                                       inv_lambda, diag, g);
+    const unsigned gb = (unsigned)((ncols * ncols + 255) / 256);
+    if (q_f64)
+        literal_gram_kernel<double><<<gb, 256, 0, st>>>((const double *)Q, ldq, S, ncols, (double *)Kss, ldk);
+    else
+        literal_gram_kernel<float><<<gb, 256, 0, st>>>((const float *)Q, ldq, S, ncols, (float *)Kss, ldk);
+    return cudaGetLastError();
+}
+
 __global__ void quantize_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n,
                                      const int32_t *rows, const float *src_scale, uint8_t *dst, int64_t ldq,
                                      float *dst_scale, int64_t count, int *err)

@@ -200,6 +200,12 @@ struct Solver {
     TcSplit tsplit;  // scratch of the balanced tensor-core apply
     void *Asr = nullptr;
     float *col_hr = nullptr;
+    // literal-order steps (DCD_FLAG_LITERAL): the stored block, the U^T alpha partial sums and
+    // the step's gradient values (at their positions)
+    bool literal = false;
+    void *Qbuf = nullptr;
+    double *lit_part = nullptr, *lit_g = nullptr;
+    int64_t lit_blocks = 0;
     // the accurate epilogue of the recomputed gradient: low parts of the RBF terms, and the
     // gathered columns' power-of-two scales of the sliced operand
     float *row_hlr = nullptr, *col_hlr = nullptr, *col_sr = nullptr;
@@ -290,7 +296,9 @@ struct Solver {
         const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
         // the look-ahead needs a stream of its own to fork from, graphs allowed, no per-phase
         // timers, and a full step that fits one cluster recurrence
-        const bool la_pos = !t_no_lookahead && problem == 1 && tcd &&
+        literal = (o.flags & DCD_FLAG_LITERAL) != 0;
+        lit_blocks = literal ? std::min<int64_t>(std::max<int64_t>(1, (m + 255) / 256), 1024) : 0;
+        const bool la_pos = !t_no_lookahead && problem == 1 && tcd && !literal &&
                             !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                             st != cudaStreamLegacy && st != cudaStreamPerThread &&
                             recur_cluster_size((int)o.s, o.b, 2) > 0;
@@ -357,6 +365,9 @@ struct Solver {
             double *rs = (double *)ar.take(sizeof(double) * 4);
             int64_t ichunk = std::min<int64_t>(m, SB_MAX);
             int32_t *io = (int32_t *)ar.take(sizeof(int32_t) * ichunk);
+            void *qb = ar.take(literal ? (size_t)m * sb * (tc ? 4 : 8) : 0, 1024);
+            double *lpart = (double *)ar.take(literal ? sizeof(double) * lit_blocks * col_pad : 0);
+            double *lg = (double *)ar.take(literal ? sizeof(double) * m : 0);
             if (pass == 0) {
                 cudaError_t e = cudaMallocAsync(&ws, ar.used + 1024, st);
                 if (e != cudaSuccess) return cuda_status(e);
@@ -412,6 +423,9 @@ struct Solver {
             partials = pt;
             result = rs;
             iota = io;
+            Qbuf = qb;
+            lit_part = lpart;
+            lit_g = lg;
             sbuf[0].S = sidx;
             sbuf[0].As = as;
             sbuf[0].col_h = ch;
@@ -1006,8 +1020,53 @@ struct Solver {
         return k;
     }
 
+    // One outer step in the printed order of Algorithms 2 / 4: Q_k = K(A, A_S) stored (m x ncols),
+    // the step's gradient values from Q_k^T alpha, the Gram from the rows of Q_k at S, the
+    // recurrence, alpha_S += delta.  The cached gradient is not used.
+    dcd_status literal_step(int64_t cnt, EventTimer &tm)
+    {
+        const int64_t ncols = cnt * o.b;
+        tm.start();
+        DCD_TRY(launch_sample(problem, o.seed, ctr, 0, m, o.b, cnt, S, err, st));
+        DCD_TRY(gather(ncols));
+        tm.stop(stats.ms_sample);
+        tm.start();
+        if (tc) {
+            TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
+            TcOperand Bop{As, ncols, op.n_pad, op.kind, col_s, S};
+            DCD_TRY(launch_block_tc(Aop, Bop, kp, op.row_h, col_h, nullptr, nullptr, nullptr, (float *)Qbuf, sb, m,
+                                    ncols, err, st));
+        } else {
+            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, nullptr, nullptr, nullptr,
+                                          (double *)Qbuf, sb, err, st));
+        }
+        tm.stop(stats.ms_block);
+        tm.start();
+        DCD_TRY(launch_literal_terms(Qbuf, tc ? 0 : 1, sb, m, ncols, S, problem, y, alpha, 1.0 / lambda, diag,
+                                     lit_part, lit_blocks, lit_g, Kss, ldk, st));
+        tm.stop(stats.ms_gram);
+        tm.start();
+        FusedUpdate fu;
+        fu.alpha = alpha;
+        fu.ctr = ctr;
+        fu.ctr_advance = (uint64_t)cnt;
+        if (problem == 0)
+            DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, lit_g, omega, nu, delta, w64,
+                                     tc ? col_w : nullptr, err, st));
+        else
+            DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, lit_g, tc ? 1 : 2, Lbuf,
+                                      delta, w64, tc ? col_w : nullptr, &fu, err, st));
+        tm.stop(stats.ms_recur);
+        tm.start();
+        if (!fu.done) DCD_TRY(launch_update(S, delta, ncols, diag, alpha, lit_g, ctr, (uint64_t)cnt, m, err, st));
+        tm.stop(stats.ms_update);
+        tm.flush();
+        return DCD_OK;
+    }
+
     dcd_status enqueue_step(int64_t cnt, EventTimer &tm)
     {
+        if (literal) return literal_step(cnt, tm);
         const int64_t ncols = cnt * o.b;
         const double *rs = problem == 0 ? y : nullptr;
         tm.start();
@@ -1070,6 +1129,11 @@ struct Solver {
                 tm.flush();
                 if (s0 != DCD_OK) break;
             }
+        }
+        // the literal order keeps no gradient between steps: recompute it from alpha
+        if (s0 == DCD_OK && literal) {
+            s0 = cuda_status(launch_init_grad(problem, y, alpha, diag, m, g, st));
+            if (s0 == DCD_OK) s0 = full_pass();
         }
         // the metric is measured at check points and when the budget ends;
         // an intermediate dcd_plan_run without a tolerance leaves it NaN
@@ -1151,6 +1215,7 @@ dcd_status validate_opts(const dcd_opts *o, int64_t m, int problem, bool csr)
     if ((int64_t)o->s * o->b > SB_MAX) return DCD_EINVAL;
     if (!(std::isfinite(o->tol) && o->tol >= 0.0) || o->check_every < 0) return DCD_EINVAL;
     if (o->prec == DCD_PREC_REFRESH) return DCD_EUNSUPPORTED;  // an apply-only precision
+    if ((o->flags & DCD_FLAG_LITERAL) && (csr || o->tol != 0.0)) return DCD_EINVAL;
     if (o->prec != DCD_PREC_FP64 && !is_tc(o->prec)) return DCD_EINVAL;
     if (o->prec == DCD_PREC_FP8 && csr) return DCD_EUNSUPPORTED;  // the CSR block has no fp8 form
     if (is_tc(o->prec) && !csr && !tc_available()) return DCD_EUNSUPPORTED;  // CSR: CUDA cores
