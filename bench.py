@@ -488,6 +488,34 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
         e2e = {"value": Hh * args.b / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps, "steps": args.steps, "wall_s": dt}
 
+    # the literal order (Algorithms 2 / 4 as printed: the m x sb block stored, U^T alpha read back from
+    # it) beside the fused step: time per outer step (one-stream steps, L2 flushed) and bytes moved
+    lit = None
+    if args.literal_steps > 0:
+        def one_stream_ms(flags):
+            pl = B.Plan(1, A, y, k, args.lam, args.b, args.s, (args.literal_steps + 4) * args.s, seed=rank,
+                        prec=args.prec, flags=flags)
+            pl.run(2)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.literal_steps)]
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                pl.enqueue(1)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            pl.close()
+            return sorted(a.elapsed_time(b_) for a, b_ in evs)[len(evs) // 2]
+        esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
+        qsz = 8 if args.prec == "fp64" else 4
+        sb = args.s * args.b
+        lit = {"ms_per_step_median": one_stream_ms(B.FLAG_LITERAL | B.FLAG_NO_GRAPH),
+               "fused_ms_per_step_median_one_stream": one_stream_ms(B.FLAG_NO_GRAPH),
+               "bytes_per_step": args.m * args.n * esz + 2 * args.m * sb * qsz + args.m * 16,
+               "fused_bytes_per_step": args.m * args.n * esz + args.m * 24,
+               "bytes_rule": "literal: A once + the m x sb block written and read back + alpha, g; fused: A once + g, "
+                             "alpha, row terms"}
     ttt = None
     if not args.no_ttt:
         ttt = time_to_tol(args, torch, B, A, y, k, rank)
@@ -511,11 +539,136 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
                "step_ms": {"min": ms_steps[0], "median": ms_steps[len(ms_steps) // 2], "max": ms_steps[-1]},
                "phase_ms": phase,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary(), "time_to_tol": ttt, "error_vs_oracle": herr}
+               "clocks": clk.summary(), "time_to_tol": ttt, "error_vs_oracle": herr, "literal_order": lit}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- K-SVM -----
+WORKLOAD_SVM = ("K-SVM-L1 DCD on two Gaussian blobs: m=2000, n=64 (means +-0.5 per coordinate, unit variance), "
+                "labels +-1, RBF sigma=8 (gamma=1/128), C=1, FP64 kernel block")
+
+
+def svm_true_gap(oracle, A64, y, ko, loss, C_, alpha):
+    ob = oracle.svm_objectives(A64, y, ko, loss, C_, alpha)
+    return (ob["primal"] - ob["dual"]) / abs(ob["primal"])
+
+
+def svm_time_to_gap(args, torch, B, A, y, k, A64, seed):
+    """Time to relative duality gap (P - D) / |P| <= tol (Section 5.1 reading:
+    P from w = sum_j alpha_j y_j phi(a_j)): the mixed forms (tensor-core block,
+    gradient recomputed by the exact-slice arithmetic before accepting) at
+    s = 8 and 64 against the plain FP64 s = 1 form, every solve run to the
+    tolerance and timed, each result's gap re-evaluated by the FP64 oracle."""
+    import oracle
+    ko = oracle.kernel("rbf", gamma=args.svm_gamma)
+    runs = {}
+    for prec, s in (("fp64", 1), (args.svm_mixed_prec, 8), (args.svm_mixed_prec, 64)):
+        flags = B.FLAG_REFRESH if prec != "fp64" else 0
+        plan = B.Plan(0, A, y, k, 1.0, 1, s, args.svm_ttg_budget, seed=seed, prec=prec, tol=args.tol,
+                      check_every=max(1, 1024 // s), flags=flags, loss=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, _ = plan.run(-1)
+        wall = time.perf_counter() - t0
+        alpha = plan.alpha.cpu().numpy()
+        plan.close()
+        gap = svm_true_gap(oracle, A64, y.cpu().numpy(), ko, 1, 1.0, alpha)
+        runs[f"{prec}_s{s}"] = {"prec": prec, "s": s, "converged": bool(st["converged"]),
+                                "coordinate_updates": st["iters_done"], "ms": st["ms_total"], "wall_s": wall,
+                                "gap_solver": st["final_metric"], "gap_fp64": gap, "refreshes": st["refreshes"],
+                                "reached_tol_fp64": bool(st["converged"] and gap <= args.tol)}
+    base = runs["fp64_s1"]
+    ok = {k_: r["ms"] for k_, r in runs.items() if k_ != "fp64_s1" and r["reached_tol_fp64"]}
+    best = min(ok, key=ok.get) if ok and base["reached_tol_fp64"] else None
+    return {"tol": args.tol, "metric": "relative duality gap (P - D) / |P|", "runs": runs,
+            "speedup_measured": base["ms"] / ok[best] if best else None, "speedup_form": best}
+
+
+def run_gpu_svm(args):
+    """Config 1: s-step DCD for the K-SVM-L1 dual on the blobs, FP64, s = 1
+    and s = 8 (value: the s = 8 form).  The block is m x s FP64 kernel entries
+    per step, so a step is bound by kernel launches and their dependent chain,
+    not by memory or arithmetic; the roofline is reported as latency (us per
+    outer step against the launch-only floor of the same kernels)."""
+    import torch
+    from paper_2406_18001_gb300 import binding as B, inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    m, n = args.svm_m, args.svm_n
+    gam = args.svm_gamma
+    res = {}
+    with torch.cuda.stream(stream):
+        p = inputs.blobs(m=m, n=n, seed=rank)
+        A, y = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.y).to(dev)
+        k = B.kernel("rbf", gamma=gam)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        with ClockSampler(local) as clk:
+            for s in (1, 8):
+                H = (args.warmup + args.steps + 4) * s
+                plan = B.Plan(0, A, y, k, 1.0, 1, s, H, seed=rank, prec="fp64", loss=1)
+                for _ in range(args.warmup):
+                    plan.run(1)
+                torch.cuda.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                for i in range(args.steps):
+                    flush.zero_()
+                    ev[i][0].record(stream)
+                    plan.enqueue(1)
+                    ev[i][1].record(stream)
+                torch.cuda.synchronize()
+                ms = rank_max(sum(a.elapsed_time(b_) for a, b_ in ev), ws, dev)
+                st, _ = plan.run(0)
+                plan.close()
+                res[s] = {"ms_per_step": ms / args.steps, "us_per_update": 1e3 * ms / (args.steps * s),
+                          "updates_per_s": job_rate(args.steps * s, ms, ws),
+                          "kernels_per_step": st["gpu_launches_per_step"]}
+        # end to end through the C ABI with host buffers, s = 8, the config's H
+        Ah, yh = p.A.copy(), p.y.copy()
+        al_h = np.zeros(m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, st_e, _ = B.svm_solve(Ah, yh, k, 1, 1.0, 8, args.svm_H, seed=rank, prec="fp64", alpha=al_h,
+                                    flags=B.FLAG_HOST_IO, stream=stream.cuda_stream)
+        dt = time.perf_counter() - t0
+        e2e = {"value": args.svm_H / dt, "unit": UNIT, "h2d_bytes_per_step": (Ah.nbytes + yh.nbytes + m * 8),
+               "d2h_bytes_per_step": 2 * m * 8, "steps": 1, "wall_s": dt, "H": args.svm_H}
+        ttg = None if args.no_ttt else svm_time_to_gap(args, torch, B, A, y, k, p.A, rank)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        nt = oracle_threads()
+        ko = oracle.kernel("rbf", gamma=gam)
+        t0 = time.perf_counter()
+        done, alpha = 0, np.zeros(m)
+        while time.perf_counter() - t0 < 12.0 and done < args.svm_H:
+            alpha = oracle.sstep_dcd_svm(p.A, p.y, ko, 1, 1.0, 8, 512, seed=rank, first=done, alpha0=alpha)
+            done += 512
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+               "sample": f"{done} of the {args.svm_H} coordinate updates (Algorithm 2, s=8) of the full workload "
+                         f"({dt:.1f} s, plain FP64 C, row loops of U_k on {nt} threads)"}
+    if rank == 0:
+        r8 = res[8]
+        roof = {"bound": "latency", "achieved": 1e3 * r8["ms_per_step"], "unit": "us/outer step", "peak": None,
+                "frac": None, "traffic": None, "kernels_per_step": r8["kernels_per_step"],
+                "kernel": "whole outer step (sample, FP64 Gram, DCD chain, FP64 block, update)",
+                "algorithmic": {"flops_per_update": 3.0 * m * n, "bytes_per_step": m * n * 8 + m * 16,
+                                "note": "A (1 MB FP64) is L2-resident; the block is 2000 x 8 entries per step"}}
+        out = {"metric": METRIC, "value": r8["updates_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": r8["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD_SVM, "m": m, "n": n, "s": 8, "gamma": gam, "C": 1.0, "loss": 1,
+                          "l2": "256 MB buffer written before every timed step; steps timed alone"},
+               "forms": {"s1": res[1], "s8": res[8]}, "time_to_gap": ttg,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r8["kernels_per_step"] * args.steps,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------ CSR -----
@@ -954,9 +1107,15 @@ def main():
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--s", type=int, default=None)
-    ap.add_argument("--workload", default="krr", choices=["krr", "csr", "sweep", "fp8"],
-                    help="krr: dense K-RR BDCD (the headline); csr: sparse K-SVM DCD; sweep: batched K-RR; "
-                         "fp8: the FP8 / BF16 storage stress configuration")
+    ap.add_argument("--workload", default="krr", choices=["krr", "svm", "csr", "sweep", "fp8"],
+                    help="krr: dense K-RR BDCD (the headline); svm: K-SVM-L1 DCD on the blobs; csr: sparse K-SVM "
+                         "DCD; sweep: batched K-RR; fp8: the FP8 / BF16 storage stress configuration")
+    ap.add_argument("--svm-m", type=int, default=2000)
+    ap.add_argument("--svm-n", type=int, default=64)
+    ap.add_argument("--svm-gamma", type=float, default=1.0 / 128, help="RBF gamma = 1/(2 sigma^2), sigma = 8")
+    ap.add_argument("--svm-H", type=int, default=20000, help="coordinate updates of the end-to-end solve")
+    ap.add_argument("--svm-ttg-budget", type=int, default=2000000, help="coordinate-update cap of the gap solves")
+    ap.add_argument("--svm-mixed-prec", default="bf16x3")
     ap.add_argument("--sweep-count", type=int, default=256)
     ap.add_argument("--sweep-H", type=int, default=2048, help="block updates per problem")
     ap.add_argument("--sweep-s", type=int, default=0, help="fixed s for every problem (0: the autotuner's)")
@@ -981,6 +1140,8 @@ def main():
     ap.add_argument("--ttt-budget", type=int, default=400000, help="block-update cap of the tolerance solve")
     ap.add_argument("--ttt-small-m", type=int, default=6000,
                     help="rows of the subproblem on which both forms run to tolerance (0: skip)")
+    ap.add_argument("--literal-steps", type=int, default=10,
+                    help="outer steps timed in the literal order beside the fused step (0: skip)")
     ap.add_argument("--err-steps", type=int, default=2,
                     help="outer steps of the headline compared with the oracle (0: skip)")
     ap.add_argument("--ttt-fp64-steps", type=int, default=200)
@@ -991,6 +1152,8 @@ def main():
         args.s = 64
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "svm":
+        run_gpu_svm(args)
     elif args.workload == "csr":
         run_gpu_csr(args)
     elif args.workload == "sweep":
