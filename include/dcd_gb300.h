@@ -365,6 +365,24 @@ dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int
  */
 dcd_status dcd_quantize_e4m3(const dcd_matrix *A, uint8_t *q, int64_t ldq, float *row_scale, void *stream);
 
+/*
+ * Failure-path hooks (the paper has no counterpart; for testing how failures
+ * are reported without faulting, trapping or hanging a GPU).
+ *
+ * dcd_selftest_bounded_wait -- runs the library's bounded device wait for
+ *   real: one thread waits on an mbarrier whose arrival count is never
+ *   reached, giving up after about limit_ns nanoseconds (1e3 <= limit_ns <=
+ *   1e9, else DCD_EINVAL); the kernel then records the timeout and returns.
+ *   Returns DCD_ETIMEOUT (the expected result), DCD_ENOMEM / DCD_ECUDA on a
+ *   runtime failure.  The stream is usable afterwards.
+ *
+ * dcd_inject_alloc_failures -- the next `count` (>= 0) device allocations the
+ *   library makes fail as if the device had no memory left, so the call that
+ *   makes them returns DCD_ENOMEM; 0 clears the injection.
+ */
+dcd_status dcd_selftest_bounded_wait(int64_t limit_ns, void *stream);
+dcd_status dcd_inject_alloc_failures(int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,8 @@ class BatchOpts(C.Structure):
 EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "bdcd_krr_solve_batched", "dcd_krr_autotune_s",
            "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
            "dcd_plan_enqueue", "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
-           "dcd_kernel_block_apply", "dcd_kernel_block_static", "dcd_quantize_e4m3"]
+           "dcd_kernel_block_apply", "dcd_kernel_block_static", "dcd_quantize_e4m3", "dcd_selftest_bounded_wait",
+           "dcd_inject_alloc_failures"]
 
 _lock = threading.Lock()
 _lib = None
@@ -112,6 +113,8 @@ def lib():
             "dcd_kernel_block_apply": (i32, [M, K, i32, P, i64, P, P, P, P]),
             "dcd_kernel_block_static": (i32, [M, K, i32, P, i64, P, i64, P, i64, P]),
             "dcd_quantize_e4m3": (i32, [M, P, i64, P, P]),
+            "dcd_selftest_bounded_wait": (i32, [i64, P]),
+            "dcd_inject_alloc_failures": (i32, [i32]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -401,6 +404,16 @@ def kernel_block_apply(A, k, prec, cols, w, g, rowscale=None):
                                       _ptr(rowscale), _ptr(g), _stream(None))
     _check(rc, "dcd_kernel_block_apply", allow_notconv=False)
     return g
+
+
+def selftest_bounded_wait(limit_ns, stream=None):
+    """dcd_selftest_bounded_wait: the status (DCD_ETIMEOUT expected), not raised."""
+    return int(lib().dcd_selftest_bounded_wait(int(limit_ns), _stream(stream)))
+
+
+def inject_alloc_failures(count):
+    """dcd_inject_alloc_failures: the next `count` device allocations fail (DCD_ENOMEM)."""
+    _check(lib().dcd_inject_alloc_failures(int(count)), "dcd_inject_alloc_failures", allow_notconv=False)
 
 
 def krr_solve_batched(problems, prec="bf16x3", tol=0.0, check_every=0, streams=0, rounds_per_graph=0, flags=0,

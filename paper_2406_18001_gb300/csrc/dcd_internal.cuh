@@ -80,6 +80,10 @@ __device__ __forceinline__ double kfun_f64(const KernelParams &kp, double v)
 dcd_status validate_kernel(const dcd_kernel *k);
 dcd_status validate_dense(const dcd_matrix *A);
 
+// Every device allocation of the library (selftest.cu): cudaMallocAsync, or a
+// failure injected by dcd_inject_alloc_failures.
+cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t st);
+
 // --------------------------------------------------------- host launches --
 // All launchers enqueue on `st` and return cudaGetLastError().
 // ctr_next (optional, not ctr_dev): receives the stream position after this

@@ -369,7 +369,7 @@ struct Solver {
             double *lpart = (double *)ar.take(literal ? sizeof(double) * lit_blocks * col_pad : 0);
             double *lg = (double *)ar.take(literal ? sizeof(double) * m : 0);
             if (pass == 0) {
-                cudaError_t e = cudaMallocAsync(&ws, ar.used + 1024, st);
+                cudaError_t e = malloc_async(&ws, ar.used + 1024, st);
                 if (e != cudaSuccess) return cuda_status(e);
                 ar.base = (char *)ws;
                 continue;
@@ -498,7 +498,7 @@ struct Solver {
             if (h[0]) return DCD_EINVAL;
             const int64_t cap = std::max<int64_t>(1, sb * (int64_t)h[1]);
             const size_t cmb = csr_colmap_bytes(n, cap);
-            DCD_TRY(cudaMallocAsync(&ws_csr, cmb, st));
+            DCD_TRY(malloc_async(&ws_csr, cmb, st));
             DCD_TRY(cudaMemsetAsync(ws_csr, 0, cmb, st));
             cm = csr_colmap_carve(ws_csr, n, cap);
         } else if (tc) {
@@ -1448,7 +1448,7 @@ dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int3
     const size_t oe = place(cur, 256), ov = place(cur, conv32 ? 4 * (size_t)nnz : conv64 ? 8 * (size_t)nnz : 0);
     const size_t on32 = place(cur, 4 * (size_t)m), on64 = place(cur, 8 * (size_t)m);
     const size_t ow = place(cur, (w && !fp64) ? 4 * (size_t)ncols : 0);
-    DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+    DCD_TRY(malloc_async(&cb.mem, cur + 1024, st));
     char *base = (char *)cb.mem;
     int *err = (int *)(base + oe);
     DCD_TRY(cudaMemsetAsync(err, 0, 4 * sizeof(int), st));
@@ -1475,7 +1475,7 @@ dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int3
     if (h[0]) return DCD_EINVAL;
     const int64_t cap = std::max<int64_t>(1, ncols * (int64_t)h[1]);
     const size_t cmb = csr_colmap_bytes(A->n, cap);
-    DCD_TRY(cudaMallocAsync(&cb2.mem, cmb, st));
+    DCD_TRY(malloc_async(&cb2.mem, cmb, st));
     DCD_TRY(cudaMemsetAsync(cb2.mem, 0, cmb, st));
     const CsrColMap cm = csr_colmap_carve(cb2.mem, A->n, cap);
     DCD_TRY(launch_csr_colmap(ca, cols, ncols, cm, err, st));
@@ -1500,7 +1500,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         size_t cur = 0;
         size_t oe = place(cur, 256);
         size_t op64 = place(cur, pack ? sizeof(double) * A->m * A->n : 0);
-        DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+        DCD_TRY(malloc_async(&cb.mem, cur + 1024, st));
         char *base = (char *)cb.mem;
         int *err = (int *)(base + oe);
         DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -1547,7 +1547,7 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     }
     size_t osp = place(cur, sizeof(double) * tc_split_part_elems(sp.pairs, sp.chunks));
     size_t osc = place(cur, sizeof(unsigned) * 2 * sp.pairs);
-    DCD_TRY(cudaMallocAsync(&cb.mem, cur + 1024, st));
+    DCD_TRY(malloc_async(&cb.mem, cur + 1024, st));
     char *base = (char *)cb.mem;
     int *err = (int *)(base + oe);
     void *pa = base + oa, *pb = base + ob;
@@ -1607,7 +1607,7 @@ extern "C" dcd_status dcd_quantize_e4m3(const dcd_matrix *A, uint8_t *q, int64_t
     cudaStream_t st = (cudaStream_t)stream;
     ComponentBufs cb;
     cb.st = st;
-    DCD_TRY(cudaMallocAsync(&cb.mem, 256, st));
+    DCD_TRY(malloc_async(&cb.mem, 256, st));
     int *err = (int *)cb.mem;
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, nullptr, q, ldq, row_scale, A->m, err,
@@ -1712,7 +1712,7 @@ dcd_status autotune_s(const dcd_matrix *A, const double *y, const dcd_kernel *k,
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf buf;
     buf.st = st;
-    DCD_TRY(cudaMallocAsync(&buf.p, 2 * sizeof(double) * A->m, st));
+    DCD_TRY(malloc_async(&buf.p, 2 * sizeof(double) * A->m, st));
     double *alpha = (double *)buf.p, *grad = alpha + A->m;
     double best = 1e300;
     int best_s = 1;
