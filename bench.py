@@ -1024,6 +1024,30 @@ def run_gpu_sweep(args):
         wall_e2e = time.perf_counter() - t0
         h2d = sum(Ah.nbytes + yh.nbytes for Ah, yh in host)
         d2h = sum(a.numel() * 8 for a in al_h)
+        # every problem to relative residual tol with an epoch cap, the gradient recomputed (exact-slice
+        # products) before a problem is accepted; a sample of the results checked by an FP64 residual
+        conv = None
+        if args.sweep_tol > 0:
+            cprobs = [dict(p, H=args.sweep_epochs * p["A"].shape[0] // p["b"]) for p in probs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cal, _, cst, _ = B.krr_solve_batched(cprobs, prec=args.prec, tol=args.sweep_tol, check_every=4,
+                                                 flags=B.FLAG_REFRESH, streams=args.sweep_streams,
+                                                 stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            wall_c = time.perf_counter() - t0
+            chk = [i for i in range(count) if cst[i]["converged"]][:: max(1, count // 8)][:8]
+            res = [fp64_residual(B, torch, cprobs[i]["A"], cprobs[i]["y"], cal[i], cprobs[i]["k"], cprobs[i]["lam"])
+                   for i in chk]
+            conv = {"tol": args.sweep_tol, "epoch_cap": args.sweep_epochs, "problems": count,
+                    "converged": sum(int(x["converged"]) for x in cst), "wall_s": wall_c,
+                    "coordinate_updates": sum(int(x["iters_done"]) * p["b"] for x, p in zip(cst, cprobs)),
+                    "refreshes": sum(int(x["refreshes"]) for x in cst),
+                    "unconverged": [{"sigma": grid[i % len(grid)][0], "lambda": grid[i % len(grid)][1],
+                                     "m": cprobs[i]["A"].shape[0], "b": cprobs[i]["b"],
+                                     "final_metric": cst[i]["final_metric"]}
+                                    for i in range(count) if not cst[i]["converged"]][:16],
+                    "fp64_resid_checked": {"problems": chk, "max": max(res) if res else None}}
     upd = sum(int(st["iters_done"]) * p["b"] for st, p in zip(sts, probs))
     wall = rank_max(wall, ws, dev)  # the job's times are its slowest replica's
     wall_e2e = rank_max(wall_e2e, ws, dev)
@@ -1063,7 +1087,7 @@ def run_gpu_sweep(args):
                           "l2": "problems total ~0.65 GB of A (above L2); one timed batched call"},
                "sweep": {"coordinate_updates": upd, "wall_s": wall, "sequential_single_solves_wall_s": wall_seq,
                          "first_call_with_autotune_s": t_first,
-                         "s_chosen": s_hist, "converged": sum(int(st["converged"]) for st in sts)},
+                         "s_chosen": s_hist, "to_tolerance": conv},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
@@ -1120,6 +1144,8 @@ def main():
     ap.add_argument("--sweep-H", type=int, default=2048, help="block updates per problem")
     ap.add_argument("--sweep-s", type=int, default=0, help="fixed s for every problem (0: the autotuner's)")
     ap.add_argument("--sweep-streams", type=int, default=16, help="worker streams of the batched call")
+    ap.add_argument("--sweep-tol", type=float, default=1e-6, help="relative residual of the converging sweep (0: skip)")
+    ap.add_argument("--sweep-epochs", type=int, default=200, help="epoch cap per problem of the converging sweep")
     ap.add_argument("--fp8-m", type=int, default=400000)
     ap.add_argument("--fp8-n", type=int, default=2048)
     ap.add_argument("--fp8-sub", type=int, default=20000, help="rows of the alpha-error subproblem")
