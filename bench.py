@@ -40,7 +40,7 @@ UNIT = "coordinate updates/s"
 # an ncu capture: (prec, m, n, b, s, first 16 hex digits of the sha256 of
 # csrc/block_tc.cu when it was taken) -> bytes.  A changed kernel source
 # matches no entry, so its traffic reads null until it is captured again.
-NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64, "30c8c00e927fe3ab"): 108.39e6}
+NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64, "89d134a9821018ef"): 108.60e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 
@@ -544,6 +544,39 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- one kernel block --
+def run_block(args):
+    """A few fused kernel-block launches (dcd_kernel_block_apply) at the
+    headline shape (m rows, n features, s*b sampled columns, RBF) in one
+    precision, "refresh" included: the launch the profiles capture.  Reports
+    the launch time (CUDA events, median) against the method's 2 m n s b flops.
+    A diagnostic line, not the headline."""
+    import torch
+    from paper_2406_18001_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    p = make_problem(args.m, args.n)
+    A = torch.from_numpy(p.A).to(dev)
+    g = np.random.default_rng(1)
+    nc = args.s * args.b
+    cols = torch.from_numpy(g.integers(0, args.m, nc).astype(np.int32)).to(dev)
+    w = torch.from_numpy(g.standard_normal(nc)).to(dev)
+    gd = torch.zeros(args.m, dtype=torch.float64, device=dev)
+    k = B.kernel("rbf", gamma=args.gamma)
+    ms = []
+    for _ in range(args.block_launches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.kernel_block_apply(A, k, args.prec, cols, w, gd)  # packs A, then the block: the call, not the kernel
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    flops = 2.0 * args.m * args.n * nc
+    med = sorted(ms)[len(ms) // 2]
+    print(json.dumps({"metric": "kernel block apply call (pack + block)", "value": flops / (med * 1e-3) / 1e12,
+                      "unit": "TFLOP/s (method flops over the whole call)", "prec": args.prec,
+                      "config": {"m": args.m, "n": args.n, "ncols": nc}, "ms_per_call": ms}), flush=True)
 
 
 # --------------------------------------------------------------- K-SVM -----
@@ -1131,9 +1164,10 @@ def main():
     ap.add_argument("--m", type=int, default=50000)
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--s", type=int, default=None)
-    ap.add_argument("--workload", default="krr", choices=["krr", "svm", "csr", "sweep", "fp8"],
+    ap.add_argument("--workload", default="krr", choices=["krr", "svm", "csr", "sweep", "fp8", "block"],
                     help="krr: dense K-RR BDCD (the headline); svm: K-SVM-L1 DCD on the blobs; csr: sparse K-SVM "
                          "DCD; sweep: batched K-RR; fp8: the FP8 / BF16 storage stress configuration")
+    ap.add_argument("--block-launches", type=int, default=4, help="block workload: apply calls")
     ap.add_argument("--svm-m", type=int, default=2000)
     ap.add_argument("--svm-n", type=int, default=64)
     ap.add_argument("--svm-gamma", type=float, default=1.0 / 128, help="RBF gamma = 1/(2 sigma^2), sigma = 8")
@@ -1157,7 +1191,8 @@ def main():
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64"])
+    ap.add_argument("--prec", default="bf16x3",
+                    choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64", "refresh"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1180,6 +1215,8 @@ def main():
         run_reference(args)
     elif args.workload == "svm":
         run_gpu_svm(args)
+    elif args.workload == "block":
+        run_block(args)
     elif args.workload == "csr":
         run_gpu_csr(args)
     elif args.workload == "sweep":
