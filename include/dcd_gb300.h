@@ -366,6 +366,91 @@ dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int
 dcd_status dcd_quantize_e4m3(const dcd_matrix *A, uint8_t *q, int64_t ldq, float *row_scale, void *stream);
 
 /*
+ * Row-sharded outer step (components).  Rows are split over ranks: a rank
+ * holds rows [row0, row0 + m_local) of A, y, alpha and g (global indices;
+ * m = the total row count).  One outer step of Algorithms 2 / 4 then takes
+ * one exchange, of s*b*(n + 4) words per rank, where the paper's 1D-column
+ * layout reduces an m x s*b block (Section 4, Theorem 2):
+ *   1. every rank draws the same S (dcd_sample_indices);
+ *   2. dcd_shard_contribute, then an all-gather of the buffers (caller's
+ *      transport), then dcd_shard_assemble: A_S, g_S, alpha_S, y_S on every
+ *      rank;
+ *   3. the sampled Gram of A_S (dcd_kernel_block on the matrix A_S with
+ *      rows = cols = first_pos from dcd_shard_assemble) and the recurrence (dcd_bdcd_recurrence /
+ *      dcd_dcd_recurrence), redundantly on every rank, as the paper's ranks
+ *      repeat the recurrence;
+ *   4. dcd_kernel_block_apply_points on the rank's own rows against A_S,
+ *      then dcd_shard_update.
+ * Buffers are device memory owned by the caller; every call synchronises the
+ * stream before it returns.
+ *
+ * dcd_shard_contribute -- buf (cnt x (n + 4) doubles): for position j whose
+ *   row S[j] lies in this rank's range, [1, g[r], alpha[r], y[r], a_r (n
+ *   values in FP64, exact from F32 / BF16)] with r = S[j] - row0; zeros for
+ *   every other position.  A: the rank's rows (dense F64 / F32 / BF16;
+ *   FP8 gives DCD_EUNSUPPORTED).  y may be NULL (0 written).  An S entry
+ *   outside [0, m) gives DCD_EINVAL.  cnt <= 8192.
+ *
+ * dcd_shard_assemble -- bufs: nranks contribution buffers one after another
+ *   (the all-gather's output).  For every position, exactly one buffer must
+ *   hold the row (else DCD_EINVAL); A_S (cnt x n, row-major FP64), g_S,
+ *   alpha_S and y_S (y_S may be NULL) receive it.  first_pos (optional,
+ *   needs S): first_pos[j] = the first position q with S[q] == S[j]; as the
+ *   rows and cols of dcd_kernel_block on the matrix A_S it gives the sampled
+ *   Gram with the ids of the single-GPU step (a repeated row is its own
+ *   sample).
+ *
+ * dcd_bdcd_recurrence -- the K-RR recurrence of Algorithm 4 on gathered
+ *   values (eq. bdcd-sstep): Kss the sampled kernel block K(A_S, A_S)
+ *   (FP64 when kss_f64, else FP32; leading dimension ldk >= nblk*b), S the
+ *   sampled row ids (repeats across the nblk blocks of b are allowed and
+ *   handled), g_S[p] = g[S[p]].  The Gram is Kss / lambda + mdiag * [S_p ==
+ *   S_q] (mdiag = m).  Output: delta[p] (the change of alpha at position p)
+ *   and, when w is non-NULL, w[p] = delta[p] / lambda (the coefficients of
+ *   the kernel-block update).  FP64 arithmetic throughout; an FP64 Kss gets
+ *   the adaptive refinement of the FP64 solve, an FP32 one a refined FP32
+ *   factorisation.  A non-positive-definite diagonal block gives DCD_ENOTSPD.
+ *
+ * dcd_dcd_recurrence -- the K-SVM recurrence of Algorithm 2 on gathered
+ *   values: Kss the sampled kernel block (raw kernel values), S the sampled
+ *   row ids (repeats allowed), y_S / alpha_S / g_S the values at them, loss 1
+ *   (hinge: omega = 0, nu = C) or 2 (squared hinge: omega = 1/(2C), nu =
+ *   infinity).  Output: theta[p] and, when w is non-NULL, w[p] = y_S[p] *
+ *   theta[p].  cnt <= 8192.
+ *
+ * dcd_kernel_block_apply_points -- dcd_kernel_block_apply with the column
+ *   points given as the rows of a matrix P (dense, P->n == A->n) instead of
+ *   indices into A:
+ *     g[i] += rowscale[i] * sum_{c < P->m} K(a_i, p_c) * w[c],  i < A->m.
+ *   In the tensor-core precisions the squared distance of a row to itself is
+ *   taken as exactly 0 (as in the single-GPU step); "itself" compares ids:
+ *   row_id0 + i for row i of A, col_ids[c] for row c of P (col_ids NULL: no
+ *   row matches).  FP8 storage or precision gives DCD_EUNSUPPORTED.
+ *
+ * dcd_shard_update -- the alpha / g update (a6) restricted to this rank's
+ *   rows: for each distinct S entry in [row0, row0 + m_local), the delta of
+ *   all its positions summed in position order, alpha[r] += sum, g[r] +=
+ *   diag * sum (diag: m for K-RR, omega for K-SVM).  Other entries are
+ *   skipped.
+ */
+dcd_status dcd_shard_contribute(const dcd_matrix *A, int64_t row0, int64_t m, const int32_t *S, int64_t cnt,
+                                const double *g, const double *alpha, const double *y, double *buf, void *stream);
+dcd_status dcd_shard_assemble(const double *bufs, int32_t nranks, const int32_t *S, int64_t cnt, int64_t n,
+                              double *A_S, double *g_S, double *alpha_S, double *y_S, int32_t *first_pos,
+                              void *stream);
+dcd_status dcd_bdcd_recurrence(const void *Kss, int32_t kss_f64, int64_t ldk, const int32_t *S, int64_t nblk,
+                               int32_t b, double lambda, double mdiag, const double *g_S, double *delta, double *w,
+                               void *stream);
+dcd_status dcd_dcd_recurrence(const void *Kss, int32_t kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
+                              const double *y_S, const double *alpha_S, const double *g_S, int32_t loss, double C,
+                              double *theta, double *w, void *stream);
+dcd_status dcd_kernel_block_apply_points(const dcd_matrix *A, int64_t row_id0, const dcd_matrix *P,
+                                         const int32_t *col_ids, const dcd_kernel *k, int32_t prec, const double *w,
+                                         const double *rowscale, double *g, void *stream);
+dcd_status dcd_shard_update(const int32_t *S, const double *delta, int64_t cnt, double diag, int64_t row0,
+                            int64_t m_local, double *alpha, double *g, void *stream);
+
+/*
  * Failure-path hooks (the paper has no counterpart; for testing how failures
  * are reported without faulting, trapping or hanging a GPU).
  *

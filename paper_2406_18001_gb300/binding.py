@@ -71,7 +71,8 @@ EXPORTS = ["dcd_svm_solve", "bdcd_krr_solve", "bdcd_krr_solve_batched", "dcd_krr
            "dcd_svm_plan_create", "bdcd_krr_plan_create", "dcd_plan_run",
            "dcd_plan_enqueue", "dcd_plan_destroy", "dcd_status_string", "dcd_sample_indices", "dcd_kernel_block",
            "dcd_kernel_block_apply", "dcd_kernel_block_static", "dcd_quantize_e4m3", "dcd_selftest_bounded_wait",
-           "dcd_inject_alloc_failures"]
+           "dcd_inject_alloc_failures", "dcd_shard_contribute", "dcd_shard_assemble", "dcd_bdcd_recurrence",
+           "dcd_dcd_recurrence", "dcd_kernel_block_apply_points", "dcd_shard_update"]
 
 _lock = threading.Lock()
 _lib = None
@@ -115,6 +116,12 @@ def lib():
             "dcd_quantize_e4m3": (i32, [M, P, i64, P, P]),
             "dcd_selftest_bounded_wait": (i32, [i64, P]),
             "dcd_inject_alloc_failures": (i32, [i32]),
+            "dcd_shard_contribute": (i32, [M, i64, i64, P, i64, P, P, P, P, P]),
+            "dcd_shard_assemble": (i32, [P, i32, P, i64, i64, P, P, P, P, P, P]),
+            "dcd_bdcd_recurrence": (i32, [P, i32, i64, P, i64, i32, d, d, P, P, P, P]),
+            "dcd_dcd_recurrence": (i32, [P, i32, i64, P, i64, P, P, P, i32, d, P, P, P]),
+            "dcd_kernel_block_apply_points": (i32, [M, i64, M, P, K, i32, P, P, P, P]),
+            "dcd_shard_update": (i32, [P, P, i64, d, i64, i64, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -404,6 +411,61 @@ def kernel_block_apply(A, k, prec, cols, w, g, rowscale=None):
                                       _ptr(rowscale), _ptr(g), _stream(None))
     _check(rc, "dcd_kernel_block_apply", allow_notconv=False)
     return g
+
+
+def kernel_block_apply_points(A, row_id0, P, col_ids, k, prec, w, g, rowscale=None):
+    """dcd_kernel_block_apply_points: g[i] += rowscale[i] sum_c K(a_i, p_c) w[c]
+    with the column points the rows of P; ids row_id0 + i and col_ids[c]
+    decide the own-sample rule (col_ids None: no row matches)."""
+    Am, Pm = dense_matrix(A), dense_matrix(P)
+    rc = lib().dcd_kernel_block_apply_points(C.byref(Am), int(row_id0), C.byref(Pm), _ptr(col_ids), C.byref(k),
+                                             _prec(prec), _ptr(w), _ptr(rowscale), _ptr(g), _stream(None))
+    _check(rc, "dcd_kernel_block_apply_points", allow_notconv=False)
+    return g
+
+
+def shard_contribute(A, row0, m, S, g, alpha, y, buf):
+    """dcd_shard_contribute: this rank's contribution of the sampled rows it
+    holds (rows row0 .. row0 + A.shape[0] - 1 of m) into buf (cnt x (n + 4))."""
+    Am = dense_matrix(A)
+    rc = lib().dcd_shard_contribute(C.byref(Am), int(row0), int(m), _ptr(S), S.numel(), _ptr(g), _ptr(alpha),
+                                    _ptr(y), _ptr(buf), _stream(None))
+    _check(rc, "dcd_shard_contribute", allow_notconv=False)
+    return buf
+
+
+def shard_assemble(bufs, nranks, S, n, A_S, g_S, alpha_S, y_S=None, first_pos=None):
+    """dcd_shard_assemble: A_S, g_S, alpha_S (and y_S, first_pos) from the
+    all-gathered contributions (nranks buffers one after another)."""
+    rc = lib().dcd_shard_assemble(_ptr(bufs), int(nranks), _ptr(S), S.numel(), int(n), _ptr(A_S), _ptr(g_S),
+                                  _ptr(alpha_S), _ptr(y_S), _ptr(first_pos), _stream(None))
+    _check(rc, "dcd_shard_assemble", allow_notconv=False)
+
+
+def bdcd_recurrence(Kss, S, b, lam, mdiag, g_S, delta, w=None):
+    """dcd_bdcd_recurrence on a (cnt x cnt) sampled kernel block (FP64 or FP32)."""
+    import torch
+    f64 = 1 if Kss.dtype == torch.float64 else 0
+    cnt = S.numel()
+    rc = lib().dcd_bdcd_recurrence(_ptr(Kss), f64, Kss.stride(0), _ptr(S), cnt // int(b), int(b), float(lam),
+                                   float(mdiag), _ptr(g_S), _ptr(delta), _ptr(w), _stream(None))
+    _check(rc, "dcd_bdcd_recurrence", allow_notconv=False)
+
+
+def dcd_recurrence(Kss, S, y_S, alpha_S, g_S, loss, C_, theta, w=None):
+    """dcd_dcd_recurrence on a (cnt x cnt) sampled kernel block (FP64 or FP32)."""
+    import torch
+    f64 = 1 if Kss.dtype == torch.float64 else 0
+    rc = lib().dcd_dcd_recurrence(_ptr(Kss), f64, Kss.stride(0), _ptr(S), S.numel(), _ptr(y_S), _ptr(alpha_S),
+                                  _ptr(g_S), int(loss), float(C_), _ptr(theta), _ptr(w), _stream(None))
+    _check(rc, "dcd_dcd_recurrence", allow_notconv=False)
+
+
+def shard_update(S, delta, diag, row0, alpha, g):
+    """dcd_shard_update: alpha / g update of the rows row0 .. row0 + len(alpha) - 1."""
+    rc = lib().dcd_shard_update(_ptr(S), _ptr(delta), S.numel(), float(diag), int(row0), alpha.numel(), _ptr(alpha),
+                                _ptr(g), _stream(None))
+    _check(rc, "dcd_shard_update", allow_notconv=False)
 
 
 def selftest_bounded_wait(limit_ns, stream=None):

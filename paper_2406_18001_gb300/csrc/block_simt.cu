@@ -2,8 +2,11 @@
 // (U_k = K(A, A_k) of Algorithm 2, Q_k of Algorithm 4) for the FP64 form.
 //
 // Two epilogues share one tile loop:
-//   apply: g[i] += rs[i] * sum_c K(a_i, a_cols[c]) w[c]   (block never stored)
-//   store: out[r, c] = K(a_rows[r], a_cols[c])            (the Gram of a3)
+//   apply: g[i] += rs[i] * sum_c K(a_i, b_cols[c]) w[c]   (block never stored)
+//   store: out[r, c] = K(a_rows[r], b_cols[c])            (the Gram of a3)
+// The column points b are rows of A itself (the sampled rows) or of a second
+// matrix B (rows gathered from other ranks in the row-sharded step);
+// cols == nullptr takes B's rows 0..ncols-1.
 // RBF distances are summed from coordinate differences (Table 1's definition)
 // rather than expanded, so the FP64 form carries no cancellation error.
 // The k-order of every dot product is fixed (0..n-1 in steps of BK), so the
@@ -22,8 +25,9 @@ constexpr int BK = 16;
 template <int RN, bool STORE, bool RBF>
 __global__ void __launch_bounds__(256) block_simt_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
                                                             int64_t n, KernelParams kp, const int32_t *rows,
-                                                            int64_t nrows, const int32_t *cols, int64_t ncols,
-                                                            const double *__restrict__ w,
+                                                            int64_t nrows, const double *__restrict__ Bm,
+                                                            int64_t ldb, int64_t mb, const int32_t *cols,
+                                                            int64_t ncols, const double *__restrict__ w,
                                                             const double *__restrict__ rs, double *g, double *out,
                                                             int64_t ldo, int *err)
 {
@@ -53,8 +57,8 @@ __global__ void __launch_bounds__(256) block_simt_f64_kernel(const double *__res
             if (threadIdx.x < BN) {
                 int64_t c = c0 + threadIdx.x, off = -1;
                 if (c < ncols) {
-                    int64_t ci = cols[c];
-                    if (ci >= 0 && ci < m) off = ci * lda;
+                    int64_t ci = cols ? (int64_t)cols[c] : c;
+                    if (ci >= 0 && ci < mb) off = ci * ldb;
                     else set_error(err, DEV_BAD_INDEX);
                 }
                 coloff[threadIdx.x] = off;
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(256) block_simt_f64_kernel(const double *__res
                 for (int e = threadIdx.x; e < BN * BK; e += 256) {
                     int cc = e / BK, kk = e % BK;
                     int64_t off = coloff[cc], k = k0 + kk;
-                    Bs[kk][cc] = (off >= 0 && k < n) ? A[off + k] : 0.0;
+                    Bs[kk][cc] = (off >= 0 && k < n) ? Bm[off + k] : 0.0;
                 }
                 __syncthreads();
 #pragma unroll
@@ -133,21 +137,22 @@ __global__ void __launch_bounds__(256) block_simt_f64_kernel(const double *__res
 
 template <bool STORE, bool RBF>
 cudaError_t launch_rn(int rn, int64_t grid, const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
-                      const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols, const double *w,
-                      const double *rs, double *g, double *out, int64_t ldo, int *err, cudaStream_t st)
+                      const int32_t *rows, int64_t nrows, const double *Bm, int64_t ldb, int64_t mb,
+                      const int32_t *cols, int64_t ncols, const double *w, const double *rs, double *g, double *out,
+                      int64_t ldo, int *err, cudaStream_t st)
 {
     switch (rn) {
     case 1:
-        block_simt_f64_kernel<1, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                           w, rs, g, out, ldo, err);
+        block_simt_f64_kernel<1, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                           cols, ncols, w, rs, g, out, ldo, err);
         break;
     case 2:
-        block_simt_f64_kernel<2, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                           w, rs, g, out, ldo, err);
+        block_simt_f64_kernel<2, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                           cols, ncols, w, rs, g, out, ldo, err);
         break;
     default:
-        block_simt_f64_kernel<4, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                           w, rs, g, out, ldo, err);
+        block_simt_f64_kernel<4, STORE, RBF><<<(unsigned)grid, 256, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                           cols, ncols, w, rs, g, out, ldo, err);
         break;
     }
     return cudaGetLastError();
@@ -164,8 +169,9 @@ cudaError_t launch_rn(int rn, int64_t grid, const double *A, int64_t lda, int64_
 template <bool STORE, bool RBF>
 __global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
                                                               int64_t n, KernelParams kp, const int32_t *rows,
-                                                              int64_t nrows, const int32_t *cols, int64_t ncols,
-                                                              int cw, const double *__restrict__ w,
+                                                              int64_t nrows, const double *__restrict__ Bm,
+                                                              int64_t ldb, int64_t mb, const int32_t *cols,
+                                                              int64_t ncols, int cw, const double *__restrict__ w,
                                                               const double *__restrict__ rs, double *g, double *out,
                                                               int64_t ldo, int *err)
 {
@@ -175,9 +181,9 @@ __global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__re
     const bool ok = r < nrows && c < ncols;
     double kv = 0.0;
     if (ok) {
-        const int64_t ri = rows ? (int64_t)rows[r] : r, ci = cols[c];
-        if (ri >= 0 && ri < m && ci >= 0 && ci < m) {
-            const double *a = A + ri * lda, *b = A + ci * lda;
+        const int64_t ri = rows ? (int64_t)rows[r] : r, ci = cols ? (int64_t)cols[c] : c;
+        if (ri >= 0 && ri < m && ci >= 0 && ci < mb) {
+            const double *a = A + ri * lda, *b = Bm + ci * ldb;
             double acc = 0.0;
             for (int64_t k = 0; k < n; ++k) {
                 if (RBF) {
@@ -206,9 +212,14 @@ __global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__re
 cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
                                   const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
                                   const double *w, const double *rs, double *g, double *out, int64_t ldo, int *err,
-                                  cudaStream_t st)
+                                  cudaStream_t st, const double *Bm, int64_t ldb, int64_t mb)
 {
     if (nrows <= 0 || ncols <= 0) return cudaSuccess;
+    if (!Bm) {  // the column points are rows of A
+        Bm = A;
+        ldb = lda;
+        mb = m;
+    }
     const int rn = ncols <= 16 ? 1 : (ncols <= 32 ? 2 : 4);
     int64_t tiles = (nrows + BM - 1) / BM;
     int dev = 0, sms = 148;
@@ -221,27 +232,27 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
         const unsigned blocks = (unsigned)((threads + 127) / 128);
         const bool store = (out != nullptr), rbf = (kp.kind == DCD_RBF);
         if (store && rbf)
-            block_small_f64_kernel<true, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols, cw,
-                                                                      w, rs, g, out, ldo, err);
+            block_small_f64_kernel<true, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                      cols, ncols, cw, w, rs, g, out, ldo, err);
         else if (store)
-            block_small_f64_kernel<true, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                       cw, w, rs, g, out, ldo, err);
+            block_small_f64_kernel<true, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                       cols, ncols, cw, w, rs, g, out, ldo, err);
         else if (rbf)
-            block_small_f64_kernel<false, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                       cw, w, rs, g, out, ldo, err);
+            block_small_f64_kernel<false, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                       cols, ncols, cw, w, rs, g, out, ldo, err);
         else
-            block_small_f64_kernel<false, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, cols, ncols,
-                                                                        cw, w, rs, g, out, ldo, err);
+            block_small_f64_kernel<false, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+                                                                        cols, ncols, cw, w, rs, g, out, ldo, err);
         return cudaGetLastError();
     }
     int64_t grid = tiles < (int64_t)sms * 8 ? tiles : (int64_t)sms * 8;
     const bool store = (out != nullptr);
     const bool rbf = (kp.kind == DCD_RBF);
     if (store)
-        return rbf ? launch_rn<true, true>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st)
-                   : launch_rn<true, false>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st);
-    return rbf ? launch_rn<false, true>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st)
-               : launch_rn<false, false>(rn, grid, A, lda, m, n, kp, rows, nrows, cols, ncols, w, rs, g, out, ldo, err, st);
+        return rbf ? launch_rn<true, true>(rn, grid, A, lda, m, n, kp, rows, nrows, Bm, ldb, mb, cols, ncols, w, rs, g, out, ldo, err, st)
+                   : launch_rn<true, false>(rn, grid, A, lda, m, n, kp, rows, nrows, Bm, ldb, mb, cols, ncols, w, rs, g, out, ldo, err, st);
+    return rbf ? launch_rn<false, true>(rn, grid, A, lda, m, n, kp, rows, nrows, Bm, ldb, mb, cols, ncols, w, rs, g, out, ldo, err, st)
+               : launch_rn<false, false>(rn, grid, A, lda, m, n, kp, rows, nrows, Bm, ldb, mb, cols, ncols, w, rs, g, out, ldo, err, st);
 }
 
 }  // namespace dcd

@@ -95,10 +95,12 @@ cudaError_t launch_sample(int method, uint64_t seed, const uint64_t *ctr_dev, ui
 // FP64 CUDA-core kernel block over a dense matrix of doubles.
 //   apply (out == nullptr): g[i] += rs[i] * sum_c K(a_i, a_cols[c]) * w[c] for i < nrows
 //   store (g == nullptr):   out[r*ldo + c] = K(a_rows[r], a_cols[c])
+// Column points: rows cols[c] (cols == nullptr: row c) of B (B == nullptr: of A).
 cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64_t n, const KernelParams &kp,
                                   const int32_t *rows, int64_t nrows, const int32_t *cols, int64_t ncols,
                                   const double *w, const double *rs, double *g, double *out, int64_t ldo,
-                                  int *err, cudaStream_t st);
+                                  int *err, cudaStream_t st, const double *B = nullptr, int64_t ldb = 0,
+                                  int64_t mb = 0);
 
 // tcgen05 kernel block over the packed, padded operand copy (bf16 or fp32
 // rows of n_pad elements, zero padded).
@@ -221,6 +223,8 @@ cudaError_t launch_pack_sliced(const void *src, int dtype, int64_t ld, int64_t m
                                void *dst, int64_t n_pad, int64_t count, float *sc, int *err, cudaStream_t st,
                                const float *src_scale = nullptr);
 cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st);
+// out[i] = start + i, i < count (shard.cu)
+cudaError_t launch_iota(int32_t *out, int64_t count, int64_t start, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
                              cudaStream_t st);
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,

@@ -1485,21 +1485,36 @@ dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int3
     return finish_component(err, st);
 }
 
+// Column points given as a matrix of their own: rows 0..ncols-1 of P stand
+// for the columns, and the own-sample rule of the tensor-core epilogue (a
+// squared distance of exactly 0 between a row and itself) compares global
+// ids: row_id0 + i for row i of A, col_ids[c] for row c of P (no column
+// matches when col_ids is null).  The FP64 form sums coordinate differences
+// and needs no ids.
+struct PointsArg {
+    const dcd_matrix *P = nullptr;
+    int64_t row_id0 = 0;
+    const int32_t *col_ids = nullptr;
+};
+
 // Runs the kernel block on rows `rows` (or the first nrows) against columns
-// `cols`: store into `out` (w == nullptr) or apply into g.
+// `cols` (or against the rows of pts->P): store into `out` (w == nullptr) or
+// apply into g.
 dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,
                            int64_t nrows, const int32_t *cols, int64_t ncols, const double *w, const double *rs,
-                           double *g, void *out, int64_t ldo, cudaStream_t st)
+                           double *g, void *out, int64_t ldo, cudaStream_t st, const PointsArg *pts = nullptr)
 {
     const KernelParams kp = to_kp(k);
     if (A->fmt == DCD_CSR) return component_block_csr(A, kp, prec, rows, nrows, cols, ncols, w, rs, g, out, ldo, st);
+    const dcd_matrix *P = pts ? pts->P : A;  // the matrix holding the column points
     ComponentBufs cb;
     cb.st = st;
     if (!is_tc(prec) && prec != DCD_PREC_REFRESH) {
-        const bool pack = A->dtype != DCD_F64;
+        const bool pack = A->dtype != DCD_F64, packp = pts && P->dtype != DCD_F64;
         size_t cur = 0;
         size_t oe = place(cur, 256);
         size_t op64 = place(cur, pack ? sizeof(double) * A->m * A->n : 0);
+        size_t opp = place(cur, packp ? sizeof(double) * P->m * P->n : 0);
         DCD_TRY(malloc_async(&cb.mem, cur + 1024, st));
         char *base = (char *)cb.mem;
         int *err = (int *)(base + oe);
@@ -1513,8 +1528,21 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
             a64 = p;
             lda = A->n;
         }
-        DCD_TRY(launch_block_simt_f64(a64, lda, A->m, A->n, kp, rows, nrows, cols, ncols, w, rs, g, (double *)out,
-                                      ldo, err, st));
+        const double *p64 = nullptr;
+        int64_t ldp = 0;
+        if (pts) {
+            p64 = (const double *)P->values;
+            ldp = P->ld;
+            if (packp) {
+                double *p = (double *)(base + opp);
+                DCD_TRY(launch_pack_rows(P->values, P->dtype, P->ld, P->m, P->n, nullptr, p, 2, P->n, P->m, err, st,
+                                         P->row_scale));
+                p64 = p;
+                ldp = P->n;
+            }
+        }
+        DCD_TRY(launch_block_simt_f64(a64, lda, A->m, A->n, kp, rows, nrows, pts ? nullptr : cols, ncols, w, rs, g,
+                                      (double *)out, ldo, err, st, p64, ldp, pts ? P->m : 0));
         return finish_component(err, st);
     }
     const bool accurate = prec == DCD_PREC_REFRESH;
@@ -1536,6 +1564,10 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     size_t ocs = place(cur, (fp8 || sliced) ? sizeof(float) * cpad : 0);
     size_t orl = place(cur, accurate ? sizeof(float) * nrows : 0);
     size_t ocl = place(cur, accurate ? sizeof(float) * cpad : 0);
+    // points form: global row ids (when offset) and column ids (-1 without col_ids)
+    const bool rid = pts && pts->row_id0 != 0, cid = pts && !pts->col_ids;
+    size_t ori = place(cur, rid ? sizeof(int32_t) * nrows : 0);
+    size_t oci = place(cur, cid ? sizeof(int32_t) * ncols : 0);
     // the apply form's balanced split over CTA pairs
     TcSplit sp;
     if (!out) {
@@ -1562,30 +1594,46 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
         sp.cnt = (unsigned *)(base + osc);
         DCD_TRY(cudaMemsetAsync(sp.cnt, 0, sizeof(unsigned) * 2 * sp.pairs, st));
     }
+    const int32_t *pcols = pts ? nullptr : cols;  // rows of P: the first ncols
     if (sliced) {
         DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
         DCD_TRY(launch_pack_sliced(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, n_pad, nrows, rsa, err, st,
                                    A->row_scale));
-        DCD_TRY(launch_pack_sliced(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, n_pad, ncols, rsb, err, st,
-                                   A->row_scale));
+        DCD_TRY(launch_pack_sliced(P->values, P->dtype, P->ld, P->m, P->n, pcols, pb, n_pad, ncols, rsb, err, st,
+                                   P->row_scale));
     } else if (fp8) {
         DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
         DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, A->row_scale, (uint8_t *)pa, n_pad,
                                      rsa, nrows, err, st));
-        DCD_TRY(launch_quantize_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, A->row_scale, (uint8_t *)pb, n_pad,
-                                     rsb, ncols, err, st));
+        DCD_TRY(launch_quantize_rows(P->values, P->dtype, P->ld, P->m, P->n, pcols, P->row_scale, (uint8_t *)pb,
+                                     n_pad, rsb, ncols, err, st));
     } else {
         DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, pk, n_pad, nrows, err, st,
                                  A->row_scale));
-        DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, cols, pb, pk, n_pad, ncols, err, st,
-                                 A->row_scale));
+        DCD_TRY(launch_pack_rows(P->values, P->dtype, P->ld, P->m, P->n, pcols, pb, pk, n_pad, ncols, err, st,
+                                 P->row_scale));
     }
     float *rl = accurate ? (float *)(base + orl) : nullptr, *cl = accurate ? (float *)(base + ocl) : nullptr;
     if (cl) DCD_TRY(cudaMemsetAsync(cl, 0, sizeof(float) * cpad, st));
     DCD_TRY(launch_row_terms(pa, pk, n_pad, nrows, kp, rh, st, rsa, rl));
     DCD_TRY(launch_row_terms(pb, pk, n_pad, ncols, kp, ch, st, rsb, cl));
     if (w) DCD_TRY(launch_f64_to_f32(w, ncols, cw, st));
-    TcOperand Aop{pa, nrows, n_pad, pk, rsa, rows}, Bop{pb, ncols, n_pad, pk, rsb, cols};
+    const int32_t *aids = rows, *bids = cols;
+    if (pts) {
+        aids = nullptr;  // row i: id i, or row_id0 + i from the array below
+        bids = pts->col_ids;
+        if (rid) {
+            int32_t *ids = (int32_t *)(base + ori);
+            DCD_TRY(launch_iota(ids, nrows, pts->row_id0, st));
+            aids = ids;
+        }
+        if (cid) {
+            int32_t *ids = (int32_t *)(base + oci);
+            DCD_TRY(cudaMemsetAsync(ids, 0xff, sizeof(int32_t) * ncols, st));  // -1: matches no row
+            bids = ids;
+        }
+    }
+    TcOperand Aop{pa, nrows, n_pad, pk, rsa, aids}, Bop{pb, ncols, n_pad, pk, rsb, bids};
     TcAccurate acc;
     acc.w64 = w;
     acc.row_hl = rl;
@@ -1637,6 +1685,26 @@ extern "C" dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kern
     if (ncols < 0 || (ncols > 0 && (!cols || !w)) || !g) return DCD_EINVAL;
     if (ncols == 0) return DCD_OK;
     return component_block(A, k, prec, nullptr, A->m, cols, ncols, w, rowscale, g, nullptr, 0, (cudaStream_t)stream);
+}
+
+extern "C" dcd_status dcd_kernel_block_apply_points(const dcd_matrix *A, int64_t row_id0, const dcd_matrix *P,
+                                                    const int32_t *col_ids, const dcd_kernel *k, int32_t prec,
+                                                    const double *w, const double *rowscale, double *g, void *stream)
+{
+    dcd_status s = component_check(A, k, prec, true);
+    if (s != DCD_OK) return s;
+    if (A->fmt != DCD_DENSE || !P || !g) return DCD_EINVAL;
+    if ((s = validate_dense(P)) != DCD_OK) return s;
+    if (P->fmt != DCD_DENSE || P->n != A->n) return DCD_EINVAL;
+    if (row_id0 < 0 || row_id0 + A->m > (int64_t)INT32_MAX) return DCD_EINVAL;
+    if (A->dtype == DCD_FP8E4M3 || P->dtype == DCD_FP8E4M3 || prec == DCD_PREC_FP8) return DCD_EUNSUPPORTED;
+    if (!w) return DCD_EINVAL;
+    PointsArg pts;
+    pts.P = P;
+    pts.row_id0 = row_id0;
+    pts.col_ids = col_ids;
+    return component_block(A, k, prec, nullptr, A->m, nullptr, P->m, w, rowscale, g, nullptr, 0, (cudaStream_t)stream,
+                           &pts);
 }
 
 // ------------------------------------------------------------- batched --
