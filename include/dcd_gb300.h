@@ -122,6 +122,9 @@ typedef enum {
                                      the end).  The verification and byte-comparison form of the fused
                                      step: it moves the m x sb block through memory twice.  Dense data
                                      matrices only; requires tol = 0 (else DCD_EINVAL) */
+#define DCD_FLAG_CSR_FULL_PASS 0x40 /* CSR data matrix: stream every nonzero in each step's kernel block (the
+                                       paper's SpMM) even where the apply through the transposed copy would
+                                       read less; both give the same bits (for comparison and testing) */
 #define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
                                      recompute the gradient from alpha by full kernel passes (tensor-core
                                      modes: DCD_PREC_REFRESH; FP64 mode: FP64) and accept convergence only

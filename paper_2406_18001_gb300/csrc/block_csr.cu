@@ -33,6 +33,11 @@ constexpr int CSR_WARPS = 8;      // warps per CTA
 constexpr int CSR_GJ = 256;       // sampled columns per Gram pass
 constexpr int MAP_THREADS = 1024;
 
+// A product rounded on its own (never contracted into an FMA with the sum it
+// joins), so that every route to a dot product adds the same rounded terms.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ T kfun_t(const KernelParams &kp, T dot, T na, T nb, bool same)
 {
@@ -111,7 +116,7 @@ __device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrCol
         if (q1 - q0 == 1) {
             const int j = M.ent_j[q0] - j0;
             ws.hj[h] = j >= 0 && j < jc ? j : -1;
-            ws.hprod[h] = v * (T)M.ent_v[q0];
+            ws.hprod[h] = mul_rn(v, (T)M.ent_v[q0]);
         } else {
             ws.hj[h] = -2 - slot;
             ws.hprod[h] = v;
@@ -137,7 +142,7 @@ __device__ __forceinline__ void flush_hits(WarpSmem<T> &ws, int nh, const CsrCol
                 for (int q = M.slot_off[slot]; q < M.slot_off[slot + 1]; ++q) {
                     const int j = M.ent_j[q] - j0;
                     if (j >= 0 && j < jc) {
-                        ws.acc[lane][j] += v * (T)M.ent_v[q];
+                        ws.acc[lane][j] += mul_rn(v, (T)M.ent_v[q]);
                         touched |= 1u << j;
                     }
                 }
@@ -176,23 +181,16 @@ __device__ __forceinline__ T kfun_k(T dot, T na, T nb, bool same, T gamma, T coe
     return exp(-gamma * d2);
 }
 
-// Apply: one warp per tile of 32 consecutive rows.  The tile's column indices
-// are streamed as int4 quads (lane l: indices 4 l .. 4 l + 3 of a 128-index
-// chunk), the next group of CSR_PF chunks loaded while the current one is
-// tested against the column bitmap (shared memory when it fits); hits are
-// listed in element order (warp prefix sum of the per-lane counts) as offsets
-// and columns only.  flush_hits resolves and applies them; lane r then forms
-// row t0 + r's sum from the base term and the touched columns (ascending j).
+// CTA set-up of an apply launch (every thread): the chunk's sampled ids,
+// norms, RBF factors and coefficients, the bitmap (shared memory when it
+// fits), zeroed accumulators and the base term's column sum (thread 0, in
+// column order).
 template <typename T, int KIND, bool SBITS>
-__global__ void __launch_bounds__(CSR_AW * 32, 3)
-    csr_block_kernel(CsrOperand A, CsrColMap M, int64_t nrows, const int32_t *S, int j0, int jc, KernelParams kp,
-                     const float *w32, const double *w64, const double *rs, double *g)
+__device__ __forceinline__ void csr_cta_setup(CtaSmem<T> &cs, WarpSmem<T> &ws, const CsrOperand &A,
+                                              const CsrColMap &M, const int32_t *S, int j0, int jc,
+                                              const KernelParams &kp, const float *w32, const double *w64)
 {
-    extern __shared__ __align__(16) unsigned char csr_sm[];
-    CtaSmem<T> &cs = *(CtaSmem<T> *)csr_sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<T> &ws = ((WarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>)))[warp];
-    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    const int lane = threadIdx.x & 31;
     const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
     const T gamma = (T)kp.gamma, coef0 = (T)kp.coef0;
     for (int j = threadIdx.x; j < jc; j += blockDim.x) {
@@ -217,8 +215,122 @@ __global__ void __launch_bounds__(CSR_AW * 32, 3)
         cs.base = KIND == DCD_LINEAR ? (T)0 : sw;
     }
     __syncthreads();
-    const uint32_t *bits = SBITS ? cs.bits : M.bits;
+}
+
+// The full pass over one tile of 32 rows starting at element e0 (n_e
+// elements): the tile's column indices are streamed as int4 quads (lane l:
+// indices 4 l .. 4 l + 3 of a 128-index chunk), the next group of CSR_PF
+// chunks loaded while the current one is tested against the column bitmap;
+// hits are listed in element order (warp prefix sum of the per-lane counts)
+// as offsets and columns, and flush_hits adds them into the row accumulators.
+template <typename T, bool SBITS>
+__device__ __forceinline__ void csr_tile_stream(const CsrOperand &A, const CsrColMap &M, WarpSmem<T> &ws,
+                                                const uint32_t *bits, const T *vals, int64_t e0, int n_e, int j0,
+                                                int jc, int lane, int nr, uint32_t &touched)
+{
+    const int lead = (int)(e0 & 3);  // quad-aligned start; offsets -3 .. -1 lie before the tile
+    int nh = 0;
+    int4 cur[CSR_PF], nxt[CSR_PF];
+#pragma unroll
+    for (int b = 0; b < CSR_PF; ++b)
+        cur[b] = -lead + 128 * b < n_e ? load_cols(A, e0 - lead + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
+    for (int ob = -lead; ob < n_e; ob += 128 * CSR_PF) {
+        const int obn = ob + 128 * CSR_PF;
+#pragma unroll
+        for (int b = 0; b < CSR_PF; ++b)  // the next group, in flight while this one is tested
+            nxt[b] = obn + 128 * b < n_e ? load_cols(A, e0 + obn + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int b = 0; b < CSR_PF; ++b) {
+            const int oq = ob + 128 * b + 4 * lane;  // offset of this lane's quad
+            const int32_t cc[4] = {cur[b].x, cur[b].y, cur[b].z, cur[b].w};
+            unsigned mk = 0;
+            if (ob + 128 * b >= 0 && ob + 128 * b + 128 <= n_e) {  // warp-uniform: the chunk lies in the tile
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t wd = SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5));
+                    mk |= ((wd >> (cc[q] & 31)) & 1u) << q;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = oq + q >= 0 && oq + q < n_e && cc[q] >= 0;
+                    if (in && ((SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5))) >> (cc[q] & 31)) & 1u)
+                        mk |= 1u << q;
+                }
+            }
+            if (!__any_sync(0xffffffffu, mk != 0)) continue;
+            // exclusive prefix of the per-lane hit counts = element order
+            const int cnt = __popc(mk);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (nh + total > CSR_HL) {
+                flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
+                nh = 0;
+            }
+            int pos = nh + incl - cnt;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((mk >> q) & 1u) {
+                    ws.hoff[pos] = oq + q;
+                    ws.hcol[pos] = cc[q];
+                    ++pos;
+                }
+            nh += total;
+        }
+#pragma unroll
+        for (int b = 0; b < CSR_PF; ++b) cur[b] = nxt[b];
+    }
+    flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
+}
+
+// Lane r's row t0 + r: the base term plus, over the touched columns in
+// ascending j, w_j (K_ij - K0_ij) (one FMA each); the accumulators return to
+// zero; g += rs * sum in FP64.
+template <typename T, int KIND>
+__device__ __forceinline__ void csr_row_finish(WarpSmem<T> &ws, const CtaSmem<T> &cs, const CsrOperand &A,
+                                               const KernelParams &kp, int64_t t0, int lane, int nr,
+                                               uint32_t touched, const double *rs, double *g)
+{
+    const T *norm = (const T *)(sizeof(T) == 8 ? (const void *)A.norm64 : (const void *)A.norm32);
+    const T gamma = (T)kp.gamma, coef0 = (T)kp.coef0;
     const T cd = KIND == DCD_POLY ? kfun_k<T, KIND>((T)0, (T)0, (T)0, false, gamma, coef0, kp.degree) : (T)0;
+    const int64_t row = t0 + lane;
+    if (lane < nr) {
+        const T na = KIND == DCD_RBF ? norm[row] : (T)0;
+        const T ea = KIND == DCD_RBF ? exp(-gamma * na) : (T)0;
+        T sum = KIND == DCD_RBF ? ea * cs.base : cs.base;
+        while (touched) {
+            const int j = __ffs(touched) - 1;
+            touched &= touched - 1;
+            const T kv = kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree);
+            const T k0 = KIND == DCD_RBF ? ea * cs.k0[j] : cd;
+            ws.acc[lane][j] = (T)0;
+            sum = fma(cs.w[j], kv - k0, sum);
+        }
+        g[row] += (rs ? rs[row] : 1.0) * (double)sum;
+    }
+    __syncwarp();
+}
+
+// Apply, full pass: one warp per tile of 32 consecutive rows, the tile's row
+// offsets for the next tile loaded while this one is streamed.
+template <typename T, int KIND, bool SBITS>
+__global__ void __launch_bounds__(CSR_AW * 32, 3)
+    csr_block_kernel(CsrOperand A, CsrColMap M, int64_t nrows, const int32_t *S, int j0, int jc, KernelParams kp,
+                     const float *w32, const double *w64, const double *rs, double *g)
+{
+    extern __shared__ __align__(16) unsigned char csr_sm[];
+    CtaSmem<T> &cs = *(CtaSmem<T> *)csr_sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<T> &ws = ((WarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>)))[warp];
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    csr_cta_setup<T, KIND, SBITS>(cs, ws, A, M, S, j0, jc, kp, w32, w64);
+    const uint32_t *bits = SBITS ? cs.bits : M.bits;
     const int64_t ntiles = (nrows + 31) / 32;
     const int64_t tstride = (int64_t)gridDim.x * CSR_AW;
     // row offsets of a tile: lane r holds row_ptr[t0 + r], every lane row_ptr[t0 + nr]; the next
@@ -241,83 +353,209 @@ __global__ void __launch_bounds__(CSR_AW * 32, 3)
         const int64_t e0 = __shfl_sync(0xffffffffu, rpv, 0);
         if (lane < nr) ws.rp[lane] = (int32_t)(rpv - e0);
         if (lane == 0) ws.rp[nr] = (int32_t)(rend - e0);
-        const int n_e = (int)(rend - e0);
-        const int lead = (int)(e0 & 3);  // quad-aligned start; offsets -3 .. -1 lie before the tile
-        int nh = 0;
         uint32_t touched = 0;
-        int4 cur[CSR_PF], nxt[CSR_PF];
+        csr_tile_stream<T, SBITS>(A, M, ws, bits, vals, e0, (int)(rend - e0), j0, jc, lane, nr, touched);
+        csr_row_finish<T, KIND>(ws, cs, A, kp, t0, lane, nr, touched, rs, g);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Apply through the transposed matrix.  With a CSC copy of A, the nonzeros a
+// step's kernel block actually needs -- a_ic with column c held by a sampled
+// row j -- are found by walking the sampled rows' columns: about
+// sum_j sum_{c in S_j} nnz(column c) "incidences" (i, element e, j), against
+// every nonzero of A for the full pass.  Per 32-column chunk:
+//   count    a warp per (sampled row j, its q-th nonzero): the column's
+//            entries counted per 32-row tile; the last CTA to finish scans
+//            the counts into tile offsets (and flags a total beyond the
+//            incidence buffer);
+//   scatter  the same walk writes key = (e << 5) | j and the product
+//            a_ie * a_{S_j},c into the tile's range (in arbitrary order);
+//   apply    a warp per tile sorts its incidences by key (rank sort in shared
+//            memory; keys are unique), so each row's products for each j come
+//            in element order -- the order of the full pass -- then forms the
+//            rows' sums exactly as the full pass does.  A tile with more
+//            incidences than its shared buffer, and every tile when the
+//            buffer overflowed, runs the full pass instead.
+// The result is bit-identical to the full pass.
+constexpr int CSC_TILE_CAP = 128;  // incidences per 32-row tile sorted in shared memory
+constexpr int CSC_COUNT_WARPS = 8;
+
+template <typename T>
+struct alignas(16) CscWarpSmem {
+    int64_t ukey[CSC_TILE_CAP], skey[CSC_TILE_CAP];
+    T uprod[CSC_TILE_CAP], sprod[CSC_TILE_CAP];
+};
+
+// The last CTA's exclusive scan of tile_cnt[0, ntiles) into tile_off (with
+// tile_off[ntiles] = total).
+__device__ void csc_scan_tiles(const CscStep &W, int64_t ntiles)
+{
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t run_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) run_base = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+        const int64_t t = b0 + threadIdx.x;
+        const int64_t v = t < ntiles ? (int64_t)__ldcg(W.tile_cnt + t) : 0;
+        int64_t incl = v;
 #pragma unroll
-        for (int b = 0; b < CSR_PF; ++b)
-            cur[b] = -lead + 128 * b < n_e ? load_cols(A, e0 - lead + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
-        for (int ob = -lead; ob < n_e; ob += 128 * CSR_PF) {
-            const int obn = ob + 128 * CSR_PF;
-#pragma unroll
-            for (int b = 0; b < CSR_PF; ++b)  // the next group, in flight while this one is tested
-                nxt[b] = obn + 128 * b < n_e ? load_cols(A, e0 + obn + 128 * b + 4 * lane) : make_int4(-1, -1, -1, -1);
-#pragma unroll
-            for (int b = 0; b < CSR_PF; ++b) {
-                const int oq = ob + 128 * b + 4 * lane;  // offset of this lane's quad
-                const int32_t cc[4] = {cur[b].x, cur[b].y, cur[b].z, cur[b].w};
-                unsigned mk = 0;
-                if (ob + 128 * b >= 0 && ob + 128 * b + 128 <= n_e) {  // warp-uniform: the chunk lies in the tile
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t wd = SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5));
-                        mk |= ((wd >> (cc[q] & 31)) & 1u) << q;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const bool in = oq + q >= 0 && oq + q < n_e && cc[q] >= 0;
-                        if (in && ((SBITS ? bits[cc[q] >> 5] : __ldg(bits + (cc[q] >> 5))) >> (cc[q] & 31)) & 1u)
-                            mk |= 1u << q;
-                    }
-                }
-                if (!__any_sync(0xffffffffu, mk != 0)) continue;
-                // exclusive prefix of the per-lane hit counts = element order
-                const int cnt = __popc(mk);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (nh + total > CSR_HL) {
-                    flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
-                    nh = 0;
-                }
-                int pos = nh + incl - cnt;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if ((mk >> q) & 1u) {
-                        ws.hoff[pos] = oq + q;
-                        ws.hcol[pos] = cc[q];
-                        ++pos;
-                    }
-                nh += total;
-            }
-#pragma unroll
-            for (int b = 0; b < CSR_PF; ++b) cur[b] = nxt[b];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        flush_hits(ws, nh, M, bits, vals, e0, j0, jc, lane, nr, touched);
-        const int64_t row = t0 + lane;
-        const bool live = lane < nr;
-        if (live) {
-            const T na = KIND == DCD_RBF ? norm[row] : (T)0;
-            const T ea = KIND == DCD_RBF ? exp(-gamma * na) : (T)0;
-            T sum = KIND == DCD_RBF ? ea * cs.base : cs.base;
-            while (touched) {
-                const int j = __ffs(touched) - 1;
-                touched &= touched - 1;
-                const T kv = kfun_k<T, KIND>(ws.acc[lane][j], na, cs.nb[j], cs.sj[j] == row, gamma, coef0, kp.degree);
-                const T k0 = KIND == DCD_RBF ? ea * cs.k0[j] : cd;
-                ws.acc[lane][j] = (T)0;
-                sum = fma(cs.w[j], kv - k0, sum);
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t x = lane < nw ? wsum[lane] : 0, xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
             }
-            g[row] += (rs ? rs[row] : 1.0) * (double)sum;
+            if (lane < nw) wsum[lane] = xi - x;
         }
-        __syncwarp();
+        __syncthreads();
+        const int64_t base = run_base;
+        if (t < ntiles) W.tile_off[t] = base + wsum[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) run_base = base + wsum[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int64_t total = run_base;
+        W.tile_off[ntiles] = total;
+        *W.ovf = total > W.cap ? 1 : 0;
+        *W.ticket = 0u;
+    }
+}
+
+// the q-th nonzero of sampled position j (element index), or -1
+__device__ __forceinline__ int64_t sampled_elem(const CsrOperand &A, const int32_t *S, int j, int q)
+{
+    const int64_t r = S[j];
+    if (r < 0 || r >= A.m) return -1;
+    const int64_t e = A.row_ptr[r] + q;
+    return e < A.row_ptr[r + 1] ? e : -1;
+}
+
+__global__ void __launch_bounds__(CSC_COUNT_WARPS * 32)
+    csc_count_kernel(CsrOperand A, CscOperand C, const int32_t *S, int j0, int jc, int maxrow, CscStep W,
+                     int64_t ntiles)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * CSC_COUNT_WARPS, total = (int64_t)jc * maxrow;
+    for (int64_t u = (int64_t)blockIdx.x * CSC_COUNT_WARPS + (threadIdx.x >> 5); u < total; u += nwarps) {
+        const int j = (int)(u / maxrow), q = (int)(u % maxrow);
+        const int64_t e = sampled_elem(A, S, j0 + j, q);
+        if (e < 0) continue;
+        const int32_t c = A.col_idx[e];
+        const int64_t k1 = C.col_ptr[c + 1];
+        for (int64_t k = C.col_ptr[c] + lane; k < k1; k += 32) atomicAdd(W.tile_cnt + (C.row[k] >> 5), 1);
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(W.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    csc_scan_tiles(W, ntiles);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CSC_COUNT_WARPS * 32)
+    csc_scatter_kernel(CsrOperand A, CscOperand C, const int32_t *S, int j0, int jc, int maxrow, CscStep W)
+{
+    if (*W.ovf) return;
+    const int lane = threadIdx.x & 31;
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    const T *cval = (const T *)C.val;
+    T *prod = (T *)W.prod;
+    const int64_t nwarps = (int64_t)gridDim.x * CSC_COUNT_WARPS, total = (int64_t)jc * maxrow;
+    for (int64_t u = (int64_t)blockIdx.x * CSC_COUNT_WARPS + (threadIdx.x >> 5); u < total; u += nwarps) {
+        const int j = (int)(u / maxrow), q = (int)(u % maxrow);
+        const int64_t e = sampled_elem(A, S, j0 + j, q);
+        if (e < 0) continue;
+        const int32_t c = A.col_idx[e];
+        const T a = vals[e];
+        const int64_t k1 = C.col_ptr[c + 1];
+        for (int64_t k = C.col_ptr[c] + lane; k < k1; k += 32) {
+            const int32_t t = C.row[k] >> 5;
+            const int64_t pos = (int64_t)W.tile_off[t] + atomicAdd(W.tile_cur + t, 1);
+            W.key[pos] = (C.elem[k] << 5) | j;
+            prod[pos] = mul_rn(cval[k], a);  // the full pass's product: a_ie * a_{S_j},c rounded in T
+        }
+    }
+}
+
+template <typename T, int KIND, bool SBITS>
+__global__ void __launch_bounds__(CSR_AW * 32, 2)
+    csc_apply_kernel(CsrOperand A, CsrColMap M, CscStep W, int64_t nrows, const int32_t *S, int j0, int jc,
+                     KernelParams kp, const float *w32, const double *w64, const double *rs, double *g)
+{
+    extern __shared__ __align__(16) unsigned char csr_sm[];
+    CtaSmem<T> &cs = *(CtaSmem<T> *)csr_sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<T> &ws = ((WarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>)))[warp];
+    CscWarpSmem<T> &xs =
+        ((CscWarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>) + sizeof(WarpSmem<T>) * CSR_AW))[warp];
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    const T *prod = (const T *)W.prod;
+    csr_cta_setup<T, KIND, SBITS>(cs, ws, A, M, S, j0, jc, kp, w32, w64);
+    const uint32_t *bits = SBITS ? cs.bits : M.bits;
+    const bool ovf = *W.ovf != 0;
+    const int64_t ntiles = (nrows + 31) / 32;
+    for (int64_t tile = (int64_t)blockIdx.x * CSR_AW + warp; tile < ntiles; tile += (int64_t)gridDim.x * CSR_AW) {
+        const int64_t t0 = tile * 32;
+        const int nr = (int)min((int64_t)32, nrows - t0);
+        const int64_t o0 = W.tile_off[tile];
+        const int nt = (int)(W.tile_off[tile + 1] - o0);
+        const int64_t rpv = lane < nr ? A.row_ptr[t0 + lane] : 0, rend = A.row_ptr[t0 + nr];
+        const int64_t e0 = __shfl_sync(0xffffffffu, rpv, 0);
+        uint32_t touched = 0;
+        if (ovf || nt > CSC_TILE_CAP) {  // the full pass over this tile
+            if (lane < nr) ws.rp[lane] = (int32_t)(rpv - e0);
+            if (lane == 0) ws.rp[nr] = (int32_t)(rend - e0);
+            csr_tile_stream<T, SBITS>(A, M, ws, bits, vals, e0, (int)(rend - e0), j0, jc, lane, nr, touched);
+        } else if (nt > 0) {
+            for (int x = lane; x < nt; x += 32) {
+                xs.ukey[x] = W.key[o0 + x];
+                xs.uprod[x] = prod[o0 + x];
+            }
+            __syncwarp();
+            for (int x = lane; x < nt; x += 32) {  // rank sort: keys are unique
+                const int64_t kx = xs.ukey[x];
+                int p = 0;
+                for (int y = 0; y < nt; ++y) p += xs.ukey[y] < kx ? 1 : 0;
+                xs.skey[p] = kx;
+                xs.sprod[p] = xs.uprod[x];
+            }
+            __syncwarp();
+            if (lane < nr) {
+                const int64_t lo = rpv << 5, hi = (lane + 1 < nr ? A.row_ptr[t0 + lane + 1] : rend) << 5;
+                int a = 0, b = nt;  // first key >= lo
+                while (a < b) {
+                    const int mid = (a + b) >> 1;
+                    if (xs.skey[mid] < lo) a = mid + 1;
+                    else b = mid;
+                }
+                for (int h = a; h < nt && xs.skey[h] < hi; ++h) {
+                    const int j = (int)(xs.skey[h] & 31);
+                    ws.acc[lane][j] += xs.sprod[h];
+                    touched |= 1u << j;
+                }
+            }
+            __syncwarp();
+        }
+        csr_row_finish<T, KIND>(ws, cs, A, kp, t0, lane, nr, touched, rs, g);
+        if (lane == 0) {  // the counters return to zero for the next chunk
+            W.tile_cnt[tile] = 0;
+            W.tile_cur[tile] = 0;
+        }
     }
 }
 
@@ -356,7 +594,7 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
                 if (q1 - q0 == 1) {
                     const int j = M.ent_j[q0] - j0;
                     jj = j >= 0 && j < jc ? j : -1;
-                    prod = v * (T)M.ent_v[q0];
+                    prod = mul_rn(v, (T)M.ent_v[q0]);
                 } else {
                     jj = -2 - slot;
                     prod = v;
@@ -375,7 +613,7 @@ __global__ void __launch_bounds__(CSR_WARPS * 32)
                     const int sl = -2 - js;
                     for (int q = M.slot_off[sl] + lane; q < M.slot_off[sl + 1]; q += 32) {
                         const int j = M.ent_j[q] - j0;
-                        if (j >= 0 && j < jc) acc[warp][j] += ps * (T)M.ent_v[q];
+                        if (j >= 0 && j < jc) acc[warp][j] += mul_rn(ps, (T)M.ent_v[q]);
                     }
                 }
                 __syncwarp();
@@ -613,6 +851,131 @@ cudaError_t launch_csr_gram(const CsrOperand &A, const CsrColMap &M, const int32
     return cudaSuccess;
 }
 
+// CSC build (once per operand): entries per column, their exclusive scan, and
+// the entries themselves (row, CSR element index, value) in arbitrary order
+// within a column -- the apply sorts by element index.
+__global__ void csc_colcount_kernel(CsrOperand A, int32_t *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= A.m) return;
+    for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) atomicAdd(cnt + A.col_idx[e], 1);
+}
+
+// One CTA: off[i] = sum_{q < i} cnt[q] for i <= count, *maxv = max cnt.
+__global__ void __launch_bounds__(1024) excl_scan_kernel(const int32_t *cnt, int64_t count, int64_t *off, int *maxv)
+{
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t run_base;
+    __shared__ int mx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        run_base = 0;
+        mx = 0;
+    }
+    __syncthreads();
+    int lmax = 0;
+    for (int64_t b0 = 0; b0 < count; b0 += blockDim.x) {
+        const int64_t t = b0 + threadIdx.x;
+        const int64_t v = t < count ? (int64_t)cnt[t] : 0;
+        lmax = max(lmax, (int)v);
+        int64_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t x = lane < nw ? wsum[lane] : 0, xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
+            }
+            if (lane < nw) wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        const int64_t base = run_base;
+        if (t < count) off[t] = base + wsum[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) run_base = base + wsum[warp] + incl;
+        __syncthreads();
+    }
+    atomicMax(&mx, lmax);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        off[count] = run_base;
+        *maxv = mx;
+    }
+}
+
+template <typename T>
+__global__ void csc_fill_kernel(CsrOperand A, const int64_t *col_ptr, int32_t *cur, int32_t *row, int64_t *elem,
+                                T *val)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= A.m) return;
+    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
+    for (int64_t e = A.row_ptr[r] + lane; e < A.row_ptr[r + 1]; e += 32) {
+        const int32_t c = A.col_idx[e];
+        const int64_t pos = col_ptr[c] + atomicAdd(cur + c, 1);
+        row[pos] = (int32_t)r;
+        elem[pos] = e;
+        val[pos] = vals[e];
+    }
+}
+
+template <typename T, int KIND, bool SBITS>
+cudaError_t launch_csc_apply_k(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
+                               int maxrow, const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
+                               const double *w64, const double *rs, double *g, cudaStream_t st)
+{
+    auto kfn = csc_apply_kernel<T, KIND, SBITS>;
+    const size_t smem = sizeof(CtaSmem<T>) + (sizeof(WarpSmem<T>) + sizeof(CscWarpSmem<T>)) * CSR_AW;
+    static int per_sm = 0;  // resident CTAs per SM, queried once per instantiation (before any capture)
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, CSR_AW * 32, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t ntiles = (A.m + 31) / 32;
+    int64_t grid = (ntiles + CSR_AW - 1) / CSR_AW;
+    if (grid > (int64_t)sm_count() * per_sm) grid = (int64_t)sm_count() * per_sm;
+    for (int64_t j0 = 0; j0 < ncols; j0 += CSR_JC) {
+        const int jc = (int)min((int64_t)CSR_JC, ncols - j0);
+        const int64_t pairs = (int64_t)jc * maxrow;
+        int64_t cgrid = (pairs + CSC_COUNT_WARPS - 1) / CSC_COUNT_WARPS;
+        if (cgrid < 1) cgrid = 1;
+        if (cgrid > (int64_t)sm_count() * 8) cgrid = (int64_t)sm_count() * 8;
+        csc_count_kernel<<<(unsigned)cgrid, CSC_COUNT_WARPS * 32, 0, st>>>(A, C, S, (int)j0, jc, maxrow, W, ntiles);
+        csc_scatter_kernel<T><<<(unsigned)cgrid, CSC_COUNT_WARPS * 32, 0, st>>>(A, C, S, (int)j0, jc, maxrow, W);
+        kfn<<<(unsigned)grid, CSR_AW * 32, smem, st>>>(A, M, W, A.m, S, (int)j0, jc, kp, w32, w64, rs, g);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_csc_apply(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
+                             int maxrow, const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
+                             const double *w64, const double *rs, double *g, cudaStream_t st)
+{
+    const bool sb = M.nw <= CSR_SMEM_BITS;
+#define CSC_K(KD)                                                                                              \
+    return sb ? launch_csc_apply_k<T, KD, true>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)        \
+              : launch_csc_apply_k<T, KD, false>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)
+    if (kp.kind == DCD_RBF) CSC_K(DCD_RBF);
+    if (kp.kind == DCD_POLY) CSC_K(DCD_POLY);
+    CSC_K(DCD_LINEAR);
+#undef CSC_K
+}
+
 }  // namespace
 
 size_t csr_colmap_bytes(int64_t n, int64_t cap)
@@ -684,6 +1047,94 @@ cudaError_t launch_csr_block(const CsrOperand &A, const CsrColMap &M, bool fp64,
     Av.vec = ((uintptr_t)A.col_idx & 15) == 0 && ((uintptr_t)vp & 15) == 0;
     return fp64 ? launch_csr_apply<double>(Av, M, nrows, S, ncols, kp, w32, w64, rs, g, st)
                 : launch_csr_apply<float>(Av, M, nrows, S, ncols, kp, w32, w64, rs, g, st);
+}
+
+namespace {
+size_t take_bytes(char *&p, size_t bytes)
+{
+    const size_t a = (bytes + 255) / 256 * 256;
+    p += a;
+    return a;
+}
+}  // namespace
+
+size_t csc_bytes(int64_t n, int64_t nnz, bool fp64)
+{
+    return (size_t)(n + 1) * 8 + (size_t)n * 4 + (size_t)nnz * (4 + 8 + (fp64 ? 8 : 4)) + 256 * 5;
+}
+
+cudaError_t launch_csc_build(const CsrOperand &A, bool fp64, void *base, CscOperand *C, int *maxcol_dev,
+                             cudaStream_t st)
+{
+    char *p = (char *)base;
+    int64_t *col_ptr = (int64_t *)p;
+    take_bytes(p, (size_t)(A.n + 1) * 8);
+    int32_t *cnt = (int32_t *)p;
+    take_bytes(p, (size_t)A.n * 4);
+    int32_t *row = (int32_t *)p;
+    take_bytes(p, (size_t)A.nnz * 4);
+    int64_t *elem = (int64_t *)p;
+    take_bytes(p, (size_t)A.nnz * 8);
+    void *val = p;
+    C->col_ptr = col_ptr;
+    C->row = row;
+    C->elem = elem;
+    C->val = val;
+    C->n = A.n;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)A.n * 4, st);
+    if (e != cudaSuccess) return e;
+    if (A.m > 0) {
+        const unsigned blocks = (unsigned)((A.m * 32 + 255) / 256);
+        csc_colcount_kernel<<<blocks, 256, 0, st>>>(A, cnt);
+    }
+    excl_scan_kernel<<<1, 1024, 0, st>>>(cnt, A.n, col_ptr, maxcol_dev);
+    if ((e = cudaMemsetAsync(cnt, 0, (size_t)A.n * 4, st)) != cudaSuccess) return e;
+    if (A.m > 0) {
+        const unsigned blocks = (unsigned)((A.m * 32 + 255) / 256);
+        if (fp64) csc_fill_kernel<double><<<blocks, 256, 0, st>>>(A, col_ptr, cnt, row, elem, (double *)val);
+        else csc_fill_kernel<float><<<blocks, 256, 0, st>>>(A, col_ptr, cnt, row, elem, (float *)val);
+    }
+    return cudaGetLastError();
+}
+
+size_t csc_step_bytes(int64_t m, int64_t cap, bool fp64)
+{
+    const int64_t ntiles = (m + 31) / 32;
+    return (size_t)ntiles * 8 + (size_t)(ntiles + 1) * 8 + 512 + (size_t)cap * (8 + (fp64 ? 8 : 4)) + 256 * 6;
+}
+
+CscStep csc_step_carve(void *base, int64_t m, int64_t cap)
+{
+    const int64_t ntiles = (m + 31) / 32;
+    char *p = (char *)base;
+    CscStep W;
+    W.tile_cnt = (int32_t *)p;
+    take_bytes(p, (size_t)ntiles * 4);
+    W.tile_cur = (int32_t *)p;
+    take_bytes(p, (size_t)ntiles * 4);
+    W.tile_off = (int64_t *)p;
+    take_bytes(p, (size_t)(ntiles + 1) * 8);
+    W.ticket = (unsigned *)p;
+    take_bytes(p, 256);
+    W.ovf = (int *)p;
+    take_bytes(p, 256);
+    W.key = (int64_t *)p;
+    take_bytes(p, (size_t)cap * 8);
+    W.prod = p;
+    W.cap = cap;
+    return W;
+}
+
+cudaError_t launch_csr_apply_csc(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
+                                 bool fp64, int maxrow, const KernelParams &kp, const int32_t *S, int64_t ncols,
+                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st)
+{
+    if (ncols <= 0 || A.m <= 0) return cudaSuccess;
+    CsrOperand Av = A;
+    const void *vp = fp64 ? (const void *)A.vals64 : (const void *)A.vals32;
+    Av.vec = ((uintptr_t)A.col_idx & 15) == 0 && ((uintptr_t)vp & 15) == 0;
+    return fp64 ? launch_csc_apply<double>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)
+                : launch_csc_apply<float>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st);
 }
 
 }  // namespace dcd

@@ -271,6 +271,38 @@ CsrColMap csr_colmap_carve(void *base, int64_t n, int64_t cap);
 cudaError_t launch_csr_prep(const CsrOperand &A, int *bad, int *maxlen, cudaStream_t st);
 cudaError_t launch_csr_colmap(const CsrOperand &A, const int32_t *S, int64_t cnt, const CsrColMap &M, int *err,
                               cudaStream_t st);
+// Transposed copy of a CSR operand: per column its entries' rows, CSR element
+// indices and values (in the block's precision), and per-step scratch of the
+// apply through it (tile counters and offsets, the incidence buffer of
+// capacity `cap`); counters zero between uses.
+struct CscOperand {
+    const int64_t *col_ptr = nullptr;
+    const int32_t *row = nullptr;
+    const int64_t *elem = nullptr;
+    const void *val = nullptr;
+    int64_t n = 0;
+};
+struct CscStep {
+    int32_t *tile_cnt = nullptr, *tile_cur = nullptr;
+    int64_t *tile_off = nullptr;
+    unsigned *ticket = nullptr;
+    int *ovf = nullptr;
+    int64_t *key = nullptr;
+    void *prod = nullptr;
+    int64_t cap = 0;
+};
+size_t csc_bytes(int64_t n, int64_t nnz, bool fp64);
+// builds the copy in `base` (csc_bytes); *maxcol_dev receives the longest column
+cudaError_t launch_csc_build(const CsrOperand &A, bool fp64, void *base, CscOperand *C, int *maxcol_dev,
+                             cudaStream_t st);
+size_t csc_step_bytes(int64_t m, int64_t cap, bool fp64);
+CscStep csc_step_carve(void *base, int64_t m, int64_t cap);  // base zeroed by the caller
+// the apply form of launch_csr_block over all m rows through the transposed
+// copy (bit-identical to the full pass); M is the step's column map (used by
+// tiles that fall back to the full pass); maxrow = the longest row
+cudaError_t launch_csr_apply_csc(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
+                                 bool fp64, int maxrow, const KernelParams &kp, const int32_t *S, int64_t ncols,
+                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st);
 // apply (out == nullptr): g[i] += rs[i] * sum_j K(a_i, a_{S_j}) w_j for i < nrows (rows == nullptr);
 // store: out[r*ldo + j] = K(a_{rows[r]}, a_{S_j}) (rows == nullptr: row r).  FP64 (w64, out
 // double) or FP32 (w32, out float).

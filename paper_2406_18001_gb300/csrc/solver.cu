@@ -63,6 +63,16 @@ dcd_status validate_dense(const dcd_matrix *A)
 
 namespace {
 
+// The transposed copy of a CSR operand and the per-step scratch of the apply
+// through it, kept when a step's incidences -- expected jc * (nnz / m) *
+// sum_c nnz_c^2 / nnz per chunk of jc sampled rows whose columns follow the
+// nonzeros -- stay below nnz / 16 (an incidence costs about 16 times the full
+// pass's 4 bytes per nonzero); else nothing is kept.  The incidence buffer
+// holds 4x the expectation (at most the worst case); a chunk beyond it runs
+// the full pass.  maxcol_dev: one device int of scratch.
+dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t jc, int maxrow, int *maxcol_dev, void **ws_csc,
+                      CscOperand *C, void **ws_step, CscStep *W, bool *use, cudaStream_t st);
+
 constexpr int64_t SB_MAX = 8192;   // s*b per outer step
 constexpr int B_MAX = 128;         // block size
 
@@ -98,6 +108,41 @@ dcd_status cuda_status(cudaError_t e)
         cudaError_t e_ = (expr);                        \
         if (e_ != cudaSuccess) return cuda_status(e_);  \
     } while (0)
+
+dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t jc, int maxrow, int *maxcol_dev, void **ws_csc,
+                      CscOperand *C, void **ws_step, CscStep *W, bool *use, cudaStream_t st)
+{
+    *use = false;
+    const int64_t m = ca.m, n = ca.n;
+    if (ca.nnz <= 0 || m <= 0 || jc <= 0) return DCD_OK;
+    DCD_TRY(malloc_async(ws_csc, csc_bytes(n, ca.nnz, fp64), st));
+    DCD_TRY(launch_csc_build(ca, fp64, *ws_csc, C, maxcol_dev, st));
+    std::vector<int64_t> cp((size_t)n + 1);
+    int maxcol = 0;
+    DCD_TRY(cudaMemcpyAsync(cp.data(), C->col_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+    DCD_TRY(cudaMemcpyAsync(&maxcol, maxcol_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DCD_TRY(cudaStreamSynchronize(st));
+    double sq = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+        const double k = (double)(cp[c + 1] - cp[c]);
+        sq += k * k;
+    }
+    const double nnzd = (double)ca.nnz;
+    const double expect = (double)jc * (nnzd / (double)m) * (sq / nnzd);
+    const double worst = (double)jc * maxrow * maxcol;
+    if (16.0 * expect > nnzd) {
+        DCD_TRY(cudaFreeAsync(*ws_csc, st));
+        *ws_csc = nullptr;
+        return DCD_OK;
+    }
+    const int64_t cap = (int64_t)std::max(1.0, std::min(worst, std::max(4.0 * expect, 1048576.0)));
+    const size_t sbytes = csc_step_bytes(m, cap, fp64);
+    DCD_TRY(malloc_async(ws_step, sbytes, st));
+    DCD_TRY(cudaMemsetAsync(*ws_step, 0, sbytes, st));
+    *W = csc_step_carve(*ws_step, m, cap);
+    *use = true;
+    return DCD_OK;
+}
 
 size_t dtype_size(int dt) { return dt == DCD_F64 ? 8 : dt == DCD_F32 ? 4 : dt == DCD_BF16 ? 2 : 1; }
 
@@ -214,6 +259,12 @@ struct Solver {
     CsrOperand ca;
     CsrColMap cm;
     void *ws_csr = nullptr;
+    // the apply through the transposed copy (chosen at set-up when it reads far less than a full pass)
+    bool use_csc = false;
+    CscOperand cscop;
+    CscStep cstep;
+    void *ws_csc = nullptr, *ws_cstep = nullptr;
+    int csr_maxrow = 0;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
     float *col_s = nullptr;       // fp8: scales of the sampled rows
@@ -243,6 +294,8 @@ struct Solver {
         if (la_fork) cudaEventDestroy(la_fork);
         if (la_join) cudaEventDestroy(la_join);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
+        if (ws_csc) cudaFreeAsync(ws_csc, st);
+        if (ws_cstep) cudaFreeAsync(ws_cstep, st);
         if (ws) cudaFreeAsync(ws, st);
     }
 
@@ -360,7 +413,7 @@ struct Solver {
             // the balanced split of the tensor-core apply over CTA pairs
             double *tsp = (double *)ar.take(tcd ? sizeof(double) * tc_split_part_elems(split_pairs, split_chunks) : 0);
             unsigned *tsc = (unsigned *)ar.take(tcd ? sizeof(unsigned) * 2 * split_pairs : 0);
-            int *er = (int *)ar.take(sizeof(int) * 4);
+            int *er = (int *)ar.take(sizeof(int) * 8);
             double *pt = (double *)ar.take(sizeof(double) * 4 * 256);
             double *rs = (double *)ar.take(sizeof(double) * 4);
             int64_t ichunk = std::min<int64_t>(m, SB_MAX);
@@ -459,7 +512,7 @@ struct Solver {
             }
         }
         const void *vals = host ? h_vals : A->values;
-        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 4, st));
+        DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int) * 8, st));
         if (tcd) DCD_TRY(cudaMemsetAsync(tsplit.cnt, 0, sizeof(unsigned) * 2 * split_pairs, st));
         DCD_TRY(cudaMemsetAsync(col_h, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
@@ -501,6 +554,11 @@ struct Solver {
             DCD_TRY(malloc_async(&ws_csr, cmb, st));
             DCD_TRY(cudaMemsetAsync(ws_csr, 0, cmb, st));
             cm = csr_colmap_carve(ws_csr, n, cap);
+            csr_maxrow = h[1];
+            if (!(o.flags & DCD_FLAG_CSR_FULL_PASS) && !literal) {
+                dcd_status cs = setup_csc();
+                if (cs != DCD_OK) return cs;
+            }
         } else if (tc) {
             op.n_pad = n_pad;
             op.kind = pack_kind(o.prec);
@@ -734,8 +792,19 @@ struct Solver {
         return e;
     }
 
+    dcd_status setup_csc()
+    {
+        bool use = false;
+        dcd_status r = csc_choose(ca, !tc, std::min<int64_t>(sb, 32), csr_maxrow, err + 4, &ws_csc, &cscop, &ws_cstep,
+                                  &cstep, &use, st);
+        use_csc = use;
+        return r;
+    }
+
     cudaError_t csr_apply(int64_t ncols, const double *rs)
     {
+        if (use_csc)
+            return launch_csr_apply_csc(ca, cm, cscop, cstep, !tc, csr_maxrow, kp, S, ncols, col_w, w64, rs, g, st);
         return launch_csr_block(ca, cm, !tc, kp, nullptr, m, S, ncols, col_w, w64, rs, g, nullptr, 0, st);
     }
 
@@ -1481,6 +1550,20 @@ dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int3
     DCD_TRY(launch_csr_colmap(ca, cols, ncols, cm, err, st));
     float *w32 = (w && !fp64) ? (float *)(base + ow) : nullptr;
     if (w32) DCD_TRY(launch_f64_to_f32(w, ncols, w32, st));
+    if (!out && !rows && nrows == m) {  // the apply over every row: through the transposed copy when it pays
+        ComponentBufs cb3, cb4;
+        cb3.st = cb4.st = st;
+        CscOperand C;
+        CscStep W;
+        bool use = false;
+        dcd_status cs = csc_choose(ca, fp64, std::min<int64_t>(ncols, 32), h[1], err + 1, &cb3.mem, &C, &cb4.mem, &W,
+                                   &use, st);
+        if (cs != DCD_OK) return cs;
+        if (use) {
+            DCD_TRY(launch_csr_apply_csc(ca, cm, C, W, fp64, h[1], kp, cols, ncols, w32, w, rs, g, st));
+            return finish_component(err, st);
+        }
+    }
     DCD_TRY(launch_csr_block(ca, cm, fp64, kp, rows, nrows, cols, ncols, w32, w, rs, g, out, ldo, st));
     return finish_component(err, st);
 }
