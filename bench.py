@@ -45,6 +45,15 @@ NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64, "89d134a9821018ef"): 109.13e6,
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 
+def emit(out, args):
+    """Prints a workload's JSON line, or collects it (the side summaries of
+    the default line)."""
+    if getattr(args, "collect", None) is not None:
+        args.collect.append(out)
+    else:
+        print(json.dumps(out), flush=True)
+
+
 def kernel_source_sha16():
     import hashlib
     path = os.path.join(ROOT, "paper_2406_18001_gb300", "csrc", "block_tc.cu")
@@ -541,6 +550,8 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
                "phase_ms": phase,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary(), "time_to_tol": ttt, "error_vs_oracle": herr, "literal_order": lit}
+        if ws == 1 and not args.no_also:
+            out["also"] = side_summaries(args)
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -548,6 +559,46 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
 
 
 # ------------------------------------------------------- one kernel block --
+def side_summaries(args):
+    """The other workloads, measured after the headline's timed region at the
+    same --steps (at least 4) with their throughput and roofline only (no CPU
+    baseline, no time-to-tolerance, FP8 without its subproblem errors and
+    end-to-end run): config 1 (K-SVM blobs, FP64 s = 8), config 3 (K-SVM on
+    CSR, block through the transposed copy, the full pass beside it), config 4
+    (batched sweep at a fixed budget) and config 5 (FP8 stress).  A workload
+    that fails reports its error instead."""
+    import copy
+    out = {}
+    for name, fn, extra in (("ksvm_blobs_fp64", run_gpu_svm, {}),
+                            ("ksvm_csr", run_gpu_csr, {"prec": "bf16x3"}),
+                            ("krr_sweep", run_gpu_sweep, {"sweep_tol": 0.0}),
+                            ("krr_fp8", run_gpu_fp8, {})):
+        a = copy.copy(args)
+        a.no_cpu, a.no_ttt, a.summary, a.collect, a.s_set = True, True, True, [], False
+        a.steps = max(4, args.steps)
+        for key, v in extra.items():
+            setattr(a, key, v)
+        try:
+            fn(a)
+            line = a.collect[-1]
+        except Exception as e:  # keep the headline line whatever happens here
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            continue
+        roof = line.get("roofline") or {}
+        ent = {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+               "ms_per_step": line["ms_per_step"], "dtype": line["dtype"],
+               "block_ms": (line.get("phase_ms") or {}).get("block"),
+               "roofline": {k: roof.get(k) for k in ("bound", "achieved", "peak", "unit", "frac")},
+               "clocks": line.get("clocks")}
+        if "moved" in roof:
+            ent["roofline"]["moved"] = roof["moved"]
+            ent["roofline"]["full_pass"] = roof["full_pass"]
+        if "bf16_storage" in line:
+            ent["bf16_storage_value"] = line["bf16_storage"]["value"]
+        out[name] = ent
+    return out
+
+
 def run_block(args):
     """A few fused kernel-block launches (dcd_kernel_block_apply) at the
     headline shape (m rows, n features, s*b sampled columns, RBF) in one
@@ -702,7 +753,7 @@ def run_gpu_svm(args):
                "forms": {"s1": res[1], "s8": res[8]}, "time_to_gap": ttg,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r8["kernels_per_step"] * args.steps,
                "clocks": clk.summary()}
-        print(json.dumps(out), flush=True)
+        emit(out, args)
 
 
 # ------------------------------------------------------------------ CSR -----
@@ -774,30 +825,23 @@ def run_gpu_csr(args):
         st, _ = plan.run(0)
         launches = st["gpu_launches_per_step"] * args.steps
         plan.close()
-        plan2 = B.Plan(0, A, y, k, 0.5, 1, s, (args.roof_steps + 4) * s, seed=rank + 1, prec=args.prec, loss=2,
-                       flags=B.FLAG_PHASE_TIMERS)
-        plan2.run(2)
-        base, _ = plan2.run(0)
-        for _ in range(args.roof_steps):
-            flush.zero_()
-            plan2.run(1)
-        st2, _ = plan2.run(0)
-        plan2.close()
-        phase = {ph: (st2[f"ms_{ph}"] - base[f"ms_{ph}"]) / args.roof_steps for ph in
-                 ("sample", "gram", "recur", "block", "update")}
-        nnz = int(p.row_ptr[-1])
+        def phases(flags):
+            pl = B.Plan(0, A, y, k, 0.5, 1, s, (args.roof_steps + 4) * s, seed=rank + 1, prec=args.prec, loss=2,
+                        flags=B.FLAG_PHASE_TIMERS | flags)
+            pl.run(2)
+            base, _ = pl.run(0)
+            for _ in range(args.roof_steps):
+                flush.zero_()
+                pl.run(1)
+            st2, _ = pl.run(0)
+            pl.close()
+            return {ph: (st2[f"ms_{ph}"] - base[f"ms_{ph}"]) / args.roof_steps for ph in
+                    ("sample", "gram", "recur", "block", "update")}
+
+        phase = phases(0)
+        phase_full = phases(B.FLAG_CSR_FULL_PASS)
         fp64 = args.prec == "fp64"
-        vb = 8 if fp64 else 4
-        # column indices of every nonzero, values of the hits only (nonzeros in a column some sampled row
-        # touches: expected nnz * touched / n for uniform columns), offsets, g read + write, y
-        touched = p.n * (1.0 - (1.0 - args.csr_nnz / p.n) ** s)
-        hits = nnz * touched / p.n
-        bytes_ = nnz * 4 + hits * vb + (p.m + 1) * 8 + p.m * (8 + 8 + 8)
-        hbm_peak, _, _, src = peaks()
-        achieved = bytes_ / (phase["block"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "peak_source": src, "kernel": "csr_block_kernel (CSR kernel block + gradient update)",
-                "algorithmic": {"bytes_per_launch": bytes_, "expected_hits": hits, "launch_ms": phase["block"]}}
+        roof = csr_roofline(p, s, fp64, phase["block"], phase_full["block"])
         # end to end through the C ABI with host arrays
         Ah = B.Csr(p.row_ptr, p.col_idx, p.values, p.n)
         yh = p.y.copy()
@@ -820,9 +864,43 @@ def run_gpu_csr(args):
                "config": {"workload": WORKLOAD_CSR, "m": p.m, "n": p.n, "nnz_per_row": args.csr_nnz, "s": s, "b": 1,
                           "precision": args.prec + (" (CSR block: FP64)" if fp64 else " (CSR block: FP32 CUDA cores)"),
                           "l2": "256 MB buffer written before every timed step; steps timed alone"},
-               "phase_ms": phase, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary()}
-        print(json.dumps(out), flush=True)
+               "phase_ms": phase, "phase_ms_full_pass": phase_full, "roofline": roof, "cpu_baseline": cpu,
+               "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+        emit(out, args)
+
+
+def csr_roofline(p, s, fp64, t_block, t_full):
+    """The CSR kernel block against HBM.  The full pass's algorithmic bytes
+    per outer step are one read of every column index and value of A, its
+    row offsets, and g read and written with y read (nnz (4 + 4|8) + (m + 1) 8
+    + m 24).  The block runs through the transposed copy, which reads only the
+    incidences: for each sampled row j and column c it holds, the entries of
+    column c (expected s (nnz / m) sum_c nnz_c^2 / nnz of them); each costs
+    its CSC row index twice (count, scatter), element index and value once,
+    and its key and product written and read back (4 + 4 + 8 + v + 2 (8 + v)
+    bytes), plus per row the offsets, g read and written and y (32 bytes).
+    `achieved` is the full pass's bytes over the transposed block's time (the
+    effective rate); `moved` is the transposed block's own bytes over its time;
+    `full_pass` times the full pass (forced) on the same steps."""
+    hbm_peak, _, _, src = peaks()
+    nnz, m = int(p.row_ptr[-1]), p.m
+    vb = 8 if fp64 else 4
+    full_bytes = nnz * (4 + vb) + (m + 1) * 8 + m * 24
+    cnt = np.bincount(p.col_idx, minlength=p.n).astype(np.float64)
+    inc = min(s, 32) * (nnz / m) * float(np.sum(cnt * cnt)) / nnz * (-(-s // 32))
+    moved = inc * (4 + 4 + 8 + vb + 2 * (8 + vb)) + m * 32
+    eff = full_bytes / (t_block * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": eff, "peak": hbm_peak, "unit": "GB/s", "frac": eff / hbm_peak,
+            "traffic": None, "peak_source": src,
+            "kernel": "CSR kernel block + gradient update through the transposed copy (csc_count, csc_scatter, "
+                      "csc_apply per 32 sampled columns)",
+            "algorithmic": {"bytes_per_launch": full_bytes, "launch_ms": t_block,
+                            "rule": "the full pass's bytes (every column index and value, offsets, g r/w, y) over "
+                                    "the transposed block's time: its effective rate"},
+            "moved": {"bytes_per_launch": moved, "expected_incidences": inc,
+                      "achieved": moved / (t_block * 1e-3) / 1e9, "frac": moved / (t_block * 1e-3) / 1e9 / hbm_peak},
+            "full_pass": {"launch_ms": t_full, "achieved": full_bytes / (t_full * 1e-3) / 1e9,
+                          "frac": full_bytes / (t_full * 1e-3) / 1e9 / hbm_peak}}
 
 
 # ------------------------------------------------------------ FP8 stress -----
@@ -877,6 +955,7 @@ def run_gpu_fp8(args):
     m, n, b = args.fp8_m, args.fp8_n, 32
     s = args.s if args.s_set else 128
     gam, lam = 1.0 / 128, 1e-6
+    summary = getattr(args, "summary", False)  # a side summary of the default line: throughput only
     k = B.kernel("rbf", gamma=gam)
     with torch.cuda.stream(stream):
         # the stored matrices, generated on the device from the seeded recipe
@@ -900,41 +979,44 @@ def run_gpu_fp8(args):
             ms8, launches, ph8 = _fp8_arm(B, torch, F, y, k, lam, b, s, "fp8", args, stream, flush, rank)
         ms16, _, ph16 = _fp8_arm(B, torch, A16, y, k, lam, b, s, "bf16", args, stream, flush, rank)
 
-        # end to end through the C ABI with host buffers (FP8 codes, scales, y)
-        q_h = F.codes.cpu().pin_memory()
-        sc_h = F.scale.cpu().pin_memory()
-        y_h = y.cpu().pin_memory()
-        al_h = torch.zeros(m, dtype=torch.float64).pin_memory()
-        gr_h = torch.zeros(m, dtype=torch.float64).pin_memory()
-        Hh = args.steps * s
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        B.krr_solve(B.Fp8(q_h.numpy(), sc_h.numpy()), y_h.numpy(), k, lam, b, s, Hh, seed=rank, prec="fp8",
-                    alpha=al_h.numpy(), grad=gr_h.numpy(), flags=B.FLAG_HOST_IO, stream=stream.cuda_stream)
-        dt = time.perf_counter() - t0
-        e2e = {"value": Hh * b / dt, "unit": UNIT, "h2d_bytes_per_step": (m * n + 4 * m + 16 * m) / args.steps,
-               "d2h_bytes_per_step": 16 * m / args.steps, "steps": args.steps, "wall_s": dt}
-        del q_h, sc_h
+        e2e = None
+        if not summary:
+            # end to end through the C ABI with host buffers (FP8 codes, scales, y)
+            q_h = F.codes.cpu().pin_memory()
+            sc_h = F.scale.cpu().pin_memory()
+            y_h = y.cpu().pin_memory()
+            al_h = torch.zeros(m, dtype=torch.float64).pin_memory()
+            gr_h = torch.zeros(m, dtype=torch.float64).pin_memory()
+            Hh = args.steps * s
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.krr_solve(B.Fp8(q_h.numpy(), sc_h.numpy()), y_h.numpy(), k, lam, b, s, Hh, seed=rank, prec="fp8",
+                        alpha=al_h.numpy(), grad=gr_h.numpy(), flags=B.FLAG_HOST_IO, stream=stream.cuda_stream)
+            dt = time.perf_counter() - t0
+            e2e = {"value": Hh * b / dt, "unit": UNIT, "h2d_bytes_per_step": (m * n + 4 * m + 16 * m) / args.steps,
+                   "d2h_bytes_per_step": 16 * m / args.steps, "steps": args.steps, "wall_s": dt}
+            del q_h, sc_h
 
-        # alpha error on the 20000-row subproblem (rows 0..19999 of the stored matrix)
-        msub = min(m, args.fp8_sub)
-        Asub16 = A16[:msub].contiguous()
-        ysub = y[:msub].contiguous()
-        Fsub = B.quantize_e4m3(Asub16, stream=stream.cuda_stream)
-        Hs = args.fp8_oracle_blocks
-        Hl = args.fp8_long_steps * s
-        err = {}
-        ref_long = {}
-        for tag, Am, prec in (("fp64_on_bf16", Asub16, "fp64"), ("fp64_on_fp8", Fsub, "fp64")):
-            ref_long[tag] = B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec="fp64")[0].cpu().numpy()
-        arms = {}
-        for tag, Am, prec in (("fp8", Fsub, "fp8"), ("bf16", Asub16, "bf16"), ("fp64_on_bf16", Asub16, "fp64"),
-                              ("fp64_on_fp8", Fsub, "fp64")):
-            arms[tag] = (B.krr_solve(Am, ysub, k, lam, b, s, Hs, seed=7, prec=prec)[0].cpu().numpy(),
-                         B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec=prec)[0].cpu().numpy())
-        torch.cuda.synchronize()
-        A_sub_h = Asub16.float().cpu().numpy().astype(np.float64)
-        y_sub_h = ysub.cpu().numpy()
+        if not summary:
+            # alpha error on the 20000-row subproblem (rows 0..19999 of the stored matrix)
+            msub = min(m, args.fp8_sub)
+            Asub16 = A16[:msub].contiguous()
+            ysub = y[:msub].contiguous()
+            Fsub = B.quantize_e4m3(Asub16, stream=stream.cuda_stream)
+            Hs = args.fp8_oracle_blocks
+            Hl = args.fp8_long_steps * s
+            err = {}
+            ref_long = {}
+            for tag, Am, prec in (("fp64_on_bf16", Asub16, "fp64"), ("fp64_on_fp8", Fsub, "fp64")):
+                ref_long[tag] = B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec="fp64")[0].cpu().numpy()
+            arms = {}
+            for tag, Am, prec in (("fp8", Fsub, "fp8"), ("bf16", Asub16, "bf16"), ("fp64_on_bf16", Asub16, "fp64"),
+                                  ("fp64_on_fp8", Fsub, "fp64")):
+                arms[tag] = (B.krr_solve(Am, ysub, k, lam, b, s, Hs, seed=7, prec=prec)[0].cpu().numpy(),
+                             B.krr_solve(Am, ysub, k, lam, b, s, Hl, seed=7, prec=prec)[0].cpu().numpy())
+            torch.cuda.synchronize()
+            A_sub_h = Asub16.float().cpu().numpy().astype(np.float64)
+            y_sub_h = ysub.cpu().numpy()
 
     def rel(a, b_):
         return float(np.linalg.norm(a - b_) / np.linalg.norm(b_))
@@ -942,28 +1024,29 @@ def run_gpu_fp8(args):
     out_err = None
     cpu = None
     if rank == 0:
-        out_err = {"rows": msub, "seed": 7,
-                   "long_H_blocks": Hl,
-                   "vs_fp64_gpu_long": {"fp8_vs_fp64_on_fp8_data": rel(arms["fp8"][1], ref_long["fp64_on_fp8"]),
-                                        "bf16_vs_fp64_on_bf16_data": rel(arms["bf16"][1], ref_long["fp64_on_bf16"]),
-                                        "fp8_storage_vs_bf16_storage_fp64": rel(ref_long["fp64_on_fp8"],
-                                                                                ref_long["fp64_on_bf16"]),
-                                        "fp8_vs_fp64_on_bf16_data": rel(arms["fp8"][1], ref_long["fp64_on_bf16"])}}
-        if not args.no_cpu:
-            import oracle
-            nt = oracle_threads()
-            ko = oracle.kernel("rbf", gamma=gam)
-            t0 = time.perf_counter()
-            want = oracle.bdcd_krr(A_sub_h, y_sub_h, ko, lam, b, Hs, seed=7)
-            t_or = time.perf_counter() - t0
-            out_err["oracle_H_blocks"] = Hs
-            out_err["vs_oracle"] = {t: rel(arms[t][0], want) for t in arms}
-            out_err["vs_oracle_note"] = ("oracle = FP64 BDCD (Algorithm 3) on the BF16-stored rows; fp64_on_fp8 and "
-                                         "fp8 differ from it by the FP8 storage")
-            upd = Hs * b
-            cpu = {"value": upd / t_or * msub / m, "unit": UNIT, "cores": nt, "kind": "oracle",
-                   "sample": f"{Hs} BDCD block updates (b={b}) on rows 0..{msub - 1} ({t_or:.1f} s, plain FP64 C, "
-                             f"row loops on {nt} threads), rate scaled by rows to m={m}"}
+        if not summary:
+            out_err = {"rows": msub, "seed": 7,
+                       "long_H_blocks": Hl,
+                       "vs_fp64_gpu_long": {"fp8_vs_fp64_on_fp8_data": rel(arms["fp8"][1], ref_long["fp64_on_fp8"]),
+                                            "bf16_vs_fp64_on_bf16_data": rel(arms["bf16"][1], ref_long["fp64_on_bf16"]),
+                                            "fp8_storage_vs_bf16_storage_fp64": rel(ref_long["fp64_on_fp8"],
+                                                                                    ref_long["fp64_on_bf16"]),
+                                            "fp8_vs_fp64_on_bf16_data": rel(arms["fp8"][1], ref_long["fp64_on_bf16"])}}
+            if not args.no_cpu:
+                import oracle
+                nt = oracle_threads()
+                ko = oracle.kernel("rbf", gamma=gam)
+                t0 = time.perf_counter()
+                want = oracle.bdcd_krr(A_sub_h, y_sub_h, ko, lam, b, Hs, seed=7)
+                t_or = time.perf_counter() - t0
+                out_err["oracle_H_blocks"] = Hs
+                out_err["vs_oracle"] = {t: rel(arms[t][0], want) for t in arms}
+                out_err["vs_oracle_note"] = ("oracle = FP64 BDCD (Algorithm 3) on the BF16-stored rows; fp64_on_fp8 and "
+                                             "fp8 differ from it by the FP8 storage")
+                upd = Hs * b
+                cpu = {"value": upd / t_or * msub / m, "unit": UNIT, "cores": nt, "kind": "oracle",
+                       "sample": f"{Hs} BDCD block updates (b={b}) on rows 0..{msub - 1} ({t_or:.1f} s, plain FP64 C, "
+                                 f"row loops on {nt} threads), rate scaled by rows to m={m}"}
         hbm_peak, bf16_peak, bf16_sus, src = peaks()
         sb = s * b
         flops = 2.0 * m * n * sb
@@ -993,7 +1076,7 @@ def run_gpu_fp8(args):
                "alpha_error": out_err,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary()}
-        print(json.dumps(out), flush=True)
+        emit(out, args)
 
 
 # ---------------------------------------------------------------- sweep -----
@@ -1126,7 +1209,7 @@ def run_gpu_sweep(args):
                          "s_chosen": s_hist, "to_tolerance": conv},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk.summary()}
-        print(json.dumps(out), flush=True)
+        emit(out, args)
 
 
 def sweep_cpu_baseline(probs, upd_total, nsample=8, budget_s=15.0):
@@ -1200,6 +1283,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
+    ap.add_argument("--no-also", action="store_true",
+                    help="default workload: skip the side summaries of the other configurations")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--ttt-budget", type=int, default=400000, help="block-update cap of the tolerance solve")
     ap.add_argument("--ttt-small-m", type=int, default=6000,
