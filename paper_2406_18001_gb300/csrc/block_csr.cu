@@ -365,134 +365,99 @@ __global__ void __launch_bounds__(CSR_AW * 32, 3)
 // row j -- are found by walking the sampled rows' columns: about
 // sum_j sum_{c in S_j} nnz(column c) "incidences" (i, element e, j), against
 // every nonzero of A for the full pass.  Per 32-column chunk:
-//   count    a warp per (sampled row j, its q-th nonzero): the column's
-//            entries counted per 32-row tile; the last CTA to finish scans
-//            the counts into tile offsets (and flags a total beyond the
-//            incidence buffer);
-//   scatter  the same walk writes key = (e << 5) | j and the product
-//            a_ie * a_{S_j},c into the tile's range (in arbitrary order);
-//   apply    a warp per tile sorts its incidences by key (rank sort in shared
-//            memory; keys are unique), so each row's products for each j come
-//            in element order -- the order of the full pass -- then forms the
-//            rows' sums exactly as the full pass does.  A tile with more
-//            incidences than its shared buffer, and every tile when the
-//            buffer overflowed, runs the full pass instead.
+//   scatter  a CTA per (sampled row j, group of CSC_G of its nonzeros): the
+//            group's columns, values and column ranges go to shared memory
+//            with their prefix sums, then the CTA's threads sweep the group's
+//            incidences as one flat range (CSC_U independent loads and
+//            atomics per thread in flight) and append key = (e << 10) | (i mod
+//            32) << 5 | j and the product a_ie * a_{S_j},c to the bucket of
+//            the incidence's 32-row tile (a fixed capacity per tile; a counter
+//            per tile, in arbitrary order);
+//   apply    a warp per tile (the next tile's bucket loaded while this one
+//            is processed) counting-sorts its incidences by row (shared
+//            memory atomics), then lane r insertion-sorts its row's few
+//            entries by key -- or, when some row holds more than
+//            CSC_SHORT_ROW (a sampled row meets itself in all its columns),
+//            the warp ranks every key of the tile jointly -- so the products
+//            for each j come in element order, the order of the full pass,
+//            and forms the row's sum exactly as the full pass does.  A tile
+//            whose bucket overflowed runs the full pass over its rows.
 // The result is bit-identical to the full pass.
-constexpr int CSC_TILE_CAP = 128;  // incidences per 32-row tile sorted in shared memory
-constexpr int CSC_COUNT_WARPS = 8;
+constexpr int CSC_TILE_CAP = 128;  // incidences per 32-row tile (bucket size, sorted in shared memory)
+constexpr int CSC_G = 4;           // sampled-row nonzeros per scatter CTA
+constexpr int CSC_U = 4;           // incidences per scatter thread in flight
+constexpr int CSC_SCATTER_THREADS = 256;
+
+constexpr int CSC_SHORT_ROW = 8;   // a row with more entries in a tile makes the warp sort the tile jointly
 
 template <typename T>
 struct alignas(16) CscWarpSmem {
-    int64_t ukey[CSC_TILE_CAP], skey[CSC_TILE_CAP];
-    T uprod[CSC_TILE_CAP], sprod[CSC_TILE_CAP];
+    int64_t skey[CSC_TILE_CAP], rkey[CSC_TILE_CAP];
+    T sprod[CSC_TILE_CAP], rprod[CSC_TILE_CAP];
+    int32_t rcnt[32], roff[32];
 };
 
-// The last CTA's exclusive scan of tile_cnt[0, ntiles) into tile_off (with
-// tile_off[ntiles] = total).
-__device__ void csc_scan_tiles(const CscStep &W, int64_t ntiles)
+template <typename T>
+__global__ void __launch_bounds__(CSC_SCATTER_THREADS)
+    csc_scatter_kernel(CscOperand C, CsrColMap M, int j0, CscStep W)
 {
-    __shared__ int64_t wsum[32];
-    __shared__ int64_t run_base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) run_base = 0;
-    __syncthreads();
-    for (int64_t b0 = 0; b0 < ntiles; b0 += blockDim.x) {
-        const int64_t t = b0 + threadIdx.x;
-        const int64_t v = t < ntiles ? (int64_t)__ldcg(W.tile_cnt + t) : 0;
-        int64_t incl = v;
+    __shared__ int64_t cstart[CSC_G];
+    __shared__ int64_t pre[CSC_G + 1];
+    __shared__ T aval[CSC_G];
+    const int j = blockIdx.x, grp = blockIdx.y;
+    const T *cval = (const T *)C.val;
+    T *prod = (T *)W.prod;
+    if (threadIdx.x < 32) {  // one warp: the group's pairs and the prefix of their column lengths
+        const int lane = threadIdx.x;
+        const int q = grp * CSC_G + lane;
+        int64_t len = 0;
+        if (lane < CSC_G && q < M.pmax) {
+            const int64_t at = (int64_t)(j0 + j) * M.pmax + q;
+            len = M.plen[at];
+            cstart[lane] = M.pstart[at];
+            aval[lane] = (T)M.pval[at];
+        }
+        int64_t incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += u;
         }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t x = lane < nw ? wsum[lane] : 0, xi = x;
+        if (lane < CSC_G) pre[lane + 1] = incl;
+        if (lane == 0) pre[0] = 0;
+    }
+    __syncthreads();
+    const int64_t total = pre[CSC_G];
+    for (int64_t x0 = threadIdx.x; x0 < total; x0 += (int64_t)blockDim.x * CSC_U) {
+        int64_t k[CSC_U];
+        int q[CSC_U];
+        int32_t row[CSC_U];
+        int pos[CSC_U];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t u = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += u;
+        for (int u = 0; u < CSC_U; ++u) {  // the pair holding incidence x: pre[q] <= x < pre[q + 1]
+            const int64_t x = x0 + (int64_t)u * blockDim.x;
+            int qq = 0;
+#pragma unroll
+            for (int b = CSC_G / 2; b > 0; b >>= 1)
+                if (qq + b < CSC_G && pre[qq + b] <= x) qq += b;
+            q[u] = qq;
+            k[u] = x < total ? cstart[qq] + (x - pre[qq]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < CSC_U; ++u) row[u] = k[u] >= 0 ? C.row[k[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < CSC_U; ++u) pos[u] = row[u] >= 0 ? atomicAdd(W.tile_cnt + (row[u] >> 5), 1) : CSC_TILE_CAP;
+#pragma unroll
+        for (int u = 0; u < CSC_U; ++u)
+            if (pos[u] < CSC_TILE_CAP) {
+                const int64_t at = (int64_t)(row[u] >> 5) * CSC_TILE_CAP + pos[u];
+                W.key[at] = (C.elem[k[u]] << 10) | ((int64_t)(row[u] & 31) << 5) | j;
+                prod[at] = mul_rn(cval[k[u]], aval[q[u]]);  // the full pass's product, rounded in T
             }
-            if (lane < nw) wsum[lane] = xi - x;
-        }
-        __syncthreads();
-        const int64_t base = run_base;
-        if (t < ntiles) W.tile_off[t] = base + wsum[warp] + incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) run_base = base + wsum[warp] + incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const int64_t total = run_base;
-        W.tile_off[ntiles] = total;
-        *W.ovf = total > W.cap ? 1 : 0;
-        *W.ticket = 0u;
     }
 }
 
-// the q-th nonzero of sampled position j (element index), or -1
-__device__ __forceinline__ int64_t sampled_elem(const CsrOperand &A, const int32_t *S, int j, int q)
-{
-    const int64_t r = S[j];
-    if (r < 0 || r >= A.m) return -1;
-    const int64_t e = A.row_ptr[r] + q;
-    return e < A.row_ptr[r + 1] ? e : -1;
-}
-
-__global__ void __launch_bounds__(CSC_COUNT_WARPS * 32)
-    csc_count_kernel(CsrOperand A, CscOperand C, const int32_t *S, int j0, int jc, int maxrow, CscStep W,
-                     int64_t ntiles)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * CSC_COUNT_WARPS, total = (int64_t)jc * maxrow;
-    for (int64_t u = (int64_t)blockIdx.x * CSC_COUNT_WARPS + (threadIdx.x >> 5); u < total; u += nwarps) {
-        const int j = (int)(u / maxrow), q = (int)(u % maxrow);
-        const int64_t e = sampled_elem(A, S, j0 + j, q);
-        if (e < 0) continue;
-        const int32_t c = A.col_idx[e];
-        const int64_t k1 = C.col_ptr[c + 1];
-        for (int64_t k = C.col_ptr[c] + lane; k < k1; k += 32) atomicAdd(W.tile_cnt + (C.row[k] >> 5), 1);
-    }
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(W.ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    csc_scan_tiles(W, ntiles);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(CSC_COUNT_WARPS * 32)
-    csc_scatter_kernel(CsrOperand A, CscOperand C, const int32_t *S, int j0, int jc, int maxrow, CscStep W)
-{
-    if (*W.ovf) return;
-    const int lane = threadIdx.x & 31;
-    const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
-    const T *cval = (const T *)C.val;
-    T *prod = (T *)W.prod;
-    const int64_t nwarps = (int64_t)gridDim.x * CSC_COUNT_WARPS, total = (int64_t)jc * maxrow;
-    for (int64_t u = (int64_t)blockIdx.x * CSC_COUNT_WARPS + (threadIdx.x >> 5); u < total; u += nwarps) {
-        const int j = (int)(u / maxrow), q = (int)(u % maxrow);
-        const int64_t e = sampled_elem(A, S, j0 + j, q);
-        if (e < 0) continue;
-        const int32_t c = A.col_idx[e];
-        const T a = vals[e];
-        const int64_t k1 = C.col_ptr[c + 1];
-        for (int64_t k = C.col_ptr[c] + lane; k < k1; k += 32) {
-            const int32_t t = C.row[k] >> 5;
-            const int64_t pos = (int64_t)W.tile_off[t] + atomicAdd(W.tile_cur + t, 1);
-            W.key[pos] = (C.elem[k] << 5) | j;
-            prod[pos] = mul_rn(cval[k], a);  // the full pass's product: a_ie * a_{S_j},c rounded in T
-        }
-    }
-}
-
-template <typename T, int KIND, bool SBITS>
+template <typename T, int KIND>
 __global__ void __launch_bounds__(CSR_AW * 32, 2)
     csc_apply_kernel(CsrOperand A, CsrColMap M, CscStep W, int64_t nrows, const int32_t *S, int j0, int jc,
                      KernelParams kp, const float *w32, const double *w64, const double *rs, double *g)
@@ -505,57 +470,117 @@ __global__ void __launch_bounds__(CSR_AW * 32, 2)
         ((CscWarpSmem<T> *)(csr_sm + sizeof(CtaSmem<T>) + sizeof(WarpSmem<T>) * CSR_AW))[warp];
     const T *vals = (const T *)(sizeof(T) == 8 ? (const void *)A.vals64 : (const void *)A.vals32);
     const T *prod = (const T *)W.prod;
-    csr_cta_setup<T, KIND, SBITS>(cs, ws, A, M, S, j0, jc, kp, w32, w64);
-    const uint32_t *bits = SBITS ? cs.bits : M.bits;
-    const bool ovf = *W.ovf != 0;
+    // the bitmap stays in global memory: only tiles that overflowed their bucket test it
+    csr_cta_setup<T, KIND, false>(cs, ws, A, M, S, j0, jc, kp, w32, w64);
     const int64_t ntiles = (nrows + 31) / 32;
-    for (int64_t tile = (int64_t)blockIdx.x * CSR_AW + warp; tile < ntiles; tile += (int64_t)gridDim.x * CSR_AW) {
+    const int64_t tstride = (int64_t)gridDim.x * CSR_AW;
+    constexpr int PER = CSC_TILE_CAP / 32;
+    // a tile's counter, row offsets and whole bucket (entries past the counter are stale and
+    // masked later); the next tile's are loaded while this one is processed
+    int nt_n = 0;
+    int64_t rpv_n = 0, rend_n = 0;
+    int64_t kk_n[PER];
+    T pp_n[PER];
+    auto load_tile = [&](int64_t tl) {
+        if (tl >= ntiles) return;
+        const int64_t t0 = tl * 32;
+        const int nr = (int)min((int64_t)32, nrows - t0);
+        nt_n = W.tile_cnt[tl];
+        rpv_n = lane < nr ? A.row_ptr[t0 + lane] : 0;
+        rend_n = A.row_ptr[t0 + nr];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            kk_n[u] = W.key[tl * CSC_TILE_CAP + lane + 32 * u];
+            pp_n[u] = prod[tl * CSC_TILE_CAP + lane + 32 * u];
+        }
+    };
+    load_tile((int64_t)blockIdx.x * CSR_AW + warp);
+    for (int64_t tile = (int64_t)blockIdx.x * CSR_AW + warp; tile < ntiles; tile += tstride) {
         const int64_t t0 = tile * 32;
         const int nr = (int)min((int64_t)32, nrows - t0);
-        const int64_t o0 = W.tile_off[tile];
-        const int nt = (int)(W.tile_off[tile + 1] - o0);
-        const int64_t rpv = lane < nr ? A.row_ptr[t0 + lane] : 0, rend = A.row_ptr[t0 + nr];
+        const int nt = nt_n;
+        const int64_t rpv = rpv_n, rend = rend_n;
+        int64_t kk[PER];
+        T pp[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            kk[u] = lane + 32 * u < nt ? kk_n[u] : -1;
+            pp[u] = pp_n[u];
+        }
+        load_tile(tile + tstride);
         const int64_t e0 = __shfl_sync(0xffffffffu, rpv, 0);
         uint32_t touched = 0;
-        if (ovf || nt > CSC_TILE_CAP) {  // the full pass over this tile
+        if (nt > CSC_TILE_CAP) {  // the bucket overflowed: the full pass over this tile
             if (lane < nr) ws.rp[lane] = (int32_t)(rpv - e0);
             if (lane == 0) ws.rp[nr] = (int32_t)(rend - e0);
-            csr_tile_stream<T, SBITS>(A, M, ws, bits, vals, e0, (int)(rend - e0), j0, jc, lane, nr, touched);
+            csr_tile_stream<T, false>(A, M, ws, M.bits, vals, e0, (int)(rend - e0), j0, jc, lane, nr, touched);
         } else if (nt > 0) {
-            for (int x = lane; x < nt; x += 32) {
-                xs.ukey[x] = W.key[o0 + x];
-                xs.uprod[x] = prod[o0 + x];
-            }
+            // counting sort by row (the row's index within the tile is bits 5..9 of the key)
+            xs.rcnt[lane] = 0;
             __syncwarp();
-            for (int x = lane; x < nt; x += 32) {  // rank sort: keys are unique
-                const int64_t kx = xs.ukey[x];
-                int p = 0;
-                for (int y = 0; y < nt; ++y) p += xs.ukey[y] < kx ? 1 : 0;
-                xs.skey[p] = kx;
-                xs.sprod[p] = xs.uprod[x];
-            }
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (kk[u] >= 0) atomicAdd(&xs.rcnt[(int)(kk[u] >> 5) & 31], 1);
             __syncwarp();
-            if (lane < nr) {
-                const int64_t lo = rpv << 5, hi = (lane + 1 < nr ? A.row_ptr[t0 + lane + 1] : rend) << 5;
-                int a = 0, b = nt;  // first key >= lo
-                while (a < b) {
-                    const int mid = (a + b) >> 1;
-                    if (xs.skey[mid] < lo) a = mid + 1;
-                    else b = mid;
+            const int rc = xs.rcnt[lane];
+            int incl = rc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            xs.roff[lane] = incl - rc;
+            xs.rcnt[lane] = 0;
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (kk[u] >= 0) {
+                    const int rl = (int)(kk[u] >> 5) & 31;
+                    const int at = xs.roff[rl] + atomicAdd(&xs.rcnt[rl], 1);
+                    xs.skey[at] = kk[u];
+                    xs.sprod[at] = pp[u];
                 }
-                for (int h = a; h < nt && xs.skey[h] < hi; ++h) {
-                    const int j = (int)(xs.skey[h] & 31);
-                    ws.acc[lane][j] += xs.sprod[h];
-                    touched |= 1u << j;
+            __syncwarp();
+            const int b0 = incl - rc, b1 = incl;
+            const int64_t *sk = xs.skey;
+            const T *sp = xs.sprod;
+            if (__reduce_max_sync(0xffffffffu, (unsigned)rc) > (unsigned)CSC_SHORT_ROW) {
+                // rank every key of the tile (keys are unique; the rank order groups the rows in
+                // the order of the counting sort, so the row segments stay where they are)
+#pragma unroll
+                for (int u = 0; u < PER; ++u)
+                    if (kk[u] >= 0) {
+                        int r = 0;
+                        for (int y = 0; y < nt; ++y) r += xs.skey[y] < kk[u] ? 1 : 0;
+                        xs.rkey[r] = kk[u];
+                        xs.rprod[r] = pp[u];
+                    }
+                __syncwarp();
+                sk = xs.rkey;
+                sp = xs.rprod;
+            } else {
+                for (int h = b0 + 1; h < b1; ++h) {  // lane r: its row's few entries by key
+                    const int64_t kv = xs.skey[h];
+                    const T pv = xs.sprod[h];
+                    int q = h - 1;
+                    while (q >= b0 && xs.skey[q] > kv) {
+                        xs.skey[q + 1] = xs.skey[q];
+                        xs.sprod[q + 1] = xs.sprod[q];
+                        --q;
+                    }
+                    xs.skey[q + 1] = kv;
+                    xs.sprod[q + 1] = pv;
                 }
+            }
+            for (int h = b0; h < b1; ++h) {  // the products per j in element order
+                const int j = (int)(sk[h] & 31);
+                ws.acc[lane][j] += sp[h];
+                touched |= 1u << j;
             }
             __syncwarp();
         }
         csr_row_finish<T, KIND>(ws, cs, A, kp, t0, lane, nr, touched, rs, g);
-        if (lane == 0) {  // the counters return to zero for the next chunk
-            W.tile_cnt[tile] = 0;
-            W.tile_cur[tile] = 0;
-        }
+        if (lane == 0) W.tile_cnt[tile] = 0;  // the counter returns to zero for the next chunk
     }
 }
 
@@ -688,6 +713,26 @@ __global__ void __launch_bounds__(MAP_THREADS) csr_colmap_kernel(CsrOperand A, c
         if (tid == 0) set_error(err, DEV_INTERNAL);
         return;
     }
+    // the transposed apply's pair table: per sampled position and nonzero slot, the column's CSC
+    // range and the value
+    if (M.plen)
+        for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
+            const int64_t r = S[j];
+            const bool ok = r >= 0 && r < A.m;
+            const int64_t e0 = ok ? A.row_ptr[r] : 0, len = ok ? A.row_ptr[r + 1] - e0 : 0;
+            for (int q = lane; q < M.pmax; q += 32) {
+                const int64_t at = (int64_t)j * M.pmax + q;
+                if (q < len) {
+                    const int32_t c = A.col_idx[e0 + q];
+                    const int64_t c0 = M.csc_col_ptr[c];
+                    M.pstart[at] = c0;
+                    M.plen[at] = (int32_t)(M.csc_col_ptr[c + 1] - c0);
+                    M.pval[at] = A.vals64 ? A.vals64[e0 + q] : (double)A.vals32[e0 + q];
+                } else {
+                    M.plen[at] = 0;
+                }
+            }
+        }
     // 1. mark the columns (warp per sampled row)
     for (int j = warp; j < cnt; j += MAP_THREADS / 32) {
         const int64_t r = S[j];
@@ -928,12 +973,21 @@ __global__ void csc_fill_kernel(CsrOperand A, const int64_t *col_ptr, int32_t *c
     }
 }
 
-template <typename T, int KIND, bool SBITS>
+template <typename T>
+cudaError_t launch_csc_scatter_chunk(const CsrColMap &M, const CscOperand &C, const CscStep &W, int maxrow,
+                                     int64_t j0, int jc, cudaStream_t st)
+{
+    const unsigned groups = (unsigned)std::max(1, (maxrow + CSC_G - 1) / CSC_G);
+    csc_scatter_kernel<T><<<dim3((unsigned)jc, groups), CSC_SCATTER_THREADS, 0, st>>>(C, M, (int)j0, W);
+    return cudaGetLastError();
+}
+
+template <typename T, int KIND>
 cudaError_t launch_csc_apply_k(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
                                int maxrow, const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
-                               const double *w64, const double *rs, double *g, cudaStream_t st)
+                               const double *w64, const double *rs, double *g, bool first_scattered, cudaStream_t st)
 {
-    auto kfn = csc_apply_kernel<T, KIND, SBITS>;
+    auto kfn = csc_apply_kernel<T, KIND>;
     const size_t smem = sizeof(CtaSmem<T>) + (sizeof(WarpSmem<T>) + sizeof(CscWarpSmem<T>)) * CSR_AW;
     static int per_sm = 0;  // resident CTAs per SM, queried once per instantiation (before any capture)
     if (!per_sm) {
@@ -948,12 +1002,10 @@ cudaError_t launch_csc_apply_k(const CsrOperand &A, const CsrColMap &M, const Cs
     if (grid > (int64_t)sm_count() * per_sm) grid = (int64_t)sm_count() * per_sm;
     for (int64_t j0 = 0; j0 < ncols; j0 += CSR_JC) {
         const int jc = (int)min((int64_t)CSR_JC, ncols - j0);
-        const int64_t pairs = (int64_t)jc * maxrow;
-        int64_t cgrid = (pairs + CSC_COUNT_WARPS - 1) / CSC_COUNT_WARPS;
-        if (cgrid < 1) cgrid = 1;
-        if (cgrid > (int64_t)sm_count() * 8) cgrid = (int64_t)sm_count() * 8;
-        csc_count_kernel<<<(unsigned)cgrid, CSC_COUNT_WARPS * 32, 0, st>>>(A, C, S, (int)j0, jc, maxrow, W, ntiles);
-        csc_scatter_kernel<T><<<(unsigned)cgrid, CSC_COUNT_WARPS * 32, 0, st>>>(A, C, S, (int)j0, jc, maxrow, W);
+        if (j0 > 0 || !first_scattered) {
+            const cudaError_t e = launch_csc_scatter_chunk<T>(M, C, W, maxrow, j0, jc, st);
+            if (e != cudaSuccess) return e;
+        }
         kfn<<<(unsigned)grid, CSR_AW * 32, smem, st>>>(A, M, W, A.m, S, (int)j0, jc, kp, w32, w64, rs, g);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -964,16 +1016,13 @@ cudaError_t launch_csc_apply_k(const CsrOperand &A, const CsrColMap &M, const Cs
 template <typename T>
 cudaError_t launch_csc_apply(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
                              int maxrow, const int32_t *S, int64_t ncols, const KernelParams &kp, const float *w32,
-                             const double *w64, const double *rs, double *g, cudaStream_t st)
+                             const double *w64, const double *rs, double *g, bool first, cudaStream_t st)
 {
-    const bool sb = M.nw <= CSR_SMEM_BITS;
-#define CSC_K(KD)                                                                                              \
-    return sb ? launch_csc_apply_k<T, KD, true>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)        \
-              : launch_csc_apply_k<T, KD, false>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)
-    if (kp.kind == DCD_RBF) CSC_K(DCD_RBF);
-    if (kp.kind == DCD_POLY) CSC_K(DCD_POLY);
-    CSC_K(DCD_LINEAR);
-#undef CSC_K
+    if (kp.kind == DCD_RBF)
+        return launch_csc_apply_k<T, DCD_RBF>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, first, st);
+    if (kp.kind == DCD_POLY)
+        return launch_csc_apply_k<T, DCD_POLY>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, first, st);
+    return launch_csc_apply_k<T, DCD_LINEAR>(A, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, first, st);
 }
 
 }  // namespace
@@ -1097,44 +1146,54 @@ cudaError_t launch_csc_build(const CsrOperand &A, bool fp64, void *base, CscOper
     return cudaGetLastError();
 }
 
-size_t csc_step_bytes(int64_t m, int64_t cap, bool fp64)
+size_t csc_step_bytes(int64_t m, int64_t cnt, int maxrow, bool fp64)
 {
-    const int64_t ntiles = (m + 31) / 32;
-    return (size_t)ntiles * 8 + (size_t)(ntiles + 1) * 8 + 512 + (size_t)cap * (8 + (fp64 ? 8 : 4)) + 256 * 6;
+    const int64_t ntiles = (m + 31) / 32, pairs = cnt * (int64_t)std::max(maxrow, 1);
+    return (size_t)ntiles * 4 + (size_t)ntiles * CSC_TILE_CAP * (8 + (fp64 ? 8 : 4)) + (size_t)pairs * (8 + 4 + 8) +
+           256 * 6;
 }
 
-CscStep csc_step_carve(void *base, int64_t m, int64_t cap)
+CscStep csc_step_carve(void *base, int64_t m, int64_t cnt, int maxrow, const CscOperand &C, CsrColMap *M)
 {
-    const int64_t ntiles = (m + 31) / 32;
+    const int64_t ntiles = (m + 31) / 32, pairs = cnt * (int64_t)std::max(maxrow, 1);
     char *p = (char *)base;
     CscStep W;
     W.tile_cnt = (int32_t *)p;
     take_bytes(p, (size_t)ntiles * 4);
-    W.tile_cur = (int32_t *)p;
-    take_bytes(p, (size_t)ntiles * 4);
-    W.tile_off = (int64_t *)p;
-    take_bytes(p, (size_t)(ntiles + 1) * 8);
-    W.ticket = (unsigned *)p;
-    take_bytes(p, 256);
-    W.ovf = (int *)p;
-    take_bytes(p, 256);
     W.key = (int64_t *)p;
-    take_bytes(p, (size_t)cap * 8);
+    take_bytes(p, (size_t)ntiles * CSC_TILE_CAP * 8);
+    M->pstart = (int64_t *)p;
+    take_bytes(p, (size_t)pairs * 8);
+    M->pval = (double *)p;
+    take_bytes(p, (size_t)pairs * 8);
+    M->plen = (int32_t *)p;
+    take_bytes(p, (size_t)pairs * 4);
+    M->pmax = std::max(maxrow, 1);
+    M->csc_col_ptr = C.col_ptr;
     W.prod = p;
-    W.cap = cap;
     return W;
 }
 
 cudaError_t launch_csr_apply_csc(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
                                  bool fp64, int maxrow, const KernelParams &kp, const int32_t *S, int64_t ncols,
-                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st)
+                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st,
+                                 bool first_scattered)
 {
     if (ncols <= 0 || A.m <= 0) return cudaSuccess;
     CsrOperand Av = A;
     const void *vp = fp64 ? (const void *)A.vals64 : (const void *)A.vals32;
     Av.vec = ((uintptr_t)A.col_idx & 15) == 0 && ((uintptr_t)vp & 15) == 0;
-    return fp64 ? launch_csc_apply<double>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st)
-                : launch_csc_apply<float>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, st);
+    return fp64 ? launch_csc_apply<double>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, first_scattered, st)
+                : launch_csc_apply<float>(Av, M, C, W, maxrow, S, ncols, kp, w32, w64, rs, g, first_scattered, st);
+}
+
+cudaError_t launch_csr_csc_scatter_first(const CsrColMap &M, const CscOperand &C, const CscStep &W, bool fp64,
+                                         int maxrow, int64_t ncols, cudaStream_t st)
+{
+    if (ncols <= 0) return cudaSuccess;
+    const int jc = (int)min((int64_t)CSR_JC, ncols);
+    return fp64 ? launch_csc_scatter_chunk<double>(M, C, W, maxrow, 0, jc, st)
+                : launch_csc_scatter_chunk<float>(M, C, W, maxrow, 0, jc, st);
 }
 
 }  // namespace dcd

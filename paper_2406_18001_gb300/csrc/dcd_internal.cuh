@@ -259,12 +259,20 @@ struct CsrOperand {
 // Column map of the sampled rows: bitmap over [0, n), popcount prefix per
 // 32-column word, per-slot entry offsets and (j, value) entries; capacity
 // `cap` >= the sampled rows' nonzeros; counts zero between uses.
+// With the apply through a transposed copy, the same kernel also writes per
+// sampled position j and nonzero q < pmax of its row the column's CSC range
+// (pstart, plen; plen = 0 past the row's end) and the value (pval).
 struct CsrColMap {
     uint32_t *bits = nullptr;
     int32_t *wprefix = nullptr, *slot_off = nullptr, *counts = nullptr, *ent_j = nullptr;
     double *ent_v = nullptr;
     int nw = 0;
     int64_t cap = 0;
+    const int64_t *csc_col_ptr = nullptr;
+    int64_t *pstart = nullptr;
+    int32_t *plen = nullptr;
+    double *pval = nullptr;
+    int pmax = 0;
 };
 size_t csr_colmap_bytes(int64_t n, int64_t cap);
 CsrColMap csr_colmap_carve(void *base, int64_t n, int64_t cap);
@@ -272,9 +280,9 @@ cudaError_t launch_csr_prep(const CsrOperand &A, int *bad, int *maxlen, cudaStre
 cudaError_t launch_csr_colmap(const CsrOperand &A, const int32_t *S, int64_t cnt, const CsrColMap &M, int *err,
                               cudaStream_t st);
 // Transposed copy of a CSR operand: per column its entries' rows, CSR element
-// indices and values (in the block's precision), and per-step scratch of the
-// apply through it (tile counters and offsets, the incidence buffer of
-// capacity `cap`); counters zero between uses.
+// indices and values (in the block's precision); and the per-step scratch of
+// the apply through it: per 32-row tile a counter (zero between uses) and a
+// bucket of incidence keys and products.
 struct CscOperand {
     const int64_t *col_ptr = nullptr;
     const int32_t *row = nullptr;
@@ -283,26 +291,30 @@ struct CscOperand {
     int64_t n = 0;
 };
 struct CscStep {
-    int32_t *tile_cnt = nullptr, *tile_cur = nullptr;
-    int64_t *tile_off = nullptr;
-    unsigned *ticket = nullptr;
-    int *ovf = nullptr;
+    int32_t *tile_cnt = nullptr;
     int64_t *key = nullptr;
     void *prod = nullptr;
-    int64_t cap = 0;
 };
 size_t csc_bytes(int64_t n, int64_t nnz, bool fp64);
 // builds the copy in `base` (csc_bytes); *maxcol_dev receives the longest column
 cudaError_t launch_csc_build(const CsrOperand &A, bool fp64, void *base, CscOperand *C, int *maxcol_dev,
                              cudaStream_t st);
-size_t csc_step_bytes(int64_t m, int64_t cap, bool fp64);
-CscStep csc_step_carve(void *base, int64_t m, int64_t cap);  // base zeroed by the caller
+// cnt: sampled positions per step, maxrow: the longest row (the pair table of the column map)
+size_t csc_step_bytes(int64_t m, int64_t cnt, int maxrow, bool fp64);
+// base zeroed by the caller; the pair-table fields of *M are set
+CscStep csc_step_carve(void *base, int64_t m, int64_t cnt, int maxrow, const CscOperand &C, CsrColMap *M);
 // the apply form of launch_csr_block over all m rows through the transposed
 // copy (bit-identical to the full pass); M is the step's column map (used by
-// tiles that fall back to the full pass); maxrow = the longest row
+// tiles whose bucket overflowed); maxrow = the longest row
+// (first_scattered: the first chunk's incidences are already in the buckets,
+// from launch_csr_csc_scatter_first after this step's column map)
 cudaError_t launch_csr_apply_csc(const CsrOperand &A, const CsrColMap &M, const CscOperand &C, const CscStep &W,
                                  bool fp64, int maxrow, const KernelParams &kp, const int32_t *S, int64_t ncols,
-                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st);
+                                 const float *w32, const double *w64, const double *rs, double *g, cudaStream_t st,
+                                 bool first_scattered = false);
+// the scatter of the first chunk only (it needs the step's sample and column map, not its coefficients)
+cudaError_t launch_csr_csc_scatter_first(const CsrColMap &M, const CscOperand &C, const CscStep &W, bool fp64,
+                                         int maxrow, int64_t ncols, cudaStream_t st);
 // apply (out == nullptr): g[i] += rs[i] * sum_j K(a_i, a_{S_j}) w_j for i < nrows (rows == nullptr);
 // store: out[r*ldo + j] = K(a_{rows[r]}, a_{S_j}) (rows == nullptr: row r).  FP64 (w64, out
 // double) or FP32 (w32, out float).

@@ -67,11 +67,10 @@ namespace {
 // through it, kept when a step's incidences -- expected jc * (nnz / m) *
 // sum_c nnz_c^2 / nnz per chunk of jc sampled rows whose columns follow the
 // nonzeros -- stay below nnz / 16 (an incidence costs about 16 times the full
-// pass's 4 bytes per nonzero); else nothing is kept.  The incidence buffer
-// holds 4x the expectation (at most the worst case); a chunk beyond it runs
-// the full pass.  maxcol_dev: one device int of scratch.
-dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t jc, int maxrow, int *maxcol_dev, void **ws_csc,
-                      CscOperand *C, void **ws_step, CscStep *W, bool *use, cudaStream_t st);
+// pass's 4 bytes per nonzero); else nothing is kept.  maxcol_dev: one device
+// int of scratch.
+dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t cnt, int maxrow, int *maxcol_dev, void **ws_csc,
+                      CscOperand *C, void **ws_step, CscStep *W, CsrColMap *M, bool *use, cudaStream_t st);
 
 constexpr int64_t SB_MAX = 8192;   // s*b per outer step
 constexpr int B_MAX = 128;         // block size
@@ -109,18 +108,17 @@ dcd_status cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_);  \
     } while (0)
 
-dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t jc, int maxrow, int *maxcol_dev, void **ws_csc,
-                      CscOperand *C, void **ws_step, CscStep *W, bool *use, cudaStream_t st)
+dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t cnt, int maxrow, int *maxcol_dev, void **ws_csc,
+                      CscOperand *C, void **ws_step, CscStep *W, CsrColMap *M, bool *use, cudaStream_t st)
 {
     *use = false;
+    const int64_t jc = std::min<int64_t>(cnt, 32);
     const int64_t m = ca.m, n = ca.n;
     if (ca.nnz <= 0 || m <= 0 || jc <= 0) return DCD_OK;
     DCD_TRY(malloc_async(ws_csc, csc_bytes(n, ca.nnz, fp64), st));
     DCD_TRY(launch_csc_build(ca, fp64, *ws_csc, C, maxcol_dev, st));
     std::vector<int64_t> cp((size_t)n + 1);
-    int maxcol = 0;
     DCD_TRY(cudaMemcpyAsync(cp.data(), C->col_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
-    DCD_TRY(cudaMemcpyAsync(&maxcol, maxcol_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     DCD_TRY(cudaStreamSynchronize(st));
     double sq = 0.0;
     for (int64_t c = 0; c < n; ++c) {
@@ -129,17 +127,15 @@ dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t jc, int maxrow, i
     }
     const double nnzd = (double)ca.nnz;
     const double expect = (double)jc * (nnzd / (double)m) * (sq / nnzd);
-    const double worst = (double)jc * maxrow * maxcol;
     if (16.0 * expect > nnzd) {
         DCD_TRY(cudaFreeAsync(*ws_csc, st));
         *ws_csc = nullptr;
         return DCD_OK;
     }
-    const int64_t cap = (int64_t)std::max(1.0, std::min(worst, std::max(4.0 * expect, 1048576.0)));
-    const size_t sbytes = csc_step_bytes(m, cap, fp64);
+    const size_t sbytes = csc_step_bytes(m, cnt, maxrow, fp64);
     DCD_TRY(malloc_async(ws_step, sbytes, st));
     DCD_TRY(cudaMemsetAsync(*ws_step, 0, sbytes, st));
-    *W = csc_step_carve(*ws_step, m, cap);
+    *W = csc_step_carve(*ws_step, m, cnt, maxrow, *C, M);
     *use = true;
     return DCD_OK;
 }
@@ -265,6 +261,9 @@ struct Solver {
     CscStep cstep;
     void *ws_csc = nullptr, *ws_cstep = nullptr;
     int csr_maxrow = 0;
+    // the first chunk's scatter runs on csr_st beside the Gram and the recurrence
+    cudaStream_t csr_st = nullptr;
+    cudaEvent_t csr_fork = nullptr, csr_join = nullptr;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
     float *col_s = nullptr;       // fp8: scales of the sampled rows
@@ -294,6 +293,12 @@ struct Solver {
         if (la_fork) cudaEventDestroy(la_fork);
         if (la_join) cudaEventDestroy(la_join);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
+        if (csr_st) {
+            cudaStreamSynchronize(csr_st);
+            cudaStreamDestroy(csr_st);
+        }
+        if (csr_fork) cudaEventDestroy(csr_fork);
+        if (csr_join) cudaEventDestroy(csr_join);
         if (ws_csc) cudaFreeAsync(ws_csc, st);
         if (ws_cstep) cudaFreeAsync(ws_cstep, st);
         if (ws) cudaFreeAsync(ws, st);
@@ -795,16 +800,42 @@ struct Solver {
     dcd_status setup_csc()
     {
         bool use = false;
-        dcd_status r = csc_choose(ca, !tc, std::min<int64_t>(sb, 32), csr_maxrow, err + 4, &ws_csc, &cscop, &ws_cstep,
-                                  &cstep, &use, st);
+        dcd_status r =
+            csc_choose(ca, !tc, sb, csr_maxrow, err + 4, &ws_csc, &cscop, &ws_cstep, &cstep, &cm, &use, st);
         use_csc = use;
+        if (r == DCD_OK && use) {
+            DCD_TRY(cudaStreamCreateWithFlags(&csr_st, cudaStreamNonBlocking));
+            DCD_TRY(cudaEventCreateWithFlags(&csr_fork, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&csr_join, cudaEventDisableTiming));
+        }
         return r;
+    }
+
+    // The first chunk's scatter forked onto csr_st after the column map (it
+    // runs beside the Gram and the recurrence); csr_apply joins it.
+    bool csr_forked = false;
+    cudaError_t csr_fork_scatter(int64_t ncols)
+    {
+        cudaError_t e = cudaEventRecord(csr_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(csr_st, csr_fork, 0);
+        if (e == cudaSuccess) e = launch_csr_csc_scatter_first(cm, cscop, cstep, !tc, csr_maxrow, ncols, csr_st);
+        if (e == cudaSuccess) e = cudaEventRecord(csr_join, csr_st);
+        csr_forked = e == cudaSuccess;
+        return e;
     }
 
     cudaError_t csr_apply(int64_t ncols, const double *rs)
     {
-        if (use_csc)
-            return launch_csr_apply_csc(ca, cm, cscop, cstep, !tc, csr_maxrow, kp, S, ncols, col_w, w64, rs, g, st);
+        if (use_csc) {
+            const bool first = csr_forked;
+            csr_forked = false;
+            if (first) {
+                const cudaError_t e = cudaStreamWaitEvent(st, csr_join, 0);
+                if (e != cudaSuccess) return e;
+            }
+            return launch_csr_apply_csc(ca, cm, cscop, cstep, !tc, csr_maxrow, kp, S, ncols, col_w, w64, rs, g, st,
+                                        first);
+        }
         return launch_csr_block(ca, cm, !tc, kp, nullptr, m, S, ncols, col_w, w64, rs, g, nullptr, 0, st);
     }
 
@@ -1142,6 +1173,9 @@ struct Solver {
         DCD_TRY(launch_sample(problem, o.seed, ctr, 0, m, o.b, cnt, S, err, st));
         DCD_TRY(gather(ncols));
         tm.stop(stats.ms_sample);
+        // CSR through the transposed copy: the first chunk's incidences are gathered beside the
+        // Gram and the recurrence (not under the phase timers, which time the block as a whole)
+        if (csr && use_csc && !tm.on) DCD_TRY(csr_fork_scatter(ncols));
         tm.start();
         DCD_TRY(gram(ncols));
         tm.stop(stats.ms_gram);
@@ -1546,23 +1580,24 @@ dcd_status component_block_csr(const dcd_matrix *A, const KernelParams &kp, int3
     const size_t cmb = csr_colmap_bytes(A->n, cap);
     DCD_TRY(malloc_async(&cb2.mem, cmb, st));
     DCD_TRY(cudaMemsetAsync(cb2.mem, 0, cmb, st));
-    const CsrColMap cm = csr_colmap_carve(cb2.mem, A->n, cap);
-    DCD_TRY(launch_csr_colmap(ca, cols, ncols, cm, err, st));
+    CsrColMap cm = csr_colmap_carve(cb2.mem, A->n, cap);
     float *w32 = (w && !fp64) ? (float *)(base + ow) : nullptr;
     if (w32) DCD_TRY(launch_f64_to_f32(w, ncols, w32, st));
-    if (!out && !rows && nrows == m) {  // the apply over every row: through the transposed copy when it pays
-        ComponentBufs cb3, cb4;
-        cb3.st = cb4.st = st;
-        CscOperand C;
-        CscStep W;
-        bool use = false;
-        dcd_status cs = csc_choose(ca, fp64, std::min<int64_t>(ncols, 32), h[1], err + 1, &cb3.mem, &C, &cb4.mem, &W,
-                                   &use, st);
+    // the apply over every row: through the transposed copy when it pays (its pair table comes
+    // with the column map)
+    ComponentBufs cb3, cb4;
+    cb3.st = cb4.st = st;
+    CscOperand C;
+    CscStep W;
+    bool use = false;
+    if (!out && !rows && nrows == m) {
+        dcd_status cs = csc_choose(ca, fp64, ncols, h[1], err + 1, &cb3.mem, &C, &cb4.mem, &W, &cm, &use, st);
         if (cs != DCD_OK) return cs;
-        if (use) {
-            DCD_TRY(launch_csr_apply_csc(ca, cm, C, W, fp64, h[1], kp, cols, ncols, w32, w, rs, g, st));
-            return finish_component(err, st);
-        }
+    }
+    DCD_TRY(launch_csr_colmap(ca, cols, ncols, cm, err, st));
+    if (use) {
+        DCD_TRY(launch_csr_apply_csc(ca, cm, C, W, fp64, h[1], kp, cols, ncols, w32, w, rs, g, st));
+        return finish_component(err, st);
     }
     DCD_TRY(launch_csr_block(ca, cm, fp64, kp, rows, nrows, cols, ncols, w32, w, rs, g, out, ldo, st));
     return finish_component(err, st);
