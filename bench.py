@@ -4,18 +4,20 @@
 Workload (default): dense K-RR, m = 50000 samples, n = 512 features, A ~
 N(0,1)/sqrt(n) stored FP32, y = sin(A w) + 0.1 N(0,1), RBF with bandwidth
 sigma = 1 (gamma = 1/(2 sigma^2) = 0.5), lambda = 1e-4, block size b = 16,
-s = 64 inner steps per outer step, split-bf16 (bf16x3) tensor-core kernel
-block with FP64-accurate recurrence and FP64 gradient accumulation (the
-mixed form that meets the alpha / objective tolerances against the FP64
-oracle).  Synthetic data stand in for the paper's LIBSVM sets.
+s = 64 inner steps per outer step, fp16 tensor-core kernel block (the matrix
+scaled by one power of two, 11 significant bits, one MMA per k-step) with
+the FP64 recurrence and FP64 gradient accumulation; the split-bf16 form
+(bf16x3, three MMAs per k-step) is measured beside it in the time-to-
+tolerance and error records.  Synthetic data stand in for the paper's
+LIBSVM sets.
 
 One "step" is one outer s-step (sample, gather, Gram, FP64 recurrence, fused
 kernel-block gradient update, alpha update) = s*b coordinate updates.  The
-metric is coordinate updates per second.  L2 (129 MB) could hold the 102 MB
-split-bf16 operand, so a buffer larger than L2 is written before every timed
-step and each step is timed alone with CUDA events on the solver's stream.
+metric is coordinate updates per second.  L2 (129 MB) could hold the packed
+operand, so a buffer larger than L2 is written before every timed step and
+each step is timed alone with CUDA events on the solver's stream.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--prec bf16x3|bf16|tf32|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--s S] [--prec fp16|bf16x3|bf16|tf32|fp64]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
 """
 from __future__ import annotations
@@ -379,13 +381,13 @@ def dense_roofline(prec, m, n, b, s, t_block, bf16_peak, hbm_peak, src, traffic=
     MMAs per k-step; that tensor-pipe work is reported apart (mma_pipe) and is
     not what frac measures."""
     sb = s * b
-    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[prec]
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8, "fp16": 2}[prec]
     mma_mult = 3 if prec in ("bf16x3", "tf32x3") else 1  # MMAs per k-step
     flops = 2.0 * m * n * sb
     bytes_ = m * n * esz + sb * n * esz + m * (8 + 8 + 4)
     ridge = bf16_peak * 1e12 / (hbm_peak * 1e9)
     # a contraction's peak is its own dtype's: the measured bf16 figure times the nominal ratio
-    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25,
+    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25,
                "tf32x3": 1.1 / 2.25}.get(prec, 0.0) * bf16_peak
     if tc_peak and flops * mma_mult / bytes_ >= ridge:
         roof = {"bound": "tensor", "achieved": flops / t_block / 1e12, "peak": tc_peak, "unit": "TFLOP/s"}
@@ -517,7 +519,7 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
             torch.cuda.synchronize()
             pl.close()
             return sorted(a.elapsed_time(b_) for a, b_ in evs)[len(evs) // 2]
-        esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
+        esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8, "fp16": 2}[args.prec]
         qsz = 8 if args.prec == "fp64" else 4
         sb = args.s * args.b
         lit = {"ms_per_step_median": one_stream_ms(B.FLAG_LITERAL | B.FLAG_NO_GRAPH),
@@ -1174,14 +1176,15 @@ def run_gpu_sweep(args):
     # roofline of the whole call on the method's work: every outer step is one fused block of 2 m n sb
     # flops that reads its problem's packed operand once (the split forms' extra MMA passes apart)
     n_sw = 128
-    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8}[args.prec]
+    esz = {"bf16": 2, "tf32": 4, "bf16x3": 4, "tf32x3": 8, "fp8": 1, "fp64": 8, "fp16": 2}[args.prec]
     mult = 3 if args.prec in ("bf16x3", "tf32x3") else 1
     flops = sum(int(st["outer_steps"]) * 2.0 * p["A"].shape[0] * n_sw * p["s"] * p["b"]
                 for st, p in zip(sts, probs))
     bytes_ = sum(int(st["outer_steps"]) * (p["A"].shape[0] * (n_sw * esz + 20) + p["s"] * p["b"] * n_sw * esz)
                  for st, p in zip(sts, probs))
     hbm_peak, bf16_peak, _, src = peaks()
-    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25}.get(args.prec, 0.0) * bf16_peak
+    tc_peak = {"bf16": 1.0, "bf16x3": 1.0, "fp16": 1.0, "fp8": 2.0, "tf32": 1.1 / 2.25,
+               "tf32x3": 1.1 / 2.25}.get(args.prec, 0.0) * bf16_peak
     roof = {"bound": "tensor", "achieved": flops / wall / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
             "frac": flops / wall / 1e12 / tc_peak if tc_peak else None, "traffic": None, "peak_source": src,
             "kernel": "whole batched call (all problems' steps)",
@@ -1277,8 +1280,8 @@ def main():
     ap.add_argument("--b", type=int, default=16)
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--lam", type=float, default=1e-4)
-    ap.add_argument("--prec", default="bf16x3",
-                    choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64", "refresh"])
+    ap.add_argument("--prec", default="fp16",
+                    choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64", "refresh", "fp16"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
     ap.add_argument("--no-cpu", action="store_true")

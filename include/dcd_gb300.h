@@ -98,6 +98,10 @@ typedef enum {
                             k-step (hi.hi + hi.lo + lo.hi), FP32 accumulation */
     DCD_PREC_TF32X3 = 5, /* split tf32 (both halves on the tf32 grid, ~22 significant bits),
                             three kind::tf32 MMAs per k-step, FP32 accumulation */
+    DCD_PREC_FP16 = 7,   /* fp16: each row scaled by a power of two so that its largest magnitude lies
+                            in [2^14, 2^15), rounded to fp16 (11 significant bits, against bf16's 8);
+                            one tcgen05 kind::f16 MMA per k-step, FP32 accumulation; the epilogue
+                            scales each dot back by s_i s_j (exact: powers of two) */
     DCD_PREC_REFRESH = 6 /* the arithmetic of the gradient recomputed under DCD_FLAG_REFRESH (every
                             tensor-core mode): each row scaled by a power of two and cut into four
                             bf16 planes of integers in [-64, 64] (27 bits of the row's largest
@@ -348,6 +352,8 @@ dcd_status dcd_kernel_block_apply(const dcd_matrix *A, const dcd_kernel *k, int3
  * Arguments are checked as dcd_kernel_block checks them.  Two valid requests
  * that dcd_kernel_block serves give DCD_EUNSUPPORTED here: a CSR data matrix
  * (its column map is sized per call) and FP8 (DCD_PREC_FP8, or FP8 storage).
+ * DCD_PREC_FP16 (per-row scales beside the packed rows) gives DCD_EUNSUPPORTED
+ * too.
  */
 #define DCD_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_kernel *k, int32_t prec, const int32_t *rows,

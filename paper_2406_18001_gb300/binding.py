@@ -20,13 +20,13 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTCONV, EINTERNAL, ENOTSPD, EUNSUPPORTED 
 DENSE, CSR = 0, 1
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 LINEAR, POLY, RBF = 0, 1, 2
-PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3, PREC_TF32X3, PREC_REFRESH = 0, 1, 2, 3, 4, 5, 6
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3, PREC_TF32X3, PREC_REFRESH, PREC_FP16 = 0, 1, 2, 3, 4, 5, 6, 7
 FLAG_GRAD_VALID, FLAG_HOST_IO, FLAG_PHASE_TIMERS, FLAG_NO_GRAPH, FLAG_REFRESH = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_LITERAL = 0x20
 FLAG_CSR_FULL_PASS = 0x40
 
 PREC_NAMES = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3,
-              "tf32x3": PREC_TF32X3, "refresh": PREC_REFRESH}
+              "tf32x3": PREC_TF32X3, "refresh": PREC_REFRESH, "fp16": PREC_FP16}
 
 
 class Matrix(C.Structure):

@@ -68,6 +68,10 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // dropping only lo.lo, about 2^-16 relative).
 // Split tf32 ("tf32x3") is the same with kind::tf32 and tf32 planes (~22
 // significant bits, at half the bf16 MMA rate).
+// fp16: kind::f16 on fp16 operands q, the matrix scaled by one power of two
+// (a ~ s q, |q| < 2^15; 11 significant bits against bf16's 8), one MMA per
+// k-step; the epilogue folds s^2 into its per-row factor (row_s[i] col_s[0]:
+// every scale of an fp16 operand is the same number).
 // fp8: e4m3 codes q with per-row scales (a_i ~ s_i q_i), kind::f8f6f4 with 32
 // codes per MMA (so a 128-byte k-block is again 4 MMAs); the products
 // q_i q_j are exact and the epilogue restores a_i.a_j = s_i s_j (q_i.q_j).
@@ -76,7 +80,7 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // two); the 10 plane products with p + q <= 3 go into 4 accumulators by
 // p + q, whose FP32 sums are exact integers; accurate epilogue (pairs only).
 constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5,
-              MODE_SLICED = 6;
+              MODE_SLICED = 6, MODE_FP16 = 7;
 constexpr int SLICED_BN = 128;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
@@ -284,8 +288,8 @@ struct TcArgs {
     const float *col_h;   // per-column term, padded with zeros to nchunks*BN
     const float *col_w;   // apply: coefficients, padded with zeros
     const double *rs;     // apply: per-row scale or null
-    const float *row_s;   // fp8: per-row scales of the A operand (nrows_out entries)
-    const float *col_s;   // fp8: per-column scales, padded with zeros like col_h
+    const float *row_s;   // fp8, fp16: per-row scales of the A operand (nrows_out entries)
+    const float *col_s;   // fp8, fp16: per-column scales, padded with zeros like col_h
     double *g;            // apply: gradient (nrows_out)
     float *out;           // store: output, row-major with ldo
     int64_t ldo;
@@ -370,8 +374,8 @@ __device__ __forceinline__ void exp2_ds(float xh, float xl, float &kh, float &kl
 }
 
 // K(a_i, b_j) from the accumulator c; rf is the per-row factor: 2 gamma
-// log2(e) (RBF) or 1 (poly, linear), times the row scale in fp8 mode (where
-// c already carries the column scale).
+// log2(e) (RBF) or 1 (poly, linear), times the row scale in the fp8 and fp16
+// modes (where c already carries the column scale).
 template <int KIND>
 __device__ __forceinline__ float kf32(float c, float hr, float hc, float rf, const TcArgs &a)
 {
@@ -457,6 +461,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 {
     constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3;
     constexpr bool FP8 = MODE == MODE_FP8;
+    constexpr bool FP16 = MODE == MODE_FP16;
+    constexpr bool SCALED = FP8 || FP16;  // operand scales restored in the epilogue
     constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
     constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3;
     constexpr int STAGES = SPLIT ? 2 : 4;
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // --------------------------------------------------------- MMA --
-            const uint32_t idesc = make_idesc(TF32 ? 2 : FP8 ? 0 : 1, bn, BM);
+            const uint32_t idesc = make_idesc(TF32 ? 2 : SCALED ? 0 : 1, bn, BM);  // tf32, e4m3 / f16, bf16
             uint32_t it = 0, acc_it = 0;
             bool ok = true, issued = false;
             for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
@@ -598,7 +604,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t row = (int64_t)tile * BM + row_in_tile;
             const bool row_ok = row < a.nrows_out;
             const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
-            const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
+            const float rsc = !SCALED ? 1.f : !row_ok ? 0.f : FP8 ? a.row_s[row] : a.row_s[row] * a.col_s[0];
             const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
             for (int nc = c0; nc < c1; ++nc, ++acc_it) {
                 const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
@@ -807,6 +813,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     constexpr bool ACC = MODE == MODE_ACC || SL;  // the accurate epilogue
     constexpr bool TF32 = MODE == MODE_TF32 || MODE == MODE_TF32X3 || MODE == MODE_ACC;
     constexpr bool FP8 = MODE == MODE_FP8;
+    constexpr bool FP16 = MODE == MODE_FP16;
+    constexpr bool SCALED = FP8 || FP16;  // operand scales restored in the epilogue
     constexpr int MK = TF32 ? 1 : FP8 ? 2 : 0;
     constexpr bool SPLIT = MODE == MODE_BF16X3 || MODE == MODE_TF32X3 || MODE == MODE_ACC;
     constexpr int PLANES = SL ? 4 : SPLIT ? 2 : 1;  // operand planes (hi, lo / the four slices)
@@ -907,7 +915,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {
             // --------------------------------------------------------- MMA --
-            const uint32_t idesc = make_idesc(TF32 ? 2 : FP8 ? 0 : 1, bn, BM2);
+            const uint32_t idesc = make_idesc(TF32 ? 2 : SCALED ? 0 : 1, bn, BM2);  // tf32, e4m3 / f16, bf16
             uint32_t it = 0, acc_it = 0;
             bool ok = true, issued = false;
             for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
@@ -989,7 +997,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 if (ACC) hrl = (KIND == DCD_RBF && row_ok) ? a.row_hl[row] : 0.f;
                 if (SL) rsl = row_ok ? a.row_s[row] * 0x1p-12f : 0.f;  // 2^(e_i - 12)
                 rid = row_ok ? (a.row_id ? a.row_id[row] : (int)row) : -2;
-                const float rsc = FP8 ? (row_ok ? a.row_s[row] : 0.f) : 1.f;
+                const float rsc = !SCALED ? 1.f : !row_ok ? 0.f : FP8 ? a.row_s[row] : a.row_s[row] * a.col_s[0];
                 rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
                 tacc = 0.0;
             }
@@ -1280,6 +1288,7 @@ bool make_map(CUtensorMap *map, const TcOperand &op, int box_rows)
     cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : op.kind == PACK_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = fn(map, dt, 2,
                     const_cast<void *>(op.rows), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1397,9 +1406,9 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     if (sliced && (!acc || !Aop.scale || !Bop.scale || Aop.n_pad > SLICED_N_MAX)) return cudaErrorInvalidValue;
     if (Aop.kind != Bop.kind || Aop.n_pad != Bop.n_pad) return cudaErrorInvalidValue;
     if (Aop.kind != PACK_BF16 && Aop.kind != PACK_TF32 && Aop.kind != PACK_BF16X3 && Aop.kind != PACK_TF32X3 &&
-        Aop.kind != PACK_FP8 && Aop.kind != PACK_SLICED)
+        Aop.kind != PACK_FP8 && Aop.kind != PACK_SLICED && Aop.kind != PACK_FP16)
         return cudaErrorInvalidValue;
-    if (Aop.kind == PACK_FP8 && (!Aop.scale || !Bop.scale)) return cudaErrorInvalidValue;
+    if ((Aop.kind == PACK_FP8 || Aop.kind == PACK_FP16) && (!Aop.scale || !Bop.scale)) return cudaErrorInvalidValue;
     const int kb_elems = k_block_elems(Aop.kind);
     if (Aop.n_pad % kb_elems) return cudaErrorInvalidValue;
     int bn = (int)((ncols + 31) / 32) * 32;
@@ -1471,6 +1480,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
         if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st, pdl);
         if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st, pdl);
+        if (Aop.kind == PACK_FP16) return launch_mode2<MODE_FP16>(npairs, mA, mB, a, kp.kind, st, pdl);
         return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st, pdl);
     }
     int grid = a.items < sms ? a.items : sms;
@@ -1479,6 +1489,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     if (Aop.kind == PACK_BF16X3) return launch_mode<MODE_BF16X3>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_TF32X3) return launch_mode<MODE_TF32X3>(grid, mA, mB, a, kp.kind, st);
     if (Aop.kind == PACK_FP8) return launch_mode<MODE_FP8>(grid, mA, mB, a, kp.kind, st);
+    if (Aop.kind == PACK_FP16) return launch_mode<MODE_FP16>(grid, mA, mB, a, kp.kind, st);
     return launch_mode<MODE_BF16>(grid, mA, mB, a, kp.kind, st);
 }
 

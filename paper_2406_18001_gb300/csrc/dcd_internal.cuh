@@ -117,16 +117,20 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
 // planes of integers in [-64, 64] (exact in bf16), a_ik ~ sc_i (s0 2^-6 + s1 2^-13 + s2 2^-20 +
 // s3 2^-27); the per-row scales travel beside the rows like FP8 scales.  The products of two
 // such rows are exact integers, and their FP32-accumulated sums stay exact for n_pad <= 1024.
+// fp16: the matrix scaled by one power of two sc with max |a_ik| / sc in [2^14, 2^15) and
+// rounded to fp16 (11 significant bits), a_ik ~ sc q_ik; sc travels as a per-row scale array
+// holding the same value for every row (the block's epilogue reads one row's and one column's).
 enum PackKind : int {
-    PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4, PACK_FP8 = 5, PACK_SLICED = 6
+    PACK_BF16 = 0, PACK_TF32 = 1, PACK_F64 = 2, PACK_BF16X3 = 3, PACK_TF32X3 = 4, PACK_FP8 = 5, PACK_SLICED = 6,
+    PACK_FP16 = 7
 };
 constexpr int64_t SLICED_N_MAX = 1024;  // exact slice-product sums up to this many features
 struct TcOperand {
     const void *rows;     // packed matrix, row-major
     int64_t nrows;
     int64_t n_pad;        // features per half, multiple of the k-block
-    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3, PACK_FP8 or PACK_SLICED
-    const float *scale = nullptr;  // PACK_FP8, PACK_SLICED: per-row scales (padded with zeros like the rows)
+    int kind;             // PACK_BF16, PACK_TF32, PACK_BF16X3, PACK_TF32X3, PACK_FP8, PACK_SLICED or PACK_FP16
+    const float *scale = nullptr;  // PACK_FP8, PACK_SLICED, PACK_FP16: per-row scales (padded with zeros)
     // the data-matrix row each packed row holds (nrows entries; nullptr: row r holds row r).
     // The RBF kernel of a row with itself is 1: where the ids of a block's row and column
     // are equal the epilogues take d^2 = 0 instead of the expansion, whose cancellation
@@ -216,6 +220,18 @@ cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t
                                void *dst, int *err, cudaStream_t st, const float *f0 = nullptr, float *d0 = nullptr,
                                const float *f1 = nullptr, float *d1 = nullptr, const float *f2 = nullptr,
                                float *d2 = nullptr);
+// The largest magnitude over rows `rows` (or the first count) of a dense
+// source, folded by atomicMax into *bits (FP32 bits; zero it first).
+cudaError_t launch_absmax_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                               int64_t count, unsigned *bits, int *err, cudaStream_t st,
+                               const float *src_scale = nullptr);
+// fp16 rows (PACK_FP16) of rows `rows` (or the first count) of a dense
+// source, all scaled by the power of two that *gbits (launch_absmax_rows over
+// every row that shares the scale) fixes, written to sc[r] for each row; an
+// FP8 source is dequantised first.  dst rows are n_pad fp16 values (zero padded).
+cudaError_t launch_pack_fp16(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                             void *dst, int64_t n_pad, int64_t count, float *sc, const unsigned *gbits, int *err,
+                             cudaStream_t st, const float *src_scale = nullptr);
 // Sliced rows (PACK_SLICED) of rows `rows` (or the first count) of a dense
 // source, with their power-of-two scales in sc (count floats); an FP8
 // source is dequantised first.  dst rows are 4 planes of n_pad bf16.

@@ -220,6 +220,85 @@ __global__ void pack_sliced_kernel(const void *src, int dtype, int64_t ld, int64
     }
 }
 
+// The largest magnitude over rows `rows` (or the first count) of a dense
+// source, folded into *bits (the FP32 bit pattern, which orders like the value
+// for non-negative floats) by atomicMax; a non-finite value sets
+// DEV_BAD_VALUE.  One warp per row.
+__global__ void absmax_rows_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                   int64_t count, unsigned *bits, int *err, const float *src_scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= count) return;
+    const int64_t sr = rows ? (int64_t)rows[r] : r;
+    if (sr < 0 || sr >= m) return;  // the pack reports bad indices
+    const float rsc = dtype == DCD_FP8E4M3 ? src_scale[sr] : 0.f;
+    float mx = 0.f;
+    bool bad = false;
+    for (int64_t c = lane; c < n; c += 32) {
+        const float v = load_as_f32(src, dtype, sr * ld + c, rsc);
+        bad |= !isfinite(v);
+        mx = fmaxf(mx, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) set_error(err, DEV_BAD_VALUE);
+        return;
+    }
+    if (lane == 0) atomicMax(bits, __float_as_uint(mx));
+}
+
+// One warp per row.  The scale is one power of two for every row, sc = 2^(e -
+// 15) with the largest magnitude over the matrix in [2^(e-1), 2^e) (from
+// *gbits), so that |a| / sc < 2^15 (fp16's largest finite value is 65504);
+// q = fp16(a / sc) rounds to nearest even (the division by a power of two is
+// exact).  fp16's exponent range keeps every value down to 2^-29 of the
+// largest at full precision.  A zero matrix gets sc = 2^-15.  sc[r] = sc for
+// every row; columns n..n_pad-1 are zero.
+__global__ void pack_fp16_kernel(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                                 __half *dst, int64_t n_pad, int64_t count, float *sc, const unsigned *gbits,
+                                 int *err, const float *src_scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= count) return;
+    const int64_t sr = rows ? (int64_t)rows[r] : r;
+    const bool inb = sr >= 0 && sr < m;
+    if (!inb && lane == 0) set_error(err, DEV_BAD_INDEX);
+    const float rsc = (dtype == DCD_FP8E4M3 && inb) ? src_scale[sr] : 0.f;
+    const float mx = __uint_as_float(*gbits);
+    int e = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);
+    e = max(e, -110);  // the scale 2^(e - 15) stays a normal FP32 number
+    if (lane == 0) sc[r] = ldexpf(1.f, e - 15);
+    __half *d = dst + r * n_pad;
+    for (int64_t c = lane; c < n_pad; c += 32)
+        d[c] = __float2half_rn((c < n && inb) ? ldexpf(load_as_f32(src, dtype, sr * ld + c, rsc), 15 - e) : 0.f);
+}
+
+cudaError_t launch_absmax_rows(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                               int64_t count, unsigned *bits, int *err, cudaStream_t st, const float *src_scale)
+{
+    if (count <= 0) return cudaSuccess;
+    if (dtype == DCD_FP8E4M3 && !src_scale) return cudaErrorInvalidValue;
+    const int64_t blocks = (count * 32 + 255) / 256;
+    absmax_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, count, bits, err, src_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fp16(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
+                             void *dst, int64_t n_pad, int64_t count, float *sc, const unsigned *gbits, int *err,
+                             cudaStream_t st, const float *src_scale)
+{
+    if (count <= 0) return cudaSuccess;
+    if (!sc || !gbits || n_pad < n || n_pad % 64 || (dtype == DCD_FP8E4M3 && !src_scale))
+        return cudaErrorInvalidValue;
+    const int64_t blocks = (count * 32 + 255) / 256;
+    pack_fp16_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dtype, ld, m, n, rows, (__half *)dst, n_pad, count, sc,
+                                                       gbits, err, src_scale);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_sliced(const void *src, int dtype, int64_t ld, int64_t m, int64_t n, const int32_t *rows,
                                void *dst, int64_t n_pad, int64_t count, float *sc, int *err, cudaStream_t st,
                                const float *src_scale)
@@ -404,9 +483,9 @@ cudaError_t launch_f64_to_f32(const double *src, int64_t count, float *dst, cuda
 // h[r] = gamma * log2(e) * ||x_r||^2 of the packed (already rounded) row, for
 // the RBF expansion ||a||^2 + ||b||^2 - 2 a.b (Section 5.2); 0 for the other
 // kernels.  For split rows the norm is the one the three MMAs reproduce,
-// sum(hi^2 + 2 hi lo), so that a row's distance to itself stays ~0; FP8 rows
-// take the dequantised norm rscale[r]^2 * sum value(q)^2.  One warp per row,
-// FP64 partial sums, fixed order.
+// sum(hi^2 + 2 hi lo), so that a row's distance to itself stays ~0; FP8 and
+// FP16 rows take the dequantised norm rscale[r]^2 * sum value(q)^2.  One warp
+// per row, FP64 partial sums, fixed order.
 __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, int64_t m, double scale, float *h,
                                  const float *rscale, float *h_lo)
 {
@@ -439,6 +518,18 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
             h[r] = vh;
             if (h_lo) h_lo[r] = (float)(v - (double)vh);
         }
+        return;
+    }
+    if (kind == PACK_FP16) {
+        // fp16 values: their squares are exact in FP64 and summed in FP64; times the row scale^2
+        const __half *row = (const __half *)packed + r * n_pad;
+        double sd = 0.0;
+        for (int64_t c = lane; c < n_pad; c += 32) {
+            const double v = __half2float(row[c]);
+            sd = fma(v, v, sd);
+        }
+        for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        if (lane == 0) h[r] = (float)(scale * sd * (double)rscale[r] * (double)rscale[r]);
         return;
     }
     if (kind == PACK_TF32X3) {
@@ -487,7 +578,7 @@ __global__ void row_terms_kernel(const void *packed, int kind, int64_t n_pad, in
 cudaError_t launch_row_terms(const void *packed, int kind, int64_t n_pad, int64_t m, const KernelParams &kp,
                              float *h, cudaStream_t st, const float *rscale, float *h_lo)
 {
-    if ((kind == PACK_FP8 || kind == PACK_SLICED) && !rscale) return cudaErrorInvalidValue;
+    if ((kind == PACK_FP8 || kind == PACK_SLICED || kind == PACK_FP16) && !rscale) return cudaErrorInvalidValue;
     if (h_lo && kind != PACK_TF32X3 && kind != PACK_SLICED) return cudaErrorInvalidValue;
     if (m <= 0) return cudaSuccess;
     double scale = (kp.kind == DCD_RBF) ? kp.gamma * 1.4426950408889634 : 0.0;

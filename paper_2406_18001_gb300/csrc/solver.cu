@@ -147,7 +147,7 @@ KernelParams to_kp(const dcd_kernel *k) { return KernelParams{k->kind, k->degree
 bool is_tc(int prec)
 {
     return prec == DCD_PREC_BF16 || prec == DCD_PREC_TF32 || prec == DCD_PREC_BF16X3 || prec == DCD_PREC_TF32X3 ||
-           prec == DCD_PREC_FP8;
+           prec == DCD_PREC_FP8 || prec == DCD_PREC_FP16;
 }
 
 // packed operand kind of a tensor-core precision
@@ -157,6 +157,7 @@ int pack_kind(int prec)
            : prec == DCD_PREC_BF16X3 ? PACK_BF16X3
            : prec == DCD_PREC_TF32X3 ? PACK_TF32X3
            : prec == DCD_PREC_FP8    ? PACK_FP8
+           : prec == DCD_PREC_FP16   ? PACK_FP16
                                      : PACK_BF16;
 }
 
@@ -170,7 +171,7 @@ struct Operand {
     int64_t n_pad = 0;
     int kind = PACK_BF16;
     float *row_h = nullptr;
-    float *row_s = nullptr;  // PACK_FP8: per-row scales
+    float *row_s = nullptr;  // PACK_FP8, PACK_FP16: per-row scales
 };
 
 // Per-phase device times of an outer step: an event pair per phase, recorded
@@ -266,7 +267,7 @@ struct Solver {
     cudaEvent_t csr_fork = nullptr, csr_join = nullptr;
     void *As = nullptr;           // packed sampled rows (tc)
     float *col_h = nullptr, *col_w = nullptr;
-    float *col_s = nullptr;       // fp8: scales of the sampled rows
+    float *col_s = nullptr;       // fp8, fp16: scales of the sampled rows
     const float *src_scale = nullptr;  // the row scales of an FP8 data matrix (device)
     int32_t *S = nullptr;
     void *Kss = nullptr;
@@ -351,6 +352,8 @@ struct Solver {
         const bool ref_op = acc_ref && (sliced_ref || o.prec != DCD_PREC_TF32X3);
         const int kind_r = sliced_ref ? PACK_SLICED : PACK_TF32X3;
         const bool fp8 = tcd && pack_kind(o.prec) == PACK_FP8;
+        const bool fp16 = tcd && pack_kind(o.prec) == PACK_FP16;
+        const bool scaled = fp8 || fp16;  // per-row scales beside the packed rows
         const bool fp8in = !csr && A->dtype == DCD_FP8E4M3;
         // the look-ahead needs a stream of its own to fork from, graphs allowed, no per-phase
         // timers, and a full step that fits one cluster recurrence
@@ -381,8 +384,8 @@ struct Solver {
             float *cv32 = (float *)ar.take(conv32 ? sizeof(float) * nnz : 0);
             double *cv64 = (double *)ar.take(conv64 ? sizeof(double) * nnz : 0);
             float *hsc = (float *)ar.take(host && fp8in ? sizeof(float) * m : 0);
-            float *rsc = (float *)ar.take(fp8 ? sizeof(float) * m : 0);
-            float *csc = (float *)ar.take(fp8 ? sizeof(float) * col_pad : 0);
+            float *rsc = (float *)ar.take(scaled ? sizeof(float) * m : 0);
+            float *csc = (float *)ar.take(scaled ? sizeof(float) * col_pad : 0);
             float *nrm32 = (float *)ar.take(csr ? sizeof(float) * m : 0);
             double *nrm64 = (double *)ar.take(csr ? sizeof(double) * m : 0);
             double *yv = (double *)ar.take(host ? sizeof(double) * m : 0);
@@ -411,7 +414,7 @@ struct Solver {
             int32_t *sidx_b = (int32_t *)ar.take(la_pos ? sizeof(int32_t) * col_pad : 0);
             void *as_b = ar.take(la_pos ? (size_t)sb * row_bytes : 0, 1024);
             float *ch_b = (float *)ar.take(la_pos ? sizeof(float) * col_pad : 0);
-            float *cs_b = (float *)ar.take(la_pos && fp8 ? sizeof(float) * col_pad : 0);
+            float *cs_b = (float *)ar.take(la_pos && scaled ? sizeof(float) * col_pad : 0);
             void *kss_b = ar.take(la_pos ? (size_t)sb * sb * 4 : 0);
             double *lb_b = (double *)ar.take(la_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             uint64_t *crl = (uint64_t *)ar.take(la_pos ? 2 * sizeof(uint64_t) : 0);
@@ -523,12 +526,12 @@ struct Solver {
         DCD_TRY(cudaMemsetAsync(col_w, 0, sizeof(float) * col_pad, st));
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
         if (tcd) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
-        if (fp8) DCD_TRY(cudaMemsetAsync(col_s, 0, sizeof(float) * col_pad, st));
+        if (scaled) DCD_TRY(cudaMemsetAsync(col_s, 0, sizeof(float) * col_pad, st));
         if (la_pos) {
             DCD_TRY(cudaMemsetAsync(sbuf[1].S, 0, sizeof(int32_t) * col_pad, st));
             DCD_TRY(cudaMemsetAsync(sbuf[1].col_h, 0, sizeof(float) * col_pad, st));
             DCD_TRY(cudaMemsetAsync(sbuf[1].As, 0, (size_t)sb * row_bytes, st));
-            if (fp8) DCD_TRY(cudaMemsetAsync(sbuf[1].col_s, 0, sizeof(float) * col_pad, st));
+            if (scaled) DCD_TRY(cudaMemsetAsync(sbuf[1].col_s, 0, sizeof(float) * col_pad, st));
             DCD_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
             DCD_TRY(cudaEventCreateWithFlags(&la_fork, cudaEventDisableTiming));
             DCD_TRY(cudaEventCreateWithFlags(&la_join, cudaEventDisableTiming));
@@ -571,6 +574,14 @@ struct Solver {
                 DCD_TRY(launch_quantize_rows(vals, A->dtype, A->ld, m, n, nullptr, src_scale, (uint8_t *)op.packed,
                                              n_pad, op.row_s, m, err, st));
                 dcd_status qs = check_device_error();  // non-finite values or scales: EINVAL
+                if (qs != DCD_OK) return qs;
+            } else if (fp16) {
+                // one power-of-two scale for the matrix, from its largest magnitude (err[5], zeroed above)
+                unsigned *gbits = (unsigned *)(err + 5);
+                DCD_TRY(launch_absmax_rows(vals, A->dtype, A->ld, m, n, nullptr, m, gbits, err, st, src_scale));
+                DCD_TRY(launch_pack_fp16(vals, A->dtype, A->ld, m, n, nullptr, op.packed, n_pad, m, op.row_s, gbits, err,
+                                         st, src_scale));
+                dcd_status qs = check_device_error();  // non-finite values: EINVAL
                 if (qs != DCD_OK) return qs;
             } else {
                 DCD_TRY(launch_pack_rows(vals, A->dtype, A->ld, m, n, nullptr, op.packed, op.kind, n_pad, m, err, st,
@@ -719,7 +730,7 @@ struct Solver {
     cudaError_t gather_op(int64_t ncols, const Operand &x, void *Asx, float *chx)
     {
         if (!tc) return cudaSuccess;
-        const bool f8 = x.kind == PACK_FP8;
+        const bool f8 = x.kind == PACK_FP8 || x.kind == PACK_FP16;  // per-row scales gathered too
         return launch_gather_rows(x.packed, packed_row_bytes(x.kind, x.n_pad), S, ncols, m, Asx, err, st, x.row_h,
                                   chx, f8 ? x.row_s : nullptr, f8 ? col_s : nullptr);
     }
@@ -778,7 +789,8 @@ struct Solver {
             e = clear_col_w_tail(ncols);
             if (e != cudaSuccess) return cuda_status(e);
             TcOperand Aop{x.packed, m, x.n_pad, x.kind, x.row_s};
-            TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 ? col_s : nullptr, S};
+            TcOperand Bop{Asx, ncols, x.n_pad, x.kind, x.kind == PACK_FP8 || x.kind == PACK_FP16 ? col_s : nullptr,
+                          S};
             return cuda_status(
                 launch_block_tc(Aop, Bop, kp, x.row_h, chx, col_w, rs, g, nullptr, 0, m, ncols, err, st, false, &tsplit));
         }
@@ -961,7 +973,7 @@ struct Solver {
         const int64_t ncols = cnt * o.b;
         // the sample reads the position in ctr_la[q] and leaves the next one in ctr_la[1 - q]
         DCD_TRY(launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, Bq.S, err, s2, ctr_la + (1 - q)));
-        const bool f8 = op.kind == PACK_FP8;
+        const bool f8 = op.kind == PACK_FP8 || op.kind == PACK_FP16;  // per-row scales gathered too
         DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2,
                                    op.row_h, Bq.col_h, f8 ? op.row_s : nullptr, f8 ? Bq.col_s : nullptr));
         TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s, Bq.S};
@@ -1677,9 +1689,9 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     size_t orh = place(cur, sizeof(float) * nrows);
     size_t och = place(cur, sizeof(float) * cpad);
     size_t ocw = place(cur, sizeof(float) * cpad);
-    const bool fp8 = pk == PACK_FP8;
-    size_t ors = place(cur, (fp8 || sliced) ? sizeof(float) * nrows : 0);
-    size_t ocs = place(cur, (fp8 || sliced) ? sizeof(float) * cpad : 0);
+    const bool fp8 = pk == PACK_FP8, fp16 = pk == PACK_FP16;
+    size_t ors = place(cur, (fp8 || fp16 || sliced) ? sizeof(float) * nrows : 0);
+    size_t ocs = place(cur, (fp8 || fp16 || sliced) ? sizeof(float) * cpad : 0);
     size_t orl = place(cur, accurate ? sizeof(float) * nrows : 0);
     size_t ocl = place(cur, accurate ? sizeof(float) * cpad : 0);
     // points form: global row ids (when offset) and column ids (-1 without col_ids)
@@ -1702,8 +1714,8 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
     int *err = (int *)(base + oe);
     void *pa = base + oa, *pb = base + ob;
     float *rh = (float *)(base + orh), *ch = (float *)(base + och), *cw = (float *)(base + ocw);
-    float *rsa = (fp8 || sliced) ? (float *)(base + ors) : nullptr;
-    float *rsb = (fp8 || sliced) ? (float *)(base + ocs) : nullptr;
+    float *rsa = (fp8 || fp16 || sliced) ? (float *)(base + ors) : nullptr;
+    float *rsb = (fp8 || fp16 || sliced) ? (float *)(base + ocs) : nullptr;
     DCD_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     DCD_TRY(cudaMemsetAsync(ch, 0, sizeof(float) * cpad, st));
     DCD_TRY(cudaMemsetAsync(cw, 0, sizeof(float) * cpad, st));
@@ -1725,6 +1737,21 @@ dcd_status component_block(const dcd_matrix *A, const dcd_kernel *k, int32_t pre
                                      rsa, nrows, err, st));
         DCD_TRY(launch_quantize_rows(P->values, P->dtype, P->ld, P->m, P->n, pcols, P->row_scale, (uint8_t *)pb,
                                      n_pad, rsb, ncols, err, st));
+    } else if (fp16) {
+        // one power-of-two scale for both operands: the largest magnitude over every row of A (the
+        // scale the solver's operand takes) and of the points (err[2])
+        unsigned *gbits = (unsigned *)(err + 2);
+        DCD_TRY(cudaMemsetAsync(gbits, 0, sizeof(unsigned), st));
+        DCD_TRY(cudaMemsetAsync(rsb, 0, sizeof(float) * cpad, st));
+        DCD_TRY(launch_absmax_rows(A->values, A->dtype, A->ld, A->m, A->n, nullptr, A->m, gbits, err, st,
+                                   A->row_scale));
+        if (pts)
+            DCD_TRY(launch_absmax_rows(P->values, P->dtype, P->ld, P->m, P->n, nullptr, P->m, gbits, err, st,
+                                       P->row_scale));
+        DCD_TRY(launch_pack_fp16(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, n_pad, nrows, rsa, gbits, err, st,
+                                 A->row_scale));
+        DCD_TRY(launch_pack_fp16(P->values, P->dtype, P->ld, P->m, P->n, pcols, pb, n_pad, ncols, rsb, gbits, err,
+                                 st, P->row_scale));
     } else {
         DCD_TRY(launch_pack_rows(A->values, A->dtype, A->ld, A->m, A->n, rows, pa, pk, n_pad, nrows, err, st,
                                  A->row_scale));

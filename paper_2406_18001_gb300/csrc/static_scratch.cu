@@ -86,9 +86,10 @@ extern "C" dcd_status dcd_kernel_block_static(const dcd_matrix *A, const dcd_ker
     if (vs != DCD_OK) return vs;
     if ((vs = validate_kernel(k)) != DCD_OK) return vs;
     if (prec != DCD_PREC_FP64 && prec != DCD_PREC_BF16 && prec != DCD_PREC_TF32 && prec != DCD_PREC_BF16X3 &&
-        prec != DCD_PREC_TF32X3 && prec != DCD_PREC_FP8 && prec != DCD_PREC_REFRESH)
+        prec != DCD_PREC_TF32X3 && prec != DCD_PREC_FP8 && prec != DCD_PREC_REFRESH && prec != DCD_PREC_FP16)
         return DCD_EINVAL;
     if (prec == DCD_PREC_REFRESH) return DCD_EUNSUPPORTED;  // an apply-only precision
+    if (prec == DCD_PREC_FP16) return DCD_EUNSUPPORTED;     // its per-row scales have no place in the scratch
     if (nrows < 0 || ncols < 0 || !cols || !out || ldo < ncols) return DCD_EINVAL;
     if (!rows && nrows > A->m) return DCD_EINVAL;
     if (A->fmt == DCD_CSR) return DCD_EUNSUPPORTED;  // the CSR block's column map is sized per call

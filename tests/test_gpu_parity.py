@@ -53,7 +53,18 @@ def round_split(A):
     return hi.astype(np.float64) + lo.astype(np.float64)
 
 
-ROUND = {"bf16": round_bf16, "bf16x3": round_split}
+def round_fp16(A):
+    """The fp16 operand: the FP32 values scaled by 2^(e - 15), with the
+    matrix's largest magnitude in [2^(e-1), 2^e), rounded to fp16 (nearest
+    even) and scaled back."""
+    a = np.ascontiguousarray(A, dtype=np.float32).astype(np.float64)
+    mx = np.max(np.abs(a))
+    e = max(int(np.frexp(mx)[1]) if mx > 0 else 0, -110)
+    sc = np.ldexp(1.0, e - 15)
+    return (a / sc).astype(np.float16).astype(np.float64) * sc
+
+
+ROUND = {"bf16": round_bf16, "bf16x3": round_split, "fp16": round_fp16}
 
 
 def round_tf32(A):
@@ -75,7 +86,7 @@ ROUND["tf32x3"] = round_split_tf32
 # max |K - K_ref| / max |K_ref| against the FP64 kernel of the rounded operand;
 # split tf32 is bounded by the FP32 epilogue (expanded distance, exp2), about
 # 3.5e-6 measured on GB300, rather than by its operands
-TC_TOL = {"bf16": 3e-5, "tf32": 3e-5, "bf16x3": 3e-5, "tf32x3": 1e-5}
+TC_TOL = {"bf16": 3e-5, "tf32": 3e-5, "bf16x3": 3e-5, "tf32x3": 1e-5, "fp16": 3e-5}
 
 KERNELS = [("rbf", dict(gamma=0.35)), ("poly", dict(coef0=1.0, degree=3)), ("linear", {})]
 
@@ -107,7 +118,7 @@ def test_kernel_block_fp64(kind, kw):
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3", "fp16"])
 @pytest.mark.parametrize("kind,kw", KERNELS)
 def test_kernel_block_tensor_core(prec, kind, kw):
     g = np.random.default_rng(2)
@@ -124,7 +135,7 @@ def test_kernel_block_tensor_core(prec, kind, kw):
         assert np.max(np.abs(got - exact)) <= 1e-5 * np.max(np.abs(exact))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32", "bf16x3", "tf32x3", "fp16"])
 @pytest.mark.parametrize("kind,kw", KERNELS)
 def test_kernel_block_apply(prec, kind, kw):
     """g += rs * K(A, A_cols) w for every row, block never stored."""
@@ -147,7 +158,7 @@ def test_kernel_block_apply(prec, kind, kw):
     assert np.max(np.abs(got - want)) <= tol * scale
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3", "fp8"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp16"])
 @pytest.mark.parametrize("m,ncols,n", [(1100, 600, 300), (257, 33, 16), (3000, 1024, 64), (129, 300, 200)])
 def test_kernel_block_apply_pair_tiles(prec, m, ncols, n):
     """The apply form runs on CTA pairs over 256-row tiles: ragged pair tiles
@@ -386,7 +397,7 @@ def test_graph_replay_and_enqueue_match_direct_launches(problem, prec):
         pl.close()
 
 
-@pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("fp8", True), ("tf32x3", False)])
+@pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("fp8", True), ("tf32x3", False), ("fp16", False)])
 def test_lookahead_matches_one_stream_steps(prec, fp8):
     """The look-ahead (next step's sample, Gram and prep on a second stream,
     ping-pong step buffers, even/odd step graphs) must give the iterates of
@@ -453,11 +464,14 @@ def test_svm_rejects_non_binary_labels():
 # alpha 1e-4; split tf32 to alpha 1e-5): their kernel entries carry the FP32
 # epilogue's ~2.5e-7 relative error, which bounds the objective at long
 # chains (s = 32) near 1e-7.
-ALPHA_TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "tf32": 1e-3, "bf16": 3e-3}
-OBJ_TOL = {"tf32x3": 1e-6, "bf16x3": 1e-6, "tf32": 1e-4, "bf16": 3e-4}
+# fp16 (11 significant bits, per-row power-of-two scales) meets the objective
+# target; its alpha error reaches 3.3e-4 to 3.8e-4 on the long K-SVM and
+# look-ahead runs here (measured on GB300), so it is held to 1e-3 there.
+ALPHA_TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "tf32": 1e-3, "bf16": 3e-3, "fp16": 1e-3}
+OBJ_TOL = {"tf32x3": 1e-6, "bf16x3": 1e-6, "tf32": 1e-4, "bf16": 3e-4, "fp16": 1e-6}
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16"])
 @pytest.mark.parametrize("s,b", [(1, 16), (16, 16), (7, 8), (40, 4), (9, 12), (64, 16)])
 def test_bdcd_mixed_matches_oracle(prec, s, b):
     """s = 1: the single-block path; (7, 8): the one-CTA refined chain with an
@@ -512,7 +526,7 @@ def test_bdcd_fp64_near_singular_blocks_fall_back():
     assert rel(al.cpu().numpy(), want) < 1e-8
 
 
-@pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("tf32x3", False), ("fp8", True)])
+@pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("tf32x3", False), ("fp8", True), ("fp16", False)])
 def test_lookahead_solve_matches_oracle(prec, fp8):
     """The look-ahead step the bench times (next step's products on a second
     stream, the block as the chain's programmatic dependent, even/odd step
@@ -535,7 +549,7 @@ def test_lookahead_solve_matches_oracle(prec, fp8):
     assert st["iters_done"] == H
     want = oracle.bdcd_krr(A64, p.y, ko, lam, b, H, seed=7)
     a = al.cpu().numpy()
-    assert rel(a, want) < 1e-4
+    assert rel(a, want) < (ALPHA_TOL["fp16"] if prec == "fp16" else 1e-4)
     f_got = oracle.krr_objective(A64, p.y, ko, lam, a)
     f_want = oracle.krr_objective(A64, p.y, ko, lam, want)
     assert abs(f_got - f_want) <= 1e-6 * abs(f_want)
@@ -567,7 +581,7 @@ def test_bdcd_long_chain_blocked_panels(prec, m, s, b):
     assert abs(f_got - f_want) <= OBJ_TOL.get(prec, 1e-6) * abs(f_want)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16"])
 @pytest.mark.parametrize("s", [8, 32])
 def test_dcd_mixed_matches_oracle(prec, s):
     """K-SVM-L1 on the blobs; s = 32 is the CSR workload's step size (the
