@@ -42,8 +42,8 @@ UNIT = "coordinate updates/s"
 # an ncu capture: (prec, m, n, b, s, first 16 hex digits of the sha256 of
 # csrc/block_tc.cu when it was taken) -> bytes.  A changed kernel source
 # matches no entry, so its traffic reads null until it is captured again.
-NCU_TRAFFIC = {("bf16x3", 50000, 512, 16, 64, "89d134a9821018ef"): 109.13e6,
-               ("bf16", 50000, 512, 16, 64, "89d134a9821018ef"): 52.93e6}
+NCU_TRAFFIC = {("fp16", 50000, 512, 16, 64, "c2490b8650123cce"): 53.15e6,
+               ("bf16x3", 50000, 512, 16, 64, "c2490b8650123cce"): 109.08e6}
 WORKLOAD = "K-RR BDCD dense m=50000 n=512 RBF sigma=1 lambda=1e-4 b=16"
 
 
