@@ -81,7 +81,11 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // p + q, whose FP32 sums are exact integers; accurate epilogue (pairs only).
 constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5,
               MODE_SLICED = 6, MODE_FP16 = 7;
-constexpr int SLICED_BN = 128;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
+constexpr int SLICED_BN = 128;
+// The apply's fast RBF epilogue factors K_ij w_j = 2^(rf c - h_i) (w_j 2^(-h_j)) when every row and
+// column term h = gamma log2(e) ||x||^2 of the launch's warp is at most this (both factors then stay
+// well inside the FP32 range); otherwise it evaluates 2^(min(0, rf c - h_i - h_j)) w_j.
+constexpr float RBF_FACTOR_HMAX = 64.f;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 320;
@@ -986,6 +990,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         const int *cid = (const int *)(cst + 512);  // staged column ids (-1 past the block)
         double tacc = 0.0;  // this half's row sum over the tile's chunks so far, in chunk order
         const int nch = a.nchunks;
+        bool fast_cols = false, fast_row = false;  // the factored RBF form applies (warp-uniform)
         for (int i = 0; ok && i < nunits; ++i, ++acc_it) {
             int item, nc;
             pair_unit(a, pair, npairs, ranged, u0, u1, i, item, nc);
@@ -999,6 +1004,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 rid = row_ok ? (a.row_id ? a.row_id[row] : (int)row) : -2;
                 const float rsc = !SCALED ? 1.f : !row_ok ? 0.f : FP8 ? a.row_s[row] : a.row_s[row] * a.col_s[0];
                 rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
+                fast_row = __all_sync(0xffffffffu, hr <= RBF_FACTOR_HMAX);
                 tacc = 0.0;
             }
             const bool whole = !ranged || (item * nch >= u0 && (item + 1) * nch <= u1);
@@ -1013,6 +1019,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             // the 32 columns' kernel values (`own`: bit q set where column q is this row's own
             // sample, d^2 = 0 there; the checked form runs only for the rare groups that hold one)
             auto group_terms = [&](const uint32_t(&r)[32], int j0, unsigned own, float &p0, float &p1) {
+                if (KIND == DCD_RBF && !FP8 && !ACC && !own && fast_cols && fast_row) {
+                    // K_ij w_j = 2^(rf c - h_i) (w_j 2^(-h_j)): the exponent's row and column terms split
+                    // apart (both <= RBF_FACTOR_HMAX, so neither factor leaves the FP32 range); rf c <=
+                    // h_i + h_j by Cauchy-Schwarz, so the first factor is at most 2^(h_j)
+                    const float4 *f4 = (const float4 *)(cst + 384 + j0);
+                    const float nh = -hr;
+#pragma unroll
+                    for (int q4 = 0; q4 < 8; ++q4) {
+                        const float4 ff = f4[q4];
+                        p0 = fmaf(ex2f(fmaf(__uint_as_float(r[4 * q4]), rf, nh)), ff.x, p0);
+                        p1 = fmaf(ex2f(fmaf(__uint_as_float(r[4 * q4 + 1]), rf, nh)), ff.y, p1);
+                        p0 = fmaf(ex2f(fmaf(__uint_as_float(r[4 * q4 + 2]), rf, nh)), ff.z, p0);
+                        p1 = fmaf(ex2f(fmaf(__uint_as_float(r[4 * q4 + 3]), rf, nh)), ff.w, p1);
+                    }
+                    return;
+                }
                 const float4 *h4 = (const float4 *)(cst + j0), *w4 = (const float4 *)(cst + 128 + j0),
                              *s4 = (const float4 *)(cst + 256 + j0);
 #pragma unroll
@@ -1155,7 +1177,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
                 } else {
                     cst[128 + j] = a.col_w[cbase + j];
                     if (FP8) cst[256 + j] = a.col_s[cbase + j];
+                    // the RBF's column factor w_j 2^(-h_j) of the factored form below
+                    if (KIND == DCD_RBF && !FP8) cst[384 + j] = a.col_w[cbase + j] * ex2f(-a.col_h[cbase + j]);
                 }
+            }
+            if (KIND == DCD_RBF && !ACC && !FP8) {  // the factored form needs every h_j <= RBF_FACTOR_HMAX
+                float hm = 0.f;
+                for (int j = lane; j < (cg1 - cg0) * 32; j += 32) hm = fmaxf(hm, cst[j]);
+                fast_cols = __all_sync(0xffffffffu, hm <= RBF_FACTOR_HMAX);
             }
             __syncwarp();
             const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
