@@ -434,7 +434,8 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     upd_per_step = args.s * args.b
     H = (args.warmup + args.steps + 8) * args.s
-    plan = B.Plan(1, A, y, k, args.lam, args.b, args.s, H, seed=rank, prec=args.prec)
+    plan = B.Plan(1, A, y, k, args.lam, args.b, args.s, H, seed=rank, prec=args.prec,
+                  flags=B.FLAG_NO_DEFER if args.no_defer else 0)
     for _ in range(args.warmup):
         plan.run(1)
     torch.cuda.synchronize()
@@ -1284,6 +1285,9 @@ def main():
                     choices=["bf16", "tf32", "bf16x3", "tf32x3", "fp8", "fp64", "refresh", "fp16"])
     ap.add_argument("--roof-steps", type=int, default=50)
     ap.add_argument("--traffic", type=float, default=None, help="dram bytes per launch from an ncu capture")
+    ap.add_argument("--no-defer", action="store_true",
+                    help="time the look-ahead steps with the in-order gradient (each recurrence after the "
+                         "previous step's block)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
     ap.add_argument("--no-also", action="store_true",

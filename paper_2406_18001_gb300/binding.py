@@ -24,6 +24,7 @@ PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP8, PREC_BF16X3, PREC_TF32X3, PREC_REFRES
 FLAG_GRAD_VALID, FLAG_HOST_IO, FLAG_PHASE_TIMERS, FLAG_NO_GRAPH, FLAG_REFRESH = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_LITERAL = 0x20
 FLAG_CSR_FULL_PASS = 0x40
+FLAG_NO_DEFER = 0x80
 
 PREC_NAMES = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp8": PREC_FP8, "bf16x3": PREC_BF16X3,
               "tf32x3": PREC_TF32X3, "refresh": PREC_REFRESH, "fp16": PREC_FP16}

@@ -81,11 +81,11 @@ constexpr int RING_BYTES = 4 * (A_STAGE + B_STAGE);  // 4 single stages or 2 spl
 // p + q, whose FP32 sums are exact integers; accurate epilogue (pairs only).
 constexpr int MODE_BF16 = 0, MODE_TF32 = 1, MODE_BF16X3 = 2, MODE_TF32X3 = 3, MODE_FP8 = 4, MODE_ACC = 5,
               MODE_SLICED = 6, MODE_FP16 = 7;
-constexpr int SLICED_BN = 128;
+constexpr int SLICED_BN = 128;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
 // The apply's fast RBF epilogue factors K_ij w_j = 2^(rf c - h_i) (w_j 2^(-h_j)) when every row and
 // column term h = gamma log2(e) ||x||^2 of the launch's warp is at most this (both factors then stay
 // well inside the FP32 range); otherwise it evaluates 2^(min(0, rf c - h_i - h_j)) w_j.
-constexpr float RBF_FACTOR_HMAX = 64.f;  // N-chunk of the sliced apply: 4 accumulators fill the 512 TMEM columns
+constexpr float RBF_FACTOR_HMAX = 64.f;
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
 constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
 constexpr int NTHREADS = 320;
@@ -320,6 +320,7 @@ struct TcArgs {
     // where they are equal (d^2 = 0 on a row's own sample)
     const int32_t *row_id;
     const int32_t *col_id;
+    int dep_wait;         // apply: the epilogue waits for the grid before this one (griddepcontrol.wait)
 };
 
 // ------------------------------------------------- double-single helpers --
@@ -972,8 +973,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     } else {
         // ------------------------------------------------------ epilogue --
         // the coefficients and the gradient may come from the grid before this one (a programmatic
-        // dependency: the tensor-memory products above start without it); a no-op otherwise
-        asm volatile("griddepcontrol.wait;" ::: "memory");
+        // dependency: the tensor-memory products above start without it); a no-op otherwise.  A
+        // launch beside a grid whose results it does not read skips the wait (dep_wait = 0).
+        if (a.dep_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
@@ -1350,7 +1352,7 @@ cudaError_t launch_mode(int grid, const CUtensorMap &mA, const CUtensorMap &mB, 
 
 template <int MODE, int KIND>
 cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, cudaStream_t st,
-                         bool pdl)
+                         bool pdl, int prio)
 {
     auto kfn = block_tc2_kernel<MODE, KIND>;
     static int max_pairs = 0;  // co-resident pairs, queried once per instantiation (before any capture)
@@ -1368,7 +1370,7 @@ cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &m
         max_pairs = n;
     }
     if (npairs > max_pairs) npairs = max_pairs;
-    if (!pdl) {
+    if (!pdl && !prio) {
         kfn<<<2 * npairs, NTHREADS, SMEM2_BYTES, st>>>(mA, mB, a);
         return cudaGetLastError();
     }
@@ -1377,21 +1379,28 @@ cudaError_t launch_kind2(int npairs, const CUtensorMap &mA, const CUtensorMap &m
     cfg.blockDim = dim3(NTHREADS, 1, 1);
     cfg.dynamicSmemBytes = SMEM2_BYTES;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na++].val.programmaticStreamSerializationAllowed = 1;
+    }
+    if (prio) {
+        at[na].id = cudaLaunchAttributePriority;
+        at[na++].val.priority = prio;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kfn, mA, mB, a);
 }
 
 template <int MODE>
 cudaError_t launch_mode2(int npairs, const CUtensorMap &mA, const CUtensorMap &mB, const TcArgs &a, int kind,
-                         cudaStream_t st, bool pdl)
+                         cudaStream_t st, bool pdl, int prio)
 {
-    if (kind == DCD_RBF) return launch_kind2<MODE, DCD_RBF>(npairs, mA, mB, a, st, pdl);
-    if (kind == DCD_POLY) return launch_kind2<MODE, DCD_POLY>(npairs, mA, mB, a, st, pdl);
-    return launch_kind2<MODE, DCD_LINEAR>(npairs, mA, mB, a, st, pdl);
+    if (kind == DCD_RBF) return launch_kind2<MODE, DCD_RBF>(npairs, mA, mB, a, st, pdl, prio);
+    if (kind == DCD_POLY) return launch_kind2<MODE, DCD_POLY>(npairs, mA, mB, a, st, pdl, prio);
+    return launch_kind2<MODE, DCD_LINEAR>(npairs, mA, mB, a, st, pdl, prio);
 }
 
 }  // namespace
@@ -1424,7 +1433,8 @@ bool make_map_f32_2d(CUtensorMap *map, const float *base, int64_t cols, int64_t 
 cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const KernelParams &kp, const float *row_h,
                             const float *col_h, const float *col_w, const double *rs, double *g, float *out,
                             int64_t ldo, int64_t nrows_out, int64_t ncols, int *err, cudaStream_t st, bool lower,
-                            const TcSplit *split, bool pdl, int max_pairs, const TcAccurate *acc)
+                            const TcSplit *split, bool pdl, int max_pairs, const TcAccurate *acc, bool pdl_wait,
+                            int prio)
 {
     if (nrows_out <= 0 || ncols <= 0) return cudaSuccess;
     // the accurate apply epilogue: split-tf32 or sliced operands, FP64 coefficients, RBF terms as hi + lo
@@ -1480,6 +1490,7 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.late_units = 0;
     a.row_id = Aop.ids;
     a.col_id = Bop.ids;
+    a.dep_wait = pdl_wait ? 1 : 0;
     a.row_hl = acc ? acc->row_hl : nullptr;
     a.col_hl = acc ? acc->col_hl : nullptr;
     a.col_w64 = acc ? acc->w64 : nullptr;
@@ -1503,14 +1514,14 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
             a.late_pairs = split->late_pairs;
             a.late_units = split->late_units;
         }
-        if (sliced) return launch_mode2<MODE_SLICED>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (acc) return launch_mode2<MODE_ACC>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st, pdl);
-        if (Aop.kind == PACK_FP16) return launch_mode2<MODE_FP16>(npairs, mA, mB, a, kp.kind, st, pdl);
-        return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st, pdl);
+        if (sliced) return launch_mode2<MODE_SLICED>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (acc) return launch_mode2<MODE_ACC>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (Aop.kind == PACK_TF32) return launch_mode2<MODE_TF32>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (Aop.kind == PACK_BF16X3) return launch_mode2<MODE_BF16X3>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (Aop.kind == PACK_TF32X3) return launch_mode2<MODE_TF32X3>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (Aop.kind == PACK_FP8) return launch_mode2<MODE_FP8>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        if (Aop.kind == PACK_FP16) return launch_mode2<MODE_FP16>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
+        return launch_mode2<MODE_BF16>(npairs, mA, mB, a, kp.kind, st, pdl, prio);
     }
     int grid = a.items < sms ? a.items : sms;
     if (max_pairs > 0 && grid > max_pairs) grid = max_pairs;

@@ -195,7 +195,12 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
                             const float *row_h, const float *col_h, const float *col_w, const double *rs,
                             double *g, float *out, int64_t ldo, int64_t nrows_out, int64_t ncols,
                             int *err, cudaStream_t st, bool lower = false, const TcSplit *split = nullptr,
-                            bool pdl = false, int max_pairs = 0, const TcAccurate *acc = nullptr);
+                            bool pdl = false, int max_pairs = 0, const TcAccurate *acc = nullptr,
+                            bool pdl_wait = true, int prio = 0);
+// (pdl: launched as the programmatic dependent of the kernel before it in the stream, whose
+// results the epilogue waits for unless pdl_wait is false: a block that reads nothing the
+// kernel before it writes, started once that kernel has started.  prio: the launch's scheduling
+// priority (0: the stream's), so that its CTAs take SMs before those of kernels beside it)
 
 // setup / per-step helpers (sample_update.cu)
 // src_scale: the per-row scales of an FP8 source (dtype DCD_FP8E4M3), else unused
@@ -243,8 +248,16 @@ cudaError_t launch_fill_f64(double *p, double v, int64_t count, cudaStream_t st)
 cudaError_t launch_iota(int32_t *out, int64_t count, int64_t start, cudaStream_t st);
 cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, double diag, int64_t m, double *g,
                              cudaStream_t st);
+// the deferred gradient (solver.cu): acc[p] += add[p] (add may be NULL) + diag * (the sum of dprev
+// over the previous step's positions q holding row S[p], in position order) where any does -- the
+// update's part of the gradient at the next step's rows.  cprev <= 8192.
+cudaError_t launch_defer_repeat(const int32_t *S, int64_t cnt, const int32_t *Sprev, const double *dprev,
+                                int64_t cprev, double diag, const double *add, double *acc, cudaStream_t st);
+// (pdl: launched as the programmatic dependent of the kernel before it, whose results it does not
+// read; it signals its own dependent at once)
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha,
-                          double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st);
+                          double *g, uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st,
+                          bool pdl = false, int prio = 0);
 // The literal-order step's middle (Algorithms 2 and 4 as printed): from the stored
 // block Q (m x ncols, FP64 or FP32, leading dimension ldq) and alpha, the gradient
 // values of the step's coordinates written at their positions in g (K-SVM:
@@ -372,9 +385,12 @@ cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32
 cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                        double lambda, double mdiag, double *g, int rounds, void *scratch,
                                        double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
-                                       cudaStream_t st, const double *rhs = nullptr, int trig_sup = -1);
+                                       cudaStream_t st, const double *rhs = nullptr, int trig_sup = -1,
+                                       bool rhs_add_g = false, int prio = 0);
 // (trig_sup: the super-block of 32 rows after whose first-round result a
-// kernel launched as this one's programmatic dependent may start; -1: at once)
+// kernel launched as this one's programmatic dependent may start; -1: at once.
+// rhs_add_g: the right-hand side is -(g[S] + rhs), rhs holding a part of the
+// gradient not yet added to g)
 // 2-D tensor map over a row-major fp32 matrix (rows x cols, leading dimension
 // ld elements, ld * 4 a multiple of 16), box of box_rows x box_cols, no
 // swizzle, out-of-range elements read as zero (block_tc.cu)

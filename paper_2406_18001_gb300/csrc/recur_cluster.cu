@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     bdcd_cluster_kernel(const __grid_constant__ CUtensorMap kmap, const int32_t *S, const float *X,
                         const float *Ng, const uint32_t *Mg, const int32_t *nextg, int nblk, int b, double lambda,
                         double mdiag, double *g, int rounds, double *delta, double *w64, float *w32, double *alpha,
-                        uint64_t *ctr, uint64_t ctr_advance, const double *rhs_in, int trig_sup, int *err)
+                        uint64_t *ctr, uint64_t ctr_advance, const double *rhs_in, int rhs_add_g, int trig_sup,
+                        int *err)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int P = (int)gridDim.x;  // the grid is one cluster
@@ -382,6 +383,15 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
     // gradient.  The CTA owning super-block trig_sup signals when its round-0 Delta is out (the
     // kernels forked beside the chain have the other SMs until then); every other CTA at once.
     const bool trig_own = trig_sup >= 0 && (trig_sup == cl_own(0, c, P) || (nown > 1 && trig_sup == cl_own(1, c, P)));
+    // -(g_S + rhs_in) is read before this CTA signals: a dependent may write g once every CTA has
+    __shared__ double rhs_pre[CL_SLOTS * 32];
+    if (rhs_in && rhs_add_g) {
+        for (int e = tid; e < nown * 32; e += CL_THREADS) {
+            const int k = e >> 5, i = e & 31, J = cl_own(k, c, P);
+            if (i < cl_rows(J, Bs, sb)) rhs_pre[e] = -(g[S[J * Bs + i]] + rhs_in[J * Bs + i]);
+        }
+        __syncthreads();
+    }
     if (tid == 0 && !trig_own) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float inv_lam = (float)(1.0 / lambda);
     const float mf = (float)mdiag;
@@ -458,7 +468,12 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
         // ---- the chain of round r ----
         // r'_J: all updates but the one from J-1, which N_J = X_J L_{J,J-1} applies after the product:
         // Delta_J = X_J r'_J - N_J Delta_{J-1}.  X_J r'_J is formed while Delta_{J-1} is on its way.
-        const double rhs = lane < rows ? (rhs_in ? rhs_in[row] : -g[S[row]]) : 0.0;
+        // the right-hand side: -g_S; or given (rhs_in); or -(g_S + rhs_in), a part of the gradient
+        // not yet in g added first (rhs_add_g; read at the start)
+        const double rhs = lane >= rows ? 0.0
+                           : !rhs_in    ? -g[S[row]]
+                           : rhs_add_g  ? rhs_pre[slot * 32 + lane]
+                                        : rhs_in[row];
         float rr = r == 0 ? (float)rhs : 0.f;  // round 0: -g_S minus updates; round 1: sum of updates
         float hi = 0.f, lo = 0.f;              // round 0: double-single sum of L_{row, T<J} Delta0_T
         bool alive = J == 0 || wait_local(pbar, abort_flag, err);
@@ -674,7 +689,7 @@ cudaError_t launch_recur_cluster_prep(const float *Kss, int64_t ldk, const int32
 cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,
                                        double lambda, double mdiag, double *g, int rounds, void *scratch,
                                        double *delta, double *w64, float *w32, const FusedUpdate *upd, int *err,
-                                       cudaStream_t st, const double *rhs, int trig_sup)
+                                       cudaStream_t st, const double *rhs, int trig_sup, bool rhs_add_g, int prio)
 {
     const ClGeom G = cl_geom(nblk, b);
     const int sb = nblk * b;
@@ -701,17 +716,19 @@ cudaError_t launch_recur_cluster_chain(const float *Kss, int64_t ldk, const int3
     cfg.blockDim = dim3(CL_THREADS, 1, 1);
     cfg.dynamicSmemBytes = cluster_smem(nblk, b, P);
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)P;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributePriority;
+    at[1].val.priority = prio;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = prio ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kfn, kmap, S, (const float *)X, (const float *)N, (const uint32_t *)M,
                               (const int32_t *)next, nblk, b, lambda, mdiag, g, rounds, delta, w64, w32,
                               upd ? upd->alpha : (double *)nullptr, upd ? upd->ctr : (uint64_t *)nullptr,
-                              upd ? upd->ctr_advance : (uint64_t)0, rhs, trig_sup, err);
+                              upd ? upd->ctr_advance : (uint64_t)0, rhs, rhs_add_g ? 1 : 0, trig_sup, err);
 }
 
 cudaError_t launch_recur_cluster(const float *Kss, int64_t ldk, const int32_t *S, int nblk, int b, int P,

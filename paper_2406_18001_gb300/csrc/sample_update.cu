@@ -721,6 +721,9 @@ __global__ void __launch_bounds__(UPD_WARPS * 32)
                   uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err)
 {
     __shared__ __align__(16) int32_t sS[UPD_MAX];
+    // a kernel launched as this one's programmatic dependent may start; it waits for this grid to
+    // finish before it touches alpha or g (a no-op without one)
+    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int c4 = (cnt + 3) & ~3;
     for (int q = threadIdx.x; q < c4; q += blockDim.x) sS[q] = q < cnt ? S[q] : -1;
     __syncthreads();
@@ -776,16 +779,84 @@ __global__ void __launch_bounds__(UPD_WARPS * 32)
     }
 }
 
+// ------------------------------------------------- deferred gradient --
+// acc[p] += add[p] (add: optional) + diag * sum of dprev[q] over q with
+// Sprev[q] == S[p] (in position order, the update's own sum), where any q
+// matches: the update's part of the gradient at a row the next step samples.
+// One warp per position p, Sprev staged in shared memory, 32 positions q per
+// ballot.
+constexpr int REP_WARPS = 8;
+
+__global__ void __launch_bounds__(REP_WARPS * 32)
+    defer_repeat_kernel(const int32_t *S, int64_t cnt, const int32_t *Sprev, const double *dprev, int cprev,
+                        double diag, const double *add, double *acc)
+{
+    __shared__ int32_t sp[UPD_MAX];
+    for (int q = threadIdx.x; q < cprev; q += blockDim.x) sp[q] = Sprev[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * REP_WARPS + (threadIdx.x >> 5);
+    if (p >= cnt) return;  // warp-uniform
+    const int32_t key = S[p];
+    double sum = 0.0;
+    bool any = false;
+    for (int q0 = 0; q0 < cprev; q0 += 32) {
+        const int q = q0 + lane;
+        unsigned hit = __ballot_sync(0xffffffffu, q < cprev && sp[q] == key);
+        any = any || hit != 0u;
+        while (hit) {  // rare: the matches in position order (every lane the same sum)
+            sum += dprev[q0 + __ffs(hit) - 1];
+            hit &= hit - 1u;
+        }
+    }
+    if (lane == 0) {
+        double v = acc[p];
+        if (add) v += add[p];
+        if (any) v += diag * sum;
+        acc[p] = v;
+    }
+}
+
+cudaError_t launch_defer_repeat(const int32_t *S, int64_t cnt, const int32_t *Sprev, const double *dprev,
+                                int64_t cprev, double diag, const double *add, double *acc, cudaStream_t st)
+{
+    if (cnt <= 0) return cudaSuccess;
+    if (cprev > UPD_MAX) return cudaErrorInvalidValue;
+    defer_repeat_kernel<<<(unsigned)((cnt + REP_WARPS - 1) / REP_WARPS), REP_WARPS * 32, 0, st>>>(
+        S, cnt, Sprev, dprev, (int)cprev, diag, add, acc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update(const int32_t *S, const double *delta, int64_t cnt, double diag, double *alpha, double *g,
-                          uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st)
+                          uint64_t *ctr, uint64_t ctr_advance, int64_t m, int *err, cudaStream_t st, bool pdl,
+                          int prio)
 {
     if (cnt <= 0) return cudaSuccess;
     if (cnt > UPD_MAX) return cudaErrorInvalidValue;
     int64_t blocks = (cnt + UPD_WARPS - 1) / UPD_WARPS;
     if (blocks > 152) blocks = 152;
-    update_kernel<<<(unsigned)blocks, UPD_WARPS * 32, 0, st>>>(S, delta, (int)cnt, diag, alpha, g, ctr, ctr_advance,
-                                                               m, err);
-    return cudaGetLastError();
+    if (!pdl && !prio) {
+        update_kernel<<<(unsigned)blocks, UPD_WARPS * 32, 0, st>>>(S, delta, (int)cnt, diag, alpha, g, ctr,
+                                                                   ctr_advance, m, err);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+    cfg.blockDim = dim3(UPD_WARPS * 32, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na++].val.programmaticStreamSerializationAllowed = 1;
+    }
+    if (prio) {
+        at[na].id = cudaLaunchAttributePriority;
+        at[na++].val.priority = prio;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, update_kernel, S, delta, (int)cnt, diag, alpha, g, ctr, ctr_advance, m, err);
 }
 
 // -------------------------------------------------------- convergence ----

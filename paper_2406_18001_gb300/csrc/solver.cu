@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -74,6 +75,8 @@ dcd_status csc_choose(const CsrOperand &ca, bool fp64, int64_t cnt, int maxrow, 
 
 constexpr int64_t SB_MAX = 8192;   // s*b per outer step
 constexpr int B_MAX = 128;         // block size
+constexpr int DF_XPAIRS = 8;       // CTA pairs (at most) of the deferred gradient's cross product
+constexpr int DF_GRAM_CTAS = 8;    // CTAs of the Gram computed beside the deferred step's block
 
 // Set while the batched driver and the autotuner build their plans: those
 // capture many plans' steps into one graph and run without the look-ahead.
@@ -293,6 +296,15 @@ struct Solver {
         }
         if (la_fork) cudaEventDestroy(la_fork);
         if (la_join) cudaEventDestroy(la_join);
+        for (auto &ge : graph_df)
+            if (ge) cudaGraphExecDestroy(ge);
+        for (cudaStream_t sx : {st3, st4})
+            if (sx) {
+                cudaStreamSynchronize(sx);
+                cudaStreamDestroy(sx);
+            }
+        for (cudaEvent_t ev : {df_fork, df_chained, df_rows, df_gram, df_side, df_xfork, df_xjoin})
+            if (ev) cudaEventDestroy(ev);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
         if (csr_st) {
             cudaStreamSynchronize(csr_st);
@@ -363,6 +375,7 @@ struct Solver {
                             !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                             st != cudaStreamLegacy && st != cudaStreamPerThread &&
                             recur_cluster_size((int)o.s, o.b, 2) > 0;
+        const bool df_pos = la_pos && !(o.flags & DCD_FLAG_NO_DEFER);
         const int64_t n_pad_r = sliced_ref ? (n + 63) / 64 * 64 : (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(kind_r, n_pad_r) : 0;
 
@@ -417,7 +430,21 @@ struct Solver {
             float *cs_b = (float *)ar.take(la_pos && scaled ? sizeof(float) * col_pad : 0);
             void *kss_b = ar.take(la_pos ? (size_t)sb * sb * 4 : 0);
             double *lb_b = (double *)ar.take(la_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
-            uint64_t *crl = (uint64_t *)ar.take(la_pos ? 2 * sizeof(uint64_t) : 0);
+            uint64_t *crl = (uint64_t *)ar.take(la_pos ? 3 * sizeof(uint64_t) : 0);
+            // the deferred gradient: a third set, the recurrence's outputs per set, x per set and the
+            // cross product's split
+            int32_t *sidx_c = (int32_t *)ar.take(df_pos ? sizeof(int32_t) * col_pad : 0);
+            void *as_c = ar.take(df_pos ? (size_t)sb * row_bytes : 0, 1024);
+            float *ch_c = (float *)ar.take(df_pos ? sizeof(float) * col_pad : 0);
+            float *cs_c = (float *)ar.take(df_pos && scaled ? sizeof(float) * col_pad : 0);
+            void *kss_c = ar.take(df_pos ? (size_t)sb * sb * 4 : 0);
+            double *lb_c = (double *)ar.take(df_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
+            double *dfd = (double *)ar.take(df_pos ? 4 * sizeof(double) * col_pad : 0);  // delta, w64 of sets 1, 2
+            float *dfw = (float *)ar.take(df_pos ? 2 * sizeof(float) * col_pad : 0);     // col_w of sets 1, 2
+            double *dfx = (double *)ar.take(df_pos ? 4 * sizeof(double) * col_pad : 0);  // x of sets 0-2, x2
+            double *xsp =
+                (double *)ar.take(df_pos ? 2 * sizeof(double) * tc_split_part_elems(DF_XPAIRS, split_chunks) : 0);
+            unsigned *xsc = (unsigned *)ar.take(df_pos ? 2 * sizeof(unsigned) * 2 * DF_XPAIRS : 0);
             // the balanced split of the tensor-core apply over CTA pairs
             double *tsp = (double *)ar.take(tcd ? sizeof(double) * tc_split_part_elems(split_pairs, split_chunks) : 0);
             unsigned *tsc = (unsigned *)ar.take(tcd ? sizeof(unsigned) * 2 * split_pairs : 0);
@@ -499,6 +526,31 @@ struct Solver {
             sbuf[1].col_s = cs_b;
             sbuf[1].Kss = kss_b;
             sbuf[1].Lbuf = lb_b;
+            sbuf[2].S = sidx_c;
+            sbuf[2].As = as_c;
+            sbuf[2].col_h = ch_c;
+            sbuf[2].col_s = cs_c;
+            sbuf[2].Kss = kss_c;
+            sbuf[2].Lbuf = lb_c;
+            sbuf[0].delta = dl;
+            sbuf[0].w64 = wv;
+            sbuf[0].col_w = cw;
+            if (df_pos)
+                for (int q = 1; q < 3; ++q) {
+                    sbuf[q].delta = dfd + (size_t)(2 * q - 2) * col_pad;
+                    sbuf[q].w64 = dfd + (size_t)(2 * q - 1) * col_pad;
+                    sbuf[q].col_w = dfw + (size_t)(q - 1) * col_pad;
+                }
+            for (int q = 0; q < 3; ++q) df_x[q] = df_pos ? dfx + (size_t)q * col_pad : nullptr;
+            df_x2 = df_pos ? dfx + 3 * (size_t)col_pad : nullptr;
+            xsplit2.part = df_pos ? xsp + tc_split_part_elems(DF_XPAIRS, split_chunks) : nullptr;
+            xsplit2.cnt = df_pos ? xsc + 2 * DF_XPAIRS : nullptr;
+            xsplit2.pairs = df_pos ? DF_XPAIRS : 0;
+            xsplit.part = xsp;
+            xsplit.cnt = xsc;
+            xsplit.pairs = df_pos ? DF_XPAIRS : 0;
+            xsplit.chunks = df_pos ? split_chunks : 0;
+            xsplit2.chunks = df_pos ? split_chunks : 0;
             ctr_la = crl;
             if (tcd) {
                 tsplit.part = tsp;
@@ -536,6 +588,31 @@ struct Solver {
             DCD_TRY(cudaEventCreateWithFlags(&la_fork, cudaEventDisableTiming));
             DCD_TRY(cudaEventCreateWithFlags(&la_join, cudaEventDisableTiming));
             la = true;
+        }
+        if (df_pos) {
+            for (int q = 1; q < 3; ++q) DCD_TRY(cudaMemsetAsync(sbuf[q].col_w, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[2].S, 0, sizeof(int32_t) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[2].col_h, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[2].As, 0, (size_t)sb * row_bytes, st));
+            if (scaled) DCD_TRY(cudaMemsetAsync(sbuf[2].col_s, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(xsplit.cnt, 0, 2 * sizeof(unsigned) * 2 * DF_XPAIRS, st));
+            DCD_TRY(cudaEventCreateWithFlags(&df_fork, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&df_chained, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&df_side, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&df_rows, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&df_gram, cudaEventDisableTiming));
+            DCD_TRY(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+            DCD_TRY(cudaStreamCreateWithFlags(&st4, cudaStreamNonBlocking));
+            DCD_TRY(cudaEventCreateWithFlags(&df_xfork, cudaEventDisableTiming));
+            DCD_TRY(cudaEventCreateWithFlags(&df_xjoin, cudaEventDisableTiming));
+            // the block leaves SMs for the recurrence ahead (one cluster) and the next step's Gram
+            const int P = recur_cluster_size((int)o.s, o.b, 2);
+            df_pairs = std::max(split_pairs - (P + 1) / 2 - DF_GRAM_CTAS / 2, 1);
+            if (const char *ev = std::getenv("DCD_DEFER_BLOCK_PAIRS")) df_pairs = std::max(std::atoi(ev), 1);
+            int p_least = 0, p_greatest = 0;
+            DCD_TRY(cudaDeviceGetStreamPriorityRange(&p_least, &p_greatest));
+            df_prio = p_greatest;
+            df = true;
         }
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
         // the recurrence scratch starts zeroed (the FP64 form keeps its refinement state there)
@@ -662,6 +739,7 @@ struct Solver {
         cudaEventRecord(e0, st);
         dcd_status s0 = cuda_status(launch_init_grad(problem, y, alpha, diag, m, g, st));
         if (s0 == DCD_OK) s0 = full_pass(true);
+        df_chain = false;  // a chain computed ahead read the gradient before the recomputation
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -939,9 +1017,12 @@ struct Solver {
         float *col_h = nullptr, *col_s = nullptr;
         void *Kss = nullptr;
         double *Lbuf = nullptr;
+        // the chain's outputs (per set with the deferred gradient; shared otherwise)
+        double *delta = nullptr, *w64 = nullptr;
+        float *col_w = nullptr;
     };
     bool la = false;
-    StepBufs sbuf[2];
+    StepBufs sbuf[3];
     cudaStream_t st2 = nullptr;
     cudaEvent_t la_fork = nullptr, la_join = nullptr;
     uint64_t *ctr_la = nullptr;
@@ -960,25 +1041,45 @@ struct Solver {
         col_s = sbuf[p].col_s;
         Kss = sbuf[p].Kss;
         Lbuf = sbuf[p].Lbuf;
+        if (df) {
+            delta = sbuf[p].delta;
+            w64 = sbuf[p].w64;
+            col_w = sbuf[p].col_w;
+        }
         if (ref_shared) {
             Asr = As;
             col_hr = col_h;
         }
     }
 
-    // step products of a step of cnt blocks into buffer set q, on stream s2
-    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2)
+    // step products of a step of cnt blocks into buffer set q, on stream s2: the sample and the
+    // gathers (la_rows), then the Gram and the prep (la_gram)
+    dcd_status la_side(int q, int64_t cnt, cudaStream_t s2, int qnext = -1, int max_ctas = 0)
+    {
+        dcd_status r = la_rows(q, cnt, s2, qnext);
+        return r != DCD_OK ? r : la_gram(q, cnt, s2, max_ctas);
+    }
+
+    dcd_status la_rows(int q, int64_t cnt, cudaStream_t s2, int qnext = -1)
     {
         const StepBufs &Bq = sbuf[q];
         const int64_t ncols = cnt * o.b;
-        // the sample reads the position in ctr_la[q] and leaves the next one in ctr_la[1 - q]
-        DCD_TRY(launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, Bq.S, err, s2, ctr_la + (1 - q)));
+        if (qnext < 0) qnext = 1 - q;
+        // the sample reads the position in ctr_la[q] and leaves the next one in ctr_la[qnext]
+        DCD_TRY(launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, Bq.S, err, s2, ctr_la + qnext));
         const bool f8 = op.kind == PACK_FP8 || op.kind == PACK_FP16;  // per-row scales gathered too
         DCD_TRY(launch_gather_rows(op.packed, packed_row_bytes(op.kind, op.n_pad), Bq.S, ncols, m, Bq.As, err, s2,
                                    op.row_h, Bq.col_h, f8 ? op.row_s : nullptr, f8 ? Bq.col_s : nullptr));
+        return DCD_OK;
+    }
+
+    dcd_status la_gram(int q, int64_t cnt, cudaStream_t s2, int max_ctas = 0)
+    {
+        const StepBufs &Bq = sbuf[q];
+        const int64_t ncols = cnt * o.b;
         TcOperand Bo{Bq.As, ncols, op.n_pad, op.kind, Bq.col_s, Bq.S};
         DCD_TRY(launch_block_tc(Bo, Bo, kp, Bq.col_h, Bq.col_h, nullptr, nullptr, nullptr, (float *)Bq.Kss, ldk, ncols,
-                                ncols, err, s2, true));
+                                ncols, err, s2, true, nullptr, false, max_ctas));
         DCD_TRY(launch_recur_cluster_prep((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, lambda, (double)m, Bq.Lbuf,
                                           err, s2));
         return DCD_OK;
@@ -1073,9 +1174,214 @@ struct Solver {
         return DCD_OK;
     }
 
+    // ---- deferred gradient (the look-ahead with the recurrence one step ahead of the block) ----
+    // The recurrence of step k+1 reads g at its sampled rows after step k's block and update.
+    // That is g before block k plus x(k+1), block k's and update k's part at those rows:
+    // K(A_S(k+1), A_S(k)) w(k) (an s b x s b product) plus m Delta(k) summed over the positions of
+    // S(k) holding the same row.  x(k+1) needs only step k's coefficients and step k+1's rows, so it
+    // is formed a step early, and the recurrence of step k+1 runs beside block k, reading
+    // -(g[S] + x) before that block writes g.  One captured body per step k, buffer sets in
+    // rotation (cur: step k with its recurrence outputs; nxt: step k+1's products and x(k+1);
+    // nn: step k+2's):
+    //   st : recurrence k+1 (one cluster, launched first), block k as its programmatic dependent
+    //        on the SMs the others leave (its epilogue does not wait: it reads nothing the
+    //        recurrence writes), update k;
+    //   st2: step k+2's sample and gathers, then its Gram (a few CTAs) and prep, into nn;
+    //   st3, st4: after the gathers and recurrence k+1, x(k+2) into nn (two column halves).
+    // The association of the gradient's sums differs from the in-order step's; results agree to
+    // rounding.  A gradient recomputation invalidates the recurrence and x computed ahead.
+    bool df = false;
+    int df_cur = 0;            // the set of the next step to run
+    bool df_chain = false;     // its recurrence outputs (and x of the step after it) are in place
+    int64_t df_prod = 0;       // step size of the products in (df_cur + 1) % 3 (0: none)
+    double *df_x[3] = {nullptr, nullptr, nullptr};  // per set: x of its step (col_pad doubles)
+    cudaStream_t st3 = nullptr, st4 = nullptr;  // x of the step after next, beside its Gram and prep
+    cudaEvent_t df_fork = nullptr, df_chained = nullptr, df_rows = nullptr, df_gram = nullptr, df_side = nullptr,
+                df_xfork = nullptr, df_xjoin = nullptr;
+    double *df_x2 = nullptr;   // the second column half's part of x
+    TcSplit xsplit2;
+    TcSplit xsplit;            // the cross product's split (it runs beside the block)
+    int df_pairs = 0;          // CTA pairs of the block
+    int df_prio = 0;           // launch priority of the recurrence, the update and the block
+    cudaGraphExec_t graph_df[3] = {nullptr, nullptr, nullptr};
+    int df_direct[3] = {0, 0, 0};
+
+    // the recurrence of the step in set q on stream s, right-hand side -(g[S] + x) (x: nullptr for
+    // -g[S]), no fused update
+    dcd_status df_chain_of(int q, int64_t cnt, const double *x, cudaStream_t s, int prio = 0)
+    {
+        const StepBufs &Bq = sbuf[q];
+        const int P = recur_cluster_size((int)cnt, o.b, 2);
+        if (P <= 0) return DCD_EINTERNAL;
+        DCD_TRY(launch_recur_cluster_chain((const float *)Bq.Kss, ldk, Bq.S, (int)cnt, o.b, P, lambda, (double)m, g,
+                                           2, Bq.Lbuf, Bq.delta, Bq.w64, Bq.col_w, nullptr, err, s, x, -1, x != nullptr,
+                                           prio));
+        return DCD_OK;
+    }
+
+    // x of the step in set r (full) from the step in set c (full, its recurrence done), on stream
+    // s; the product's columns in two launches (the second on sb, joined back), each on as many
+    // CTA pairs as row tiles, and the halves added in the repeat kernel
+    dcd_status df_cross(int r, int c, cudaStream_t s, cudaStream_t sb2)
+    {
+        const StepBufs &Br = sbuf[r], &Bc = sbuf[c];
+        const int64_t nc = o.s * o.b;
+        // split at a multiple of the 256-column chunk, so that neither launch reads the other's columns
+        const int64_t h = nc >= 512 ? nc / 2 / 256 * 256 : nc;
+        TcOperand Ax{Br.As, nc, op.n_pad, op.kind, Br.col_s, Br.S};
+        if (h < nc) {
+            if (sb2 != s) {
+                DCD_TRY(cudaEventRecord(df_xfork, s));
+                DCD_TRY(cudaStreamWaitEvent(sb2, df_xfork, 0));
+            }
+            const size_t rb = (size_t)packed_row_bytes(op.kind, op.n_pad);
+            DCD_TRY(cudaMemsetAsync(df_x2, 0, sizeof(double) * nc, sb2));
+            TcOperand Bx{(const char *)Bc.As + h * rb, nc - h, op.n_pad, op.kind, Bc.col_s ? Bc.col_s + h : nullptr,
+                         Bc.S + h};
+            DCD_TRY(launch_block_tc(Ax, Bx, kp, Br.col_h, Bc.col_h + h, Bc.col_w + h, nullptr, df_x2, nullptr, 0, nc,
+                                    nc - h, err, sb2, false, &xsplit2, false, DF_XPAIRS));
+            if (sb2 != s) DCD_TRY(cudaEventRecord(df_xjoin, sb2));
+        }
+        DCD_TRY(cudaMemsetAsync(df_x[r], 0, sizeof(double) * nc, s));
+        TcOperand Bx{Bc.As, h, op.n_pad, op.kind, Bc.col_s, Bc.S};
+        DCD_TRY(launch_block_tc(Ax, Bx, kp, Br.col_h, Bc.col_h, Bc.col_w, nullptr, df_x[r], nullptr, 0, nc, h, err, s,
+                                false, &xsplit, false, DF_XPAIRS));
+        if (h < nc && sb2 != s) DCD_TRY(cudaStreamWaitEvent(s, df_xjoin, 0));
+        DCD_TRY(launch_defer_repeat(Br.S, nc, Bc.S, Bc.delta, nc, diag, h < nc ? df_x2 : nullptr, df_x[r], s));
+        return DCD_OK;
+    }
+
+    dcd_status df_body(int cur, int64_t cnt, bool has1, bool has2)
+    {
+        const int nxt = (cur + 1) % 3, nn = (cur + 2) % 3;
+        const StepBufs &Bc = sbuf[cur];
+        const int64_t ncols = cnt * o.b;
+        if (has2) {
+            DCD_TRY(cudaEventRecord(df_fork, st));
+            DCD_TRY(cudaStreamWaitEvent(st2, df_fork, 0));
+            dcd_status r = la_rows(nn, o.s, st2, (nn + 1) % 3);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(df_rows, st2));
+            DCD_TRY(cudaStreamWaitEvent(st3, df_rows, 0));
+            r = la_gram(nn, o.s, st2, DF_GRAM_CTAS);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(df_gram, st2));
+        }
+        if (has1) {
+            dcd_status r = df_chain_of(nxt, o.s, df_x[nxt], st, df_prio);
+            if (r != DCD_OK) return r;
+            if (has2) {
+                // x of step k+2 waits for recurrence k+1.  Under capture the recurrence's node is
+                // added to the side stream's dependencies directly: an event recorded on st
+                // between the recurrence and the block would stand between the two kernels of
+                // the programmatic launch
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                const cudaGraphNode_t *deps = nullptr;
+                size_t nd = 0;
+                DCD_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+                if (cs == cudaStreamCaptureStatusActive) {
+                    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+                    DCD_TRY(cudaStreamUpdateCaptureDependencies(st3, dv.data(), nullptr, dv.size(),
+                                                                cudaStreamAddCaptureDependencies));
+                } else {
+                    DCD_TRY(cudaEventRecord(df_chained, st));
+                    DCD_TRY(cudaStreamWaitEvent(st3, df_chained, 0));
+                }
+                r = df_cross(nn, nxt, st3, st4);
+                if (r != DCD_OK) return r;
+                DCD_TRY(cudaEventRecord(df_side, st3));
+            }
+        }
+        // block k as the programmatic dependent of recurrence k+1 (which read g before signalling):
+        // its epilogue does not wait, it reads nothing the recurrence writes; the recurrence and
+        // the block take SMs before the side kernels (higher launch priority).  (Update k before
+        // the block, as a dependent of the recurrence, would make the block's epilogue wait for
+        // the recurrence too: a grid's completion as a programmatic prerequisite includes its own
+        // prerequisite's.)
+        TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
+        TcOperand Bop{Bc.As, ncols, op.n_pad, op.kind, Bc.col_s, Bc.S};
+        DCD_TRY(launch_block_tc(Aop, Bop, kp, op.row_h, Bc.col_h, Bc.col_w, nullptr, g, nullptr, 0, m, ncols, err, st,
+                                false, &tsplit, has1, has1 ? df_pairs : 0, nullptr, false, df_prio));
+        DCD_TRY(launch_update(Bc.S, Bc.delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+        if (has2) {
+            DCD_TRY(cudaStreamWaitEvent(st, df_gram, 0));
+            DCD_TRY(cudaStreamWaitEvent(st, df_side, 0));
+        }
+        return DCD_OK;
+    }
+
+    // one full step through the deferred bodies
+    dcd_status df_step(int64_t cnt)
+    {
+        const int cur = df_cur, nxt = (cur + 1) % 3, nn = (cur + 2) % 3;
+        const int64_t rem1 = o.max_iters - done - cnt, rem2 = rem1 - o.s;
+        const bool has1 = rem1 >= o.s, has2 = has1 && rem2 >= o.s;
+        if (!df_chain) {  // prologue: this step's products (unless prepared), its recurrence on g itself
+            if (la_cnt != cnt) {
+                DCD_TRY(cudaMemcpyAsync(ctr_la + cur, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+                dcd_status r = la_side(cur, cnt, st, nxt);
+                if (r != DCD_OK) return r;
+                la_cnt = cnt;
+                df_prod = 0;  // the position after this step is in ctr_la[nxt]; nothing sampled there
+            }
+            dcd_status r = df_chain_of(cur, cnt, nullptr, st);
+            if (r != DCD_OK) return r;
+            if (has1) {  // step k+1's products and x
+                if (df_prod != o.s) {
+                    r = la_side(nxt, o.s, st, nn);
+                    if (r != DCD_OK) return r;
+                    df_prod = o.s;
+                }
+                r = df_cross(nxt, cur, st, st);
+                if (r != DCD_OK) return r;
+            }
+            df_chain = true;
+        }
+        const bool graphable = !graph_failed && has1 && has2;  // the steady state replays three graphs
+        if (graphable && graph_df[cur]) {
+            DCD_TRY(cudaGraphLaunch(graph_df[cur], st));
+        } else if (graphable && df_direct[cur] >= 1) {
+            DCD_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const dcd_status sc = df_body(cur, cnt, has1, has2);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            const bool ok = sc == DCD_OK && ec == cudaSuccess && graph != nullptr &&
+                            cudaGraphInstantiate(&graph_df[cur], graph, 0) == cudaSuccess;
+            if (ok) stats.gpu_launches_per_step = count_kernel_nodes(graph);
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                cudaGetLastError();
+                graph_df[cur] = nullptr;
+                graph_failed = true;
+                dcd_status r = df_body(cur, cnt, has1, has2);
+                if (r != DCD_OK) return r;
+            } else {
+                DCD_TRY(cudaGraphLaunch(graph_df[cur], st));
+            }
+        } else {
+            dcd_status r = df_body(cur, cnt, has1, has2);
+            if (r != DCD_OK) return r;
+            if (graphable) ++df_direct[cur];
+        }
+        df_cur = nxt;
+        df_chain = has1;
+        df_prod = has2 ? o.s : 0;
+        la_cnt = has1 ? o.s : 0;  // the products of the next step are in place
+        use_bufs(cur);  // the set just used is free (for a gradient recomputation)
+        col_w_hi = std::max<int64_t>(col_w_hi, sb);  // any set's coefficients may fill sb entries
+        return DCD_OK;
+    }
+
     dcd_status outer_step(int64_t cnt, EventTimer &tm)
     {
-        if (la && !tm.on && recur_cluster_size((int)cnt, o.b, 2) > 0) {
+        if (df && !tm.on && cnt == o.s) {
+            dcd_status r = df_step(cnt);
+            if (r != DCD_OK) return r;
+            done += cnt;
+            ++steps;
+            return DCD_OK;
+        }
+        if (la && !df && !tm.on && recur_cluster_size((int)cnt, o.b, 2) > 0) {
             dcd_status r = la_step(cnt);
             if (r != DCD_OK) return r;
             done += cnt;

@@ -399,10 +399,13 @@ def test_graph_replay_and_enqueue_match_direct_launches(problem, prec):
 
 @pytest.mark.parametrize("prec,fp8", [("bf16x3", False), ("fp8", True), ("tf32x3", False), ("fp16", False)])
 def test_lookahead_matches_one_stream_steps(prec, fp8):
-    """The look-ahead (next step's sample, Gram and prep on a second stream,
-    ping-pong step buffers, even/odd step graphs) must give the iterates of
-    the one-stream steps bit for bit, also with convergence checks and
-    gradient recomputations between steps (which use the idle buffer set)."""
+    """The look-ahead with the in-order gradient (next step's sample, Gram and
+    prep on a second stream, rotating step buffers, step graphs) must give the
+    iterates of the one-stream steps bit for bit, also with convergence checks
+    and gradient recomputations between steps (which use the idle buffer
+    set).  The default look-ahead (the recurrence one step ahead, beside the
+    block) gives the same iterates up to rounding: within 1e-5 of them (see
+    DEFER_TOL), the same number of steps and recomputations."""
     p = inputs.krr_dense(m=2000, n=48, seed=31, dtype=np.float32)
     kb = B().kernel("rbf", gamma=0.5)
     b, s, H = 16, 64, 23 * 64 + 16 * 5
@@ -415,14 +418,53 @@ def test_lookahead_matches_one_stream_steps(prec, fp8):
             A = dev(p.A)
         y = dev(p.y)
         runs = []
-        for flags in (B().FLAG_NO_GRAPH, 0):  # one stream (direct) / look-ahead (graphs)
+        # one stream (direct) / look-ahead, in-order gradient / look-ahead, deferred gradient
+        for flags in (B().FLAG_NO_GRAPH, B().FLAG_NO_DEFER, 0):
             al, gr, st, rc = B().krr_solve(A, y, kb, 1e-3, b, s, H, seed=7, prec=prec, tol=5e-3, check_every=2,
                                            flags=flags | B().FLAG_REFRESH, stream=side.cuda_stream)
             runs.append((al, gr, st))
         side.synchronize()
-    (a0, g0, s0), (a1, g1, s1) = runs
+    (a0, g0, s0), (a1, g1, s1), (a2, g2, s2) = runs
     assert s0["iters_done"] == s1["iters_done"] and s0["refreshes"] == s1["refreshes"] >= 1
     assert torch.equal(a0, a1) and torch.equal(g0, g1)
+    assert s2["iters_done"] == s0["iters_done"] and s2["refreshes"] == s0["refreshes"]
+    assert rel(a2.cpu().numpy(), a0.cpu().numpy()) < DEFER_TOL
+    # the gradient (the residual) is small against its terms: its error is on the scale of ||y||
+    assert np.linalg.norm(g2.cpu().numpy() - g0.cpu().numpy()) <= DEFER_TOL * np.linalg.norm(p.y)
+
+
+# The deferred gradient evaluates the block's part at the next step's rows in
+# a separate s b x s b product whose FP32 epilogue groups other rows into
+# warps: where a warp's RBF terms decide between the factored and the clamped
+# exponent form differently, the kernel value differs by FP32 rounding
+# (~1e-7 relative), and the iterates drift from the in-order steps' by a few
+# 1e-7 (measured 3e-7).  A dropped or misplaced term (the cross product, the
+# update's repeat term) changes them at order 1, far above this tolerance and
+# the mixed forms' error against the oracle (1e-4).
+DEFER_TOL = 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16x3"])
+@pytest.mark.parametrize("m,s,b,H", [(2000, 64, 16, 64 * 9), (600, 40, 16, 40 * 7 + 13), (5000, 16, 8, 16 * 12)])
+def test_deferred_gradient_matches_in_order_steps(prec, m, s, b, H):
+    """The recurrence of step k+1 computed beside the block of step k, from the
+    gradient before that block, the s b x s b cross product at the rows step
+    k+1 samples and the update's repeat term: the iterates equal those of the
+    in-order steps up to rounding (DEFER_TOL).  m = 600 with s b = 640 repeats most rows within and across
+    consecutive steps (the repeat term); the ragged budget ends on a short
+    step after the deferred ones."""
+    p = inputs.krr_dense(m=m, n=40, seed=41, dtype=np.float32)
+    kb = B().kernel("rbf", gamma=0.5)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        A, y = dev(p.A), dev(p.y)
+        runs = [B().krr_solve(A, y, kb, 1e-3, b, s, H, seed=9, prec=prec, flags=f, stream=side.cuda_stream)
+                for f in (B().FLAG_NO_DEFER, 0)]
+        side.synchronize()
+    (a1, g1, s1, _), (a2, g2, s2, _) = runs
+    assert s1["iters_done"] == s2["iters_done"] == H
+    assert rel(a2.cpu().numpy(), a1.cpu().numpy()) < DEFER_TOL
+    assert np.linalg.norm(g2.cpu().numpy() - g1.cpu().numpy()) <= DEFER_TOL * np.linalg.norm(p.y)
 
 
 def test_nonzero_alpha0_gradient_pass():
