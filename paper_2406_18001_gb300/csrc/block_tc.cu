@@ -87,7 +87,10 @@ constexpr int SLICED_BN = 128;  // N-chunk of the sliced apply: 4 accumulators f
 // well inside the FP32 range); otherwise it evaluates 2^(min(0, rf c - h_i - h_j)) w_j.
 constexpr float RBF_FACTOR_HMAX = 64.f;
 constexpr int XCH_BYTES = 2 * BM * 8;  // apply: row sums of the second epilogue half, double-buffered
-constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/;
+// single-CTA kernel, per epilogue warp: the column terms of its half of an N-chunk (RBF term,
+// id, fp8 scale: 3 x 128 words) and a 32 x 16 transpose tile (row stride 17) for the store form
+constexpr int STG_WORDS = 3 * 128 + 32 * 17;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*alignment slack*/ + 256 /*barriers*/ + 8 * STG_WORDS * 4;
 constexpr int NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any single wait
@@ -452,12 +455,30 @@ __device__ __forceinline__ void k_accurate(float dh, float dl, float hr, float h
 // store form: one item = one (row tile, N-chunk) pair; with `lower`, the
 // chunks that start past the tile's last row are empty items (every role
 // skips them alike)
+// N-chunks of row tile t that reach the lower triangle (the store form's lower option)
+__host__ __device__ __forceinline__ int lower_chunks(int t, int bn, int nchunks)
+{
+    const int64_t n = ((int64_t)t * BM + BM - 1) / bn + 1;
+    return n < nchunks ? (int)n : nchunks;
+}
+
+// The single-CTA kernel's work item: one (row tile, N-chunk); with lower, only the chunks that
+// reach the lower triangle are items, numbered tile by tile
 __device__ __forceinline__ void item_range(const TcArgs &a, int item, int &tile, int &c0, int &c1)
 {
+    if (a.lower) {
+        int t = 0, rem = item;
+        for (int n = lower_chunks(0, a.bn, a.nchunks); rem >= n && t + 1 < a.num_tiles;
+             n = lower_chunks(++t, a.bn, a.nchunks))
+            rem -= n;
+        tile = t;
+        c0 = rem;
+        c1 = c0 + 1;
+        return;
+    }
     tile = item / a.nchunks;
     c0 = item % a.nchunks;
     c1 = c0 + 1;
-    if (a.lower && (int64_t)c0 * a.bn > (int64_t)tile * BM + BM - 1) c1 = c0;
 }
 
 template <int MODE, int KIND>
@@ -601,6 +622,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int row_in_tile = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         const int ngrp = bn / 32, cg0 = half ? ngrp / 2 : 0, cg1 = half ? ngrp : ngrp / 2;
+        // this warp's column terms of the current chunk (staged once per chunk) and transpose tile
+        float *sh = (float *)(smem + RING_BYTES + 256) + (warp - 2) * STG_WORDS;
+        int *sid = (int *)(sh + 128);
+        float *ssc = sh + 256;
+        float *xt = sh + 384;
         uint32_t acc_it = 0;
         bool ok = true;
         for (int item = blockIdx.x; ok && item < a.items; item += gridDim.x) {
@@ -611,8 +637,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const float hr = (KIND == DCD_RBF && row_ok) ? a.row_h[row] : 0.f;
             const float rsc = !SCALED ? 1.f : !row_ok ? 0.f : FP8 ? a.row_s[row] : a.row_s[row] * a.col_s[0];
             const float rf = KIND == DCD_RBF ? a.two_gl * rsc : rsc;
+            const int rid = !row_ok ? -2 : a.row_id ? a.row_id[row] : (int)row;
             for (int nc = c0; nc < c1; ++nc, ++acc_it) {
                 const uint32_t buf = acc_it & 1, aph = (acc_it >> 1) & 1;
+                const int64_t cw0 = (int64_t)nc * bn + cg0 * 32;  // this warp's first column
+                for (int j = lane; j < (cg1 - cg0) * 32; j += 32) {
+                    const int64_t c = cw0 + j;
+                    const bool in = c < a.ncols;
+                    sh[j] = KIND == DCD_RBF && in ? a.col_h[c] : 0.f;
+                    sid[j] = !in ? -1 : a.col_id ? a.col_id[c] : (int)c;
+                    if (FP8) ssc[j] = in ? a.col_s[c] : 0.f;
+                }
+                __syncwarp();
                 // every lane polls; the warp proceeds only if all lanes saw the
                 // phase complete, so the aligned tcgen05.ld never diverges
                 const bool seen = mbar_wait(&tfull[buf], aph, abort_flag, a.err);
@@ -624,40 +660,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int cg = cg0; cg < cg1; ++cg) {
                     float v[32];
                     tmem_ld32(tmem_base + lane_addr + buf * (uint32_t)bn + (uint32_t)(cg * 32), v);
+                    const int j0 = (cg - cg0) * 32;
                     const int64_t colbase = (int64_t)nc * bn + cg * 32;
-                    if (FP8) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) v[q] *= a.col_s[colbase + q];
+                    for (int q = 0; q < 32; ++q) {
+                        const float c = FP8 ? v[q] * ssc[j0 + q] : v[q];
+                        // K with the own-sample rule of the RBF (d^2 = 0 where the row and the column
+                        // are the same data row)
+                        v[q] = KIND == DCD_RBF && rid == sid[j0 + q] ? 1.f : kf32<KIND>(c, hr, sh[j0 + q], rf, a);
                     }
-                    if (row_ok) {
-                        float *dst = a.out + row * a.ldo + colbase;
-                        const int64_t rid = a.row_id ? (int64_t)a.row_id[row] : row;
-                        // column ids inside the block (the last group may be ragged)
-                        auto cid = [&](int q) -> int64_t {
-                            const int64_t c = colbase + q;
-                            return c < a.ncols ? (a.col_id ? (int64_t)a.col_id[c] : c) : -1;
-                        };
-                        if (colbase + 32 <= a.ncols && (a.ldo & 3) == 0) {  // whole group: 16-byte stores
+                    // the 32 x 32 group to memory in two 16-column halves through the transpose tile:
+                    // lanes 0..15 write columns 0..15 of one row, lanes 16..31 of the next
 #pragma unroll
-                            for (int q = 0; q < 32; q += 4) {
-                                float4 o;
-                                o.x = kf32_id<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf, a,
-                                                    rid, cid(q));
-                                o.y = kf32_id<KIND>(v[q + 1], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 1] : 0.f, rf,
-                                                    a, rid, cid(q + 1));
-                                o.z = kf32_id<KIND>(v[q + 2], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 2] : 0.f, rf,
-                                                    a, rid, cid(q + 2));
-                                o.w = kf32_id<KIND>(v[q + 3], hr, KIND == DCD_RBF ? a.col_h[colbase + q + 3] : 0.f, rf,
-                                                    a, rid, cid(q + 3));
-                                *reinterpret_cast<float4 *>(dst + q) = o;
-                            }
-                        } else {
+                    for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
-                            for (int q = 0; q < 32; ++q)
-                                if (colbase + q < a.ncols)
-                                    dst[q] = kf32_id<KIND>(v[q], hr, KIND == DCD_RBF ? a.col_h[colbase + q] : 0.f, rf,
-                                                           a, rid, cid(q));
+                        for (int q = 0; q < 16; ++q) xt[lane * 17 + q] = v[16 * hh + q];
+                        __syncwarp();
+                        const int cq = lane & 15;
+                        const int64_t col = colbase + 16 * hh + cq;
+#pragma unroll 4
+                        for (int r2 = 0; r2 < 32; r2 += 2) {
+                            const int rr = r2 + (lane >> 4);
+                            const int64_t orow = (int64_t)tile * BM + quarter * 32 + rr;
+                            if (orow < a.nrows_out && col < a.ncols) a.out[orow * a.ldo + col] = xt[rr * 17 + cq];
                         }
+                        __syncwarp();
                     }
                 }
                 fence_before();
@@ -1480,6 +1507,10 @@ cudaError_t launch_block_tc(const TcOperand &Aop, const TcOperand &Bop, const Ke
     a.store = out != nullptr;
     a.lower = a.store && lower;
     a.items = a.store ? a.num_tiles * a.nchunks : a.num_tiles;
+    if (a.lower) {
+        a.items = 0;
+        for (int t = 0; t < a.num_tiles; ++t) a.items += lower_chunks(t, a.bn, a.nchunks);
+    }
     a.degree = kp.degree;
     a.two_gl = (float)(2.0 * kp.gamma * 1.4426950408889634);
     a.coef0 = (float)kp.coef0;

@@ -18,7 +18,6 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -605,10 +604,15 @@ struct Solver {
             DCD_TRY(cudaStreamCreateWithFlags(&st4, cudaStreamNonBlocking));
             DCD_TRY(cudaEventCreateWithFlags(&df_xfork, cudaEventDisableTiming));
             DCD_TRY(cudaEventCreateWithFlags(&df_xjoin, cudaEventDisableTiming));
-            // the block leaves SMs for the recurrence ahead (one cluster) and the next step's Gram
+            // the block leaves SMs for the recurrence ahead (one cluster) and, about, the next step's
+            // Gram; within two pairs of that, the fewest pairs that give the fewest (256-row tile,
+            // 256-column chunk) units to the most loaded pair
             const int P = recur_cluster_size((int)o.s, o.b, 2);
-            df_pairs = std::max(split_pairs - (P + 1) / 2 - DF_GRAM_CTAS / 2, 1);
-            if (const char *ev = std::getenv("DCD_DEFER_BLOCK_PAIRS")) df_pairs = std::max(std::atoi(ev), 1);
+            const int base = split_pairs - (P + 1) / 2 - DF_GRAM_CTAS / 2;
+            const int64_t units = (m + 255) / 256 * ((sb + 255) / 256);
+            df_pairs = std::max(base, 1);
+            for (int n = std::max(base - 2, 1); n <= std::min(base + 2, split_pairs - (P + 1) / 2); ++n)
+                if ((units + n - 1) / n < (units + df_pairs - 1) / df_pairs) df_pairs = n;
             int p_least = 0, p_greatest = 0;
             DCD_TRY(cudaDeviceGetStreamPriorityRange(&p_least, &p_greatest));
             df_prio = p_greatest;

@@ -384,7 +384,8 @@ def test_graph_replay_and_enqueue_match_direct_launches(problem, prec):
         A, y = dev(p.A), dev(p.y)
         ref = B().Plan(problem, A, y, kb, param, b, s, H, seed=4, prec=prec, flags=B().FLAG_NO_GRAPH)
         ref.run(-1)
-        pl = B().Plan(problem, A, y, kb, param, b, s, H, seed=4, prec=prec)
+        # (the look-ahead with the in-order gradient: the deferred one differs by rounding)
+        pl = B().Plan(problem, A, y, kb, param, b, s, H, seed=4, prec=prec, flags=B().FLAG_NO_DEFER)
         assert pl.enqueue(3) == 3
         st, _ = pl.run(2)
         assert st["outer_steps"] == 5 and st["gpu_launches_per_step"] > 0
