@@ -399,16 +399,6 @@ __device__ __forceinline__ float kf32(float c, float hr, float hc, float rf, con
     }
 }
 
-// K with the own-sample rule of the RBF (d^2 = 0 where the row and column
-// are the same data row)
-template <int KIND>
-__device__ __forceinline__ float kf32_id(float c, float hr, float hc, float rf, const TcArgs &a, int64_t rid,
-                                         int64_t cid)
-{
-    if (KIND == DCD_RBF && rid == cid) return 1.f;
-    return kf32<KIND>(c, hr, hc, rf, a);
-}
-
 // The accurate epilogue's kernel value (kh + kl) from a dot product given as
 // dh + dl (double-single): the RBF exponent x = 2 gamma log2(e) (a.b) - (h_i
 // + h_j) = -gamma log2(e) d^2 in double-single, clamped at 0, then exp2_ds;
