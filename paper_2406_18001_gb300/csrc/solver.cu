@@ -258,6 +258,8 @@ struct Solver {
     CsrOperand ca;
     CsrColMap cm;
     void *ws_csr = nullptr;
+    CsrColMap cm_set[2];     // the column map of each buffer set (the K-SVM look-ahead)
+    void *ws_csr2 = nullptr;
     // the apply through the transposed copy (chosen at set-up when it reads far less than a full pass)
     bool use_csc = false;
     CscOperand cscop;
@@ -305,6 +307,7 @@ struct Solver {
         for (cudaEvent_t ev : {df_fork, df_chained, df_rows, df_gram, df_side, df_xfork, df_xjoin})
             if (ev) cudaEventDestroy(ev);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
+        if (ws_csr2) cudaFreeAsync(ws_csr2, st);
         if (csr_st) {
             cudaStreamSynchronize(csr_st);
             cudaStreamDestroy(csr_st);
@@ -375,6 +378,12 @@ struct Solver {
                             st != cudaStreamLegacy && st != cudaStreamPerThread &&
                             recur_cluster_size((int)o.s, o.b, 2) > 0;
         const bool df_pos = la_pos && !(o.flags & DCD_FLAG_NO_DEFER);
+        // the look-ahead of the K-SVM steps (dense, tensor-core or FP64, and CSR): the next step's
+        // sample, column map or gathers and Gram on a second stream beside the recurrence and block
+        const bool lag_pos = !t_no_lookahead && problem == 0 && !literal &&
+                             !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
+                             st != cudaStreamLegacy && st != cudaStreamPerThread;
+        const bool set2 = la_pos || lag_pos;  // a second set of step buffers
         const int64_t n_pad_r = sliced_ref ? (n + 63) / 64 * 64 : (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(kind_r, n_pad_r) : 0;
 
@@ -423,13 +432,13 @@ struct Solver {
             double *lb = (double *)ar.take(problem == 1 ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             uint64_t *cr = (uint64_t *)ar.take(sizeof(uint64_t));
             // the second set of step buffers and the look-ahead counter
-            int32_t *sidx_b = (int32_t *)ar.take(la_pos ? sizeof(int32_t) * col_pad : 0);
-            void *as_b = ar.take(la_pos ? (size_t)sb * row_bytes : 0, 1024);
-            float *ch_b = (float *)ar.take(la_pos ? sizeof(float) * col_pad : 0);
-            float *cs_b = (float *)ar.take(la_pos && scaled ? sizeof(float) * col_pad : 0);
-            void *kss_b = ar.take(la_pos ? (size_t)sb * sb * 4 : 0);
+            int32_t *sidx_b = (int32_t *)ar.take(set2 ? sizeof(int32_t) * col_pad : 0);
+            void *as_b = ar.take(set2 && tcd ? (size_t)sb * row_bytes : 0, 1024);
+            float *ch_b = (float *)ar.take(set2 ? sizeof(float) * col_pad : 0);
+            float *cs_b = (float *)ar.take(set2 && scaled ? sizeof(float) * col_pad : 0);
+            void *kss_b = ar.take(set2 ? (size_t)sb * sb * (tc ? 4 : 8) : 0);
             double *lb_b = (double *)ar.take(la_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
-            uint64_t *crl = (uint64_t *)ar.take(la_pos ? 3 * sizeof(uint64_t) : 0);
+            uint64_t *crl = (uint64_t *)ar.take(set2 ? 3 * sizeof(uint64_t) : 0);
             // the deferred gradient: a third set, the recurrence's outputs per set, x per set and the
             // cross product's split
             int32_t *sidx_c = (int32_t *)ar.take(df_pos ? sizeof(int32_t) * col_pad : 0);
@@ -524,7 +533,7 @@ struct Solver {
             sbuf[1].col_h = ch_b;
             sbuf[1].col_s = cs_b;
             sbuf[1].Kss = kss_b;
-            sbuf[1].Lbuf = lb_b;
+            sbuf[1].Lbuf = la_pos ? lb_b : lb;  // the K-SVM recurrences keep no per-set scratch
             sbuf[2].S = sidx_c;
             sbuf[2].As = as_c;
             sbuf[2].col_h = ch_c;
@@ -578,15 +587,16 @@ struct Solver {
         DCD_TRY(cudaMemsetAsync(S, 0, sizeof(int32_t) * col_pad, st));
         if (tcd) DCD_TRY(cudaMemsetAsync(As, 0, (size_t)sb * row_bytes, st));
         if (scaled) DCD_TRY(cudaMemsetAsync(col_s, 0, sizeof(float) * col_pad, st));
-        if (la_pos) {
+        if (set2) {
             DCD_TRY(cudaMemsetAsync(sbuf[1].S, 0, sizeof(int32_t) * col_pad, st));
             DCD_TRY(cudaMemsetAsync(sbuf[1].col_h, 0, sizeof(float) * col_pad, st));
-            DCD_TRY(cudaMemsetAsync(sbuf[1].As, 0, (size_t)sb * row_bytes, st));
+            if (tcd) DCD_TRY(cudaMemsetAsync(sbuf[1].As, 0, (size_t)sb * row_bytes, st));
             if (scaled) DCD_TRY(cudaMemsetAsync(sbuf[1].col_s, 0, sizeof(float) * col_pad, st));
             DCD_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
             DCD_TRY(cudaEventCreateWithFlags(&la_fork, cudaEventDisableTiming));
             DCD_TRY(cudaEventCreateWithFlags(&la_join, cudaEventDisableTiming));
-            la = true;
+            la = la_pos;
+            lag = lag_pos;
         }
         if (df_pos) {
             for (int q = 1; q < 3; ++q) DCD_TRY(cudaMemsetAsync(sbuf[q].col_w, 0, sizeof(float) * col_pad, st));
@@ -647,6 +657,23 @@ struct Solver {
             if (!(o.flags & DCD_FLAG_CSR_FULL_PASS) && !literal) {
                 dcd_status cs = setup_csc();
                 if (cs != DCD_OK) return cs;
+            }
+            cm_set[0] = cm;
+            if (lag) {  // the look-ahead's second column map and pair table
+                const int64_t pairs = sb * (int64_t)std::max(csr_maxrow, 1);
+                const size_t pb = (size_t)pairs * (8 + 8 + 4) + 256 * 3;
+                DCD_TRY(malloc_async(&ws_csr2, cmb + pb, st));
+                DCD_TRY(cudaMemsetAsync(ws_csr2, 0, cmb + pb, st));
+                CsrColMap c2 = csr_colmap_carve(ws_csr2, n, cap);
+                char *pp = (char *)ws_csr2 + (cmb + 255) / 256 * 256;
+                c2.pstart = (int64_t *)pp;
+                pp += ((size_t)pairs * 8 + 255) / 256 * 256;
+                c2.pval = (double *)pp;
+                pp += ((size_t)pairs * 8 + 255) / 256 * 256;
+                c2.plen = (int32_t *)pp;
+                c2.pmax = cm.pmax;
+                c2.csc_col_ptr = cm.csc_col_ptr;
+                cm_set[1] = c2;
             }
         } else if (tc) {
             op.n_pad = n_pad;
@@ -1026,6 +1053,7 @@ struct Solver {
         float *col_w = nullptr;
     };
     bool la = false;
+    bool lag = false;  // the K-SVM look-ahead (in-order: products of step k+1 beside step k)
     StepBufs sbuf[3];
     cudaStream_t st2 = nullptr;
     cudaEvent_t la_fork = nullptr, la_join = nullptr;
@@ -1050,6 +1078,7 @@ struct Solver {
             w64 = sbuf[p].w64;
             col_w = sbuf[p].col_w;
         }
+        if (lag && csr) cm = cm_set[p];
         if (ref_shared) {
             Asr = As;
             col_hr = col_h;
@@ -1376,8 +1405,108 @@ struct Solver {
         return DCD_OK;
     }
 
+    // ---- the K-SVM look-ahead ----
+    // Step k+1's sample (from ctr_la, as above), its column map (CSR) or gathered rows (dense
+    // tensor-core form) and its Gram, into buffer set q on stream s2; the helpers enqueue on the
+    // plan's stream member, pointed at s2 meanwhile
+    dcd_status lag_side(int q, int64_t cnt, cudaStream_t s2)
+    {
+        const cudaStream_t keep = st;
+        st = s2;
+        use_bufs(q);
+        const int64_t ncols = cnt * o.b;
+        cudaError_t e = launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, S, err, st, ctr_la + (1 - q));
+        if (e == cudaSuccess) e = gather(ncols);
+        if (e == cudaSuccess) e = gram(ncols);
+        st = keep;
+        return cuda_status(e);
+    }
+
+    // one K-SVM look-ahead step with products in set p: the recurrence, the block and the update on
+    // st (the CSR block's first scatter forked beside the recurrence); the next step's products
+    // (next > 0) into set 1 - p on st2, forked first and joined after the update
+    dcd_status lag_body(int p, int64_t cnt, int64_t next)
+    {
+        if (next) {
+            DCD_TRY(cudaEventRecord(la_fork, st));
+            DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
+            dcd_status r = lag_side(1 - p, next, st2);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(la_join, st2));
+        }
+        use_bufs(p);
+        const int64_t ncols = cnt * o.b;
+        if (csr && use_csc) DCD_TRY(csr_fork_scatter(ncols));
+        DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
+                                 tc ? col_w : nullptr, err, st));
+        if (tc) DCD_TRY(clear_col_w_tail(ncols));
+        if (csr)
+            DCD_TRY(csr_apply(ncols, y));
+        else if (tc)
+            DCD_TRY(block_tc_apply(ncols, y));
+        else
+            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, y, g, nullptr, 0, err,
+                                          st));
+        DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+        if (next) DCD_TRY(cudaStreamWaitEvent(st, la_join, 0));
+        return DCD_OK;
+    }
+
+    dcd_status lag_step(int64_t cnt)
+    {
+        if (la_cnt != cnt) {  // nothing pending: this step's products first, on st
+            DCD_TRY(cudaMemcpyAsync(ctr_la + la_par, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+            dcd_status r = lag_side(la_par, cnt, st);
+            if (r != DCD_OK) return r;
+            la_cnt = cnt;
+        }
+        const int p = la_par;
+        const int64_t next = (o.max_iters - done - cnt) >= o.s ? o.s : 0;  // only full steps are prepared ahead
+        if (next && cnt == o.s && !graph_failed) {
+            if (graph_la[p]) {
+                DCD_TRY(cudaGraphLaunch(graph_la[p], st));
+            } else if (la_direct[p] >= 1) {
+                DCD_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                const dcd_status sc = lag_body(p, cnt, next);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+                const bool ok = sc == DCD_OK && ec == cudaSuccess && graph != nullptr &&
+                                cudaGraphInstantiate(&graph_la[p], graph, 0) == cudaSuccess;
+                if (ok) stats.gpu_launches_per_step = count_kernel_nodes(graph);
+                if (graph) cudaGraphDestroy(graph);
+                if (!ok) {
+                    cudaGetLastError();
+                    graph_la[p] = nullptr;
+                    graph_failed = true;
+                    dcd_status r = lag_body(p, cnt, next);
+                    if (r != DCD_OK) return r;
+                } else {
+                    DCD_TRY(cudaGraphLaunch(graph_la[p], st));
+                }
+            } else {
+                dcd_status r = lag_body(p, cnt, next);
+                if (r != DCD_OK) return r;
+                ++la_direct[p];
+            }
+        } else {
+            dcd_status r = lag_body(p, cnt, next);
+            if (r != DCD_OK) return r;
+        }
+        la_par = 1 - p;
+        la_cnt = next;
+        use_bufs(p);  // the set just used is free (for a gradient recomputation)
+        return DCD_OK;
+    }
+
     dcd_status outer_step(int64_t cnt, EventTimer &tm)
     {
+        if (lag && !tm.on) {
+            dcd_status r = lag_step(cnt);
+            if (r != DCD_OK) return r;
+            done += cnt;
+            ++steps;
+            return DCD_OK;
+        }
         if (df && !tm.on && cnt == o.s) {
             dcd_status r = df_step(cnt);
             if (r != DCD_OK) return r;

@@ -104,6 +104,30 @@ def test_krr_solve_through_csc_equals_full_pass_over_several_column_chunks(spars
     assert res["csc"][2] == res["full"][2] + 3
 
 
+@pytest.mark.parametrize("prec,flags", [("fp64", 0), ("bf16x3", 0), ("bf16x3", "full")])
+def test_svm_lookahead_on_csr_matches_one_stream_steps(sparse, prec, flags):
+    """The K-SVM look-ahead on CSR data (the next step's column map, pair table
+    and Gram in the other buffer set on a second stream, this step's scatter
+    beside its recurrence) gives the one-stream steps' iterates bit for bit,
+    with gap checks, recomputations and a short last step; through the
+    transposed copy and with the full pass."""
+    p = sparse
+    A = lib_csr(p, np.float64 if prec == "fp64" else np.float32)
+    kb = B().kernel("poly", coef0=1.0, degree=3)
+    f = B().FLAG_CSR_FULL_PASS if flags == "full" else 0
+    side = torch.cuda.Stream()
+    res = []
+    with torch.cuda.stream(side):
+        for extra in (B().FLAG_NO_GRAPH, 0):
+            al, gr, st, _ = B().svm_solve(A, dev(p.y), kb, 2, 0.5, 32, 32 * 11 + 7, seed=9, prec=prec, tol=1e-3,
+                                          check_every=3, flags=f | extra | B().FLAG_REFRESH,
+                                          stream=side.cuda_stream)
+            res.append((al.cpu().numpy(), gr.cpu().numpy(), st))
+        side.synchronize()
+    assert res[0][2]["iters_done"] == res[1][2]["iters_done"]
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 def test_tiles_beyond_the_shared_buffer_take_the_full_pass(sparse):
     # 64 rows of 3000 nonzeros (two whole 32-row tiles and parts of two more)
     p = with_dense_rows(sparse, range(1000, 1064), 3000, seed=8)

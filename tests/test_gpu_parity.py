@@ -434,6 +434,32 @@ def test_lookahead_matches_one_stream_steps(prec, fp8):
     assert np.linalg.norm(g2.cpu().numpy() - g0.cpu().numpy()) <= DEFER_TOL * np.linalg.norm(p.y)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "fp16", "bf16"])
+@pytest.mark.parametrize("loss", [1, 2])
+def test_svm_lookahead_matches_one_stream_steps(prec, loss):
+    """The K-SVM look-ahead (the next step's sample and Gram on a second
+    stream, two buffer sets, step graphs) gives the iterates of the one-stream
+    steps bit for bit, with duality-gap checks and gradient recomputations
+    between steps and a short last step."""
+    p = inputs.blobs(m=1500, n=48, seed=17)
+    A = p.A.astype(np.float32)
+    kb = B().kernel("rbf", gamma=1 / 64)
+    s, H = 16, 16 * 37 + 5
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        Ad, yd = dev(A), dev(p.y)
+        runs = []
+        for flags in (B().FLAG_NO_GRAPH, 0):
+            al, gr, st, rc = B().svm_solve(Ad, yd, kb, loss, 1.0, s, H, seed=3, prec=prec, tol=1e-3, check_every=3,
+                                           flags=flags | B().FLAG_REFRESH, stream=side.cuda_stream)
+            runs.append((al, gr, st))
+        side.synchronize()
+    (a0, g0, s0), (a1, g1, s1) = runs
+    assert s0["iters_done"] == s1["iters_done"] and s0["refreshes"] == s1["refreshes"]
+    assert s1["gpu_launches_per_step"] > 0
+    assert torch.equal(a0, a1) and torch.equal(g0, g1)
+
+
 # The deferred gradient evaluates the block's part at the next step's rows in
 # a separate s b x s b product whose FP32 epilogue groups other rows into
 # warps: where a warp's RBF terms decide between the factored and the clamped
