@@ -378,9 +378,10 @@ struct Solver {
                             st != cudaStreamLegacy && st != cudaStreamPerThread &&
                             recur_cluster_size((int)o.s, o.b, 2) > 0;
         const bool df_pos = la_pos && !(o.flags & DCD_FLAG_NO_DEFER);
-        // the look-ahead of the K-SVM steps (dense, tensor-core or FP64, and CSR): the next step's
-        // sample, column map or gathers and Gram on a second stream beside the recurrence and block
-        const bool lag_pos = !t_no_lookahead && problem == 0 && !literal &&
+        // the look-ahead of the other steps (K-SVM, dense or CSR; K-RR in FP64, on CSR or with a
+        // chain longer than one cluster): the next step's sample, column map or gathers and Gram
+        // on a second stream beside the recurrence and block
+        const bool lag_pos = !t_no_lookahead && !la_pos && !literal &&
                              !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                              st != cudaStreamLegacy && st != cudaStreamPerThread;
         const bool set2 = la_pos || lag_pos;  // a second set of step buffers
@@ -533,7 +534,7 @@ struct Solver {
             sbuf[1].col_h = ch_b;
             sbuf[1].col_s = cs_b;
             sbuf[1].Kss = kss_b;
-            sbuf[1].Lbuf = la_pos ? lb_b : lb;  // the K-SVM recurrences keep no per-set scratch
+            sbuf[1].Lbuf = la_pos ? lb_b : lb;  // off the cluster path only the main stream uses the scratch
             sbuf[2].S = sidx_c;
             sbuf[2].As = as_c;
             sbuf[2].col_h = ch_c;
@@ -1405,7 +1406,7 @@ struct Solver {
         return DCD_OK;
     }
 
-    // ---- the K-SVM look-ahead ----
+    // ---- the look-ahead of the other steps (K-SVM; K-RR off the single-cluster path) ----
     // Step k+1's sample (from ctr_la, as above), its column map (CSR) or gathered rows (dense
     // tensor-core form) and its Gram, into buffer set q on stream s2; the helpers enqueue on the
     // plan's stream member, pointed at s2 meanwhile
@@ -1422,7 +1423,7 @@ struct Solver {
         return cuda_status(e);
     }
 
-    // one K-SVM look-ahead step with products in set p: the recurrence, the block and the update on
+    // one look-ahead step with products in set p: the recurrence, the block and the update on
     // st (the CSR block's first scatter forked beside the recurrence); the next step's products
     // (next > 0) into set 1 - p on st2, forked first and joined after the update
     dcd_status lag_body(int p, int64_t cnt, int64_t next)
@@ -1436,18 +1437,27 @@ struct Solver {
         }
         use_bufs(p);
         const int64_t ncols = cnt * o.b;
+        const double *rs = problem == 0 ? y : nullptr;
         if (csr && use_csc) DCD_TRY(csr_fork_scatter(ncols));
-        DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
-                                 tc ? col_w : nullptr, err, st));
+        FusedUpdate fu;  // a6 done by the K-RR recurrence when it can
+        fu.alpha = alpha;
+        fu.ctr = ctr;
+        fu.ctr_advance = (uint64_t)cnt;
+        if (problem == 0)
+            DCD_TRY(launch_recur_dcd(Kss, tc ? 0 : 1, ldk, S, cnt, y, alpha, g, omega, nu, delta, w64,
+                                     tc ? col_w : nullptr, err, st));
+        else
+            DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, tc ? 1 : 2, Lbuf,
+                                      delta, w64, tc ? col_w : nullptr, &fu, err, st));
         if (tc) DCD_TRY(clear_col_w_tail(ncols));
         if (csr)
-            DCD_TRY(csr_apply(ncols, y));
+            DCD_TRY(csr_apply(ncols, rs));
         else if (tc)
-            DCD_TRY(block_tc_apply(ncols, y));
+            DCD_TRY(block_tc_apply(ncols, rs));
         else
-            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, y, g, nullptr, 0, err,
-                                          st));
-        DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr, 0,
+                                          err, st));
+        if (!fu.done) DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
         if (next) DCD_TRY(cudaStreamWaitEvent(st, la_join, 0));
         return DCD_OK;
     }

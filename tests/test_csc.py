@@ -128,6 +128,25 @@ def test_svm_lookahead_on_csr_matches_one_stream_steps(sparse, prec, flags):
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
+def test_krr_lookahead_on_csr_matches_one_stream_steps(sparse):
+    """K-RR BDCD on CSR data with the look-ahead (the next step's column map,
+    pair table and Gram beside this step): the one-stream steps' bits."""
+    p = sparse
+    A = lib_csr(p, np.float32)
+    y = np.random.default_rng(4).standard_normal(p.m)
+    kb = B().kernel("rbf", gamma=0.5)
+    side = torch.cuda.Stream()
+    res = []
+    with torch.cuda.stream(side):
+        for extra in (B().FLAG_NO_GRAPH, 0):
+            al, gr, st, _ = B().krr_solve(A, dev(y), kb, 1e-3, 8, 9, 9 * 7 + 2, seed=2, prec="bf16x3",
+                                          flags=extra, stream=side.cuda_stream)
+            res.append((al.cpu().numpy(), gr.cpu().numpy(), st))
+        side.synchronize()
+    assert res[0][2]["iters_done"] == res[1][2]["iters_done"]
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 def test_tiles_beyond_the_shared_buffer_take_the_full_pass(sparse):
     # 64 rows of 3000 nonzeros (two whole 32-row tiles and parts of two more)
     p = with_dense_rows(sparse, range(1000, 1064), 3000, seed=8)

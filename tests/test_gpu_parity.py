@@ -460,6 +460,35 @@ def test_svm_lookahead_matches_one_stream_steps(prec, loss):
     assert torch.equal(a0, a1) and torch.equal(g0, g1)
 
 
+@pytest.mark.parametrize("prec,fp8,s,b", [("fp64", False, 8, 8), ("bf16x3", False, 48, 32), ("fp8", True, 40, 32),
+                                          ("fp16", False, 64, 32)])
+def test_krr_lookahead_off_the_cluster_path_matches_one_stream_steps(prec, fp8, s, b):
+    """K-RR steps that do not take the single-cluster recurrence (FP64, or s b
+    above one cluster: the blocked recurrence) get the in-order look-ahead:
+    the iterates equal the one-stream steps' bit for bit, with residual
+    checks, gradient recomputations and a short last step."""
+    p = inputs.krr_dense(m=3000, n=64, seed=23, dtype=np.float32)
+    kb = B().kernel("rbf", gamma=0.5)
+    H = 5 * s + 3
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        if fp8:
+            q, sc = oracle.quantize_e4m3_rows(p.A)
+            A = B().Fp8(dev(q), dev(sc))
+        else:
+            A = dev(p.A.astype(np.float64) if prec == "fp64" else p.A)
+        y = dev(p.y)
+        runs = []
+        for flags in (B().FLAG_NO_GRAPH, 0):
+            al, gr, st, rc = B().krr_solve(A, y, kb, 1e-2, b, s, H, seed=5, prec=prec, tol=1e-3, check_every=2,
+                                           flags=flags | B().FLAG_REFRESH, stream=side.cuda_stream)
+            runs.append((al, gr, st))
+        side.synchronize()
+    (a0, g0, s0), (a1, g1, s1) = runs
+    assert s0["iters_done"] == s1["iters_done"] and s0["refreshes"] == s1["refreshes"]
+    assert torch.equal(a0, a1) and torch.equal(g0, g1)
+
+
 # The deferred gradient evaluates the block's part at the next step's rows in
 # a separate s b x s b product whose FP32 epilogue groups other rows into
 # warps: where a warp's RBF terms decide between the factored and the clamped
