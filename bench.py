@@ -547,6 +547,8 @@ def _run_gpu(args, torch, B, ws, rank, local, dev, stream):
                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                "config": {"workload": WORKLOAD, "m": args.m, "n": args.n, "s": args.s, "b": args.b,
                           "gamma": args.gamma, "lambda": args.lam, "precision": args.prec,
+                          "step": ("look-ahead, in-order gradient" if args.no_defer
+                                   else "look-ahead, deferred gradient (step k+1's recurrence beside step k's block)"),
                           "l2": "256 MB buffer written before every timed step; steps timed alone",
                           "parallelism": "replicas" if ws > 1 else "single"},
                "step_ms": {"min": ms_steps[0], "median": ms_steps[len(ms_steps) // 2], "max": ms_steps[-1]},

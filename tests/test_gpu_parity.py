@@ -489,6 +489,31 @@ def test_krr_lookahead_off_the_cluster_path_matches_one_stream_steps(prec, fp8, 
     assert torch.equal(a0, a1) and torch.equal(g0, g1)
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16x3"])
+def test_deferred_steps_split_over_calls_match_one_call(prec):
+    """The deferred look-ahead keeps the recurrence and x computed ahead across
+    dcd_plan_enqueue / dcd_plan_run calls: a solve split into pieces (with a
+    final short step) gives the bits of the same solve in one call."""
+    p = inputs.krr_dense(m=2000, n=48, seed=29, dtype=np.float32)
+    kb = B().kernel("rbf", gamma=0.5)
+    b, s, H = 16, 64, 64 * 11 + 16 * 3
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        A, y = dev(p.A), dev(p.y)
+        ref = B().Plan(1, A, y, kb, 1e-3, b, s, H, seed=4, prec=prec)
+        ref.run(-1)
+        pl = B().Plan(1, A, y, kb, 1e-3, b, s, H, seed=4, prec=prec)
+        assert pl.enqueue(3) == 3
+        st, _ = pl.run(2)
+        assert pl.enqueue(4) == 4
+        st, _ = pl.run(-1)
+        assert st["iters_done"] == H and st["outer_steps"] == 12
+        side.synchronize()
+        assert torch.equal(ref.alpha, pl.alpha) and torch.equal(ref.grad, pl.grad)
+        ref.close()
+        pl.close()
+
+
 # The deferred gradient evaluates the block's part at the next step's rows in
 # a separate s b x s b product whose FP32 epilogue groups other rows into
 # warps: where a warp's RBF terms decide between the factored and the clamped
