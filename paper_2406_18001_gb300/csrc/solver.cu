@@ -1233,10 +1233,9 @@ struct Solver {
     cudaEvent_t df_fork = nullptr, df_chained = nullptr, df_rows = nullptr, df_gram = nullptr, df_side = nullptr,
                 df_xfork = nullptr, df_xjoin = nullptr;
     double *df_x2 = nullptr;   // the second column half's part of x
-    TcSplit xsplit2;
-    TcSplit xsplit;            // the cross product's split (it runs beside the block)
+    TcSplit xsplit, xsplit2;   // the cross product's halves' splits (they run beside the block)
     int df_pairs = 0;          // CTA pairs of the block
-    int df_prio = 0;           // launch priority of the recurrence, the update and the block
+    int df_prio = 0;           // launch priority of the recurrence and the block
     cudaGraphExec_t graph_df[3] = {nullptr, nullptr, nullptr};
     int df_direct[3] = {0, 0, 0};
 
