@@ -1427,17 +1427,14 @@ struct Solver {
     // (next > 0) into set 1 - p on st2, forked first and joined after the update
     dcd_status lag_body(int p, int64_t cnt, int64_t next)
     {
-        if (next) {
-            DCD_TRY(cudaEventRecord(la_fork, st));
-            DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
-            dcd_status r = lag_side(1 - p, next, st2);
-            if (r != DCD_OK) return r;
-            DCD_TRY(cudaEventRecord(la_join, st2));
-        }
+        // the forks are recorded first and the recurrence is launched before the kernels that
+        // branch off them, so that it is the first of the step's kernels to take an SM
+        const bool scatter = csr && use_csc;
+        if (next) DCD_TRY(cudaEventRecord(la_fork, st));
+        if (scatter) DCD_TRY(cudaEventRecord(csr_fork, st));
         use_bufs(p);
         const int64_t ncols = cnt * o.b;
         const double *rs = problem == 0 ? y : nullptr;
-        if (csr && use_csc) DCD_TRY(csr_fork_scatter(ncols));
         FusedUpdate fu;  // a6 done by the K-RR recurrence when it can
         fu.alpha = alpha;
         fu.ctr = ctr;
@@ -1448,6 +1445,19 @@ struct Solver {
         else
             DCD_TRY(launch_recur_bdcd(Kss, tc ? 0 : 1, ldk, S, cnt, o.b, lambda, (double)m, g, tc ? 1 : 2, Lbuf,
                                       delta, w64, tc ? col_w : nullptr, &fu, err, st));
+        if (next) {
+            DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
+            dcd_status r = lag_side(1 - p, next, st2);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(la_join, st2));
+            use_bufs(p);
+        }
+        if (scatter) {  // this step's first scatter through the transposed copy, beside the recurrence
+            DCD_TRY(cudaStreamWaitEvent(csr_st, csr_fork, 0));
+            DCD_TRY(launch_csr_csc_scatter_first(cm, cscop, cstep, !tc, csr_maxrow, ncols, csr_st));
+            DCD_TRY(cudaEventRecord(csr_join, csr_st));
+            csr_forked = true;
+        }
         if (tc) DCD_TRY(clear_col_w_tail(ncols));
         if (csr)
             DCD_TRY(csr_apply(ncols, rs));
