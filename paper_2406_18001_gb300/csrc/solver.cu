@@ -1289,8 +1289,14 @@ struct Solver {
         const int nxt = (cur + 1) % 3, nn = (cur + 2) % 3;
         const StepBufs &Bc = sbuf[cur];
         const int64_t ncols = cnt * o.b;
+        // the fork is recorded first and the recurrence launched before the side streams' kernels,
+        // so that its cluster takes SMs first
+        if (has2) DCD_TRY(cudaEventRecord(df_fork, st));
+        if (has1) {
+            dcd_status r = df_chain_of(nxt, o.s, df_x[nxt], st, df_prio);
+            if (r != DCD_OK) return r;
+        }
         if (has2) {
-            DCD_TRY(cudaEventRecord(df_fork, st));
             DCD_TRY(cudaStreamWaitEvent(st2, df_fork, 0));
             dcd_status r = la_rows(nn, o.s, st2, (nn + 1) % 3);
             if (r != DCD_OK) return r;
@@ -1300,30 +1306,26 @@ struct Solver {
             if (r != DCD_OK) return r;
             DCD_TRY(cudaEventRecord(df_gram, st2));
         }
-        if (has1) {
-            dcd_status r = df_chain_of(nxt, o.s, df_x[nxt], st, df_prio);
-            if (r != DCD_OK) return r;
-            if (has2) {
-                // x of step k+2 waits for recurrence k+1.  Under capture the recurrence's node is
-                // added to the side stream's dependencies directly: an event recorded on st
-                // between the recurrence and the block would stand between the two kernels of
-                // the programmatic launch
-                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-                const cudaGraphNode_t *deps = nullptr;
-                size_t nd = 0;
-                DCD_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
-                if (cs == cudaStreamCaptureStatusActive) {
-                    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
-                    DCD_TRY(cudaStreamUpdateCaptureDependencies(st3, dv.data(), nullptr, dv.size(),
-                                                                cudaStreamAddCaptureDependencies));
-                } else {
-                    DCD_TRY(cudaEventRecord(df_chained, st));
-                    DCD_TRY(cudaStreamWaitEvent(st3, df_chained, 0));
-                }
-                r = df_cross(nn, nxt, st3, st4);
-                if (r != DCD_OK) return r;
-                DCD_TRY(cudaEventRecord(df_side, st3));
+        if (has1 && has2) {
+            // x of step k+2 waits for recurrence k+1.  Under capture the recurrence's node (still
+            // st's last) is added to the side stream's dependencies directly: an event recorded on
+            // st between the recurrence and the block would stand between the two kernels of the
+            // programmatic launch
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            DCD_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+            if (cs == cudaStreamCaptureStatusActive) {
+                std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+                DCD_TRY(cudaStreamUpdateCaptureDependencies(st3, dv.data(), nullptr, dv.size(),
+                                                            cudaStreamAddCaptureDependencies));
+            } else {
+                DCD_TRY(cudaEventRecord(df_chained, st));
+                DCD_TRY(cudaStreamWaitEvent(st3, df_chained, 0));
             }
+            const dcd_status r = df_cross(nn, nxt, st3, st4);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(df_side, st3));
         }
         // block k as the programmatic dependent of recurrence k+1 (which read g before signalling):
         // its epilogue does not wait, it reads nothing the recurrence writes; the recurrence and
