@@ -1135,17 +1135,19 @@ struct Solver {
         fu.ctr_advance = (uint64_t)cnt;
         const int P = recur_cluster_size((int)cnt, o.b, 2);
         if (P <= 0) return DCD_EINTERNAL;
+        // the fork is recorded first and the chain launched before the side kernels (its cluster
+        // takes SMs first); the block may start once the side kernels are done: about 5/8 of the
+        // chain
+        if (next) DCD_TRY(cudaEventRecord(la_fork, st));
+        const int trig = next ? (int)((cnt * o.b / 32) * 5 / 8) : -1;
+        DCD_TRY(launch_recur_cluster_chain((const float *)Bp.Kss, ldk, Bp.S, (int)cnt, o.b, P, lambda, (double)m, g, 2,
+                                           Bp.Lbuf, delta, w64, col_w, &fu, err, st, nullptr, trig));
         if (next) {
-            DCD_TRY(cudaEventRecord(la_fork, st));
             DCD_TRY(cudaStreamWaitEvent(st2, la_fork, 0));
             dcd_status r = la_side(1 - p, next, st2);
             if (r != DCD_OK) return r;
             DCD_TRY(cudaEventRecord(la_join, st2));
         }
-        // the block may start once the side kernels are done: about 5/8 of the chain
-        const int trig = next ? (int)((cnt * o.b / 32) * 5 / 8) : -1;
-        DCD_TRY(launch_recur_cluster_chain((const float *)Bp.Kss, ldk, Bp.S, (int)cnt, o.b, P, lambda, (double)m, g, 2,
-                                           Bp.Lbuf, delta, w64, col_w, &fu, err, st, nullptr, trig));
         DCD_TRY(clear_col_w_tail(ncols));
         TcOperand Aop{op.packed, m, op.n_pad, op.kind, op.row_s};
         TcOperand Bop{Bp.As, ncols, op.n_pad, op.kind, Bp.col_s, Bp.S};
