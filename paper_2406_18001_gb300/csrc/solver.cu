@@ -615,15 +615,10 @@ struct Solver {
             DCD_TRY(cudaStreamCreateWithFlags(&st4, cudaStreamNonBlocking));
             DCD_TRY(cudaEventCreateWithFlags(&df_xfork, cudaEventDisableTiming));
             DCD_TRY(cudaEventCreateWithFlags(&df_xjoin, cudaEventDisableTiming));
-            // the block leaves SMs for the recurrence ahead (one cluster) and, about, the next step's
-            // Gram; within two pairs of that, the fewest pairs that give the fewest (256-row tile,
-            // 256-column chunk) units to the most loaded pair
+            // the block leaves SMs for the recurrence ahead (one cluster) and the next step's Gram
+            // (measured at config 2: 64 of 76 pairs 88.0 us per step, 66 90.0, 68 100.5, 60 88.8)
             const int P = recur_cluster_size((int)o.s, o.b, 2);
-            const int base = split_pairs - (P + 1) / 2 - DF_GRAM_CTAS / 2;
-            const int64_t units = (m + 255) / 256 * ((sb + 255) / 256);
-            df_pairs = std::max(base, 1);
-            for (int n = std::max(base - 2, 1); n <= std::min(base + 2, split_pairs - (P + 1) / 2); ++n)
-                if ((units + n - 1) / n < (units + df_pairs - 1) / df_pairs) df_pairs = n;
+            df_pairs = std::max(split_pairs - (P + 1) / 2 - DF_GRAM_CTAS / 2, 1);
             int p_least = 0, p_greatest = 0;
             DCD_TRY(cudaDeviceGetStreamPriorityRange(&p_least, &p_greatest));
             df_prio = p_greatest;
