@@ -228,20 +228,22 @@ cudaError_t launch_block_simt_f64(const double *A, int64_t lda, int64_t m, int64
     if (ncols <= 32 && tiles < 2 * (int64_t)sms) {  // too few tiles to occupy the GPU: an entry per thread
         int cw = 1;
         while (cw < ncols) cw <<= 1;
+        // one warp per CTA: a few thousand entries then spread over every SM (the FP64 pipe, not
+        // the warp count, bounds each SM)
         const int64_t threads = nrows * cw;
-        const unsigned blocks = (unsigned)((threads + 127) / 128);
+        const unsigned blocks = (unsigned)((threads + 31) / 32);
         const bool store = (out != nullptr), rbf = (kp.kind == DCD_RBF);
         if (store && rbf)
-            block_small_f64_kernel<true, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+            block_small_f64_kernel<true, true><<<blocks, 32, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
                                                                       cols, ncols, cw, w, rs, g, out, ldo, err);
         else if (store)
-            block_small_f64_kernel<true, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+            block_small_f64_kernel<true, false><<<blocks, 32, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
                                                                        cols, ncols, cw, w, rs, g, out, ldo, err);
         else if (rbf)
-            block_small_f64_kernel<false, true><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+            block_small_f64_kernel<false, true><<<blocks, 32, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
                                                                        cols, ncols, cw, w, rs, g, out, ldo, err);
         else
-            block_small_f64_kernel<false, false><<<blocks, 128, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
+            block_small_f64_kernel<false, false><<<blocks, 32, 0, st>>>(A, lda, m, n, kp, rows, nrows, Bm, ldb, mb,
                                                                         cols, ncols, cw, w, rs, g, out, ldo, err);
         return cudaGetLastError();
     }
