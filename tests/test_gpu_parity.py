@@ -531,9 +531,9 @@ def test_deferred_gradient_matches_in_order_steps(prec, m, s, b, H):
     """The recurrence of step k+1 computed beside the block of step k, from the
     gradient before that block, the s b x s b cross product at the rows step
     k+1 samples and the update's repeat term: the iterates equal those of the
-    in-order steps up to rounding (DEFER_TOL).  m = 600 with s b = 640 repeats most rows within and across
-    consecutive steps (the repeat term); the ragged budget ends on a short
-    step after the deferred ones."""
+    in-order steps up to rounding (DEFER_TOL).  m = 600 with s b = 640
+    repeats most rows within and across consecutive steps (the repeat term);
+    the ragged budget ends on a short step after the deferred ones."""
     p = inputs.krr_dense(m=m, n=40, seed=41, dtype=np.float32)
     kb = B().kernel("rbf", gamma=0.5)
     side = torch.cuda.Stream()
@@ -546,6 +546,40 @@ def test_deferred_gradient_matches_in_order_steps(prec, m, s, b, H):
     assert s1["iters_done"] == s2["iters_done"] == H
     assert rel(a2.cpu().numpy(), a1.cpu().numpy()) < DEFER_TOL
     assert np.linalg.norm(g2.cpu().numpy() - g1.cpu().numpy()) <= DEFER_TOL * np.linalg.norm(p.y)
+
+
+@pytest.mark.parametrize("kind,kw", [("poly", dict(coef0=1.0, degree=3)), ("linear", {})])
+@pytest.mark.parametrize("prec", ["fp16", "bf16x3", "fp8"])
+def test_deferred_gradient_other_kernels_match_oracle(kind, kw, prec):
+    """The deferred look-ahead with the polynomial and linear kernels (the cross
+    product's epilogue takes their forms, with no own-sample rule), at the
+    bench's (s, b) = (64, 16): against the FP64 oracle (Algorithm 3) within
+    the mixed forms' tolerances, and against the in-order steps (DEFER_TOL).
+    fp8: the oracle runs on the dequantised rows."""
+    p = inputs.krr_dense(m=2000, n=48, seed=37, dtype=np.float32)
+    A32 = p.A
+    b, s, H, lam = 16, 64, 64 * 8 + 16, 1e-2
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    if prec == "fp8":
+        q, sc = oracle.quantize_e4m3_rows(A32)
+        A64 = oracle.dequantize_e4m3_rows(q, sc)
+    else:
+        A64 = A32.astype(np.float64)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        A = B().Fp8(dev(q), dev(sc)) if prec == "fp8" else dev(A32)
+        runs = [B().krr_solve(A, dev(p.y), kb, lam, b, s, H, seed=5, prec=prec, flags=f, stream=side.cuda_stream)
+                for f in (B().FLAG_NO_DEFER, 0)]
+        side.synchronize()
+    (a1, _, _, _), (a2, _, st2, _) = runs
+    assert st2["iters_done"] == H
+    assert rel(a2.cpu().numpy(), a1.cpu().numpy()) < DEFER_TOL
+    want = oracle.bdcd_krr(A64, p.y, ko, lam, b, H, seed=5)
+    a = a2.cpu().numpy()
+    assert rel(a, want) < (ALPHA_TOL["fp16"] if prec in ("fp16", "fp8") else 1e-4)
+    f_got = oracle.krr_objective(A64, p.y, ko, lam, a)
+    f_want = oracle.krr_objective(A64, p.y, ko, lam, want)
+    assert abs(f_got - f_want) <= 1e-6 * abs(f_want)
 
 
 def test_nonzero_alpha0_gradient_pass():
