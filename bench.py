@@ -1308,6 +1308,10 @@ def main():
     args.s_set = args.s is not None
     if args.s is None:
         args.s = 64
+    if args.impl != "reference":
+        # a plan captures its step graphs in its first steps (one per buffer set, up to three, each
+        # after one direct run of that set): the warm-up covers them
+        args.warmup = max(args.warmup, 8)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "svm":

@@ -129,14 +129,16 @@ typedef enum {
 #define DCD_FLAG_CSR_FULL_PASS 0x40 /* CSR data matrix: stream every nonzero in each step's kernel block (the
                                        paper's SpMM) even where the apply through the transposed copy would
                                        read less; both give the same bits (for comparison and testing) */
-#define DCD_FLAG_NO_DEFER 0x80  /* tensor-core K-RR steps with the look-ahead (a stream of the caller's, graphs
-                                   allowed, no phase timers): run each step's recurrence after the previous
-                                   step's block and update, which it then overlaps no longer.  By default the
-                                   recurrence of step k+1 runs beside the block of step k, on the gradient
-                                   before that block plus the block's part at the rows step k+1 samples
-                                   (an s b x s b product) and the update's: the same sums up to their
-                                   association, so the bits differ from the in-order steps by rounding only.
-                                   With this flag the steps give the bits of the one-stream steps */
+#define DCD_FLAG_NO_DEFER 0x80  /* steps with the look-ahead (a stream of the caller's, graphs allowed, no
+                                   phase timers) of tensor-core K-RR, and of K-SVM on CSR or dense FP64 data
+                                   with s <= 128: run each step's recurrence after the previous step's block
+                                   and update, which it then overlaps no longer.  By default the recurrence
+                                   of step k+1 runs beside the block of step k, on the gradient (K-SVM: and
+                                   alpha) before that block plus the block's part at the rows step k+1
+                                   samples (an s b x s b product) and the update's: the same sums up to
+                                   their association, so the bits differ from the in-order steps by
+                                   rounding only.  With this flag the steps give the bits of the one-stream
+                                   steps */
 #define DCD_FLAG_REFRESH 0x10     /* with tol > 0: when the metric of the cached gradient first meets tol,
                                      recompute the gradient from alpha by full kernel passes (tensor-core
                                      modes: DCD_PREC_REFRESH; FP64 mode: FP64) and accept convergence only

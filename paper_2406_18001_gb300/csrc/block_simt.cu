@@ -163,29 +163,79 @@ cudaError_t launch_rn(int rn, int64_t grid, const double *A, int64_t lda, int64_
 // clock per SM) spreads over every SM instead of filling a few 64 x 16 tiles.
 // Each entry's dot product (or squared distance) runs over k = 0..n-1 with the
 // operations of block_simt_f64_kernel, so both kernels produce the same bits.
-// A warp holds 32 / CW rows x CW columns (CW a power of two >= the columns);
-// the apply sums a row's CW terms by a fixed butterfly and lane 0 of the row's
-// group adds rs * sum to g.
-template <bool STORE, bool RBF>
-__global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
-                                                              int64_t n, KernelParams kp, const int32_t *rows,
-                                                              int64_t nrows, const double *__restrict__ Bm,
-                                                              int64_t ldb, int64_t mb, const int32_t *cols,
-                                                              int64_t ncols, int cw, const double *__restrict__ w,
-                                                              const double *__restrict__ rs, double *g, double *out,
-                                                              int64_t ldo, int *err)
+// A one-warp CTA holds 32 / CW rows x CW columns (CW a power of two >= the
+// columns).  Their vectors go through shared memory SMALL_KC dimensions at a
+// time by asynchronous copies, all of a chunk in flight at once (coalesced, a
+// lane per dimension): the dependent FMA chain then reads shared memory
+// instead of waiting on an L2 round trip every few steps.  The apply sums a row's CW
+// terms by a fixed butterfly and lane 0 of the row's group adds rs * sum to g.
+constexpr int SMALL_KC = 64;
+
+// an 8-byte asynchronous copy from global to shared memory (completed by cp.async.wait_all)
+__device__ __forceinline__ void cp_async_8(double *dst, const double *src)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int c = (int)(t % cw);
-    const int64_t r = t / cw;
-    const bool ok = r < nrows && c < ncols;
-    double kv = 0.0;
-    if (ok) {
-        const int64_t ri = rows ? (int64_t)rows[r] : r, ci = cols ? (int64_t)cols[c] : c;
-        if (ri >= 0 && ri < m && ci >= 0 && ci < mb) {
-            const double *a = A + ri * lda, *b = Bm + ci * ldb;
-            double acc = 0.0;
-            for (int64_t k = 0; k < n; ++k) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+
+template <bool STORE, bool RBF>
+__global__ void __launch_bounds__(32) block_small_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m,
+                                                             int64_t n, KernelParams kp, const int32_t *rows,
+                                                             int64_t nrows, const double *__restrict__ Bm,
+                                                             int64_t ldb, int64_t mb, const int32_t *cols,
+                                                             int64_t ncols, int cw, const double *__restrict__ w,
+                                                             const double *__restrict__ rs, double *g, double *out,
+                                                             int64_t ldo, int *err)
+{
+    // vectors 0..R-1: the CTA's rows; R..R+ncols-1: the columns (R + cw <= 33)
+    __shared__ double sv[33][SMALL_KC + 1];
+    __shared__ const double *src[33];
+    const int lane = threadIdx.x;
+    const int R = 32 / cw;
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int nc = (int)(ncols < cw ? ncols : cw);
+    const int nv = R + nc;
+    for (int v = lane; v < nv; v += 32) {  // nv reaches 33 (one column, or one row)
+        const double *p = nullptr;
+        if (v < R) {
+            const int64_t r = r0 + v;
+            if (r < nrows) {
+                const int64_t ri = rows ? (int64_t)rows[r] : r;
+                if (ri >= 0 && ri < m)
+                    p = A + ri * lda;
+                else
+                    set_error(err, DEV_BAD_INDEX);
+            }
+        } else {
+            const int64_t ci = cols ? (int64_t)cols[v - R] : (int64_t)(v - R);
+            if (ci >= 0 && ci < mb)
+                p = Bm + ci * ldb;
+            else
+                set_error(err, DEV_BAD_INDEX);
+        }
+        src[v] = p;
+    }
+    __syncwarp();
+    const int c = lane % cw, rl = lane / cw;
+    const int64_t r = r0 + rl;
+    const bool ok = r < nrows && c < nc && src[rl] != nullptr && src[R + c] != nullptr;
+    double acc = 0.0;
+    for (int64_t k0 = 0; k0 < n; k0 += SMALL_KC) {
+        const int kc = (int)(n - k0 < SMALL_KC ? n - k0 : SMALL_KC);
+        // stage the chunk: two dimensions per lane per vector, every copy in flight at once (only
+        // the valid vectors' first kc entries are read below)
+        for (int v = 0; v < nv; ++v) {
+            const double *p = src[v];
+            if (!p) continue;
+            if (lane < kc) cp_async_8(&sv[v][lane], p + k0 + lane);
+            if (lane + 32 < kc) cp_async_8(&sv[v][lane + 32], p + k0 + lane + 32);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        if (ok) {
+            const double *a = sv[rl], *b = sv[R + c];
+#pragma unroll 8
+            for (int k = 0; k < kc; ++k) {
                 if (RBF) {
                     const double d = a[k] - b[k];
                     acc = fma(d, d, acc);
@@ -193,11 +243,10 @@ __global__ void __launch_bounds__(128) block_small_f64_kernel(const double *__re
                     acc = fma(a[k], b[k], acc);
                 }
             }
-            kv = kfun_f64(kp, acc);
-        } else {
-            set_error(err, DEV_BAD_INDEX);
         }
+        __syncwarp();
     }
+    const double kv = ok ? kfun_f64(kp, acc) : 0.0;
     if (STORE) {
         if (ok) out[r * ldo + c] = kv;
         return;

@@ -251,6 +251,14 @@ cudaError_t launch_init_grad(int problem, const double *y, const double *alpha, 
 // the deferred gradient (solver.cu): acc[p] += add[p] (add may be NULL) + diag * (the sum of dprev
 // over the previous step's positions q holding row S[p], in position order) where any does -- the
 // update's part of the gradient at the next step's rows.  cprev <= 8192.
+// the deferred K-SVM step (sample_update.cu): alpha and g at S (before they change), and the
+// pending parts of the next step's alpha and g from this step's Kx = K(A_S, A_Sc) (row-major,
+// leading dimension ldx), theta and w = y theta
+cudaError_t launch_dcd_snapshot(const int32_t *S, int64_t cnt, int64_t m, const double *alpha, const double *g,
+                                double *alpha_out, double *g_out, cudaStream_t st);
+cudaError_t launch_dcd_pending(const int32_t *S, int64_t cnt, const double *y, const void *Kx, bool kx_f64,
+                               int64_t ldx, const int32_t *Sc, const double *theta, const double *w, int64_t cc,
+                               double diag, double *alpha_add, double *g_add, cudaStream_t st);
 cudaError_t launch_defer_repeat(const int32_t *S, int64_t cnt, const int32_t *Sprev, const double *dprev,
                                 int64_t cprev, double diag, const double *add, double *acc, cudaStream_t st);
 // (pdl: launched as the programmatic dependent of the kernel before it, whose results it does not
@@ -352,9 +360,16 @@ cudaError_t launch_csr_block(const CsrOperand &A, const CsrColMap &M, bool fp64,
                              const double *w64, const double *rs, double *g, void *out, int64_t ldo, cudaStream_t st);
 
 // recurrence (recur.cu)
+// alpha and g at a DCD step's coordinates given as a snapshot plus the parts not yet in it (the
+// deferred K-SVM step; position order of the step)
+struct DcdPending {
+    const double *alpha_snap = nullptr, *alpha_add = nullptr, *g_snap = nullptr, *g_add = nullptr;
+};
+// (pend: the chain reads alpha and g from it; only for cnt <= 128, else cudaErrorInvalidValue)
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
                              const double *y, const double *alpha, const double *g, double omega, double nu,
-                             double *delta, double *w64, float *w32, int *err, cudaStream_t st);
+                             double *delta, double *w64, float *w32, int *err, cudaStream_t st,
+                             const DcdPending *pend = nullptr);
 size_t recur_bdcd_scratch_bytes(int64_t nblk, int b);
 // true when launch_recur_bdcd with these arguments reads only the lower
 // triangle (with the diagonal blocks) of an FP32 Gram

@@ -798,10 +798,13 @@ constexpr int DCD_FAST_MAX = 128;
 constexpr int DCD_FAST_K = DCD_FAST_MAX / 32;
 
 template <typename KT>
+// pend (optional): alpha and g at the step's coordinates are pend[0][t] + pend[1][t] and
+// pend[2][t] + pend[3][t] (a snapshot and the parts not yet in it) instead of alpha[S[t]], g[S[t]]
 __global__ void __launch_bounds__(DCD_THREADS) recur_dcd_fast_kernel(const KT *Kss, int64_t ldk, const int32_t *S,
                                                                      int cnt, const double *y, const double *alpha,
                                                                      const double *g, double omega, double nu,
-                                                                     double *delta, double *w64, float *w32)
+                                                                     double *delta, double *w64, float *w32,
+                                                                     DcdPending pend)
 {
     extern __shared__ double fsm[];
     double *C = fsm;                                   // C[j * cnt + t]
@@ -824,8 +827,13 @@ __global__ void __launch_bounds__(DCD_THREADS) recur_dcd_fast_kernel(const KT *K
             const bool v = t < cnt;
             const int32_t i = v ? sI[t] : -1;
             id[k] = i;
-            a[k] = v ? alpha[i] : 0.0;
-            gg[k] = v ? g[i] : 0.0;
+            if (pend.alpha_snap) {
+                a[k] = v ? pend.alpha_snap[t] + pend.alpha_add[t] : 0.0;
+                gg[k] = v ? pend.g_snap[t] + pend.g_add[t] : 0.0;
+            } else {
+                a[k] = v ? alpha[i] : 0.0;
+                gg[k] = v ? g[i] : 0.0;
+            }
             const double eta = v ? kval(Kss, ldk, t, t) + omega : 0.0;  // G_k = V^T U_k + omega I, y_t^2 = 1
             ie[k] = eta > 0.0 ? 1.0 / eta : 0.0;
             corr[k] = gg[k];  // the gradient of coordinate t as the corrections arrive
@@ -894,9 +902,12 @@ __global__ void __launch_bounds__(DCD_THREADS) recur_dcd_fast_kernel(const KT *K
 
 cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const int32_t *S, int64_t cnt,
                              const double *y, const double *alpha, const double *g, double omega, double nu,
-                             double *delta, double *w64, float *w32, int *err, cudaStream_t st)
+                             double *delta, double *w64, float *w32, int *err, cudaStream_t st,
+                             const DcdPending *pend)
 {
     if (cnt <= 0) return cudaSuccess;
+    const DcdPending pd = pend ? *pend : DcdPending{};
+    if (pend && cnt > DCD_FAST_MAX) return cudaErrorInvalidValue;
     if (cnt <= DCD_FAST_MAX) {
         const size_t fsm = sizeof(double) * (size_t)(cnt * cnt + cnt) + sizeof(int32_t) * cnt;
         static bool fattr[2] = {false, false};
@@ -908,7 +919,7 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
                 fattr[1] = true;
             }
             recur_dcd_fast_kernel<double><<<1, DCD_THREADS, fsm, st>>>((const double *)Kss, ldk, S, (int)cnt, y, alpha,
-                                                                       g, omega, nu, delta, w64, w32);
+                                                                       g, omega, nu, delta, w64, w32, pd);
         } else {
             if (!fattr[0]) {
                 cudaError_t e = cudaFuncSetAttribute(recur_dcd_fast_kernel<float>,
@@ -917,7 +928,7 @@ cudaError_t launch_recur_dcd(const void *Kss, int kss_f64, int64_t ldk, const in
                 fattr[0] = true;
             }
             recur_dcd_fast_kernel<float><<<1, DCD_THREADS, fsm, st>>>((const float *)Kss, ldk, S, (int)cnt, y, alpha,
-                                                                      g, omega, nu, delta, w64, w32);
+                                                                      g, omega, nu, delta, w64, w32, pd);
         }
         return cudaGetLastError();
     }

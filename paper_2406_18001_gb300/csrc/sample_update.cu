@@ -780,6 +780,78 @@ __global__ void __launch_bounds__(UPD_WARPS * 32)
 }
 
 // ------------------------------------------------- deferred gradient --
+// The deferred K-SVM step.  snapshot: alpha and g at the next step's coordinates, taken before
+// this step's block and update write them.
+__global__ void dcd_snapshot_kernel(const int32_t *S, int64_t cnt, int64_t m, const double *alpha, const double *g,
+                                    double *alpha_out, double *g_out)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= cnt) return;
+    const int64_t i = S[p];
+    const bool ok = i >= 0 && i < m;
+    alpha_out[p] = ok ? alpha[i] : 0.0;
+    g_out[p] = ok ? g[i] : 0.0;
+}
+
+cudaError_t launch_dcd_snapshot(const int32_t *S, int64_t cnt, int64_t m, const double *alpha, const double *g,
+                                double *alpha_out, double *g_out, cudaStream_t st)
+{
+    if (cnt <= 0) return cudaSuccess;
+    dcd_snapshot_kernel<<<(unsigned)((cnt + 127) / 128), 128, 0, st>>>(S, cnt, m, alpha, g, alpha_out, g_out);
+    return cudaGetLastError();
+}
+
+// The pending parts of the next step's alpha and g at its coordinates p (rows S[p]) from this
+// step (coordinates Sc, steps theta, coefficients w = y theta):
+//   g_add[p] = y[S[p]] (sum_j Kx[p][j] w[j]) + diag * (sum of theta over this step's positions
+//              holding row S[p], in position order), alpha_add[p] = that sum.
+// One warp per p; the lanes' partial sums over j are combined by a fixed butterfly.
+template <typename KT>
+__global__ void dcd_pending_kernel(const int32_t *S, int cnt, const double *y, const KT *Kx, int64_t ldx,
+                                   const int32_t *Sc, const double *theta, const double *w, int cc, double diag,
+                                   double *alpha_add, double *g_add)
+{
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= cnt) return;  // warp-uniform
+    const int32_t key = S[p];
+    double dot = 0.0;
+    for (int j = lane; j < cc; j += 32) dot = fma((double)Kx[(int64_t)p * ldx + j], w[j], dot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    double sum = 0.0;
+    bool any = false;
+    for (int q0 = 0; q0 < cc; q0 += 32) {
+        unsigned hit = __ballot_sync(0xffffffffu, q0 + lane < cc && Sc[q0 + lane] == key);
+        any = any || hit != 0u;
+        while (hit) {  // in position order
+            sum += theta[q0 + __ffs(hit) - 1];
+            hit &= hit - 1u;
+        }
+    }
+    if (lane == 0) {
+        double v = y[key] * dot;
+        if (any) v += diag * sum;
+        g_add[p] = v;
+        alpha_add[p] = any ? sum : 0.0;
+    }
+}
+
+cudaError_t launch_dcd_pending(const int32_t *S, int64_t cnt, const double *y, const void *Kx, bool kx_f64,
+                               int64_t ldx, const int32_t *Sc, const double *theta, const double *w, int64_t cc,
+                               double diag, double *alpha_add, double *g_add, cudaStream_t st)
+{
+    if (cnt <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((cnt + 3) / 4);
+    if (kx_f64)
+        dcd_pending_kernel<double><<<blocks, 128, 0, st>>>(S, (int)cnt, y, (const double *)Kx, ldx, Sc, theta, w,
+                                                           (int)cc, diag, alpha_add, g_add);
+    else
+        dcd_pending_kernel<float><<<blocks, 128, 0, st>>>(S, (int)cnt, y, (const float *)Kx, ldx, Sc, theta, w,
+                                                          (int)cc, diag, alpha_add, g_add);
+    return cudaGetLastError();
+}
+
 // acc[p] += add[p] (add: optional) + diag * sum of dprev[q] over q with
 // Sprev[q] == S[p] (in position order, the update's own sum), where any q
 // matches: the update's part of the gradient at a row the next step samples.

@@ -258,8 +258,8 @@ struct Solver {
     CsrOperand ca;
     CsrColMap cm;
     void *ws_csr = nullptr;
-    CsrColMap cm_set[2];     // the column map of each buffer set (the K-SVM look-ahead)
-    void *ws_csr2 = nullptr;
+    CsrColMap cm_set[3];     // the column map of each buffer set (the K-SVM look-ahead)
+    void *ws_csr2[2] = {nullptr, nullptr};
     // the apply through the transposed copy (chosen at set-up when it reads far less than a full pass)
     bool use_csc = false;
     CscOperand cscop;
@@ -304,10 +304,11 @@ struct Solver {
                 cudaStreamSynchronize(sx);
                 cudaStreamDestroy(sx);
             }
-        for (cudaEvent_t ev : {df_fork, df_chained, df_rows, df_gram, df_side, df_xfork, df_xjoin})
+        for (cudaEvent_t ev : {df_fork, df_chained, df_rows, df_gram, df_side, df_xfork, df_xjoin, df_kx})
             if (ev) cudaEventDestroy(ev);
         if (ws_csr) cudaFreeAsync(ws_csr, st);
-        if (ws_csr2) cudaFreeAsync(ws_csr2, st);
+        for (void *w : ws_csr2)
+            if (w) cudaFreeAsync(w, st);
         if (csr_st) {
             cudaStreamSynchronize(csr_st);
             cudaStreamDestroy(csr_st);
@@ -385,6 +386,11 @@ struct Solver {
                              !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                              st != cudaStreamLegacy && st != cudaStreamPerThread;
         const bool set2 = la_pos || lag_pos;  // a second set of step buffers
+        // the deferred K-SVM step (the recurrence one step ahead of the block): CSR or dense FP64
+        // data, a step the one-block recurrence takes
+        const bool dfs_pos = lag_pos && problem == 0 && o.b == 1 && (csr || !tc) && o.s <= 128 &&
+                             !(o.flags & DCD_FLAG_NO_DEFER);
+        const bool set3 = df_pos || dfs_pos;  // a third set
         const int64_t n_pad_r = sliced_ref ? (n + 63) / 64 * 64 : (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(kind_r, n_pad_r) : 0;
 
@@ -442,14 +448,18 @@ struct Solver {
             uint64_t *crl = (uint64_t *)ar.take(set2 ? 3 * sizeof(uint64_t) : 0);
             // the deferred gradient: a third set, the recurrence's outputs per set, x per set and the
             // cross product's split
-            int32_t *sidx_c = (int32_t *)ar.take(df_pos ? sizeof(int32_t) * col_pad : 0);
+            int32_t *sidx_c = (int32_t *)ar.take(set3 ? sizeof(int32_t) * col_pad : 0);
             void *as_c = ar.take(df_pos ? (size_t)sb * row_bytes : 0, 1024);
             float *ch_c = (float *)ar.take(df_pos ? sizeof(float) * col_pad : 0);
             float *cs_c = (float *)ar.take(df_pos && scaled ? sizeof(float) * col_pad : 0);
-            void *kss_c = ar.take(df_pos ? (size_t)sb * sb * 4 : 0);
+            void *kss_c = ar.take(set3 ? (size_t)sb * sb * (tc ? 4 : 8) : 0);
             double *lb_c = (double *)ar.take(df_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
-            double *dfd = (double *)ar.take(df_pos ? 4 * sizeof(double) * col_pad : 0);  // delta, w64 of sets 1, 2
-            float *dfw = (float *)ar.take(df_pos ? 2 * sizeof(float) * col_pad : 0);     // col_w of sets 1, 2
+            double *dfd = (double *)ar.take(set3 ? 4 * sizeof(double) * col_pad : 0);  // delta, w64 of sets 1, 2
+            float *dfw = (float *)ar.take(set3 ? 2 * sizeof(float) * col_pad : 0);     // col_w of sets 1, 2
+            // the deferred K-SVM step: per set alpha and g at its rows (snapshot, pending parts), and
+            // the kernel values of the step after next's rows against the next step's
+            double *dsn = (double *)ar.take(dfs_pos ? 12 * sizeof(double) * col_pad : 0);
+            void *dkx = ar.take(dfs_pos ? (size_t)sb * sb * (tc ? 4 : 8) : 0);
             double *dfx = (double *)ar.take(df_pos ? 4 * sizeof(double) * col_pad : 0);  // x of sets 0-2, x2
             double *xsp =
                 (double *)ar.take(df_pos ? 2 * sizeof(double) * tc_split_part_elems(DF_XPAIRS, split_chunks) : 0);
@@ -544,13 +554,16 @@ struct Solver {
             sbuf[0].delta = dl;
             sbuf[0].w64 = wv;
             sbuf[0].col_w = cw;
-            if (df_pos)
+            if (set3)
                 for (int q = 1; q < 3; ++q) {
                     sbuf[q].delta = dfd + (size_t)(2 * q - 2) * col_pad;
                     sbuf[q].w64 = dfd + (size_t)(2 * q - 1) * col_pad;
                     sbuf[q].col_w = dfw + (size_t)(q - 1) * col_pad;
                 }
             for (int q = 0; q < 3; ++q) df_x[q] = df_pos ? dfx + (size_t)q * col_pad : nullptr;
+            for (int q = 0; q < 3; ++q)
+                for (int k = 0; k < 4; ++k) dfs_v[q][k] = dfs_pos ? dsn + (size_t)(4 * q + k) * col_pad : nullptr;
+            dfs_kx = dkx;
             df_x2 = df_pos ? dfx + 3 * (size_t)col_pad : nullptr;
             xsplit2.part = df_pos ? xsp + tc_split_part_elems(DF_XPAIRS, split_chunks) : nullptr;
             xsplit2.cnt = df_pos ? xsc + 2 * DF_XPAIRS : nullptr;
@@ -624,6 +637,16 @@ struct Solver {
             df_prio = p_greatest;
             df = true;
         }
+        if (dfs_pos) {
+            for (int q = 1; q < 3; ++q) DCD_TRY(cudaMemsetAsync(sbuf[q].col_w, 0, sizeof(float) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[2].S, 0, sizeof(int32_t) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(dfs_v[0][0], 0, 12 * sizeof(double) * col_pad, st));
+            for (cudaEvent_t *ev : {&df_fork, &df_chained, &df_rows, &df_side, &df_kx})
+                DCD_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+            DCD_TRY(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+            DCD_TRY(cudaStreamCreateWithFlags(&st4, cudaStreamNonBlocking));
+            dfs = true;
+        }
         DCD_TRY(cudaMemcpyAsync(ctr, &o.start_iter, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
         // the recurrence scratch starts zeroed (the FP64 form keeps its refinement state there)
         if (problem == 1) DCD_TRY(cudaMemsetAsync(Lbuf, 0, recur_bdcd_scratch_bytes(o.s, o.b), st));
@@ -655,13 +678,14 @@ struct Solver {
                 if (cs != DCD_OK) return cs;
             }
             cm_set[0] = cm;
-            if (lag) {  // the look-ahead's second column map and pair table
+            // the look-ahead's second column map and pair table (and the deferred step's third)
+            for (int q = 1; q < (dfs ? 3 : lag ? 2 : 1); ++q) {
                 const int64_t pairs = sb * (int64_t)std::max(csr_maxrow, 1);
                 const size_t pb = (size_t)pairs * (8 + 8 + 4) + 256 * 3;
-                DCD_TRY(malloc_async(&ws_csr2, cmb + pb, st));
-                DCD_TRY(cudaMemsetAsync(ws_csr2, 0, cmb + pb, st));
-                CsrColMap c2 = csr_colmap_carve(ws_csr2, n, cap);
-                char *pp = (char *)ws_csr2 + (cmb + 255) / 256 * 256;
+                DCD_TRY(malloc_async(&ws_csr2[q - 1], cmb + pb, st));
+                DCD_TRY(cudaMemsetAsync(ws_csr2[q - 1], 0, cmb + pb, st));
+                CsrColMap c2 = csr_colmap_carve(ws_csr2[q - 1], n, cap);
+                char *pp = (char *)ws_csr2[q - 1] + (cmb + 255) / 256 * 256;
                 c2.pstart = (int64_t *)pp;
                 pp += ((size_t)pairs * 8 + 255) / 256 * 256;
                 c2.pval = (double *)pp;
@@ -669,7 +693,7 @@ struct Solver {
                 c2.plen = (int32_t *)pp;
                 c2.pmax = cm.pmax;
                 c2.csc_col_ptr = cm.csc_col_ptr;
-                cm_set[1] = c2;
+                cm_set[q] = c2;
             }
         } else if (tc) {
             op.n_pad = n_pad;
@@ -1069,7 +1093,7 @@ struct Solver {
         col_s = sbuf[p].col_s;
         Kss = sbuf[p].Kss;
         Lbuf = sbuf[p].Lbuf;
-        if (df) {
+        if (df || dfs) {
             delta = sbuf[p].delta;
             w64 = sbuf[p].w64;
             col_w = sbuf[p].col_w;
@@ -1404,17 +1428,172 @@ struct Solver {
         return DCD_OK;
     }
 
+    // ---- the deferred K-SVM step (the recurrence one step ahead of the block and update) ----
+    // The recurrence of step k+1 needs alpha and g at its rows S(k+1) after step k's block and
+    // update.  Those are the values before block k (a snapshot taken once update k-1 is done)
+    // plus step k's part, which needs only step k's steps theta(k) and coefficients w(k) = y theta(k):
+    //   alpha: the sum of theta(k) over the positions of S(k) holding the same row,
+    //   g:     y_i K(a_i, A_S(k)) w(k) (an s x s product) plus diag times that sum.
+    // Step k+2's part is formed as soon as recurrence k+1 ends, so each body runs recurrence k+1
+    // beside block k.  One captured body per step k, buffer sets in rotation (cur: step k with its
+    // recurrence outputs; nxt: step k+1's products and pending parts; nn: step k+2's):
+    //   st : the snapshot at S(k+1), block k (the CSR block's first scatter forked beside it), update k;
+    //   st3: recurrence k+1 on the snapshot plus the pending parts, then step k+2's pending parts;
+    //   st2: step k+2's sample, column map (CSR) and Gram, into nn;
+    //   st4: after that sample, K(A_S(k+2), A_S(k+1)) for the pending parts.
+    // The sums are associated differently from the in-order step's; results agree to rounding.
+    // A gradient recomputation invalidates the recurrence and the parts computed ahead.
+    bool dfs = false;
+    double *dfs_v[3][4] = {};  // per set: alpha snapshot, alpha pending, g snapshot, g pending
+    void *dfs_kx = nullptr;    // s x s kernel values (FP32 when tc, else FP64), row-major
+    cudaEvent_t df_kx = nullptr;
+
+    // K(A_S(q2) rows, A_S(q) columns) into dfs_kx on stream s2 (the column map of set q)
+    cudaError_t dfs_cross(int q2, int q, int64_t cnt, cudaStream_t s2)
+    {
+        if (csr)
+            return launch_csr_block(ca, cm_set[q], !tc, kp, sbuf[q2].S, cnt, sbuf[q].S, cnt, nullptr, nullptr,
+                                    nullptr, nullptr, dfs_kx, cnt, s2);
+        return launch_block_simt_f64(op.a64, op.lda, m, n, kp, sbuf[q2].S, cnt, sbuf[q].S, cnt, nullptr, nullptr,
+                                     nullptr, (double *)dfs_kx, cnt, err, s2);
+    }
+
+    // the pending parts of set q2 (the step after set q's) from set q's recurrence outputs
+    cudaError_t dfs_pending(int q2, int q, int64_t cnt, cudaStream_t s2)
+    {
+        return launch_dcd_pending(sbuf[q2].S, cnt, y, dfs_kx, !tc, cnt, sbuf[q].S, sbuf[q].delta, sbuf[q].w64, cnt,
+                                  diag, dfs_v[q2][1], dfs_v[q2][3], s2);
+    }
+
+    // the recurrence of the step in set q on stream s2 (pend: from the snapshot and pending parts)
+    cudaError_t dfs_chain_of(int q, int64_t cnt, bool pend, cudaStream_t s2)
+    {
+        const StepBufs &Bq = sbuf[q];
+        DcdPending pd{dfs_v[q][0], dfs_v[q][1], dfs_v[q][2], dfs_v[q][3]};
+        return launch_recur_dcd(Bq.Kss, tc ? 0 : 1, ldk, Bq.S, cnt, y, alpha, g, omega, nu, Bq.delta, Bq.w64,
+                                tc ? Bq.col_w : nullptr, err, s2, pend ? &pd : nullptr);
+    }
+
+    dcd_status dfs_body(int cur, int64_t cnt, bool has1, bool has2)
+    {
+        const int nxt = (cur + 1) % 3, nn = (cur + 2) % 3;
+        const bool scatter = csr && use_csc;
+        if (has1) {
+            DCD_TRY(launch_dcd_snapshot(sbuf[nxt].S, o.s, m, alpha, g, dfs_v[nxt][0], dfs_v[nxt][2], st));
+            DCD_TRY(cudaEventRecord(df_fork, st));
+        }
+        if (scatter) DCD_TRY(cudaEventRecord(csr_fork, st));
+        if (has1) {  // the recurrence first, so that it is the first of the step's kernels to take an SM
+            DCD_TRY(cudaStreamWaitEvent(st3, df_fork, 0));
+            DCD_TRY(dfs_chain_of(nxt, o.s, true, st3));
+        }
+        if (has2) {
+            DCD_TRY(cudaStreamWaitEvent(st2, df_fork, 0));
+            dcd_status r = lag_side(nn, o.s, st2, (nn + 1) % 3, df_rows);
+            if (r != DCD_OK) return r;
+            DCD_TRY(cudaEventRecord(la_join, st2));
+            DCD_TRY(cudaStreamWaitEvent(st4, df_rows, 0));
+            DCD_TRY(dfs_cross(nn, nxt, o.s, st4));
+            DCD_TRY(cudaEventRecord(df_kx, st4));
+            DCD_TRY(cudaStreamWaitEvent(st3, df_kx, 0));
+            DCD_TRY(dfs_pending(nn, nxt, o.s, st3));
+        }
+        if (has1) DCD_TRY(cudaEventRecord(df_side, st3));
+        use_bufs(cur);
+        const int64_t ncols = cnt * o.b;
+        if (scatter) {  // this step's first scatter through the transposed copy, beside the block's start
+            DCD_TRY(cudaStreamWaitEvent(csr_st, csr_fork, 0));
+            DCD_TRY(launch_csr_csc_scatter_first(cm, cscop, cstep, !tc, csr_maxrow, ncols, csr_st));
+            DCD_TRY(cudaEventRecord(csr_join, csr_st));
+            csr_forked = true;
+        }
+        const double *rs = y;
+        if (csr)
+            DCD_TRY(csr_apply(ncols, rs));
+        else
+            DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr, 0,
+                                          err, st));
+        DCD_TRY(launch_update(S, delta, ncols, diag, alpha, g, ctr, (uint64_t)cnt, m, err, st));
+        if (has2) DCD_TRY(cudaStreamWaitEvent(st, la_join, 0));
+        if (has1) DCD_TRY(cudaStreamWaitEvent(st, df_side, 0));
+        return DCD_OK;
+    }
+
+    // one full step through the deferred bodies
+    dcd_status dfs_step(int64_t cnt)
+    {
+        const int cur = df_cur, nxt = (cur + 1) % 3, nn = (cur + 2) % 3;
+        const int64_t rem1 = o.max_iters - done - cnt, rem2 = rem1 - o.s;
+        const bool has1 = rem1 >= o.s, has2 = has1 && rem2 >= o.s;
+        if (!df_chain) {  // prologue: this step's products (unless prepared), its recurrence on alpha and g
+            if (la_cnt != cnt) {
+                DCD_TRY(cudaMemcpyAsync(ctr_la + cur, ctr, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+                dcd_status r = lag_side(cur, cnt, st, nxt);
+                if (r != DCD_OK) return r;
+                la_cnt = cnt;
+                df_prod = 0;  // the position after this step is in ctr_la[nxt]; nothing sampled there
+            }
+            DCD_TRY(dfs_chain_of(cur, cnt, false, st));
+            if (has1) {  // step k+1's products and pending parts
+                if (df_prod != o.s) {
+                    dcd_status r = lag_side(nxt, o.s, st, nn);
+                    if (r != DCD_OK) return r;
+                    df_prod = o.s;
+                }
+                DCD_TRY(dfs_cross(nxt, cur, o.s, st));
+                DCD_TRY(dfs_pending(nxt, cur, o.s, st));
+            }
+            df_chain = true;
+        }
+        const bool graphable = !graph_failed && has1 && has2;  // the steady state replays three graphs
+        if (graphable && graph_df[cur]) {
+            DCD_TRY(cudaGraphLaunch(graph_df[cur], st));
+        } else if (graphable && df_direct[cur] >= 1) {
+            DCD_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const dcd_status sc = dfs_body(cur, cnt, has1, has2);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            const bool ok = sc == DCD_OK && ec == cudaSuccess && graph != nullptr &&
+                            cudaGraphInstantiate(&graph_df[cur], graph, 0) == cudaSuccess;
+            if (ok) stats.gpu_launches_per_step = count_kernel_nodes(graph);
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                cudaGetLastError();
+                graph_df[cur] = nullptr;
+                graph_failed = true;
+                dcd_status r = dfs_body(cur, cnt, has1, has2);
+                if (r != DCD_OK) return r;
+            } else {
+                DCD_TRY(cudaGraphLaunch(graph_df[cur], st));
+            }
+        } else {
+            dcd_status r = dfs_body(cur, cnt, has1, has2);
+            if (r != DCD_OK) return r;
+            if (graphable) ++df_direct[cur];
+        }
+        df_cur = nxt;
+        df_chain = has1;
+        df_prod = has2 ? o.s : 0;
+        la_cnt = has1 ? o.s : 0;  // the products of the next step are in place
+        la_par = nxt < 2 ? nxt : 0;
+        use_bufs(cur);  // the set just used is free (for a gradient recomputation)
+        return DCD_OK;
+    }
+
     // ---- the look-ahead of the other steps (K-SVM; K-RR off the single-cluster path) ----
     // Step k+1's sample (from ctr_la, as above), its column map (CSR) or gathered rows (dense
     // tensor-core form) and its Gram, into buffer set q on stream s2; the helpers enqueue on the
-    // plan's stream member, pointed at s2 meanwhile
-    dcd_status lag_side(int q, int64_t cnt, cudaStream_t s2)
+    // plan's stream member, pointed at s2 meanwhile.  The sample leaves the following position in
+    // ctr_la[qnext] (1 - q by default); `sampled` (optional) is recorded after it.
+    dcd_status lag_side(int q, int64_t cnt, cudaStream_t s2, int qnext = -1, cudaEvent_t sampled = nullptr)
     {
         const cudaStream_t keep = st;
         st = s2;
         use_bufs(q);
         const int64_t ncols = cnt * o.b;
-        cudaError_t e = launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, S, err, st, ctr_la + (1 - q));
+        cudaError_t e =
+            launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, S, err, st, ctr_la + (qnext < 0 ? 1 - q : qnext));
+        if (e == cudaSuccess && sampled) e = cudaEventRecord(sampled, st);
         if (e == cudaSuccess) e = gather(ncols);
         if (e == cudaSuccess) e = gram(ncols);
         st = keep;
@@ -1518,6 +1697,13 @@ struct Solver {
 
     dcd_status outer_step(int64_t cnt, EventTimer &tm)
     {
+        if (dfs && !tm.on && cnt == o.s) {
+            dcd_status r = dfs_step(cnt);
+            if (r != DCD_OK) return r;
+            done += cnt;
+            ++steps;
+            return DCD_OK;
+        }
         if (lag && !tm.on) {
             dcd_status r = lag_step(cnt);
             if (r != DCD_OK) return r;

@@ -106,11 +106,15 @@ def test_krr_solve_through_csc_equals_full_pass_over_several_column_chunks(spars
 
 @pytest.mark.parametrize("prec,flags", [("fp64", 0), ("bf16x3", 0), ("bf16x3", "full")])
 def test_svm_lookahead_on_csr_matches_one_stream_steps(sparse, prec, flags):
-    """The K-SVM look-ahead on CSR data (the next step's column map, pair table
-    and Gram in the other buffer set on a second stream, this step's scatter
-    beside its recurrence) gives the one-stream steps' iterates bit for bit,
-    with gap checks, recomputations and a short last step; through the
-    transposed copy and with the full pass."""
+    """The K-SVM look-ahead on CSR data with in-order steps (the next step's
+    column map, pair table and Gram in the other buffer set on a second
+    stream, this step's scatter beside its recurrence) gives the one-stream
+    steps' iterates bit for bit, with gap checks, recomputations and a short
+    last step; through the transposed copy and with the full pass.  The
+    default deferred step (the recurrence one step ahead, beside the block)
+    gives them up to the association of the sums: 1e-10 relative in FP64,
+    1e-5 with the FP32 block (its s x s cross product rounds each kernel value
+    in FP32 as the block does, its sum over the step runs in FP64)."""
     p = sparse
     A = lib_csr(p, np.float64 if prec == "fp64" else np.float32)
     kb = B().kernel("poly", coef0=1.0, degree=3)
@@ -118,14 +122,38 @@ def test_svm_lookahead_on_csr_matches_one_stream_steps(sparse, prec, flags):
     side = torch.cuda.Stream()
     res = []
     with torch.cuda.stream(side):
-        for extra in (B().FLAG_NO_GRAPH, 0):
+        for extra in (B().FLAG_NO_GRAPH, B().FLAG_NO_DEFER, 0):
             al, gr, st, _ = B().svm_solve(A, dev(p.y), kb, 2, 0.5, 32, 32 * 11 + 7, seed=9, prec=prec, tol=1e-3,
                                           check_every=3, flags=f | extra | B().FLAG_REFRESH,
                                           stream=side.cuda_stream)
             res.append((al.cpu().numpy(), gr.cpu().numpy(), st))
         side.synchronize()
-    assert res[0][2]["iters_done"] == res[1][2]["iters_done"]
+    assert res[0][2]["iters_done"] == res[1][2]["iters_done"] == res[2][2]["iters_done"]
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[2][2]["gpu_launches_per_step"] == res[1][2]["gpu_launches_per_step"] + 3
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    a0, a2 = res[0][0], res[2][0]
+    assert np.linalg.norm(a2 - a0) <= tol * np.linalg.norm(a0)
+    assert np.max(np.abs(res[2][1] - res[0][1])) <= tol * max(1.0, np.max(np.abs(res[0][1])))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x3", 1e-5)])
+def test_svm_deferred_step_on_csr_matches_oracle(prec, tol):
+    """The deferred K-SVM step on CSR data (squared hinge, s = 32, through the
+    transposed copy) against the oracle's DCD on the same index sequence,
+    dense rows of the matrix (m = 3000: rows recur within and across steps)."""
+    p = inputs.sparse_csr(m=3000, n=2000, nnz_per_row=12, seed=6)
+    A = lib_csr(p, np.float64 if prec == "fp64" else np.float32)
+    kb, ko = B().kernel("poly", coef0=1.0, degree=3), oracle.kernel("poly", coef0=1.0, degree=3)
+    side = torch.cuda.Stream()
+    H = 32 * 20 + 11
+    with torch.cuda.stream(side):
+        al, _, st, rc = B().svm_solve(A, dev(p.y), kb, 2, 0.5, 32, H, seed=4, prec=prec, stream=side.cuda_stream)
+        side.synchronize()
+    assert rc == B().OK and st["iters_done"] == H
+    want = oracle.dcd_svm(p.to_dense(), p.y, ko, 2, 0.5, H, seed=4)  # float32 values, exact in FP64
+    got = al.cpu().numpy()
+    assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
 
 
 def test_krr_lookahead_on_csr_matches_one_stream_steps(sparse):

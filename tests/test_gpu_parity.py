@@ -437,10 +437,15 @@ def test_lookahead_matches_one_stream_steps(prec, fp8):
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "fp16", "bf16"])
 @pytest.mark.parametrize("loss", [1, 2])
 def test_svm_lookahead_matches_one_stream_steps(prec, loss):
-    """The K-SVM look-ahead (the next step's sample and Gram on a second
-    stream, two buffer sets, step graphs) gives the iterates of the one-stream
-    steps bit for bit, with duality-gap checks and gradient recomputations
-    between steps and a short last step."""
+    """The K-SVM look-ahead with in-order steps (the next step's sample and
+    Gram on a second stream, two buffer sets, step graphs) gives the iterates
+    of the one-stream steps bit for bit, with duality-gap checks and gradient
+    recomputations between steps and a short last step.  In FP64 the default
+    is the deferred step (the recurrence one step ahead, beside the block, on
+    a snapshot of alpha and g plus the previous step's part): the same
+    iterates up to the association of the sums (1e-10 relative), with the
+    snapshot, the s x s cross product and the pending parts as three more
+    kernels per step; the tensor-core forms keep the in-order look-ahead."""
     p = inputs.blobs(m=1500, n=48, seed=17)
     A = p.A.astype(np.float32)
     kb = B().kernel("rbf", gamma=1 / 64)
@@ -449,15 +454,68 @@ def test_svm_lookahead_matches_one_stream_steps(prec, loss):
     with torch.cuda.stream(side):
         Ad, yd = dev(A), dev(p.y)
         runs = []
-        for flags in (B().FLAG_NO_GRAPH, 0):
+        for flags in (B().FLAG_NO_GRAPH, B().FLAG_NO_DEFER, 0):
             al, gr, st, rc = B().svm_solve(Ad, yd, kb, loss, 1.0, s, H, seed=3, prec=prec, tol=1e-3, check_every=3,
                                            flags=flags | B().FLAG_REFRESH, stream=side.cuda_stream)
             runs.append((al, gr, st))
         side.synchronize()
-    (a0, g0, s0), (a1, g1, s1) = runs
-    assert s0["iters_done"] == s1["iters_done"] and s0["refreshes"] == s1["refreshes"]
+    (a0, g0, s0), (a1, g1, s1), (a2, g2, s2) = runs
+    assert s0["iters_done"] == s1["iters_done"] == s2["iters_done"]
+    assert s0["refreshes"] == s1["refreshes"] == s2["refreshes"]
     assert s1["gpu_launches_per_step"] > 0
     assert torch.equal(a0, a1) and torch.equal(g0, g1)
+    if prec == "fp64":
+        assert s2["gpu_launches_per_step"] == s1["gpu_launches_per_step"] + 3
+        assert rel(a2.cpu().numpy(), a0.cpu().numpy()) < 1e-10
+        assert np.max(np.abs(g2.cpu().numpy() - g0.cpu().numpy())) <= 1e-10 * max(1.0, float(g0.abs().max()))
+    else:
+        assert torch.equal(a0, a2) and torch.equal(g0, g2)
+
+
+@pytest.mark.parametrize("loss", [1, 2])
+@pytest.mark.parametrize("m,s,H", [(200, 64, 64 * 9 + 17), (1200, 8, 8 * 40), (700, 128, 128 * 4 + 1)])
+def test_svm_deferred_step_matches_oracle(loss, m, s, H):
+    """The deferred K-SVM step in FP64 against the oracle's DCD (Algorithm 1,
+    the same index sequence): rows sampled several times within a step and
+    across consecutive steps (m = 200 with s = 64) exercise the pending
+    alpha and the diagonal term of the squared hinge; the longest step the
+    one-block recurrence takes (s = 128); a short last step."""
+    p = inputs.blobs(m=m, n=24, seed=41)
+    kb, ko = B().kernel("rbf", gamma=0.1), oracle.kernel("rbf", gamma=0.1)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        al, gr, st, rc = B().svm_solve(dev(p.A), dev(p.y), kb, loss, 0.9, s, H, seed=13, prec="fp64",
+                                       stream=side.cuda_stream)
+        side.synchronize()
+    assert rc == B().OK and st["iters_done"] == H
+    want = oracle.dcd_svm(p.A, p.y, ko, loss, 0.9, H, seed=13)
+    assert rel(al.cpu().numpy(), want) < 1e-10
+    gw = oracle.svm_gradient(p.A, p.y, ko, loss, 0.9, want)
+    assert np.max(np.abs(gr.cpu().numpy() - gw)) < 1e-10 * max(1.0, np.max(np.abs(gw)))
+
+
+def test_svm_deferred_steps_split_over_calls_match_one_call():
+    """The deferred K-SVM step keeps the recurrence and the pending parts
+    computed ahead across dcd_plan_enqueue / dcd_plan_run calls: a solve in
+    pieces (with a short last step) gives the bits of the solve in one call."""
+    p = inputs.blobs(m=900, n=32, seed=5)
+    kb = B().kernel("rbf", gamma=0.05)
+    s, H = 16, 16 * 13 + 9
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        A, y = dev(p.A), dev(p.y)
+        ref = B().Plan(0, A, y, kb, 1.0, 1, s, H, seed=8, prec="fp64", loss=2)
+        ref.run(-1)
+        pl = B().Plan(0, A, y, kb, 1.0, 1, s, H, seed=8, prec="fp64", loss=2)
+        assert pl.enqueue(4) == 4
+        st, _ = pl.run(3)
+        assert pl.enqueue(2) == 2
+        st, _ = pl.run(-1)
+        assert st["iters_done"] == H and st["outer_steps"] == 14
+        side.synchronize()
+        assert torch.equal(ref.alpha, pl.alpha) and torch.equal(ref.grad, pl.grad)
+        ref.close()
+        pl.close()
 
 
 @pytest.mark.parametrize("prec,fp8,s,b", [("fp64", False, 8, 8), ("bf16x3", False, 48, 32), ("fp8", True, 40, 32),
