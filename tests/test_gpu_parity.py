@@ -494,6 +494,35 @@ def test_svm_deferred_step_matches_oracle(loss, m, s, H):
     assert np.max(np.abs(gr.cpu().numpy() - gw)) < 1e-10 * max(1.0, np.max(np.abs(gw)))
 
 
+@pytest.mark.parametrize("csr", [False, True])
+def test_svm_deferred_step_with_host_buffers_matches_device_buffers(csr):
+    """The end-to-end form the bench times: a solve through the C ABI with the
+    data, labels and alpha in host memory (copies in and out on the caller's
+    stream, the deferred K-SVM steps between them) gives the bits of the same
+    solve on device buffers on that stream."""
+    kb = B().kernel("poly", coef0=1.0, degree=3) if csr else B().kernel("rbf", gamma=0.05)
+    if csr:
+        p = inputs.sparse_csr(m=2500, n=3000, nnz_per_row=10, seed=12)
+        Ad = B().Csr(dev(p.row_ptr), dev(p.col_idx), dev(p.values), p.n)
+        Ah = B().Csr(p.row_ptr, p.col_idx, p.values, p.n)
+        prec, loss, C_ = "bf16x3", 2, 0.5
+    else:
+        p = inputs.blobs(m=1200, n=40, seed=12)
+        Ad, Ah = dev(p.A), np.ascontiguousarray(p.A)
+        prec, loss, C_ = "fp64", 1, 1.0
+    s, H = 16, 16 * 9 + 3
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ad, gd, sd, _ = B().svm_solve(Ad, dev(p.y), kb, loss, C_, s, H, seed=6, prec=prec,
+                                      stream=side.cuda_stream)
+        ah, gh, sh, _ = B().svm_solve(Ah, p.y.copy(), kb, loss, C_, s, H, seed=6, prec=prec,
+                                      flags=B().FLAG_HOST_IO, stream=side.cuda_stream)
+        side.synchronize()
+    assert sd["iters_done"] == sh["iters_done"] == H
+    assert sd["gpu_launches_per_step"] == sh["gpu_launches_per_step"] > 0
+    assert np.array_equal(ad.cpu().numpy(), ah) and np.array_equal(gd.cpu().numpy(), gh)
+
+
 def test_svm_deferred_steps_split_over_calls_match_one_call():
     """The deferred K-SVM step keeps the recurrence and the pending parts
     computed ahead across dcd_plan_enqueue / dcd_plan_run calls: a solve in
