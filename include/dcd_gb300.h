@@ -130,9 +130,9 @@ typedef enum {
                                        paper's SpMM) even where the apply through the transposed copy would
                                        read less; both give the same bits (for comparison and testing) */
 #define DCD_FLAG_NO_DEFER 0x80  /* steps with the look-ahead (a stream of the caller's, graphs allowed, no
-                                   phase timers) of tensor-core K-RR, and of K-SVM on CSR or dense FP64 data
-                                   with s <= 128: run each step's recurrence after the previous step's block
-                                   and update, which it then overlaps no longer.  By default the recurrence
+                                   phase timers) of tensor-core K-RR, and of K-SVM with s <= 128: run each
+                                   step's recurrence after the previous step's block and update, which it
+                                   then overlaps no longer.  By default the recurrence
                                    of step k+1 runs beside the block of step k, on the gradient (K-SVM: and
                                    alpha) before that block plus the block's part at the rows step k+1
                                    samples (an s b x s b product) and the update's: the same sums up to

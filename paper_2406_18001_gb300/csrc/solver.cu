@@ -386,10 +386,9 @@ struct Solver {
                              !(o.flags & (DCD_FLAG_NO_GRAPH | DCD_FLAG_PHASE_TIMERS)) && st != nullptr &&
                              st != cudaStreamLegacy && st != cudaStreamPerThread;
         const bool set2 = la_pos || lag_pos;  // a second set of step buffers
-        // the deferred K-SVM step (the recurrence one step ahead of the block): CSR or dense FP64
-        // data, a step the one-block recurrence takes
-        const bool dfs_pos = lag_pos && problem == 0 && o.b == 1 && (csr || !tc) && o.s <= 128 &&
-                             !(o.flags & DCD_FLAG_NO_DEFER);
+        // the deferred K-SVM step (the recurrence one step ahead of the block): a step the one-block
+        // recurrence takes
+        const bool dfs_pos = lag_pos && problem == 0 && o.b == 1 && o.s <= 128 && !(o.flags & DCD_FLAG_NO_DEFER);
         const bool set3 = df_pos || dfs_pos;  // a third set
         const int64_t n_pad_r = sliced_ref ? (n + 63) / 64 * 64 : (n + 31) / 32 * 32;
         const size_t row_bytes_r = ref_op ? (size_t)packed_row_bytes(kind_r, n_pad_r) : 0;
@@ -449,9 +448,9 @@ struct Solver {
             // the deferred gradient: a third set, the recurrence's outputs per set, x per set and the
             // cross product's split
             int32_t *sidx_c = (int32_t *)ar.take(set3 ? sizeof(int32_t) * col_pad : 0);
-            void *as_c = ar.take(df_pos ? (size_t)sb * row_bytes : 0, 1024);
-            float *ch_c = (float *)ar.take(df_pos ? sizeof(float) * col_pad : 0);
-            float *cs_c = (float *)ar.take(df_pos && scaled ? sizeof(float) * col_pad : 0);
+            void *as_c = ar.take(set3 && tcd ? (size_t)sb * row_bytes : 0, 1024);
+            float *ch_c = (float *)ar.take(set3 ? sizeof(float) * col_pad : 0);
+            float *cs_c = (float *)ar.take(set3 && scaled ? sizeof(float) * col_pad : 0);
             void *kss_c = ar.take(set3 ? (size_t)sb * sb * (tc ? 4 : 8) : 0);
             double *lb_c = (double *)ar.take(df_pos ? recur_bdcd_scratch_bytes(o.s, o.b) : 0);
             double *dfd = (double *)ar.take(set3 ? 4 * sizeof(double) * col_pad : 0);  // delta, w64 of sets 1, 2
@@ -640,6 +639,9 @@ struct Solver {
         if (dfs_pos) {
             for (int q = 1; q < 3; ++q) DCD_TRY(cudaMemsetAsync(sbuf[q].col_w, 0, sizeof(float) * col_pad, st));
             DCD_TRY(cudaMemsetAsync(sbuf[2].S, 0, sizeof(int32_t) * col_pad, st));
+            DCD_TRY(cudaMemsetAsync(sbuf[2].col_h, 0, sizeof(float) * col_pad, st));
+            if (tcd) DCD_TRY(cudaMemsetAsync(sbuf[2].As, 0, (size_t)sb * row_bytes, st));
+            if (scaled) DCD_TRY(cudaMemsetAsync(sbuf[2].col_s, 0, sizeof(float) * col_pad, st));
             DCD_TRY(cudaMemsetAsync(dfs_v[0][0], 0, 12 * sizeof(double) * col_pad, st));
             for (cudaEvent_t *ev : {&df_fork, &df_chained, &df_rows, &df_side, &df_kx})
                 DCD_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
@@ -1448,12 +1450,20 @@ struct Solver {
     void *dfs_kx = nullptr;    // s x s kernel values (FP32 when tc, else FP64), row-major
     cudaEvent_t df_kx = nullptr;
 
-    // K(A_S(q2) rows, A_S(q) columns) into dfs_kx on stream s2 (the column map of set q)
+    // K(A_S(q2) rows, A_S(q) columns) into dfs_kx on stream s2 (CSR: the column map of set q;
+    // tensor-core form: both sets' gathered rows)
     cudaError_t dfs_cross(int q2, int q, int64_t cnt, cudaStream_t s2)
     {
         if (csr)
             return launch_csr_block(ca, cm_set[q], !tc, kp, sbuf[q2].S, cnt, sbuf[q].S, cnt, nullptr, nullptr,
                                     nullptr, nullptr, dfs_kx, cnt, s2);
+        if (tc) {
+            const StepBufs &R = sbuf[q2], &Cq = sbuf[q];
+            TcOperand Ro{R.As, cnt, op.n_pad, op.kind, R.col_s, R.S};
+            TcOperand Co{Cq.As, cnt, op.n_pad, op.kind, Cq.col_s, Cq.S};
+            return launch_block_tc(Ro, Co, kp, R.col_h, Cq.col_h, nullptr, nullptr, nullptr, (float *)dfs_kx, cnt, cnt,
+                                   cnt, err, s2);
+        }
         return launch_block_simt_f64(op.a64, op.lda, m, n, kp, sbuf[q2].S, cnt, sbuf[q].S, cnt, nullptr, nullptr,
                                      nullptr, (double *)dfs_kx, cnt, err, s2);
     }
@@ -1510,6 +1520,8 @@ struct Solver {
         const double *rs = y;
         if (csr)
             DCD_TRY(csr_apply(ncols, rs));
+        else if (tc)
+            DCD_TRY(block_tc_apply(ncols, rs));  // (every set's coefficients past sb stay zero)
         else
             DCD_TRY(launch_block_simt_f64(op.a64, op.lda, m, n, kp, nullptr, m, S, ncols, w64, rs, g, nullptr, 0,
                                           err, st));
@@ -1577,6 +1589,7 @@ struct Solver {
         la_cnt = has1 ? o.s : 0;  // the products of the next step are in place
         la_par = nxt < 2 ? nxt : 0;
         use_bufs(cur);  // the set just used is free (for a gradient recomputation)
+        col_w_hi = std::max<int64_t>(col_w_hi, sb);  // any set's coefficients may fill sb entries
         return DCD_OK;
     }
 
@@ -1584,7 +1597,8 @@ struct Solver {
     // Step k+1's sample (from ctr_la, as above), its column map (CSR) or gathered rows (dense
     // tensor-core form) and its Gram, into buffer set q on stream s2; the helpers enqueue on the
     // plan's stream member, pointed at s2 meanwhile.  The sample leaves the following position in
-    // ctr_la[qnext] (1 - q by default); `sampled` (optional) is recorded after it.
+    // ctr_la[qnext] (1 - q by default); `sampled` (optional) is recorded after it (after the
+    // gathered rows in the dense tensor-core form).
     dcd_status lag_side(int q, int64_t cnt, cudaStream_t s2, int qnext = -1, cudaEvent_t sampled = nullptr)
     {
         const cudaStream_t keep = st;
@@ -1593,8 +1607,10 @@ struct Solver {
         const int64_t ncols = cnt * o.b;
         cudaError_t e =
             launch_sample(problem, o.seed, ctr_la + q, 0, m, o.b, cnt, S, err, st, ctr_la + (qnext < 0 ? 1 - q : qnext));
-        if (e == cudaSuccess && sampled) e = cudaEventRecord(sampled, st);
+        const bool rows_gathered = tc && !csr;  // the cross product reads the gathered rows
+        if (e == cudaSuccess && sampled && !rows_gathered) e = cudaEventRecord(sampled, st);
         if (e == cudaSuccess) e = gather(ncols);
+        if (e == cudaSuccess && sampled && rows_gathered) e = cudaEventRecord(sampled, st);
         if (e == cudaSuccess) e = gram(ncols);
         st = keep;
         return cuda_status(e);
