@@ -522,6 +522,28 @@ def test_svm_deferred_step_with_host_buffers_matches_device_buffers(csr):
     assert np.array_equal(ad.cpu().numpy(), ah) and np.array_equal(gd.cpu().numpy(), gh)
 
 
+@pytest.mark.parametrize("kind,kw", [("poly", dict(coef0=1.0, degree=3)), ("linear", {})])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("bf16x3", 1e-4)])
+def test_svm_deferred_step_other_kernels_match_oracle(kind, kw, prec, tol):
+    """The deferred K-SVM step with the polynomial and linear kernels (the
+    s x s cross product and the block in the same kernel family), squared
+    hinge, s = 32 with rows recurring across steps (m = 300), against the
+    oracle's DCD on the same index sequence."""
+    p = inputs.blobs(m=300, n=20, seed=44)
+    A = p.A / np.sqrt(20.0)
+    kb, ko = B().kernel(kind, **kw), oracle.kernel(kind, **kw)
+    side = torch.cuda.Stream()
+    H = 32 * 12 + 5
+    with torch.cuda.stream(side):
+        Ad = dev(A if prec == "fp64" else A.astype(np.float32))
+        al, _, st, rc = B().svm_solve(Ad, dev(p.y), kb, 2, 0.7, 32, H, seed=21, prec=prec, stream=side.cuda_stream)
+        side.synchronize()
+    assert rc == B().OK and st["iters_done"] == H
+    Ar = A if prec == "fp64" else A.astype(np.float32).astype(np.float64)
+    want = oracle.dcd_svm(Ar, p.y, ko, 2, 0.7, H, seed=21)
+    assert rel(al.cpu().numpy(), want) < tol
+
+
 def test_svm_deferred_steps_split_over_calls_match_one_call():
     """The deferred K-SVM step keeps the recurrence and the pending parts
     computed ahead across dcd_plan_enqueue / dcd_plan_run calls: a solve in
